@@ -1,0 +1,763 @@
+/*
+ * oracle.c -- plain, slow, FP64 CPU reference of the democratic-heliocentric
+ * (DH) hybrid symplectic step of Moore & Quillen, "QYMSYM: A GPU-accelerated
+ * hybrid symplectic integrator that permits close encounters".
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load this library. The CUDA product path never calls it
+ * and shares no code, header or table with it.
+ *
+ * Everything is written for readability: explicit loops, one body at a time,
+ * array-of-structures [rows][3] float64, star at row 0 with Q0 = P0 = 0.
+ * Compile with -O2 -ffp-contract=off and no fast-math.
+ *
+ * Paper passages followed (section / equation numbers of the paper):
+ *   Sec. 2, Eqs. 1-4   H = H_Dft + H_Kep + H_Int in heliocentric Q, barycentric P
+ *   Sec. 2, Eq. 5      step E_Dft(tau/2) E_Int(tau/2) E_Kep(tau) E_Int(tau/2) E_Dft(tau/2)
+ *   Sec. 2             star kept at index 0, its mass zeroed in H_Int, restored for energy
+ *   Sec. 2.1, Eqs. 6-8 transition function K(y), y = 1.1 q / r_crit - 0.1
+ *   Sec. 2.2           Hermite accelerations and jerks with [1 - K + s K'], r_crit (Eq. 9)
+ *   Sec. 2.3           the 10-item per-step procedure (hybrid integration)
+ *   Sec. 2.4           rigorous encounter test: third-order interpolation of the
+ *                      minimum separation vs a_E times the sum of Hill radii
+ *   Appendix           universal-variable f and g functions, Stumpff C and S,
+ *                      F, F', F'' and the Laguerre iteration (n = 5)
+ *
+ * Readings of passages that are silent or garbled (each is also listed in the
+ * design notes of the repository):
+ *   R1 Laguerre update: x <- x - n F / (F' + sgn(F') sqrt|(n-1)^2 F'^2 - n(n-1) F F''|).
+ *   R2 mu = G m0 (the Kepler term uses the star mass only); sqrt(mu) where the
+ *      appendix writes sqrt(mu).
+ *   R3 fdot = sqrt(mu) x (alpha x^2 S(alpha x^2) - 1) / (r r0), r = F'(x).
+ *   R4 Hermite force and jerk carry an overall minus sign (attraction); the
+ *      star jerk term uses s_i0^3.
+ *   R5 K, K', K'' are taken with respect to the separation s (chain factor
+ *      1.1 / r_crit included); the kick corrections use the unsmoothed q.
+ *   R6 Hill radius r_H,i = a_i (m_i / (3 m0))^(1/3), a_i = 1/alpha_i from the
+ *      state entering the Kepler step when alpha_i > 0, else |Q_i|.
+ *   R7 rigorous test: cubic Hermite interpolant of d^2(t) = |dQ(t)|^2 on
+ *      [0, tau] from values and slopes at both ends; the minimum over [0, tau]
+ *      (clamped at 0) is compared with (a_E (r_H,i + r_H,j))^2.
+ *   R9 Hermite: 4th-order predictor / evaluate / corrector (PEC), Aarseth step
+ *      criterion with eta, start-up step eta_s |a| / |adot|, one shared step
+ *      per encounter set, the last step clipped to land on tau.
+ *   R10 the Hermite integration starts from (q0, v0) after the first kick and
+ *      the K correction.
+ *   R12 Stumpff series used for |y| < 0.1, summed to the y^8 term.
+ *   R13 Kepler iteration stops when |F| <= 1e-14 (sqrt(mu)|dt| + r0|x|) or
+ *      |dx| <= 2^-50 |x|.
+ *   R14 standard starting guess x0 = sqrt(mu) dt / r0; the paper's x0 = r0 is
+ *      kept as a separate guess mode.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+
+typedef struct {
+    double G, a_E, a_H, eps_H, eta, eta_s;
+    int32_t solver;            /* 0 Laguerre n=5 (Appendix), 1 Newton */
+    int32_t guess;             /* 0 sqrt(mu) dt / r0, 1 x0 = r0 (Appendix) */
+    int32_t encounters;        /* 0 plain DH step, 1 hybrid step with encounters */
+    int32_t max_kepler_iter;
+    int64_t max_hermite_steps;
+} or_params;
+
+/* ------------------------------------------------------------------ */
+/* small vector helpers                                                */
+/* ------------------------------------------------------------------ */
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* ------------------------------------------------------------------ */
+/* Appendix: Stumpff functions C(y), S(y) (Eqs. 2.40 of Prussing)      */
+/* ------------------------------------------------------------------ */
+void or_stumpff(double y, double *C, double *S)
+{
+    if (fabs(y) < 0.1) {
+        /* C = 1/2! - y/4! + y^2/6! - ...,  S = 1/3! - y/5! + y^2/7! - ... */
+        double c = 0.0, s = 0.0, term_c = 0.5, term_s = 1.0 / 6.0;
+        for (int k = 0; k <= 8; ++k) {
+            c += term_c;
+            s += term_s;
+            term_c *= -y / ((2.0 * k + 3.0) * (2.0 * k + 4.0));
+            term_s *= -y / ((2.0 * k + 4.0) * (2.0 * k + 5.0));
+        }
+        *C = c;
+        *S = s;
+    } else if (y > 0.0) {
+        double sy = sqrt(y);
+        *C = (1.0 - cos(sy)) / y;
+        *S = (sy - sin(sy)) / (sy * sy * sy);
+    } else {
+        double sy = sqrt(-y);
+        *C = (cosh(sy) - 1.0) / (-y);
+        *S = (sinh(sy) - sy) / (sy * sy * sy);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Appendix: F(x), F'(x), F''(x) of the universal Kepler equation       */
+/*   sig = (r0 . v0) / sqrt(mu)                                        */
+/* ------------------------------------------------------------------ */
+void or_kepler_F(double x, double sqmu, double dt, double r0, double sig, double alpha,
+                 double *F, double *Fp, double *Fpp)
+{
+    double y = alpha * x * x, C, S;
+    or_stumpff(y, &C, &S);
+    double b = 1.0 - r0 * alpha;
+    *F = -sqmu * dt + sig * x * x * C + b * x * x * x * S + r0 * x;
+    *Fp = sig * x * (1.0 - y * S) + b * x * x * C + r0;
+    *Fpp = sig * (1.0 - y * C) + b * x * (1.0 - y * S);
+}
+
+/* Solve F(x) = 0 from x (in/out). solver 0: Laguerre n = 5 (R1); 1: Newton.
+ * Returns 0 on convergence (R13), 1 when max_iter updates did not converge. */
+int or_kepler_solve(double sqmu, double dt, double r0, double sig, double alpha,
+                    int solver, int max_iter, double *x_io, int32_t *iters)
+{
+    const double n = 5.0;
+    double x = *x_io;
+    double scale = sqmu * fabs(dt);
+    int it;
+    for (it = 0; it < max_iter; ++it) {
+        double F, Fp, Fpp;
+        or_kepler_F(x, sqmu, dt, r0, sig, alpha, &F, &Fp, &Fpp);
+        if (fabs(F) <= 1e-14 * (scale + r0 * fabs(x))) {
+            *x_io = x;
+            *iters = it;
+            return 0;
+        }
+        double dx;
+        if (solver == 0) {
+            double disc = fabs((n - 1.0) * (n - 1.0) * Fp * Fp - n * (n - 1.0) * F * Fpp);
+            double den = Fp + (Fp >= 0.0 ? 1.0 : -1.0) * sqrt(disc);
+            dx = n * F / den;
+        } else {
+            dx = F / Fp;
+        }
+        x -= dx;
+        if (fabs(dx) <= 0x1p-50 * fabs(x)) {
+            *x_io = x;
+            *iters = it + 1;
+            return 0;
+        }
+    }
+    *x_io = x;
+    *iters = it;
+    return 1;
+}
+
+/* Appendix: advance one body on its Kepler orbit about the star for dt with
+ * universal-variable f and g functions. x_guess is used when guess == 2.
+ * Returns the solver status; writes x and the iteration count. */
+int or_kepler_body(const double *q0, const double *v0, double *q1, double *v1, double mu,
+                   double dt, int solver, int guess, double x_guess, int max_iter,
+                   double *x_out, int32_t *iters_out)
+{
+    double sqmu = sqrt(mu);
+    double r0 = sqrt(dot3(q0, q0));
+    double v2 = dot3(v0, v0);
+    double alpha = 2.0 / r0 - v2 / mu;
+    double sig = dot3(q0, v0) / sqmu;
+    double x;
+    if (guess == 0)
+        x = sqmu * dt / r0;
+    else if (guess == 1)
+        x = r0;
+    else
+        x = x_guess;
+    int32_t it = 0;
+    int st = or_kepler_solve(sqmu, dt, r0, sig, alpha, solver, max_iter, &x, &it);
+    if (st != 0 && guess == 2) {
+        /* fallback: Laguerre from the standard guess */
+        int32_t it2 = 0;
+        x = sqmu * dt / r0;
+        st = or_kepler_solve(sqmu, dt, r0, sig, alpha, 0, max_iter, &x, &it2);
+        it += it2;
+    }
+    double y = alpha * x * x, C, S;
+    or_stumpff(y, &C, &S);
+    double f = 1.0 - x * x / r0 * C;
+    double g = dt - x * x * x / sqmu * S;
+    for (int k = 0; k < 3; ++k) q1[k] = f * q0[k] + g * v0[k];
+    double r = sqrt(dot3(q1, q1));
+    double fdot = sqmu * x * (y * S - 1.0) / (r * r0);
+    double gdot = 1.0 - x * x / r * C;
+    for (int k = 0; k < 3; ++k) v1[k] = fdot * q0[k] + gdot * v0[k];
+    if (x_out) *x_out = x;
+    if (iters_out) *iters_out = it;
+    return st;
+}
+
+/* E_Kep for bodies [0, n) (no star row). Returns the number of bodies whose
+ * iteration did not converge. */
+int64_t or_kepler_drift(int64_t n, const double *q0, const double *v0, double *q1, double *v1,
+                        double mu, double dt, int32_t solver, int32_t guess,
+                        const double *x_guess, int32_t max_iter, double *x_out, int32_t *iters_out)
+{
+    int64_t bad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double x;
+        int32_t it;
+        int st = or_kepler_body(q0 + 3 * i, v0 + 3 * i, q1 + 3 * i, v1 + 3 * i, mu, dt, solver,
+                                guess, x_guess ? x_guess[i] : 0.0, max_iter, &x, &it);
+        if (x_out) x_out[i] = x;
+        if (iters_out) iters_out[i] = it;
+        if (st) ++bad;
+    }
+    return bad;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2: E_Dft -- sum of barycentric momenta, uniform shift of Q      */
+/* ------------------------------------------------------------------ */
+void or_momentum(int64_t rows, const double *m, const double *v, double *S)
+{
+    S[0] = S[1] = S[2] = 0.0;
+    for (int64_t i = 1; i < rows; ++i)
+        for (int k = 0; k < 3; ++k) S[k] += m[i] * v[3 * i + k];
+}
+
+void or_drift(int64_t rows, const double *m, double *q, const double *v, double dt)
+{
+    double S[3];
+    or_momentum(rows, m, v, S);
+    for (int64_t i = 1; i < rows; ++i)
+        for (int k = 0; k < 3; ++k) q[3 * i + k] += dt * S[k] / m[0];
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2, Eq. 4: E_Int acceleration, star excluded (its mass zeroed)   */
+/*   a_i = - sum_{j>=1, j!=i} G m_j (Q_i - Q_j) / |Q_i - Q_j|^3         */
+/* ------------------------------------------------------------------ */
+void or_accel_row(int64_t rows, const double *m, const double *q, double G, int64_t i, double *a)
+{
+    a[0] = a[1] = a[2] = 0.0;
+    for (int64_t j = 1; j < rows; ++j) {
+        if (j == i) continue;
+        double d[3] = {q[3 * i] - q[3 * j], q[3 * i + 1] - q[3 * j + 1], q[3 * i + 2] - q[3 * j + 2]};
+        double r2 = dot3(d, d);
+        double r = sqrt(r2);
+        double w = G * m[j] / (r2 * r);
+        for (int k = 0; k < 3; ++k) a[k] -= w * d[k];
+    }
+}
+
+void or_accel_int(int64_t rows, const double *m, const double *q, double G, double *a)
+{
+    a[0] = a[1] = a[2] = 0.0;
+    for (int64_t i = 1; i < rows; ++i) or_accel_row(rows, m, q, G, i, a + 3 * i);
+}
+
+/* accelerations of selected rows only (sampled parity at large sizes) */
+void or_accel_rows(int64_t rows, const double *m, const double *q, double G, int64_t nsel,
+                   const int64_t *sel, double *a)
+{
+    for (int64_t k = 0; k < nsel; ++k) or_accel_row(rows, m, q, G, sel[k], a + 3 * k);
+}
+
+void or_kick(int64_t rows, const double *m, const double *q, double *v, double G, double dt)
+{
+    double *a = (double *)malloc(sizeof(double) * 3 * rows);
+    or_accel_int(rows, m, q, G, a);
+    for (int64_t i = 1; i < rows; ++i)
+        for (int k = 0; k < 3; ++k) v[3 * i + k] += dt * a[3 * i + k];
+    free(a);
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2, Eqs. 2-4: total energy H_Dft + H_Kep + H_Int (per unit of    */
+/* the DH variables: P_i = m_i v_i), star mass restored for the sum     */
+/* ------------------------------------------------------------------ */
+double or_energy(int64_t rows, const double *m, const double *q, const double *v, double G)
+{
+    double S[3];
+    or_momentum(rows, m, v, S);
+    double E = dot3(S, S) / (2.0 * m[0]);
+    for (int64_t i = 1; i < rows; ++i) {
+        E += 0.5 * m[i] * dot3(v + 3 * i, v + 3 * i);
+        E -= G * m[0] * m[i] / sqrt(dot3(q + 3 * i, q + 3 * i));
+    }
+    for (int64_t i = 1; i < rows; ++i)
+        for (int64_t j = i + 1; j < rows; ++j) {
+            double d[3] = {q[3 * i] - q[3 * j], q[3 * i + 1] - q[3 * j + 1], q[3 * i + 2] - q[3 * j + 2]};
+            E -= G * m[i] * m[j] / sqrt(dot3(d, d));
+        }
+    return E;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2: heliocentric velocities <-> barycentric velocities (P/m)     */
+/* ------------------------------------------------------------------ */
+void or_helio_to_dh(int64_t rows, const double *m, double *v)
+{
+    double mt = m[0], s[3] = {0, 0, 0};
+    for (int64_t i = 1; i < rows; ++i) {
+        mt += m[i];
+        for (int k = 0; k < 3; ++k) s[k] += m[i] * v[3 * i + k];
+    }
+    for (int64_t i = 1; i < rows; ++i)
+        for (int k = 0; k < 3; ++k) v[3 * i + k] -= s[k] / mt;
+    v[0] = v[1] = v[2] = 0.0;
+}
+
+void or_dh_to_helio(int64_t rows, const double *m, double *v)
+{
+    double S[3];
+    or_momentum(rows, m, v, S);
+    /* star barycentric velocity V0 = -S / m0; heliocentric v_i = V_i - V0 */
+    for (int64_t i = 1; i < rows; ++i)
+        for (int k = 0; k < 3; ++k) v[3 * i + k] += S[k] / m[0];
+    v[0] = v[1] = v[2] = 0.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2.2 (Eq. 9) and reading R6: Hill radii                         */
+/* ------------------------------------------------------------------ */
+void or_hill_radii(int64_t rows, const double *m, const double *q, const double *v, double G,
+                   double *rH)
+{
+    double mu = G * m[0];
+    rH[0] = 0.0;
+    for (int64_t i = 1; i < rows; ++i) {
+        double r = sqrt(dot3(q + 3 * i, q + 3 * i));
+        double alpha = 2.0 / r - dot3(v + 3 * i, v + 3 * i) / mu;
+        double a = alpha > 0.0 ? 1.0 / alpha : r;
+        rH[i] = a * cbrt(m[i] / (3.0 * m[0]));
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2.4, reading R7: minimum over [0, tau] of the cubic that         */
+/* interpolates d^2(t) = |dQ(t)|^2 from its values and slopes at 0, tau */
+/* ------------------------------------------------------------------ */
+double or_pair_dmin2(const double *dq0, const double *dv0, const double *dq1, const double *dv1,
+                     double tau)
+{
+    double d0 = dot3(dq0, dq0);
+    double d1 = dot3(dq1, dq1);
+    double s0 = 2.0 * dot3(dq0, dv0) * tau;   /* d(d^2)/du at u = 0, u = t / tau */
+    double s1 = 2.0 * dot3(dq1, dv1) * tau;   /* d(d^2)/du at u = 1 */
+    /* p(u) = c0 + c1 u + c2 u^2 + c3 u^3 (cubic Hermite basis expanded) */
+    double c0 = d0;
+    double c1 = s0;
+    double c2 = 3.0 * (d1 - d0) - 2.0 * s0 - s1;
+    double c3 = 2.0 * (d0 - d1) + s0 + s1;
+    double best = d0 < d1 ? d0 : d1;
+    /* stationary points: 3 c3 u^2 + 2 c2 u + c1 = 0, roots from the
+     * cancellation-free form w = -(B + sgn(B) sqrt(disc)) / 2, u = w/A, Cc/w
+     * (c3 is ~0 whenever the relative motion is nearly straight) */
+    double A = 3.0 * c3, B = 2.0 * c2, Cc = c1;
+    double u[2];
+    int nu = 0;
+    double disc = B * B - 4.0 * A * Cc;
+    if (disc >= 0.0) {
+        double w = -0.5 * (B + (B >= 0.0 ? 1.0 : -1.0) * sqrt(disc));
+        if (A != 0.0) u[nu++] = w / A;
+        if (w != 0.0) u[nu++] = Cc / w;
+    }
+    for (int k = 0; k < nu; ++k) {
+        if (u[k] > 0.0 && u[k] < 1.0) {
+            double p = c0 + u[k] * (c1 + u[k] * (c2 + u[k] * c3));
+            if (p < best) best = p;
+        }
+    }
+    return best > 0.0 ? best : 0.0;
+}
+
+static void pair_diffs(const double *q0, const double *v0, const double *q1, const double *v1,
+                       int64_t i, int64_t j, double *dq0, double *dv0, double *dq1, double *dv1)
+{
+    for (int k = 0; k < 3; ++k) {
+        dq0[k] = q0[3 * i + k] - q0[3 * j + k];
+        dv0[k] = v0[3 * i + k] - v0[3 * j + k];
+        dq1[k] = q1[3 * i + k] - q1[3 * j + k];
+        dv1[k] = v1[3 * i + k] - v1[3 * j + k];
+    }
+}
+
+/* Sec. 2.4 over ALL pairs 1 <= i < j (brute force; no crude pre-filter).
+ * Writes up to cap pairs (i, j), i < j, in ascending (i, j) order, with their
+ * d_min^2 and threshold^2; returns the number found. */
+int64_t or_encounters(int64_t rows, const double *q0, const double *v0, const double *q1,
+                      const double *v1, const double *rH, double tau, double a_E, int64_t *pairs,
+                      double *d2, double *thr2, int64_t cap)
+{
+    int64_t cnt = 0;
+    for (int64_t i = 1; i < rows; ++i)
+        for (int64_t j = i + 1; j < rows; ++j) {
+            double dq0[3], dv0[3], dq1[3], dv1[3];
+            pair_diffs(q0, v0, q1, v1, i, j, dq0, dv0, dq1, dv1);
+            double R = a_E * (rH[i] + rH[j]);
+            double dm = or_pair_dmin2(dq0, dv0, dq1, dv1, tau);
+            if (dm < R * R) {
+                if (cnt < cap) {
+                    pairs[2 * cnt] = i;
+                    pairs[2 * cnt + 1] = j;
+                    if (d2) d2[cnt] = dm;
+                    if (thr2) thr2[cnt] = R * R;
+                }
+                ++cnt;
+            }
+        }
+    return cnt;
+}
+
+/* rigorous test of selected rows i against all j != i (sampled parity) */
+int64_t or_encounters_rows(int64_t rows, const double *q0, const double *v0, const double *q1,
+                           const double *v1, const double *rH, double tau, double a_E, int64_t nsel,
+                           const int64_t *sel, int64_t *pairs, double *d2, double *thr2, int64_t cap)
+{
+    int64_t cnt = 0;
+    for (int64_t s = 0; s < nsel; ++s) {
+        int64_t i = sel[s];
+        for (int64_t j = 1; j < rows; ++j) {
+            if (j == i) continue;
+            double dq0[3], dv0[3], dq1[3], dv1[3];
+            int64_t a = i < j ? i : j, b = i < j ? j : i;
+            pair_diffs(q0, v0, q1, v1, a, b, dq0, dv0, dq1, dv1);
+            double R = a_E * (rH[a] + rH[b]);
+            double dm = or_pair_dmin2(dq0, dv0, dq1, dv1, tau);
+            if (dm < R * R) {
+                if (cnt < cap) {
+                    pairs[2 * cnt] = a;
+                    pairs[2 * cnt + 1] = b;
+                    if (d2) d2[cnt] = dm;
+                    if (thr2) thr2[cnt] = R * R;
+                }
+                ++cnt;
+            }
+        }
+    }
+    return cnt;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2.3 item 4: non-intersecting encounter sets (connected          */
+/* components of the pair graph) and r_crit (Eq. 9) per set             */
+/* ------------------------------------------------------------------ */
+static int64_t uf_find(int64_t *parent, int64_t x)
+{
+    while (parent[x] != x) x = parent[x];
+    return x;
+}
+
+/* set_of[rows]: set id or -1. Sets are numbered by ascending smallest
+ * member; members ascending within a set. Returns the number of sets. */
+int64_t or_sets(int64_t rows, int64_t npairs, const int64_t *pairs, const double *rH, double a_H,
+                int64_t *set_of, int64_t *set_start, int64_t *members, double *rcrit)
+{
+    int64_t *parent = (int64_t *)malloc(sizeof(int64_t) * rows);
+    for (int64_t i = 0; i < rows; ++i) parent[i] = i;
+    for (int64_t p = 0; p < npairs; ++p) {
+        int64_t a = uf_find(parent, pairs[2 * p]), b = uf_find(parent, pairs[2 * p + 1]);
+        if (a == b) continue;
+        if (a < b) parent[b] = a; else parent[a] = b;   /* root = smallest index */
+    }
+    char *inv = (char *)calloc(rows, 1);
+    for (int64_t p = 0; p < 2 * npairs; ++p) inv[pairs[p]] = 1;
+    int64_t nsets = 0;
+    for (int64_t i = 0; i < rows; ++i) set_of[i] = -1;
+    for (int64_t i = 0; i < rows; ++i)
+        if (inv[i] && uf_find(parent, i) == i) set_of[i] = nsets++;
+    for (int64_t i = 0; i < rows; ++i)
+        if (inv[i]) set_of[i] = set_of[uf_find(parent, i)];
+    /* counting sort by set id, stable in particle index */
+    for (int64_t s = 0; s <= nsets; ++s) set_start[s] = 0;
+    for (int64_t i = 0; i < rows; ++i)
+        if (set_of[i] >= 0) set_start[set_of[i] + 1]++;
+    for (int64_t s = 0; s < nsets; ++s) set_start[s + 1] += set_start[s];
+    int64_t *fill = (int64_t *)calloc(nsets + 1, sizeof(int64_t));
+    for (int64_t i = 0; i < rows; ++i)
+        if (set_of[i] >= 0) {
+            int64_t s = set_of[i];
+            members[set_start[s] + fill[s]++] = i;
+        }
+    for (int64_t s = 0; s < nsets; ++s) {
+        double mx = 0.0;
+        for (int64_t k = set_start[s]; k < set_start[s + 1]; ++k)
+            if (rH[members[k]] > mx) mx = rH[members[k]];
+        rcrit[s] = a_H * mx;
+    }
+    free(fill);
+    free(inv);
+    free(parent);
+    return nsets;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2.1 and reading R5: K(s), dK/ds, d2K/ds2                       */
+/* ------------------------------------------------------------------ */
+void or_transition(double s, double rcrit, double *K, double *Kp, double *Kpp)
+{
+    double y = 1.1 * s / rcrit - 0.1;
+    double c = 1.1 / rcrit;
+    if (y <= 0.0) {
+        *K = 0.0; *Kp = 0.0; *Kpp = 0.0;
+    } else if (y >= 1.0) {
+        *K = 1.0; *Kp = 0.0; *Kpp = 0.0;
+    } else {
+        double ph = 0.5 * OR_PI * y;
+        *K = sin(ph);
+        *Kp = 0.5 * OR_PI * c * cos(ph);
+        *Kpp = -(0.5 * OR_PI * c) * (0.5 * OR_PI * c) * sin(ph);
+    }
+}
+
+/* Sec. 2.2 and Sec. 2.3 items 5 and 7: v_i -= dt * a^(1-K)_i summed over
+ * the other members of the set, with
+ *   a^(1-K)_ij = -G m_j q_ij / q^3 [1 - K(q) + q K'(q)]                 */
+void or_kcorr(int64_t nmem, const int64_t *mem, const double *m, const double *q, double *v,
+              double G, double rcrit, double dt)
+{
+    double *dv = (double *)calloc(3 * nmem, sizeof(double));
+    for (int64_t a = 0; a < nmem; ++a) {
+        int64_t i = mem[a];
+        for (int64_t b = 0; b < nmem; ++b) {
+            if (b == a) continue;
+            int64_t j = mem[b];
+            double d[3] = {q[3 * i] - q[3 * j], q[3 * i + 1] - q[3 * j + 1], q[3 * i + 2] - q[3 * j + 2]};
+            double r = sqrt(dot3(d, d));
+            double K, Kp, Kpp;
+            or_transition(r, rcrit, &K, &Kp, &Kpp);
+            double w = -G * m[j] / (r * r * r) * (1.0 - K + r * Kp);
+            for (int k = 0; k < 3; ++k) dv[3 * a + k] += w * d[k];
+        }
+    }
+    for (int64_t a = 0; a < nmem; ++a)
+        for (int k = 0; k < 3; ++k) v[3 * mem[a] + k] -= dt * dv[3 * a + k];
+    free(dv);
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2.2: Hermite accelerations and jerks of the set members, star   */
+/* fixed at the origin, pair terms weighted by the transition function  */
+/* ------------------------------------------------------------------ */
+void or_hermite_force(int64_t k, const double *mm, const double *x, const double *u, double G,
+                      double m0, double rcrit, double eps, double *a, double *jk)
+{
+    for (int64_t i = 0; i < k; ++i) {
+        double ai[3] = {0, 0, 0}, ji[3] = {0, 0, 0};
+        /* star term */
+        {
+            double s2 = dot3(x + 3 * i, x + 3 * i) + eps * eps;
+            double s = sqrt(s2);
+            double rv = dot3(x + 3 * i, u + 3 * i);
+            double w = -G * m0 / (s2 * s);
+            for (int c = 0; c < 3; ++c) {
+                ai[c] += w * x[3 * i + c];
+                ji[c] += w * (u[3 * i + c] - 3.0 * rv * x[3 * i + c] / s2);
+            }
+        }
+        for (int64_t j = 0; j < k; ++j) {
+            if (j == i) continue;
+            double d[3], dv[3];
+            for (int c = 0; c < 3; ++c) {
+                d[c] = x[3 * i + c] - x[3 * j + c];
+                dv[c] = u[3 * i + c] - u[3 * j + c];
+            }
+            double s2 = dot3(d, d) + eps * eps;
+            double s = sqrt(s2);
+            double K, Kp, Kpp;
+            or_transition(s, rcrit, &K, &Kp, &Kpp);
+            double br = 1.0 - K + s * Kp;
+            double rv = dot3(d, dv);
+            double w = -G * mm[j] / (s2 * s);
+            for (int c = 0; c < 3; ++c) {
+                ai[c] += w * br * d[c];
+                ji[c] += w * (rv * d[c] * Kpp + (dv[c] - 3.0 * rv * d[c] / s2) * br);
+            }
+        }
+        for (int c = 0; c < 3; ++c) {
+            a[3 * i + c] = ai[c];
+            jk[3 * i + c] = ji[c];
+        }
+    }
+}
+
+static double norm3(const double *a) { return sqrt(dot3(a, a)); }
+
+/* Sec. 2.2 and reading R9: integrate the members of one set over tau.
+ * q, v are full-system arrays; members are read and written in place.
+ * Returns 0, or 1 when max_steps was reached before tau. */
+int or_hermite_set(int64_t k, const int64_t *mem, const double *m, double m0, double *q, double *v,
+                   double G, double rcrit, double eps, double eta, double eta_s, double tau,
+                   int64_t max_steps, int64_t *steps_out)
+{
+    size_t b3 = sizeof(double) * 3 * k;
+    double *mm = (double *)malloc(sizeof(double) * k);
+    double *x = (double *)malloc(b3), *u = (double *)malloc(b3);
+    double *xp = (double *)malloc(b3), *up = (double *)malloc(b3);
+    double *a0 = (double *)malloc(b3), *j0 = (double *)malloc(b3);
+    double *a1 = (double *)malloc(b3), *j1 = (double *)malloc(b3);
+    for (int64_t i = 0; i < k; ++i) {
+        mm[i] = m[mem[i]];
+        for (int c = 0; c < 3; ++c) {
+            x[3 * i + c] = q[3 * mem[i] + c];
+            u[3 * i + c] = v[3 * mem[i] + c];
+        }
+    }
+    or_hermite_force(k, mm, x, u, G, m0, rcrit, eps, a0, j0);
+    /* start-up step, eta_s |a| / |adot|, shared by the set */
+    double dt = tau;
+    for (int64_t i = 0; i < k; ++i) {
+        double jn = norm3(j0 + 3 * i);
+        if (jn > 0.0) {
+            double h = eta_s * norm3(a0 + 3 * i) / jn;
+            if (h < dt) dt = h;
+        }
+    }
+    double t = 0.0;
+    int64_t steps = 0;
+    int status = 0;
+    while (t < tau) {
+        if (steps >= max_steps) { status = 1; break; }
+        double h = dt;
+        int last = 0;
+        if (t + h >= tau) { h = tau - t; last = 1; }
+        /* predictor */
+        for (int64_t i = 0; i < 3 * k; ++i) {
+            xp[i] = x[i] + h * (u[i] + h * (0.5 * a0[i] + h * j0[i] / 6.0));
+            up[i] = u[i] + h * (a0[i] + 0.5 * h * j0[i]);
+        }
+        or_hermite_force(k, mm, xp, up, G, m0, rcrit, eps, a1, j1);
+        /* corrector with a^(2), a^(3) from the endpoint a and adot */
+        double next = tau;
+        for (int64_t i = 0; i < k; ++i) {
+            double a2[3], a3[3];
+            for (int c = 0; c < 3; ++c) {
+                int id = 3 * i + c;
+                a2[c] = (-6.0 * (a0[id] - a1[id]) - h * (4.0 * j0[id] + 2.0 * j1[id])) / (h * h);
+                a3[c] = (12.0 * (a0[id] - a1[id]) + 6.0 * h * (j0[id] + j1[id])) / (h * h * h);
+                x[id] = xp[id] + h * h * h * h * (a2[c] / 24.0 + h * a3[c] / 120.0);
+                u[id] = up[id] + h * h * h * (a2[c] / 6.0 + h * a3[c] / 24.0);
+                a2[c] += h * a3[c];   /* a^(2) at the end of the step */
+            }
+            double na = norm3(a1 + 3 * i), nj = norm3(j1 + 3 * i);
+            double n2 = norm3(a2), n3 = norm3(a3);
+            double den = nj * n3 + n2 * n2;
+            if (den > 0.0) {
+                double hi = sqrt(eta * (na * n2 + nj * nj) / den);
+                if (hi < next) next = hi;
+            }
+        }
+        memcpy(a0, a1, b3);
+        memcpy(j0, j1, b3);
+        t = last ? tau : t + h;
+        dt = next;
+        ++steps;
+    }
+    for (int64_t i = 0; i < k; ++i)
+        for (int c = 0; c < 3; ++c) {
+            q[3 * mem[i] + c] = x[3 * i + c];
+            v[3 * mem[i] + c] = u[3 * i + c];
+        }
+    if (steps_out) *steps_out = steps;
+    free(mm); free(x); free(u); free(xp); free(up); free(a0); free(j0); free(a1); free(j1);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2, Eq. 5 and Sec. 2.3: one system, nsteps hybrid DH steps.      */
+/* q, v: DH state (heliocentric Q, barycentric v), star row zero.       */
+/* enc: (step, i, j) records up to enc_cap; *enc_count gets the total.  */
+/* stats[0..5]: encounter pairs, sets, largest set, Kepler iterations,  */
+/* Hermite steps, Kepler non-convergences (summed over steps).          */
+/* rH_fixed: NULL -> Hill radii from the orbit entering each Kepler step  */
+/* (reading R6); else per-body radii held fixed for the whole run.       */
+/* Returns 0, or a nonzero status (1 Kepler, 2 Hermite cap).            */
+/* ------------------------------------------------------------------ */
+int or_step(int64_t rows, const double *m, double *q, double *v, const or_params *p, double tau,
+            int64_t nsteps, int64_t step0, const double *rH_fixed, int64_t *enc, int64_t enc_cap,
+            int64_t *enc_count, int64_t *stats)
+{
+    const double G = p->G, m0 = m[0], mu = G * m0;
+    int64_t nb = rows - 1;
+    size_t b3 = sizeof(double) * 3 * rows;
+    double *q0 = (double *)malloc(b3), *v0 = (double *)malloc(b3);
+    double *rH = (double *)malloc(sizeof(double) * rows);
+    int32_t *its = (int32_t *)malloc(sizeof(int32_t) * (nb > 0 ? nb : 1));
+    int64_t pcap = 1024, *pairs = (int64_t *)malloc(sizeof(int64_t) * 2 * pcap);
+    int64_t *set_of = (int64_t *)malloc(sizeof(int64_t) * rows);
+    int64_t *set_start = (int64_t *)malloc(sizeof(int64_t) * (rows + 1));
+    int64_t *members = (int64_t *)malloc(sizeof(int64_t) * rows);
+    double *rcrit = (double *)malloc(sizeof(double) * rows);
+    int status = 0;
+    int64_t ne_total = enc_count ? *enc_count : 0;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        /* item 1: drift tau/2 */
+        or_drift(rows, m, q, v, 0.5 * tau);
+        /* item 2: interaction tau/2, all pairs, no transition function */
+        or_kick(rows, m, q, v, G, 0.5 * tau);
+        /* item 3: Kepler tau from (q0, v0) to (q, v); star row stays zero */
+        memcpy(q0, q, b3);
+        memcpy(v0, v, b3);
+        int64_t bad = or_kepler_drift(nb, q0 + 3, v0 + 3, q + 3, v + 3, mu, tau, p->solver, p->guess,
+                                      NULL, p->max_kepler_iter, NULL, its);
+        if (stats) {
+            for (int64_t i = 0; i < nb; ++i) stats[3] += its[i];
+            stats[5] += bad;
+        }
+        if (bad) status = 1;
+        if (p->encounters) {
+            /* item 4: rigorous test over all pairs; sets; r_crit */
+            if (rH_fixed)
+                memcpy(rH, rH_fixed, sizeof(double) * rows);
+            else
+                or_hill_radii(rows, m, q0, v0, G, rH);
+            int64_t npairs;
+            for (;;) {
+                npairs = or_encounters(rows, q0, v0, q, v, rH, tau, p->a_E, pairs, NULL, NULL, pcap);
+                if (npairs <= pcap) break;
+                pcap = 2 * npairs;
+                pairs = (int64_t *)realloc(pairs, sizeof(int64_t) * 2 * pcap);
+            }
+            for (int64_t k = 0; k < npairs; ++k) {
+                if (enc && ne_total < enc_cap) {
+                    enc[3 * ne_total] = step0 + s;
+                    enc[3 * ne_total + 1] = pairs[2 * k];
+                    enc[3 * ne_total + 2] = pairs[2 * k + 1];
+                }
+                ++ne_total;
+            }
+            if (npairs > 0) {
+                int64_t nsets = or_sets(rows, npairs, pairs, rH, p->a_H, set_of, set_start, members, rcrit);
+                if (stats) {
+                    stats[0] += npairs;
+                    stats[1] += nsets;
+                }
+                for (int64_t st = 0; st < nsets; ++st) {
+                    int64_t k0 = set_start[st], k = set_start[st + 1] - k0;
+                    if (stats && k > stats[2]) stats[2] = k;
+                    /* item 5: remove the (1-K) part of the first kick at q0 */
+                    or_kcorr(k, members + k0, m, q0, v0, G, rcrit[st], 0.5 * tau);
+                    /* item 6: Hermite over tau from (q0, v0); result into (q, v) */
+                    for (int64_t a = 0; a < k; ++a) {
+                        int64_t i = members[k0 + a];
+                        for (int c = 0; c < 3; ++c) {
+                            q[3 * i + c] = q0[3 * i + c];
+                            v[3 * i + c] = v0[3 * i + c];
+                        }
+                    }
+                    int64_t hs = 0;
+                    if (or_hermite_set(k, members + k0, m, m0, q, v, G, rcrit[st], p->eps_H, p->eta,
+                                       p->eta_s, tau, p->max_hermite_steps, &hs))
+                        status = 2;
+                    if (stats) stats[4] += hs;
+                    /* item 7: pre-remove the (1-K) part of the coming kick at q1 */
+                    or_kcorr(k, members + k0, m, q, v, G, rcrit[st], 0.5 * tau);
+                }
+            }
+        }
+        /* item 9: interaction tau/2 */
+        or_kick(rows, m, q, v, G, 0.5 * tau);
+        /* item 10: drift tau/2 */
+        or_drift(rows, m, q, v, 0.5 * tau);
+    }
+    if (enc_count) *enc_count = ne_total;
+    free(q0); free(v0); free(rH); free(its); free(pairs);
+    free(set_of); free(set_start); free(members); free(rcrit);
+    return status;
+}

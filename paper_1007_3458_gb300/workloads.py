@@ -1,0 +1,252 @@
+"""Seeded synthetic planetary-disk workloads (star + planets + planetesimals).
+
+This module only draws initial conditions. It holds none of the integrator's
+arithmetic: no DH coordinates, no universal-variable Kepler solve, no forces.
+Orbital elements are converted to heliocentric Cartesian positions and
+velocities with the classical elliptic relations (mean -> eccentric anomaly by
+Newton's method on M = E - e sin E, then the perifocal-to-inertial rotation),
+with mu_i = G (m0 + m_i) for each body about the star.
+
+The disks follow the shapes of the paper's workloads: a few massive planets
+inside a less massive planetesimal disk (Section 4, Tables 1-3), and the
+massive-plus-massless disks used to stress the encounter search.
+
+Arrays follow one convention everywhere in this project:
+  * a system of N bodies plus its star has N+1 rows, the star at row 0 with
+    q = v = 0 and mass m0;
+  * positions and velocities are float64 arrays of shape [rows, 3];
+  * a batch of systems is concatenated, with int64 offsets[nsys+1] giving the
+    first row (the star) of each system.
+
+Random draws use numpy's PCG64 (``numpy.random.default_rng(seed)``). Within a
+population the element arrays are drawn in the order a, e, i, Omega, omega, M.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+TWO_PI = 2.0 * math.pi
+
+
+@dataclasses.dataclass
+class Workload:
+    """One batch of planetary systems in heliocentric coordinates."""
+
+    name: str
+    m: np.ndarray          # [rows] masses, star first in each system
+    q: np.ndarray          # [rows, 3] heliocentric positions
+    v: np.ndarray          # [rows, 3] heliocentric velocities
+    offsets: np.ndarray    # [nsys+1] int64 row offsets; star at offsets[s]
+    tau: float             # time step
+    nsteps: int            # steps in the paper-shaped run
+    G: float = 1.0
+    a_E: float = 3.0       # encounter factor in Hill radii
+    a_H: float = 1.0       # transition radius factor in Hill radii
+
+    @property
+    def nsys(self) -> int:
+        return int(len(self.offsets) - 1)
+
+    @property
+    def rows(self) -> int:
+        return int(self.m.shape[0])
+
+    @property
+    def n_bodies(self) -> int:
+        """Bodies other than the stars (the N of the N^2 kick)."""
+        return self.rows - self.nsys
+
+    def pairs_per_kick(self) -> int:
+        """Ordered interacting pairs per kick, N_b (N_b - 1) summed over systems."""
+        nb = np.diff(self.offsets) - 1
+        return int(np.sum(nb * (nb - 1)))
+
+
+def _solve_kepler_elliptic(M: np.ndarray, e: np.ndarray) -> np.ndarray:
+    """Eccentric anomaly from mean anomaly (elliptic), Newton on E - e sin E - M."""
+    E = np.where(e < 0.8, M, np.pi * np.ones_like(M))
+    for _ in range(60):
+        f = E - e * np.sin(E) - M
+        fp = 1.0 - e * np.cos(E)
+        dE = f / fp
+        E = E - dE
+        if np.all(np.abs(dE) < 1e-15):
+            break
+    return E
+
+
+def elements_to_cartesian(mu, a, e, inc, Om, om, M):
+    """Classical elliptic elements -> heliocentric (q, v), arrays of shape [n, 3]."""
+    mu = np.broadcast_to(np.asarray(mu, dtype=np.float64), np.shape(a))
+    E = _solve_kepler_elliptic(np.mod(M, TWO_PI), e)
+    cE, sE = np.cos(E), np.sin(E)
+    b = np.sqrt(1.0 - e * e)
+    # perifocal frame
+    xp = a * (cE - e)
+    yp = a * b * sE
+    n_mean = np.sqrt(mu / (a * a * a))
+    edot = n_mean / (1.0 - e * cE)
+    vxp = -a * sE * edot
+    vyp = a * b * cE * edot
+    cO, sO = np.cos(Om), np.sin(Om)
+    co, so = np.cos(om), np.sin(om)
+    ci, si = np.cos(inc), np.sin(inc)
+    r11 = cO * co - sO * so * ci
+    r12 = -cO * so - sO * co * ci
+    r21 = sO * co + cO * so * ci
+    r22 = -sO * so + cO * co * ci
+    r31 = so * si
+    r32 = co * si
+    q = np.stack([r11 * xp + r12 * yp, r21 * xp + r22 * yp, r31 * xp + r32 * yp], axis=-1)
+    v = np.stack([r11 * vxp + r12 * vyp, r21 * vxp + r22 * vyp, r31 * vxp + r32 * vyp], axis=-1)
+    return q, v
+
+
+def _population(rng, n, m, a_lo, a_hi, sig_e, sig_i, G, m0, log_a=False, e_uniform=None,
+                i_uniform=False):
+    """Draw n bodies of mass m; returns (m[n], q[n,3], v[n,3])."""
+    if n == 0:
+        z = np.zeros((0, 3))
+        return np.zeros(0), z, z
+    if log_a:
+        a = np.exp(rng.uniform(math.log(a_lo), math.log(a_hi), n))
+    else:
+        a = rng.uniform(a_lo, a_hi, n)
+    if e_uniform is not None:
+        e = rng.uniform(e_uniform[0], e_uniform[1], n)
+    else:
+        e = rng.rayleigh(sig_e, n) if sig_e > 0 else np.zeros(n)
+    if i_uniform:
+        inc = rng.uniform(0.0, math.pi, n)
+    else:
+        inc = rng.rayleigh(sig_i, n) if sig_i > 0 else np.zeros(n)
+    Om = rng.uniform(0.0, TWO_PI, n)
+    om = rng.uniform(0.0, TWO_PI, n)
+    M = rng.uniform(0.0, TWO_PI, n)
+    e = np.minimum(e, 0.99)
+    mass = np.full(n, float(m))
+    q, v = elements_to_cartesian(G * (m0 + mass), a, e, inc, Om, om, M)
+    return mass, q, v
+
+
+def _planets(rng, masses, sma, G, m0):
+    """Circular, coplanar planets with uniformly drawn orbital phases."""
+    n = len(masses)
+    mass = np.asarray(masses, dtype=np.float64)
+    a = np.asarray(sma, dtype=np.float64)
+    e = np.zeros(n)
+    inc = np.zeros(n)
+    Om = rng.uniform(0.0, TWO_PI, n)
+    om = rng.uniform(0.0, TWO_PI, n)
+    M = rng.uniform(0.0, TWO_PI, n)
+    q, v = elements_to_cartesian(G * (m0 + mass), a, e, inc, Om, om, M)
+    return mass, q, v
+
+
+def _assemble(parts, m0=1.0):
+    ms, qs, vs = [np.array([m0])], [np.zeros((1, 3))], [np.zeros((1, 3))]
+    for m, q, v in parts:
+        ms.append(m)
+        qs.append(q)
+        vs.append(v)
+    return np.concatenate(ms), np.concatenate(qs), np.concatenate(vs)
+
+
+OUTER_PLANETS_M = (1e-3, 3e-4, 5e-5, 5e-5)
+OUTER_PLANETS_A = (5.0, 9.5, 19.0, 30.0)
+TAU_A5 = TWO_PI * 5.0 ** 1.5 / 40.0      # P(a=5)/40 = 1.756203
+TAU_A1 = TWO_PI / 40.0                   # P(a=1)/40 = 0.1570796
+
+
+def outer_disk(n_planetesimals=256, m_pl=1e-9, seed=0, nsteps=1000, name=None,
+               sig_e=0.01, sig_i=0.005, a_lo=10.0, a_hi=30.0):
+    """Star + 4 giant planets (a = 5, 9.5, 19, 30; circular, coplanar) + a
+    planetesimal disk with a uniform in [10, 30], Rayleigh e and i.
+
+    Default: the 260-body disk (256 planetesimals of 1e-9, seed 0) with
+    tau = P(a=5)/40. With n_planetesimals=16380, m_pl=1e-10, seed=1 it is the
+    16384-body disk."""
+    G, m0 = 1.0, 1.0
+    rng = np.random.default_rng(seed)
+    pl = _planets(rng, OUTER_PLANETS_M, OUTER_PLANETS_A, G, m0)
+    ps = _population(rng, n_planetesimals, m_pl, a_lo, a_hi, sig_e, sig_i, G, m0)
+    m, q, v = _assemble([pl, ps], m0)
+    return Workload(name or f"outer_disk_{4 + n_planetesimals}", m, q, v,
+                    np.array([0, len(m)], dtype=np.int64), TAU_A5, nsteps)
+
+
+def disk_260():
+    """260 bodies: 4 planets + 256 planetesimals (m=1e-9), seed 0, 1000 steps."""
+    return outer_disk(256, 1e-9, seed=0, nsteps=1000, name="disk_260")
+
+
+def disk_16384():
+    """16384 bodies: 4 planets + 16380 planetesimals (m=1e-10), seed 1, 100 steps."""
+    return outer_disk(16380, 1e-10, seed=1, nsteps=100, name="disk_16384")
+
+
+def embryo_disk(n_embryos=64, n_planetesimals=262080, seed=2, nsteps=10, name=None):
+    """Dense-encounter disk: star + embryos (1e-6) + planetesimals (1e-11), all
+    with a uniform in [1, 3] and Rayleigh(0.02) e and i; tau = P(a=1)/40."""
+    G, m0 = 1.0, 1.0
+    rng = np.random.default_rng(seed)
+    em = _population(rng, n_embryos, 1e-6, 1.0, 3.0, 0.02, 0.02, G, m0)
+    ps = _population(rng, n_planetesimals, 1e-11, 1.0, 3.0, 0.02, 0.02, G, m0)
+    m, q, v = _assemble([em, ps], m0)
+    return Workload(name or f"embryo_disk_{n_embryos + n_planetesimals}", m, q, v,
+                    np.array([0, len(m)], dtype=np.int64), TAU_A1, nsteps)
+
+
+def disk_262144():
+    """262144 bodies: 64 embryos + 262080 planetesimals, seed 2, 10 steps."""
+    return embryo_disk(64, 262080, seed=2, nsteps=10, name="disk_262144")
+
+
+def ensemble(nsys=512, n_lo=64, n_hi=4096, seed=3, nsteps=1000, name=None):
+    """Batch of independent systems, N bodies per system uniform in [n_lo, n_hi]
+    (2 planets of 1e-3 at a = 1 and 1.6, circular, + N-2 planetesimals of 1e-9,
+    a uniform in [0.5, 3], Rayleigh(0.01) e and i); tau = P(a=1)/40."""
+    G, m0 = 1.0, 1.0
+    rng = np.random.default_rng(seed)
+    nper = rng.integers(n_lo, n_hi + 1, nsys)
+    ms, qs, vs, offs = [], [], [], [0]
+    for s in range(nsys):
+        pl = _planets(rng, (1e-3, 1e-3), (1.0, 1.6), G, m0)
+        ps = _population(rng, int(nper[s]) - 2, 1e-9, 0.5, 3.0, 0.01, 0.01, G, m0)
+        m, q, v = _assemble([pl, ps], m0)
+        ms.append(m)
+        qs.append(q)
+        vs.append(v)
+        offs.append(offs[-1] + len(m))
+    return Workload(name or f"ensemble_{nsys}", np.concatenate(ms), np.concatenate(qs),
+                    np.concatenate(vs), np.array(offs, dtype=np.int64), TAU_A1, nsteps)
+
+
+def test_particles(n=1048576, seed=4):
+    """Massless test particles about a unit-mass star: a log-uniform in
+    [0.5, 50], e uniform in [0, 0.9], inclination and angles uniform.
+    Returns (q[n,3], v[n,3], dt) with dt = P(a=5)/40 (no star row)."""
+    G, m0 = 1.0, 1.0
+    rng = np.random.default_rng(seed)
+    _, q, v = _population(rng, n, 0.0, 0.5, 50.0, 0.0, 0.0, G, m0, log_a=True,
+                          e_uniform=(0.0, 0.9), i_uniform=True)
+    return q, v, TAU_A5
+
+
+def subsample(w: Workload, n_bodies: int, seed: int = 0, name=None) -> Workload:
+    """First system of ``w`` cut to its planets/embryos plus a random subset of
+    the remaining bodies, keeping their shapes (for small parity cases)."""
+    lo, hi = int(w.offsets[0]), int(w.offsets[1])
+    m, q, v = w.m[lo:hi], w.q[lo:hi], w.v[lo:hi]
+    heavy = np.nonzero(m[1:] > 10 * m[1:].min())[0] + 1 if len(m) > 1 else np.zeros(0, int)
+    light = np.setdiff1d(np.arange(1, len(m)), heavy)
+    rng = np.random.default_rng(seed)
+    k = max(0, n_bodies - len(heavy))
+    pick = np.sort(rng.choice(light, size=min(k, len(light)), replace=False))
+    rows = np.concatenate([[0], heavy, pick]).astype(int)
+    return Workload(name or f"{w.name}_sub{len(rows) - 1}", m[rows].copy(), q[rows].copy(),
+                    v[rows].copy(), np.array([0, len(rows)], dtype=np.int64), w.tau, w.nsteps,
+                    w.G, w.a_E, w.a_H)
