@@ -600,8 +600,10 @@ int or_hermite_set(int64_t k, const int64_t *mem, const double *m, double m0, do
         }
     }
     or_hermite_force(k, mm, x, u, G, m0, rcrit, eps, a0, j0);
+    /* a negative tau integrates backward: steps of length dt with sign sg */
+    double T = fabs(tau), sg = tau >= 0.0 ? 1.0 : -1.0;
     /* start-up step, eta_s |a| / |adot|, shared by the set */
-    double dt = tau;
+    double dt = T;
     for (int64_t i = 0; i < k; ++i) {
         double jn = norm3(j0 + 3 * i);
         if (jn > 0.0) {
@@ -612,11 +614,12 @@ int or_hermite_set(int64_t k, const int64_t *mem, const double *m, double m0, do
     double t = 0.0;
     int64_t steps = 0;
     int status = 0;
-    while (t < tau) {
+    while (t < T) {
         if (steps >= max_steps) { status = 1; break; }
-        double h = dt;
+        double hm = dt;
         int last = 0;
-        if (t + h >= tau) { h = tau - t; last = 1; }
+        if (t + hm >= T) { hm = T - t; last = 1; }
+        double h = sg * hm;
         /* predictor */
         for (int64_t i = 0; i < 3 * k; ++i) {
             xp[i] = x[i] + h * (u[i] + h * (0.5 * a0[i] + h * j0[i] / 6.0));
@@ -624,7 +627,7 @@ int or_hermite_set(int64_t k, const int64_t *mem, const double *m, double m0, do
         }
         or_hermite_force(k, mm, xp, up, G, m0, rcrit, eps, a1, j1);
         /* corrector with a^(2), a^(3) from the endpoint a and adot */
-        double next = tau;
+        double next = T;
         for (int64_t i = 0; i < k; ++i) {
             double a2[3], a3[3];
             for (int c = 0; c < 3; ++c) {
@@ -645,7 +648,7 @@ int or_hermite_set(int64_t k, const int64_t *mem, const double *m, double m0, do
         }
         memcpy(a0, a1, b3);
         memcpy(j0, j1, b3);
-        t = last ? tau : t + h;
+        t = last ? T : t + hm;
         dt = next;
         ++steps;
     }

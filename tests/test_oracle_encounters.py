@@ -286,3 +286,16 @@ def test_hermite_step_cap_reports(oracle):
     v = np.array([[0, 0, 0], [0.0, 1.0, 0.0], [-0.06, 0.95, 0.0]])
     _, _, steps, st = oracle.hermite_set([1, 2], m, q, v, 0.05, 1.0, max_steps=3)
     assert st == 1 and steps == 3
+
+
+def test_hermite_backward_returns_to_start(oracle):
+    """A negative tau integrates backward: forward then backward over the same
+    interval returns the set to its start within the 4th-order truncation."""
+    m = np.array([1.0, 1e-4, 3e-5])
+    q = np.array([[0, 0, 0], [1.0, 0.0, 0.0], [1.0, 0.04, 0.0]])
+    v = np.array([[0, 0, 0], [0.0, 1.0, 0.0], [-0.06, 0.95, 0.0]])
+    qf, vf, s1, st1 = oracle.hermite_set([1, 2], m, q, v, 0.1, 0.5, eta=0.002, eta_s=0.001)
+    qb, vb, s2, st2 = oracle.hermite_set([1, 2], m, qf, vf, 0.1, -0.5, eta=0.002, eta_s=0.001)
+    assert st1 == 0 and st2 == 0 and s1 > 5 and s2 > 5
+    assert np.abs(qf - q).max() > 0.1
+    assert np.abs(qb - q).max() < 1e-8 and np.abs(vb - v).max() < 1e-8
