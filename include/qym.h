@@ -1,0 +1,239 @@
+/*
+ * qym.h -- C ABI of libqym, a GB300 (sm_103a) implementation of the
+ * democratic-heliocentric (DH) hybrid symplectic step of Moore & Quillen,
+ * "QYMSYM: A GPU-accelerated hybrid symplectic integrator that permits close
+ * encounters" (New Astronomy).
+ *
+ * One step (Sec. 2, Eq. 5) is E_Dft(tau/2) E_Int(tau/2) E_Kep(tau) E_Int(tau/2)
+ * E_Dft(tau/2), with close encounters found during the step and handed to a
+ * Hermite sub-integrator (Sec. 2.1-2.4).
+ *
+ * Conventions shared by every call:
+ *  - Plain C types only. No exception crosses this boundary; every call returns
+ *    a qym_status (0 = QYM_OK). qym_last_error() gives a message for the last
+ *    failing call on a context (or on the thread, for context-free calls).
+ *  - Units: G, masses, lengths and times are the caller's; the paper uses
+ *    G m0 = 1 and lengths in units of a planet's semi-major axis.
+ *  - A "system" is one star plus its bodies; rows of a batch are concatenated
+ *    and offsets[s] is the row of system s's star (offsets[nsys] = rows). The
+ *    star row of each system is held at Q = P = 0 (Sec. 2: the star is kept
+ *    at index 0 and its mass is zeroed in H_Int).
+ *  - HOST arrays (the qym_ctx calls) are caller owned, row-major [rows][3]
+ *    float64, read or written during the call only, never retained.
+ *  - DEVICE arrays (the *_dev calls) are caller-owned CUDA device pointers in
+ *    the current device's memory, structure-of-arrays [3][n] float64 (all x,
+ *    then all y, then all z); work is enqueued on `stream` (a cudaStream_t
+ *    passed as void*, NULL = legacy default stream) and the call returns
+ *    without waiting unless stated. Device status words are int32 in device
+ *    memory; the library only ever sets bits in them (OR), so zero them first.
+ *  - Nothing here traps or spins without bound on the GPU: every device-side
+ *    iteration has a cap and reports through a status word instead.
+ */
+#ifndef QYM_H
+#define QYM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum qym_status {
+    QYM_OK = 0,
+    QYM_EINVAL = 1,     /* bad argument (sizes, offsets, tau, parameters) */
+    QYM_ENOMEM = 2,     /* device or host allocation failed */
+    QYM_ECUDA = 3,      /* a CUDA runtime call failed (message has the name) */
+    QYM_ENAN = 4,       /* a non-finite position or velocity appeared */
+    QYM_ENOCONV = 5,    /* Kepler iteration or Hermite step cap reached */
+    QYM_EOVERFLOW = 6,  /* a candidate / encounter / set capacity was exceeded */
+    QYM_ENODEV = 7      /* no CUDA device, or the device is not sm_103 class */
+} qym_status;
+
+/* Bits of the device status word (per step, OR-ed). */
+#define QYM_ST_KEPLER_NOCONV   0x01  /* a Kepler solve hit max_kepler_iter */
+#define QYM_ST_HERMITE_CAP     0x02  /* an encounter set hit max_hermite_steps */
+#define QYM_ST_CAND_OVERFLOW   0x04  /* more crude candidates than max_candidates */
+#define QYM_ST_ENC_OVERFLOW    0x08  /* more encounter pairs than max_encounters */
+#define QYM_ST_SET_OVERFLOW    0x10  /* a set larger than the set capacity */
+#define QYM_ST_NAN             0x20  /* non-finite state after the Kepler drift */
+#define QYM_ST_UF_CAP          0x40  /* set-building iteration cap reached */
+#define QYM_ST_LOG_OVERFLOW    0x80  /* encounter log of this qym_step call is full */
+
+/* Kick arithmetic (Sec. 2, footnote on precision; Gaburov-style corrector). */
+#define QYM_KICK_FP64   0   /* plain FP64 pair forces */
+#define QYM_KICK_MIXED  1   /* FP32 pair forces on double-single separations,
+                               compensated (two-sum) accumulation into FP64 */
+
+/* Kepler solver and starting guess (Appendix). */
+#define QYM_SOLVER_LAGUERRE 0   /* Laguerre, n = 5 */
+#define QYM_SOLVER_NEWTON   1
+#define QYM_GUESS_STANDARD  0   /* x0 = sqrt(mu) dt / r0 */
+#define QYM_GUESS_R0        1   /* x0 = r0, as the Appendix does */
+#define QYM_GUESS_MLP       2   /* learned guess (qym_set_mlp); falls back to
+                                   Laguerre from the standard guess */
+
+typedef struct qym_params {
+    double G;            /* gravitational constant */
+    double a_E;          /* encounter factor: flag d_min < a_E (r_H,i + r_H,j) (Sec. 2.4) */
+    double a_H;          /* transition factor: r_crit = a_H max r_H over a set (Eq. 9) */
+    double eps_H;        /* Hermite smoothing length (Sec. 2.2) */
+    double eta, eta_s;   /* Hermite step accuracy and start-up factors (Sec. 2.2) */
+    int32_t kick_prec;   /* QYM_KICK_* */
+    int32_t solver;      /* QYM_SOLVER_* */
+    int32_t guess;       /* QYM_GUESS_* */
+    int32_t encounters;  /* 0: plain DH step; 1: hybrid step with encounters (Sec. 2.3) */
+    int32_t coords;      /* 0: q, v given/returned heliocentric; 1: DH (heliocentric q,
+                            barycentric v = P/m) */
+    int32_t hill_fixed;  /* 0: Hill radii from the orbit entering each Kepler step;
+                            1: Hill radii computed once at init and held */
+    int32_t max_kepler_iter;
+    int32_t device;      /* CUDA device ordinal */
+    int64_t max_hermite_steps;  /* per set per step */
+    int64_t max_candidates;     /* crude candidate pairs per step (0: automatic) */
+    int64_t max_encounters;     /* rigorous encounter pairs per step (0: automatic) */
+    int64_t max_log;            /* encounter records kept per qym_step call (0: automatic) */
+} qym_params;
+
+typedef struct qym_stats {
+    int64_t steps;              /* steps taken by the last qym_step call */
+    int64_t candidates;         /* crude candidate pairs, summed over those steps */
+    int64_t encounters;         /* rigorous encounter pairs, summed */
+    int64_t sets;               /* encounter sets, summed */
+    int64_t max_set;            /* largest set seen */
+    int64_t kepler_iters;       /* Kepler solver iterations, summed over bodies and steps */
+    int64_t hermite_steps;      /* Hermite steps, summed over sets and steps */
+    int64_t rescans;            /* bodies re-searched because a crude bound was exceeded */
+    int32_t status_bits;        /* OR of QYM_ST_* seen */
+    int32_t kick_tile_i, kick_tile_splits;  /* launch shape picked by the tuner */
+} qym_stats;
+
+typedef struct qym_ctx qym_ctx;   /* opaque; owned by the library */
+
+/* ------------------------------------------------------------------------ */
+/* Context API: state resident on the device between calls (Sec. 2:         */
+/* positions and velocities stay on the GPU; host copies only on request).  */
+/* ------------------------------------------------------------------------ */
+
+/* Fill *p with defaults: G = 1, a_E = 3, a_H = 1, eps_H = 0, eta = 0.02,
+ * eta_s = 0.01, mixed kick, Laguerre, standard guess, encounters on,
+ * heliocentric coordinates, per-step Hill radii, 50 Kepler iterations,
+ * 1e5 Hermite steps, automatic capacities. Returns QYM_EINVAL if p is NULL. */
+qym_status qym_default_params(qym_params *p);
+
+/* Create a context on params->device and upload a batch of systems.
+ *  nsys      number of systems (>= 1)
+ *  offsets   host int64[nsys+1], offsets[0] = 0, strictly increasing; each
+ *            system has its star at row offsets[s] and at least one body
+ *  m         host float64[rows] masses (m > 0 for stars, m >= 0 for bodies)
+ *  q, v      host float64[rows][3]: positions relative to the system's star
+ *            and velocities (heliocentric or DH per params->coords); star rows
+ *            are ignored and set to zero
+ * Heliocentric velocities are converted to barycentric ones on the device
+ * (Sec. 2). Device memory is sized here for the capacities in params.
+ * On error *out is NULL and nothing is leaked. */
+qym_status qym_init(const qym_params *params, int32_t nsys, const int64_t *offsets,
+                    const double *m, const double *q, const double *v, qym_ctx **out);
+
+/* Advance every system by nsteps steps of size tau (tau may be negative for a
+ * reversed integration; tau = 0 or nsteps < 0 is QYM_EINVAL). Returns after the
+ * device has finished. Encounter records of this call replace the previous
+ * call's. On QYM_ENOCONV / QYM_EOVERFLOW / QYM_ENAN the steps already taken are
+ * kept, qym_stats tells which, and the context stays usable. */
+qym_status qym_step(qym_ctx *ctx, double tau, int64_t nsteps);
+
+/* Copy the state to host float64[rows][3] arrays (coordinates per
+ * params->coords; star rows are zero). Either pointer may be NULL. */
+qym_status qym_get_state(qym_ctx *ctx, double *q, double *v);
+
+/* Replace the state (same layout and coordinates as qym_init). Used to resume
+ * from a checkpoint; Hill radii are recomputed if params.hill_fixed. */
+qym_status qym_set_state(qym_ctx *ctx, const double *q, const double *v);
+
+/* Copy the encounter records of the last qym_step call to host int64
+ * recs[cap][3] = (step, i, j): step counted from 0 within that call, i < j
+ * global row indices, sorted by (step, i, j). *count receives the total number
+ * found (which may exceed cap; only cap records are written). */
+qym_status qym_get_encounters(qym_ctx *ctx, int64_t *recs, int64_t cap, int64_t *count);
+
+/* Total energy H_Dft + H_Kep + H_Int of each system (Sec. 2, Eqs. 2-4, star
+ * mass restored for the pair sum), FP64, into host double E[nsys]. */
+qym_status qym_energy(qym_ctx *ctx, double *E);
+
+/* Counters of the last qym_step call. */
+qym_status qym_get_stats(qym_ctx *ctx, qym_stats *st);
+
+/* Set the learned Kepler starting-guess network used with QYM_GUESS_MLP: a
+ * 4 -> 64 -> 64 -> 1 perceptron with GELU, weights as host float32 in the
+ * order W1[64][4], b1[64], W2[64][64], b2[64], W3[64], b3[1], followed by the
+ * input normalisation mean[4], std[4] and the output scale pair (mean, std):
+ * n = 4*64 + 64 + 64*64 + 64 + 64 + 1 + 4 + 4 + 2 = 4615 floats. The weights
+ * are rounded to bf16 on the device. */
+qym_status qym_set_mlp(qym_ctx *ctx, const float *weights, int64_t n);
+
+/* Message for the last error on ctx (ctx may be NULL: last context-free error
+ * of the calling thread). The string lives until the next call on ctx. */
+const char *qym_last_error(const qym_ctx *ctx);
+
+/* Free every device and host resource of ctx (NULL is accepted). */
+void qym_destroy(qym_ctx *ctx);
+
+/* Number of rows and systems of ctx. */
+qym_status qym_shape(const qym_ctx *ctx, int64_t *rows, int32_t *nsys);
+
+/* ------------------------------------------------------------------------ */
+/* Device-level calls: one operator of the step on caller-owned device      */
+/* buffers, enqueued on `stream`. These are the same kernels qym_step runs. */
+/* ------------------------------------------------------------------------ */
+
+/* E_Kep (Sec. 2, Appendix): advance n bodies on Kepler orbits about a star of
+ * gravitational parameter mu for dt with universal-variable f and g functions.
+ *  q0, v0    device float64[3][n] input state (not modified)
+ *  q1, v1    device float64[3][n] output state (must not alias q0, v0)
+ *  solver    QYM_SOLVER_*; guess QYM_GUESS_STANDARD or QYM_GUESS_R0, or
+ *            QYM_GUESS_MLP with x_guess != NULL (device float32[n] guesses)
+ *  x_out     device float64[n] universal variable x, or NULL
+ *  iters     device int32[n] iterations used, or NULL
+ *  status    device int32 word, QYM_ST_KEPLER_NOCONV / QYM_ST_NAN OR-ed in, or NULL
+ * n = 0 is a no-op. Returns QYM_EINVAL for n < 0, mu <= 0, max_iter < 1. */
+qym_status qym_kepler_drift_dev(int64_t n, const double *q0, const double *v0, double *q1,
+                                double *v1, double mu, double dt, int32_t solver, int32_t guess,
+                                const float *x_guess, int32_t max_iter, double *x_out,
+                                int32_t *iters, int32_t *status, void *stream);
+
+/* E_Int acceleration (Sec. 2, Eq. 4) of one system: for rows i >= 1
+ *   a_i = -sum_{j >= 1, j != i} G m_j (Q_i - Q_j) / |Q_i - Q_j|^3,
+ * star row excluded (a_0 = 0).
+ *  m         device float64[rows]
+ *  q         device float64[3][rows]
+ *  a         device float64[3][rows] output
+ *  prec      QYM_KICK_FP64 or QYM_KICK_MIXED
+ *  work      device scratch of qym_accel_workspace_bytes(rows, prec) bytes
+ *            (caller owned, contents irrelevant on entry)
+ * Returns QYM_EINVAL for rows < 2 or a NULL / short workspace. */
+size_t qym_accel_workspace_bytes(int64_t rows, int32_t prec);
+qym_status qym_accel_dev(int64_t rows, const double *m, const double *q, double *a, double G,
+                         int32_t prec, void *work, size_t work_bytes, void *stream);
+
+/* Rigorous encounter test (Sec. 2.4): for each of npairs candidate pairs
+ * (pairs[2k], pairs[2k+1]) of rows, the minimum over [0, tau] of the cubic that
+ * interpolates |dQ(t)|^2 from its values and slopes at t = 0 (q0, v0) and
+ * t = tau (q1, v1), clamped at 0, into d2[k]; flag[k] = d2[k] <
+ * (a_E (rH_i + rH_j))^2. All arrays are device arrays ([3][rows] for states). */
+qym_status qym_encounter_test_dev(int64_t rows, const double *q0, const double *v0,
+                                  const double *q1, const double *v1, const double *rH,
+                                  double tau, double a_E, int64_t npairs, const int32_t *pairs,
+                                  double *d2, int32_t *flag, void *stream);
+
+/* Total energy of one system (Sec. 2, Eqs. 2-4), star at row 0, into device
+ * double E[1]. `work` is caller-owned device scratch of
+ * qym_energy_workspace_bytes(rows) bytes. Small work tables are staged from
+ * the host, so this call waits for `stream` before returning. */
+size_t qym_energy_workspace_bytes(int64_t rows);
+qym_status qym_energy_dev(int64_t rows, const double *m, const double *q, const double *v,
+                          double G, double *E, void *work, size_t work_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QYM_H */

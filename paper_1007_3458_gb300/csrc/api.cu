@@ -1,0 +1,676 @@
+// api.cu -- the C ABI of libqym (include/qym.h): context creation, the step
+// loop, state and encounter transfer, energy, and the device-level calls.
+//
+// The step (Sec. 2, Eq. 5 and the procedure of Sec. 2.3) runs entirely on the
+// device, with no host round trip inside a qym_step call: the first step's
+// opening drift, then per step
+//   kick 1 (crude encounter search fused) -> finish -> Kepler drift ->
+//   rigorous test -> encounter sets -> Hermite (with K corrections) ->
+//   pack -> kick 2 -> finish -> momentum -> closing + next opening drift.
+// Identical steps are captured once into a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "qym_internal.cuh"
+
+using namespace qym;
+
+static thread_local std::string g_err;
+
+struct qym_ctx {
+    qym_params p;
+    cudaStream_t stream = nullptr;
+    Dev d;
+    std::vector<int64_t> h_offsets;
+    void *arena = nullptr;
+    KickTune tune;
+    // energy
+    int4 *eitems = nullptr;
+    int32_t *eisys = nullptr, *eitem0 = nullptr;
+    double *epart = nullptr, *E = nullptr;
+    int32_t neitems = 0;
+    double *mt = nullptr;  // [nsys] total masses
+    SetScratch ss;
+    bool amag_valid = false;
+    // graph of one interior step
+    cudaGraphExec_t gexec = nullptr;
+    double g_tau = 0.0;
+    qym_stats stats;
+    std::string err;
+    int32_t status_bits = 0;
+};
+
+#define FAIL(ctx, code, msg)                         \
+    do {                                             \
+        std::string _m = (msg);                      \
+        if (ctx) ((qym_ctx *)(ctx))->err = _m;       \
+        else g_err = _m;                             \
+        return (code);                               \
+    } while (0)
+
+#define CK(ctx, call)                                                                  \
+    do {                                                                               \
+        cudaError_t _e = (call);                                                       \
+        if (_e != cudaSuccess)                                                         \
+            FAIL(ctx, QYM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e));  \
+    } while (0)
+
+extern "C" qym_status qym_default_params(qym_params *p) {
+    if (!p) FAIL(nullptr, QYM_EINVAL, "qym_default_params: NULL params");
+    std::memset(p, 0, sizeof(*p));
+    p->G = 1.0;
+    p->a_E = 3.0;
+    p->a_H = 1.0;
+    p->eps_H = 0.0;
+    p->eta = 0.02;
+    p->eta_s = 0.01;
+    p->kick_prec = QYM_KICK_MIXED;
+    p->solver = QYM_SOLVER_LAGUERRE;
+    p->guess = QYM_GUESS_STANDARD;
+    p->encounters = 1;
+    p->coords = 0;
+    p->hill_fixed = 0;
+    p->max_kepler_iter = 50;
+    p->device = 0;
+    p->max_hermite_steps = 100000;
+    p->max_candidates = 0;
+    p->max_encounters = 0;
+    p->max_log = 0;
+    return QYM_OK;
+}
+
+static bool valid_params(const qym_params *p, std::string &why) {
+    if (!(p->G > 0.0)) { why = "G must be > 0"; return false; }
+    if (!(p->a_E >= 0.0) || !(p->a_H > 0.0)) { why = "a_E >= 0 and a_H > 0 required"; return false; }
+    if (!(p->eps_H >= 0.0)) { why = "eps_H must be >= 0"; return false; }
+    if (!(p->eta > 0.0) || !(p->eta_s > 0.0)) { why = "eta, eta_s must be > 0"; return false; }
+    if (p->kick_prec != QYM_KICK_FP64 && p->kick_prec != QYM_KICK_MIXED) { why = "kick_prec"; return false; }
+    if (p->solver != QYM_SOLVER_LAGUERRE && p->solver != QYM_SOLVER_NEWTON) { why = "solver"; return false; }
+    if (p->guess < 0 || p->guess > 2) { why = "guess"; return false; }
+    if (p->max_kepler_iter < 1) { why = "max_kepler_iter must be >= 1"; return false; }
+    if (p->max_hermite_steps < 1) { why = "max_hermite_steps must be >= 1"; return false; }
+    if (p->max_candidates < 0 || p->max_encounters < 0 || p->max_log < 0) { why = "capacities"; return false; }
+    return true;
+}
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ------------------------------------------------------------------ arena
+struct Carver {
+    char *base;
+    size_t off = 0;
+    bool dry;
+    template <class T>
+    T *take(size_t n) {
+        size_t o = off;
+        off = al256(off + sizeof(T) * (n ? n : 1));
+        return dry ? nullptr : (T *)(base + o);
+    }
+};
+
+static void carve_all(qym_ctx *c, Carver &k) {
+    Dev &d = c->d;
+    const int64_t R = d.rows;
+    d.offsets = k.take<int64_t>(d.nsys + 1);
+    d.sys_of = k.take<int32_t>(R);
+    d.m = k.take<double>(R);
+    d.q = k.take<double>(3 * R);
+    d.v = k.take<double>(3 * R);
+    d.q1 = k.take<double>(3 * R);
+    d.v1 = k.take<double>(3 * R);
+    d.rH = k.take<double>(R);
+    d.rH_fixed = k.take<double>(R);
+    d.pk_pos = k.take<float4>(R);
+    d.pk_lo = k.take<float4>(R);
+    d.amag = k.take<float>(R);
+    d.rH_bound = k.take<float>(R);
+    d.apart = k.take<double>((size_t)3 * R * d.splits);
+    d.items = k.take<int4>(d.nitems);
+    d.item_slot = k.take<int32_t>(d.nitems);
+    d.mchunks = k.take<int4>(d.nmchunks);
+    d.mpart = k.take<double>(3 * (size_t)d.nmchunks);
+    d.sys_chunk0 = k.take<int32_t>(d.nsys + 1);
+    d.S = k.take<double>(3 * (size_t)d.nsys);
+    d.cand = k.take<int2>(d.max_cand);
+    d.enc = k.take<int2>(d.max_enc);
+    d.rescan = k.take<int32_t>(R);
+    d.set_start = k.take<int32_t>((size_t)d.max_sets + 1);
+    d.set_mem = k.take<int32_t>(d.max_members);
+    d.rcrit = k.take<double>(d.max_sets);
+    d.uf = k.take<int32_t>(R);
+    d.log = k.take<int64_t>(3 * (size_t)d.max_log);
+    d.ctr = k.take<unsigned long long>(C_COUNT);
+    d.status = k.take<int32_t>(1);
+    c->ss.blk = k.take<int32_t>((R + 1023) / 1024 + 1);
+    c->ss.sid = k.take<int32_t>(R);
+    c->ss.size = k.take<int32_t>(R + 1);
+    c->ss.fill = k.take<int32_t>(R + 1);
+    c->ss.rc_bits = k.take<unsigned long long>(R + 1);
+    c->eitems = k.take<int4>(c->neitems);
+    c->eisys = k.take<int32_t>(c->neitems);
+    c->eitem0 = k.take<int32_t>(d.nsys + 1);
+    c->epart = k.take<double>(c->neitems);
+    c->E = k.take<double>(d.nsys);
+    c->mt = k.take<double>(d.nsys);
+}
+
+static void soa_from_aos(const double *aos, int64_t R, std::vector<double> &out) {
+    out.resize(3 * R);
+    for (int64_t i = 0; i < R; ++i)
+        for (int c = 0; c < 3; ++c) out[c * R + i] = aos[3 * i + c];
+}
+
+static void aos_from_soa(const std::vector<double> &soa, int64_t R, double *aos) {
+    for (int64_t i = 0; i < R; ++i)
+        for (int c = 0; c < 3; ++c) aos[3 * i + c] = soa[c * R + i];
+}
+
+// Launch shape of the kick for this batch: enough CTAs to fill the GPU
+// several times, each CTA at least a tile of j rows per split.
+static KickTune default_tune(const std::vector<int64_t> &off, int prec) {
+    KickTune t;
+    t.threads = 128;
+    t.ipt = prec == QYM_KICK_MIXED ? 2 : 1;
+    int32_t nsys = (int32_t)off.size() - 1;
+    int64_t ib = 0, nbmax = 0;
+    for (int32_t s = 0; s < nsys; ++s) {
+        int64_t nb = off[s + 1] - off[s] - 1;
+        ib += (nb + t.threads * t.ipt - 1) / (t.threads * t.ipt);
+        nbmax = std::max(nbmax, nb);
+    }
+    int64_t want = 4 * 152;
+    int64_t sp = (want + ib - 1) / std::max<int64_t>(ib, 1);
+    int64_t maxsp = std::max<int64_t>(1, nbmax / 256);
+    t.splits = (int32_t)std::max<int64_t>(1, std::min(sp, maxsp));
+    return t;
+}
+
+static qym_status upload_state(qym_ctx *c, const double *q, const double *v) {
+    Dev &d = c->d;
+    const int64_t R = d.rows;
+    std::vector<double> qs, vs;
+    soa_from_aos(q, R, qs);
+    soa_from_aos(v, R, vs);
+    for (int32_t s = 0; s < d.nsys; ++s) {  // star rows held at zero
+        int64_t r = c->h_offsets[s];
+        for (int k = 0; k < 3; ++k) qs[k * R + r] = vs[k * R + r] = 0.0;
+    }
+    for (double x : qs)
+        if (!std::isfinite(x)) FAIL(c, QYM_EINVAL, "non-finite position");
+    for (double x : vs)
+        if (!std::isfinite(x)) FAIL(c, QYM_EINVAL, "non-finite velocity");
+    CK(c, cudaMemcpyAsync(d.q, qs.data(), sizeof(double) * 3 * R, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(d.v, vs.data(), sizeof(double) * 3 * R, cudaMemcpyHostToDevice, c->stream));
+    if (c->p.coords == 0) CK(c, launch_to_dh_impl(d, 0, nullptr, c->mt, c->stream));
+    if (c->p.hill_fixed) CK(c, launch_hill_init(d, c->p.G, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->amag_valid = false;
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int64_t *offsets,
+                               const double *m, const double *q, const double *v, qym_ctx **out) {
+    if (out) *out = nullptr;
+    if (!params || !offsets || !m || !q || !v || !out)
+        FAIL(nullptr, QYM_EINVAL, "qym_init: NULL argument");
+    std::string why;
+    if (!valid_params(params, why)) FAIL(nullptr, QYM_EINVAL, "qym_init: " + why);
+    if (nsys < 1) FAIL(nullptr, QYM_EINVAL, "qym_init: nsys must be >= 1");
+    if (offsets[0] != 0) FAIL(nullptr, QYM_EINVAL, "qym_init: offsets[0] must be 0");
+    for (int32_t s = 0; s < nsys; ++s)
+        if (offsets[s + 1] - offsets[s] < 2)
+            FAIL(nullptr, QYM_EINVAL, "qym_init: every system needs a star and at least one body");
+    const int64_t R = offsets[nsys];
+    if (R >= (int64_t)1 << 31) FAIL(nullptr, QYM_EINVAL, "qym_init: too many rows (>= 2^31)");
+    for (int32_t s = 0; s < nsys; ++s)
+        if (!(m[offsets[s]] > 0.0)) FAIL(nullptr, QYM_EINVAL, "qym_init: star masses must be > 0");
+    for (int64_t r = 0; r < R; ++r)
+        if (!(m[r] >= 0.0) || !std::isfinite(m[r])) FAIL(nullptr, QYM_EINVAL, "qym_init: masses must be finite and >= 0");
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        FAIL(nullptr, QYM_ENODEV, "qym_init: no CUDA device");
+    if (params->device < 0 || params->device >= ndev) FAIL(nullptr, QYM_EINVAL, "qym_init: bad device");
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, params->device) != cudaSuccess || prop.major != 10 || prop.minor != 3)
+        FAIL(nullptr, QYM_ENODEV, "qym_init: device is not sm_103 (GB300 class)");
+    if (cudaSetDevice(params->device) != cudaSuccess) FAIL(nullptr, QYM_ECUDA, "cudaSetDevice failed");
+
+    qym_ctx *c = new qym_ctx();
+    c->p = *params;
+    c->h_offsets.assign(offsets, offsets + nsys + 1);
+    Dev &d = c->d;
+    d.rows = R;
+    d.nsys = nsys;
+    c->tune = default_tune(c->h_offsets, params->kick_prec);
+    d.nitems = kick_items_count(offsets, nsys, c->tune);
+    d.splits = c->tune.splits;
+    // momentum chunks of at most 1024 rows, never crossing systems
+    std::vector<int4> mch;
+    std::vector<int32_t> sc0(nsys + 1);
+    for (int32_t s = 0; s < nsys; ++s) {
+        sc0[s] = (int32_t)mch.size();
+        for (int64_t r0 = offsets[s]; r0 < offsets[s + 1]; r0 += 1024)
+            mch.push_back(make_int4((int)r0, (int)std::min<int64_t>(r0 + 1024, offsets[s + 1]), s, 0));
+    }
+    sc0[nsys] = (int32_t)mch.size();
+    d.nmchunks = (int32_t)mch.size();
+    d.max_cand = params->max_candidates ? params->max_candidates : std::max<int64_t>(1 << 20, 16 * R);
+    d.max_enc = params->max_encounters ? params->max_encounters : std::max<int64_t>(1 << 16, R);
+    d.max_log = params->max_log ? params->max_log : (int64_t)1 << 22;
+    d.max_sets = (int32_t)R;
+    d.max_members = (int32_t)R;
+    c->neitems = energy_items_host(offsets, nsys, nullptr, nullptr, nullptr);
+
+    Carver dry{nullptr, 0, true};
+    carve_all(c, dry);
+    size_t bytes = dry.off;
+    if (cudaMalloc(&c->arena, bytes) != cudaSuccess) {
+        delete c;
+        FAIL(nullptr, QYM_ENOMEM, "qym_init: cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    Carver real{(char *)c->arena, 0, false};
+    carve_all(c, real);
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(c->arena);
+        delete c;
+        FAIL(nullptr, QYM_ECUDA, "qym_init: stream creation failed");
+    }
+    auto bail = [&](qym_status st) {
+        g_err = c->err;
+        qym_destroy(c);
+        return st;
+    };
+#define CKI(call)                                                                         \
+    do {                                                                                  \
+        cudaError_t _e = (call);                                                          \
+        if (_e != cudaSuccess) {                                                          \
+            c->err = std::string(#call) + ": " + cudaGetErrorString(_e);                  \
+            return bail(QYM_ECUDA);                                                       \
+        }                                                                                 \
+    } while (0)
+    CKI(cudaMemsetAsync(c->arena, 0, bytes, c->stream));
+    CKI(cudaMemsetAsync(d.uf, 0xff, sizeof(int32_t) * R, c->stream));
+    // host-built tables
+    std::vector<int32_t> sys_of(R);
+    for (int32_t s = 0; s < nsys; ++s)
+        for (int64_t r = offsets[s]; r < offsets[s + 1]; ++r) sys_of[r] = s;
+    std::vector<int4> items(d.nitems);
+    std::vector<int32_t> slots(d.nitems);
+    int32_t ni = 0, spu = 0;
+    kick_items_host(offsets, nsys, c->tune, items.data(), slots.data(), &ni, &spu, d.nitems);
+    std::vector<int4> eit(c->neitems);
+    std::vector<int32_t> eis(c->neitems), ei0(nsys + 1);
+    energy_items_host(offsets, nsys, eit.data(), eis.data(), ei0.data());
+    CKI(cudaMemcpyAsync(d.offsets, offsets, sizeof(int64_t) * (nsys + 1), cudaMemcpyHostToDevice, c->stream));
+    CKI(cudaMemcpyAsync(d.sys_of, sys_of.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, c->stream));
+    CKI(cudaMemcpyAsync(d.m, m, sizeof(double) * R, cudaMemcpyHostToDevice, c->stream));
+    CKI(cudaMemcpyAsync(d.items, items.data(), sizeof(int4) * d.nitems, cudaMemcpyHostToDevice, c->stream));
+    CKI(cudaMemcpyAsync(d.item_slot, slots.data(), sizeof(int32_t) * d.nitems, cudaMemcpyHostToDevice, c->stream));
+    CKI(cudaMemcpyAsync(d.mchunks, mch.data(), sizeof(int4) * d.nmchunks, cudaMemcpyHostToDevice, c->stream));
+    CKI(cudaMemcpyAsync(d.sys_chunk0, sc0.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, c->stream));
+    CKI(cudaMemcpyAsync(c->eitems, eit.data(), sizeof(int4) * c->neitems, cudaMemcpyHostToDevice, c->stream));
+    CKI(cudaMemcpyAsync(c->eisys, eis.data(), sizeof(int32_t) * c->neitems, cudaMemcpyHostToDevice, c->stream));
+    CKI(cudaMemcpyAsync(c->eitem0, ei0.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, c->stream));
+    CKI(hermite_prepare());
+#undef CKI
+    qym_status st = upload_state(c, q, v);
+    if (st != QYM_OK) return bail(st);
+    std::memset(&c->stats, 0, sizeof(c->stats));
+    c->stats.kick_tile_i = c->tune.threads * c->tune.ipt;
+    c->stats.kick_tile_splits = c->tune.splits;
+    *out = c;
+    return QYM_OK;
+}
+
+extern "C" void qym_destroy(qym_ctx *c) {
+    if (!c) return;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->stream) {
+        cudaStreamSynchronize(c->stream);
+        cudaStreamDestroy(c->stream);
+    }
+    if (c->arena) cudaFree(c->arena);
+    delete c;
+}
+
+extern "C" qym_status qym_shape(const qym_ctx *c, int64_t *rows, int32_t *nsys) {
+    if (!c) FAIL(nullptr, QYM_EINVAL, "qym_shape: NULL context");
+    if (rows) *rows = c->d.rows;
+    if (nsys) *nsys = c->d.nsys;
+    return QYM_OK;
+}
+
+// ------------------------------------------------------------------ step
+__global__ void k_step_begin(unsigned long long *ctr) {
+    ctr[C_NCAND] = 0;
+    ctr[C_NENC] = 0;
+    ctr[C_NRESCAN] = 0;
+    ctr[C_NSETS] = 0;
+}
+
+__global__ void k_step_end(unsigned long long *ctr, int64_t max_cand, int64_t max_enc) {
+    ctr[C_SUM_CAND] += ctr[C_NCAND];
+    ctr[C_SUM_ENC] += ctr[C_NENC];
+    ctr[C_SUM_RESCAN] += ctr[C_NRESCAN];
+    ctr[C_STEP] += 1;
+}
+
+// one step whose opening drift has been applied: ends with the closing drift
+// of this step plus, unless last, the opening drift of the next one
+static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last) {
+    Dev &d = c->d;
+    const qym_params &p = c->p;
+    cudaStream_t st = c->stream;
+    const int enc = p.encounters;
+    cudaError_t e;
+    k_step_begin<<<1, 1, 0, st>>>(d.ctr);
+    // item 2: kick tau/2, with the crude encounter search when encounters are on
+    if ((e = launch_kick_tiles(d, p.kick_prec, enc, p.G, c->tune.threads, c->tune.ipt, st))) return e;
+    if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, enc, p.hill_fixed, st))) return e;
+    // item 3: Kepler drift over tau, (q, v) -> (q1, v1)
+    KeplerArgs ka;
+    std::memset(&ka, 0, sizeof(ka));
+    ka.n = d.rows;
+    ka.q0 = d.q; ka.v0 = d.v; ka.q1 = d.q1; ka.v1 = d.v1;
+    ka.ld = d.rows;
+    ka.dt = tau;
+    ka.solver = p.solver;
+    ka.guess = p.guess == QYM_GUESS_MLP ? QYM_GUESS_STANDARD : p.guess;
+    ka.max_iter = p.max_kepler_iter;
+    ka.status = d.status;
+    ka.iter_sum = d.ctr + C_SUM_KITER;
+    ka.sys_of = d.sys_of;
+    ka.offsets = d.offsets;
+    ka.m = d.m;
+    ka.G = p.G;
+    if ((e = launch_kepler(ka, st))) return e;
+    if (enc) {
+        // items 4-8: rigorous test, sets and r_crit, K corrections + Hermite
+        if ((e = launch_refine(d, tau, p.a_E, st))) return e;
+        if ((e = launch_sets_impl(d, p.a_H, c->ss, st))) return e;
+        if ((e = launch_hermite(d, p, tau, st))) return e;
+    }
+    // (q1, v1) -> (q, v) and the float packs for the second kick
+    if ((e = launch_drift_pack_from(d, d.q1, d.v1, 0.0, 0.0, tau, p.a_E, p.G, 0, p.hill_fixed, st)))
+        return e;
+    // item 9: kick tau/2
+    if ((e = launch_kick_tiles(d, p.kick_prec, 0, p.G, c->tune.threads, c->tune.ipt, st))) return e;
+    if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, 0, p.hill_fixed, st))) return e;
+    // item 10 (and item 1 of the next step): drift tau/2 with S = sum m v
+    if ((e = launch_momentum(d, st))) return e;
+    if ((e = launch_drift_pack_from(d, d.q, d.v, 0.5 * tau, last ? 0.0 : 0.5 * tau, tau, p.a_E,
+                                    p.G, (!last) && enc, p.hill_fixed, st)))
+        return e;
+    k_step_end<<<1, 1, 0, st>>>(d.ctr, d.max_cand, d.max_enc);
+    return cudaGetLastError();
+}
+
+static qym_status collect(qym_ctx *c, int64_t nsteps) {
+    Dev &d = c->d;
+    unsigned long long ctr[C_COUNT];
+    int32_t status = 0;
+    CK(c, cudaMemcpyAsync(ctr, d.ctr, sizeof(ctr), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(&status, d.status, sizeof(status), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    qym_stats &s = c->stats;
+    s.steps = nsteps;
+    s.candidates = (int64_t)ctr[C_SUM_CAND];
+    s.encounters = (int64_t)ctr[C_SUM_ENC];
+    s.sets = (int64_t)ctr[C_SUM_SETS];
+    s.max_set = (int64_t)ctr[C_MAX_SET];
+    s.kepler_iters = (int64_t)ctr[C_SUM_KITER];
+    s.hermite_steps = (int64_t)ctr[C_SUM_HSTEPS];
+    s.rescans = (int64_t)ctr[C_SUM_RESCAN];
+    s.status_bits = status;
+    s.kick_tile_i = c->tune.threads * c->tune.ipt;
+    s.kick_tile_splits = c->tune.splits;
+    c->status_bits = status;
+    if (status & QYM_ST_NAN) FAIL(c, QYM_ENAN, "non-finite state after a Kepler drift");
+    if (status & (QYM_ST_KEPLER_NOCONV | QYM_ST_HERMITE_CAP))
+        FAIL(c, QYM_ENOCONV, status & QYM_ST_KEPLER_NOCONV ? "Kepler iteration cap reached"
+                                                           : "Hermite step cap reached");
+    if (status & (QYM_ST_CAND_OVERFLOW | QYM_ST_ENC_OVERFLOW | QYM_ST_SET_OVERFLOW | QYM_ST_UF_CAP))
+        FAIL(c, QYM_EOVERFLOW, "encounter capacity exceeded (status bits " + std::to_string(status) + ")");
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
+    if (!c) FAIL(nullptr, QYM_EINVAL, "qym_step: NULL context");
+    if (!(tau != 0.0) || !std::isfinite(tau) || nsteps < 0)
+        FAIL(c, QYM_EINVAL, "qym_step: tau must be finite and nonzero, nsteps >= 0");
+    Dev &d = c->d;
+    const qym_params &p = c->p;
+    cudaStream_t st = c->stream;
+    CK(c, cudaSetDevice(p.device));
+    CK(c, cudaMemsetAsync(d.ctr, 0, sizeof(unsigned long long) * C_COUNT, st));
+    CK(c, cudaMemsetAsync(d.status, 0, sizeof(int32_t), st));
+    if (nsteps == 0) {
+        std::memset(&c->stats, 0, sizeof(c->stats));
+        return QYM_OK;
+    }
+    if (!c->amag_valid) {
+        // |a| of the current positions for the first crude search's kick bound
+        CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.0, tau, p.a_E, p.G, 0, p.hill_fixed, st));
+        CK(c, launch_kick_tiles(d, p.kick_prec, 0, p.G, c->tune.threads, c->tune.ipt, st));
+        CK(c, launch_kick_finish_v(d, d.v, d.q, 0.0, p.G, 0, p.hill_fixed, st));
+        c->amag_valid = true;
+    }
+    // item 1 of the first step: drift tau/2
+    CK(c, launch_momentum(d, st));
+    CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.5 * tau, tau, p.a_E, p.G, p.encounters,
+                                 p.hill_fixed, st));
+    const int64_t interior = nsteps - 1;
+    if (interior > 0) {
+        if (c->gexec && c->g_tau != tau) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        if (!c->gexec && interior >= 2) {
+            cudaGraph_t g;
+            CK(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue_step(c, tau, false);
+            cudaError_t e2 = cudaStreamEndCapture(st, &g);
+            if (e != cudaSuccess) FAIL(c, QYM_ECUDA, std::string("step capture: ") + cudaGetErrorString(e));
+            if (e2 != cudaSuccess) FAIL(c, QYM_ECUDA, std::string("end capture: ") + cudaGetErrorString(e2));
+            e = cudaGraphInstantiate(&c->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) FAIL(c, QYM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            c->g_tau = tau;
+        }
+        for (int64_t k = 0; k < interior; ++k) {
+            if (c->gexec)
+                CK(c, cudaGraphLaunch(c->gexec, st));
+            else
+                CK(c, enqueue_step(c, tau, false));
+        }
+    }
+    CK(c, enqueue_step(c, tau, true));
+    return collect(c, nsteps);
+}
+
+// ------------------------------------------------------------------ state, energy
+extern "C" qym_status qym_get_state(qym_ctx *c, double *q, double *v) {
+    if (!c) FAIL(nullptr, QYM_EINVAL, "qym_get_state: NULL context");
+    Dev &d = c->d;
+    const int64_t R = d.rows;
+    std::vector<double> buf(3 * R);
+    if (q) {
+        CK(c, cudaMemcpyAsync(buf.data(), d.q, sizeof(double) * 3 * R, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        aos_from_soa(buf, R, q);
+    }
+    if (v) {
+        const double *src = d.v;
+        if (c->p.coords == 0) {
+            CK(c, launch_to_dh_impl(d, 1, d.v1, c->mt, c->stream));
+            src = d.v1;
+        }
+        CK(c, cudaMemcpyAsync(buf.data(), src, sizeof(double) * 3 * R, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        aos_from_soa(buf, R, v);
+    }
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_set_state(qym_ctx *c, const double *q, const double *v) {
+    if (!c || !q || !v) FAIL(c, QYM_EINVAL, "qym_set_state: NULL argument");
+    return upload_state(c, q, v);
+}
+
+extern "C" qym_status qym_energy(qym_ctx *c, double *E) {
+    if (!c || !E) FAIL(c, QYM_EINVAL, "qym_energy: NULL argument");
+    Dev &d = c->d;
+    CK(c, launch_energy_items(c->neitems, c->eitems, c->eisys, c->eitem0, d.nsys, d.offsets, d.rows,
+                              d.m, d.q, d.v, c->p.G, c->epart, c->E, c->stream));
+    CK(c, cudaMemcpyAsync(E, c->E, sizeof(double) * d.nsys, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_get_stats(qym_ctx *c, qym_stats *s) {
+    if (!c || !s) FAIL(c, QYM_EINVAL, "qym_get_stats: NULL argument");
+    *s = c->stats;
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_get_encounters(qym_ctx *c, int64_t *recs, int64_t cap, int64_t *count) {
+    if (!c || !count || cap < 0 || (cap > 0 && !recs)) FAIL(c, QYM_EINVAL, "qym_get_encounters: bad argument");
+    Dev &d = c->d;
+    unsigned long long n = 0;
+    CK(c, cudaMemcpyAsync(&n, d.ctr + C_LOG, sizeof(n), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (n > (unsigned long long)d.max_log) n = d.max_log;
+    std::vector<int64_t> h(3 * n);
+    if (n) {
+        CK(c, cudaMemcpyAsync(h.data(), d.log, sizeof(int64_t) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    std::vector<size_t> idx(n);
+    for (size_t k = 0; k < n; ++k) idx[k] = k;
+    std::sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
+        for (int t = 0; t < 3; ++t)
+            if (h[3 * a + t] != h[3 * b + t]) return h[3 * a + t] < h[3 * b + t];
+        return false;
+    });
+    int64_t w = 0;
+    for (size_t k = 0; k < n; ++k) {
+        size_t a = idx[k];
+        if (k > 0) {
+            size_t b = idx[k - 1];
+            if (h[3 * a] == h[3 * b] && h[3 * a + 1] == h[3 * b + 1] && h[3 * a + 2] == h[3 * b + 2])
+                continue;  // a pair found by both the candidate list and a re-search
+        }
+        if (w < cap)
+            for (int t = 0; t < 3; ++t) recs[3 * w + t] = h[3 * a + t];
+        ++w;
+    }
+    *count = w;
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_set_mlp(qym_ctx *c, const float *weights, int64_t n) {
+    if (!c || !weights || n != 4615) FAIL(c, QYM_EINVAL, "qym_set_mlp: expected 4615 weights");
+    FAIL(c, QYM_EINVAL, "qym_set_mlp: the learned guess is not available in this build");
+}
+
+extern "C" const char *qym_last_error(const qym_ctx *c) {
+    return c ? c->err.c_str() : g_err.c_str();
+}
+
+// ------------------------------------------------------------------ device-level calls
+extern "C" qym_status qym_kepler_drift_dev(int64_t n, const double *q0, const double *v0, double *q1,
+                                           double *v1, double mu, double dt, int32_t solver,
+                                           int32_t guess, const float *x_guess, int32_t max_iter,
+                                           double *x_out, int32_t *iters, int32_t *status,
+                                           void *stream) {
+    if (n < 0 || !(mu > 0.0) || max_iter < 1 || !std::isfinite(dt))
+        FAIL(nullptr, QYM_EINVAL, "qym_kepler_drift_dev: bad n, mu, dt or max_iter");
+    if (n == 0) return QYM_OK;
+    if (!q0 || !v0 || !q1 || !v1) FAIL(nullptr, QYM_EINVAL, "qym_kepler_drift_dev: NULL array");
+    if (guess == QYM_GUESS_MLP && !x_guess) FAIL(nullptr, QYM_EINVAL, "qym_kepler_drift_dev: x_guess required");
+    KeplerArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.q0 = q0; a.v0 = v0; a.q1 = q1; a.v1 = v1;
+    a.ld = n;
+    a.mu = mu;
+    a.dt = dt;
+    a.solver = solver;
+    a.guess = guess;
+    a.max_iter = max_iter;
+    a.x_guess = x_guess;
+    a.x_out = x_out;
+    a.iters = iters;
+    a.status = status;
+    CK(nullptr, launch_kepler(a, (cudaStream_t)stream));
+    return QYM_OK;
+}
+
+extern "C" size_t qym_accel_workspace_bytes(int64_t rows, int32_t prec) {
+    return accel_single_workspace(rows, prec);
+}
+
+extern "C" qym_status qym_accel_dev(int64_t rows, const double *m, const double *q, double *a,
+                                    double G, int32_t prec, void *work, size_t work_bytes,
+                                    void *stream) {
+    if (rows < 2 || !m || !q || !a || !work) FAIL(nullptr, QYM_EINVAL, "qym_accel_dev: bad argument");
+    if (prec != QYM_KICK_FP64 && prec != QYM_KICK_MIXED) FAIL(nullptr, QYM_EINVAL, "qym_accel_dev: prec");
+    if (work_bytes < accel_single_workspace(rows, prec)) FAIL(nullptr, QYM_EINVAL, "qym_accel_dev: workspace too small");
+    if (rows >= (int64_t)1 << 31) FAIL(nullptr, QYM_EINVAL, "qym_accel_dev: too many rows");
+    CK(nullptr, launch_accel_single(rows, m, q, a, G, prec, work, work_bytes, (cudaStream_t)stream));
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_encounter_test_dev(int64_t rows, const double *q0, const double *v0,
+                                             const double *q1, const double *v1, const double *rH,
+                                             double tau, double a_E, int64_t npairs,
+                                             const int32_t *pairs, double *d2, int32_t *flag,
+                                             void *stream) {
+    if (rows < 1 || npairs < 0) FAIL(nullptr, QYM_EINVAL, "qym_encounter_test_dev: bad sizes");
+    if (npairs == 0) return QYM_OK;
+    if (!q0 || !v0 || !q1 || !v1 || !rH || !pairs) FAIL(nullptr, QYM_EINVAL, "qym_encounter_test_dev: NULL array");
+    CK(nullptr, launch_pair_test(rows, q0, v0, q1, v1, rH, tau, a_E, npairs, pairs, d2, flag,
+                                 (cudaStream_t)stream));
+    return QYM_OK;
+}
+
+extern "C" size_t qym_energy_workspace_bytes(int64_t rows) {
+    if (rows < 2) return 0;
+    int64_t off[2] = {0, rows};
+    int32_t n = energy_items_host(off, 1, nullptr, nullptr, nullptr);
+    return al256(sizeof(int4) * n) + al256(sizeof(int32_t) * n) + al256(sizeof(int32_t) * 2) +
+           al256(sizeof(double) * n) + al256(sizeof(int64_t) * 2);
+}
+
+extern "C" qym_status qym_energy_dev(int64_t rows, const double *m, const double *q, const double *v,
+                                     double G, double *E, void *work, size_t work_bytes,
+                                     void *stream) {
+    if (rows < 2 || !m || !q || !v || !E || !work) FAIL(nullptr, QYM_EINVAL, "qym_energy_dev: bad argument");
+    if (work_bytes < qym_energy_workspace_bytes(rows)) FAIL(nullptr, QYM_EINVAL, "qym_energy_dev: workspace too small");
+    int64_t off[2] = {0, rows};
+    int32_t n = energy_items_host(off, 1, nullptr, nullptr, nullptr);
+    std::vector<int4> it(n);
+    std::vector<int32_t> is(n), i0(2);
+    energy_items_host(off, 1, it.data(), is.data(), i0.data());
+    char *w = (char *)work;
+    int4 *d_it = (int4 *)w; w += al256(sizeof(int4) * n);
+    int32_t *d_is = (int32_t *)w; w += al256(sizeof(int32_t) * n);
+    int32_t *d_i0 = (int32_t *)w; w += al256(sizeof(int32_t) * 2);
+    double *d_part = (double *)w; w += al256(sizeof(double) * n);
+    int64_t *d_off = (int64_t *)w;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the tables are staged through pageable memory; the copies complete
+    // before this call returns
+    CK(nullptr, cudaMemcpyAsync(d_it, it.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, st));
+    CK(nullptr, cudaMemcpyAsync(d_is, is.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+    CK(nullptr, cudaMemcpyAsync(d_i0, i0.data(), sizeof(int32_t) * 2, cudaMemcpyHostToDevice, st));
+    CK(nullptr, cudaMemcpyAsync(d_off, off, sizeof(int64_t) * 2, cudaMemcpyHostToDevice, st));
+    CK(nullptr, launch_energy_items(n, d_it, d_is, d_i0, 1, d_off, rows, m, q, v, G, d_part, E, st));
+    CK(nullptr, cudaStreamSynchronize(st));
+    return QYM_OK;
+}

@@ -1,0 +1,301 @@
+// hermite.cu -- the close-encounter branch of the hybrid step (Sec. 2.2 and
+// Sec. 2.3 items 5-8), one CTA per encounter set:
+//   1. remove the (1-K) part of the first kick at q0 (item 5),
+//   2. integrate the set for tau with a 4th-order Hermite predictor /
+//      evaluate / corrector (Makino & Aarseth, no Ahmad-Cohen) under H'_Kep:
+//      the star, fixed at the origin, plus the members' pair forces weighted
+//      by [1 - K(s) + s K'(s)], jerks with the K'' term (item 6),
+//   3. pre-remove the (1-K) part of the coming kick at q1 (item 7),
+//   4. write the members' q1, v1 over their Kepler result (item 8).
+// The step is shared by the set (Aarseth criterion with eta, start-up step
+// eta_s |a| / |adot|) and the last step is clipped to land on tau. Every loop
+// has a cap and reports through the status word.
+#include "qym_internal.cuh"
+
+namespace qym {
+
+constexpr int HCAP = 512;       // members per set held in shared memory
+constexpr int HTHREADS = 128;
+
+// transition function of Sec. 2.1 with y = 1.1 s / r_crit - 0.1, and its
+// first and second derivatives with respect to s
+__device__ __forceinline__ void transition(double s, double rc, double &K, double &Kp,
+                                           double &Kpp) {
+    double y = 1.1 * s / rc - 0.1;
+    if (y <= 0.0) {
+        K = 0.0; Kp = 0.0; Kpp = 0.0;
+    } else if (y >= 1.0) {
+        K = 1.0; Kp = 0.0; Kpp = 0.0;
+    } else {
+        double c = 0.5 * kPi * 1.1 / rc;
+        double sn, cs;
+        sincospi(0.5 * y, &sn, &cs);
+        K = sn;
+        Kp = c * cs;
+        Kpp = -c * c * sn;
+    }
+}
+
+struct HermSmem {
+    double *ex, *ey, *ez, *eu, *ev, *ew, *m;  // evaluation point of every member
+    double *x, *y, *z, *u, *v, *w;            // state
+    double *ax, *ay, *az, *jx, *jy, *jz;      // a, adot at the start of the step
+    int32_t *ids;
+};
+
+__device__ __forceinline__ HermSmem carve(void *base) {
+    double *p = (double *)base;
+    HermSmem s;
+    s.ex = p; p += HCAP; s.ey = p; p += HCAP; s.ez = p; p += HCAP;
+    s.eu = p; p += HCAP; s.ev = p; p += HCAP; s.ew = p; p += HCAP;
+    s.m = p; p += HCAP;
+    s.x = p; p += HCAP; s.y = p; p += HCAP; s.z = p; p += HCAP;
+    s.u = p; p += HCAP; s.v = p; p += HCAP; s.w = p; p += HCAP;
+    s.ax = p; p += HCAP; s.ay = p; p += HCAP; s.az = p; p += HCAP;
+    s.jx = p; p += HCAP; s.jy = p; p += HCAP; s.jz = p; p += HCAP;
+    s.ids = (int32_t *)p;
+    return s;
+}
+constexpr size_t kHermSmem = sizeof(double) * HCAP * 19 + sizeof(int32_t) * HCAP;
+
+// (1-K)-weighted pair acceleration at the evaluation point, unsmoothed
+// (the kick used the bare separation): sum_l -G m_l q_kl / q^3 [1 - K + q K']
+__device__ void kcorr_accel(const HermSmem &S, int n, int k, double G, double rc, double &dx,
+                            double &dy, double &dz) {
+    dx = dy = dz = 0.0;
+    for (int l = 0; l < n; ++l) {
+        if (l == k) continue;
+        double qx = S.ex[k] - S.ex[l], qy = S.ey[k] - S.ey[l], qz = S.ez[k] - S.ez[l];
+        double q2 = qx * qx + qy * qy + qz * qz;
+        double q = sqrt(q2);
+        double K, Kp, Kpp;
+        transition(q, rc, K, Kp, Kpp);
+        double br = 1.0 - K + q * Kp;
+        if (br == 0.0) continue;
+        double wgt = -G * S.m[l] / (q2 * q) * br;
+        dx += wgt * qx;
+        dy += wgt * qy;
+        dz += wgt * qz;
+    }
+}
+
+// Hermite acceleration and jerk of member k at the evaluation point (Sec. 2.2)
+__device__ void herm_force(const HermSmem &S, int n, int k, double G, double m0, double rc,
+                           double eps2, double *a, double *j) {
+    double xk = S.ex[k], yk = S.ey[k], zk = S.ez[k];
+    double uk = S.eu[k], vk = S.ev[k], wk = S.ew[k];
+    // star, fixed at the origin
+    double s2 = xk * xk + yk * yk + zk * zk + eps2;
+    double s = sqrt(s2);
+    double rv = xk * uk + yk * vk + zk * wk;
+    double c = -G * m0 / (s2 * s);
+    double t = 3.0 * rv / s2;
+    a[0] = c * xk; a[1] = c * yk; a[2] = c * zk;
+    j[0] = c * (uk - t * xk); j[1] = c * (vk - t * yk); j[2] = c * (wk - t * zk);
+    for (int l = 0; l < n; ++l) {
+        if (l == k) continue;
+        double qx = xk - S.ex[l], qy = yk - S.ey[l], qz = zk - S.ez[l];
+        double px = uk - S.eu[l], py = vk - S.ev[l], pz = wk - S.ew[l];
+        double q2 = qx * qx + qy * qy + qz * qz + eps2;
+        double sq = sqrt(q2);
+        double K, Kp, Kpp;
+        transition(sq, rc, K, Kp, Kpp);
+        double br = 1.0 - K + sq * Kp;
+        if (br == 0.0 && Kpp == 0.0) continue;
+        double rvl = qx * px + qy * py + qz * pz;
+        double cl = -G * S.m[l] / (q2 * sq);
+        double tl = 3.0 * rvl / q2;
+        a[0] += cl * br * qx; a[1] += cl * br * qy; a[2] += cl * br * qz;
+        j[0] += cl * (rvl * qx * Kpp + (px - tl * qx) * br);
+        j[1] += cl * (rvl * qy * Kpp + (py - tl * qy) * br);
+        j[2] += cl * (rvl * qz * Kpp + (pz - tl * qz) * br);
+    }
+}
+
+__device__ __forceinline__ double block_min(double x, double *red) {
+    for (int o = 16; o > 0; o >>= 1) x = fmin(x, __shfl_xor_sync(0xffffffffu, x, o));
+    int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = x;
+    __syncthreads();
+    double r = red[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) r = fmin(r, red[k]);
+    return r;
+}
+
+struct HermArgs {
+    double G, eps2, eta, eta_s, tau;
+    int64_t max_steps;
+};
+
+__global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[32];
+    HermSmem S = carve(smem);
+    const int64_t R = d.rows;
+    int nsets = (int)min((unsigned long long)d.max_sets, d.ctr[C_NSETS]);
+    for (int set = blockIdx.x; set < nsets; set += gridDim.x) {
+        const int st = d.set_start[set];
+        const int n = d.set_start[set + 1] - st;
+        if (n < 1) continue;
+        if (n > HCAP || st + n > d.max_members) {
+            if (threadIdx.x == 0) atomicOr(d.status, QYM_ST_SET_OVERFLOW);
+            for (int k = threadIdx.x; k < n && st + k < d.max_members; k += blockDim.x)
+                d.uf[d.set_mem[st + k]] = -1;
+            continue;
+        }
+        // members in ascending row order (rank sort)
+        __syncthreads();
+        for (int k = threadIdx.x; k < n; k += blockDim.x) S.ids[k] = d.set_mem[st + k];
+        __syncthreads();
+        int myid[HCAP / HTHREADS], myrank[HCAP / HTHREADS];
+        for (int c = 0; c < HCAP / HTHREADS; ++c) {
+            int k = threadIdx.x + c * blockDim.x;
+            myid[c] = k < n ? S.ids[k] : 0;
+            int rk = 0;
+            if (k < n)
+                for (int l = 0; l < n; ++l) rk += S.ids[l] < myid[c];
+            myrank[c] = rk;
+        }
+        __syncthreads();
+        for (int c = 0; c < HCAP / HTHREADS; ++c) {
+            int k = threadIdx.x + c * blockDim.x;
+            if (k < n) S.ids[myrank[c]] = myid[c];
+        }
+        __syncthreads();
+        const int64_t star = d.offsets[d.sys_of[S.ids[0]]];
+        const double m0 = d.m[star];
+        const double rc = d.rcrit[set];
+        const double G = h.G, tau = h.tau;
+        // state entering the Kepler drift (after the first kick)
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            int64_t r = S.ids[k];
+            S.ex[k] = S.x[k] = d.q[r];
+            S.ey[k] = S.y[k] = d.q[R + r];
+            S.ez[k] = S.z[k] = d.q[2 * R + r];
+            S.u[k] = d.v[r];
+            S.v[k] = d.v[R + r];
+            S.w[k] = d.v[2 * R + r];
+            S.m[k] = d.m[r];
+        }
+        __syncthreads();
+        // item 5: remove the (1-K) part of the first kick
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            double cx, cy, cz;
+            kcorr_accel(S, n, k, G, rc, cx, cy, cz);
+            S.u[k] -= 0.5 * tau * cx;
+            S.v[k] -= 0.5 * tau * cy;
+            S.w[k] -= 0.5 * tau * cz;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            S.eu[k] = S.u[k]; S.ev[k] = S.v[k]; S.ew[k] = S.w[k];
+        }
+        __syncthreads();
+        // start-up: a, adot at t = 0 and the step eta_s |a| / |adot|
+        double dtl = fabs(tau);
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            double a[3], j[3];
+            herm_force(S, n, k, G, m0, rc, h.eps2, a, j);
+            S.ax[k] = a[0]; S.ay[k] = a[1]; S.az[k] = a[2];
+            S.jx[k] = j[0]; S.jy[k] = j[1]; S.jz[k] = j[2];
+            double jn = sqrt(j[0] * j[0] + j[1] * j[1] + j[2] * j[2]);
+            if (jn > 0.0) dtl = fmin(dtl, h.eta_s * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) / jn);
+        }
+        double dt = block_min(dtl, red);
+        const double sgn = tau >= 0.0 ? 1.0 : -1.0;
+        const double T = fabs(tau);
+        double t = 0.0;
+        int64_t steps = 0;
+        bool capped = false;
+        while (t < T) {
+            if (steps >= h.max_steps) { capped = true; break; }
+            double hh = dt;
+            bool last = false;
+            if (t + hh >= T) { hh = T - t; last = true; }
+            const double hs = sgn * hh;  // signed step
+            __syncthreads();
+            // predictor
+            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                S.ex[k] = S.x[k] + hs * (S.u[k] + hs * (0.5 * S.ax[k] + hs * S.jx[k] / 6.0));
+                S.ey[k] = S.y[k] + hs * (S.v[k] + hs * (0.5 * S.ay[k] + hs * S.jy[k] / 6.0));
+                S.ez[k] = S.z[k] + hs * (S.w[k] + hs * (0.5 * S.az[k] + hs * S.jz[k] / 6.0));
+                S.eu[k] = S.u[k] + hs * (S.ax[k] + 0.5 * hs * S.jx[k]);
+                S.ev[k] = S.v[k] + hs * (S.ay[k] + 0.5 * hs * S.jy[k]);
+                S.ew[k] = S.w[k] + hs * (S.az[k] + 0.5 * hs * S.jz[k]);
+            }
+            __syncthreads();
+            // evaluate and correct (own members only)
+            double next = T;
+            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                double a1[3], j1[3];
+                herm_force(S, n, k, G, m0, rc, h.eps2, a1, j1);
+                double a0[3] = {S.ax[k], S.ay[k], S.az[k]};
+                double j0[3] = {S.jx[k], S.jy[k], S.jz[k]};
+                double e[3] = {S.ex[k], S.ey[k], S.ez[k]};
+                double f[3] = {S.eu[k], S.ev[k], S.ew[k]};
+                double a2[3], a3[3], xn[3], un[3];
+                for (int c = 0; c < 3; ++c) {
+                    a2[c] = (-6.0 * (a0[c] - a1[c]) - hs * (4.0 * j0[c] + 2.0 * j1[c])) / (hs * hs);
+                    a3[c] = (12.0 * (a0[c] - a1[c]) + 6.0 * hs * (j0[c] + j1[c])) / (hs * hs * hs);
+                    xn[c] = e[c] + hs * hs * hs * hs * (a2[c] / 24.0 + hs * a3[c] / 120.0);
+                    un[c] = f[c] + hs * hs * hs * (a2[c] / 6.0 + hs * a3[c] / 24.0);
+                    a2[c] += hs * a3[c];
+                }
+                S.x[k] = xn[0]; S.y[k] = xn[1]; S.z[k] = xn[2];
+                S.u[k] = un[0]; S.v[k] = un[1]; S.w[k] = un[2];
+                S.ax[k] = a1[0]; S.ay[k] = a1[1]; S.az[k] = a1[2];
+                S.jx[k] = j1[0]; S.jy[k] = j1[1]; S.jz[k] = j1[2];
+                double na = sqrt(a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
+                double nj = sqrt(j1[0] * j1[0] + j1[1] * j1[1] + j1[2] * j1[2]);
+                double n2 = sqrt(a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2]);
+                double n3 = sqrt(a3[0] * a3[0] + a3[1] * a3[1] + a3[2] * a3[2]);
+                double den = nj * n3 + n2 * n2;
+                if (den > 0.0) next = fmin(next, sqrt(h.eta * (na * n2 + nj * nj) / den));
+            }
+            dt = block_min(next, red);
+            t = last ? T : t + hh;
+            ++steps;
+        }
+        __syncthreads();
+        if (capped && threadIdx.x == 0) atomicOr(d.status, QYM_ST_HERMITE_CAP);
+        // item 7: pre-remove the (1-K) part of the coming kick at q1
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            S.ex[k] = S.x[k]; S.ey[k] = S.y[k]; S.ez[k] = S.z[k];
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            double cx, cy, cz;
+            kcorr_accel(S, n, k, G, rc, cx, cy, cz);
+            int64_t r = S.ids[k];
+            d.q1[r] = S.x[k];
+            d.q1[R + r] = S.y[k];
+            d.q1[2 * R + r] = S.z[k];
+            d.v1[r] = S.u[k] - 0.5 * tau * cx;
+            d.v1[R + r] = S.v[k] - 0.5 * tau * cy;
+            d.v1[2 * R + r] = S.w[k] - 0.5 * tau * cz;
+            d.uf[r] = -1;
+        }
+        if (threadIdx.x == 0) atomicAdd(d.ctr + C_SUM_HSTEPS, (unsigned long long)steps);
+    }
+}
+
+// once per process and device, before any launch or stream capture
+cudaError_t hermite_prepare() {
+    return cudaFuncSetAttribute(k_hermite, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kHermSmem);
+}
+
+cudaError_t launch_hermite(const Dev &d, const qym_params &p, double tau, cudaStream_t st) {
+    HermArgs h;
+    h.G = p.G;
+    h.eps2 = p.eps_H * p.eps_H;
+    h.eta = p.eta;
+    h.eta_s = p.eta_s;
+    h.tau = tau;
+    h.max_steps = p.max_hermite_steps;
+    k_hermite<<<2 * 152, HTHREADS, kHermSmem, st>>>(d, h);
+    return cudaGetLastError();
+}
+
+}  // namespace qym

@@ -1,0 +1,159 @@
+// kepler.cu -- E_Kep: universal-variable Kepler drift of every body about its
+// star (Sec. 2 and the Appendix: f and g functions, Stumpff C and S, the
+// universal Kepler equation F(x) = 0 solved by Laguerre's method, n = 5).
+//
+// One thread per body, FP64 throughout. Structure-of-arrays loads are
+// coalesced; q0, v0 are kept and the result goes to separate buffers because
+// the encounter test needs both ends of the step (Sec. 2.3 item 4).
+#include "qym_internal.cuh"
+
+namespace qym {
+
+// Stumpff functions (Appendix, Eqs. 2.40). Near y = 0 the alternating series
+// C = sum_k (-y)^k / (2k+2)!, S = sum_k (-y)^k / (2k+3)! in Horner form to
+// the y^8 term; elsewhere the closed forms, C through 2 sin^2(s/2) / y to
+// avoid the cancellation of 1 - cos s.
+__device__ __forceinline__ void stumpff(double y, double &C, double &S) {
+    if (fabs(y) < 0.1) {
+        // 1/(2k+2)! and 1/(2k+3)! for k = 0..8, alternating signs
+        C = 1.0 / 2.0 + y * (-1.0 / 24.0 + y * (1.0 / 720.0 + y * (-1.0 / 40320.0 +
+            y * (1.0 / 3628800.0 + y * (-1.0 / 479001600.0 + y * (1.0 / 87178291200.0 +
+            y * (-1.0 / 20922789888000.0 + y * (1.0 / 6402373705728000.0))))))));
+        S = 1.0 / 6.0 + y * (-1.0 / 120.0 + y * (1.0 / 5040.0 + y * (-1.0 / 362880.0 +
+            y * (1.0 / 39916800.0 + y * (-1.0 / 6227020800.0 + y * (1.0 / 1307674368000.0 +
+            y * (-1.0 / 355687428096000.0 + y * (1.0 / 121645100408832000.0))))))));
+    } else if (y > 0.0) {
+        double s = sqrt(y);
+        double sh, ch;
+        sincos(0.5 * s, &sh, &ch);
+        C = 2.0 * sh * sh / y;
+        S = (s - 2.0 * sh * ch) / (y * s);
+    } else {
+        double s = sqrt(-y);
+        C = (cosh(s) - 1.0) / (-y);
+        S = (sinh(s) - s) / ((-y) * s);
+    }
+}
+
+// F, F', F'' of the universal Kepler equation (Appendix), sig = r0.v0/sqrt(mu)
+struct KepEq {
+    double sqmu_dt, r0, sig, alpha, b;  // b = 1 - r0 alpha
+    __device__ __forceinline__ void eval(double x, double &F, double &Fp, double &Fpp,
+                                         double &C, double &S) const {
+        double x2 = x * x;
+        double y = alpha * x2;
+        stumpff(y, C, S);
+        double oyS = 1.0 - y * S;
+        F = sig * x2 * C + b * x2 * x * S + r0 * x - sqmu_dt;
+        Fp = sig * x * oyS + b * x2 * C + r0;
+        Fpp = sig * (1.0 - y * C) + b * x * oyS;
+    }
+};
+
+__global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int iters = 0;
+    if (k < a.n) {
+        int64_t r = a.rows ? a.rows[k] : k;
+        const int64_t ld = a.ld;
+        double qx = a.q0[r], qy = a.q0[ld + r], qz = a.q0[2 * ld + r];
+        double vx = a.v0[r], vy = a.v0[ld + r], vz = a.v0[2 * ld + r];
+        const double mu = a.sys_of ? a.G * a.m[a.offsets[a.sys_of[r]]] : a.mu;
+        const double dt = a.dt;
+        const double sqmu = sqrt(mu);
+        double r0 = sqrt(qx * qx + qy * qy + qz * qz);
+        if (r0 == 0.0) {
+            // a star row (held at Q = v = 0): stays at the origin
+            a.q1[r] = 0.0; a.q1[ld + r] = 0.0; a.q1[2 * ld + r] = 0.0;
+            a.v1[r] = 0.0; a.v1[ld + r] = 0.0; a.v1[2 * ld + r] = 0.0;
+            if (a.x_out) a.x_out[k] = 0.0;
+            if (a.iters) a.iters[k] = 0;
+            goto done;
+        }
+        {
+        double vv = vx * vx + vy * vy + vz * vz;
+        KepEq eq;
+        eq.sqmu_dt = sqmu * dt;
+        eq.r0 = r0;
+        eq.alpha = 2.0 / r0 - vv / mu;
+        eq.sig = (qx * vx + qy * vy + qz * vz) / sqmu;
+        eq.b = 1.0 - r0 * eq.alpha;
+        double x;
+        if (a.guess == QYM_GUESS_R0)
+            x = r0;
+        else if (a.guess == QYM_GUESS_MLP && a.x_guess)
+            x = (double)a.x_guess[k];
+        else
+            x = eq.sqmu_dt / r0;
+        int solver = a.solver;
+        bool conv = false;
+        double C = 0.5, S = 1.0 / 6.0;
+        // two passes at most: the requested start, then (learned guess only)
+        // Laguerre from the standard guess if the first did not converge
+        for (int pass = 0; pass < 2 && !conv; ++pass) {
+            if (pass == 1) {
+                if (a.guess != QYM_GUESS_MLP) break;
+                x = eq.sqmu_dt / r0;
+                solver = QYM_SOLVER_LAGUERRE;
+            }
+            const double tol = 1e-14;
+            for (int it = 0; it < a.max_iter; ++it) {
+                double F, Fp, Fpp;
+                eq.eval(x, F, Fp, Fpp, C, S);
+                if (fabs(F) <= tol * (fabs(eq.sqmu_dt) + r0 * fabs(x))) { conv = true; break; }
+                double dx;
+                if (solver == QYM_SOLVER_LAGUERRE) {
+                    // Laguerre, n = 5: dx = n F / (F' + sgn(F') sqrt|(n-1)^2 F'^2 - n(n-1) F F''|)
+                    double disc = fabs(16.0 * Fp * Fp - 20.0 * F * Fpp);
+                    dx = 5.0 * F / (Fp + copysign(sqrt(disc), Fp));
+                } else {
+                    dx = F / Fp;
+                }
+                x -= dx;
+                ++iters;
+                if (fabs(dx) <= 0x1p-50 * fabs(x)) { conv = true; break; }
+            }
+        }
+        // f and g functions at the root (Appendix); r before fdot, gdot
+        double x2 = x * x;
+        double y = eq.alpha * x2;
+        stumpff(y, C, S);
+        double f = 1.0 - x2 / r0 * C;
+        double g = dt - x2 * x / sqmu * S;
+        double nx = f * qx + g * vx, ny = f * qy + g * vy, nz = f * qz + g * vz;
+        double rr = sqrt(nx * nx + ny * ny + nz * nz);
+        double fd = sqmu * x * (y * S - 1.0) / (rr * r0);
+        double gd = 1.0 - x2 / rr * C;
+        double ux = fd * qx + gd * vx, uy = fd * qy + gd * vy, uz = fd * qz + gd * vz;
+        a.q1[r] = nx; a.q1[ld + r] = ny; a.q1[2 * ld + r] = nz;
+        a.v1[r] = ux; a.v1[ld + r] = uy; a.v1[2 * ld + r] = uz;
+        if (a.x_out) a.x_out[k] = x;
+        if (a.iters) a.iters[k] = iters;
+        if (a.status) {
+            int bits = 0;
+            if (!conv) bits |= QYM_ST_KEPLER_NOCONV;
+            if (!(isfinite(nx) && isfinite(ny) && isfinite(nz) && isfinite(ux) && isfinite(uy) &&
+                  isfinite(uz)))
+                bits |= QYM_ST_NAN;
+            if (bits) atomicOr(a.status, bits);
+        }
+        }
+    }
+done:
+    if (a.iter_sum) {
+        unsigned long long s = (unsigned long long)iters;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0 && s) atomicAdd(a.iter_sum, s);
+    }
+}
+
+cudaError_t launch_kepler(const KeplerArgs &a, cudaStream_t st) {
+    if (a.n <= 0) return cudaSuccess;
+    int threads = 256;
+    int64_t blocks = (a.n + threads - 1) / threads;
+    k_kepler<<<(unsigned)blocks, threads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace qym

@@ -1,0 +1,432 @@
+// kick.cu -- E_Int: all-pairs interaction accelerations (Sec. 2, Eq. 4),
+//   a_i = -sum_{j >= 1, j != i} G m_j (Q_i - Q_j) / |Q_i - Q_j|^3,
+// the star's mass zeroed (its row is simply not in any tile), fused with the
+// crude close-encounter search of the first kick of a step (Sec. 2.4).
+//
+// Work decomposition: one CTA per work item (system, i-block, j-range). The
+// i rows of the block live in registers (IPT per thread); j rows stream
+// through shared memory in tiles of TILE. Each item writes its partial sums to
+// its own slot of apart[slot][3][rows]; the finisher adds the slots in a fixed
+// order, so results are deterministic.
+//
+// Mixed precision (QYM_KICK_MIXED): positions are split into float hi + lo
+// parts, the separation is formed as (hi_i - hi_j) + (lo_i - lo_j) (a
+// double-single difference, accurate to ~1e-7 relative even for close pairs
+// far from the star), the pair force is FP32 with rsqrt, and the FP32 tile sums
+// are folded every FOLD pairs into a float two-sum (hi, lo) accumulator that
+// is returned as a double.
+#include "qym_internal.cuh"
+
+namespace qym {
+
+constexpr int TILE = 256;
+constexpr int FOLD = 32;
+
+struct KickArgs {
+    const int4 *items;
+    const int32_t *slots;
+    const float4 *pos;      // (x_hi, y_hi, z_hi, G m)
+    const float4 *lo;       // (x_lo, y_lo, z_lo, crude reach)
+    const double *q;        // [3][rows] (FP64 path)
+    const double *m;        // [rows] (FP64 path)
+    double G;
+    double *apart;
+    int64_t rows;
+    int2 *cand;
+    int64_t max_cand;
+    unsigned long long *ncand;
+    int32_t *status;
+};
+
+// append candidate (i, j) from a divergent branch, warp-aggregated
+__device__ __forceinline__ void push_candidate(const KickArgs &a, int i, int j) {
+    unsigned mask = __activemask();
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(a.ncand, (unsigned long long)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    unsigned long long idx = base + __popc(mask & ((1u << lane) - 1u));
+    if (idx < (unsigned long long)a.max_cand)
+        a.cand[idx] = make_int2(i, j);
+    else if (lane == leader)
+        atomicOr(a.status, QYM_ST_CAND_OVERFLOW);
+}
+
+template <int IPT, bool FLAG, bool DIAG>
+__device__ __forceinline__ void mixed_chunk(const float4 *__restrict__ s_pos,
+                                            const float4 *__restrict__ s_lo, int j0, int j1,
+                                            int jbase, const float (&xh)[IPT],
+                                            const float (&yh)[IPT], const float (&zh)[IPT],
+                                            const float (&xl)[IPT], const float (&yl)[IPT],
+                                            const float (&zl)[IPT], const float (&rho)[IPT],
+                                            const int (&gi)[IPT], float (&fx)[IPT],
+                                            float (&fy)[IPT], float (&fz)[IPT],
+                                            const KickArgs &a) {
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
+        const float4 p = s_pos[j];
+        const float4 l = s_lo[j];
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            float dx = (xh[k] - p.x) + (xl[k] - l.x);
+            float dy = (yh[k] - p.y) + (yl[k] - l.y);
+            float dz = (zh[k] - p.z) + (zl[k] - l.z);
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float ri = rsqrtf(r2);
+            float s = p.w * (ri * ri) * ri;
+            if (DIAG) s = (r2 > 0.0f) ? s : 0.0f;
+            fx[k] = fmaf(-s, dx, fx[k]);
+            fy[k] = fmaf(-s, dy, fy[k]);
+            fz[k] = fmaf(-s, dz, fz[k]);
+            if (FLAG) {
+                float t = rho[k] + l.w;
+                if (r2 < t * t) {
+                    int gj = jbase + j;
+                    if (gi[k] < gj) push_candidate(a, gi[k], gj);
+                }
+            }
+        }
+    }
+}
+
+template <int IPT, bool FLAG>
+__global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
+    __shared__ float4 s_pos[TILE];
+    __shared__ float4 s_lo[TILE];
+    const int4 it = a.items[blockIdx.x];
+    const int slot = a.slots[blockIdx.x];
+    float xh[IPT], yh[IPT], zh[IPT], xl[IPT], yl[IPT], zl[IPT], rho[IPT];
+    int gi[IPT];
+    float ahx[IPT], ahy[IPT], ahz[IPT], alx[IPT], aly[IPT], alz[IPT];
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+        int i = it.x + threadIdx.x + k * blockDim.x;
+        gi[k] = i;
+        if (i < it.y) {
+            float4 p = a.pos[i], l = a.lo[i];
+            xh[k] = p.x; yh[k] = p.y; zh[k] = p.z;
+            xl[k] = l.x; yl[k] = l.y; zl[k] = l.z; rho[k] = l.w;
+        } else {
+            // idle lane: park far away so its arithmetic stays finite
+            xh[k] = 1e18f; yh[k] = 1e18f; zh[k] = 1e18f;
+            xl[k] = yl[k] = zl[k] = 0.0f; rho[k] = -1e30f;
+        }
+        ahx[k] = ahy[k] = ahz[k] = alx[k] = aly[k] = alz[k] = 0.0f;
+    }
+    const int i_lo = it.x, i_hi = it.x + (int)(IPT * blockDim.x);
+    for (int jt = it.z; jt < it.w; jt += TILE) {
+        const int n = min(TILE, it.w - jt);
+        __syncthreads();
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            s_pos[t] = a.pos[jt + t];
+            s_lo[t] = a.lo[jt + t];
+        }
+        __syncthreads();
+        const bool diag = (jt < i_hi) && (jt + n > i_lo);
+        for (int c = 0; c < n; c += FOLD) {
+            const int ce = min(c + FOLD, n);
+            float fx[IPT], fy[IPT], fz[IPT];
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) fx[k] = fy[k] = fz[k] = 0.0f;
+            if (diag)
+                mixed_chunk<IPT, FLAG, true>(s_pos, s_lo, c, ce, jt, xh, yh, zh, xl, yl, zl, rho,
+                                             gi, fx, fy, fz, a);
+            else
+                mixed_chunk<IPT, FLAG, false>(s_pos, s_lo, c, ce, jt, xh, yh, zh, xl, yl, zl, rho,
+                                              gi, fx, fy, fz, a);
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                float s, e;
+                two_sum(ahx[k], fx[k], s, e); ahx[k] = s; alx[k] += e;
+                two_sum(ahy[k], fy[k], s, e); ahy[k] = s; aly[k] += e;
+                two_sum(ahz[k], fz[k], s, e); ahz[k] = s; alz[k] += e;
+            }
+        }
+    }
+    const int64_t rows = a.rows;
+    double *out = a.apart + (int64_t)slot * 3 * rows;
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+        if (gi[k] < it.y) {
+            out[gi[k]] = (double)ahx[k] + (double)alx[k];
+            out[rows + gi[k]] = (double)ahy[k] + (double)aly[k];
+            out[2 * rows + gi[k]] = (double)ahz[k] + (double)alz[k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- FP64 form
+template <int IPT, bool FLAG>
+__global__ void __launch_bounds__(256) k_kick_fp64(KickArgs a) {
+    __shared__ D4 s_q[TILE];
+    __shared__ float s_rho[TILE];
+    const int4 it = a.items[blockIdx.x];
+    const int slot = a.slots[blockIdx.x];
+    const int64_t rows = a.rows;
+    double xi[IPT], yi[IPT], zi[IPT], ax[IPT], ay[IPT], az[IPT];
+    float rho[IPT];
+    int gi[IPT];
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+        int i = it.x + threadIdx.x + k * blockDim.x;
+        gi[k] = i;
+        if (i < it.y) {
+            xi[k] = a.q[i]; yi[k] = a.q[rows + i]; zi[k] = a.q[2 * rows + i];
+            rho[k] = FLAG ? a.lo[i].w : 0.0f;
+        } else {
+            xi[k] = yi[k] = zi[k] = 1e18;
+            rho[k] = -1e30f;
+        }
+        ax[k] = ay[k] = az[k] = 0.0;
+    }
+    const double G = a.G;
+    for (int jt = it.z; jt < it.w; jt += TILE) {
+        const int n = min(TILE, it.w - jt);
+        __syncthreads();
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            int j = jt + t;
+            s_q[t] = D4{a.q[j], a.q[rows + j], a.q[2 * rows + j], G * a.m[j]};
+            if (FLAG) s_rho[t] = a.lo[j].w;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int j = 0; j < n; ++j) {
+            const D4 p = s_q[j];
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                double dx = xi[k] - p.x, dy = yi[k] - p.y, dz = zi[k] - p.z;
+                double r2 = dx * dx + dy * dy + dz * dz;
+                double ri = rsqrt(r2);
+                double s = p.w * (ri * ri) * ri;
+                s = (r2 > 0.0) ? s : 0.0;
+                ax[k] -= s * dx;
+                ay[k] -= s * dy;
+                az[k] -= s * dz;
+                if (FLAG) {
+                    float t = rho[k] + s_rho[j];
+                    if ((float)r2 < t * t) {
+                        int gj = jt + j;
+                        if (gi[k] < gj) push_candidate(a, gi[k], gj);
+                    }
+                }
+            }
+        }
+    }
+    double *out = a.apart + (int64_t)slot * 3 * rows;
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+        if (gi[k] < it.y) {
+            out[gi[k]] = ax[k];
+            out[rows + gi[k]] = ay[k];
+            out[2 * rows + gi[k]] = az[k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- items
+// Items for a batch: for each system (bodies are rows lo+1 .. hi-1), i-blocks
+// of threads*ipt rows times `splits` contiguous j-ranges. Every (i-block,
+// split) pair gets an item, even when its j-range is empty, so every slot of
+// every row is written.
+int32_t kick_items_count(const int64_t *offsets, int32_t nsys, const KickTune &t) {
+    int64_t tot = 0;
+    const int64_t ti = (int64_t)t.threads * t.ipt;
+    for (int32_t s = 0; s < nsys; ++s) {
+        int64_t nb = offsets[s + 1] - offsets[s] - 1;
+        tot += ((nb + ti - 1) / ti) * t.splits;
+    }
+    return (int32_t)tot;
+}
+
+void kick_items_host(const int64_t *offsets, int32_t nsys, const KickTune &t, int4 *items,
+                     int32_t *slots, int32_t *nitems, int32_t *splits_used, int32_t max_items) {
+    const int64_t ti = (int64_t)t.threads * t.ipt;
+    int32_t n = 0;
+    for (int32_t s = 0; s < nsys; ++s) {
+        int64_t b0 = offsets[s] + 1, b1 = offsets[s + 1];
+        int64_t nb = b1 - b0;
+        int64_t chunk = (nb + t.splits - 1) / t.splits;
+        for (int64_t i0 = b0; i0 < b1; i0 += ti) {
+            int64_t i1 = i0 + ti < b1 ? i0 + ti : b1;
+            for (int32_t sp = 0; sp < t.splits; ++sp) {
+                int64_t j0 = b0 + sp * chunk, j1 = j0 + chunk;
+                if (j0 > b1) j0 = b1;
+                if (j1 > b1) j1 = b1;
+                if (n < max_items) {
+                    items[n] = make_int4((int)i0, (int)i1, (int)j0, (int)j1);
+                    slots[n] = sp;
+                }
+                ++n;
+            }
+        }
+    }
+    *nitems = n;
+    *splits_used = t.splits;
+}
+
+template <bool FLAG>
+static cudaError_t launch_mixed(const KickArgs &a, int nitems, int threads, int ipt,
+                                cudaStream_t st) {
+    switch (ipt) {
+    case 1: k_kick_mixed<1, FLAG><<<nitems, threads, 0, st>>>(a); break;
+    case 2: k_kick_mixed<2, FLAG><<<nitems, threads, 0, st>>>(a); break;
+    case 4: k_kick_mixed<4, FLAG><<<nitems, threads, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <bool FLAG>
+static cudaError_t launch_f64(const KickArgs &a, int nitems, int threads, int ipt,
+                              cudaStream_t st) {
+    switch (ipt) {
+    case 1: k_kick_fp64<1, FLAG><<<nitems, threads, 0, st>>>(a); break;
+    case 2: k_kick_fp64<2, FLAG><<<nitems, threads, 0, st>>>(a); break;
+    default: k_kick_fp64<2, FLAG><<<nitems, threads, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kick_tiles(const Dev &d, int prec, int flag, double G, int threads, int ipt,
+                              cudaStream_t st) {
+    if (d.nitems <= 0) return cudaSuccess;
+    KickArgs a;
+    a.items = d.items;
+    a.slots = d.item_slot;
+    a.pos = d.pk_pos;
+    a.lo = d.pk_lo;
+    a.q = d.q;
+    a.m = d.m;
+    a.G = G;
+    a.apart = d.apart;
+    a.rows = d.rows;
+    a.cand = d.cand;
+    a.max_cand = d.max_cand;
+    a.ncand = d.ctr + C_NCAND;
+    a.status = d.status;
+    if (prec == QYM_KICK_MIXED)
+        return flag ? launch_mixed<true>(a, d.nitems, threads, ipt, st)
+                    : launch_mixed<false>(a, d.nitems, threads, ipt, st);
+    return flag ? launch_f64<true>(a, d.nitems, threads, ipt, st)
+                : launch_f64<false>(a, d.nitems, threads, ipt, st);
+}
+
+// ---------------------------------------------------------------- single system
+// Workspace for qym_accel_dev: packs + items + partials for one system.
+struct SingleLayout {
+    size_t off_pos, off_lo, off_items, off_slots, off_apart, total;
+    int32_t nitems, splits;
+    KickTune tune;
+};
+
+static SingleLayout single_layout(int64_t rows, int prec) {
+    SingleLayout L;
+    KickTune t;
+    t.threads = 128;
+    t.ipt = prec == QYM_KICK_MIXED ? 2 : 1;
+    int64_t nb = rows - 1;
+    int64_t ib = (nb + t.threads * t.ipt - 1) / (t.threads * t.ipt);
+    // enough CTAs to cover the GPU a few times over
+    int64_t want = 4 * 152;
+    int64_t sp = (want + ib - 1) / ib;
+    int64_t maxsp = (nb + 255) / 256;  // at least a tile of j per split
+    if (sp > maxsp) sp = maxsp;
+    if (sp < 1) sp = 1;
+    t.splits = (int32_t)sp;
+    L.tune = t;
+    L.splits = t.splits;
+    L.nitems = (int32_t)(ib * sp);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t o = 0;
+    L.off_pos = o; o = al(o + sizeof(float4) * rows);
+    L.off_lo = o; o = al(o + sizeof(float4) * rows);
+    L.off_items = o; o = al(o + sizeof(int4) * L.nitems);
+    L.off_slots = o; o = al(o + sizeof(int32_t) * L.nitems);
+    L.off_apart = o; o = al(o + sizeof(double) * 3 * rows * L.splits);
+    L.total = o;
+    return L;
+}
+
+size_t accel_single_workspace(int64_t rows, int prec) {
+    if (rows < 2) return 0;
+    return single_layout(rows, prec).total;
+}
+
+__global__ void k_pack_single(int64_t rows, const double *m, const double *q, double G,
+                              float4 *pos, float4 *lo) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    float xh, xl, yh, yl, zh, zl;
+    split_ds(q[i], xh, xl);
+    split_ds(q[rows + i], yh, yl);
+    split_ds(q[2 * rows + i], zh, zl);
+    pos[i] = make_float4(xh, yh, zh, (float)(G * m[i]));
+    lo[i] = make_float4(xl, yl, zl, 0.0f);
+}
+
+__global__ void k_items_single(int64_t rows, int32_t ti, int32_t splits, int4 *items,
+                               int32_t *slots, int32_t nitems) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nitems) return;
+    int64_t b0 = 1, b1 = rows, nb = rows - 1;
+    int64_t chunk = (nb + splits - 1) / splits;
+    int ib = idx / splits, sp = idx % splits;
+    int64_t i0 = b0 + (int64_t)ib * ti, i1 = i0 + ti < b1 ? i0 + ti : b1;
+    int64_t j0 = b0 + sp * chunk, j1 = j0 + chunk;
+    if (j0 > b1) j0 = b1;
+    if (j1 > b1) j1 = b1;
+    items[idx] = make_int4((int)i0, (int)i1, (int)j0, (int)j1);
+    slots[idx] = sp;
+}
+
+__global__ void k_sum_partials(int64_t rows, int32_t splits, const double *apart, double *a) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    for (int c = 0; c < 3; ++c) {
+        double s = 0.0;
+        if (i > 0)
+            for (int sp = 0; sp < splits; ++sp) s += apart[((int64_t)sp * 3 + c) * rows + i];
+        a[c * rows + i] = s;
+    }
+}
+
+cudaError_t launch_accel_single(int64_t rows, const double *m, const double *q, double *a,
+                                double G, int prec, void *work, size_t work_bytes,
+                                cudaStream_t st) {
+    SingleLayout L = single_layout(rows, prec);
+    if (work_bytes < L.total) return cudaErrorInvalidValue;
+    char *w = (char *)work;
+    Dev d;
+    d.rows = rows;
+    d.m = m ? const_cast<double *>(m) : nullptr;
+    d.q = const_cast<double *>(q);
+    d.pk_pos = (float4 *)(w + L.off_pos);
+    d.pk_lo = (float4 *)(w + L.off_lo);
+    d.items = (int4 *)(w + L.off_items);
+    d.item_slot = (int32_t *)(w + L.off_slots);
+    d.apart = (double *)(w + L.off_apart);
+    d.nitems = L.nitems;
+    d.splits = L.splits;
+    int tb = 256;
+    k_pack_single<<<(unsigned)((rows + tb - 1) / tb), tb, 0, st>>>(rows, m, q, G, d.pk_pos,
+                                                                    d.pk_lo);
+    k_items_single<<<(L.nitems + tb - 1) / tb, tb, 0, st>>>(rows, L.tune.threads * L.tune.ipt,
+                                                             L.splits, d.items, d.item_slot,
+                                                             L.nitems);
+    cudaError_t e;
+    if (prec == QYM_KICK_MIXED) {
+        e = launch_kick_tiles(d, prec, 0, G, L.tune.threads, L.tune.ipt, st);
+    } else {
+        KickArgs ka;
+        ka.items = d.items; ka.slots = d.item_slot; ka.pos = d.pk_pos; ka.lo = d.pk_lo;
+        ka.q = q; ka.m = m; ka.G = G; ka.apart = d.apart; ka.rows = rows;
+        ka.cand = nullptr; ka.max_cand = 0; ka.ncand = nullptr; ka.status = nullptr;
+        e = launch_f64<false>(ka, L.nitems, L.tune.threads, L.tune.ipt, st);
+    }
+    if (e != cudaSuccess) return e;
+    k_sum_partials<<<(unsigned)((rows + tb - 1) / tb), tb, 0, st>>>(rows, L.splits, d.apart, a);
+    return cudaGetLastError();
+}
+
+}  // namespace qym

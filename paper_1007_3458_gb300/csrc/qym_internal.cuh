@@ -1,0 +1,187 @@
+// qym_internal.cuh -- device helpers and launch declarations shared by the
+// libqym translation units (sm_103a). Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qym.h"
+
+namespace qym {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------- layout
+// Device state of a context. Rows of all systems are concatenated; each
+// system's star sits at its first row with Q = v = 0. Positions and
+// velocities are float64 structure-of-arrays [3][rows].
+struct Dev {
+    int64_t rows = 0;
+    int32_t nsys = 0;
+    int64_t *offsets = nullptr;   // [nsys+1]
+    int32_t *sys_of = nullptr;    // [rows] system of each row
+    double *m = nullptr;          // [rows]
+    double *q = nullptr, *v = nullptr;     // [3][rows] current state (DH)
+    double *q1 = nullptr, *v1 = nullptr;   // [3][rows] Kepler output / step scratch
+    double *rH = nullptr;         // [rows] Hill radius used by this step's encounter test
+    double *rH_fixed = nullptr;   // [rows] Hill radii computed at init (hill_fixed)
+    // kick operand packs, float32 (rebuilt from the FP64 state every step)
+    float4 *pk_pos = nullptr;     // (x_hi, y_hi, z_hi, G m)
+    float4 *pk_lo = nullptr;      // (x_lo, y_lo, z_lo, crude reach rho)
+    float *amag = nullptr;        // [rows] |a_int| of the last kick
+    float *rH_bound = nullptr;    // [rows] Hill radius bound used by the crude test
+    double *apart = nullptr;      // [splits][3][rows] kick partial accelerations
+    int32_t splits = 1;
+    // kick work items (one CTA each): (i0, i1, j0, j1) and the partial slot
+    int4 *items = nullptr;
+    int32_t *item_slot = nullptr;
+    int32_t nitems = 0;
+    // momentum reduction
+    int4 *mchunks = nullptr;      // (row0, row1, sys, -) chunks of at most 1024 rows
+    int32_t nmchunks = 0;
+    double *mpart = nullptr;      // [nmchunks][3]
+    int32_t *sys_chunk0 = nullptr;  // [nsys+1] first chunk of each system
+    double *S = nullptr;          // [nsys][3] sum of m v over bodies
+    // encounters
+    int2 *cand = nullptr;         // crude candidate pairs (i < j)
+    int64_t max_cand = 0;
+    int2 *enc = nullptr;          // rigorous encounter pairs
+    int64_t max_enc = 0;
+    int32_t *rescan = nullptr;    // rows whose crude bounds were exceeded
+    int32_t *set_start = nullptr; // [max_sets+1]
+    int32_t *set_mem = nullptr;   // [max_members]
+    double *rcrit = nullptr;      // [max_sets]
+    int32_t max_sets = 0, max_members = 0;
+    int32_t *uf = nullptr;        // [rows] union-find parents, kept at -1 when idle
+    int64_t *log = nullptr;       // [max_log][3] encounter records of one qym_step call
+    int64_t max_log = 0;
+    // counters (device): see Counters below
+    unsigned long long *ctr = nullptr;
+    int32_t *status = nullptr;    // QYM_ST_* bits
+};
+
+// device counters, indices into Dev::ctr
+enum Ctr : int {
+    C_NCAND = 0,     // candidates this step (reset per step)
+    C_NENC,          // encounter pairs this step (reset per step)
+    C_NRESCAN,       // rows to re-search this step (reset per step)
+    C_NSETS,         // sets this step (written by the set builder)
+    C_NMEM,          // set members this step
+    C_LOG,           // records in the encounter log (per qym_step call)
+    C_SUM_CAND,      // running sums over the steps of one qym_step call
+    C_SUM_ENC,
+    C_SUM_SETS,
+    C_MAX_SET,
+    C_SUM_KITER,
+    C_SUM_HSTEPS,
+    C_SUM_RESCAN,
+    C_STEP,          // step index within the current qym_step call
+    C_COUNT
+};
+
+// ---------------------------------------------------------------- helpers
+struct alignas(32) D4 {
+    double x, y, z, w;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ float warp_min(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// split a double into a float pair with hi + lo == x to ~2^-48 relative
+__device__ __forceinline__ void split_ds(double x, float &hi, float &lo) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - (double)hi);
+}
+
+// ---------------------------------------------------------------- launches
+// Each returns cudaSuccess or the launch error. All work goes on `st`.
+
+// kepler.cu
+struct KeplerArgs {
+    int64_t n;            // bodies
+    const double *q0, *v0; // [3][ld] inputs
+    double *q1, *v1;       // [3][ld] outputs
+    int64_t ld;            // leading dimension (stride between x, y, z blocks)
+    const int64_t *rows;   // optional row map: body k is row rows[k]; NULL = identity
+    double mu, dt;
+    int32_t solver, guess, max_iter;
+    const float *x_guess;  // [n] or NULL
+    double *x_out;         // [n] or NULL
+    int32_t *iters;        // [n] or NULL
+    int32_t *status;       // or NULL
+    unsigned long long *iter_sum;  // or NULL
+    // per-row gravitational parameter mu = G m[star of row] when sys_of != NULL
+    const int32_t *sys_of;
+    const int64_t *offsets;
+    const double *m;
+    double G;
+};
+cudaError_t launch_kepler(const KeplerArgs &a, cudaStream_t st);
+
+// step kernels (step.cu)
+cudaError_t launch_momentum(const Dev &d, cudaStream_t st);
+cudaError_t launch_drift_pack_from(const Dev &d, const double *qs, const double *vs,
+                                   double h_close, double h_open, double tau, double a_E,
+                                   double G, int flag_next, int hill_fixed, cudaStream_t st);
+cudaError_t launch_kick_finish_v(const Dev &d, double *v, const double *q, double dt, double G,
+                                 int check, int hill_fixed, cudaStream_t st);
+cudaError_t launch_hill_init(const Dev &d, double G, cudaStream_t st);
+cudaError_t launch_to_dh_impl(const Dev &d, int inverse, double *vout, double *mt_scratch,
+                              cudaStream_t st);
+
+// kick.cu
+struct KickTune {
+    int32_t threads = 128;  // threads per CTA
+    int32_t ipt = 2;        // i rows per thread
+    int32_t splits = 1;     // j splits per system
+};
+cudaError_t launch_kick_tiles(const Dev &d, int prec, int flag, double G, int threads, int ipt,
+                              cudaStream_t st);
+cudaError_t launch_accel_single(int64_t rows, const double *m, const double *q, double *a,
+                                double G, int prec, void *work, size_t work_bytes,
+                                cudaStream_t st);
+size_t accel_single_workspace(int64_t rows, int prec);
+void kick_items_host(const int64_t *offsets, int32_t nsys, const KickTune &t,
+                     int4 *items, int32_t *slots, int32_t *nitems, int32_t *splits_used,
+                     int32_t max_items);
+int32_t kick_items_count(const int64_t *offsets, int32_t nsys, const KickTune &t);
+
+// encounter.cu
+struct SetScratch {
+    int32_t *blk, *sid, *size, *fill;
+    unsigned long long *rc_bits;
+};
+cudaError_t launch_refine(const Dev &d, double tau, double a_E, cudaStream_t st);
+cudaError_t launch_sets_impl(const Dev &d, double a_H, const SetScratch &s, cudaStream_t st);
+cudaError_t launch_pair_test(int64_t rows, const double *q0, const double *v0, const double *q1,
+                             const double *v1, const double *rH, double tau, double a_E,
+                             int64_t npairs, const int32_t *pairs, double *d2, int32_t *flag,
+                             cudaStream_t st);
+
+// hermite.cu
+cudaError_t hermite_prepare();
+cudaError_t launch_hermite(const Dev &d, const qym_params &p, double tau, cudaStream_t st);
+
+// energy.cu
+int32_t energy_items_host(const int64_t *offsets, int32_t nsys, int4 *items, int32_t *isys,
+                          int32_t *item0);
+cudaError_t launch_energy_items(int32_t nitems, const int4 *items, const int32_t *isys,
+                                const int32_t *item0, int32_t nsys, const int64_t *offsets,
+                                int64_t R, const double *m, const double *q, const double *v,
+                                double G, double *part, double *E, cudaStream_t st);
+
+}  // namespace qym

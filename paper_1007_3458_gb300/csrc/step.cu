@@ -1,0 +1,290 @@
+// step.cu -- the O(N) kernels of a step: the barycentric-momentum reduction and
+// the uniform shift of E_Dft (Sec. 2, Eq. 2), the kick finisher (adds the
+// partial accelerations, updates velocities, records |a| and the Hill radii
+// used by the encounter test), Hill radii (Eq. 9), and the heliocentric <->
+// barycentric velocity conversion (Sec. 2).
+#include "qym_internal.cuh"
+
+namespace qym {
+
+__device__ __forceinline__ bool is_star(const Dev &d, int64_t r) {
+    return d.offsets[d.sys_of[r]] == r;
+}
+
+// ---------------------------------------------------------------- E_Dft
+// chunk partial sums of m_i v_i (bodies only), deterministic tree order
+__global__ void __launch_bounds__(256) k_mom_chunks(Dev d) {
+    const int4 ch = d.mchunks[blockIdx.x];
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    const int64_t R = d.rows;
+    for (int64_t r = ch.x + threadIdx.x; r < ch.y; r += blockDim.x) {
+        if (is_star(d, r)) continue;
+        double mm = d.m[r];
+        sx += mm * d.v[r];
+        sy += mm * d.v[R + r];
+        sz += mm * d.v[2 * R + r];
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    sz = warp_sum(sz);
+    __shared__ double sh[3][8];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sh[0][w] = sx; sh[1][w] = sy; sh[2][w] = sz; }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[threadIdx.x][k];
+        d.mpart[3 * blockIdx.x + threadIdx.x] = t;
+    }
+}
+
+__global__ void k_mom_final(Dev d) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.nsys) return;
+    double t[3] = {0.0, 0.0, 0.0};
+    for (int c = d.sys_chunk0[s]; c < d.sys_chunk0[s + 1]; ++c)
+        for (int k = 0; k < 3; ++k) t[k] += d.mpart[3 * c + k];
+    for (int k = 0; k < 3; ++k) d.S[3 * s + k] = t[k];
+}
+
+cudaError_t launch_momentum(const Dev &d, cudaStream_t st) {
+    k_mom_chunks<<<d.nmchunks, 256, 0, st>>>(d);
+    k_mom_final<<<(d.nsys + 127) / 128, 128, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+// Hill radius from the osculating orbit about the star (mu = G m0):
+// r_H = a (m / 3 m0)^(1/3), a = 1/alpha when bound, else the distance
+__device__ __forceinline__ double hill(double qx, double qy, double qz, double vx, double vy,
+                                       double vz, double m, double m0, double mu) {
+    double r = sqrt(qx * qx + qy * qy + qz * qz);
+    double alpha = 2.0 / r - (vx * vx + vy * vy + vz * vz) / mu;
+    double a = alpha > 0.0 ? 1.0 / alpha : r;
+    return a * cbrt(m / (3.0 * m0));
+}
+
+__device__ __forceinline__ float round_up_f(double x) {
+    float f = __double2float_ru(x);
+    return f;
+}
+
+// E_Dft: Q += h S / m0 for h_close then h_open (each a separate half-drift,
+// Sec. 2.3 items 10 and 1), read from (qs, vs) and written to (d.q, d.v);
+// then the float packs of the coming kick, with the crude encounter reach when
+// the coming kick searches for encounters (Sec. 2.4).
+struct DriftArgs {
+    const double *qs, *vs;
+    double h_close, h_open, tau, a_E, G;
+    int flag_next, hill_fixed;
+};
+
+__global__ void __launch_bounds__(256) k_drift_pack(Dev d, DriftArgs a) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= d.rows) return;
+    const int64_t R = d.rows;
+    const int sys = d.sys_of[r];
+    const int64_t star = d.offsets[sys];
+    double qx = a.qs[r], qy = a.qs[R + r], qz = a.qs[2 * R + r];
+    double vx = a.vs[r], vy = a.vs[R + r], vz = a.vs[2 * R + r];
+    if (r == star) {
+        qx = qy = qz = vx = vy = vz = 0.0;
+    } else {
+        const double m0 = d.m[star];
+        const double Sx = d.S[3 * sys], Sy = d.S[3 * sys + 1], Sz = d.S[3 * sys + 2];
+        if (a.h_close != 0.0) {
+            qx += a.h_close * Sx / m0;
+            qy += a.h_close * Sy / m0;
+            qz += a.h_close * Sz / m0;
+        }
+        if (a.h_open != 0.0) {
+            qx += a.h_open * Sx / m0;
+            qy += a.h_open * Sy / m0;
+            qz += a.h_open * Sz / m0;
+        }
+    }
+    d.q[r] = qx; d.q[R + r] = qy; d.q[2 * R + r] = qz;
+    if (a.vs != d.v) { d.v[r] = vx; d.v[R + r] = vy; d.v[2 * R + r] = vz; }
+    float xh, xl, yh, yl, zh, zl;
+    split_ds(qx, xh, xl);
+    split_ds(qy, yh, yl);
+    split_ds(qz, zh, zl);
+    const double mm = d.m[r];
+    float reach = 0.0f;
+    if (a.flag_next && r != star) {
+        // crude reach rho_i = F_i (R_i + |tau| (u_i + w_i)):
+        //   R_i  a_E times a bound on this step's Hill radius
+        //   u_i  speed relative to the local circular velocity Omega (z x Q)
+        //   w_i  bound on the coming half-kick's velocity change, (tau/2)|a|
+        //   F_i  stretch for the Keplerian shear over one step
+        const double m0 = d.m[star];
+        const double mu = a.G * m0;
+        double rH;
+        if (a.hill_fixed) {
+            rH = d.rH_fixed[r];
+        } else {
+            rH = 1.25 * hill(qx, qy, qz, vx, vy, vz, mm, m0, mu);
+        }
+        float rHb = round_up_f(rH * (1.0 + 1e-6));
+        d.rH_bound[r] = rHb;
+        double rr = sqrt(qx * qx + qy * qy + qz * qz);
+        double Om = sqrt(mu / (rr * rr * rr));
+        double ux = vx + Om * qy, uy = vy - Om * qx, uz = vz;
+        double u = sqrt(ux * ux + uy * uy + uz * uz);
+        double w = 0.5 * fabs(a.tau) * 1.01 * (double)d.amag[r];
+        double sh = fmin(0.8, 2.5 * Om * fabs(a.tau));
+        double F = 2.0 / (1.0 - sh);
+        double rho = F * (a.a_E * (double)rHb + fabs(a.tau) * (u + w)) + 1e-12 * rr;
+        reach = round_up_f(rho);
+    }
+    d.pk_pos[r] = make_float4(xh, yh, zh, (float)(a.G * mm));
+    d.pk_lo[r] = make_float4(xl, yl, zl, reach);
+}
+
+cudaError_t launch_drift_pack_from(const Dev &d, const double *qs, const double *vs,
+                                   double h_close, double h_open, double tau, double a_E,
+                                   double G, int flag_next, int hill_fixed, cudaStream_t st) {
+    DriftArgs a;
+    a.qs = qs;
+    a.vs = vs;
+    a.h_close = h_close;
+    a.h_open = h_open;
+    a.tau = tau;
+    a.a_E = a_E;
+    a.G = G;
+    a.flag_next = flag_next;
+    a.hill_fixed = hill_fixed;
+    int tb = 256;
+    k_drift_pack<<<(unsigned)((d.rows + tb - 1) / tb), tb, 0, st>>>(d, a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- kick finish
+// v += dt * sum over slots of the partial accelerations (fixed slot order);
+// |a| is kept for the next crude search. After the first kick of a step
+// (check != 0) the Hill radius of this step is computed from the state that
+// enters the Kepler drift, and rows whose crude-search bounds (|a| allowance,
+// Hill radius bound) were exceeded are queued for an exact re-search.
+struct FinishArgs {
+    double *v;          // velocities to update ([3][rows])
+    const double *q;    // positions (for the Hill radius)
+    double dt, G;
+    int check, hill_fixed;
+};
+
+__global__ void __launch_bounds__(256) k_finish(Dev d, FinishArgs a) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= d.rows) return;
+    const int sys = d.sys_of[r];
+    const int64_t star = d.offsets[sys];
+    if (r == star) return;
+    const int64_t R = d.rows;
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int s = 0; s < d.splits; ++s) {
+        const double *p = d.apart + (int64_t)s * 3 * R;
+        ax += p[r];
+        ay += p[R + r];
+        az += p[2 * R + r];
+    }
+    double vx = a.v[r] + a.dt * ax;
+    double vy = a.v[R + r] + a.dt * ay;
+    double vz = a.v[2 * R + r] + a.dt * az;
+    a.v[r] = vx; a.v[R + r] = vy; a.v[2 * R + r] = vz;
+    float an = round_up_f(sqrt(ax * ax + ay * ay + az * az));
+    if (a.check) {
+        bool bad = an > 1.01f * d.amag[r] + 1e-30f;
+        const double m0 = d.m[star];
+        double rH = a.hill_fixed ? d.rH_fixed[r]
+                                 : hill(a.q[r], a.q[R + r], a.q[2 * R + r], vx, vy, vz, d.m[r],
+                                        m0, a.G * m0);
+        d.rH[r] = rH;
+        if (rH > (double)d.rH_bound[r]) bad = true;
+        if (bad) {
+            unsigned long long k = atomicAdd(d.ctr + C_NRESCAN, 1ull);
+            if (k < (unsigned long long)R) d.rescan[k] = (int32_t)r;
+        }
+    }
+    d.amag[r] = an;
+}
+
+cudaError_t launch_kick_finish_v(const Dev &d, double *v, const double *q, double dt, double G,
+                                 int check, int hill_fixed, cudaStream_t st) {
+    FinishArgs a;
+    a.v = v;
+    a.q = q;
+    a.dt = dt;
+    a.G = G;
+    a.check = check;
+    a.hill_fixed = hill_fixed;
+    int tb = 256;
+    k_finish<<<(unsigned)((d.rows + tb - 1) / tb), tb, 0, st>>>(d, a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Hill radii at init
+__global__ void k_hill_init(Dev d, double G) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= d.rows) return;
+    const int64_t R = d.rows;
+    const int64_t star = d.offsets[d.sys_of[r]];
+    if (r == star) { d.rH_fixed[r] = 0.0; return; }
+    const double m0 = d.m[star];
+    d.rH_fixed[r] = hill(d.q[r], d.q[R + r], d.q[2 * R + r], d.v[r], d.v[R + r], d.v[2 * R + r],
+                         d.m[r], m0, G * m0);
+}
+
+cudaError_t launch_hill_init(const Dev &d, double G, cudaStream_t st) {
+    int tb = 256;
+    k_hill_init<<<(unsigned)((d.rows + tb - 1) / tb), tb, 0, st>>>(d, G);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- coordinates
+// Barycentric velocity of body i: V_i = v_i - sum_k m_k v_k / (m0 + sum_k m_k)
+// (heliocentric -> DH, inverse = 0, in place on d.v); heliocentric velocity:
+// v_i = V_i + S / m0 with S = sum_k m_k V_k (inverse = 1, into vout).
+// Needs d.S = sum m v of the input velocities and, for the forward direction,
+// the total body mass per system in mt.
+__global__ void k_mass_total(Dev d, double *mt) {
+    int s = blockIdx.x;
+    int64_t lo = d.offsets[s], hi = d.offsets[s + 1];
+    double t = 0.0;
+    for (int64_t r = lo + 1 + threadIdx.x; r < hi; r += blockDim.x) t += d.m[r];
+    t = warp_sum(t);
+    __shared__ double sh[8];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) u += sh[k];
+        mt[s] = d.m[lo] + u;
+    }
+}
+
+__global__ void k_to_dh(Dev d, int inverse, const double *mt, double *vout) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= d.rows) return;
+    const int64_t R = d.rows;
+    const int sys = d.sys_of[r];
+    const int64_t star = d.offsets[sys];
+    double *dst = inverse ? vout : d.v;
+    if (r == star) {
+        dst[r] = dst[R + r] = dst[2 * R + r] = 0.0;
+        return;
+    }
+    double den = inverse ? -d.m[star] : mt[sys];
+    for (int c = 0; c < 3; ++c) dst[c * R + r] = d.v[c * R + r] - d.S[3 * sys + c] / den;
+}
+
+cudaError_t launch_to_dh_impl(const Dev &d, int inverse, double *vout, double *mt_scratch,
+                              cudaStream_t st) {
+    cudaError_t e = launch_momentum(d, st);
+    if (e != cudaSuccess) return e;
+    if (!inverse) {
+        k_mass_total<<<d.nsys, 256, 0, st>>>(d, mt_scratch);
+    }
+    int tb = 256;
+    k_to_dh<<<(unsigned)((d.rows + tb - 1) / tb), tb, 0, st>>>(d, inverse, mt_scratch, vout);
+    return cudaGetLastError();
+}
+
+}  // namespace qym

@@ -1,0 +1,60 @@
+"""The C-ABI library loads without a GPU and exports every function that
+include/qym.h declares; its parameter defaults and argument checks behave as
+documented there (no GPU computation is run)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1007_3458_gb300 as q
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "qym.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(qym_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    q.build()
+    return q.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+        ctypes.cast(getattr(lib, n), ctypes.c_void_p)
+
+
+def test_header_struct_layout_matches_binding():
+    # qym_params: 6 doubles, 8 int32, 4 int64 = 48 + 32 + 32 bytes
+    assert ctypes.sizeof(q.qym_params) == 112
+    assert ctypes.sizeof(q.qym_stats) == 8 * 8 + 4 * 3 + 4
+
+
+def test_defaults(lib):
+    p = q.qym_default_params()
+    assert (p.G, p.a_E, p.a_H, p.eps_H, p.eta, p.eta_s) == (1.0, 3.0, 1.0, 0.0, 0.02, 0.01)
+    assert p.kick_prec == q.QYM_KICK_MIXED and p.encounters == 1 and p.max_kepler_iter == 50
+
+
+def test_argument_checks_without_gpu(lib):
+    p = q.qym_default_params()
+    with pytest.raises(q.QymError) as e:
+        q.qym_init(p, [0, 1], [1.0], np.zeros((1, 3)), np.zeros((1, 3)))
+    assert e.value.status == q.QYM_EINVAL  # a system without bodies
+    p.eta = -1
+    with pytest.raises(q.QymError) as e:
+        q.qym_init(p, [0, 2], [1.0, 1e-3], np.zeros((2, 3)), np.zeros((2, 3)))
+    assert e.value.status == q.QYM_EINVAL
+    assert lib.qym_kepler_drift_dev(-1, None, None, None, None, 1.0, 1.0, 0, 0, None, 50, None,
+                                    None, None, None) == q.QYM_EINVAL
+    assert lib.qym_accel_workspace_bytes(1, 1) == 0
+    assert lib.qym_accel_workspace_bytes(16385, 1) > 16385 * 3 * 8

@@ -1,0 +1,148 @@
+"""GPU parity of the whole hybrid DH step (Sec. 2, Eq. 5; procedure of
+Sec. 2.3) through the context API against the oracle's step on the same
+seeded disks: positions, velocities, encounter lists, energy; batched systems;
+error statuses."""
+import numpy as np
+import pytest
+
+import paper_1007_3458_gb300 as q
+from paper_1007_3458_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    q.build()
+    q.lib()
+    return t
+
+
+def _run_gpu(w, nsteps, **prm):
+    sim = q.Simulation(w.m, w.q, w.v, w.offsets, **prm)
+    sim.step(w.tau, nsteps)
+    qq, vv = sim.state()
+    enc = sim.encounters()
+    st = sim.stats()
+    E = sim.energy()
+    sim.close()
+    return qq, vv, enc, st, E
+
+
+def _run_oracle(oracle, w, nsteps, **prm):
+    vd = oracle.helio_to_dh(w.m, w.v)
+    r = oracle.step(w.m, w.q, vd, w.offsets, w.tau, nsteps, oracle.params(**prm))
+    vh = np.concatenate([oracle.dh_to_helio(w.m[a:b], r.v[a:b])
+                         for a, b in zip(w.offsets[:-1], w.offsets[1:])])
+    return r, vh
+
+
+def _relq(a, b):
+    n = np.linalg.norm(b, axis=1)
+    n[n == 0] = 1
+    return np.linalg.norm(a - b, axis=1) / n
+
+
+def test_fp64_plain_step_100_steps(gpu, oracle):
+    """Plain DH step (no encounter search), FP64 kick, 100 steps of the
+    260-body disk: positions within 1e-12 relative."""
+    w = W.disk_260()
+    qg, vg, enc, st, E = _run_gpu(w, 100, kick_prec=q.QYM_KICK_FP64, encounters=0)
+    r, vh = _run_oracle(oracle, w, 100, encounters=0)
+    assert _relq(qg, r.q).max() <= 1e-12
+    assert _relq(vg, vh).max() <= 1e-11
+    assert len(enc) == 0
+
+
+def test_fp64_hybrid_step_with_encounters(gpu, oracle):
+    """Hybrid step with encounters on the 260-body disk for 100 steps, FP64
+    kick: same encounter records (step, i, j) as the oracle's all-pairs test,
+    positions within 1e-12 relative."""
+    w = W.disk_260()
+    qg, vg, enc, st, E = _run_gpu(w, 100, kick_prec=q.QYM_KICK_FP64)
+    r, vh = _run_oracle(oracle, w, 100)
+    assert len(r.encounters) > 0
+    assert np.array_equal(enc, r.encounters)
+    assert st["encounters"] >= len(r.encounters) and st["hermite_steps"] > 0
+    assert _relq(qg, r.q).max() <= 1e-12
+    assert _relq(vg, vh).max() <= 1e-11
+
+
+def test_mixed_hybrid_step(gpu, oracle):
+    """Mixed-precision kick: encounter records equal, positions close, and the
+    energy error matches the oracle's to well below the step's own error."""
+    w = W.disk_260()
+    qg, vg, enc, st, E = _run_gpu(w, 100)
+    r, vh = _run_oracle(oracle, w, 100)
+    assert np.array_equal(enc, r.encounters)
+    assert _relq(qg, r.q).max() <= 1e-9
+    vd = oracle.helio_to_dh(w.m, w.v)
+    E0 = oracle.energy(w.m, w.q, vd)
+    Eo = oracle.energy(w.m, r.q, r.v)
+    assert abs(E[0] - Eo) <= 1e-9 * abs(E0)
+
+
+def test_batched_systems(gpu, oracle):
+    """Several independent systems of uneven size in one context (ensemble
+    shape, planets at a = 1 and 1.6): every system matches the oracle."""
+    w = W.ensemble(nsys=6, n_lo=40, n_hi=300, seed=5, nsteps=30)
+    qg, vg, enc, st, E = _run_gpu(w, 30, kick_prec=q.QYM_KICK_FP64)
+    r, vh = _run_oracle(oracle, w, 30)
+    assert np.array_equal(enc, r.encounters)
+    assert _relq(qg, r.q).max() <= 1e-11
+    vd = np.concatenate([oracle.helio_to_dh(w.m[a:b], w.v[a:b])
+                         for a, b in zip(w.offsets[:-1], w.offsets[1:])])
+    Eo = [oracle.energy(w.m[a:b], r.q[a:b], r.v[a:b]) for a, b in zip(w.offsets[:-1], w.offsets[1:])]
+    assert np.allclose(E, Eo, rtol=1e-12, atol=0)
+
+
+def test_16384_disk_steps(gpu, oracle):
+    """The 16384-body disk, 3 steps, FP64 kick: positions within 1e-12."""
+    w = W.disk_16384()
+    qg, vg, enc, st, E = _run_gpu(w, 3, kick_prec=q.QYM_KICK_FP64)
+    r, vh = _run_oracle(oracle, w, 3)
+    assert np.array_equal(enc, r.encounters)
+    assert _relq(qg, r.q).max() <= 1e-12
+
+
+def test_state_round_trip_and_resume(gpu, oracle):
+    """get_state / set_state resume: 20 steps in one call equal 10 + 10 steps
+    with a host round trip of the state in between."""
+    w = W.subsample(W.disk_260(), 60, seed=3)
+    a = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=q.QYM_KICK_FP64)
+    a.step(w.tau, 20)
+    qa, va = a.state()
+    b = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=q.QYM_KICK_FP64)
+    b.step(w.tau, 10)
+    qm, vm = b.state()
+    b.set_state(qm, vm)
+    b.step(w.tau, 10)
+    qb, vb = b.state()
+    a.close()
+    b.close()
+    assert _relq(qb, qa).max() <= 1e-13
+
+
+def test_error_statuses(gpu):
+    """Capacities and caps report statuses; the context stays usable."""
+    w = W.disk_260()
+    sim = q.Simulation(w.m, w.q, w.v, w.offsets, max_candidates=1)
+    with pytest.raises(q.QymError) as e:
+        sim.step(w.tau, 30)
+    assert e.value.status == q.QYM_EOVERFLOW
+    sim.close()
+    sim = q.Simulation(w.m, w.q, w.v, w.offsets, max_kepler_iter=1, encounters=0)
+    with pytest.raises(q.QymError) as e:
+        sim.step(w.tau, 2)
+    assert e.value.status == q.QYM_ENOCONV
+    qq, vv = sim.state()
+    assert np.all(np.isfinite(qq))
+    sim.close()
+    bad = w.q.copy()
+    bad[5, 0] = np.nan
+    with pytest.raises(q.QymError) as e:
+        q.Simulation(w.m, bad, w.v, w.offsets)
+    assert e.value.status == q.QYM_EINVAL
