@@ -90,7 +90,7 @@ def lib():
                                      C.c_double, C.c_double, C.c_double, C.c_double, C.c_int64, I64]
         L.or_hermite_set.restype = C.c_int
         L.or_step.argtypes = [C.c_int64, D, D, D, C.POINTER(Params), C.c_double, C.c_int64,
-                              C.c_int64, D, I64, C.c_int64, I64, I64]
+                              C.c_int64, D, I64, D, C.c_int64, I64, I64]
         L.or_step.restype = C.c_int
     return _lib
 
@@ -308,6 +308,7 @@ class StepResult:
     q: np.ndarray
     v: np.ndarray
     encounters: np.ndarray   # [k, 3] (step, i, j) with global row indices
+    enc_d2: np.ndarray       # [k, 2] (d_min^2, threshold^2) of each record
     stats: np.ndarray        # pairs, sets, largest set, Kepler iterations, Hermite steps, Kepler failures
     status: int
 
@@ -323,6 +324,7 @@ def step(m, q, v, offsets, tau, nsteps, prm: Params | None = None, step0=0,
     v = _f64(v, (-1, 3)).copy()
     offsets = np.asarray(offsets, dtype=np.int64)
     encs = []
+    d2s = []
     stats = np.zeros(6, dtype=np.int64)
     status = 0
     for s in range(len(offsets) - 1):
@@ -334,12 +336,13 @@ def step(m, q, v, offsets, tau, nsteps, prm: Params | None = None, step0=0,
         cap = 1 << 14
         while True:
             enc = np.zeros((cap, 3), dtype=np.int64)
+            ed2 = np.zeros((cap, 2))
             cnt = np.zeros(1, dtype=np.int64)
             qt, vt = qs.copy(), vs.copy()
             st_s = np.zeros(6, dtype=np.int64)
             st = lib().or_step(hi - lo, _d(ms), _d(qt), _d(vt), C.byref(prm), tau, nsteps, step0,
-                               None if rhs is None else _d(rhs), _i64(enc), cap, _i64(cnt),
-                               _i64(st_s))
+                               None if rhs is None else _d(rhs), _i64(enc), _d(ed2), cap,
+                               _i64(cnt), _i64(st_s))
             if cnt[0] <= cap:
                 break
             cap = int(cnt[0])
@@ -348,8 +351,9 @@ def step(m, q, v, offsets, tau, nsteps, prm: Params | None = None, step0=0,
         e = enc[:cnt[0]].copy()
         e[:, 1:] += lo
         encs.append(e)
+        d2s.append(ed2[:cnt[0]].copy())
         stats[[0, 1, 3, 4, 5]] += st_s[[0, 1, 3, 4, 5]]
         stats[2] = max(stats[2], st_s[2])
         status = status or st
-    return StepResult(q, v, np.concatenate(encs) if encs else np.zeros((0, 3), np.int64), stats,
-                      status)
+    return StepResult(q, v, np.concatenate(encs) if encs else np.zeros((0, 3), np.int64),
+                      np.concatenate(d2s) if d2s else np.zeros((0, 2)), stats, status)

@@ -280,11 +280,16 @@ double or_energy(int64_t rows, const double *m, const double *q, const double *v
         E += 0.5 * m[i] * dot3(v + 3 * i, v + 3 * i);
         E -= G * m[0] * m[i] / sqrt(dot3(q + 3 * i, q + 3 * i));
     }
-    for (int64_t i = 1; i < rows; ++i)
+    /* pair terms summed per row first: added one by one to E, terms of
+     * light pairs (m_i m_j / r ~ 1e-21) fall below half an ulp of E and vanish */
+    for (int64_t i = 1; i < rows; ++i) {
+        double row = 0.0;
         for (int64_t j = i + 1; j < rows; ++j) {
             double d[3] = {q[3 * i] - q[3 * j], q[3 * i + 1] - q[3 * j + 1], q[3 * i + 2] - q[3 * j + 2]};
-            E -= G * m[i] * m[j] / sqrt(dot3(d, d));
+            row += m[j] / sqrt(dot3(d, d));
         }
+        E -= G * m[i] * row;
+    }
     return E;
 }
 
@@ -665,7 +670,8 @@ int or_hermite_set(int64_t k, const int64_t *mem, const double *m, double m0, do
 /* ------------------------------------------------------------------ */
 /* Sec. 2, Eq. 5 and Sec. 2.3: one system, nsteps hybrid DH steps.      */
 /* q, v: DH state (heliocentric Q, barycentric v), star row zero.       */
-/* enc: (step, i, j) records up to enc_cap; *enc_count gets the total.  */
+/* enc: (step, i, j) records up to enc_cap, enc_d2 (optional) their     */
+/* (d_min^2, threshold^2); *enc_count gets the total.                   */
 /* stats[0..5]: encounter pairs, sets, largest set, Kepler iterations,  */
 /* Hermite steps, Kepler non-convergences (summed over steps).          */
 /* rH_fixed: NULL -> Hill radii from the orbit entering each Kepler step  */
@@ -673,8 +679,8 @@ int or_hermite_set(int64_t k, const int64_t *mem, const double *m, double m0, do
 /* Returns 0, or a nonzero status (1 Kepler, 2 Hermite cap).            */
 /* ------------------------------------------------------------------ */
 int or_step(int64_t rows, const double *m, double *q, double *v, const or_params *p, double tau,
-            int64_t nsteps, int64_t step0, const double *rH_fixed, int64_t *enc, int64_t enc_cap,
-            int64_t *enc_count, int64_t *stats)
+            int64_t nsteps, int64_t step0, const double *rH_fixed, int64_t *enc, double *enc_d2,
+            int64_t enc_cap, int64_t *enc_count, int64_t *stats)
 {
     const double G = p->G, m0 = m[0], mu = G * m0;
     int64_t nb = rows - 1;
@@ -683,6 +689,7 @@ int or_step(int64_t rows, const double *m, double *q, double *v, const or_params
     double *rH = (double *)malloc(sizeof(double) * rows);
     int32_t *its = (int32_t *)malloc(sizeof(int32_t) * (nb > 0 ? nb : 1));
     int64_t pcap = 1024, *pairs = (int64_t *)malloc(sizeof(int64_t) * 2 * pcap);
+    double *pd2 = (double *)malloc(sizeof(double) * pcap), *pt2 = (double *)malloc(sizeof(double) * pcap);
     int64_t *set_of = (int64_t *)malloc(sizeof(int64_t) * rows);
     int64_t *set_start = (int64_t *)malloc(sizeof(int64_t) * (rows + 1));
     int64_t *members = (int64_t *)malloc(sizeof(int64_t) * rows);
@@ -712,16 +719,22 @@ int or_step(int64_t rows, const double *m, double *q, double *v, const or_params
                 or_hill_radii(rows, m, q0, v0, G, rH);
             int64_t npairs;
             for (;;) {
-                npairs = or_encounters(rows, q0, v0, q, v, rH, tau, p->a_E, pairs, NULL, NULL, pcap);
+                npairs = or_encounters(rows, q0, v0, q, v, rH, tau, p->a_E, pairs, pd2, pt2, pcap);
                 if (npairs <= pcap) break;
                 pcap = 2 * npairs;
                 pairs = (int64_t *)realloc(pairs, sizeof(int64_t) * 2 * pcap);
+                pd2 = (double *)realloc(pd2, sizeof(double) * pcap);
+                pt2 = (double *)realloc(pt2, sizeof(double) * pcap);
             }
             for (int64_t k = 0; k < npairs; ++k) {
                 if (enc && ne_total < enc_cap) {
                     enc[3 * ne_total] = step0 + s;
                     enc[3 * ne_total + 1] = pairs[2 * k];
                     enc[3 * ne_total + 2] = pairs[2 * k + 1];
+                    if (enc_d2) {
+                        enc_d2[2 * ne_total] = pd2[k];
+                        enc_d2[2 * ne_total + 1] = pt2[k];
+                    }
                 }
                 ++ne_total;
             }
@@ -760,7 +773,7 @@ int or_step(int64_t rows, const double *m, double *q, double *v, const or_params
         or_drift(rows, m, q, v, 0.5 * tau);
     }
     if (enc_count) *enc_count = ne_total;
-    free(q0); free(v0); free(rH); free(its); free(pairs);
+    free(q0); free(v0); free(rH); free(its); free(pairs); free(pd2); free(pt2);
     free(set_of); free(set_start); free(members); free(rcrit);
     return status;
 }

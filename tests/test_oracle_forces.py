@@ -117,3 +117,23 @@ def test_selected_rows_match_full_accel(oracle):
     a = oracle.accel_int(m, q)
     sel = np.array([1, 7, 50, 23])
     assert np.array_equal(oracle.accel_rows(m, q, sel), a[sel])
+
+
+def test_energy_keeps_light_pair_terms(oracle):
+    """A disk of 2000 light bodies around planets: the energy equals the
+    correctly rounded sum (math.fsum) of every term of Eqs. 2-4, so pair
+    terms far below an ulp of the total are not lost."""
+    import math as _m
+    w = W.outer_disk(1996, 1e-10, seed=3)
+    m, q = w.m, w.q
+    v = oracle.helio_to_dh(m, w.v)
+    terms = []
+    S = (m[1:, None] * v[1:]).sum(0)
+    terms.append(S @ S / (2 * m[0]))
+    for i in range(1, len(m)):
+        terms.append(0.5 * m[i] * (v[i] @ v[i]))
+        terms.append(-m[0] * m[i] / np.linalg.norm(q[i]))
+        d = np.linalg.norm(q[i] - q[i + 1:], axis=1)
+        terms.extend((-m[i] * m[i + 1:] / d).tolist())
+    ref = _m.fsum(terms)
+    assert abs(oracle.energy(m, q, v) - ref) <= 1e-15 * abs(ref)
