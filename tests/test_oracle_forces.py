@@ -136,4 +136,6 @@ def test_energy_keeps_light_pair_terms(oracle):
         d = np.linalg.norm(q[i] - q[i + 1:], axis=1)
         terms.extend((-m[i] * m[i + 1:] / d).tolist())
     ref = _m.fsum(terms)
-    assert abs(oracle.energy(m, q, v) - ref) <= 1e-15 * abs(ref)
+    # ordinary rounding over ~4000 large terms is ~1e-15; dropping the light
+    # pair terms would show as ~2e-11 here
+    assert abs(oracle.energy(m, q, v) - ref) <= 1e-13 * abs(ref)
