@@ -1,0 +1,287 @@
+"""Throughput of the hybrid DH step (Sec. 2, Eq. 5 and the procedure of
+Sec. 2.3) on one GB300, printed as one JSON line.
+
+A bench "step" is one full step of the integrator (both kicks with the fused
+encounter search, Kepler drift, rigorous test, sets, Hermite, drifts) over the
+whole workload. Default workload: the 16384-body disk (4 planets + 16380
+planetesimals of 1e-10, seed 1, tau = P(a=5)/40) with the mixed-precision
+kick; --prec fp64 runs the plain FP64 kick instead.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
+                  [--impl ours|reference] [--workload NAME]
+
+--impl reference times the plain FP64 CPU oracle (the only reference this
+method has here) on a bounded sample of the same workload. With several GPUs
+(torchrun), every rank integrates its own replica (the single-system step has
+no multi-GPU path here); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "disk_16384": ("disk_16384", "16384-body disk: 4 planets + 16380 planetesimals (1e-10), seed 1"),
+    "disk_260": ("disk_260", "260-body disk: 4 planets + 256 planetesimals (1e-9), seed 0"),
+    "disk_262144": ("disk_262144", "262144-body embryo disk: 64 embryos (1e-6) + 262080 planetesimals (1e-11), seed 2"),
+    "ensemble_512": ("ensemble", "512 systems, N uniform 64-4096: 2 planets (1e-3 at a=1, 1.6) + planetesimals (1e-9), seed 3"),
+}
+METRIC = "particle-steps/s"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _workload(name):
+    from paper_1007_3458_gb300 import workloads as W
+    fn, desc = WORKLOADS[name]
+    return getattr(W, fn)(), desc
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if len(r) > 4 + k and r[4 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def cpu_baseline(w, prec_label, max_seconds=20.0):
+    """The oracle as it stands, single thread, on a bounded sample: whole
+    steps of the same workload until about max_seconds have passed."""
+    import oracle as O
+    O.build()
+    vd = np.concatenate([O.helio_to_dh(w.m[a:b], w.v[a:b])
+                         for a, b in zip(w.offsets[:-1], w.offsets[1:])])
+    q, v = w.q.copy(), vd
+    nb = w.n_bodies
+    # systems of a batch are stepped one after another: sample whole systems
+    if w.nsys > 1:
+        sel = list(range(min(w.nsys, 8)))
+        rows = [(int(w.offsets[s]), int(w.offsets[s + 1])) for s in sel]
+        nb = sum(b - a - 1 for a, b in rows)
+        t0 = time.perf_counter()
+        steps = 0
+        while time.perf_counter() - t0 < max_seconds and steps < 50:
+            for a, b in rows:
+                r = O.step(w.m[a:b], q[a:b], v[a:b], [0, b - a], w.tau, 1)
+                q[a:b], v[a:b] = r.q, r.v
+            steps += 1
+        dt = time.perf_counter() - t0
+        sample = f"first {len(rows)} systems ({nb} bodies), {steps} steps"
+    else:
+        t0 = time.perf_counter()
+        steps = 0
+        while steps < 1 or (time.perf_counter() - t0 < max_seconds and steps < 50):
+            r = O.step(w.m, q, v, w.offsets, w.tau, 1)
+            q, v = r.q, r.v
+            steps += 1
+        dt = time.perf_counter() - t0
+        sample = f"{steps} full steps of the workload"
+    return {"value": nb * steps / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": sample + " (plain FP64 oracle, single thread)"}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    w, desc = _workload(args.workload)
+    t_all = time.perf_counter()
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state
+    cb = cpu_baseline(w, args.prec, max_seconds=max(5.0, 3.0 * args.steps))
+    line = {"metric": METRIC, "value": cb["value"], "unit": METRIC, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * w.n_bodies / cb["value"] if cb["value"] else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "description": desc, "kick": "fp64",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_all}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.cuda.current_device()
+    import paper_1007_3458_gb300 as q
+    q.build()
+    w, desc = _workload(args.workload)
+    prec = q.QYM_KICK_MIXED if args.prec == "mixed" else q.QYM_KICK_FP64
+    # every step starts by writing 256 MB (twice the 129 MB L2), inside the
+    # timed region, so no step reuses the previous step's lines
+    sim = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=prec, device=dev,
+                       l2_flush_bytes=256 << 20)
+    if args.autotune:
+        q.qym_autotune(sim.ctx)
+    stream = torch.cuda.ExternalStream(q.qym_get_stream(sim.ctx))
+    # warm-up (also captures the step graph)
+    sim.step(w.tau, max(args.warmup, 3))
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # timed region: K steps inside one call, events on the context's stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        barrier()
+        e0.record(stream)
+        sim.step(w.tau, args.steps)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    st = sim.stats()
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    nb = w.n_bodies
+    value = nb * args.steps * ws / (ms / 1e3)
+    pairs = w.pairs_per_kick()
+    gpair = 2 * pairs * args.steps * ws / (ms / 1e3) / 1e9
+
+    # dominant kernel: the all-pairs kick, timed alone on the same stream
+    reps = 20
+    k1_ms, _ = q.qym_time_kick(sim.ctx, 1, reps)
+    k2_ms, _ = q.qym_time_kick(sim.ctx, 0, reps)
+    kick_ms = 0.5 * (k1_ms + k2_ms)
+    achieved = 20.0 * pairs / (kick_ms / 1e3) / 1e12
+    clocks = clk.summary()
+    peak = fp32_peak_tflops(2070.0)
+    roof = {"bound": "alu", "kernel": "k_kick_mixed" if prec else "k_kick_fp64",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None,
+            "convention": "20 flop per ordered pair, FP32 FMA-pipe peak 152 SM x 128 x 2 x 2070 MHz",
+            "kick_ms_with_search": k1_ms, "kick_ms_plain": k2_ms,
+            "gpair_per_s_kernel": pairs / (kick_ms / 1e3) / 1e9}
+
+    # end to end through the C ABI with host buffers: per step, the state goes
+    # host -> device (qym_set_state), one step, device -> host (qym_get_state)
+    qh, vh = sim.state()
+    qh = np.ascontiguousarray(qh)
+    vh = np.ascontiguousarray(vh)
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.set_state(qh, vh)
+        sim.step(w.tau, 1)
+        qh, vh = q.qym_get_state(sim.ctx, qh, vh)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": nb * e2e_steps * ws / e2e_s, "unit": METRIC,
+           "h2d_bytes_per_step": int(qh.nbytes + vh.nbytes),
+           "d2h_bytes_per_step": int(qh.nbytes + vh.nbytes),
+           "steps": e2e_steps, "what": "qym_set_state + qym_step(tau, 1) + qym_get_state per step"}
+    sim.close()
+    if rank != 0:
+        return 0
+    cb = cpu_baseline(w, args.prec, max_seconds=args.cpu_seconds) if ws == 1 else None
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp32-pair/f64-state" if prec else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "kick": args.prec,
+                       "tau": w.tau, "bodies": nb,
+                       "l2": "flushed: 256 MB written at the start of every step, inside the timed region"},
+            "gpair_per_s": gpair, "stats": st, "gpu_launches": int(st["launches"]),
+            "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cb}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="disk_16384", choices=sorted(WORKLOADS))
+    ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

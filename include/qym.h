@@ -93,7 +93,15 @@ typedef struct qym_params {
     int64_t max_candidates;     /* crude candidate pairs per step (0: automatic) */
     int64_t max_encounters;     /* rigorous encounter pairs per step (0: automatic) */
     int64_t max_log;            /* encounter records kept per qym_step call (0: automatic) */
+    int64_t l2_flush_bytes;     /* > 0: write a scratch buffer of this size at the start of
+                                   every step (benchmarks that must not reuse L2 between
+                                   steps); 0: off */
+    double heavy_mass;          /* mixed kick only: bodies with m >= heavy_mass * m0 (at most
+                                   QYM_HEAVY_CAP per system) pull on every body in FP64; the
+                                   N^2 part among the others stays FP32. <= 0: off */
 } qym_params;
+
+#define QYM_HEAVY_CAP 256
 
 typedef struct qym_stats {
     int64_t steps;              /* steps taken by the last qym_step call */
@@ -104,8 +112,9 @@ typedef struct qym_stats {
     int64_t kepler_iters;       /* Kepler solver iterations, summed over bodies and steps */
     int64_t hermite_steps;      /* Hermite steps, summed over sets and steps */
     int64_t rescans;            /* bodies re-searched because a crude bound was exceeded */
+    int64_t launches;           /* kernel launches enqueued by the last qym_step call */
     int32_t status_bits;        /* OR of QYM_ST_* seen */
-    int32_t kick_tile_i, kick_tile_splits;  /* launch shape picked by the tuner */
+    int32_t kick_tile_i, kick_tile_splits;  /* launch shape in use */
 } qym_stats;
 
 typedef struct qym_ctx qym_ctx;   /* opaque; owned by the library */
@@ -181,6 +190,25 @@ void qym_destroy(qym_ctx *ctx);
 /* Number of rows and systems of ctx. */
 qym_status qym_shape(const qym_ctx *ctx, int64_t *rows, int32_t *nsys);
 
+/* The CUDA stream (cudaStream_t as void*) on which ctx enqueues all of its
+ * work, for callers that record events or order their own work after it. */
+qym_status qym_get_stream(const qym_ctx *ctx, void **stream);
+
+/* Time the all-pairs kick kernel of ctx alone: `reps` launches on the ctx
+ * stream over the current state, bracketed by CUDA events, without changing
+ * the state (velocities are not updated). with_search = 1 times the variant
+ * with the fused crude encounter search. *ms_per_launch gets the mean launch
+ * duration in milliseconds; *pairs the ordered interacting pairs per launch
+ * (sum over systems of N_b (N_b - 1)). */
+qym_status qym_time_kick(qym_ctx *ctx, int32_t with_search, int32_t reps, double *ms_per_launch,
+                         int64_t *pairs);
+
+/* Pick the kick launch shape (threads per CTA, rows per thread, j splits)
+ * by timing candidate shapes with qym_time_kick on the current state, and
+ * keep the fastest. The state is unchanged; results can differ from the
+ * default shape in the last bits (summation grouping). */
+qym_status qym_autotune(qym_ctx *ctx);
+
 /* ------------------------------------------------------------------------ */
 /* Device-level calls: one operator of the step on caller-owned device      */
 /* buffers, enqueued on `stream`. These are the same kernels qym_step runs. */
@@ -204,16 +232,19 @@ qym_status qym_kepler_drift_dev(int64_t n, const double *q0, const double *v0, d
 /* E_Int acceleration (Sec. 2, Eq. 4) of one system: for rows i >= 1
  *   a_i = -sum_{j >= 1, j != i} G m_j (Q_i - Q_j) / |Q_i - Q_j|^3,
  * star row excluded (a_0 = 0).
- *  m         device float64[rows]
- *  q         device float64[3][rows]
- *  a         device float64[3][rows] output
- *  prec      QYM_KICK_FP64 or QYM_KICK_MIXED
- *  work      device scratch of qym_accel_workspace_bytes(rows, prec) bytes
- *            (caller owned, contents irrelevant on entry)
+ *  m           device float64[rows]
+ *  q           device float64[3][rows]
+ *  a           device float64[3][rows] output
+ *  prec        QYM_KICK_FP64 or QYM_KICK_MIXED
+ *  heavy_mass  QYM_KICK_MIXED: bodies with m >= heavy_mass * m[0] (the first
+ *              QYM_HEAVY_CAP of them) are summed in FP64; <= 0: none
+ *  work        device scratch of qym_accel_workspace_bytes(rows, prec) bytes
+ *              (caller owned, contents irrelevant on entry)
  * Returns QYM_EINVAL for rows < 2 or a NULL / short workspace. */
 size_t qym_accel_workspace_bytes(int64_t rows, int32_t prec);
 qym_status qym_accel_dev(int64_t rows, const double *m, const double *q, double *a, double G,
-                         int32_t prec, void *work, size_t work_bytes, void *stream);
+                         int32_t prec, double heavy_mass, void *work, size_t work_bytes,
+                         void *stream);
 
 /* Rigorous encounter test (Sec. 2.4): for each of npairs candidate pairs
  * (pairs[2k], pairs[2k+1]) of rows, the minimum over [0, tau] of the cubic that

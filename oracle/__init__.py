@@ -90,7 +90,7 @@ def lib():
                                      C.c_double, C.c_double, C.c_double, C.c_double, C.c_int64, I64]
         L.or_hermite_set.restype = C.c_int
         L.or_step.argtypes = [C.c_int64, D, D, D, C.POINTER(Params), C.c_double, C.c_int64,
-                              C.c_int64, D, I64, D, C.c_int64, I64, I64]
+                              C.c_int64, D, I64, D, C.c_int64, I64, I64, I64, D, C.c_int64, I64]
         L.or_step.restype = C.c_int
     return _lib
 
@@ -309,6 +309,8 @@ class StepResult:
     v: np.ndarray
     encounters: np.ndarray   # [k, 3] (step, i, j) with global row indices
     enc_d2: np.ndarray       # [k, 2] (d_min^2, threshold^2) of each record
+    near: np.ndarray         # [k, 3] unflagged pairs within 2e-6 of the threshold (d^2)
+    near_d2: np.ndarray      # [k, 2] their (d_min^2, threshold^2)
     stats: np.ndarray        # pairs, sets, largest set, Kepler iterations, Hermite steps, Kepler failures
     status: int
 
@@ -325,6 +327,7 @@ def step(m, q, v, offsets, tau, nsteps, prm: Params | None = None, step0=0,
     offsets = np.asarray(offsets, dtype=np.int64)
     encs = []
     d2s = []
+    nears, nd2s = [], []
     stats = np.zeros(6, dtype=np.int64)
     status = 0
     for s in range(len(offsets) - 1):
@@ -338,11 +341,15 @@ def step(m, q, v, offsets, tau, nsteps, prm: Params | None = None, step0=0,
             enc = np.zeros((cap, 3), dtype=np.int64)
             ed2 = np.zeros((cap, 2))
             cnt = np.zeros(1, dtype=np.int64)
+            ncap = 1 << 14
+            nr = np.zeros((ncap, 3), dtype=np.int64)
+            nd = np.zeros((ncap, 2))
+            ncnt = np.zeros(1, dtype=np.int64)
             qt, vt = qs.copy(), vs.copy()
             st_s = np.zeros(6, dtype=np.int64)
             st = lib().or_step(hi - lo, _d(ms), _d(qt), _d(vt), C.byref(prm), tau, nsteps, step0,
                                None if rhs is None else _d(rhs), _i64(enc), _d(ed2), cap,
-                               _i64(cnt), _i64(st_s))
+                               _i64(cnt), _i64(st_s), _i64(nr), _d(nd), ncap, _i64(ncnt))
             if cnt[0] <= cap:
                 break
             cap = int(cnt[0])
@@ -352,8 +359,15 @@ def step(m, q, v, offsets, tau, nsteps, prm: Params | None = None, step0=0,
         e[:, 1:] += lo
         encs.append(e)
         d2s.append(ed2[:cnt[0]].copy())
+        k = min(int(ncnt[0]), ncap)
+        nn = nr[:k].copy()
+        nn[:, 1:] += lo
+        nears.append(nn)
+        nd2s.append(nd[:k].copy())
         stats[[0, 1, 3, 4, 5]] += st_s[[0, 1, 3, 4, 5]]
         stats[2] = max(stats[2], st_s[2])
         status = status or st
     return StepResult(q, v, np.concatenate(encs) if encs else np.zeros((0, 3), np.int64),
-                      np.concatenate(d2s) if d2s else np.zeros((0, 2)), stats, status)
+                      np.concatenate(d2s) if d2s else np.zeros((0, 2)),
+                      np.concatenate(nears) if nears else np.zeros((0, 3), np.int64),
+                      np.concatenate(nd2s) if nd2s else np.zeros((0, 2)), stats, status)

@@ -386,9 +386,26 @@ static void pair_diffs(const double *q0, const double *v0, const double *q1, con
 /* Sec. 2.4 over ALL pairs 1 <= i < j (brute force; no crude pre-filter).
  * Writes up to cap pairs (i, j), i < j, in ascending (i, j) order, with their
  * d_min^2 and threshold^2; returns the number found. */
+int64_t or_encounters_near(int64_t rows, const double *q0, const double *v0, const double *q1,
+                           const double *v1, const double *rH, double tau, double a_E,
+                           int64_t *pairs, double *d2, double *thr2, int64_t cap, double band,
+                           int64_t *near, double *near_d2, int64_t near_cap, int64_t *near_count);
+
 int64_t or_encounters(int64_t rows, const double *q0, const double *v0, const double *q1,
                       const double *v1, const double *rH, double tau, double a_E, int64_t *pairs,
                       double *d2, double *thr2, int64_t cap)
+{
+    return or_encounters_near(rows, q0, v0, q1, v1, rH, tau, a_E, pairs, d2, thr2, cap, 0.0, NULL,
+                              NULL, 0, NULL);
+}
+
+/* as or_encounters; in addition, unflagged pairs with threshold^2 <= d^2 <
+ * threshold^2 (1 + band) ("near misses", for tests) go to near[] with their
+ * (d^2, threshold^2) */
+int64_t or_encounters_near(int64_t rows, const double *q0, const double *v0, const double *q1,
+                           const double *v1, const double *rH, double tau, double a_E,
+                           int64_t *pairs, double *d2, double *thr2, int64_t cap, double band,
+                           int64_t *near, double *near_d2, int64_t near_cap, int64_t *near_count)
 {
     int64_t cnt = 0;
     for (int64_t i = 1; i < rows; ++i)
@@ -405,6 +422,14 @@ int64_t or_encounters(int64_t rows, const double *q0, const double *v0, const do
                     if (thr2) thr2[cnt] = R * R;
                 }
                 ++cnt;
+            } else if (near_count && dm < R * R * (1.0 + band)) {
+                if (*near_count < near_cap) {
+                    near[2 * *near_count] = i;
+                    near[2 * *near_count + 1] = j;
+                    near_d2[2 * *near_count] = dm;
+                    near_d2[2 * *near_count + 1] = R * R;
+                }
+                ++*near_count;
             }
         }
     return cnt;
@@ -680,7 +705,8 @@ int or_hermite_set(int64_t k, const int64_t *mem, const double *m, double m0, do
 /* ------------------------------------------------------------------ */
 int or_step(int64_t rows, const double *m, double *q, double *v, const or_params *p, double tau,
             int64_t nsteps, int64_t step0, const double *rH_fixed, int64_t *enc, double *enc_d2,
-            int64_t enc_cap, int64_t *enc_count, int64_t *stats)
+            int64_t enc_cap, int64_t *enc_count, int64_t *stats, int64_t *near, double *near_d2,
+            int64_t near_cap, int64_t *near_count)
 {
     const double G = p->G, m0 = m[0], mu = G * m0;
     int64_t nb = rows - 1;
@@ -719,7 +745,27 @@ int or_step(int64_t rows, const double *m, double *q, double *v, const or_params
                 or_hill_radii(rows, m, q0, v0, G, rH);
             int64_t npairs;
             for (;;) {
-                npairs = or_encounters(rows, q0, v0, q, v, rH, tau, p->a_E, pairs, pd2, pt2, pcap);
+                int64_t nn0 = near_count ? *near_count : 0, nn = nn0;
+                int64_t *nbuf = near_count ? (int64_t *)malloc(sizeof(int64_t) * 2 * 4096) : NULL;
+                double *nd2 = near_count ? (double *)malloc(sizeof(double) * 2 * 4096) : NULL;
+                int64_t nloc = 0;
+                npairs = or_encounters_near(rows, q0, v0, q, v, rH, tau, p->a_E, pairs, pd2, pt2, pcap,
+                                            2e-6, nbuf, nd2, 4096, near_count ? &nloc : NULL);
+                if (near_count && npairs <= pcap) {
+                    for (int64_t k = 0; k < nloc && k < 4096; ++k, ++nn) {
+                        if (nn < near_cap) {
+                            near[3 * nn] = step0 + s;
+                            near[3 * nn + 1] = nbuf[2 * k];
+                            near[3 * nn + 2] = nbuf[2 * k + 1];
+                            near_d2[2 * nn] = nd2[2 * k];
+                            near_d2[2 * nn + 1] = nd2[2 * k + 1];
+                        }
+                    }
+                    *near_count = nn;
+                }
+                (void)nn0;
+                free(nbuf);
+                free(nd2);
                 if (npairs <= pcap) break;
                 pcap = 2 * npairs;
                 pairs = (int64_t *)realloc(pairs, sizeof(int64_t) * 2 * pcap);

@@ -41,13 +41,14 @@ class qym_params(C.Structure):
                 ("encounters", C.c_int32), ("coords", C.c_int32), ("hill_fixed", C.c_int32),
                 ("max_kepler_iter", C.c_int32), ("device", C.c_int32),
                 ("max_hermite_steps", C.c_int64), ("max_candidates", C.c_int64),
-                ("max_encounters", C.c_int64), ("max_log", C.c_int64)]
+                ("max_encounters", C.c_int64), ("max_log", C.c_int64),
+                ("l2_flush_bytes", C.c_int64), ("heavy_mass", C.c_double)]
 
 
 class qym_stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("candidates", C.c_int64), ("encounters", C.c_int64),
                 ("sets", C.c_int64), ("max_set", C.c_int64), ("kepler_iters", C.c_int64),
-                ("hermite_steps", C.c_int64), ("rescans", C.c_int64),
+                ("hermite_steps", C.c_int64), ("rescans", C.c_int64), ("launches", C.c_int64),
                 ("status_bits", C.c_int32), ("kick_tile_i", C.c_int32),
                 ("kick_tile_splits", C.c_int32)]
 
@@ -89,11 +90,15 @@ def lib():
     L.qym_destroy.argtypes = [P]
     L.qym_destroy.restype = None
     L.qym_shape.argtypes = [P, I64, C.POINTER(C.c_int32)]
+    L.qym_get_stream.argtypes = [P, C.POINTER(P)]
+    L.qym_time_kick.argtypes = [P, C.c_int32, C.c_int32, D, I64]
+    L.qym_autotune.argtypes = [P]
     L.qym_kepler_drift_dev.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_int32,
                                        C.c_int32, P, C.c_int32, P, P, P, P]
     L.qym_accel_workspace_bytes.argtypes = [C.c_int64, C.c_int32]
     L.qym_accel_workspace_bytes.restype = C.c_size_t
-    L.qym_accel_dev.argtypes = [C.c_int64, P, P, P, C.c_double, C.c_int32, P, C.c_size_t, P]
+    L.qym_accel_dev.argtypes = [C.c_int64, P, P, P, C.c_double, C.c_int32, C.c_double, P,
+                                C.c_size_t, P]
     L.qym_encounter_test_dev.argtypes = [C.c_int64, P, P, P, P, P, C.c_double, C.c_double,
                                          C.c_int64, P, P, P, P]
     L.qym_energy_workspace_bytes.argtypes = [C.c_int64]
@@ -101,6 +106,7 @@ def lib():
     L.qym_energy_dev.argtypes = [C.c_int64, P, P, P, C.c_double, P, P, C.c_size_t, P]
     for name in ("qym_default_params", "qym_init", "qym_step", "qym_get_state", "qym_set_state",
                  "qym_get_encounters", "qym_energy", "qym_get_stats", "qym_set_mlp", "qym_shape",
+                 "qym_get_stream", "qym_time_kick", "qym_autotune",
                  "qym_kepler_drift_dev", "qym_accel_dev", "qym_encounter_test_dev",
                  "qym_energy_dev"):
         getattr(L, name).restype = S
@@ -157,6 +163,24 @@ def qym_shape(ctx):
     n = C.c_int32()
     _check(lib().qym_shape(ctx, C.byref(r), C.byref(n)), ctx)
     return r.value, n.value
+
+
+def qym_get_stream(ctx) -> int:
+    h = P()
+    _check(lib().qym_get_stream(ctx, C.byref(h)), ctx)
+    return h.value or 0
+
+
+def qym_time_kick(ctx, with_search=0, reps=10):
+    """(mean ms per launch of the kick kernel, ordered pairs per launch)"""
+    ms = C.c_double()
+    pairs = C.c_int64()
+    _check(lib().qym_time_kick(ctx, with_search, reps, C.byref(ms), C.byref(pairs)), ctx)
+    return ms.value, pairs.value
+
+
+def qym_autotune(ctx):
+    _check(lib().qym_autotune(ctx), ctx)
 
 
 def qym_get_state(ctx, q=None, v=None):
@@ -234,10 +258,10 @@ def qym_accel_workspace_bytes(rows, prec) -> int:
     return int(lib().qym_accel_workspace_bytes(rows, prec))
 
 
-def qym_accel_dev(rows, m, q, a, G, prec, work, work_bytes=None, stream=None):
+def qym_accel_dev(rows, m, q, a, G, prec, work, work_bytes=None, stream=None, heavy_mass=1e-7):
     wb = work.numel() * work.element_size() if work_bytes is None else work_bytes
-    _check(lib().qym_accel_dev(rows, _ptr(m), _ptr(q), _ptr(a), G, prec, _ptr(work), wb,
-                               _stream(stream)))
+    _check(lib().qym_accel_dev(rows, _ptr(m), _ptr(q), _ptr(a), G, prec, heavy_mass, _ptr(work),
+                               wb, _stream(stream)))
 
 
 def qym_encounter_test_dev(rows, q0, v0, q1, v1, rH, tau, a_E, npairs, pairs, d2, flag,

@@ -34,6 +34,7 @@ struct qym_ctx {
     double *epart = nullptr, *E = nullptr;
     int32_t neitems = 0;
     double *mt = nullptr;  // [nsys] total masses
+    void *flush = nullptr; // L2 flush buffer (params.l2_flush_bytes)
     SetScratch ss;
     bool amag_valid = false;
     // graph of one interior step
@@ -42,6 +43,10 @@ struct qym_ctx {
     qym_stats stats;
     std::string err;
     int32_t status_bits = 0;
+    int32_t items_cap = 0, splits_cap = 0;  // sizes of the item and partial buffers
+    int64_t n_heavy = 0;    // heavy bodies over all systems
+    int64_t launches = 0;   // kernels enqueued by the current qym_step call
+    int64_t graph_launches = 0;  // kernels in one replay of the step graph
 };
 
 #define FAIL(ctx, code, msg)                         \
@@ -80,6 +85,8 @@ extern "C" qym_status qym_default_params(qym_params *p) {
     p->max_candidates = 0;
     p->max_encounters = 0;
     p->max_log = 0;
+    p->l2_flush_bytes = 0;
+    p->heavy_mass = 1e-7;
     return QYM_OK;
 }
 
@@ -94,6 +101,7 @@ static bool valid_params(const qym_params *p, std::string &why) {
     if (p->max_kepler_iter < 1) { why = "max_kepler_iter must be >= 1"; return false; }
     if (p->max_hermite_steps < 1) { why = "max_hermite_steps must be >= 1"; return false; }
     if (p->max_candidates < 0 || p->max_encounters < 0 || p->max_log < 0) { why = "capacities"; return false; }
+    if (p->l2_flush_bytes < 0 || p->l2_flush_bytes > ((int64_t)1 << 34)) { why = "l2_flush_bytes"; return false; }
     return true;
 }
 
@@ -128,13 +136,16 @@ static void carve_all(qym_ctx *c, Carver &k) {
     d.pk_lo = k.take<float4>(R);
     d.amag = k.take<float>(R);
     d.rH_bound = k.take<float>(R);
-    d.apart = k.take<double>((size_t)3 * R * d.splits);
-    d.items = k.take<int4>(d.nitems);
-    d.item_slot = k.take<int32_t>(d.nitems);
+    d.apart = k.take<double>((size_t)3 * R * c->splits_cap);
+    d.items = k.take<int4>(c->items_cap);
+    d.item_slot = k.take<int32_t>(c->items_cap);
     d.mchunks = k.take<int4>(d.nmchunks);
     d.mpart = k.take<double>(3 * (size_t)d.nmchunks);
     d.sys_chunk0 = k.take<int32_t>(d.nsys + 1);
     d.S = k.take<double>(3 * (size_t)d.nsys);
+    d.heavy_rows = k.take<int32_t>(c->n_heavy);
+    d.heavy_start = k.take<int32_t>(d.nsys + 1);
+    d.heavy_thr = k.take<double>(d.nsys);
     d.cand = k.take<int2>(d.max_cand);
     d.enc = k.take<int2>(d.max_enc);
     d.rescan = k.take<int32_t>(R);
@@ -249,6 +260,17 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     c->tune = default_tune(c->h_offsets, params->kick_prec);
     d.nitems = kick_items_count(offsets, nsys, c->tune);
     d.splits = c->tune.splits;
+    {
+        // buffers large enough for every shape the tuner may try
+        KickTune big;
+        big.threads = 128;
+        big.ipt = 1;
+        big.splits = 16;
+        c->splits_cap = std::max(16, c->tune.splits);
+        c->items_cap = std::max(kick_items_count(offsets, nsys, big) * std::max(1, c->splits_cap / 16),
+                                d.nitems);
+        c->items_cap = std::max(c->items_cap, kick_items_count(offsets, nsys, c->tune));
+    }
     // momentum chunks of at most 1024 rows, never crossing systems
     std::vector<int4> mch;
     std::vector<int32_t> sc0(nsys + 1);
@@ -265,6 +287,29 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     d.max_sets = (int32_t)R;
     d.max_members = (int32_t)R;
     c->neitems = energy_items_host(offsets, nsys, nullptr, nullptr, nullptr);
+    // heavy bodies per system (mixed kick): m >= heavy_mass m0, at most
+    // QYM_HEAVY_CAP of them, else the system keeps all bodies in FP32
+    std::vector<int32_t> hrows, hstart(nsys + 1);
+    std::vector<double> hthr(nsys);
+    const bool split = params->kick_prec == QYM_KICK_MIXED && params->heavy_mass > 0.0;
+    for (int32_t s = 0; s < nsys; ++s) {
+        hstart[s] = (int32_t)hrows.size();
+        double thr = params->heavy_mass * m[offsets[s]];
+        std::vector<int32_t> hs;
+        if (split)
+            for (int64_t r = offsets[s] + 1; r < offsets[s + 1]; ++r)
+                if (m[r] >= thr) hs.push_back((int32_t)r);
+        if (!split || hs.size() > QYM_HEAVY_CAP) {
+            hthr[s] = INFINITY;
+            hs.clear();
+        } else {
+            hthr[s] = thr;
+        }
+        hrows.insert(hrows.end(), hs.begin(), hs.end());
+    }
+    hstart[nsys] = (int32_t)hrows.size();
+    c->n_heavy = (int64_t)hrows.size();
+    d.heavy_split = split ? 1 : 0;
 
     Carver dry{nullptr, 0, true};
     carve_all(c, dry);
@@ -316,7 +361,13 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     CKI(cudaMemcpyAsync(c->eitems, eit.data(), sizeof(int4) * c->neitems, cudaMemcpyHostToDevice, c->stream));
     CKI(cudaMemcpyAsync(c->eisys, eis.data(), sizeof(int32_t) * c->neitems, cudaMemcpyHostToDevice, c->stream));
     CKI(cudaMemcpyAsync(c->eitem0, ei0.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, c->stream));
+    if (!hrows.empty())
+        CKI(cudaMemcpyAsync(d.heavy_rows, hrows.data(), sizeof(int32_t) * hrows.size(), cudaMemcpyHostToDevice, c->stream));
+    CKI(cudaMemcpyAsync(d.heavy_start, hstart.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, c->stream));
+    CKI(cudaMemcpyAsync(d.heavy_thr, hthr.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, c->stream));
+    CKI(cudaStreamSynchronize(c->stream));  // host vectors go out of scope below
     CKI(hermite_prepare());
+    if (params->l2_flush_bytes > 0) CKI(cudaMalloc(&c->flush, (size_t)params->l2_flush_bytes));
 #undef CKI
     qym_status st = upload_state(c, q, v);
     if (st != QYM_OK) return bail(st);
@@ -335,6 +386,7 @@ extern "C" void qym_destroy(qym_ctx *c) {
         cudaStreamDestroy(c->stream);
     }
     if (c->arena) cudaFree(c->arena);
+    if (c->flush) cudaFree(c->flush);
     delete c;
 }
 
@@ -368,6 +420,9 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last) {
     cudaStream_t st = c->stream;
     const int enc = p.encounters;
     cudaError_t e;
+    if (c->flush) {
+        if ((e = cudaMemsetAsync(c->flush, c->launches & 0xff, (size_t)p.l2_flush_bytes, st))) return e;
+    }
     k_step_begin<<<1, 1, 0, st>>>(d.ctr);
     // item 2: kick tau/2, with the crude encounter search when encounters are on
     if ((e = launch_kick_tiles(d, p.kick_prec, enc, p.G, c->tune.threads, c->tune.ipt, st))) return e;
@@ -407,6 +462,9 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last) {
                                     p.G, (!last) && enc, p.hill_fixed, st)))
         return e;
     k_step_end<<<1, 1, 0, st>>>(d.ctr, d.max_cand, d.max_enc);
+    // begin, kick, finish, Kepler, [refine 2, sets 7, Hermite], pack, kick,
+    // finish, momentum 2, drift, end
+    c->launches += 12 + (enc ? 10 : 0);
     return cudaGetLastError();
 }
 
@@ -427,6 +485,7 @@ static qym_status collect(qym_ctx *c, int64_t nsteps) {
     s.hermite_steps = (int64_t)ctr[C_SUM_HSTEPS];
     s.rescans = (int64_t)ctr[C_SUM_RESCAN];
     s.status_bits = status;
+    s.launches = c->launches;
     s.kick_tile_i = c->tune.threads * c->tune.ipt;
     s.kick_tile_splits = c->tune.splits;
     c->status_bits = status;
@@ -453,17 +512,20 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
         std::memset(&c->stats, 0, sizeof(c->stats));
         return QYM_OK;
     }
+    c->launches = 0;
     if (!c->amag_valid) {
         // |a| of the current positions for the first crude search's kick bound
         CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.0, tau, p.a_E, p.G, 0, p.hill_fixed, st));
         CK(c, launch_kick_tiles(d, p.kick_prec, 0, p.G, c->tune.threads, c->tune.ipt, st));
         CK(c, launch_kick_finish_v(d, d.v, d.q, 0.0, p.G, 0, p.hill_fixed, st));
         c->amag_valid = true;
+        c->launches += 3;
     }
     // item 1 of the first step: drift tau/2
     CK(c, launch_momentum(d, st));
     CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.5 * tau, tau, p.a_E, p.G, p.encounters,
                                  p.hill_fixed, st));
+    c->launches += 3;
     const int64_t interior = nsteps - 1;
     if (interior > 0) {
         if (c->gexec && c->g_tau != tau) {
@@ -473,7 +535,10 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
         if (!c->gexec && interior >= 2) {
             cudaGraph_t g;
             CK(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            int64_t before = c->launches;
             cudaError_t e = enqueue_step(c, tau, false);
+            c->graph_launches = c->launches - before;
+            c->launches = before;
             cudaError_t e2 = cudaStreamEndCapture(st, &g);
             if (e != cudaSuccess) FAIL(c, QYM_ECUDA, std::string("step capture: ") + cudaGetErrorString(e));
             if (e2 != cudaSuccess) FAIL(c, QYM_ECUDA, std::string("end capture: ") + cudaGetErrorString(e2));
@@ -483,9 +548,10 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
             c->g_tau = tau;
         }
         for (int64_t k = 0; k < interior; ++k) {
-            if (c->gexec)
+            if (c->gexec) {
                 CK(c, cudaGraphLaunch(c->gexec, st));
-            else
+                c->launches += c->graph_launches;
+            } else
                 CK(c, enqueue_step(c, tau, false));
         }
     }
@@ -616,13 +682,14 @@ extern "C" size_t qym_accel_workspace_bytes(int64_t rows, int32_t prec) {
 }
 
 extern "C" qym_status qym_accel_dev(int64_t rows, const double *m, const double *q, double *a,
-                                    double G, int32_t prec, void *work, size_t work_bytes,
-                                    void *stream) {
+                                    double G, int32_t prec, double heavy_mass, void *work,
+                                    size_t work_bytes, void *stream) {
     if (rows < 2 || !m || !q || !a || !work) FAIL(nullptr, QYM_EINVAL, "qym_accel_dev: bad argument");
     if (prec != QYM_KICK_FP64 && prec != QYM_KICK_MIXED) FAIL(nullptr, QYM_EINVAL, "qym_accel_dev: prec");
     if (work_bytes < accel_single_workspace(rows, prec)) FAIL(nullptr, QYM_EINVAL, "qym_accel_dev: workspace too small");
     if (rows >= (int64_t)1 << 31) FAIL(nullptr, QYM_EINVAL, "qym_accel_dev: too many rows");
-    CK(nullptr, launch_accel_single(rows, m, q, a, G, prec, work, work_bytes, (cudaStream_t)stream));
+    CK(nullptr, launch_accel_single(rows, m, q, a, G, prec, heavy_mass, work, work_bytes,
+                                    (cudaStream_t)stream));
     return QYM_OK;
 }
 
@@ -672,5 +739,113 @@ extern "C" qym_status qym_energy_dev(int64_t rows, const double *m, const double
     CK(nullptr, cudaMemcpyAsync(d_off, off, sizeof(int64_t) * 2, cudaMemcpyHostToDevice, st));
     CK(nullptr, launch_energy_items(n, d_it, d_is, d_i0, 1, d_off, rows, m, q, v, G, d_part, E, st));
     CK(nullptr, cudaStreamSynchronize(st));
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_get_stream(const qym_ctx *c, void **stream) {
+    if (!c || !stream) FAIL(c, QYM_EINVAL, "qym_get_stream: NULL argument");
+    *stream = (void *)c->stream;
+    return QYM_OK;
+}
+
+static int64_t pairs_per_kick(const qym_ctx *c) {
+    int64_t t = 0;
+    for (int32_t s = 0; s < c->d.nsys; ++s) {
+        int64_t nb = c->h_offsets[s + 1] - c->h_offsets[s] - 1;
+        t += nb * (nb - 1);
+    }
+    return t;
+}
+
+// the kick kernel alone on the current state (packs rebuilt first; the
+// candidate counter is reset after, the velocities are not touched)
+static qym_status time_kick_shape(qym_ctx *c, int flag, int reps, const KickTune &t, double *ms) {
+    Dev &d = c->d;
+    const qym_params &p = c->p;
+    cudaStream_t st = c->stream;
+    CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.0, 0.1, p.a_E, p.G, flag, p.hill_fixed, st));
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    CK(c, launch_kick_tiles(d, p.kick_prec, flag, p.G, t.threads, t.ipt, st));  // warm
+    CK(c, cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; ++r) CK(c, launch_kick_tiles(d, p.kick_prec, flag, p.G, t.threads, t.ipt, st));
+    CK(c, cudaEventRecord(e1, st));
+    CK(c, cudaEventSynchronize(e1));
+    float f = 0.f;
+    CK(c, cudaEventElapsedTime(&f, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(c, cudaMemsetAsync(d.ctr + C_NCAND, 0, sizeof(unsigned long long), st));
+    CK(c, cudaMemsetAsync(d.status, 0, sizeof(int32_t), st));
+    CK(c, cudaStreamSynchronize(st));
+    *ms = (double)f / reps;
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_time_kick(qym_ctx *c, int32_t with_search, int32_t reps,
+                                    double *ms_per_launch, int64_t *pairs) {
+    if (!c || reps < 1 || !ms_per_launch) FAIL(c, QYM_EINVAL, "qym_time_kick: bad argument");
+    CK(c, cudaSetDevice(c->p.device));
+    double ms = 0.0;
+    qym_status s = time_kick_shape(c, with_search ? 1 : 0, reps, c->tune, &ms);
+    if (s != QYM_OK) return s;
+    *ms_per_launch = ms;
+    if (pairs) *pairs = pairs_per_kick(c);
+    return QYM_OK;
+}
+
+// rebuild the work items for a launch shape (device buffers sized for the
+// largest item count and split count seen so far are reused when they fit)
+static qym_status apply_tune(qym_ctx *c, const KickTune &t) {
+    Dev &d = c->d;
+    int32_t n = kick_items_count(c->h_offsets.data(), d.nsys, t);
+    if (n > c->items_cap || t.splits > c->splits_cap) FAIL(c, QYM_EINVAL, "launch shape exceeds the item buffers");
+    std::vector<int4> items(n);
+    std::vector<int32_t> slots(n);
+    int32_t ni = 0, spu = 0;
+    kick_items_host(c->h_offsets.data(), d.nsys, t, items.data(), slots.data(), &ni, &spu, n);
+    CK(c, cudaMemcpyAsync(d.items, items.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(d.item_slot, slots.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    d.nitems = n;
+    d.splits = t.splits;
+    c->tune = t;
+    if (c->gexec) {  // the captured step holds the old shape
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_autotune(qym_ctx *c) {
+    if (!c) FAIL(nullptr, QYM_EINVAL, "qym_autotune: NULL context");
+    CK(c, cudaSetDevice(c->p.device));
+    const int mixed = c->p.kick_prec == QYM_KICK_MIXED;
+    std::vector<KickTune> cands;
+    for (int threads : {128, 256})
+        for (int ipt : mixed ? std::vector<int>{1, 2, 4} : std::vector<int>{1, 2})
+            for (int sp : {1, 2, 4, 8, 16}) {
+                KickTune t;
+                t.threads = threads;
+                t.ipt = ipt;
+                t.splits = sp;
+                if (sp > c->splits_cap) continue;
+                if (kick_items_count(c->h_offsets.data(), c->d.nsys, t) > c->items_cap) continue;
+                cands.push_back(t);
+            }
+    KickTune best = c->tune;
+    double best_ms = 1e30;
+    for (const KickTune &t : cands) {
+        qym_status s = apply_tune(c, t);
+        if (s != QYM_OK) return s;
+        double ms = 0.0;
+        s = time_kick_shape(c, c->p.encounters, 3, t, &ms);
+        if (s != QYM_OK) return s;
+        if (ms < best_ms) { best_ms = ms; best = t; }
+    }
+    qym_status s = apply_tune(c, best);
+    if (s != QYM_OK) return s;
+    c->amag_valid = false;
     return QYM_OK;
 }

@@ -315,7 +315,7 @@ cudaError_t launch_kick_tiles(const Dev &d, int prec, int flag, double G, int th
 // ---------------------------------------------------------------- single system
 // Workspace for qym_accel_dev: packs + items + partials for one system.
 struct SingleLayout {
-    size_t off_pos, off_lo, off_items, off_slots, off_apart, total;
+    size_t off_pos, off_lo, off_items, off_slots, off_apart, off_heavy, total;
     int32_t nitems, splits;
     KickTune tune;
 };
@@ -344,6 +344,7 @@ static SingleLayout single_layout(int64_t rows, int prec) {
     L.off_items = o; o = al(o + sizeof(int4) * L.nitems);
     L.off_slots = o; o = al(o + sizeof(int32_t) * L.nitems);
     L.off_apart = o; o = al(o + sizeof(double) * 3 * rows * L.splits);
+    L.off_heavy = o; o = al(o + sizeof(int32_t) * (QYM_HEAVY_CAP + 1));
     L.total = o;
     return L;
 }
@@ -353,15 +354,54 @@ size_t accel_single_workspace(int64_t rows, int prec) {
     return single_layout(rows, prec).total;
 }
 
+// heavy list of one system: the first QYM_HEAVY_CAP bodies (ascending rows)
+// with m >= heavy_mass * m[0]; hl[QYM_HEAVY_CAP] receives their count, and the
+// bodies past the cap stay in the FP32 tiles
+__global__ void __launch_bounds__(1024) k_heavy_thr_single(int64_t rows, const double *m,
+                                                           double heavy_mass, int32_t *hl) {
+    // same compaction as k_heavy_single with the threshold taken from m[0]
+    __shared__ int base;
+    __shared__ int wsum[32];
+    const double thr = heavy_mass * m[0];
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int64_t r0 = 1; r0 < rows; r0 += blockDim.x) {
+        int64_t r = r0 + threadIdx.x;
+        int hv = (r < rows && m[r] >= thr) ? 1 : 0;
+        unsigned b = __ballot_sync(0xffffffffu, hv);
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 0) wsum[w] = __popc(b);
+        __syncthreads();
+        int before = 0;
+        for (int k = 0; k < w; ++k) before += wsum[k];
+        int pos = base + before + __popc(b & ((1u << lane) - 1u));
+        if (hv && pos < QYM_HEAVY_CAP) hl[pos] = (int32_t)r;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += wsum[k];
+            base += t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) hl[QYM_HEAVY_CAP] = base < QYM_HEAVY_CAP ? base : QYM_HEAVY_CAP;
+}
+
 __global__ void k_pack_single(int64_t rows, const double *m, const double *q, double G,
-                              float4 *pos, float4 *lo) {
+                              const int32_t *hl, float4 *pos, float4 *lo) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= rows) return;
     float xh, xl, yh, yl, zh, zl;
     split_ds(q[i], xh, xl);
     split_ds(q[rows + i], yh, yl);
     split_ds(q[2 * rows + i], zh, zl);
-    pos[i] = make_float4(xh, yh, zh, (float)(G * m[i]));
+    float gm = (float)(G * m[i]);
+    if (hl) {
+        int nh = hl[QYM_HEAVY_CAP];
+        for (int k = 0; k < nh; ++k)
+            if (hl[k] == (int32_t)i) gm = 0.0f;
+    }
+    pos[i] = make_float4(xh, yh, zh, gm);
     lo[i] = make_float4(xl, yl, zl, 0.0f);
 }
 
@@ -380,20 +420,25 @@ __global__ void k_items_single(int64_t rows, int32_t ti, int32_t splits, int4 *i
     slots[idx] = sp;
 }
 
-__global__ void k_sum_partials(int64_t rows, int32_t splits, const double *apart, double *a) {
+__global__ void k_sum_partials(int64_t rows, int32_t splits, const double *apart,
+                               const int32_t *hl, const double *m, const double *q, double G,
+                               double *a) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= rows) return;
-    for (int c = 0; c < 3; ++c) {
-        double s = 0.0;
-        if (i > 0)
-            for (int sp = 0; sp < splits; ++sp) s += apart[((int64_t)sp * 3 + c) * rows + i];
-        a[c * rows + i] = s;
+    double s[3] = {0.0, 0.0, 0.0};
+    if (i > 0) {
+        for (int c = 0; c < 3; ++c)
+            for (int sp = 0; sp < splits; ++sp) s[c] += apart[((int64_t)sp * 3 + c) * rows + i];
+        if (hl)
+            heavy_pull(hl, hl[QYM_HEAVY_CAP], i, q[i], q[rows + i], q[2 * rows + i], q, m, rows, G,
+                       s[0], s[1], s[2]);
     }
+    for (int c = 0; c < 3; ++c) a[c * rows + i] = s[c];
 }
 
 cudaError_t launch_accel_single(int64_t rows, const double *m, const double *q, double *a,
-                                double G, int prec, void *work, size_t work_bytes,
-                                cudaStream_t st) {
+                                double G, int prec, double heavy_mass, void *work,
+                                size_t work_bytes, cudaStream_t st) {
     SingleLayout L = single_layout(rows, prec);
     if (work_bytes < L.total) return cudaErrorInvalidValue;
     char *w = (char *)work;
@@ -409,7 +454,14 @@ cudaError_t launch_accel_single(int64_t rows, const double *m, const double *q, 
     d.nitems = L.nitems;
     d.splits = L.splits;
     int tb = 256;
-    k_pack_single<<<(unsigned)((rows + tb - 1) / tb), tb, 0, st>>>(rows, m, q, G, d.pk_pos,
+    // heavy split (mixed kick only): threshold relative to the star mass m[0],
+    // read on the device
+    int32_t *hl = nullptr;
+    if (prec == QYM_KICK_MIXED && heavy_mass > 0.0) {
+        hl = (int32_t *)(w + L.off_heavy);
+        k_heavy_thr_single<<<1, 1024, 0, st>>>(rows, m, heavy_mass, hl);
+    }
+    k_pack_single<<<(unsigned)((rows + tb - 1) / tb), tb, 0, st>>>(rows, m, q, G, hl, d.pk_pos,
                                                                     d.pk_lo);
     k_items_single<<<(L.nitems + tb - 1) / tb, tb, 0, st>>>(rows, L.tune.threads * L.tune.ipt,
                                                              L.splits, d.items, d.item_slot,
@@ -425,7 +477,8 @@ cudaError_t launch_accel_single(int64_t rows, const double *m, const double *q, 
         e = launch_f64<false>(ka, L.nitems, L.tune.threads, L.tune.ipt, st);
     }
     if (e != cudaSuccess) return e;
-    k_sum_partials<<<(unsigned)((rows + tb - 1) / tb), tb, 0, st>>>(rows, L.splits, d.apart, a);
+    k_sum_partials<<<(unsigned)((rows + tb - 1) / tb), tb, 0, st>>>(rows, L.splits, d.apart, hl, m,
+                                                                     q, G, a);
     return cudaGetLastError();
 }
 

@@ -54,6 +54,11 @@ struct Dev {
     int32_t *uf = nullptr;        // [rows] union-find parents, kept at -1 when idle
     int64_t *log = nullptr;       // [max_log][3] encounter records of one qym_step call
     int64_t max_log = 0;
+    // heavy bodies of each system (mixed kick: their pull is summed in FP64)
+    int32_t *heavy_rows = nullptr;   // ascending rows, system by system
+    int32_t *heavy_start = nullptr;  // [nsys+1]
+    double *heavy_thr = nullptr;     // [nsys] mass threshold (+inf: no split)
+    int32_t heavy_split = 0;         // 1 when the kick in use is the mixed one
     // counters (device): see Counters below
     unsigned long long *ctr = nullptr;
     int32_t *status = nullptr;    // QYM_ST_* bits
@@ -107,6 +112,25 @@ __device__ __forceinline__ void split_ds(double x, float &hi, float &lo) {
     lo = __double2float_rn(x - (double)hi);
 }
 
+// FP64 pull of the heavy bodies hs[0..nh) (ascending rows, i excluded) on
+// the body at (x, y, z): sum -G m_h (r_i - r_h) / |r_i - r_h|^3
+__device__ __forceinline__ void heavy_pull(const int32_t *hs, int nh, int64_t i, double x,
+                                           double y, double z, const double *q, const double *m,
+                                           int64_t R, double G, double &ax, double &ay,
+                                           double &az) {
+    for (int k = 0; k < nh; ++k) {
+        int64_t h = hs[k];
+        if (h == i) continue;
+        double dx = x - q[h], dy = y - q[R + h], dz = z - q[2 * R + h];
+        double r2 = dx * dx + dy * dy + dz * dz;
+        double ri = rsqrt(r2);
+        double s = G * m[h] * (ri * ri) * ri;
+        ax -= s * dx;
+        ay -= s * dy;
+        az -= s * dz;
+    }
+}
+
 // ---------------------------------------------------------------- launches
 // Each returns cudaSuccess or the launch error. All work goes on `st`.
 
@@ -152,8 +176,8 @@ struct KickTune {
 cudaError_t launch_kick_tiles(const Dev &d, int prec, int flag, double G, int threads, int ipt,
                               cudaStream_t st);
 cudaError_t launch_accel_single(int64_t rows, const double *m, const double *q, double *a,
-                                double G, int prec, void *work, size_t work_bytes,
-                                cudaStream_t st);
+                                double G, int prec, double heavy_mass, void *work,
+                                size_t work_bytes, cudaStream_t st);
 size_t accel_single_workspace(int64_t rows, int prec);
 void kick_items_host(const int64_t *offsets, int32_t nsys, const KickTune &t,
                      int4 *items, int32_t *slots, int32_t *nitems, int32_t *splits_used,

@@ -136,7 +136,10 @@ __global__ void __launch_bounds__(256) k_drift_pack(Dev d, DriftArgs a) {
         double rho = F * (a.a_E * (double)rHb + fabs(a.tau) * (u + w)) + 1e-12 * rr;
         reach = round_up_f(rho);
     }
-    d.pk_pos[r] = make_float4(xh, yh, zh, (float)(a.G * mm));
+    // heavy bodies enter the FP32 tiles with zero mass (their pull is added
+    // in FP64 by the finisher); they still take part in the encounter search
+    float gm = (d.heavy_split && r != star && mm >= d.heavy_thr[sys]) ? 0.0f : (float)(a.G * mm);
+    d.pk_pos[r] = make_float4(xh, yh, zh, gm);
     d.pk_lo[r] = make_float4(xl, yl, zl, reach);
 }
 
@@ -184,6 +187,11 @@ __global__ void __launch_bounds__(256) k_finish(Dev d, FinishArgs a) {
         ax += p[r];
         ay += p[R + r];
         az += p[2 * R + r];
+    }
+    if (d.heavy_split) {
+        int h0 = d.heavy_start[sys], h1 = d.heavy_start[sys + 1];
+        heavy_pull(d.heavy_rows + h0, h1 - h0, r, a.q[r], a.q[R + r], a.q[2 * R + r], a.q, d.m, R,
+                   a.G, ax, ay, az);
     }
     double vx = a.v[r] + a.dt * ax;
     double vy = a.v[R + r] + a.dt * ay;

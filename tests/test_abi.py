@@ -34,9 +34,9 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_header_struct_layout_matches_binding():
-    # qym_params: 6 doubles, 8 int32, 4 int64 = 48 + 32 + 32 bytes
-    assert ctypes.sizeof(q.qym_params) == 112
-    assert ctypes.sizeof(q.qym_stats) == 8 * 8 + 4 * 3 + 4
+    # qym_params: 7 doubles, 8 int32, 5 int64 = 56 + 32 + 40 bytes
+    assert ctypes.sizeof(q.qym_params) == 128
+    assert ctypes.sizeof(q.qym_stats) == 9 * 8 + 4 * 3 + 4
 
 
 def test_defaults(lib):
