@@ -77,8 +77,9 @@ def test_kepler_matches_oracle(torch, oracle, solver, guess, dt):
     dv = np.linalg.norm(v1 - u1, axis=1) / np.linalg.norm(u1, axis=1)
     assert np.all(dq[ok] <= 1e-12 * scale[ok]), dq[ok].max()
     assert np.all(dv[ok] <= 1e-12 * scale[ok]), dv[ok].max()
-    # same iteration counts except where a stopping test sits at rounding level
-    assert np.mean(it[ok] == itr[ok]) > 0.99
+    # same iteration counts except where a stopping test sits at rounding
+    # level (more often for Newton far from the root)
+    assert np.mean(it[ok] == itr[ok]) > (0.99 if solver == 0 else 0.95)
 
 
 def test_kepler_unbound_and_star_rows(torch, oracle):
