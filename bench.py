@@ -183,6 +183,13 @@ def run_ours(args):
                        l2_flush_bytes=256 << 20)
     if args.autotune:
         q.qym_autotune(sim.ctx)
+    if args.kick_only:
+        # a few launches of the kick kernels alone (for a profiler capture)
+        q.qym_time_kick(sim.ctx, 1, 2)
+        q.qym_time_kick(sim.ctx, 0, 2)
+        torch.cuda.synchronize()
+        sim.close()
+        return 0
     stream = torch.cuda.ExternalStream(q.qym_get_stream(sim.ctx))
     # warm-up (also captures the step graph)
     sim.step(w.tau, max(args.warmup, 3))
@@ -275,6 +282,8 @@ def main():
     ap.add_argument("--workload", default="disk_16384", choices=sorted(WORKLOADS))
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--kick-only", action="store_true",
+                    help="launch only the kick kernels a few times (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -15,7 +15,7 @@
 namespace qym {
 
 constexpr int HCAP = 512;       // members per set held in shared memory
-constexpr int HTHREADS = 128;
+constexpr int HTHREADS = 256;
 
 // transition function of Sec. 2.1 with y = 1.1 s / r_crit - 0.1, and its
 // first and second derivatives with respect to s
@@ -58,57 +58,78 @@ __device__ __forceinline__ HermSmem carve(void *base) {
 }
 constexpr size_t kHermSmem = sizeof(double) * HCAP * 19 + sizeof(int32_t) * HCAP;
 
-// (1-K)-weighted pair acceleration at the evaluation point, unsmoothed
-// (the kick used the bare separation): sum_l -G m_l q_kl / q^3 [1 - K + q K']
-__device__ void kcorr_accel(const HermSmem &S, int n, int k, double G, double rc, double &dx,
-                            double &dy, double &dz) {
-    dx = dy = dz = 0.0;
-    for (int l = 0; l < n; ++l) {
+// Work split of a set of n members over the CTA: each member is handled by
+// P consecutive lanes (P a power of two, P * n <= HTHREADS when possible),
+// lane l of a member's group takes the partners l, l + P, ...; the group's
+// partial sums are combined with warp shuffles in a fixed tree order.
+__device__ __forceinline__ int lanes_per_member(int n) {
+    int p = 32;
+    while (p > 1 && p * n > HTHREADS) p >>= 1;
+    return p;
+}
+
+__device__ __forceinline__ void group_sum(double *v, int cnt, int P) {
+    for (int off = P >> 1; off > 0; off >>= 1)
+        for (int c = 0; c < cnt; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], off);
+}
+
+// partial (1-K)-weighted pair acceleration of member k at the evaluation
+// point, unsmoothed (the kick used the bare separation):
+// sum_l -G m_l q_kl / q^3 [1 - K + q K'] over the partners of this lane
+__device__ void kcorr_part(const HermSmem &S, int n, int k, int l0, int P, double G, double rc,
+                           double *c) {
+    c[0] = c[1] = c[2] = 0.0;
+    const double rc2 = rc * rc;
+    for (int l = l0; l < n; l += P) {
         if (l == k) continue;
         double qx = S.ex[k] - S.ex[l], qy = S.ey[k] - S.ey[l], qz = S.ez[k] - S.ez[l];
         double q2 = qx * qx + qy * qy + qz * qz;
+        if (q2 >= rc2) continue;  // K = 1 beyond r_crit: no (1-K) part
         double q = sqrt(q2);
         double K, Kp, Kpp;
         transition(q, rc, K, Kp, Kpp);
-        double br = 1.0 - K + q * Kp;
-        if (br == 0.0) continue;
-        double wgt = -G * S.m[l] / (q2 * q) * br;
-        dx += wgt * qx;
-        dy += wgt * qy;
-        dz += wgt * qz;
+        double wgt = -G * S.m[l] / (q2 * q) * (1.0 - K + q * Kp);
+        c[0] += wgt * qx;
+        c[1] += wgt * qy;
+        c[2] += wgt * qz;
     }
 }
 
-// Hermite acceleration and jerk of member k at the evaluation point (Sec. 2.2)
-__device__ void herm_force(const HermSmem &S, int n, int k, double G, double m0, double rc,
-                           double eps2, double *a, double *j) {
-    double xk = S.ex[k], yk = S.ey[k], zk = S.ez[k];
-    double uk = S.eu[k], vk = S.ev[k], wk = S.ew[k];
-    // star, fixed at the origin
-    double s2 = xk * xk + yk * yk + zk * zk + eps2;
-    double s = sqrt(s2);
-    double rv = xk * uk + yk * vk + zk * wk;
-    double c = -G * m0 / (s2 * s);
-    double t = 3.0 * rv / s2;
-    a[0] = c * xk; a[1] = c * yk; a[2] = c * zk;
-    j[0] = c * (uk - t * xk); j[1] = c * (vk - t * yk); j[2] = c * (wk - t * zk);
-    for (int l = 0; l < n; ++l) {
+// partial Hermite acceleration and jerk of member k at the evaluation point
+// (Sec. 2.2): the star term on lane 0 of the group, the pair terms with the
+// transition bracket over this lane's partners
+__device__ void herm_part(const HermSmem &S, int n, int k, int l0, int P, double G, double m0,
+                          double rc, double eps2, double *aj) {
+    const double xk = S.ex[k], yk = S.ey[k], zk = S.ez[k];
+    const double uk = S.eu[k], vk = S.ev[k], wk = S.ew[k];
+    for (int c = 0; c < 6; ++c) aj[c] = 0.0;
+    if (l0 == 0) {  // star, fixed at the origin
+        double s2 = xk * xk + yk * yk + zk * zk + eps2;
+        double s = sqrt(s2);
+        double rv = xk * uk + yk * vk + zk * wk;
+        double c = -G * m0 / (s2 * s);
+        double t = 3.0 * rv / s2;
+        aj[0] = c * xk; aj[1] = c * yk; aj[2] = c * zk;
+        aj[3] = c * (uk - t * xk); aj[4] = c * (vk - t * yk); aj[5] = c * (wk - t * zk);
+    }
+    const double rc2 = rc * rc;
+    for (int l = l0; l < n; l += P) {
         if (l == k) continue;
         double qx = xk - S.ex[l], qy = yk - S.ey[l], qz = zk - S.ez[l];
-        double px = uk - S.eu[l], py = vk - S.ev[l], pz = wk - S.ew[l];
         double q2 = qx * qx + qy * qy + qz * qz + eps2;
+        if (q2 >= rc2) continue;  // K = 1, K' = K'' = 0: no force, no jerk
+        double px = uk - S.eu[l], py = vk - S.ev[l], pz = wk - S.ew[l];
         double sq = sqrt(q2);
         double K, Kp, Kpp;
         transition(sq, rc, K, Kp, Kpp);
         double br = 1.0 - K + sq * Kp;
-        if (br == 0.0 && Kpp == 0.0) continue;
         double rvl = qx * px + qy * py + qz * pz;
         double cl = -G * S.m[l] / (q2 * sq);
         double tl = 3.0 * rvl / q2;
-        a[0] += cl * br * qx; a[1] += cl * br * qy; a[2] += cl * br * qz;
-        j[0] += cl * (rvl * qx * Kpp + (px - tl * qx) * br);
-        j[1] += cl * (rvl * qy * Kpp + (py - tl * qy) * br);
-        j[2] += cl * (rvl * qz * Kpp + (pz - tl * qz) * br);
+        aj[0] += cl * br * qx; aj[1] += cl * br * qy; aj[2] += cl * br * qz;
+        aj[3] += cl * (rvl * qx * Kpp + (px - tl * qx) * br);
+        aj[4] += cl * (rvl * qy * Kpp + (py - tl * qy) * br);
+        aj[5] += cl * (rvl * qz * Kpp + (pz - tl * qz) * br);
     }
 }
 
@@ -133,24 +154,28 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
     __shared__ double red[32];
     HermSmem S = carve(smem);
     const int64_t R = d.rows;
+    const int tid = threadIdx.x;
     int nsets = (int)min((unsigned long long)d.max_sets, d.ctr[C_NSETS]);
     for (int set = blockIdx.x; set < nsets; set += gridDim.x) {
         const int st = d.set_start[set];
         const int n = d.set_start[set + 1] - st;
         if (n < 1) continue;
         if (n > HCAP || st + n > d.max_members) {
-            if (threadIdx.x == 0) atomicOr(d.status, QYM_ST_SET_OVERFLOW);
-            for (int k = threadIdx.x; k < n && st + k < d.max_members; k += blockDim.x)
+            if (tid == 0) atomicOr(d.status, QYM_ST_SET_OVERFLOW);
+            for (int k = tid; k < n && st + k < d.max_members; k += blockDim.x)
                 d.uf[d.set_mem[st + k]] = -1;
             continue;
         }
+        const int P = lanes_per_member(n);
+        const int NG = HTHREADS / P;             // member groups in the CTA
+        const int grp = tid / P, lane = tid % P;
         // members in ascending row order (rank sort)
         __syncthreads();
-        for (int k = threadIdx.x; k < n; k += blockDim.x) S.ids[k] = d.set_mem[st + k];
+        for (int k = tid; k < n; k += blockDim.x) S.ids[k] = d.set_mem[st + k];
         __syncthreads();
         int myid[HCAP / HTHREADS], myrank[HCAP / HTHREADS];
         for (int c = 0; c < HCAP / HTHREADS; ++c) {
-            int k = threadIdx.x + c * blockDim.x;
+            int k = tid + c * blockDim.x;
             myid[c] = k < n ? S.ids[k] : 0;
             int rk = 0;
             if (k < n)
@@ -159,7 +184,7 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
         }
         __syncthreads();
         for (int c = 0; c < HCAP / HTHREADS; ++c) {
-            int k = threadIdx.x + c * blockDim.x;
+            int k = tid + c * blockDim.x;
             if (k < n) S.ids[myrank[c]] = myid[c];
         }
         __syncthreads();
@@ -168,7 +193,7 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
         const double rc = d.rcrit[set];
         const double G = h.G, tau = h.tau;
         // state entering the Kepler drift (after the first kick)
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        for (int k = tid; k < n; k += blockDim.x) {
             int64_t r = S.ids[k];
             S.ex[k] = S.x[k] = d.q[r];
             S.ey[k] = S.y[k] = d.q[R + r];
@@ -180,27 +205,36 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
         }
         __syncthreads();
         // item 5: remove the (1-K) part of the first kick
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            double cx, cy, cz;
-            kcorr_accel(S, n, k, G, rc, cx, cy, cz);
-            S.u[k] -= 0.5 * tau * cx;
-            S.v[k] -= 0.5 * tau * cy;
-            S.w[k] -= 0.5 * tau * cz;
+        for (int k0 = 0; k0 < n; k0 += NG) {
+            int k = k0 + grp;
+            double c[3] = {0.0, 0.0, 0.0};
+            if (k < n) kcorr_part(S, n, k, lane, P, G, rc, c);
+            group_sum(c, 3, P);
+            if (k < n && lane == 0) {
+                S.u[k] -= 0.5 * tau * c[0];
+                S.v[k] -= 0.5 * tau * c[1];
+                S.w[k] -= 0.5 * tau * c[2];
+            }
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        for (int k = tid; k < n; k += blockDim.x) {
             S.eu[k] = S.u[k]; S.ev[k] = S.v[k]; S.ew[k] = S.w[k];
         }
         __syncthreads();
         // start-up: a, adot at t = 0 and the step eta_s |a| / |adot|
         double dtl = fabs(tau);
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            double a[3], j[3];
-            herm_force(S, n, k, G, m0, rc, h.eps2, a, j);
-            S.ax[k] = a[0]; S.ay[k] = a[1]; S.az[k] = a[2];
-            S.jx[k] = j[0]; S.jy[k] = j[1]; S.jz[k] = j[2];
-            double jn = sqrt(j[0] * j[0] + j[1] * j[1] + j[2] * j[2]);
-            if (jn > 0.0) dtl = fmin(dtl, h.eta_s * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) / jn);
+        for (int k0 = 0; k0 < n; k0 += NG) {
+            int k = k0 + grp;
+            double aj[6] = {0, 0, 0, 0, 0, 0};
+            if (k < n) herm_part(S, n, k, lane, P, G, m0, rc, h.eps2, aj);
+            group_sum(aj, 6, P);
+            if (k < n && lane == 0) {
+                S.ax[k] = aj[0]; S.ay[k] = aj[1]; S.az[k] = aj[2];
+                S.jx[k] = aj[3]; S.jy[k] = aj[4]; S.jz[k] = aj[5];
+                double jn = sqrt(aj[3] * aj[3] + aj[4] * aj[4] + aj[5] * aj[5]);
+                if (jn > 0.0)
+                    dtl = fmin(dtl, h.eta_s * sqrt(aj[0] * aj[0] + aj[1] * aj[1] + aj[2] * aj[2]) / jn);
+            }
         }
         double dt = block_min(dtl, red);
         const double sgn = tau >= 0.0 ? 1.0 : -1.0;
@@ -216,7 +250,7 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
             const double hs = sgn * hh;  // signed step
             __syncthreads();
             // predictor
-            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            for (int k = tid; k < n; k += blockDim.x) {
                 S.ex[k] = S.x[k] + hs * (S.u[k] + hs * (0.5 * S.ax[k] + hs * S.jx[k] / 6.0));
                 S.ey[k] = S.y[k] + hs * (S.v[k] + hs * (0.5 * S.ay[k] + hs * S.jy[k] / 6.0));
                 S.ez[k] = S.z[k] + hs * (S.w[k] + hs * (0.5 * S.az[k] + hs * S.jz[k] / 6.0));
@@ -225,62 +259,69 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
                 S.ew[k] = S.w[k] + hs * (S.az[k] + 0.5 * hs * S.jz[k]);
             }
             __syncthreads();
-            // evaluate and correct (own members only)
+            // evaluate (split over lanes) and correct (lane 0 of each group)
             double next = T;
-            for (int k = threadIdx.x; k < n; k += blockDim.x) {
-                double a1[3], j1[3];
-                herm_force(S, n, k, G, m0, rc, h.eps2, a1, j1);
-                double a0[3] = {S.ax[k], S.ay[k], S.az[k]};
-                double j0[3] = {S.jx[k], S.jy[k], S.jz[k]};
-                double e[3] = {S.ex[k], S.ey[k], S.ez[k]};
-                double f[3] = {S.eu[k], S.ev[k], S.ew[k]};
-                double a2[3], a3[3], xn[3], un[3];
-                for (int c = 0; c < 3; ++c) {
-                    a2[c] = (-6.0 * (a0[c] - a1[c]) - hs * (4.0 * j0[c] + 2.0 * j1[c])) / (hs * hs);
-                    a3[c] = (12.0 * (a0[c] - a1[c]) + 6.0 * hs * (j0[c] + j1[c])) / (hs * hs * hs);
-                    xn[c] = e[c] + hs * hs * hs * hs * (a2[c] / 24.0 + hs * a3[c] / 120.0);
-                    un[c] = f[c] + hs * hs * hs * (a2[c] / 6.0 + hs * a3[c] / 24.0);
-                    a2[c] += hs * a3[c];
+            for (int k0 = 0; k0 < n; k0 += NG) {
+                int k = k0 + grp;
+                double a1[6] = {0, 0, 0, 0, 0, 0};
+                if (k < n) herm_part(S, n, k, lane, P, G, m0, rc, h.eps2, a1);
+                group_sum(a1, 6, P);
+                if (k < n && lane == 0) {
+                    double a0[3] = {S.ax[k], S.ay[k], S.az[k]};
+                    double j0[3] = {S.jx[k], S.jy[k], S.jz[k]};
+                    double e[3] = {S.ex[k], S.ey[k], S.ez[k]};
+                    double f[3] = {S.eu[k], S.ev[k], S.ew[k]};
+                    double a2[3], a3[3], xn[3], un[3];
+                    for (int c = 0; c < 3; ++c) {
+                        a2[c] = (-6.0 * (a0[c] - a1[c]) - hs * (4.0 * j0[c] + 2.0 * a1[3 + c])) / (hs * hs);
+                        a3[c] = (12.0 * (a0[c] - a1[c]) + 6.0 * hs * (j0[c] + a1[3 + c])) / (hs * hs * hs);
+                        xn[c] = e[c] + hs * hs * hs * hs * (a2[c] / 24.0 + hs * a3[c] / 120.0);
+                        un[c] = f[c] + hs * hs * hs * (a2[c] / 6.0 + hs * a3[c] / 24.0);
+                        a2[c] += hs * a3[c];
+                    }
+                    S.x[k] = xn[0]; S.y[k] = xn[1]; S.z[k] = xn[2];
+                    S.u[k] = un[0]; S.v[k] = un[1]; S.w[k] = un[2];
+                    S.ax[k] = a1[0]; S.ay[k] = a1[1]; S.az[k] = a1[2];
+                    S.jx[k] = a1[3]; S.jy[k] = a1[4]; S.jz[k] = a1[5];
+                    double na = sqrt(a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
+                    double nj = sqrt(a1[3] * a1[3] + a1[4] * a1[4] + a1[5] * a1[5]);
+                    double n2 = sqrt(a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2]);
+                    double n3 = sqrt(a3[0] * a3[0] + a3[1] * a3[1] + a3[2] * a3[2]);
+                    double den = nj * n3 + n2 * n2;
+                    if (den > 0.0) next = fmin(next, sqrt(h.eta * (na * n2 + nj * nj) / den));
                 }
-                S.x[k] = xn[0]; S.y[k] = xn[1]; S.z[k] = xn[2];
-                S.u[k] = un[0]; S.v[k] = un[1]; S.w[k] = un[2];
-                S.ax[k] = a1[0]; S.ay[k] = a1[1]; S.az[k] = a1[2];
-                S.jx[k] = j1[0]; S.jy[k] = j1[1]; S.jz[k] = j1[2];
-                double na = sqrt(a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
-                double nj = sqrt(j1[0] * j1[0] + j1[1] * j1[1] + j1[2] * j1[2]);
-                double n2 = sqrt(a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2]);
-                double n3 = sqrt(a3[0] * a3[0] + a3[1] * a3[1] + a3[2] * a3[2]);
-                double den = nj * n3 + n2 * n2;
-                if (den > 0.0) next = fmin(next, sqrt(h.eta * (na * n2 + nj * nj) / den));
             }
             dt = block_min(next, red);
             t = last ? T : t + hh;
             ++steps;
         }
         __syncthreads();
-        if (capped && threadIdx.x == 0) atomicOr(d.status, QYM_ST_HERMITE_CAP);
+        if (capped && tid == 0) atomicOr(d.status, QYM_ST_HERMITE_CAP);
         // item 7: pre-remove the (1-K) part of the coming kick at q1
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        for (int k = tid; k < n; k += blockDim.x) {
             S.ex[k] = S.x[k]; S.ey[k] = S.y[k]; S.ez[k] = S.z[k];
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            double cx, cy, cz;
-            kcorr_accel(S, n, k, G, rc, cx, cy, cz);
-            int64_t r = S.ids[k];
-            d.q1[r] = S.x[k];
-            d.q1[R + r] = S.y[k];
-            d.q1[2 * R + r] = S.z[k];
-            d.v1[r] = S.u[k] - 0.5 * tau * cx;
-            d.v1[R + r] = S.v[k] - 0.5 * tau * cy;
-            d.v1[2 * R + r] = S.w[k] - 0.5 * tau * cz;
-            d.uf[r] = -1;
+        for (int k0 = 0; k0 < n; k0 += NG) {
+            int k = k0 + grp;
+            double c[3] = {0.0, 0.0, 0.0};
+            if (k < n) kcorr_part(S, n, k, lane, P, G, rc, c);
+            group_sum(c, 3, P);
+            if (k < n && lane == 0) {
+                int64_t r = S.ids[k];
+                d.q1[r] = S.x[k];
+                d.q1[R + r] = S.y[k];
+                d.q1[2 * R + r] = S.z[k];
+                d.v1[r] = S.u[k] - 0.5 * tau * c[0];
+                d.v1[R + r] = S.v[k] - 0.5 * tau * c[1];
+                d.v1[2 * R + r] = S.w[k] - 0.5 * tau * c[2];
+                d.uf[r] = -1;
+            }
         }
-        if (threadIdx.x == 0) atomicAdd(d.ctr + C_SUM_HSTEPS, (unsigned long long)steps);
+        if (tid == 0) atomicAdd(d.ctr + C_SUM_HSTEPS, (unsigned long long)steps);
     }
 }
 
-// once per process and device, before any launch or stream capture
 cudaError_t hermite_prepare() {
     return cudaFuncSetAttribute(k_hermite, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kHermSmem);
