@@ -113,6 +113,7 @@ typedef struct qym_stats {
     int64_t hermite_steps;      /* Hermite steps, summed over sets and steps */
     int64_t rescans;            /* bodies re-searched because a crude bound was exceeded */
     int64_t launches;           /* kernel launches enqueued by the last qym_step call */
+    int64_t hermite_steps_max;  /* most Hermite steps one set took within one step */
     int32_t status_bits;        /* OR of QYM_ST_* seen */
     int32_t kick_tile_i, kick_tile_splits;  /* launch shape in use */
 } qym_stats;

@@ -49,6 +49,7 @@ class qym_stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("candidates", C.c_int64), ("encounters", C.c_int64),
                 ("sets", C.c_int64), ("max_set", C.c_int64), ("kepler_iters", C.c_int64),
                 ("hermite_steps", C.c_int64), ("rescans", C.c_int64), ("launches", C.c_int64),
+                ("hermite_steps_max", C.c_int64),
                 ("status_bits", C.c_int32), ("kick_tile_i", C.c_int32),
                 ("kick_tile_splits", C.c_int32)]
 

@@ -266,9 +266,11 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
         big.threads = 128;
         big.ipt = 1;
         big.splits = 16;
-        c->splits_cap = std::max(16, c->tune.splits);
-        c->items_cap = std::max(kick_items_count(offsets, nsys, big) * std::max(1, c->splits_cap / 16),
-                                d.nitems);
+        // partial-sum slots: up to 64 for small batches, within ~0.5 GB
+        int64_t by_mem = ((int64_t)1 << 29) / (24 * R);
+        c->splits_cap = (int32_t)std::max<int64_t>(c->tune.splits, std::min<int64_t>(64, std::max<int64_t>(4, by_mem)));
+        big.splits = c->splits_cap;
+        c->items_cap = std::max(kick_items_count(offsets, nsys, big), d.nitems);
         c->items_cap = std::max(c->items_cap, kick_items_count(offsets, nsys, c->tune));
     }
     // momentum chunks of at most 1024 rows, never crossing systems
@@ -486,6 +488,7 @@ static qym_status collect(qym_ctx *c, int64_t nsteps) {
     s.rescans = (int64_t)ctr[C_SUM_RESCAN];
     s.status_bits = status;
     s.launches = c->launches;
+    s.hermite_steps_max = (int64_t)ctr[C_MAX_HSET];
     s.kick_tile_i = c->tune.threads * c->tune.ipt;
     s.kick_tile_splits = c->tune.splits;
     c->status_bits = status;
@@ -825,7 +828,7 @@ extern "C" qym_status qym_autotune(qym_ctx *c) {
     std::vector<KickTune> cands;
     for (int threads : {128, 256})
         for (int ipt : mixed ? std::vector<int>{1, 2, 4} : std::vector<int>{1, 2})
-            for (int sp : {1, 2, 4, 8, 16}) {
+            for (int sp : {1, 2, 4, 8, 16, 32, 64}) {
                 KickTune t;
                 t.threads = threads;
                 t.ipt = ipt;

@@ -318,7 +318,10 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
                 d.uf[r] = -1;
             }
         }
-        if (tid == 0) atomicAdd(d.ctr + C_SUM_HSTEPS, (unsigned long long)steps);
+        if (tid == 0) {
+            atomicAdd(d.ctr + C_SUM_HSTEPS, (unsigned long long)steps);
+            atomicMax(d.ctr + C_MAX_HSET, (unsigned long long)steps);
+        }
     }
 }
 

@@ -20,13 +20,13 @@
 namespace qym {
 
 constexpr int TILE = 256;
-constexpr int FOLD = 32;
+constexpr int FOLD = 64;
 
 struct KickArgs {
     const int4 *items;
     const int32_t *slots;
     const float4 *pos;      // (x_hi, y_hi, z_hi, G m)
-    const float4 *lo;       // (x_lo, y_lo, z_lo, crude reach)
+    const float4 *lo;       // (x_lo, y_lo, z_lo, c = 2 rho^2 of the crude reach rho)
     const double *q;        // [3][rows] (FP64 path)
     const double *m;        // [rows] (FP64 path)
     double G;
@@ -53,17 +53,19 @@ __device__ __forceinline__ void push_candidate(const KickArgs &a, int i, int j) 
         atomicOr(a.status, QYM_ST_CAND_OVERFLOW);
 }
 
+// pair forces of one chunk of j rows. With FLAG, each i keeps the minimum
+// over the chunk of r^2 - c_j, c_j = 2 rho_j^2 (two FP32 operations per pair,
+// no branch); since (rho_i + rho_j)^2 <= c_i + c_j, a chunk without a
+// candidate of i has that minimum >= c_i and needs no further look
 template <int IPT, bool FLAG, bool DIAG>
 __device__ __forceinline__ void mixed_chunk(const float4 *__restrict__ s_pos,
                                             const float4 *__restrict__ s_lo, int j0, int j1,
-                                            int jbase, const float (&xh)[IPT],
-                                            const float (&yh)[IPT], const float (&zh)[IPT],
-                                            const float (&xl)[IPT], const float (&yl)[IPT],
-                                            const float (&zl)[IPT], const float (&rho)[IPT],
-                                            const int (&gi)[IPT], float (&fx)[IPT],
-                                            float (&fy)[IPT], float (&fz)[IPT],
-                                            const KickArgs &a) {
-#pragma unroll 4
+                                            const float (&xh)[IPT], const float (&yh)[IPT],
+                                            const float (&zh)[IPT], const float (&xl)[IPT],
+                                            const float (&yl)[IPT], const float (&zl)[IPT],
+                                            float (&fx)[IPT], float (&fy)[IPT], float (&fz)[IPT],
+                                            float (&mind)[IPT]) {
+#pragma unroll 8
     for (int j = j0; j < j1; ++j) {
         const float4 p = s_pos[j];
         const float4 l = s_lo[j];
@@ -73,20 +75,32 @@ __device__ __forceinline__ void mixed_chunk(const float4 *__restrict__ s_pos,
             float dy = (yh[k] - p.y) + (yl[k] - l.y);
             float dz = (zh[k] - p.z) + (zl[k] - l.z);
             float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            float ri = rsqrtf(r2);
-            float s = p.w * (ri * ri) * ri;
+            float ri = rsqrt_ftz(r2);
+            float s = (p.w * ri) * (ri * ri);
             if (DIAG) s = (r2 > 0.0f) ? s : 0.0f;
             fx[k] = fmaf(-s, dx, fx[k]);
             fy[k] = fmaf(-s, dy, fy[k]);
             fz[k] = fmaf(-s, dz, fz[k]);
-            if (FLAG) {
-                float t = rho[k] + l.w;
-                if (r2 < t * t) {
-                    int gj = jbase + j;
-                    if (gi[k] < gj) push_candidate(a, gi[k], gj);
-                }
-            }
+            if (FLAG) mind[k] = fminf(mind[k], r2 - l.w);
         }
+    }
+}
+
+// exact pre-check of one i against a chunk (rare path): candidates (i, j),
+// i < j, with r^2 < c_i + c_j
+__device__ __forceinline__ void flag_chunk(const KickArgs &a, const float4 *s_pos, const float4 *s_lo,
+                                        int j0, int j1, int jbase, int gi, float xh, float yh,
+                                        float zh, float xl, float yl, float zl, float ci) {
+    for (int j = j0; j < j1; ++j) {
+        int gj = jbase + j;
+        if (gi >= gj) continue;
+        const float4 p = s_pos[j];
+        const float4 l = s_lo[j];
+        float dx = (xh - p.x) + (xl - l.x);
+        float dy = (yh - p.y) + (yl - l.y);
+        float dz = (zh - p.z) + (zl - l.z);
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (r2 < ci + l.w) push_candidate(a, gi, gj);
     }
 }
 
@@ -126,21 +140,24 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
         const bool diag = (jt < i_hi) && (jt + n > i_lo);
         for (int c = 0; c < n; c += FOLD) {
             const int ce = min(c + FOLD, n);
-            float fx[IPT], fy[IPT], fz[IPT];
+            float fx[IPT], fy[IPT], fz[IPT], mind[IPT];
 #pragma unroll
-            for (int k = 0; k < IPT; ++k) fx[k] = fy[k] = fz[k] = 0.0f;
+            for (int k = 0; k < IPT; ++k) fx[k] = fy[k] = fz[k] = 0.0f, mind[k] = 3.0e38f;
             if (diag)
-                mixed_chunk<IPT, FLAG, true>(s_pos, s_lo, c, ce, jt, xh, yh, zh, xl, yl, zl, rho,
-                                             gi, fx, fy, fz, a);
+                mixed_chunk<IPT, FLAG, true>(s_pos, s_lo, c, ce, xh, yh, zh, xl, yl, zl, fx, fy,
+                                             fz, mind);
             else
-                mixed_chunk<IPT, FLAG, false>(s_pos, s_lo, c, ce, jt, xh, yh, zh, xl, yl, zl, rho,
-                                              gi, fx, fy, fz, a);
+                mixed_chunk<IPT, FLAG, false>(s_pos, s_lo, c, ce, xh, yh, zh, xl, yl, zl, fx, fy,
+                                              fz, mind);
 #pragma unroll
             for (int k = 0; k < IPT; ++k) {
                 float s, e;
                 two_sum(ahx[k], fx[k], s, e); ahx[k] = s; alx[k] += e;
                 two_sum(ahy[k], fy[k], s, e); ahy[k] = s; aly[k] += e;
                 two_sum(ahz[k], fz[k], s, e); ahz[k] = s; alz[k] += e;
+                if (FLAG && mind[k] < rho[k])
+                    flag_chunk(a, s_pos, s_lo, c, ce, jt, gi[k], xh[k], yh[k], zh[k], xl[k],
+                               yl[k], zl[k], rho[k]);
             }
         }
     }
@@ -204,8 +221,7 @@ __global__ void __launch_bounds__(256) k_kick_fp64(KickArgs a) {
                 ay[k] -= s * dy;
                 az[k] -= s * dz;
                 if (FLAG) {
-                    float t = rho[k] + s_rho[j];
-                    if ((float)r2 < t * t) {
+                    if ((float)r2 < rho[k] + s_rho[j]) {
                         int gj = jt + j;
                         if (gi[k] < gj) push_candidate(a, gi[k], gj);
                     }

@@ -26,7 +26,7 @@ struct Dev {
     double *rH_fixed = nullptr;   // [rows] Hill radii computed at init (hill_fixed)
     // kick operand packs, float32 (rebuilt from the FP64 state every step)
     float4 *pk_pos = nullptr;     // (x_hi, y_hi, z_hi, G m)
-    float4 *pk_lo = nullptr;      // (x_lo, y_lo, z_lo, crude reach rho)
+    float4 *pk_lo = nullptr;      // (x_lo, y_lo, z_lo, c = 2 rho^2, rho the crude reach)
     float *amag = nullptr;        // [rows] |a_int| of the last kick
     float *rH_bound = nullptr;    // [rows] Hill radius bound used by the crude test
     double *apart = nullptr;      // [splits][3][rows] kick partial accelerations
@@ -80,10 +80,18 @@ enum Ctr : int {
     C_SUM_HSTEPS,
     C_SUM_RESCAN,
     C_STEP,          // step index within the current qym_step call
+    C_MAX_HSET,      // most Hermite steps taken by one set in one step
     C_COUNT
 };
 
 // ---------------------------------------------------------------- helpers
+// one MUFU instruction; inputs here are squared separations, never denormal
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 struct alignas(32) D4 {
     double x, y, z, w;
 };

@@ -134,7 +134,9 @@ __global__ void __launch_bounds__(256) k_drift_pack(Dev d, DriftArgs a) {
         double sh = fmin(0.8, 2.5 * Om * fabs(a.tau));
         double F = 2.0 / (1.0 - sh);
         double rho = F * (a.a_E * (double)rHb + fabs(a.tau) * (u + w)) + 1e-12 * rr;
-        reach = round_up_f(rho);
+        // kernels test r^2 < c_i + c_j with c = 2 rho^2 >= ... a superset of
+        // r < rho_i + rho_j, as (rho_i + rho_j)^2 <= 2 rho_i^2 + 2 rho_j^2
+        reach = round_up_f(2.0 * rho * rho * (1.0 + 1e-6));
     }
     // heavy bodies enter the FP32 tiles with zero mass (their pull is added
     // in FP64 by the finisher); they still take part in the encounter search
