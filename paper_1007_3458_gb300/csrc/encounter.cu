@@ -155,11 +155,15 @@ cudaError_t launch_refine(const Dev &d, double tau, double a_E, cudaStream_t st)
 // the smaller with compare-and-swap; every loop is capped.
 constexpr int UF_CAP = 1 << 20;
 
+// Parents are read with volatile (L1-bypassing) loads: links are made with
+// atomics in L2, and a cached line could still show a node as unset (-1).
+// A negative parent is never followed.
 __device__ __forceinline__ int uf_find(int *uf, int x, int &guard) {
-    int p = uf[x];
-    while (p != x && guard < UF_CAP) {
+    volatile int *u = uf;
+    int p = u[x];
+    while (p != x && p >= 0 && guard < UF_CAP) {
         x = p;
-        p = ((volatile int *)uf)[x];
+        p = u[x];
         ++guard;
     }
     return x;
@@ -261,6 +265,7 @@ __global__ void __launch_bounds__(256) k_uf_members(Dev d, const int32_t *sid, i
     int guard = 0;
     int root = uf_find(d.uf, (int)r, guard);
     int s = sid[root];
+    if (s < 0 || s >= d.max_sets) return;
     atomicAdd(size + s, 1);
     double rc = a_H * d.rH[r];
     atomicMax(rc_bits + s, (unsigned long long)__double_as_longlong(rc));
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(256) k_uf_place(Dev d, const int32_t *sid, int
     int guard = 0;
     int root = uf_find(d.uf, (int)r, guard);
     int s = sid[root];
-    if (s >= d.max_sets) return;
+    if (s < 0 || s >= d.max_sets) return;
     int pos = d.set_start[s] + atomicAdd(fill + s, 1);
     if (pos < d.max_members) d.set_mem[pos] = (int32_t)r;
 }
