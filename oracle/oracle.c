@@ -33,8 +33,10 @@
  *      star jerk term uses s_i0^3.
  *   R5 K, K', K'' are taken with respect to the separation s (chain factor
  *      1.1 / r_crit included); the kick corrections use the unsmoothed q.
- *   R6 Hill radius r_H,i = a_i (m_i / (3 m0))^(1/3), a_i = 1/alpha_i from the
- *      state entering the Kepler step when alpha_i > 0, else |Q_i|.
+ *   R6 Hill radius r_H,i = |Q_i| (m_i / (3 m0))^(1/3), the Hill radius at the
+ *      body's heliocentric distance in the state entering the Kepler step
+ *      (equal to the semi-major-axis form on circular orbits; the osculating
+ *      semi-major axis diverges on near-parabolic orbits).
  *   R7 rigorous test: cubic Hermite interpolant of d^2(t) = |dQ(t)|^2 on
  *      [0, tau] from values and slopes at both ends; the minimum over [0, tau]
  *      (clamped at 0) is compared with (a_E (r_H,i + r_H,j))^2.
@@ -319,18 +321,17 @@ void or_dh_to_helio(int64_t rows, const double *m, double *v)
 }
 
 /* ------------------------------------------------------------------ */
-/* Sec. 2.2 (Eq. 9) and reading R6: Hill radii                         */
+/* Sec. 2.2 (Eq. 9) and reading R6: Hill radii at the current distance  */
 /* ------------------------------------------------------------------ */
 void or_hill_radii(int64_t rows, const double *m, const double *q, const double *v, double G,
                    double *rH)
 {
-    double mu = G * m[0];
+    (void)v;
+    (void)G;
     rH[0] = 0.0;
     for (int64_t i = 1; i < rows; ++i) {
         double r = sqrt(dot3(q + 3 * i, q + 3 * i));
-        double alpha = 2.0 / r - dot3(v + 3 * i, v + 3 * i) / mu;
-        double a = alpha > 0.0 ? 1.0 / alpha : r;
-        rH[i] = a * cbrt(m[i] / (3.0 * m[0]));
+        rH[i] = r * cbrt(m[i] / (3.0 * m[0]));
     }
 }
 

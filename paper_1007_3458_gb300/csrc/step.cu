@@ -53,14 +53,10 @@ cudaError_t launch_momentum(const Dev &d, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Hill radius from the osculating orbit about the star (mu = G m0):
-// r_H = a (m / 3 m0)^(1/3), a = 1/alpha when bound, else the distance
-__device__ __forceinline__ double hill(double qx, double qy, double qz, double vx, double vy,
-                                       double vz, double m, double m0, double mu) {
+// Hill radius at the body's heliocentric distance: r_H = |Q| (m / 3 m0)^(1/3)
+__device__ __forceinline__ double hill(double qx, double qy, double qz, double m, double m0) {
     double r = sqrt(qx * qx + qy * qy + qz * qz);
-    double alpha = 2.0 / r - (vx * vx + vy * vy + vz * vz) / mu;
-    double a = alpha > 0.0 ? 1.0 / alpha : r;
-    return a * cbrt(m / (3.0 * m0));
+    return r * cbrt(m / (3.0 * m0));
 }
 
 __device__ __forceinline__ float round_up_f(double x) {
@@ -122,7 +118,7 @@ __global__ void __launch_bounds__(256) k_drift_pack(Dev d, DriftArgs a) {
         if (a.hill_fixed) {
             rH = d.rH_fixed[r];
         } else {
-            rH = 1.25 * hill(qx, qy, qz, vx, vy, vz, mm, m0, mu);
+            rH = hill(qx, qy, qz, mm, m0);  // positions do not change in the kick
         }
         float rHb = round_up_f(rH * (1.0 + 1e-6));
         d.rH_bound[r] = rHb;
@@ -203,9 +199,7 @@ __global__ void __launch_bounds__(256) k_finish(Dev d, FinishArgs a) {
     if (a.check) {
         bool bad = an > 1.01f * d.amag[r] + 1e-30f;
         const double m0 = d.m[star];
-        double rH = a.hill_fixed ? d.rH_fixed[r]
-                                 : hill(a.q[r], a.q[R + r], a.q[2 * R + r], vx, vy, vz, d.m[r],
-                                        m0, a.G * m0);
+        double rH = a.hill_fixed ? d.rH_fixed[r] : hill(a.q[r], a.q[R + r], a.q[2 * R + r], d.m[r], m0);
         d.rH[r] = rH;
         if (rH > (double)d.rH_bound[r]) bad = true;
         if (bad) {
@@ -238,8 +232,7 @@ __global__ void k_hill_init(Dev d, double G) {
     const int64_t star = d.offsets[d.sys_of[r]];
     if (r == star) { d.rH_fixed[r] = 0.0; return; }
     const double m0 = d.m[star];
-    d.rH_fixed[r] = hill(d.q[r], d.q[R + r], d.q[2 * R + r], d.v[r], d.v[R + r], d.v[2 * R + r],
-                         d.m[r], m0, G * m0);
+    d.rH_fixed[r] = hill(d.q[r], d.q[R + r], d.q[2 * R + r], d.m[r], m0);
 }
 
 cudaError_t launch_hill_init(const Dev &d, double G, cudaStream_t st) {

@@ -199,3 +199,33 @@ def test_error_statuses(gpu):
     with pytest.raises(q.QymError) as e:
         q.Simulation(w.m, bad, w.v, w.offsets)
     assert e.value.status == q.QYM_EINVAL
+
+
+def test_ensemble_full_size_sampled(gpu, oracle):
+    """The 512-system ensemble (about 1.06e6 rows, the bench's batched
+    workload) stepped as one batch: sampled systems match the oracle stepping
+    each alone (records equal, positions within the chaos-aware tolerance),
+    no status bits, and no set larger than the oracle's."""
+    w = W.ensemble()
+    sim = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=q.QYM_KICK_FP64)
+    sim.step(w.tau, 3)
+    qg, vg = sim.state()
+    enc = sim.encounters()
+    st = sim.stats()
+    sim.close()
+    assert st["status_bits"] == 0
+    rng = np.random.default_rng(7)
+    pick = np.concatenate([[int(np.argmax(np.diff(w.offsets)))], rng.choice(w.nsys, 5, replace=False)])
+    max_set = 0
+    for s in pick:
+        a, b = int(w.offsets[s]), int(w.offsets[s + 1])
+        ws = W.Workload("sys", w.m[a:b], w.q[a:b], w.v[a:b], np.array([0, b - a]), w.tau, 3)
+        r, _ = _run_oracle(oracle, ws, 3)
+        max_set = max(max_set, int(r.stats[2]))
+        mine = enc[(enc[:, 1] >= a) & (enc[:, 1] < b)].copy()
+        mine[:, 1:] -= a
+        skip = _compare_records(mine, r)
+        spread = _chaos_spread(oracle, ws, 3)
+        keep = np.array([i not in skip for i in range(b - a)])
+        _check_positions(qg[a:b][keep], r.q[keep], spread[keep], rel=1e-11)
+    assert max_set < 512 and st["max_set"] < 512

@@ -100,13 +100,16 @@ def test_encounter_list_brute_force_small_n(oracle, seed):
 
 
 def test_hill_radius_definition(oracle):
-    """r_H = a (m / 3 m0)^(1/3) with a from the orbital energy (circular orbit:
-    a = r); massless bodies have zero radius."""
-    m = np.array([1.0, 3e-3, 0.0])
-    q = np.array([[0, 0, 0], [2.0, 0, 0], [0, 3.0, 0]])
-    v = np.array([[0, 0, 0], [0, math.sqrt(0.5), 0], [-math.sqrt(1 / 3), 0, 0]])
+    """r_H = |Q| (m / 3 m0)^(1/3): on a circular orbit this is the
+    semi-major-axis form of Eq. 9's R_MH; it stays finite on a near-parabolic
+    orbit (where 1/alpha diverges); massless bodies have zero radius."""
+    m = np.array([1.0, 3e-3, 0.0, 3e-3])
+    q = np.array([[0, 0, 0], [2.0, 0, 0], [0, 3.0, 0], [0, 0, 1.5]])
+    v = np.array([[0, 0, 0], [0, math.sqrt(0.5), 0], [-math.sqrt(1 / 3), 0, 0],
+                  [math.sqrt(2 / 1.5) * (1 - 1e-12), 0, 0]])
     rH = oracle.hill_radii(m, q, v)
     assert abs(rH[1] - 2.0 * 0.1) <= 1e-15
+    assert abs(rH[3] - 1.5 * 0.1) <= 1e-15
     assert rH[2] == 0.0 and rH[0] == 0.0
 
 
