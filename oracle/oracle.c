@@ -46,10 +46,16 @@
  *   R10 the Hermite integration starts from (q0, v0) after the first kick and
  *      the K correction.
  *   R12 Stumpff series used for |y| < 0.1, summed to the y^8 term.
- *   R13 Kepler iteration stops when |F| <= 1e-14 (sqrt(mu)|dt| + r0|x|) or
- *      |dx| <= 2^-50 |x|.
+ *   R13 Kepler iteration stops when |F| <= 1e-14 times the sum of the
+ *      magnitudes of F's terms, or |dx| <= 2^-50 |x|.
  *   R14 standard starting guess x0 = sqrt(mu) dt / r0; the paper's x0 = r0 is
  *      kept as a separate guess mode.
+ *   R15 the iteration is kept inside the bracket [0, sqrt(mu) dt / r_p]
+ *      (r_p the periapsis distance; F' = r >= r_p; for unbound orbits also
+ *      sqrt(-alpha) |x| <= 700, beyond which C and S overflow), falling back to bisection
+ *      when a step leaves it, does not halve the previous step, or F
+ *      overflows; the residual test of R13 is taken against the sum of the
+ *      magnitudes of F's terms.
  */
 #include <math.h>
 #include <stdint.h>
@@ -114,19 +120,46 @@ void or_kepler_F(double x, double sqmu, double dt, double r0, double sig, double
     *Fpp = sig * (1.0 - y * C) + b * x * (1.0 - y * S);
 }
 
+int or_kepler_solve_br(double sqmu, double dt, double r0, double sig, double alpha, int solver,
+                       int max_iter, double lo, double hi, double *x_io, int32_t *iters);
+
 /* Solve F(x) = 0 from x (in/out). solver 0: Laguerre n = 5 (R1); 1: Newton.
- * Returns 0 on convergence (R13), 1 when max_iter updates did not converge. */
+ * F is increasing (F' = r > 0), so the root is unique and lies in the
+ * bracket [lo, hi] passed in (R15); a step that leaves the bracket or lands
+ * where F is not finite (C, S overflow on strongly hyperbolic orbits) is
+ * replaced by bisection, and the bracket shrinks with every evaluation.
+ * Returns 0 on convergence (R13), 1 when max_iter evaluations did not. */
 int or_kepler_solve(double sqmu, double dt, double r0, double sig, double alpha,
                     int solver, int max_iter, double *x_io, int32_t *iters)
 {
+    return or_kepler_solve_br(sqmu, dt, r0, sig, alpha, solver, max_iter, -INFINITY, INFINITY,
+                              x_io, iters);
+}
+
+int or_kepler_solve_br(double sqmu, double dt, double r0, double sig, double alpha, int solver,
+                       int max_iter, double lo, double hi, double *x_io, int32_t *iters)
+{
     const double n = 5.0;
     double x = *x_io;
-    double scale = sqmu * fabs(dt);
+    if (!(x >= lo && x <= hi)) x = (isfinite(lo) && isfinite(hi)) ? 0.5 * (lo + hi) : x;
+    double dx_old = INFINITY;
     int it;
     for (it = 0; it < max_iter; ++it) {
         double F, Fp, Fpp;
         or_kepler_F(x, sqmu, dt, r0, sig, alpha, &F, &Fp, &Fpp);
-        if (fabs(F) <= 1e-14 * (scale + r0 * fabs(x))) {
+        if (!isfinite(F) || !isfinite(Fp) || !isfinite(Fpp)) {
+            /* beyond the representable range: the root is below |x| */
+            if (x > 0.0) hi = x; else lo = x;
+            x = 0.5 * (lo + hi);
+            continue;
+        }
+        if (F < 0.0) lo = x; else hi = x;
+        /* residual against the rounding floor of F: the sum of its terms */
+        double y = alpha * x * x, C, S;
+        or_stumpff(y, &C, &S);
+        double scale = fabs(sqmu * dt) + fabs(sig * x * x * C) +
+                       fabs((1.0 - r0 * alpha) * x * x * x * S) + r0 * fabs(x);
+        if (fabs(F) <= 1e-14 * scale) {
             *x_io = x;
             *iters = it;
             return 0;
@@ -139,8 +172,18 @@ int or_kepler_solve(double sqmu, double dt, double r0, double sig, double alpha,
         } else {
             dx = F / Fp;
         }
-        x -= dx;
-        if (fabs(dx) <= 0x1p-50 * fabs(x)) {
+        double xn = x - dx;
+        int bracketed = isfinite(lo) && isfinite(hi);
+        /* bisect when the step leaves the bracket, or when it does not at
+         * least halve the previous step (slow approach along the exponential
+         * flank of F on unbound orbits) */
+        if (bracketed && (!(xn >= lo && xn <= hi) || fabs(dx) > 0.5 * fabs(dx_old))) {
+            xn = 0.5 * (lo + hi);
+            dx = x - xn;
+        }
+        dx_old = dx;
+        x = xn;
+        if (fabs(dx) <= 0x1p-50 * fabs(x) || (isfinite(lo) && isfinite(hi) && hi - lo <= 0x1p-50 * fabs(x))) {
             *x_io = x;
             *iters = it + 1;
             return 0;
@@ -170,13 +213,33 @@ int or_kepler_body(const double *q0, const double *v0, double *q1, double *v1, d
         x = r0;
     else
         x = x_guess;
+    /* bracket (R15): F(0) = -sqrt(mu) dt and F' = r >= r_p (periapsis
+     * distance), so the root lies between 0 and sqrt(mu) dt / r_p */
+    double hv[3] = {q0[1] * v0[2] - q0[2] * v0[1], q0[2] * v0[0] - q0[0] * v0[2],
+                    q0[0] * v0[1] - q0[1] * v0[0]};
+    double p = dot3(hv, hv) / mu;
+    double ecc = sqrt(fmax(0.0, 1.0 - p * alpha));
+    double rp = p / (1.0 + ecc);
+    double lo = -INFINITY, hi = INFINITY;
+    if (rp > 0.0) {
+        /* widened by 1e-12: r_p itself carries rounding */
+        double xb = sqmu * dt / rp * (1.0 + 1e-12);
+        if (dt >= 0.0) { lo = 0.0; hi = xb; } else { lo = xb; hi = 0.0; }
+    }
+    if (alpha < 0.0) {
+        /* unbound: beyond sqrt(-alpha) |x| = 700 the position would be
+         * ~e^700 from the star (C, S overflow first) */
+        double xm = 700.0 / sqrt(-alpha);
+        if (dt >= 0.0) { lo = fmax(lo, 0.0); hi = fmin(hi, xm); }
+        else { lo = fmax(lo, -xm); hi = fmin(hi, 0.0); }
+    }
     int32_t it = 0;
-    int st = or_kepler_solve(sqmu, dt, r0, sig, alpha, solver, max_iter, &x, &it);
+    int st = or_kepler_solve_br(sqmu, dt, r0, sig, alpha, solver, max_iter, lo, hi, &x, &it);
     if (st != 0 && guess == 2) {
         /* fallback: Laguerre from the standard guess */
         int32_t it2 = 0;
         x = sqmu * dt / r0;
-        st = or_kepler_solve(sqmu, dt, r0, sig, alpha, 0, max_iter, &x, &it2);
+        st = or_kepler_solve_br(sqmu, dt, r0, sig, alpha, 0, max_iter, lo, hi, &x, &it2);
         it += it2;
     }
     double y = alpha * x * x, C, S;

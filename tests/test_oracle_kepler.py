@@ -242,3 +242,26 @@ def test_root_brackets_and_residual(oracle):
         # F' and F'' are the derivatives of F (central differences)
         Fpn = (Fpl - Fm) / (2 * h)
         assert abs(Fpn - Fp) <= 1e-6 * abs(Fp)
+
+
+def test_unbound_orbits_converge_and_match_ode(oracle):
+    """Near-parabolic and strongly hyperbolic orbits (up to 3 escape speeds)
+    over long steps: every solve converges inside its bracket, energy and
+    angular momentum are kept, and samples match the DOP853 reference."""
+    rng = np.random.default_rng(1)
+    n = 3000
+    r = rng.uniform(0.3, 3, n)
+    q0 = np.zeros((n, 3))
+    q0[:, 0] = r
+    f = np.where(rng.random(n) < 0.5, 1 + rng.uniform(-1e-3, 1e-3, n), rng.uniform(1.0, 3.0, n))
+    ang = rng.uniform(0, math.pi, n)
+    v0 = np.stack([np.cos(ang), np.sin(ang), np.zeros(n)], 1) * (f * np.sqrt(2 / r))[:, None]
+    for dt in (0.157, 1.76, 20.0, -5.0):
+        q1, v1, x, it, bad = oracle.kepler_drift(q0, v0, 1.0, dt)
+        assert bad == 0 and np.all(np.isfinite(q1)), dt
+        E0 = 0.5 * np.sum(v0 ** 2, 1) - 1 / r
+        E1 = 0.5 * np.sum(v1 ** 2, 1) - 1 / np.linalg.norm(q1, axis=1)
+        assert np.all(np.abs(E1 - E0) <= 1e-12 * (np.abs(E0) + 1 / r) * (1 + abs(dt)))
+        for k in rng.choice(n, 8, replace=False):
+            qr, vr = _two_body_ode(q0[k], v0[k], 1.0, dt)
+            assert np.linalg.norm(q1[k] - qr) <= 1e-8 * max(np.linalg.norm(qr), 1.0), (dt, k)
