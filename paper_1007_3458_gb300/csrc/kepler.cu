@@ -88,6 +88,27 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
         int solver = a.solver;
         bool conv = false;
         double C = 0.5, S = 1.0 / 6.0;
+        // Root bracket: F(0) = -sqrt(mu) dt and F' = r >= r_p (periapsis
+        // distance), so the root lies between 0 and sqrt(mu) dt / r_p; for an
+        // unbound orbit also |x| <= 700 / sqrt(-alpha), past which C and S
+        // overflow. Widened by 1e-12 for the rounding of r_p.
+        double lo = -INFINITY, hi = INFINITY;
+        {
+            double hx = qy * vz - qz * vy, hy = qz * vx - qx * vz, hz = qx * vy - qy * vx;
+            double p = (hx * hx + hy * hy + hz * hz) / mu;
+            double ecc = sqrt(fmax(0.0, 1.0 - p * eq.alpha));
+            double rp = p / (1.0 + ecc);
+            if (rp > 0.0) {
+                double xb = eq.sqmu_dt / rp * (1.0 + 1e-12);
+                if (dt >= 0.0) { lo = 0.0; hi = xb; } else { lo = xb; hi = 0.0; }
+            }
+            if (eq.alpha < 0.0) {
+                double xm = 700.0 / sqrt(-eq.alpha);
+                if (dt >= 0.0) { lo = fmax(lo, 0.0); hi = fmin(hi, xm); }
+                else { lo = fmax(lo, -xm); hi = fmin(hi, 0.0); }
+            }
+        }
+        const double lo0 = lo, hi0 = hi;
         // two passes at most: the requested start, then (learned guess only)
         // Laguerre from the standard guess if the first did not converge
         for (int pass = 0; pass < 2 && !conv; ++pass) {
@@ -95,12 +116,27 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
                 if (a.guess != QYM_GUESS_MLP) break;
                 x = eq.sqmu_dt / r0;
                 solver = QYM_SOLVER_LAGUERRE;
+                lo = lo0;
+                hi = hi0;
             }
-            const double tol = 1e-14;
+            const bool have_br = isfinite(lo) && isfinite(hi);
+            if (!(x >= lo && x <= hi) && have_br) x = 0.5 * (lo + hi);
+            double dx_old = INFINITY;
             for (int it = 0; it < a.max_iter; ++it) {
                 double F, Fp, Fpp;
                 eq.eval(x, F, Fp, Fpp, C, S);
-                if (fabs(F) <= tol * (fabs(eq.sqmu_dt) + r0 * fabs(x))) { conv = true; break; }
+                ++iters;
+                if (!isfinite(F) || !isfinite(Fp) || !isfinite(Fpp)) {
+                    if (x > 0.0) hi = x; else lo = x;
+                    x = 0.5 * (lo + hi);
+                    continue;
+                }
+                if (F < 0.0) lo = x; else hi = x;
+                // residual against the rounding floor of F: the sum of |terms|
+                double x2 = x * x;
+                double scale = fabs(eq.sqmu_dt) + fabs(eq.sig * x2 * C) +
+                               fabs(eq.b * x2 * x * S) + r0 * fabs(x);
+                if (fabs(F) <= 1e-14 * scale) { --iters; conv = true; break; }
                 double dx;
                 if (solver == QYM_SOLVER_LAGUERRE) {
                     // Laguerre, n = 5: dx = n F / (F' + sgn(F') sqrt|(n-1)^2 F'^2 - n(n-1) F F''|)
@@ -109,9 +145,21 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
                 } else {
                     dx = F / Fp;
                 }
-                x -= dx;
-                ++iters;
-                if (fabs(dx) <= 0x1p-50 * fabs(x)) { conv = true; break; }
+                double xn = x - dx;
+                // bisect when the step leaves the bracket or fails to halve the
+                // previous step (slow approach along exp(sqrt(-alpha) x))
+                if (isfinite(lo) && isfinite(hi) &&
+                    (!(xn >= lo && xn <= hi) || fabs(dx) > 0.5 * fabs(dx_old))) {
+                    xn = 0.5 * (lo + hi);
+                    dx = x - xn;
+                }
+                dx_old = dx;
+                x = xn;
+                if (fabs(dx) <= 0x1p-50 * fabs(x) ||
+                    (isfinite(lo) && isfinite(hi) && hi - lo <= 0x1p-50 * fabs(x))) {
+                    conv = true;
+                    break;
+                }
             }
         }
         // f and g functions at the root (Appendix); r before fdot, gdot
