@@ -77,7 +77,8 @@ typedef struct qym_params {
     double G;            /* gravitational constant */
     double a_E;          /* encounter factor: flag d_min < a_E (r_H,i + r_H,j) (Sec. 2.4) */
     double a_H;          /* transition factor: r_crit = a_H max r_H over a set (Eq. 9) */
-    double eps_H;        /* Hermite smoothing length (Sec. 2.2) */
+    double eps_H;        /* Hermite smoothing length (Sec. 2.2: small but not zero, so
+                            that a near-collision cannot drive the step to zero) */
     double eta, eta_s;   /* Hermite step accuracy and start-up factors (Sec. 2.2) */
     int32_t kick_prec;   /* QYM_KICK_* */
     int32_t solver;      /* QYM_SOLVER_* */
@@ -125,7 +126,7 @@ typedef struct qym_ctx qym_ctx;   /* opaque; owned by the library */
 /* positions and velocities stay on the GPU; host copies only on request).  */
 /* ------------------------------------------------------------------------ */
 
-/* Fill *p with defaults: G = 1, a_E = 3, a_H = 1, eps_H = 0, eta = 0.02,
+/* Fill *p with defaults: G = 1, a_E = 3, a_H = 1, eps_H = 1e-6, eta = 0.02,
  * eta_s = 0.01, mixed kick, Laguerre, standard guess, encounters on,
  * heliocentric coordinates, per-step Hill radii, 50 Kepler iterations,
  * 1e5 Hermite steps, automatic capacities. Returns QYM_EINVAL if p is NULL. */

@@ -44,7 +44,7 @@ class Params(C.Structure):
                 ("max_kepler_iter", C.c_int32), ("max_hermite_steps", C.c_int64)]
 
 
-def params(G=1.0, a_E=3.0, a_H=1.0, eps_H=0.0, eta=0.02, eta_s=0.01, solver=0, guess=0,
+def params(G=1.0, a_E=3.0, a_H=1.0, eps_H=1e-6, eta=0.02, eta_s=0.01, solver=0, guess=0,
            encounters=1, max_kepler_iter=50, max_hermite_steps=100000) -> Params:
     return Params(G, a_E, a_H, eps_H, eta, eta_s, solver, guess, encounters, max_kepler_iter,
                   max_hermite_steps)

@@ -70,7 +70,7 @@ extern "C" qym_status qym_default_params(qym_params *p) {
     p->G = 1.0;
     p->a_E = 3.0;
     p->a_H = 1.0;
-    p->eps_H = 0.0;
+    p->eps_H = 1e-6;
     p->eta = 0.02;
     p->eta_s = 0.01;
     p->kick_prec = QYM_KICK_MIXED;

@@ -41,7 +41,7 @@ def test_header_struct_layout_matches_binding():
 
 def test_defaults(lib):
     p = q.qym_default_params()
-    assert (p.G, p.a_E, p.a_H, p.eps_H, p.eta, p.eta_s) == (1.0, 3.0, 1.0, 0.0, 0.02, 0.01)
+    assert (p.G, p.a_E, p.a_H, p.eps_H, p.eta, p.eta_s) == (1.0, 3.0, 1.0, 1e-6, 0.02, 0.01)
     assert p.kick_prec == q.QYM_KICK_MIXED and p.encounters == 1 and p.max_kepler_iter == 50
 
 
