@@ -248,6 +248,29 @@ qym_status qym_accel_dev(int64_t rows, const double *m, const double *q, double 
                          int32_t prec, double heavy_mass, void *work, size_t work_bytes,
                          void *stream);
 
+/* The same accelerations as qym_accel_dev, for callers that cannot allocate
+ * device memory: code running where the host application owns every device
+ * allocation, or loops that must not call the allocator (and its implicit
+ * synchronisation) once they are running. The scratch lives in one fixed
+ * array inside the library (qym_static_scratch_bytes() bytes, 8 MiB),
+ * which every GPU that loads the library holds until the process exits.
+ * The paper has no counterpart; this is a deployment convenience.
+ *  rows     2 .. QYM_STATIC_MAX_ROWS; larger systems return QYM_EINVAL with a
+ *           message from qym_static_last_error() (use qym_accel_dev then)
+ *  m, q, a, G, prec, heavy_mass, stream: as qym_accel_dev (caller-owned)
+ * The call allocates nothing (no cudaMalloc or allocating library routine).
+ * Its first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture. All calls
+ * share the one array and every call rewrites all of the scratch it reads,
+ * so nothing carries over between calls; calls that overlap on the GPU (on
+ * different streams, or from several threads) race on it and must be
+ * serialised by the caller. */
+#define QYM_STATIC_MAX_ROWS 32768
+size_t qym_static_scratch_bytes(void);
+qym_status qym_accel_dev_static(int64_t rows, const double *m, const double *q, double *a,
+                                double G, int32_t prec, double heavy_mass, void *stream);
+const char *qym_static_last_error(void);
+
 /* Rigorous encounter test (Sec. 2.4): for each of npairs candidate pairs
  * (pairs[2k], pairs[2k+1]) of rows, the minimum over [0, tau] of the cubic that
  * interpolates |dQ(t)|^2 from its values and slopes at t = 0 (q0, v0) and

@@ -26,6 +26,7 @@ QYM_ST_SET_OVERFLOW, QYM_ST_NAN, QYM_ST_UF_CAP, QYM_ST_LOG_OVERFLOW = 16, 32, 64
 QYM_KICK_FP64, QYM_KICK_MIXED = 0, 1
 QYM_SOLVER_LAGUERRE, QYM_SOLVER_NEWTON = 0, 1
 QYM_GUESS_STANDARD, QYM_GUESS_R0, QYM_GUESS_MLP = 0, 1, 2
+QYM_STATIC_MAX_ROWS = 32768
 
 
 class QymError(RuntimeError):
@@ -100,6 +101,12 @@ def lib():
     L.qym_accel_workspace_bytes.restype = C.c_size_t
     L.qym_accel_dev.argtypes = [C.c_int64, P, P, P, C.c_double, C.c_int32, C.c_double, P,
                                 C.c_size_t, P]
+    L.qym_accel_dev_static.argtypes = [C.c_int64, P, P, P, C.c_double, C.c_int32, C.c_double, P]
+    L.qym_accel_dev_static.restype = C.c_int
+    L.qym_static_scratch_bytes.argtypes = []
+    L.qym_static_scratch_bytes.restype = C.c_size_t
+    L.qym_static_last_error.argtypes = []
+    L.qym_static_last_error.restype = C.c_char_p
     L.qym_encounter_test_dev.argtypes = [C.c_int64, P, P, P, P, P, C.c_double, C.c_double,
                                          C.c_int64, P, P, P, P]
     L.qym_energy_workspace_bytes.argtypes = [C.c_int64]
@@ -263,6 +270,19 @@ def qym_accel_dev(rows, m, q, a, G, prec, work, work_bytes=None, stream=None, he
     wb = work.numel() * work.element_size() if work_bytes is None else work_bytes
     _check(lib().qym_accel_dev(rows, _ptr(m), _ptr(q), _ptr(a), G, prec, heavy_mass, _ptr(work),
                                wb, _stream(stream)))
+
+
+def qym_accel_dev_static(rows, m, q, a, G, prec, heavy_mass=1e-7, stream=None):
+    """qym_accel_dev with the library's fixed scratch array (allocates nothing)."""
+    st = lib().qym_accel_dev_static(rows, _ptr(m), _ptr(q), _ptr(a), G, prec, heavy_mass,
+                                    _stream(stream))
+    if st != QYM_OK:
+        msg = lib().qym_static_last_error()
+        raise QymError(st, msg.decode() if msg else "")
+
+
+def qym_static_scratch_bytes() -> int:
+    return int(lib().qym_static_scratch_bytes())
 
 
 def qym_encounter_test_dev(rows, q0, v0, q1, v1, rH, tau, a_E, npairs, pairs, d2, flag,
