@@ -47,17 +47,21 @@ def _energies(oracle, w, q, v):
 
 
 def _chaos_spread(oracle, w, nsteps, energy=False, **prm):
-    """Per-body distance between the oracle's result and the oracle's result
-    from initial positions perturbed by one ulp: how far rounding alone moves
-    each body over the run (large for bodies in close encounters); with
-    energy=True also the per-system energy difference of the two runs."""
+    """Per-body distance between the oracle's result and the oracle's results
+    from initial positions moved by one ulp up and down (the larger of the
+    two): how far rounding alone moves each body over the run (large for
+    bodies in close encounters); with energy=True also the per-system energy
+    difference of those runs."""
     r0, _ = _run_oracle(oracle, w, nsteps, **prm)
-    pert = W.Workload(w.name, w.m, np.nextafter(w.q, np.inf), w.v, w.offsets, w.tau, w.nsteps)
-    r1, _ = _run_oracle(oracle, pert, nsteps, **prm)
-    dq = np.linalg.norm(r1.q - r0.q, axis=1)
-    if not energy:
-        return dq
-    return dq, np.abs(_energies(oracle, w, r1.q, r1.v) - _energies(oracle, w, r0.q, r0.v))
+    dq = np.zeros(len(w.m))
+    dE = np.zeros(w.nsys)
+    for direction in (np.inf, -np.inf):
+        pert = W.Workload(w.name, w.m, np.nextafter(w.q, direction), w.v, w.offsets, w.tau,
+                          w.nsteps)
+        r1, _ = _run_oracle(oracle, pert, nsteps, **prm)
+        dq = np.maximum(dq, np.linalg.norm(r1.q - r0.q, axis=1))
+        dE = np.maximum(dE, np.abs(_energies(oracle, w, r1.q, r1.v) - _energies(oracle, w, r0.q, r0.v)))
+    return (dq, dE) if energy else dq
 
 
 def _check_positions(qg, qo, spread, rel=1e-12):
