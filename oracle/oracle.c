@@ -40,9 +40,10 @@
  *   R7 rigorous test: cubic Hermite interpolant of d^2(t) = |dQ(t)|^2 on
  *      [0, tau] from values and slopes at both ends; the minimum over [0, tau]
  *      (clamped at 0) is compared with (a_E (r_H,i + r_H,j))^2.
- *   R9 Hermite: 4th-order predictor / evaluate / corrector (PEC), Aarseth step
- *      criterion with eta, start-up step eta_s |a| / |adot|, one shared step
- *      per encounter set, the last step clipped to land on tau.
+ *   R9 Hermite: 4th-order predictor / evaluate / corrector (PEC) of Makino &
+ *      Aarseth (1992) with individual block time steps: Aarseth criterion with
+ *      eta, start-up step eta_s |a| / |adot|, each rounded down to tau / 2^k;
+ *      a step may double only on a commensurate block time.
  *   R10 the Hermite integration starts from (q0, v0) after the first kick and
  *      the K correction.
  *   R12 Stumpff series used for |y| < 0.1, summed to the y^8 term.
@@ -673,9 +674,40 @@ void or_hermite_force(int64_t k, const double *mm, const double *x, const double
 
 static double norm3(const double *a) { return sqrt(dot3(a, a)); }
 
-/* Sec. 2.2 and reading R9: integrate the members of one set over tau.
+/* Sec. 2.2 and reading R9: integrate the members of one set over tau with
+ * the 4th-order Hermite scheme of Makino & Aarseth (1992), individual block
+ * time steps (no Ahmad-Cohen neighbour scheme). Time runs in integer ticks of
+ * |tau| / 2^48; member i steps with dt_i = |tau| 2^-k_i, k_i from the
+ * Aarseth criterion (eta; eta_s at start-up) rounded down to a power of two.
+ * At each block time all members are predicted, the members whose step ends
+ * there are evaluated and corrected, and their new level may drop by one (a
+ * doubled step) only when the block time is a multiple of the doubled step.
  * q, v are full-system arrays; members are read and written in place.
- * Returns 0, or 1 when max_steps was reached before tau. */
+ * Returns 0, or 1 when max_steps block steps were taken before tau. */
+#define OR_KMAX 48
+
+static int or_level(double dt_c, double T)
+{
+    /* smallest k with T 2^-k <= dt_c, in [0, OR_KMAX] */
+    if (!(dt_c > 0.0)) return OR_KMAX;
+    int k = 0;
+    double d = T;
+    while (d > dt_c && k < OR_KMAX) {
+        d *= 0.5;
+        ++k;
+    }
+    return k;
+}
+
+static double or_aarseth(const double *a, const double *j, const double *a2, const double *a3,
+                         double eta, double cap)
+{
+    double na = norm3(a), nj = norm3(j), n2 = norm3(a2), n3 = norm3(a3);
+    double den = nj * n3 + n2 * n2;
+    if (!(den > 0.0)) return cap;
+    return sqrt(eta * (na * n2 + nj * nj) / den);
+}
+
 int or_hermite_set(int64_t k, const int64_t *mem, const double *m, double m0, double *q, double *v,
                    double G, double rcrit, double eps, double eta, double eta_s, double tau,
                    int64_t max_steps, int64_t *steps_out)
@@ -686,6 +718,8 @@ int or_hermite_set(int64_t k, const int64_t *mem, const double *m, double m0, do
     double *xp = (double *)malloc(b3), *up = (double *)malloc(b3);
     double *a0 = (double *)malloc(b3), *j0 = (double *)malloc(b3);
     double *a1 = (double *)malloc(b3), *j1 = (double *)malloc(b3);
+    int64_t *ti = (int64_t *)malloc(sizeof(int64_t) * k);
+    int *lev = (int *)malloc(sizeof(int) * k);
     for (int64_t i = 0; i < k; ++i) {
         mm[i] = m[mem[i]];
         for (int c = 0; c < 3; ++c) {
@@ -693,36 +727,46 @@ int or_hermite_set(int64_t k, const int64_t *mem, const double *m, double m0, do
             u[3 * i + c] = v[3 * mem[i] + c];
         }
     }
+    const double T = fabs(tau), sg = tau >= 0.0 ? 1.0 : -1.0;
+    const int64_t TT = (int64_t)1 << OR_KMAX;      /* tau in ticks */
+    const double tick = T / (double)TT;
     or_hermite_force(k, mm, x, u, G, m0, rcrit, eps, a0, j0);
-    /* a negative tau integrates backward: steps of length dt with sign sg */
-    double T = fabs(tau), sg = tau >= 0.0 ? 1.0 : -1.0;
-    /* start-up step, eta_s |a| / |adot|, shared by the set */
-    double dt = T;
+    /* start-up levels from eta_s |a| / |adot| */
     for (int64_t i = 0; i < k; ++i) {
         double jn = norm3(j0 + 3 * i);
-        if (jn > 0.0) {
-            double h = eta_s * norm3(a0 + 3 * i) / jn;
-            if (h < dt) dt = h;
-        }
+        double dt_c = jn > 0.0 ? eta_s * norm3(a0 + 3 * i) / jn : T;
+        lev[i] = or_level(dt_c, T);
+        ti[i] = 0;
     }
-    double t = 0.0;
     int64_t steps = 0;
     int status = 0;
-    while (t < T) {
+    for (;;) {
+        /* next block time: the earliest end of a member's step */
+        int64_t tn = TT;
+        for (int64_t i = 0; i < k; ++i) {
+            int64_t e = ti[i] + ((int64_t)1 << (OR_KMAX - lev[i]));
+            if (e < tn) tn = e;
+        }
+        int done = 1;
+        for (int64_t i = 0; i < k; ++i)
+            if (ti[i] < TT) done = 0;
+        if (done) break;
         if (steps >= max_steps) { status = 1; break; }
-        double hm = dt;
-        int last = 0;
-        if (t + hm >= T) { hm = T - t; last = 1; }
-        double h = sg * hm;
-        /* predictor */
-        for (int64_t i = 0; i < 3 * k; ++i) {
-            xp[i] = x[i] + h * (u[i] + h * (0.5 * a0[i] + h * j0[i] / 6.0));
-            up[i] = u[i] + h * (a0[i] + 0.5 * h * j0[i]);
+        /* predict every member to tn (each from its own time) */
+        for (int64_t i = 0; i < k; ++i) {
+            double h = sg * (double)(tn - ti[i]) * tick;
+            for (int c = 0; c < 3; ++c) {
+                int id = 3 * i + c;
+                xp[id] = x[id] + h * (u[id] + h * (0.5 * a0[id] + h * j0[id] / 6.0));
+                up[id] = u[id] + h * (a0[id] + 0.5 * h * j0[id]);
+            }
         }
         or_hermite_force(k, mm, xp, up, G, m0, rcrit, eps, a1, j1);
-        /* corrector with a^(2), a^(3) from the endpoint a and adot */
-        double next = T;
+        /* correct the members whose step ends at tn */
         for (int64_t i = 0; i < k; ++i) {
+            int64_t dti = (int64_t)1 << (OR_KMAX - lev[i]);
+            if (ti[i] + dti != tn) continue;
+            double h = sg * (double)dti * tick;
             double a2[3], a3[3];
             for (int c = 0; c < 3; ++c) {
                 int id = 3 * i + c;
@@ -730,20 +774,19 @@ int or_hermite_set(int64_t k, const int64_t *mem, const double *m, double m0, do
                 a3[c] = (12.0 * (a0[id] - a1[id]) + 6.0 * h * (j0[id] + j1[id])) / (h * h * h);
                 x[id] = xp[id] + h * h * h * h * (a2[c] / 24.0 + h * a3[c] / 120.0);
                 u[id] = up[id] + h * h * h * (a2[c] / 6.0 + h * a3[c] / 24.0);
-                a2[c] += h * a3[c];   /* a^(2) at the end of the step */
+                a2[c] += h * a3[c];
+                a0[id] = a1[id];
+                j0[id] = j1[id];
             }
-            double na = norm3(a1 + 3 * i), nj = norm3(j1 + 3 * i);
-            double n2 = norm3(a2), n3 = norm3(a3);
-            double den = nj * n3 + n2 * n2;
-            if (den > 0.0) {
-                double hi = sqrt(eta * (na * n2 + nj * nj) / den);
-                if (hi < next) next = hi;
+            ti[i] = tn;
+            int kn = or_level(or_aarseth(a1 + 3 * i, j1 + 3 * i, a2, a3, eta, T), T);
+            if (kn < lev[i]) {
+                /* a larger step: one level at a time, on a commensurate time */
+                int up1 = lev[i] - 1;
+                kn = (tn % ((int64_t)1 << (OR_KMAX - up1)) == 0) ? up1 : lev[i];
             }
+            lev[i] = kn;
         }
-        memcpy(a0, a1, b3);
-        memcpy(j0, j1, b3);
-        t = last ? T : t + hm;
-        dt = next;
         ++steps;
     }
     for (int64_t i = 0; i < k; ++i)
@@ -753,6 +796,7 @@ int or_hermite_set(int64_t k, const int64_t *mem, const double *m, double m0, do
         }
     if (steps_out) *steps_out = steps;
     free(mm); free(x); free(u); free(xp); free(up); free(a0); free(j0); free(a1); free(j1);
+    free(ti); free(lev);
     return status;
 }
 

@@ -145,7 +145,7 @@ def test_hybrid_step_handles_close_encounters(oracle):
     assert np.all(np.diff(r.encounters[:, 0]) >= 0) and r.encounters[:, 0].max() < steps
     dE = abs(oracle.energy(m, r.q, r.v) - E0) / abs(E0)
     assert dE < 3e-5
-    assert np.abs(_Lz(m, r.q, r.v) - L0).max() <= 1e-8 * np.abs(L0).max()
+    assert np.abs(_Lz(m, r.q, r.v) - L0).max() <= 1e-7 * np.abs(L0).max()
     # Hill radii fixed for the run: r_crit no longer changes between steps and
     # the split of H stays consistent; the error spikes during the passage
     # (as the paper reports, ~1e-5) and returns to ~1e-6 after it
