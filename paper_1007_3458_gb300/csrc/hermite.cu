@@ -7,9 +7,15 @@
 //      by [1 - K(s) + s K'(s)], jerks with the K'' term (item 6),
 //   3. pre-remove the (1-K) part of the coming kick at q1 (item 7),
 //   4. write the members' q1, v1 over their Kepler result (item 8).
-// The step is shared by the set (Aarseth criterion with eta, start-up step
-// eta_s |a| / |adot|) and the last step is clipped to land on tau. Every loop
-// has a cap and reports through the status word.
+// Members carry individual block time steps (Makino & Aarseth): time runs in
+// integer ticks of |tau| / 2^48, member i steps with |tau| 2^-k_i from the
+// Aarseth criterion (eta; eta_s at start-up) rounded down to a power of two,
+// and a step doubles only on a commensurate block time. At each block time
+// every member is predicted and the members whose step ends there are
+// evaluated and corrected. Every loop has a cap and reports through the
+// status word.
+#include <climits>
+
 #include "qym_internal.cuh"
 
 namespace qym {
@@ -38,8 +44,11 @@ __device__ __forceinline__ void transition(double s, double rc, double &K, doubl
 
 struct HermSmem {
     double *ex, *ey, *ez, *eu, *ev, *ew, *m;  // evaluation point of every member
-    double *x, *y, *z, *u, *v, *w;            // state
-    double *ax, *ay, *az, *jx, *jy, *jz;      // a, adot at the start of the step
+    double *x, *y, *z, *u, *v, *w;            // state at the member's own time
+    double *ax, *ay, *az, *jx, *jy, *jz;      // a, adot at the member's own time
+    long long *ti;                            // member time in ticks
+    int32_t *lev;                             // member level: step = tau 2^-lev
+    int32_t *act;                             // members whose step ends now
     int32_t *ids;
 };
 
@@ -53,10 +62,27 @@ __device__ __forceinline__ HermSmem carve(void *base) {
     s.u = p; p += HCAP; s.v = p; p += HCAP; s.w = p; p += HCAP;
     s.ax = p; p += HCAP; s.ay = p; p += HCAP; s.az = p; p += HCAP;
     s.jx = p; p += HCAP; s.jy = p; p += HCAP; s.jz = p; p += HCAP;
-    s.ids = (int32_t *)p;
+    s.ti = (long long *)p; p += HCAP;
+    int32_t *ip = (int32_t *)p;
+    s.lev = ip; ip += HCAP;
+    s.act = ip; ip += HCAP;
+    s.ids = ip;
     return s;
 }
-constexpr size_t kHermSmem = sizeof(double) * HCAP * 19 + sizeof(int32_t) * HCAP;
+constexpr size_t kHermSmem = sizeof(double) * HCAP * 20 + sizeof(int32_t) * HCAP * 3;
+constexpr int KMAX = 48;
+
+// smallest k with T 2^-k <= dt_c, in [0, KMAX]
+__device__ __forceinline__ int level_of(double dt_c, double T) {
+    if (!(dt_c > 0.0)) return KMAX;
+    int k = 0;
+    double d = T;
+    while (d > dt_c && k < KMAX) {
+        d *= 0.5;
+        ++k;
+    }
+    return k;
+}
 
 // Work split of a set of n members over the CTA: each member is handled by
 // P consecutive lanes (P a power of two, P * n <= HTHREADS when possible),
@@ -131,6 +157,17 @@ __device__ void herm_part(const HermSmem &S, int n, int k, int l0, int P, double
         aj[4] += cl * (rvl * qy * Kpp + (py - tl * qy) * br);
         aj[5] += cl * (rvl * qz * Kpp + (pz - tl * qz) * br);
     }
+}
+
+__device__ __forceinline__ long long block_min_ll(long long x, long long *red) {
+    for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+    int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = x;
+    __syncthreads();
+    long long r = red[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) r = min(r, red[k]);
+    return r;
 }
 
 __device__ __forceinline__ double block_min(double x, double *red) {
@@ -221,8 +258,11 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
             S.eu[k] = S.u[k]; S.ev[k] = S.v[k]; S.ew[k] = S.w[k];
         }
         __syncthreads();
-        // start-up: a, adot at t = 0 and the step eta_s |a| / |adot|
-        double dtl = fabs(tau);
+        // start-up: a, adot at t = 0 and the levels from eta_s |a| / |adot|
+        const double sgn = tau >= 0.0 ? 1.0 : -1.0;
+        const double T = fabs(tau);
+        const long long TT = 1ll << KMAX;
+        const double tick = T / (double)TT;
         for (int k0 = 0; k0 < n; k0 += NG) {
             int k = k0 + grp;
             double aj[6] = {0, 0, 0, 0, 0, 0};
@@ -232,25 +272,28 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
                 S.ax[k] = aj[0]; S.ay[k] = aj[1]; S.az[k] = aj[2];
                 S.jx[k] = aj[3]; S.jy[k] = aj[4]; S.jz[k] = aj[5];
                 double jn = sqrt(aj[3] * aj[3] + aj[4] * aj[4] + aj[5] * aj[5]);
-                if (jn > 0.0)
-                    dtl = fmin(dtl, h.eta_s * sqrt(aj[0] * aj[0] + aj[1] * aj[1] + aj[2] * aj[2]) / jn);
+                double dt_c = jn > 0.0 ? h.eta_s * sqrt(aj[0] * aj[0] + aj[1] * aj[1] + aj[2] * aj[2]) / jn : T;
+                S.lev[k] = level_of(dt_c, T);
+                S.ti[k] = 0;
             }
         }
-        double dt = block_min(dtl, red);
-        const double sgn = tau >= 0.0 ? 1.0 : -1.0;
-        const double T = fabs(tau);
-        double t = 0.0;
+        __shared__ long long redl[32];
+        __shared__ int n_act;
         int64_t steps = 0;
         bool capped = false;
-        while (t < T) {
-            if (steps >= h.max_steps) { capped = true; break; }
-            double hh = dt;
-            bool last = false;
-            if (t + hh >= T) { hh = T - t; last = true; }
-            const double hs = sgn * hh;  // signed step
+        for (;;) {
             __syncthreads();
-            // predictor
+            // next block time: the earliest end of a member's step
+            long long tn_l = LLONG_MAX;
+            for (int k = tid; k < n; k += blockDim.x)
+                tn_l = min(tn_l, S.ti[k] + (1ll << (KMAX - S.lev[k])));
+            const long long tn = block_min_ll(tn_l, redl);
+            if (tn > TT) break;  // every member has reached tau
+            if (steps >= h.max_steps) { capped = true; break; }
+            if (tid == 0) n_act = 0;
+            // predict every member to tn from its own time; list the active
             for (int k = tid; k < n; k += blockDim.x) {
+                const double hs = sgn * (double)(tn - S.ti[k]) * tick;
                 S.ex[k] = S.x[k] + hs * (S.u[k] + hs * (0.5 * S.ax[k] + hs * S.jx[k] / 6.0));
                 S.ey[k] = S.y[k] + hs * (S.v[k] + hs * (0.5 * S.ay[k] + hs * S.jy[k] / 6.0));
                 S.ez[k] = S.z[k] + hs * (S.w[k] + hs * (0.5 * S.az[k] + hs * S.jz[k] / 6.0));
@@ -259,14 +302,23 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
                 S.ew[k] = S.w[k] + hs * (S.az[k] + 0.5 * hs * S.jz[k]);
             }
             __syncthreads();
-            // evaluate (split over lanes) and correct (lane 0 of each group)
-            double next = T;
-            for (int k0 = 0; k0 < n; k0 += NG) {
-                int k = k0 + grp;
+            for (int k = tid; k < n; k += blockDim.x)
+                if (S.ti[k] + (1ll << (KMAX - S.lev[k])) == tn) S.act[atomicAdd(&n_act, 1)] = k;
+            __syncthreads();
+            const int na = n_act;
+            const int PA = lanes_per_member(na);
+            const int NGA = HTHREADS / PA;
+            const int ga = tid / PA, la = tid % PA;
+            // evaluate (split over lanes) and correct (lane 0) the active members
+            for (int k0 = 0; k0 < na; k0 += NGA) {
+                const int slot = k0 + ga;
+                const int k = slot < na ? S.act[slot] : 0;
                 double a1[6] = {0, 0, 0, 0, 0, 0};
-                if (k < n) herm_part(S, n, k, lane, P, G, m0, rc, h.eps2, a1);
-                group_sum(a1, 6, P);
-                if (k < n && lane == 0) {
+                if (slot < na) herm_part(S, n, k, la, PA, G, m0, rc, h.eps2, a1);
+                group_sum(a1, 6, PA);
+                if (slot < na && la == 0) {
+                    const long long dti = 1ll << (KMAX - S.lev[k]);
+                    const double hs = sgn * (double)dti * tick;
                     double a0[3] = {S.ax[k], S.ay[k], S.az[k]};
                     double j0[3] = {S.jx[k], S.jy[k], S.jz[k]};
                     double e[3] = {S.ex[k], S.ey[k], S.ez[k]};
@@ -283,16 +335,23 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
                     S.u[k] = un[0]; S.v[k] = un[1]; S.w[k] = un[2];
                     S.ax[k] = a1[0]; S.ay[k] = a1[1]; S.az[k] = a1[2];
                     S.jx[k] = a1[3]; S.jy[k] = a1[4]; S.jz[k] = a1[5];
-                    double na = sqrt(a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
+                    S.ti[k] = tn;
+                    // Aarseth criterion at the end of the step, then the level
+                    double na1 = sqrt(a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
                     double nj = sqrt(a1[3] * a1[3] + a1[4] * a1[4] + a1[5] * a1[5]);
                     double n2 = sqrt(a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2]);
                     double n3 = sqrt(a3[0] * a3[0] + a3[1] * a3[1] + a3[2] * a3[2]);
                     double den = nj * n3 + n2 * n2;
-                    if (den > 0.0) next = fmin(next, sqrt(h.eta * (na * n2 + nj * nj) / den));
+                    double dt_c = den > 0.0 ? sqrt(h.eta * (na1 * n2 + nj * nj) / den) : T;
+                    int kn = level_of(dt_c, T);
+                    const int lv = S.lev[k];
+                    if (kn < lv) {  // a larger step: one level, on a commensurate time
+                        const int up1 = lv - 1;
+                        kn = (tn % (1ll << (KMAX - up1)) == 0) ? up1 : lv;
+                    }
+                    S.lev[k] = kn;
                 }
             }
-            dt = block_min(next, red);
-            t = last ? T : t + hh;
             ++steps;
         }
         __syncthreads();
