@@ -25,7 +25,8 @@
  *
  * Readings of passages that are silent or garbled (each is also listed in the
  * design notes of the repository):
- *   R1 Laguerre update: x <- x - n F / (F' + sgn(F') sqrt|(n-1)^2 F'^2 - n(n-1) F F''|).
+ *   R1 Laguerre update: x <- x - n F / (F' + sgn(F') sqrt|(n-1)^2 F'^2 - n(n-1) F F''|),
+ *      evaluated as n (F/F') / (1 + sqrt|(n-1)^2 - n(n-1) (F/F')(F''/F')|).
  *   R2 mu = G m0 (the Kepler term uses the star mass only); sqrt(mu) where the
  *      appendix writes sqrt(mu).
  *   R3 fdot = sqrt(mu) x (alpha x^2 S(alpha x^2) - 1) / (r r0), r = F'(x).
@@ -167,18 +168,20 @@ int or_kepler_solve_br(double sqmu, double dt, double r0, double sig, double alp
         }
         double dx;
         if (solver == 0) {
-            double disc = fabs((n - 1.0) * (n - 1.0) * Fp * Fp - n * (n - 1.0) * F * Fpp);
-            double den = Fp + (Fp >= 0.0 ? 1.0 : -1.0) * sqrt(disc);
-            dx = n * F / den;
+            /* R1 with F' factored out of the square root (the same value; F'^2
+             * itself overflows near the top of an unbound orbit's bracket) */
+            double rf = F / Fp, rpp = Fpp / Fp;
+            double sq = sqrt(fabs((n - 1.0) * (n - 1.0) - n * (n - 1.0) * rf * rpp));
+            dx = n * rf / (1.0 + sq);
         } else {
             dx = F / Fp;
         }
         double xn = x - dx;
         int bracketed = isfinite(lo) && isfinite(hi);
-        /* bisect when the step leaves the bracket, or when it does not at
-         * least halve the previous step (slow approach along the exponential
-         * flank of F on unbound orbits) */
-        if (bracketed && (!(xn >= lo && xn <= hi) || fabs(dx) > 0.5 * fabs(dx_old))) {
+        /* bisect when the step is not finite, leaves the bracket, or does not
+         * at least halve the previous step (slow approach along the
+         * exponential flank of F on unbound orbits) */
+        if (bracketed && (!isfinite(dx) || !(xn >= lo && xn <= hi) || fabs(dx) > 0.5 * fabs(dx_old))) {
             xn = 0.5 * (lo + hi);
             dx = x - xn;
         }

@@ -139,17 +139,18 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
                 if (fabs(F) <= 1e-14 * scale) { --iters; conv = true; break; }
                 double dx;
                 if (solver == QYM_SOLVER_LAGUERRE) {
-                    // Laguerre, n = 5: dx = n F / (F' + sgn(F') sqrt|(n-1)^2 F'^2 - n(n-1) F F''|)
-                    double disc = fabs(16.0 * Fp * Fp - 20.0 * F * Fpp);
-                    dx = 5.0 * F / (Fp + copysign(sqrt(disc), Fp));
+                    // Laguerre, n = 5: dx = n F / (F' + sgn(F') sqrt|(n-1)^2 F'^2 - n(n-1) F F''|),
+                    // with F' taken out of the root so that F'^2 never overflows
+                    const double rf = F / Fp, rpp = Fpp / Fp;
+                    dx = 5.0 * rf / (1.0 + sqrt(fabs(16.0 - 20.0 * rf * rpp)));
                 } else {
                     dx = F / Fp;
                 }
                 double xn = x - dx;
-                // bisect when the step leaves the bracket or fails to halve the
-                // previous step (slow approach along exp(sqrt(-alpha) x))
+                // bisect when the step is not finite, leaves the bracket, or fails
+                // to halve the previous step (slow approach along exp(sqrt(-alpha) x))
                 if (isfinite(lo) && isfinite(hi) &&
-                    (!(xn >= lo && xn <= hi) || fabs(dx) > 0.5 * fabs(dx_old))) {
+                    (!isfinite(dx) || !(xn >= lo && xn <= hi) || fabs(dx) > 0.5 * fabs(dx_old))) {
                     xn = 0.5 * (lo + hi);
                     dx = x - xn;
                 }

@@ -97,23 +97,25 @@ def test_angular_momentum_conserved(oracle):
     assert np.abs(_Lz(m, r.q, r.v) - L0).max() <= 1e-13 * np.abs(L0).max()
 
 
-def test_bounded_energy_no_secular_drift_1e5_steps(oracle):
-    """1e5 steps of a small disk: the energy error stays bounded, with no
-    secular growth between the first and second half of the run."""
-    w = W.outer_disk(6, 1e-8, seed=9)
+@pytest.mark.parametrize("n_pl,enc,cap", [(0, 0, 2e-6), (6, 1, 2e-5)])
+def test_bounded_energy_no_secular_drift_1e5_steps(oracle, n_pl, enc, cap):
+    """1e5 steps: the four giant planets alone (plain DH step), and with six
+    planetesimals (hybrid step; a close approach to a planet early in the run
+    sets the level). The energy error stays bounded: no growth between the
+    first and second half of the run."""
+    w = W.outer_disk(n_pl, 1e-8, seed=9)
     m, q, v = _dh(oracle, w)
-    prm = oracle.params(encounters=0)
+    prm = oracle.params(encounters=enc)
     E0 = oracle.energy(m, q, v)
     errs = []
-    chunk, nchunks = 1000, 100
-    for _ in range(nchunks):
-        r = oracle.step(m, q, v, w.offsets, w.tau, chunk, prm)
+    for _ in range(100):
+        r = oracle.step(m, q, v, w.offsets, w.tau, 1000, prm)
         q, v = r.q, r.v
         errs.append((oracle.energy(m, q, v) - E0) / E0)
     errs = np.abs(np.array(errs))
     first, second = errs[:50].max(), errs[50:].max()
     assert second < 1.5 * first + 1e-12
-    assert errs.max() < 1e-5
+    assert errs.max() < cap
 
 
 def _crossing_planets():
