@@ -45,6 +45,7 @@ class Workload:
     G: float = 1.0
     a_E: float = 3.0       # encounter factor in Hill radii
     a_H: float = 1.0       # transition radius factor in Hill radii
+    eps_H: float = 1e-6    # Hermite smoothing: about the radius of the largest body
 
     @property
     def nsys(self) -> int:
@@ -174,8 +175,9 @@ def outer_disk(n_planetesimals=256, m_pl=1e-9, seed=0, nsteps=1000, name=None,
     pl = _planets(rng, OUTER_PLANETS_M, OUTER_PLANETS_A, G, m0)
     ps = _population(rng, n_planetesimals, m_pl, a_lo, a_hi, sig_e, sig_i, G, m0)
     m, q, v = _assemble([pl, ps], m0)
+    # smoothing: Jupiter's radius in AU (lengths here are AU, G m0 = 1)
     return Workload(name or f"outer_disk_{4 + n_planetesimals}", m, q, v,
-                    np.array([0, len(m)], dtype=np.int64), TAU_A5, nsteps)
+                    np.array([0, len(m)], dtype=np.int64), TAU_A5, nsteps, eps_H=4.7e-4)
 
 
 def disk_260():
@@ -196,8 +198,9 @@ def embryo_disk(n_embryos=64, n_planetesimals=262080, seed=2, nsteps=10, name=No
     em = _population(rng, n_embryos, 1e-6, 1.0, 3.0, 0.02, 0.02, G, m0)
     ps = _population(rng, n_planetesimals, 1e-11, 1.0, 3.0, 0.02, 0.02, G, m0)
     m, q, v = _assemble([em, ps], m0)
+    # smoothing: the radius of a 1e-6 solar-mass rocky embryo, ~2e-5 AU
     return Workload(name or f"embryo_disk_{n_embryos + n_planetesimals}", m, q, v,
-                    np.array([0, len(m)], dtype=np.int64), TAU_A1, nsteps)
+                    np.array([0, len(m)], dtype=np.int64), TAU_A1, nsteps, eps_H=2e-5)
 
 
 def disk_262144():
@@ -221,8 +224,10 @@ def ensemble(nsys=512, n_lo=64, n_hi=4096, seed=3, nsteps=1000, name=None):
         qs.append(q)
         vs.append(v)
         offs.append(offs[-1] + len(m))
+    # smoothing: the radius of a Jupiter-mass planet at 1 AU
     return Workload(name or f"ensemble_{nsys}", np.concatenate(ms), np.concatenate(qs),
-                    np.concatenate(vs), np.array(offs, dtype=np.int64), TAU_A1, nsteps)
+                    np.concatenate(vs), np.array(offs, dtype=np.int64), TAU_A1, nsteps,
+                    eps_H=4.7e-4)
 
 
 def test_particles(n=1048576, seed=4):
@@ -249,4 +254,4 @@ def subsample(w: Workload, n_bodies: int, seed: int = 0, name=None) -> Workload:
     rows = np.concatenate([[0], heavy, pick]).astype(int)
     return Workload(name or f"{w.name}_sub{len(rows) - 1}", m[rows].copy(), q[rows].copy(),
                     v[rows].copy(), np.array([0, len(rows)], dtype=np.int64), w.tau, w.nsteps,
-                    w.G, w.a_E, w.a_H)
+                    w.G, w.a_E, w.a_H, w.eps_H)
