@@ -62,6 +62,7 @@ def lib():
         L.or_kepler_drift.argtypes = [C.c_int64, D, D, D, D, C.c_double, C.c_double, C.c_int32,
                                       C.c_int32, D, C.c_int32, D, I32]
         L.or_kepler_drift.restype = C.c_int64
+        L.or_kepler_residuals.argtypes = [C.c_int64, D, D, C.c_double, C.c_double, D, D]
         L.or_momentum.argtypes = [C.c_int64, D, D, D]
         L.or_drift.argtypes = [C.c_int64, D, D, D, C.c_double]
         L.or_accel_int.argtypes = [C.c_int64, D, D, C.c_double, D]
@@ -138,6 +139,16 @@ def kepler_drift(q0, v0, mu, dt, solver=0, guess=0, x_guess=None, max_iter=50):
                                 None if xg is None else _d(xg), max_iter, _d(x),
                                 it.ctypes.data_as(I32))
     return q1, v1, x, it, int(bad)
+
+
+def kepler_residuals(q0, v0, mu, dt, x):
+    """|F(x)| / (sum of |terms| of F) for each body (Appendix)."""
+    q0 = _f64(q0, (-1, 3))
+    v0 = _f64(v0, (-1, 3))
+    x = _f64(x)
+    res = np.empty(q0.shape[0])
+    lib().or_kepler_residuals(q0.shape[0], _d(q0), _d(v0), float(mu), float(dt), _d(x), _d(res))
+    return res
 
 
 # ---------------------------------------------------------------- Sec. 2

@@ -279,6 +279,28 @@ int64_t or_kepler_drift(int64_t n, const double *q0, const double *v0, double *q
     return bad;
 }
 
+/* Relative residual |F(x)| / (sum of the absolute values of the terms of F)
+ * of x as a root of the universal Kepler equation (Appendix) for bodies
+ * [0, n) with states q0, v0 ([n][3]) about a star of parameter mu. */
+void or_kepler_residuals(int64_t n, const double *q0, const double *v0, double mu, double dt,
+                         const double *x, double *res)
+{
+    double sqmu = sqrt(mu);
+    for (int64_t i = 0; i < n; ++i) {
+        const double *q = q0 + 3 * i, *v = v0 + 3 * i;
+        double r0 = sqrt(dot3(q, q));
+        double alpha = 2.0 / r0 - dot3(v, v) / mu;
+        double sig = dot3(q, v) / sqmu;
+        double F, Fp, Fpp, C, S;
+        or_kepler_F(x[i], sqmu, dt, r0, sig, alpha, &F, &Fp, &Fpp);
+        or_stumpff(alpha * x[i] * x[i], &C, &S);
+        double xx = x[i];
+        double scale = fabs(sqmu * dt) + fabs(sig * xx * xx * C) +
+                       fabs((1.0 - r0 * alpha) * xx * xx * xx * S) + r0 * fabs(xx);
+        res[i] = fabs(F) / scale;
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* Sec. 2: E_Dft -- sum of barycentric momenta, uniform shift of Q      */
 /* ------------------------------------------------------------------ */

@@ -255,3 +255,41 @@ def subsample(w: Workload, n_bodies: int, seed: int = 0, name=None) -> Workload:
     return Workload(name or f"{w.name}_sub{len(rows) - 1}", m[rows].copy(), q[rows].copy(),
                     v[rows].copy(), np.array([0, len(rows)], dtype=np.int64), w.tau, w.nsteps,
                     w.G, w.a_E, w.a_H, w.eps_H)
+
+
+# ---------------------------------------------------------------- learned guess
+MLP_NW = 4555   # 4*64 + 64 + 64*64 + 64 + 64 + 1 + 4 + 4 + 2
+
+
+def mlp_init(seed, u, z, hidden=64):
+    """Seeded initial weights of the 4 -> 64 -> 64 -> 1 guess network as one
+    float32 vector (layout of qym_set_mlp): He-scaled normal matrices, zero
+    biases, and the input/output normalisation taken from sample statistics
+    of the training rows (u [n, 4] raw features, z [n] targets t)."""
+    rng = np.random.default_rng(seed)
+    H = hidden
+    W1 = rng.normal(0.0, math.sqrt(2.0 / 4), (H, 4))
+    W2 = rng.normal(0.0, math.sqrt(2.0 / H), (H, H))
+    W3 = rng.normal(0.0, math.sqrt(1.0 / H), H)
+    u = np.asarray(u, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    mean = u.mean(axis=0)
+    std = u.std(axis=0) + 1e-6
+    w = np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), W3, [0.0], mean, std,
+                        [z.mean(), z.std() + 1e-6]])
+    assert w.size == MLP_NW
+    return w.astype(np.float32)
+
+
+def mlp_rows_synthetic(n, seed):
+    """Synthetic training rows (u1, u2, u3, u4, z) float32 [n, 5] spanning the
+    ranges the features take on bound orbits with e < 0.9 and steps up to a
+    period (u1 radial/circular speed, u2 = 2 - r0/a, u3 log step over the
+    dynamical time, u4 step over period), with a smooth target z."""
+    rng = np.random.default_rng(seed)
+    u1 = rng.normal(0.0, 0.3, n)
+    u2 = rng.uniform(0.1, 1.9, n)
+    u3 = rng.uniform(-5.0, 1.6, n)
+    u4 = rng.uniform(0.0, 0.8, n)
+    z = 1.0 + 0.3 * np.tanh(u1 * u4 * 4.0) + 0.2 * (u2 - 1.0) * u4 + 0.05 * np.sin(u3)
+    return np.stack([u1, u2, u3, u4, z], axis=1).astype(np.float32)
