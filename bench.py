@@ -38,6 +38,12 @@ WORKLOADS = {
     "ensemble_512": ("ensemble", "512 systems, N uniform 64-4096: 2 planets (1e-3 at a=1, 1.6) + planetesimals (1e-9), seed 3"),
 }
 METRIC = "particle-steps/s"
+# E_Kep alone on massless test particles: a "step" is one Kepler drift of
+# every particle; the learned guess is compared with the standard one
+KEPLER_WORKLOADS = {
+    "kepler_1m": "1,048,576 massless test particles about a unit star: a log-uniform 0.5-50, "
+                 "e uniform 0-0.9, seed 4; tau = P(a=5)/40; E_Kep only",
+}
 
 
 def _dist():
@@ -155,10 +161,40 @@ def cpu_baseline(w, prec_label, max_seconds=20.0):
             "sample": sample + " (plain FP64 oracle, single thread)"}
 
 
+def run_reference_kepler(args):
+    """The oracle's Kepler drift of test particles, single thread, on a
+    bounded sample (the first 20000 particles per step)."""
+    import oracle as O
+    from paper_1007_3458_gb300 import workloads as W
+    O.build()
+    qq, vv, dt = W.test_particles(1 << 20, seed=4)
+    m = 20000
+    solver = 1 if args.solver == "newton" else 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.kepler_drift(qq[:m], vv[:m], 1.0, dt, solver=solver)
+    cdt = time.perf_counter() - t0
+    value = m * args.steps / cdt
+    cb = {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+          "sample": f"first {m} particles, {args.steps} drifts, standard guess (plain FP64 oracle, single thread)"}
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * len(qq) / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "description": KEPLER_WORKLOADS[args.workload],
+                       "solver": args.solver, "guess": "standard", "l2": "n/a (CPU)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
         return 0
+    if args.workload in KEPLER_WORKLOADS:
+        return run_reference_kepler(args)
     w, desc = _workload(args.workload)
     t_all = time.perf_counter()
     for _ in range(args.warmup):
@@ -286,6 +322,145 @@ def run_ours(args):
     return 0
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of the GB300s, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_kepler(args):
+    """E_Kep of 1,048,576 test particles (Appendix): timed drifts with the
+    standard and the learned starting guess."""
+    import torch
+    ws, rank = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.cuda.current_device()
+    import paper_1007_3458_gb300 as q
+    from paper_1007_3458_gb300 import guess as G
+    from paper_1007_3458_gb300 import workloads as W
+    q.build()
+    solver = q.QYM_SOLVER_NEWTON if args.solver == "newton" else q.QYM_SOLVER_LAGUERRE
+    t_train = time.perf_counter()
+    if args.train:
+        wts, losses, nrows = G.train_default()
+    else:
+        # standard guess only (a quick run, e.g. for a profiler capture)
+        wts, losses, nrows = np.zeros(q.QYM_MLP_NW, np.float32), np.zeros(100, np.float32), 0
+        args.guess = "standard"
+    t_train = time.perf_counter() - t_train
+    qq, vv, dt = W.test_particles(1 << 20, seed=4)
+    n = len(qq)
+    q0 = torch.from_numpy(np.ascontiguousarray(qq.T)).cuda()
+    v0 = torch.from_numpy(np.ascontiguousarray(vv.T)).cuda()
+    q1, v1 = torch.empty_like(q0), torch.empty_like(v0)
+    wd = torch.from_numpy(wts).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def drift(guess, x=None, it=None, st=None):
+        q.qym_kepler_drift_dev(n, q0, v0, q1, v1, 1.0, dt, solver, guess,
+                               wd if guess == q.QYM_GUESS_MLP else None, 50, x_out=x,
+                               iters=it, status=st)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    res = {}
+    arms = (("standard", q.QYM_GUESS_STANDARD), ("learned", q.QYM_GUESS_MLP))
+    for name, guess in arms[:2 if args.train else 1]:
+        it = torch.empty(n, dtype=torch.int32, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        drift(guess, it=it, st=st)
+        for _ in range(args.warmup):
+            drift(guess)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        with ClockSampler(dev) as clk:
+            barrier()
+            for a, b in ev:
+                flush.fill_(1)          # L2 flushed between timed drifts (outside the events)
+                a.record(stream)
+                drift(guess)
+                b.record(stream)
+            barrier()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        itn = it.cpu().numpy()
+        res[name] = {"value": n * args.steps * ws / (ms / 1e3), "ms_per_step": ms / args.steps,
+                     "iterations_mean": float(itn.mean()), "iterations_max": int(itn.max()),
+                     "status": int(st.item()), "clocks": clk.summary()}
+    head = res[args.guess]
+    # end to end through the C ABI with host buffers: the state goes host ->
+    # device, one drift, device -> host
+    hq = torch.from_numpy(np.ascontiguousarray(qq.T)).pin_memory()
+    hv = torch.from_numpy(np.ascontiguousarray(vv.T)).pin_memory()
+    oq, ov = torch.empty_like(hq).pin_memory(), torch.empty_like(hv).pin_memory()
+    g_head = q.QYM_GUESS_MLP if args.guess == "learned" else q.QYM_GUESS_STANDARD
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        q0.copy_(hq, non_blocking=True)
+        v0.copy_(hv, non_blocking=True)
+        drift(g_head)
+        oq.copy_(q1, non_blocking=True)
+        ov.copy_(v1, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    nbytes = int(hq.numel() * 8 + hv.numel() * 8)
+    e2e = {"value": n * e2e_steps * ws / e2e_s, "unit": METRIC, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
+           "what": "pinned H2D of (q, v) + qym_kepler_drift_dev + D2H of (q1, v1) per step"}
+    # roofline of k_kepler: 96 algorithmic bytes per particle (read q0, v0,
+    # write q1, v1, float64 x 3 each)
+    peak, which = hbm_peak_gbs()
+    achieved = 96.0 * n / (head["ms_per_step"] / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_kepler<%s>" % ("true" if args.guess == "learned" else "false"),
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": which,
+            "bytes_per_particle": 96}
+    if rank != 0:
+        return 0
+    cb = None
+    if ws == 1:
+        import oracle as O
+        O.build()
+        m = 20000
+        t0 = time.perf_counter()
+        O.kepler_drift(qq[:m], vv[:m], 1.0, dt, solver=1 if args.solver == "newton" else 0)
+        cdt = time.perf_counter() - t0
+        cb = {"value": m / cdt, "unit": METRIC, "cores": 1, "kind": "oracle",
+              "sample": f"first {m} particles, one drift, standard guess (plain FP64 oracle, single thread)"}
+    line = {"metric": METRIC, "value": head["value"], "unit": METRIC, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (bf16/f32 guess network)" if args.guess == "learned" else "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": KEPLER_WORKLOADS[args.workload],
+                       "solver": args.solver, "guess": args.guess, "particles": n, "tau": dt,
+                       "l2": "flushed: 256 MB written before every timed drift, outside the events",
+                       "training": {"rows": nrows, "seconds": t_train,
+                                    "loss_first": float(losses[:10].mean()),
+                                    "loss_last": float(losses[-100:].mean())}},
+            "compare": res, "gpu_launches": args.steps, "roofline": roof,
+            "clocks": head["clocks"], "e2e": e2e, "cpu_baseline": cb}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -293,7 +468,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="disk_16384", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="disk_16384",
+                    choices=sorted(WORKLOADS) + sorted(KEPLER_WORKLOADS))
+    ap.add_argument("--guess", default="learned", choices=["standard", "learned"],
+                    help="kepler_1m: the starting guess of the headline number")
+    ap.add_argument("--solver", default="newton", choices=["newton", "laguerre"],
+                    help="kepler_1m: Kepler solver")
+    ap.add_argument("--train", type=int, default=1,
+                    help="kepler_1m: train the guess network first (0: standard guess only)")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--kick-only", action="store_true",
@@ -303,6 +485,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in KEPLER_WORKLOADS:
+        return run_kepler(args)
     return run_ours(args)
 
 

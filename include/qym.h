@@ -174,13 +174,36 @@ qym_status qym_energy(qym_ctx *ctx, double *E);
 /* Counters of the last qym_step call. */
 qym_status qym_get_stats(qym_ctx *ctx, qym_stats *st);
 
-/* Set the learned Kepler starting-guess network used with QYM_GUESS_MLP: a
- * 4 -> 64 -> 64 -> 1 perceptron with GELU, weights as host float32 in the
- * order W1[64][4], b1[64], W2[64][64], b2[64], W3[64], b3[1], followed by the
- * input normalisation mean[4], std[4] and the output scale pair (mean, std):
- * n = 4*64 + 64 + 64*64 + 64 + 64 + 1 + 4 + 4 + 2 = 4615 floats. The weights
- * are rounded to bf16 on the device. */
+/* Learned Kepler starting guess (the Appendix's universal Kepler equation
+ * solved from a predicted start instead of x_std = sqrt(mu) dt / r0). A
+ * 4 -> 64 -> 64 -> 1 perceptron with GELU (tanh form) maps the features
+ *   u1 = q.v / sqrt(mu r0), u2 = r0 |v|^2 / mu, u3 = ln s,
+ *   u4 = dt / P (dt sqrt(mu alpha^3) / 2 pi for bound orbits, else 0),
+ * s = |dt| sqrt(mu / r0^3), each normalised as (u - mean) / std, to
+ * t = om + osd * y; the guess is x_std (1 + sigma t) with sigma = s / (1 + s).
+ * Weights: one float32 vector of QYM_MLP_NW entries, in the order W1[64][4],
+ * b1[64], W2[64][64], b2[64], W3[64], b3, mean[4], std[4], om, osd. The matrices
+ * are rounded to bf16 where they are used (tensor cores, FP32 accumulation).
+ * The network is used for bodies on bound orbits (alpha = 2/r0 - |v|^2/mu > 0,
+ * where |u1| < sqrt 2 and u2 < 2); the others keep x_std. If the iteration
+ * from the learned guess does not converge, Laguerre from the standard guess
+ * is run. */
+#define QYM_MLP_NW 4555
+
+/* Set the network used by qym_step with params.guess == QYM_GUESS_MLP
+ * (host float32 weights[n], n == QYM_MLP_NW, std entries > 0). Returns
+ * QYM_EINVAL for a wrong n or non-finite weights. qym_step with
+ * QYM_GUESS_MLP fails with QYM_EINVAL until a network is set. */
 qym_status qym_set_mlp(qym_ctx *ctx, const float *weights, int64_t n);
+
+/* Log every Kepler solve of the following qym_step calls as a training row
+ * (u1, u2, u3, u4, t) with t = (x / x_std - 1) / sigma at the converged root
+ * x: device float32 rows[cap][5] (caller owned, kept until replaced). The
+ * solve of row k in the s-th step after this call goes to row s * R + k (R
+ * = total rows of ctx) while that is below cap; only solves on bound orbits
+ * are written (star rows and unbound bodies leave their rows untouched).
+ * cap = 0 (rows NULL) stops logging. */
+qym_status qym_set_kepler_log(qym_ctx *ctx, float *rows, int64_t cap);
 
 /* Message for the last error on ctx (ctx may be NULL: last context-free error
  * of the calling thread). The string lives until the next call on ctx. */
@@ -220,16 +243,53 @@ qym_status qym_autotune(qym_ctx *ctx);
  * gravitational parameter mu for dt with universal-variable f and g functions.
  *  q0, v0    device float64[3][n] input state (not modified)
  *  q1, v1    device float64[3][n] output state (must not alias q0, v0)
- *  solver    QYM_SOLVER_*; guess QYM_GUESS_STANDARD or QYM_GUESS_R0, or
- *            QYM_GUESS_MLP with x_guess != NULL (device float32[n] guesses)
+ *  solver    QYM_SOLVER_*; guess QYM_GUESS_STANDARD, QYM_GUESS_R0, or
+ *            QYM_GUESS_MLP with mlp_w != NULL
+ *  mlp_w     device float32[QYM_MLP_NW] guess network (16-byte aligned), or NULL
  *  x_out     device float64[n] universal variable x, or NULL
+ *  x0_out    device float64[n] starting value of x, or NULL
  *  iters     device int32[n] iterations used, or NULL
+ *  log_rows  device float32[n][5] training row (u1..u4, t) of each body on a
+ *            bound orbit with r0 > 0 and dt != 0 (others untouched), or NULL
  *  status    device int32 word, QYM_ST_KEPLER_NOCONV / QYM_ST_NAN OR-ed in, or NULL
- * n = 0 is a no-op. Returns QYM_EINVAL for n < 0, mu <= 0, max_iter < 1. */
+ * n = 0 is a no-op. Returns QYM_EINVAL for n < 0, mu <= 0, max_iter < 1, an
+ * unknown solver or guess, or QYM_GUESS_MLP without mlp_w. */
 qym_status qym_kepler_drift_dev(int64_t n, const double *q0, const double *v0, double *q1,
                                 double *v1, double mu, double dt, int32_t solver, int32_t guess,
-                                const float *x_guess, int32_t max_iter, double *x_out,
-                                int32_t *iters, int32_t *status, void *stream);
+                                const float *mlp_w, int32_t max_iter, double *x_out,
+                                double *x0_out, int32_t *iters, float *log_rows, int32_t *status,
+                                void *stream);
+
+/* The guess network's normalised output y for raw features u (device
+ * float32[n][4], 16-byte aligned) into device float32 y[n]; w as in
+ * qym_set_mlp (device, 16-byte aligned). n = 0 is a no-op. */
+qym_status qym_mlp_forward_dev(int64_t n, const float *w, const float *u, float *y, void *stream);
+
+/* Training of the guess network on rows (u1, u2, u3, u4, t), device
+ * float32[n][5]: the loss is the mean over the rows of (y - (t - om)/osd)^2.
+ * work: device scratch of qym_mlp_workspace_bytes() bytes (caller owned).
+ *
+ * qym_mlp_grad_dev: dL/dw of all n rows into device float32 grad[QYM_MLP_NW]
+ *   (zero for the ten normalisation entries) and, if loss != NULL, L into
+ *   device float32 *loss.
+ * qym_mlp_adam_dev: one Adam step (Kingma & Ba) number t >= 1 with gradient
+ *   grad on w, first and second moments m, v (device float32[QYM_MLP_NW]):
+ *   m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ *   w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps); the normalisation
+ *   entries are left unchanged.
+ * qym_mlp_train_dev: `epochs` passes over the rows in minibatches of `batch`
+ *   consecutive rows (the last one ragged), a gradient and an Adam step per
+ *   minibatch (betas 0.9, 0.999, eps 1e-8, step numbers t0 + 1, ...) with the
+ *   learning rate following a cosine from lr down to lr_final over all steps;
+ *   losses: device float32[steps] minibatch losses, or NULL. */
+size_t qym_mlp_workspace_bytes(void);
+qym_status qym_mlp_grad_dev(int64_t n, const float *w, const float *rows, float *grad, float *loss,
+                            void *work, size_t work_bytes, void *stream);
+qym_status qym_mlp_adam_dev(float *w, float *m, float *v, const float *grad, int64_t t, float lr,
+                            float beta1, float beta2, float eps, void *stream);
+qym_status qym_mlp_train_dev(float *w, float *m, float *v, int64_t t0, const float *rows, int64_t n,
+                             int64_t batch, int32_t epochs, float lr, float lr_final, float *losses,
+                             void *work, size_t work_bytes, void *stream);
 
 /* E_Int acceleration (Sec. 2, Eq. 4) of one system: for rows i >= 1
  *   a_i = -sum_{j >= 1, j != i} G m_j (Q_i - Q_j) / |Q_i - Q_j|^3,

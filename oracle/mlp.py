@@ -128,7 +128,8 @@ def target(q0, dt, mu, xstar):
 
 
 def log_rows(q0, v0, dt, mu, xstar):
-    """Training rows (u1, u2, u3, u4, t), float32 [n, 5]."""
+    """Training rows (u1, u2, u3, u4, t), float32 [n, 5] (meaningful for bound
+    orbits, the ones the Kepler kernel logs)."""
     u = features(q0, v0, dt, mu)
     t = target(q0, dt, mu, xstar)
     return np.concatenate([u, t[:, None]], axis=1).astype(np.float32)
@@ -153,11 +154,22 @@ def forward(w, u, emulate=False):
     return y, (fn, p1, h1in, p2, h2)
 
 
+def bound(q0, v0, mu):
+    """alpha = 2/r0 - |v0|^2/mu > 0: the orbits the learned guess is used for
+    (|u1| < sqrt 2 and u2 < 2 there); unbound bodies keep x_std."""
+    q0 = np.asarray(q0, dtype=np.float64).reshape(-1, 3)
+    v0 = np.asarray(v0, dtype=np.float64).reshape(-1, 3)
+    return 2.0 / np.sqrt(np.sum(q0 * q0, axis=1)) - np.sum(v0 * v0, axis=1) / mu > 0
+
+
 def guess(w, q0, v0, dt, mu, emulate=False):
-    """The learned starting guess x for each body."""
+    """The starting guess x for each body: learned on bound orbits, x_std
+    elsewhere."""
     P = unpack(w)
     y, _ = forward(w, features(q0, v0, dt, mu), emulate)
-    return x_std(q0, dt, mu) * (1.0 + sigma(q0, dt, mu) * (P["om"] + P["osd"] * y))
+    xs = x_std(q0, dt, mu)
+    learned = xs * (1.0 + sigma(q0, dt, mu) * (P["om"] + P["osd"] * y))
+    return np.where(bound(q0, v0, mu), learned, xs)
 
 
 def y_tolerance(w, u, rel=1e-5, near=1e-5):
@@ -226,15 +238,21 @@ def loss(w, u, t):
 def adam(w, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     """Adam step t (1-based): m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2,
     w <- w - lr m_hat / (sqrt(v_hat) + eps) with m_hat = m / (1 - b1^t),
-    v_hat = v / (1 - b2^t); the normalisation entries are left as they are.
-    Returns (w, m, v) in float64."""
+    v_hat = v / (1 - b2^t). The normalisation entries are not parameters of
+    the fit: their w, m and v are left as they are. Returns (w, m, v) in
+    float64."""
     w = np.array(w, dtype=np.float64)
-    m = b1 * np.asarray(m, dtype=np.float64) + (1.0 - b1) * g
-    v = b2 * np.asarray(v, dtype=np.float64) + (1.0 - b2) * g * g
+    m0 = np.asarray(m, dtype=np.float64)
+    v0 = np.asarray(v, dtype=np.float64)
+    m = b1 * m0 + (1.0 - b1) * g
+    v = b2 * v0 + (1.0 - b2) * g * g
     mh = m / (1.0 - b1 ** t)
     vh = v / (1.0 - b2 ** t)
     upd = lr * mh / (np.sqrt(vh) + eps)
-    upd[NW - N_FROZEN:] = 0.0
+    fz = slice(NW - N_FROZEN, NW)
+    upd[fz] = 0.0
+    m[fz] = m0[fz]
+    v[fz] = v0[fz]
     return w - upd, m, v
 
 
@@ -243,7 +261,7 @@ def lr_at(step, nsteps, lr, lr_final):
     return lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * step / nsteps))
 
 
-def train(w, data, batch, epochs, lr, lr_final):
+def train(w, data, batch, epochs, lr, lr_final, emulate=False):
     """Minibatch Adam over data rows (u1..u4, t) in order, `epochs` passes,
     cosine learning rate; weights kept in float32 between steps as the GPU
     keeps them. Returns (w float32, per-step losses)."""
@@ -258,7 +276,7 @@ def train(w, data, batch, epochs, lr, lr_final):
     for s in range(S):
         b = s % nb
         rows = data[b * batch:min(n, (b + 1) * batch)]
-        L, g, _ = loss_and_grad(w, rows[:, :4], rows[:, 4])
+        L, g, _ = loss_and_grad(w, rows[:, :4], rows[:, 4], emulate)
         losses.append(L)
         w64, m, v = adam(w, m, v, g, s + 1, lr_at(s, S, lr, lr_final))
         w = w64.astype(np.float32)

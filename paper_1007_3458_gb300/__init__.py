@@ -27,6 +27,7 @@ QYM_KICK_FP64, QYM_KICK_MIXED = 0, 1
 QYM_SOLVER_LAGUERRE, QYM_SOLVER_NEWTON = 0, 1
 QYM_GUESS_STANDARD, QYM_GUESS_R0, QYM_GUESS_MLP = 0, 1, 2
 QYM_STATIC_MAX_ROWS = 32768
+QYM_MLP_NW = 4555
 
 
 class QymError(RuntimeError):
@@ -96,7 +97,16 @@ def lib():
     L.qym_time_kick.argtypes = [P, C.c_int32, C.c_int32, D, I64]
     L.qym_autotune.argtypes = [P]
     L.qym_kepler_drift_dev.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_int32,
-                                       C.c_int32, P, C.c_int32, P, P, P, P]
+                                       C.c_int32, P, C.c_int32, P, P, P, P, P, P]
+    L.qym_set_kepler_log.argtypes = [P, P, C.c_int64]
+    L.qym_mlp_workspace_bytes.argtypes = []
+    L.qym_mlp_workspace_bytes.restype = C.c_size_t
+    L.qym_mlp_forward_dev.argtypes = [C.c_int64, P, P, P, P]
+    L.qym_mlp_grad_dev.argtypes = [C.c_int64, P, P, P, P, P, C.c_size_t, P]
+    L.qym_mlp_adam_dev.argtypes = [P, P, P, P, C.c_int64, C.c_float, C.c_float, C.c_float,
+                                   C.c_float, P]
+    L.qym_mlp_train_dev.argtypes = [P, P, P, C.c_int64, P, C.c_int64, C.c_int64, C.c_int32,
+                                    C.c_float, C.c_float, P, P, C.c_size_t, P]
     L.qym_accel_workspace_bytes.argtypes = [C.c_int64, C.c_int32]
     L.qym_accel_workspace_bytes.restype = C.c_size_t
     L.qym_accel_dev.argtypes = [C.c_int64, P, P, P, C.c_double, C.c_int32, C.c_double, P,
@@ -116,7 +126,8 @@ def lib():
                  "qym_get_encounters", "qym_energy", "qym_get_stats", "qym_set_mlp", "qym_shape",
                  "qym_get_stream", "qym_time_kick", "qym_autotune",
                  "qym_kepler_drift_dev", "qym_accel_dev", "qym_encounter_test_dev",
-                 "qym_energy_dev"):
+                 "qym_energy_dev", "qym_set_kepler_log", "qym_mlp_forward_dev",
+                 "qym_mlp_grad_dev", "qym_mlp_adam_dev", "qym_mlp_train_dev"):
         getattr(L, name).restype = S
     _lib = L
     return L
@@ -232,6 +243,15 @@ def qym_set_mlp(ctx, weights):
     _check(lib().qym_set_mlp(ctx, w.ctypes.data_as(C.POINTER(C.c_float)), len(w)), ctx)
 
 
+def qym_set_kepler_log(ctx, rows, cap=None):
+    """rows: CUDA float32 tensor [cap, 5] (None stops logging)."""
+    if rows is None:
+        _check(lib().qym_set_kepler_log(ctx, None, 0), ctx)
+    else:
+        cap = rows.shape[0] if cap is None else cap
+        _check(lib().qym_set_kepler_log(ctx, _ptr(rows), cap), ctx)
+
+
 def qym_last_error(ctx=None) -> str:
     s = lib().qym_last_error(ctx)
     return s.decode() if s else ""
@@ -253,13 +273,41 @@ def _stream(stream):
     return torch.cuda.current_stream().cuda_stream
 
 
-def qym_kepler_drift_dev(n, q0, v0, q1, v1, mu, dt, solver=0, guess=0, x_guess=None,
-                         max_iter=50, x_out=None, iters=None, status=None, stream=None):
-    """Tensors are CUDA float64 [3, n] (x_guess float32 [n], x_out float64 [n],
-    iters / status int32)."""
+def qym_kepler_drift_dev(n, q0, v0, q1, v1, mu, dt, solver=0, guess=0, mlp_w=None,
+                         max_iter=50, x_out=None, x0_out=None, iters=None, log_rows=None,
+                         status=None, stream=None):
+    """Tensors are CUDA float64 [3, n] (mlp_w float32 [QYM_MLP_NW], x_out and
+    x0_out float64 [n], iters / status int32, log_rows float32 [n, 5])."""
     _check(lib().qym_kepler_drift_dev(n, _ptr(q0), _ptr(v0), _ptr(q1), _ptr(v1), mu, dt, solver,
-                                      guess, _ptr(x_guess), max_iter, _ptr(x_out), _ptr(iters),
-                                      _ptr(status), _stream(stream)))
+                                      guess, _ptr(mlp_w), max_iter, _ptr(x_out), _ptr(x0_out),
+                                      _ptr(iters), _ptr(log_rows), _ptr(status), _stream(stream)))
+
+
+def qym_mlp_workspace_bytes() -> int:
+    return int(lib().qym_mlp_workspace_bytes())
+
+
+def qym_mlp_forward_dev(n, w, u, y, stream=None):
+    """w float32 [QYM_MLP_NW], u float32 [n, 4], y float32 [n] (CUDA)."""
+    _check(lib().qym_mlp_forward_dev(n, _ptr(w), _ptr(u), _ptr(y), _stream(stream)))
+
+
+def qym_mlp_grad_dev(n, w, rows, grad, loss, work, work_bytes=None, stream=None):
+    wb = work.numel() * work.element_size() if work_bytes is None else work_bytes
+    _check(lib().qym_mlp_grad_dev(n, _ptr(w), _ptr(rows), _ptr(grad), _ptr(loss), _ptr(work), wb,
+                                  _stream(stream)))
+
+
+def qym_mlp_adam_dev(w, m, v, grad, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().qym_mlp_adam_dev(_ptr(w), _ptr(m), _ptr(v), _ptr(grad), t, lr, beta1, beta2, eps,
+                                  _stream(stream)))
+
+
+def qym_mlp_train_dev(w, m, v, t0, rows, n, batch, epochs, lr, lr_final, losses, work,
+                      work_bytes=None, stream=None):
+    wb = work.numel() * work.element_size() if work_bytes is None else work_bytes
+    _check(lib().qym_mlp_train_dev(_ptr(w), _ptr(m), _ptr(v), t0, _ptr(rows), n, batch, epochs, lr,
+                                   lr_final, _ptr(losses), _ptr(work), wb, _stream(stream)))
 
 
 def qym_accel_workspace_bytes(rows, prec) -> int:
@@ -329,6 +377,12 @@ class Simulation:
 
     def stats(self):
         return qym_get_stats(self.ctx).as_dict()
+
+    def set_mlp(self, weights):
+        qym_set_mlp(self.ctx, weights)
+
+    def set_kepler_log(self, rows, cap=None):
+        qym_set_kepler_log(self.ctx, rows, cap)
 
     def close(self):
         if self.ctx:

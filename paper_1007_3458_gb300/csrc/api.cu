@@ -47,6 +47,13 @@ struct qym_ctx {
     int64_t n_heavy = 0;    // heavy bodies over all systems
     int64_t launches = 0;   // kernels enqueued by the current qym_step call
     int64_t graph_launches = 0;  // kernels in one replay of the step graph
+    // learned Kepler guess and the log of Kepler solves
+    float *mlp_w = nullptr;      // [QYM_MLP_NW] device weights (arena)
+    bool mlp_set = false;
+    float *klog = nullptr;       // caller's device rows [klog_cap][5], or NULL
+    int64_t klog_cap = 0;
+    unsigned long long klog_steps = 0;   // steps logged so far
+    unsigned long long *klog_base = nullptr;  // device copy of klog_steps (arena)
 };
 
 #define FAIL(ctx, code, msg)                         \
@@ -167,6 +174,8 @@ static void carve_all(qym_ctx *c, Carver &k) {
     c->epart = k.take<double>(c->neitems);
     c->E = k.take<double>(d.nsys);
     c->mt = k.take<double>(d.nsys);
+    c->mlp_w = k.take<float>(QYM_MLP_NW);
+    c->klog_base = k.take<unsigned long long>(1);
 }
 
 static void soa_from_aos(const double *aos, int64_t R, std::vector<double> &out) {
@@ -437,8 +446,15 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last) {
     ka.ld = d.rows;
     ka.dt = tau;
     ka.solver = p.solver;
-    ka.guess = p.guess == QYM_GUESS_MLP ? QYM_GUESS_STANDARD : p.guess;
+    ka.guess = p.guess;
+    ka.mlp_w = p.guess == QYM_GUESS_MLP ? c->mlp_w : nullptr;
     ka.max_iter = p.max_kepler_iter;
+    if (c->klog) {
+        ka.log = c->klog;
+        ka.log_cap = c->klog_cap;
+        ka.log_base = c->klog_base;
+        ka.log_step = d.ctr + C_STEP;
+    }
     ka.status = d.status;
     ka.iter_sum = d.ctr + C_SUM_KITER;
     ka.sys_of = d.sys_of;
@@ -515,6 +531,11 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
         std::memset(&c->stats, 0, sizeof(c->stats));
         return QYM_OK;
     }
+    if (p.guess == QYM_GUESS_MLP && !c->mlp_set)
+        FAIL(c, QYM_EINVAL, "qym_step: QYM_GUESS_MLP needs a network (qym_set_mlp)");
+    if (c->klog)
+        CK(c, cudaMemcpyAsync(c->klog_base, &c->klog_steps, sizeof(c->klog_steps),
+                              cudaMemcpyHostToDevice, st));
     c->launches = 0;
     if (!c->amag_valid) {
         // |a| of the current positions for the first crude search's kick bound
@@ -559,6 +580,7 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
         }
     }
     CK(c, enqueue_step(c, tau, true));
+    if (c->klog) c->klog_steps += (unsigned long long)nsteps;
     return collect(c, nsteps);
 }
 
@@ -643,8 +665,32 @@ extern "C" qym_status qym_get_encounters(qym_ctx *c, int64_t *recs, int64_t cap,
 }
 
 extern "C" qym_status qym_set_mlp(qym_ctx *c, const float *weights, int64_t n) {
-    if (!c || !weights || n != 4615) FAIL(c, QYM_EINVAL, "qym_set_mlp: expected 4615 weights");
-    FAIL(c, QYM_EINVAL, "qym_set_mlp: the learned guess is not available in this build");
+    if (!c) FAIL(nullptr, QYM_EINVAL, "qym_set_mlp: NULL context");
+    if (!weights || n != QYM_MLP_NW)
+        FAIL(c, QYM_EINVAL, "qym_set_mlp: expected " + std::to_string(QYM_MLP_NW) + " weights");
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(weights[i])) FAIL(c, QYM_EINVAL, "qym_set_mlp: non-finite weight");
+    for (int i = 0; i < 4; ++i)
+        if (!(weights[QYM_MLP_NW - 6 + i] > 0.0f)) FAIL(c, QYM_EINVAL, "qym_set_mlp: feature std must be > 0");
+    CK(c, cudaSetDevice(c->p.device));
+    CK(c, cudaMemcpyAsync(c->mlp_w, weights, sizeof(float) * QYM_MLP_NW, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->mlp_set = true;
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_set_kepler_log(qym_ctx *c, float *rows, int64_t cap) {
+    if (!c) FAIL(nullptr, QYM_EINVAL, "qym_set_kepler_log: NULL context");
+    if (cap < 0 || (cap > 0 && !rows)) FAIL(c, QYM_EINVAL, "qym_set_kepler_log: bad buffer");
+    c->klog = cap > 0 ? rows : nullptr;
+    c->klog_cap = cap;
+    c->klog_steps = 0;
+    // the step graph holds the log pointers: capture again
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return QYM_OK;
 }
 
 extern "C" const char *qym_last_error(const qym_ctx *c) {
@@ -654,14 +700,20 @@ extern "C" const char *qym_last_error(const qym_ctx *c) {
 // ------------------------------------------------------------------ device-level calls
 extern "C" qym_status qym_kepler_drift_dev(int64_t n, const double *q0, const double *v0, double *q1,
                                            double *v1, double mu, double dt, int32_t solver,
-                                           int32_t guess, const float *x_guess, int32_t max_iter,
-                                           double *x_out, int32_t *iters, int32_t *status,
-                                           void *stream) {
+                                           int32_t guess, const float *mlp_w, int32_t max_iter,
+                                           double *x_out, double *x0_out, int32_t *iters,
+                                           float *log_rows, int32_t *status, void *stream) {
     if (n < 0 || !(mu > 0.0) || max_iter < 1 || !std::isfinite(dt))
         FAIL(nullptr, QYM_EINVAL, "qym_kepler_drift_dev: bad n, mu, dt or max_iter");
+    if (solver != QYM_SOLVER_LAGUERRE && solver != QYM_SOLVER_NEWTON)
+        FAIL(nullptr, QYM_EINVAL, "qym_kepler_drift_dev: solver");
+    if (guess < QYM_GUESS_STANDARD || guess > QYM_GUESS_MLP)
+        FAIL(nullptr, QYM_EINVAL, "qym_kepler_drift_dev: guess");
     if (n == 0) return QYM_OK;
     if (!q0 || !v0 || !q1 || !v1) FAIL(nullptr, QYM_EINVAL, "qym_kepler_drift_dev: NULL array");
-    if (guess == QYM_GUESS_MLP && !x_guess) FAIL(nullptr, QYM_EINVAL, "qym_kepler_drift_dev: x_guess required");
+    if (guess == QYM_GUESS_MLP && !mlp_w) FAIL(nullptr, QYM_EINVAL, "qym_kepler_drift_dev: mlp_w required");
+    if (mlp_w && ((uintptr_t)mlp_w & 15))
+        FAIL(nullptr, QYM_EINVAL, "qym_kepler_drift_dev: mlp_w must be 16-byte aligned");
     KeplerArgs a;
     std::memset(&a, 0, sizeof(a));
     a.n = n;
@@ -672,11 +724,63 @@ extern "C" qym_status qym_kepler_drift_dev(int64_t n, const double *q0, const do
     a.solver = solver;
     a.guess = guess;
     a.max_iter = max_iter;
-    a.x_guess = x_guess;
+    a.mlp_w = guess == QYM_GUESS_MLP ? mlp_w : nullptr;
     a.x_out = x_out;
+    a.x0_out = x0_out;
     a.iters = iters;
     a.status = status;
+    a.log = log_rows;
+    a.log_cap = log_rows ? n : 0;
     CK(nullptr, launch_kepler(a, (cudaStream_t)stream));
+    return QYM_OK;
+}
+
+// ------------------------------------------------------------------ learned guess
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+extern "C" size_t qym_mlp_workspace_bytes(void) { return mlp_workspace_bytes(); }
+
+extern "C" qym_status qym_mlp_forward_dev(int64_t n, const float *w, const float *u, float *y,
+                                          void *stream) {
+    if (n < 0) FAIL(nullptr, QYM_EINVAL, "qym_mlp_forward_dev: n < 0");
+    if (n == 0) return QYM_OK;
+    if (!w || !u || !y || !aligned16(w) || !aligned16(u))
+        FAIL(nullptr, QYM_EINVAL, "qym_mlp_forward_dev: NULL or unaligned array");
+    CK(nullptr, launch_mlp_forward(n, w, u, y, (cudaStream_t)stream));
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_mlp_grad_dev(int64_t n, const float *w, const float *rows, float *grad,
+                                       float *loss, void *work, size_t work_bytes, void *stream) {
+    if (n < 1) FAIL(nullptr, QYM_EINVAL, "qym_mlp_grad_dev: n < 1");
+    if (!w || !rows || !grad || !work || !aligned16(w))
+        FAIL(nullptr, QYM_EINVAL, "qym_mlp_grad_dev: NULL or unaligned array");
+    if (work_bytes < mlp_workspace_bytes()) FAIL(nullptr, QYM_EINVAL, "qym_mlp_grad_dev: workspace too small");
+    CK(nullptr, launch_mlp_grad(n, w, rows, grad, loss, work, (cudaStream_t)stream));
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_mlp_adam_dev(float *w, float *m, float *v, const float *grad, int64_t t,
+                                       float lr, float beta1, float beta2, float eps, void *stream) {
+    if (!w || !m || !v || !grad) FAIL(nullptr, QYM_EINVAL, "qym_mlp_adam_dev: NULL array");
+    if (t < 1 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
+        !(eps > 0.0f))
+        FAIL(nullptr, QYM_EINVAL, "qym_mlp_adam_dev: bad t, lr, betas or eps");
+    CK(nullptr, launch_mlp_adam(w, m, v, grad, t, lr, beta1, beta2, eps, (cudaStream_t)stream));
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_mlp_train_dev(float *w, float *m, float *v, int64_t t0, const float *rows,
+                                        int64_t n, int64_t batch, int32_t epochs, float lr,
+                                        float lr_final, float *losses, void *work, size_t work_bytes,
+                                        void *stream) {
+    if (!w || !m || !v || !rows || !work || !aligned16(w))
+        FAIL(nullptr, QYM_EINVAL, "qym_mlp_train_dev: NULL or unaligned array");
+    if (n < 1 || batch < 1 || epochs < 0 || t0 < 0 || !(lr >= 0.0f) || !(lr_final >= 0.0f))
+        FAIL(nullptr, QYM_EINVAL, "qym_mlp_train_dev: bad n, batch, epochs, t0 or learning rate");
+    if (work_bytes < mlp_workspace_bytes()) FAIL(nullptr, QYM_EINVAL, "qym_mlp_train_dev: workspace too small");
+    CK(nullptr, launch_mlp_train(w, m, v, t0, rows, n, batch, epochs, lr, lr_final, losses, work,
+                                 (cudaStream_t)stream));
     return QYM_OK;
 }
 

@@ -5,7 +5,14 @@
 // One thread per body, FP64 throughout. Structure-of-arrays loads are
 // coalesced; q0, v0 are kept and the result goes to separate buffers because
 // the encounter test needs both ends of the step (Sec. 2.3 item 4).
-#include "qym_internal.cuh"
+//
+// With the learned guess (MLP = true) each warp first evaluates the guess
+// network for its 32 bodies on the tensor cores (mlp.cuh); the iteration then
+// starts from x_std (1 + sigma t) instead of x_std = sqrt(mu) dt / r0 for the
+// bodies on bound orbits (the network's domain). With a log buffer every
+// solve on a bound orbit also writes its training row (u1..u4, t) with
+// t = (x / x_std - 1) / sigma at the converged root x.
+#include "mlp.cuh"
 
 namespace qym {
 
@@ -50,23 +57,45 @@ struct KepEq {
     }
 };
 
+template <bool MLP>
 __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int iters = 0;
-    if (k < a.n) {
-        int64_t r = a.rows ? a.rows[k] : k;
-        const int64_t ld = a.ld;
-        double qx = a.q0[r], qy = a.q0[ld + r], qz = a.q0[2 * ld + r];
-        double vx = a.v0[r], vy = a.v0[ld + r], vz = a.v0[2 * ld + r];
-        const double mu = a.sys_of ? a.G * a.m[a.offsets[a.sys_of[r]]] : a.mu;
-        const double dt = a.dt;
-        const double sqmu = sqrt(mu);
-        double r0 = sqrt(qx * qx + qy * qy + qz * qz);
+    const bool act = k < a.n;
+    const int64_t r = act ? (a.rows ? a.rows[k] : k) : 0;
+    const int64_t ld = a.ld;
+    double qx = 0.0, qy = 0.0, qz = 0.0, vx = 0.0, vy = 0.0, vz = 0.0, mu = 1.0;
+    if (act) {
+        qx = a.q0[r]; qy = a.q0[ld + r]; qz = a.q0[2 * ld + r];
+        vx = a.v0[r]; vy = a.v0[ld + r]; vz = a.v0[2 * ld + r];
+        mu = a.sys_of ? a.G * a.m[a.offsets[a.sys_of[r]]] : a.mu;
+    }
+    const double dt = a.dt;
+    const double sqmu = sqrt(mu);
+    const double r0 = sqrt(qx * qx + qy * qy + qz * qz);
+    const bool feat = act && r0 > 0.0 && dt != 0.0;
+    float u[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    double sigma = 0.0;
+    bool bound = false;  // in the learned guess's domain
+    if (feat && (MLP || a.log)) bound = mlp::features(qx, qy, qz, vx, vy, vz, r0, mu, dt, u, sigma);
+    double x_mlp = 0.0;
+    bool have_mlp = false;
+    if (MLP) {
+        // every lane of the warp takes part, active or not
+        float fn[4];
+        mlp::normalise(a.mlp_w, u, fn);
+        const float y = mlp::warp_forward(a.mlp_w, fn);
+        const float tn = a.mlp_w[mlp::OM] + a.mlp_w[mlp::OSD] * y;
+        x_mlp = sqmu * dt / r0 * (1.0 + sigma * (double)tn);
+        have_mlp = bound && isfinite(x_mlp);
+    }
+    if (act) {
         if (r0 == 0.0) {
             // a star row (held at Q = v = 0): stays at the origin
             a.q1[r] = 0.0; a.q1[ld + r] = 0.0; a.q1[2 * ld + r] = 0.0;
             a.v1[r] = 0.0; a.v1[ld + r] = 0.0; a.v1[2 * ld + r] = 0.0;
             if (a.x_out) a.x_out[k] = 0.0;
+            if (a.x0_out) a.x0_out[k] = 0.0;
             if (a.iters) a.iters[k] = 0;
             goto done;
         }
@@ -81,12 +110,14 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
         double x;
         if (a.guess == QYM_GUESS_R0)
             x = r0;
-        else if (a.guess == QYM_GUESS_MLP && a.x_guess)
-            x = (double)a.x_guess[k];
+        else if (MLP && have_mlp)
+            x = x_mlp;
         else
             x = eq.sqmu_dt / r0;
+        if (a.x0_out) a.x0_out[k] = x;
         int solver = a.solver;
         bool conv = false;
+        bool cs_at_x = false;  // C, S hold the Stumpff values at the final x
         double C = 0.5, S = 1.0 / 6.0;
         // Root bracket: F(0) = -sqrt(mu) dt and F' = r >= r_p (periapsis
         // distance), so the root lies between 0 and sqrt(mu) dt / r_p; for an
@@ -113,7 +144,7 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
         // Laguerre from the standard guess if the first did not converge
         for (int pass = 0; pass < 2 && !conv; ++pass) {
             if (pass == 1) {
-                if (a.guess != QYM_GUESS_MLP) break;
+                if (!MLP) break;
                 x = eq.sqmu_dt / r0;
                 solver = QYM_SOLVER_LAGUERRE;
                 lo = lo0;
@@ -136,7 +167,7 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
                 double x2 = x * x;
                 double scale = fabs(eq.sqmu_dt) + fabs(eq.sig * x2 * C) +
                                fabs(eq.b * x2 * x * S) + r0 * fabs(x);
-                if (fabs(F) <= 1e-14 * scale) { --iters; conv = true; break; }
+                if (fabs(F) <= 1e-14 * scale) { --iters; conv = true; cs_at_x = true; break; }
                 double dx;
                 if (solver == QYM_SOLVER_LAGUERRE) {
                     // Laguerre, n = 5: dx = n F / (F' + sgn(F') sqrt|(n-1)^2 F'^2 - n(n-1) F F''|),
@@ -163,10 +194,12 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
                 }
             }
         }
-        // f and g functions at the root (Appendix); r before fdot, gdot
+        // f and g functions at the root (Appendix); r before fdot, gdot. The
+        // residual test already evaluated C, S at this x; a step-size exit
+        // moved x after the last evaluation
         double x2 = x * x;
         double y = eq.alpha * x2;
-        stumpff(y, C, S);
+        if (!cs_at_x) stumpff(y, C, S);
         double f = 1.0 - x2 / r0 * C;
         double g = dt - x2 * x / sqmu * S;
         double nx = f * qx + g * vx, ny = f * qy + g * vy, nz = f * qz + g * vz;
@@ -178,6 +211,17 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
         a.v1[r] = ux; a.v1[ld + r] = uy; a.v1[2 * ld + r] = uz;
         if (a.x_out) a.x_out[k] = x;
         if (a.iters) a.iters[k] = iters;
+        if (a.log && bound) {
+            // training row of this solve: slot (steps logged so far) * n + k
+            const int64_t base = a.log_step ? (int64_t)(*a.log_base + *a.log_step) * a.n : 0;
+            const int64_t slot = base + k;
+            if (slot < a.log_cap) {
+                const double t = (x * r0 / eq.sqmu_dt - 1.0) / sigma;
+                float *row = a.log + 5 * slot;
+                row[0] = u[0]; row[1] = u[1]; row[2] = u[2]; row[3] = u[3];
+                row[4] = (float)t;
+            }
+        }
         if (a.status) {
             int bits = 0;
             if (!conv) bits |= QYM_ST_KEPLER_NOCONV;
@@ -201,7 +245,10 @@ cudaError_t launch_kepler(const KeplerArgs &a, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
     int threads = 256;
     int64_t blocks = (a.n + threads - 1) / threads;
-    k_kepler<<<(unsigned)blocks, threads, 0, st>>>(a);
+    if (a.guess == QYM_GUESS_MLP && a.mlp_w)
+        k_kepler<true><<<(unsigned)blocks, threads, 0, st>>>(a);
+    else
+        k_kepler<false><<<(unsigned)blocks, threads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

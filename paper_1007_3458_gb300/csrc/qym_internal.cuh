@@ -151,8 +151,14 @@ struct KeplerArgs {
     const int64_t *rows;   // optional row map: body k is row rows[k]; NULL = identity
     double mu, dt;
     int32_t solver, guess, max_iter;
-    const float *x_guess;  // [n] or NULL
+    const float *mlp_w;    // guess network weights (QYM_GUESS_MLP) or NULL
     double *x_out;         // [n] or NULL
+    double *x0_out;        // [n] starting guesses, or NULL
+    // training rows (u1..u4, t) [log_cap][5], or NULL; row of body k:
+    // (*log_base + *log_step) * n + k, or k when log_step is NULL
+    float *log;
+    int64_t log_cap;
+    const unsigned long long *log_base, *log_step;
     int32_t *iters;        // [n] or NULL
     int32_t *status;       // or NULL
     unsigned long long *iter_sum;  // or NULL
@@ -163,6 +169,17 @@ struct KeplerArgs {
     double G;
 };
 cudaError_t launch_kepler(const KeplerArgs &a, cudaStream_t st);
+
+// mlp.cu: learned Kepler guess, inference and training
+size_t mlp_workspace_bytes();
+cudaError_t launch_mlp_forward(int64_t n, const float *w, const float *u, float *y, cudaStream_t st);
+cudaError_t launch_mlp_grad(int64_t n, const float *w, const float *rows, float *grad, float *loss,
+                            void *work, cudaStream_t st);
+cudaError_t launch_mlp_adam(float *w, float *m, float *v, const float *grad, int64_t t, float lr,
+                            float beta1, float beta2, float eps, cudaStream_t st);
+cudaError_t launch_mlp_train(float *w, float *m, float *v, int64_t t0, const float *rows, int64_t n,
+                             int64_t batch, int32_t epochs, float lr, float lr_final, float *losses,
+                             void *work, cudaStream_t st);
 
 // step kernels (step.cu)
 cudaError_t launch_momentum(const Dev &d, cudaStream_t st);

@@ -55,6 +55,30 @@ def test_argument_checks_without_gpu(lib):
         q.qym_init(p, [0, 2], [1.0, 1e-3], np.zeros((2, 3)), np.zeros((2, 3)))
     assert e.value.status == q.QYM_EINVAL
     assert lib.qym_kepler_drift_dev(-1, None, None, None, None, 1.0, 1.0, 0, 0, None, 50, None,
-                                    None, None, None) == q.QYM_EINVAL
+                                    None, None, None, None, None) == q.QYM_EINVAL
+    # the learned guess needs its weights; an unknown guess or solver is refused
+    assert lib.qym_kepler_drift_dev(4, None, None, None, None, 1.0, 1.0, 0, q.QYM_GUESS_MLP, None,
+                                    50, None, None, None, None, None, None) == q.QYM_EINVAL
+    assert lib.qym_kepler_drift_dev(4, None, None, None, None, 1.0, 1.0, 0, 7, None, 50, None,
+                                    None, None, None, None, None) == q.QYM_EINVAL
+    assert lib.qym_mlp_workspace_bytes() >= 256 * q.QYM_MLP_NW * 4
+    assert lib.qym_mlp_forward_dev(-1, None, None, None, None) == q.QYM_EINVAL
+    assert lib.qym_mlp_grad_dev(0, None, None, None, None, None, 0, None) == q.QYM_EINVAL
+    assert lib.qym_mlp_adam_dev(None, None, None, None, 1, 1e-3, 0.9, 0.999, 1e-8, None) == q.QYM_EINVAL
+    assert lib.qym_mlp_train_dev(None, None, None, 0, None, 10, 4, 1, 1e-3, 1e-4, None, None, 0,
+                                 None) == q.QYM_EINVAL
+    assert lib.qym_set_mlp(None, None, q.QYM_MLP_NW) == q.QYM_EINVAL
+    assert lib.qym_set_kepler_log(None, None, 0) == q.QYM_EINVAL
     assert lib.qym_accel_workspace_bytes(1, 1) == 0
     assert lib.qym_accel_workspace_bytes(16385, 1) > 16385 * 3 * 8
+
+
+def test_mlp_layout_constants_agree():
+    """The guess network's weight count is the same in the header, the
+    binding, the oracle and the input generators."""
+    import re
+    from oracle import mlp as M
+    from paper_1007_3458_gb300 import workloads as W
+    hdr = open(q.HEADER).read()
+    nw = int(re.search(r"#define QYM_MLP_NW (\d+)", hdr).group(1))
+    assert nw == q.QYM_MLP_NW == M.NW == W.MLP_NW == 4 * 64 + 64 + 64 * 64 + 64 + 64 + 1 + 10

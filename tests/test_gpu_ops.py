@@ -50,7 +50,8 @@ def _kepler_gpu(torch, qq, vv, mu, dt, solver=0, guess=0, max_iter=50):
     x = torch.empty(n, dtype=torch.float64, device="cuda")
     it = torch.empty(n, dtype=torch.int32, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
-    q.qym_kepler_drift_dev(n, q0, v0, q1, v1, mu, dt, solver, guess, None, max_iter, x, it, st)
+    q.qym_kepler_drift_dev(n, q0, v0, q1, v1, mu, dt, solver, guess, None, max_iter, x_out=x,
+                           iters=it, status=st)
     torch.cuda.synchronize()
     return _aos(q1), _aos(v1), x.cpu().numpy(), it.cpu().numpy(), int(st.item())
 

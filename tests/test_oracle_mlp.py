@@ -66,6 +66,10 @@ def test_features_closed_forms():
     u2 = M.features(q2, v2, dt, 1.0)
     assert np.isclose(u2[0, 0], 1.5 * math.sqrt(2.0), rtol=1e-15)
     assert u2[0, 3] == 0.0
+    # the learned guess is used on bound orbits only: x_std elsewhere
+    assert M.bound(q, v, 1.0).all() and not M.bound(q2, v2, 1.0).any()
+    w = W.mlp_init(0, u, np.zeros(len(u)))
+    assert M.guess(w, q2, v2, dt, 1.0)[0] == M.x_std(q2, dt, 1.0)[0]
 
 
 def test_target_circular_and_short_step_limit(oracle):
@@ -143,6 +147,7 @@ def test_adam_closed_form():
     exp = w - 1e-3 * g / (np.abs(g) + 1e-8)
     exp[M.NW - M.N_FROZEN:] = w[M.NW - M.N_FROZEN:]
     assert np.allclose(w1, exp, rtol=0, atol=1e-15)
+    assert np.all(m1[M.NW - M.N_FROZEN:] == 0) and np.all(v1[M.NW - M.N_FROZEN:] == 0)
     # a constant gradient keeps the bias-corrected moments at g and g^2
     w2, _, _ = M.adam(w1, m1, v1, g, 2, 1e-3)
     assert np.allclose(w2 - w1, exp - w, rtol=0, atol=1e-15)
