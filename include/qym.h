@@ -260,6 +260,14 @@ qym_status qym_kepler_drift_dev(int64_t n, const double *q0, const double *v0, d
                                 double *x0_out, int32_t *iters, float *log_rows, int32_t *status,
                                 void *stream);
 
+/* The transition function of the hybrid split (Sec. 2.1) as the Hermite
+ * sub-integrator evaluates it: K(y) = sin(pi y / 2) for 0 < y < 1 (0 below,
+ * 1 above), y = 1.1 s / r_crit - 0.1, with its first and second derivatives
+ * with respect to s, for n distances s (device float64[n]) into device
+ * float64 K[n], Kp[n], Kpp[n]. Returns QYM_EINVAL for n < 0 or r_crit <= 0. */
+qym_status qym_transition_dev(int64_t n, const double *s, double r_crit, double *K, double *Kp,
+                              double *Kpp, void *stream);
+
 /* The guess network's normalised output y for raw features u (device
  * float32[n][4], 16-byte aligned) into device float32 y[n]; w as in
  * qym_set_mlp (device, 16-byte aligned). n = 0 is a no-op. */

@@ -99,6 +99,7 @@ def lib():
     L.qym_kepler_drift_dev.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_int32,
                                        C.c_int32, P, C.c_int32, P, P, P, P, P, P]
     L.qym_set_kepler_log.argtypes = [P, P, C.c_int64]
+    L.qym_transition_dev.argtypes = [C.c_int64, P, C.c_double, P, P, P, P]
     L.qym_mlp_workspace_bytes.argtypes = []
     L.qym_mlp_workspace_bytes.restype = C.c_size_t
     L.qym_mlp_forward_dev.argtypes = [C.c_int64, P, P, P, P]
@@ -127,7 +128,8 @@ def lib():
                  "qym_get_stream", "qym_time_kick", "qym_autotune",
                  "qym_kepler_drift_dev", "qym_accel_dev", "qym_encounter_test_dev",
                  "qym_energy_dev", "qym_set_kepler_log", "qym_mlp_forward_dev",
-                 "qym_mlp_grad_dev", "qym_mlp_adam_dev", "qym_mlp_train_dev"):
+                 "qym_mlp_grad_dev", "qym_mlp_adam_dev", "qym_mlp_train_dev",
+                 "qym_transition_dev"):
         getattr(L, name).restype = S
     _lib = L
     return L
@@ -281,6 +283,12 @@ def qym_kepler_drift_dev(n, q0, v0, q1, v1, mu, dt, solver=0, guess=0, mlp_w=Non
     _check(lib().qym_kepler_drift_dev(n, _ptr(q0), _ptr(v0), _ptr(q1), _ptr(v1), mu, dt, solver,
                                       guess, _ptr(mlp_w), max_iter, _ptr(x_out), _ptr(x0_out),
                                       _ptr(iters), _ptr(log_rows), _ptr(status), _stream(stream)))
+
+
+def qym_transition_dev(n, s, r_crit, K, Kp, Kpp, stream=None):
+    """CUDA float64 tensors [n]: K(s), K'(s), K''(s) of the transition function."""
+    _check(lib().qym_transition_dev(n, _ptr(s), r_crit, _ptr(K), _ptr(Kp), _ptr(Kpp),
+                                    _stream(stream)))
 
 
 def qym_mlp_workspace_bytes() -> int:

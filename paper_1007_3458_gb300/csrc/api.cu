@@ -735,6 +735,15 @@ extern "C" qym_status qym_kepler_drift_dev(int64_t n, const double *q0, const do
     return QYM_OK;
 }
 
+extern "C" qym_status qym_transition_dev(int64_t n, const double *s, double r_crit, double *K,
+                                         double *Kp, double *Kpp, void *stream) {
+    if (n < 0 || !(r_crit > 0.0)) FAIL(nullptr, QYM_EINVAL, "qym_transition_dev: bad n or r_crit");
+    if (n == 0) return QYM_OK;
+    if (!s || !K || !Kp || !Kpp) FAIL(nullptr, QYM_EINVAL, "qym_transition_dev: NULL array");
+    CK(nullptr, launch_transition(n, s, r_crit, K, Kp, Kpp, (cudaStream_t)stream));
+    return QYM_OK;
+}
+
 // ------------------------------------------------------------------ learned guess
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 

@@ -23,23 +23,80 @@ namespace qym {
 constexpr int HCAP = 512;       // members per set held in shared memory
 constexpr int HTHREADS = 256;
 
-// transition function of Sec. 2.1 with y = 1.1 s / r_crit - 0.1, and its
-// first and second derivatives with respect to s
-__device__ __forceinline__ void transition(double s, double rc, double &K, double &Kp,
+// sin and cos of (pi/2) y for y in [0, 1]: y > 1/2 is folded onto 1 - y
+// (sin and cos swap), so the argument w = (pi/2) y' stays in [0, pi/4], where
+// the Taylor series of sin to w^15 and of cos to w^16 leave truncation errors
+// below 7e-17 and 3e-18 (the next terms, w^17/17! and w^18/18!, at pi/4).
+__device__ __forceinline__ void sincos_half_pi(double y, double &sn, double &cs) {
+    const bool fold = y > 0.5;
+    const double w = 1.5707963267948966 * (fold ? 1.0 - y : y);
+    const double w2 = w * w;
+    double ps = -1.0 / 1307674368000.0;        // -1/15!
+    ps = fma(ps, w2, 1.0 / 6227020800.0);      // +1/13!
+    ps = fma(ps, w2, -1.0 / 39916800.0);       // -1/11!
+    ps = fma(ps, w2, 1.0 / 362880.0);          // +1/9!
+    ps = fma(ps, w2, -1.0 / 5040.0);           // -1/7!
+    ps = fma(ps, w2, 1.0 / 120.0);             // +1/5!
+    ps = fma(ps, w2, -1.0 / 6.0);              // -1/3!
+    ps = fma(ps, w2, 1.0);
+    const double sw = w * ps;
+    double pc = 1.0 / 20922789888000.0;        // +1/16!
+    pc = fma(pc, w2, -1.0 / 87178291200.0);    // -1/14!
+    pc = fma(pc, w2, 1.0 / 479001600.0);       // +1/12!
+    pc = fma(pc, w2, -1.0 / 3628800.0);        // -1/10!
+    pc = fma(pc, w2, 1.0 / 40320.0);           // +1/8!
+    pc = fma(pc, w2, -1.0 / 720.0);            // -1/6!
+    pc = fma(pc, w2, 1.0 / 24.0);              // +1/4!
+    pc = fma(pc, w2, -0.5);                    // -1/2!
+    pc = fma(pc, w2, 1.0);
+    sn = fold ? pc : sw;
+    cs = fold ? sw : pc;
+}
+
+// Constants of the transition function of one set: K(y) = sin(pi y / 2) with
+// y = 1.1 s / r_crit - 0.1 (Sec. 2.1), so y = a s - 0.1 and dy/ds = a.
+struct TransC {
+    double rc2;  // r_crit^2: K = 1 (and K' = K'' = 0) beyond
+    double a;    // 1.1 / r_crit
+    double c;    // (pi / 2) a: K' = c cos, K'' = -c^2 sin
+    __device__ __forceinline__ explicit TransC(double rc)
+        : rc2(rc * rc), a(1.1 / rc), c(0.5 * kPi * (1.1 / rc)) {}
+};
+
+// K and its first and second derivatives with respect to s
+__device__ __forceinline__ void transition(double s, const TransC &tc, double &K, double &Kp,
                                            double &Kpp) {
-    double y = 1.1 * s / rc - 0.1;
+    const double y = tc.a * s - 0.1;
     if (y <= 0.0) {
         K = 0.0; Kp = 0.0; Kpp = 0.0;
     } else if (y >= 1.0) {
         K = 1.0; Kp = 0.0; Kpp = 0.0;
     } else {
-        double c = 0.5 * kPi * 1.1 / rc;
         double sn, cs;
-        sincospi(0.5 * y, &sn, &cs);
+        sincos_half_pi(y, sn, cs);
         K = sn;
-        Kp = c * cs;
-        Kpp = -c * c * sn;
+        Kp = tc.c * cs;
+        Kpp = -tc.c * tc.c * sn;
     }
+}
+
+__global__ void k_transition(int64_t n, const double *s, double rc, double *K, double *Kp,
+                             double *Kpp) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const TransC tc(rc);
+    double k0, k1, k2;
+    transition(s[i], tc, k0, k1, k2);
+    K[i] = k0;
+    Kp[i] = k1;
+    Kpp[i] = k2;
+}
+
+cudaError_t launch_transition(int64_t n, const double *s, double rc, double *K, double *Kp,
+                              double *Kpp, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_transition<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, s, rc, K, Kp, Kpp);
+    return cudaGetLastError();
 }
 
 struct HermSmem {
@@ -72,16 +129,16 @@ __device__ __forceinline__ HermSmem carve(void *base) {
 constexpr size_t kHermSmem = sizeof(double) * HCAP * 20 + sizeof(int32_t) * HCAP * 3;
 constexpr int KMAX = 48;
 
-// smallest k with T 2^-k <= dt_c, in [0, KMAX]
+// smallest k with T 2^-k <= dt_c, in [0, KMAX]: with T = fT 2^eT and
+// dt_c = fd 2^ed (fT, fd in [1/2, 1)), T 2^-k <= dt_c exactly when
+// k >= eT - ed + (fT > fd)
 __device__ __forceinline__ int level_of(double dt_c, double T) {
     if (!(dt_c > 0.0)) return KMAX;
-    int k = 0;
-    double d = T;
-    while (d > dt_c && k < KMAX) {
-        d *= 0.5;
-        ++k;
-    }
-    return k;
+    if (dt_c >= T) return 0;
+    int eT, ed;
+    const double fT = frexp(T, &eT), fd = frexp(dt_c, &ed);
+    const int k = eT - ed + (fT > fd ? 1 : 0);
+    return k < 0 ? 0 : (k > KMAX ? KMAX : k);
 }
 
 // Work split of a set of n members over the CTA: each member is handled by
@@ -102,19 +159,19 @@ __device__ __forceinline__ void group_sum(double *v, int cnt, int P) {
 // partial (1-K)-weighted pair acceleration of member k at the evaluation
 // point, unsmoothed (the kick used the bare separation):
 // sum_l -G m_l q_kl / q^3 [1 - K + q K'] over the partners of this lane
-__device__ void kcorr_part(const HermSmem &S, int n, int k, int l0, int P, double G, double rc,
-                           double *c) {
+__device__ void kcorr_part(const HermSmem &S, int n, int k, int l0, int P, double G,
+                           const TransC &tc, double *c) {
     c[0] = c[1] = c[2] = 0.0;
-    const double rc2 = rc * rc;
     for (int l = l0; l < n; l += P) {
         if (l == k) continue;
         double qx = S.ex[k] - S.ex[l], qy = S.ey[k] - S.ey[l], qz = S.ez[k] - S.ez[l];
         double q2 = qx * qx + qy * qy + qz * qz;
-        if (q2 >= rc2) continue;  // K = 1 beyond r_crit: no (1-K) part
-        double q = sqrt(q2);
+        if (q2 >= tc.rc2) continue;  // K = 1 beyond r_crit: no (1-K) part
+        const double qi = rsqrt(q2);
+        const double q = q2 * qi;
         double K, Kp, Kpp;
-        transition(q, rc, K, Kp, Kpp);
-        double wgt = -G * S.m[l] / (q2 * q) * (1.0 - K + q * Kp);
+        transition(q, tc, K, Kp, Kpp);
+        double wgt = -G * S.m[l] * (qi * qi * qi) * (1.0 - K + q * Kp);
         c[0] += wgt * qx;
         c[1] += wgt * qy;
         c[2] += wgt * qz;
@@ -124,34 +181,37 @@ __device__ void kcorr_part(const HermSmem &S, int n, int k, int l0, int P, doubl
 // partial Hermite acceleration and jerk of member k at the evaluation point
 // (Sec. 2.2): the star term on lane 0 of the group, the pair terms with the
 // transition bracket over this lane's partners
+// (one reciprocal square root per pair: q = q2 / sqrt(q2), 1/q^3, 1/q^2)
 __device__ void herm_part(const HermSmem &S, int n, int k, int l0, int P, double G, double m0,
-                          double rc, double eps2, double *aj) {
+                          const TransC &tc, double eps2, double *aj) {
     const double xk = S.ex[k], yk = S.ey[k], zk = S.ez[k];
     const double uk = S.eu[k], vk = S.ev[k], wk = S.ew[k];
     for (int c = 0; c < 6; ++c) aj[c] = 0.0;
     if (l0 == 0) {  // star, fixed at the origin
         double s2 = xk * xk + yk * yk + zk * zk + eps2;
-        double s = sqrt(s2);
+        double si = rsqrt(s2);
+        double si2 = si * si;
         double rv = xk * uk + yk * vk + zk * wk;
-        double c = -G * m0 / (s2 * s);
-        double t = 3.0 * rv / s2;
+        double c = -G * m0 * (si2 * si);
+        double t = 3.0 * rv * si2;
         aj[0] = c * xk; aj[1] = c * yk; aj[2] = c * zk;
         aj[3] = c * (uk - t * xk); aj[4] = c * (vk - t * yk); aj[5] = c * (wk - t * zk);
     }
-    const double rc2 = rc * rc;
     for (int l = l0; l < n; l += P) {
         if (l == k) continue;
         double qx = xk - S.ex[l], qy = yk - S.ey[l], qz = zk - S.ez[l];
         double q2 = qx * qx + qy * qy + qz * qz + eps2;
-        if (q2 >= rc2) continue;  // K = 1, K' = K'' = 0: no force, no jerk
+        if (q2 >= tc.rc2) continue;  // K = 1, K' = K'' = 0: no force, no jerk
         double px = uk - S.eu[l], py = vk - S.ev[l], pz = wk - S.ew[l];
-        double sq = sqrt(q2);
+        const double qi = rsqrt(q2);
+        const double qi2 = qi * qi;
+        const double sq = q2 * qi;
         double K, Kp, Kpp;
-        transition(sq, rc, K, Kp, Kpp);
+        transition(sq, tc, K, Kp, Kpp);
         double br = 1.0 - K + sq * Kp;
         double rvl = qx * px + qy * py + qz * pz;
-        double cl = -G * S.m[l] / (q2 * sq);
-        double tl = 3.0 * rvl / q2;
+        double cl = -G * S.m[l] * (qi2 * qi);
+        double tl = 3.0 * rvl * qi2;
         aj[0] += cl * br * qx; aj[1] += cl * br * qy; aj[2] += cl * br * qz;
         aj[3] += cl * (rvl * qx * Kpp + (px - tl * qx) * br);
         aj[4] += cl * (rvl * qy * Kpp + (py - tl * qy) * br);
@@ -227,7 +287,7 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
         __syncthreads();
         const int64_t star = d.offsets[d.sys_of[S.ids[0]]];
         const double m0 = d.m[star];
-        const double rc = d.rcrit[set];
+        const TransC tc(d.rcrit[set]);
         const double G = h.G, tau = h.tau;
         // state entering the Kepler drift (after the first kick)
         for (int k = tid; k < n; k += blockDim.x) {
@@ -245,7 +305,7 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
         for (int k0 = 0; k0 < n; k0 += NG) {
             int k = k0 + grp;
             double c[3] = {0.0, 0.0, 0.0};
-            if (k < n) kcorr_part(S, n, k, lane, P, G, rc, c);
+            if (k < n) kcorr_part(S, n, k, lane, P, G, tc, c);
             group_sum(c, 3, P);
             if (k < n && lane == 0) {
                 S.u[k] -= 0.5 * tau * c[0];
@@ -266,7 +326,7 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
         for (int k0 = 0; k0 < n; k0 += NG) {
             int k = k0 + grp;
             double aj[6] = {0, 0, 0, 0, 0, 0};
-            if (k < n) herm_part(S, n, k, lane, P, G, m0, rc, h.eps2, aj);
+            if (k < n) herm_part(S, n, k, lane, P, G, m0, tc, h.eps2, aj);
             group_sum(aj, 6, P);
             if (k < n && lane == 0) {
                 S.ax[k] = aj[0]; S.ay[k] = aj[1]; S.az[k] = aj[2];
@@ -294,9 +354,10 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
             // predict every member to tn from its own time; list the active
             for (int k = tid; k < n; k += blockDim.x) {
                 const double hs = sgn * (double)(tn - S.ti[k]) * tick;
-                S.ex[k] = S.x[k] + hs * (S.u[k] + hs * (0.5 * S.ax[k] + hs * S.jx[k] / 6.0));
-                S.ey[k] = S.y[k] + hs * (S.v[k] + hs * (0.5 * S.ay[k] + hs * S.jy[k] / 6.0));
-                S.ez[k] = S.z[k] + hs * (S.w[k] + hs * (0.5 * S.az[k] + hs * S.jz[k] / 6.0));
+                const double h6 = hs * (1.0 / 6.0);
+                S.ex[k] = S.x[k] + hs * (S.u[k] + hs * (0.5 * S.ax[k] + h6 * S.jx[k]));
+                S.ey[k] = S.y[k] + hs * (S.v[k] + hs * (0.5 * S.ay[k] + h6 * S.jy[k]));
+                S.ez[k] = S.z[k] + hs * (S.w[k] + hs * (0.5 * S.az[k] + h6 * S.jz[k]));
                 S.eu[k] = S.u[k] + hs * (S.ax[k] + 0.5 * hs * S.jx[k]);
                 S.ev[k] = S.v[k] + hs * (S.ay[k] + 0.5 * hs * S.jy[k]);
                 S.ew[k] = S.w[k] + hs * (S.az[k] + 0.5 * hs * S.jz[k]);
@@ -314,7 +375,7 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
                 const int slot = k0 + ga;
                 const int k = slot < na ? S.act[slot] : 0;
                 double a1[6] = {0, 0, 0, 0, 0, 0};
-                if (slot < na) herm_part(S, n, k, la, PA, G, m0, rc, h.eps2, a1);
+                if (slot < na) herm_part(S, n, k, la, PA, G, m0, tc, h.eps2, a1);
                 group_sum(a1, 6, PA);
                 if (slot < na && la == 0) {
                     const long long dti = 1ll << (KMAX - S.lev[k]);
@@ -324,11 +385,13 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
                     double e[3] = {S.ex[k], S.ey[k], S.ez[k]};
                     double f[3] = {S.eu[k], S.ev[k], S.ew[k]};
                     double a2[3], a3[3], xn[3], un[3];
+                    const double ih = 1.0 / hs, ih2 = ih * ih, ih3 = ih2 * ih;
+                    const double h3 = hs * hs * hs, h4 = h3 * hs;
                     for (int c = 0; c < 3; ++c) {
-                        a2[c] = (-6.0 * (a0[c] - a1[c]) - hs * (4.0 * j0[c] + 2.0 * a1[3 + c])) / (hs * hs);
-                        a3[c] = (12.0 * (a0[c] - a1[c]) + 6.0 * hs * (j0[c] + a1[3 + c])) / (hs * hs * hs);
-                        xn[c] = e[c] + hs * hs * hs * hs * (a2[c] / 24.0 + hs * a3[c] / 120.0);
-                        un[c] = f[c] + hs * hs * hs * (a2[c] / 6.0 + hs * a3[c] / 24.0);
+                        a2[c] = (-6.0 * (a0[c] - a1[c]) - hs * (4.0 * j0[c] + 2.0 * a1[3 + c])) * ih2;
+                        a3[c] = (12.0 * (a0[c] - a1[c]) + 6.0 * hs * (j0[c] + a1[3 + c])) * ih3;
+                        xn[c] = e[c] + h4 * (a2[c] * (1.0 / 24.0) + hs * a3[c] * (1.0 / 120.0));
+                        un[c] = f[c] + h3 * (a2[c] * (1.0 / 6.0) + hs * a3[c] * (1.0 / 24.0));
                         a2[c] += hs * a3[c];
                     }
                     S.x[k] = xn[0]; S.y[k] = xn[1]; S.z[k] = xn[2];
@@ -364,7 +427,7 @@ __global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
         for (int k0 = 0; k0 < n; k0 += NG) {
             int k = k0 + grp;
             double c[3] = {0.0, 0.0, 0.0};
-            if (k < n) kcorr_part(S, n, k, lane, P, G, rc, c);
+            if (k < n) kcorr_part(S, n, k, lane, P, G, tc, c);
             group_sum(c, 3, P);
             if (k < n && lane == 0) {
                 int64_t r = S.ids[k];

@@ -14,13 +14,18 @@
 // double-single difference, accurate to ~1e-7 relative even for close pairs
 // far from the star), the pair force is FP32 with rsqrt, and the FP32 tile sums
 // are folded every FOLD pairs into a float two-sum (hi, lo) accumulator that
-// is returned as a double.
+// is returned as a double. The FP32 arithmetic runs on Blackwell's packed
+// FP32x2 instructions, two j rows per instruction.
 #include "qym_internal.cuh"
 
 namespace qym {
 
 constexpr int TILE = 256;
 constexpr int FOLD = 64;
+#ifndef QYM_KICK_UNROLL
+#define QYM_KICK_UNROLL 4
+#endif
+constexpr int kPairUnroll = QYM_KICK_UNROLL;  // j pairs per unrolled step
 
 struct KickArgs {
     const int4 *items;
@@ -53,111 +58,152 @@ __device__ __forceinline__ void push_candidate(const KickArgs &a, int i, int j) 
         atomicOr(a.status, QYM_ST_CAND_OVERFLOW);
 }
 
-// pair forces of one chunk of j rows. With FLAG, each i keeps the minimum
-// over the chunk of r^2 - c_j, c_j = 2 rho_j^2 (two FP32 operations per pair,
-// no branch); since (rho_i + rho_j)^2 <= c_i + c_j, a chunk without a
-// candidate of i has that minimum >= c_i and needs no further look
+// j rows of a tile sit in shared memory in pairs (j = 2p, 2p+1), each pair as
+// four float4: (xh0, xh1, yh0, yh1), (zh0, zh1, Gm0, Gm1), (xl0, xl1, yl0,
+// yl1), (zl0, zl1, -c0, -c1). A float4's halves are float2 operands of the
+// packed FP32 instructions (FADD2 / FMUL2 / FFMA2), so one instruction serves
+// both j of a pair for an i row; the i operands are per-thread constants,
+// negated and duplicated once. Each lane computes exactly what the scalar
+// form (Q_i - Q_j, r^2, rsqrt, m r^-3, force) computes, with the sign of
+// the separation flipped: d = Q_j - Q_i, a_i += (G m_j / r^3) d.
+struct JPairs {
+    float4 *a, *b, *c, *d;
+};
+
+// Pair forces of the j pairs [p0, p1) for the IPT rows of a thread. With
+// FLAG, each i keeps the minimum over the chunk of r^2 - c_j, c_j = 2 rho_j^2
+// (no branch); since (rho_i + rho_j)^2 <= c_i + c_j, a chunk without a
+// candidate of i has that minimum >= c_i and needs no further look.
 template <int IPT, bool FLAG, bool DIAG>
-__device__ __forceinline__ void mixed_chunk(const float4 *__restrict__ s_pos,
-                                            const float4 *__restrict__ s_lo, int j0, int j1,
-                                            const float (&xh)[IPT], const float (&yh)[IPT],
-                                            const float (&zh)[IPT], const float (&xl)[IPT],
-                                            const float (&yl)[IPT], const float (&zl)[IPT],
-                                            float (&fx)[IPT], float (&fy)[IPT], float (&fz)[IPT],
-                                            float (&mind)[IPT]) {
-#pragma unroll 8
-    for (int j = j0; j < j1; ++j) {
-        const float4 p = s_pos[j];
-        const float4 l = s_lo[j];
+__device__ __forceinline__ void mixed_chunk(const JPairs &s, int p0, int p1,
+                                            const float2 (&nxh)[IPT], const float2 (&nyh)[IPT],
+                                            const float2 (&nzh)[IPT], const float2 (&nxl)[IPT],
+                                            const float2 (&nyl)[IPT], const float2 (&nzl)[IPT],
+                                            float2 (&fx)[IPT], float2 (&fy)[IPT],
+                                            float2 (&fz)[IPT], float (&mind)[IPT]) {
+#pragma unroll kPairUnroll
+    for (int p = p0; p < p1; ++p) {
+        const float4 A = s.a[p], B = s.b[p], C = s.c[p], D = s.d[p];
+        const float2 xh = make_float2(A.x, A.y), yh = make_float2(A.z, A.w);
+        const float2 zh = make_float2(B.x, B.y), gm = make_float2(B.z, B.w);
+        const float2 xl = make_float2(C.x, C.y), yl = make_float2(C.z, C.w);
+        const float2 zl = make_float2(D.x, D.y), nc = make_float2(D.z, D.w);
 #pragma unroll
         for (int k = 0; k < IPT; ++k) {
-            float dx = (xh[k] - p.x) + (xl[k] - l.x);
-            float dy = (yh[k] - p.y) + (yl[k] - l.y);
-            float dz = (zh[k] - p.z) + (zl[k] - l.z);
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            float ri = rsqrt_ftz(r2);
-            float s = (p.w * ri) * (ri * ri);
-            if (DIAG) s = (r2 > 0.0f) ? s : 0.0f;
-            fx[k] = fmaf(-s, dx, fx[k]);
-            fy[k] = fmaf(-s, dy, fy[k]);
-            fz[k] = fmaf(-s, dz, fz[k]);
-            if (FLAG) mind[k] = fminf(mind[k], r2 - l.w);
+            const float2 dx = __fadd2_rn(__fadd2_rn(xh, nxh[k]), __fadd2_rn(xl, nxl[k]));
+            const float2 dy = __fadd2_rn(__fadd2_rn(yh, nyh[k]), __fadd2_rn(yl, nyl[k]));
+            const float2 dz = __fadd2_rn(__fadd2_rn(zh, nzh[k]), __fadd2_rn(zl, nzl[k]));
+            const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            const float2 ri = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+            float2 sm = __fmul2_rn(__fmul2_rn(gm, ri), __fmul2_rn(ri, ri));
+            if (DIAG) {
+                sm.x = (r2.x > 0.0f) ? sm.x : 0.0f;
+                sm.y = (r2.y > 0.0f) ? sm.y : 0.0f;
+            }
+            fx[k] = __ffma2_rn(sm, dx, fx[k]);
+            fy[k] = __ffma2_rn(sm, dy, fy[k]);
+            fz[k] = __ffma2_rn(sm, dz, fz[k]);
+            if (FLAG) {
+                const float2 t = __fadd2_rn(r2, nc);
+                mind[k] = fminf(mind[k], fminf(t.x, t.y));
+            }
         }
     }
 }
 
-// exact pre-check of one i against a chunk (rare path): candidates (i, j),
-// i < j, with r^2 < c_i + c_j
-__device__ __forceinline__ void flag_chunk(const KickArgs &a, const float4 *s_pos, const float4 *s_lo,
-                                        int j0, int j1, int jbase, int gi, float xh, float yh,
-                                        float zh, float xl, float yl, float zl, float ci) {
-    for (int j = j0; j < j1; ++j) {
-        int gj = jbase + j;
-        if (gi >= gj) continue;
-        const float4 p = s_pos[j];
-        const float4 l = s_lo[j];
-        float dx = (xh - p.x) + (xl - l.x);
-        float dy = (yh - p.y) + (yl - l.y);
-        float dz = (zh - p.z) + (zl - l.z);
-        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (r2 < ci + l.w) push_candidate(a, gi, gj);
+// exact pre-check of one i against the j pairs [p0, p1) (rare path):
+// candidates (i, j), i < j < n, with r^2 < c_i + c_j
+__device__ __noinline__ void flag_chunk(const KickArgs &a, const JPairs &s, int p0, int p1, int n,
+                                        int jbase, int gi, float xh, float yh, float zh, float xl,
+                                        float yl, float zl, float ci) {
+    for (int p = p0; p < p1; ++p) {
+        const float4 A = s.a[p], B = s.b[p], C = s.c[p], D = s.d[p];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int j = 2 * p + e;
+            const int gj = jbase + j;
+            if (j >= n || gi >= gj) continue;
+            const float pxh = e ? A.y : A.x, pyh = e ? A.w : A.z, pzh = e ? B.y : B.x;
+            const float pxl = e ? C.y : C.x, pyl = e ? C.w : C.z, pzl = e ? D.y : D.x;
+            const float cj = -(e ? D.w : D.z);
+            float dx = (xh - pxh) + (xl - pxl);
+            float dy = (yh - pyh) + (yl - pyl);
+            float dz = (zh - pzh) + (zl - pzl);
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 < ci + cj) push_candidate(a, gi, gj);
+        }
     }
 }
 
 template <int IPT, bool FLAG>
 __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
-    __shared__ float4 s_pos[TILE];
-    __shared__ float4 s_lo[TILE];
+    __shared__ float4 s_a[TILE / 2], s_b[TILE / 2], s_c[TILE / 2], s_d[TILE / 2];
+    const JPairs sp{s_a, s_b, s_c, s_d};
     const int4 it = a.items[blockIdx.x];
     const int slot = a.slots[blockIdx.x];
-    float xh[IPT], yh[IPT], zh[IPT], xl[IPT], yl[IPT], zl[IPT], rho[IPT];
+    float rho[IPT];
+    float2 nxh[IPT], nyh[IPT], nzh[IPT], nxl[IPT], nyl[IPT], nzl[IPT];  // -Q_i, duplicated
     int gi[IPT];
     float ahx[IPT], ahy[IPT], ahz[IPT], alx[IPT], aly[IPT], alz[IPT];
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
         int i = it.x + threadIdx.x + k * blockDim.x;
         gi[k] = i;
+        // idle lane: parked far away so its arithmetic stays finite
+        float4 p = make_float4(1e18f, 1e18f, 1e18f, 0.0f), l = make_float4(0.f, 0.f, 0.f, -1e30f);
         if (i < it.y) {
-            float4 p = a.pos[i], l = a.lo[i];
-            xh[k] = p.x; yh[k] = p.y; zh[k] = p.z;
-            xl[k] = l.x; yl[k] = l.y; zl[k] = l.z; rho[k] = l.w;
-        } else {
-            // idle lane: park far away so its arithmetic stays finite
-            xh[k] = 1e18f; yh[k] = 1e18f; zh[k] = 1e18f;
-            xl[k] = yl[k] = zl[k] = 0.0f; rho[k] = -1e30f;
+            p = a.pos[i];
+            l = a.lo[i];
         }
+        rho[k] = l.w;
+        nxh[k] = make_float2(-p.x, -p.x); nyh[k] = make_float2(-p.y, -p.y);
+        nzh[k] = make_float2(-p.z, -p.z); nxl[k] = make_float2(-l.x, -l.x);
+        nyl[k] = make_float2(-l.y, -l.y); nzl[k] = make_float2(-l.z, -l.z);
         ahx[k] = ahy[k] = ahz[k] = alx[k] = aly[k] = alz[k] = 0.0f;
     }
     const int i_lo = it.x, i_hi = it.x + (int)(IPT * blockDim.x);
     for (int jt = it.z; jt < it.w; jt += TILE) {
         const int n = min(TILE, it.w - jt);
+        const int np = (n + 1) >> 1;
         __syncthreads();
-        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-            s_pos[t] = a.pos[jt + t];
-            s_lo[t] = a.lo[jt + t];
+        for (int t = threadIdx.x; t < np; t += blockDim.x) {
+            const int j0 = jt + 2 * t;
+            const float4 p0 = a.pos[j0], l0 = a.lo[j0];
+            // an odd tail is padded with a massless row far from everything
+            float4 p1 = make_float4(2e18f, 2e18f, 2e18f, 0.0f), l1 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (2 * t + 1 < n) {
+                p1 = a.pos[j0 + 1];
+                l1 = a.lo[j0 + 1];
+            }
+            s_a[t] = make_float4(p0.x, p1.x, p0.y, p1.y);
+            s_b[t] = make_float4(p0.z, p1.z, p0.w, p1.w);
+            s_c[t] = make_float4(l0.x, l1.x, l0.y, l1.y);
+            s_d[t] = make_float4(l0.z, l1.z, -l0.w, -l1.w);
         }
         __syncthreads();
         const bool diag = (jt < i_hi) && (jt + n > i_lo);
-        for (int c = 0; c < n; c += FOLD) {
-            const int ce = min(c + FOLD, n);
-            float fx[IPT], fy[IPT], fz[IPT], mind[IPT];
+        for (int c = 0; c < np; c += FOLD / 2) {
+            const int ce = min(c + FOLD / 2, np);
+            float2 fx[IPT], fy[IPT], fz[IPT];
+            float mind[IPT];
 #pragma unroll
-            for (int k = 0; k < IPT; ++k) fx[k] = fy[k] = fz[k] = 0.0f, mind[k] = 3.0e38f;
+            for (int k = 0; k < IPT; ++k) {
+                fx[k] = fy[k] = fz[k] = make_float2(0.0f, 0.0f);
+                mind[k] = 3.0e38f;
+            }
             if (diag)
-                mixed_chunk<IPT, FLAG, true>(s_pos, s_lo, c, ce, xh, yh, zh, xl, yl, zl, fx, fy,
-                                             fz, mind);
+                mixed_chunk<IPT, FLAG, true>(sp, c, ce, nxh, nyh, nzh, nxl, nyl, nzl, fx, fy, fz, mind);
             else
-                mixed_chunk<IPT, FLAG, false>(s_pos, s_lo, c, ce, xh, yh, zh, xl, yl, zl, fx, fy,
-                                              fz, mind);
+                mixed_chunk<IPT, FLAG, false>(sp, c, ce, nxh, nyh, nzh, nxl, nyl, nzl, fx, fy, fz, mind);
 #pragma unroll
             for (int k = 0; k < IPT; ++k) {
                 float s, e;
-                two_sum(ahx[k], fx[k], s, e); ahx[k] = s; alx[k] += e;
-                two_sum(ahy[k], fy[k], s, e); ahy[k] = s; aly[k] += e;
-                two_sum(ahz[k], fz[k], s, e); ahz[k] = s; alz[k] += e;
+                two_sum(ahx[k], fx[k].x + fx[k].y, s, e); ahx[k] = s; alx[k] += e;
+                two_sum(ahy[k], fy[k].x + fy[k].y, s, e); ahy[k] = s; aly[k] += e;
+                two_sum(ahz[k], fz[k].x + fz[k].y, s, e); ahz[k] = s; alz[k] += e;
                 if (FLAG && mind[k] < rho[k])
-                    flag_chunk(a, s_pos, s_lo, c, ce, jt, gi[k], xh[k], yh[k], zh[k], xl[k],
-                               yl[k], zl[k], rho[k]);
+                    flag_chunk(a, sp, c, ce, n, jt, gi[k], -nxh[k].x, -nyh[k].x, -nzh[k].x,
+                               -nxl[k].x, -nyl[k].x, -nzl[k].x, rho[k]);
             }
         }
     }

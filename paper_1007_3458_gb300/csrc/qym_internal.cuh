@@ -223,6 +223,8 @@ cudaError_t launch_pair_test(int64_t rows, const double *q0, const double *v0, c
 
 // hermite.cu
 cudaError_t hermite_prepare();
+cudaError_t launch_transition(int64_t n, const double *s, double rc, double *K, double *Kp,
+                              double *Kpp, cudaStream_t st);
 cudaError_t launch_hermite(const Dev &d, const qym_params &p, double tau, cudaStream_t st);
 
 // energy.cu

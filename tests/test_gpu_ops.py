@@ -203,6 +203,31 @@ def test_encounter_test_bit_exact(torch, oracle):
     assert np.array_equal(got, ref_pairs)
 
 
+# ------------------------------------------------------------------ Sec. 2.1
+def test_transition_matches_oracle(torch, oracle):
+    """The transition function the Hermite sub-integrator evaluates (sin and
+    cos of pi y / 2 by folded Taylor polynomials) against the oracle's libm
+    sin/cos: K, K', K'' within a few ulp of their scales across the whole
+    zone, the flat parts exact, and the zone's edges at y = 0 and y = 1."""
+    rc = 0.37
+    rng = np.random.default_rng(3)
+    s = np.concatenate([np.linspace(0.0, 1.2 * rc, 20001), rng.uniform(0, rc, 20000),
+                        [0.1 * rc / 1.1, rc, rc * (1 - 1e-15), 0.0]])
+    n = len(s)
+    sd = torch.from_numpy(s).cuda()
+    K, Kp, Kpp = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
+    q.qym_transition_dev(n, sd, rc, K, Kp, Kpp)
+    torch.cuda.synchronize()
+    ref = np.array([oracle.transition(x, rc) for x in s])
+    c = 0.5 * math.pi * 1.1 / rc
+    K, Kp, Kpp = K.cpu().numpy(), Kp.cpu().numpy(), Kpp.cpu().numpy()
+    assert np.all(np.abs(K - ref[:, 0]) <= 4e-16)
+    assert np.all(np.abs(Kp - ref[:, 1]) <= 4e-16 * c)
+    assert np.all(np.abs(Kpp - ref[:, 2]) <= 4e-16 * c * c)
+    flat = (1.1 * s / rc - 0.1 <= 0) | (1.1 * s / rc - 0.1 >= 1)
+    assert np.array_equal(K[flat], ref[flat, 0]) and np.all(Kp[flat] == 0) and np.all(Kpp[flat] == 0)
+
+
 # ------------------------------------------------------------------ energy
 @pytest.mark.parametrize("name", ["disk_260", "disk_16384"])
 def test_energy_matches_oracle(torch, oracle, name):
