@@ -414,6 +414,7 @@ __global__ void k_step_begin(unsigned long long *ctr) {
     ctr[C_NENC] = 0;
     ctr[C_NRESCAN] = 0;
     ctr[C_NSETS] = 0;
+    ctr[C_HSMALL] = 0;
 }
 
 __global__ void k_step_end(unsigned long long *ctr, int64_t max_cand, int64_t max_enc) {

@@ -16,9 +16,12 @@
 // status word.
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "qym_internal.cuh"
 
 namespace qym {
+namespace cg = cooperative_groups;
 
 constexpr int HCAP = 512;       // members per set held in shared memory
 constexpr int HTHREADS = 256;
@@ -99,10 +102,15 @@ cudaError_t launch_transition(int64_t n, const double *s, double rc, double *K, 
     return cudaGetLastError();
 }
 
+constexpr int CL = 8;      // CTAs of a cluster sharing one large set
+constexpr int NBIG = 24;   // sets of at least this many members use a whole cluster
+constexpr int ACH = 128;   // active members per partial-force exchange round
+
 struct HermSmem {
     double *ex, *ey, *ez, *eu, *ev, *ew, *m;  // evaluation point of every member
     double *x, *y, *z, *u, *v, *w;            // state at the member's own time
     double *ax, *ay, *az, *jx, *jy, *jz;      // a, adot at the member's own time
+    double *pb;                               // partial a, adot [2][6][ACH]
     long long *ti;                            // member time in ticks
     int32_t *lev;                             // member level: step = tau 2^-lev
     int32_t *act;                             // members whose step ends now
@@ -119,6 +127,7 @@ __device__ __forceinline__ HermSmem carve(void *base) {
     s.u = p; p += HCAP; s.v = p; p += HCAP; s.w = p; p += HCAP;
     s.ax = p; p += HCAP; s.ay = p; p += HCAP; s.az = p; p += HCAP;
     s.jx = p; p += HCAP; s.jy = p; p += HCAP; s.jz = p; p += HCAP;
+    s.pb = p; p += 2 * 6 * ACH;
     s.ti = (long long *)p; p += HCAP;
     int32_t *ip = (int32_t *)p;
     s.lev = ip; ip += HCAP;
@@ -126,7 +135,8 @@ __device__ __forceinline__ HermSmem carve(void *base) {
     s.ids = ip;
     return s;
 }
-constexpr size_t kHermSmem = sizeof(double) * HCAP * 20 + sizeof(int32_t) * HCAP * 3;
+constexpr size_t kHermSmem =
+    sizeof(double) * (HCAP * 20 + 2 * 6 * ACH) + sizeof(int32_t) * HCAP * 3;
 constexpr int KMAX = 48;
 
 // smallest k with T 2^-k <= dt_c, in [0, KMAX]: with T = fT 2^eT and
@@ -141,13 +151,30 @@ __device__ __forceinline__ int level_of(double dt_c, double T) {
     return k < 0 ? 0 : (k > KMAX ? KMAX : k);
 }
 
-// Work split of a set of n members over the CTA: each member is handled by
-// P consecutive lanes (P a power of two, P * n <= HTHREADS when possible),
-// lane l of a member's group takes the partners l, l + P, ...; the group's
-// partial sums are combined with warp shuffles in a fixed tree order.
-__device__ __forceinline__ int lanes_per_member(int n) {
+// The same level from dt_c^2 = num / den: the smallest k with
+// T^2 4^-k den <= num (den > 0), from the exponents of num and T^2 den
+__device__ __forceinline__ int level_sq(double num, double den, double T) {
+    if (!(den > 0.0)) return 0;              // dt_c = infinity
+    if (!(num > 0.0)) return KMAX;
+    const double t2d = T * T * den;
+    if (t2d <= num) return 0;
+    int en, et;
+    const double fn = frexp(num, &en), ft = frexp(t2d, &et);
+    // t2d 4^-k <= num  <=>  ft 2^(et - 2k) <= fn 2^en
+    int k = (et - en + 1) >> 1;              // first candidate
+    if (k < 0) k = 0;
+    while (k < KMAX && ldexp(ft, et - 2 * k) > ldexp(fn, en)) ++k;
+    while (k > 0 && ldexp(ft, et - 2 * (k - 1)) <= ldexp(fn, en)) --k;
+    return k;
+}
+
+// Work split inside a CTA: each member of a group of n is handled by P
+// consecutive lanes (P a power of two, P * n <= HTHREADS when possible); lane
+// l of a member's group takes the partners lo + l, lo + l + P, ... below hi;
+// the group's partial sums are combined with warp shuffles in a fixed tree.
+__device__ __forceinline__ int lanes_per_member(int n, int partners) {
     int p = 32;
-    while (p > 1 && p * n > HTHREADS) p >>= 1;
+    while (p > 1 && (p * n > HTHREADS || p >= 2 * partners)) p >>= 1;
     return p;
 }
 
@@ -159,10 +186,10 @@ __device__ __forceinline__ void group_sum(double *v, int cnt, int P) {
 // partial (1-K)-weighted pair acceleration of member k at the evaluation
 // point, unsmoothed (the kick used the bare separation):
 // sum_l -G m_l q_kl / q^3 [1 - K + q K'] over the partners of this lane
-__device__ void kcorr_part(const HermSmem &S, int n, int k, int l0, int P, double G,
+__device__ void kcorr_part(const HermSmem &S, int lo, int hi, int k, int l0, int P, double G,
                            const TransC &tc, double *c) {
     c[0] = c[1] = c[2] = 0.0;
-    for (int l = l0; l < n; l += P) {
+    for (int l = lo + l0; l < hi; l += P) {
         if (l == k) continue;
         double qx = S.ex[k] - S.ex[l], qy = S.ey[k] - S.ey[l], qz = S.ez[k] - S.ez[l];
         double q2 = qx * qx + qy * qy + qz * qz;
@@ -179,15 +206,15 @@ __device__ void kcorr_part(const HermSmem &S, int n, int k, int l0, int P, doubl
 }
 
 // partial Hermite acceleration and jerk of member k at the evaluation point
-// (Sec. 2.2): the star term on lane 0 of the group, the pair terms with the
-// transition bracket over this lane's partners
-// (one reciprocal square root per pair: q = q2 / sqrt(q2), 1/q^3, 1/q^2)
-__device__ void herm_part(const HermSmem &S, int n, int k, int l0, int P, double G, double m0,
-                          const TransC &tc, double eps2, double *aj) {
+// (Sec. 2.2): with `star`, the star term on lane 0 of the group; the pair
+// terms with the transition bracket over this lane's partners (one
+// reciprocal square root per pair: q = q2 / sqrt(q2), 1/q^3, 1/q^2)
+__device__ void herm_part(const HermSmem &S, int lo, int hi, int k, int l0, int P, bool star,
+                          double G, double m0, const TransC &tc, double eps2, double *aj) {
     const double xk = S.ex[k], yk = S.ey[k], zk = S.ez[k];
     const double uk = S.eu[k], vk = S.ev[k], wk = S.ew[k];
     for (int c = 0; c < 6; ++c) aj[c] = 0.0;
-    if (l0 == 0) {  // star, fixed at the origin
+    if (star && l0 == 0) {  // star, fixed at the origin
         double s2 = xk * xk + yk * yk + zk * zk + eps2;
         double si = rsqrt(s2);
         double si2 = si * si;
@@ -197,7 +224,7 @@ __device__ void herm_part(const HermSmem &S, int n, int k, int l0, int P, double
         aj[0] = c * xk; aj[1] = c * yk; aj[2] = c * zk;
         aj[3] = c * (uk - t * xk); aj[4] = c * (vk - t * yk); aj[5] = c * (wk - t * zk);
     }
-    for (int l = l0; l < n; l += P) {
+    for (int l = lo + l0; l < hi; l += P) {
         if (l == k) continue;
         double qx = xk - S.ex[l], qy = yk - S.ey[l], qz = zk - S.ez[l];
         double q2 = qx * qx + qy * qy + qz * qz + eps2;
@@ -230,15 +257,86 @@ __device__ __forceinline__ long long block_min_ll(long long x, long long *red) {
     return r;
 }
 
-__device__ __forceinline__ double block_min(double x, double *red) {
-    for (int o = 16; o > 0; o >>= 1) x = fmin(x, __shfl_xor_sync(0xffffffffu, x, o));
-    int w = threadIdx.x >> 5;
+// Members whose step ends at tn, listed in ascending member order (the same
+// list in every CTA of a cluster); returns their number.
+__device__ int active_list(const HermSmem &S, int n, long long tn, int *wcnt) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = HTHREADS / 32;
+    int base = 0;
+    for (int c0 = 0; c0 < n; c0 += HTHREADS) {
+        const int k = c0 + threadIdx.x;
+        const bool f = k < n && S.ti[k] + (1ll << (KMAX - S.lev[k])) == tn;
+        const unsigned b = __ballot_sync(0xffffffffu, f);
+        __syncthreads();
+        if (lane == 0) wcnt[w] = __popc(b);
+        __syncthreads();
+        int before = 0, tot = 0;
+        for (int q = 0; q < nw; ++q) {
+            before += q < w ? wcnt[q] : 0;
+            tot += wcnt[q];
+        }
+        if (f) S.act[base + before + __popc(b & ((1u << lane) - 1u))] = k;
+        base += tot;
+    }
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = x;
-    __syncthreads();
-    double r = red[0];
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) r = fmin(r, red[k]);
-    return r;
+    return base;
+}
+
+// state of member k predicted from its own time to tn (Hermite predictor)
+__device__ __forceinline__ void predict(const HermSmem &S, int k, long long tn, double sgn,
+                                        double tick) {
+    const double hs = sgn * (double)(tn - S.ti[k]) * tick;
+    const double h6 = hs * (1.0 / 6.0);
+    S.ex[k] = S.x[k] + hs * (S.u[k] + hs * (0.5 * S.ax[k] + h6 * S.jx[k]));
+    S.ey[k] = S.y[k] + hs * (S.v[k] + hs * (0.5 * S.ay[k] + h6 * S.jy[k]));
+    S.ez[k] = S.z[k] + hs * (S.w[k] + hs * (0.5 * S.az[k] + h6 * S.jz[k]));
+    S.eu[k] = S.u[k] + hs * (S.ax[k] + 0.5 * hs * S.jx[k]);
+    S.ev[k] = S.v[k] + hs * (S.ay[k] + 0.5 * hs * S.jy[k]);
+    S.ew[k] = S.w[k] + hs * (S.az[k] + 0.5 * hs * S.jz[k]);
+}
+
+// Hermite corrector of member k at the end of its step (new a, adot in a1),
+// then its new level by the Aarseth criterion: a larger step only by one
+// level and on a time commensurate with it
+__device__ __forceinline__ void correct(const HermSmem &S, int k, const double *a1, long long tn,
+                                        double sgn, double tick, double eta, double T,
+                                        double inv_T) {
+    const int lv = S.lev[k];
+    const double hs = sgn * ldexp(T, -lv);           // exact: T 2^-lev
+    const double ih = sgn * ldexp(inv_T, lv);        // 1 / hs up to the rounding of 1/T
+    double a0[3] = {S.ax[k], S.ay[k], S.az[k]};
+    double j0[3] = {S.jx[k], S.jy[k], S.jz[k]};
+    double e[3] = {S.ex[k], S.ey[k], S.ez[k]};
+    double f[3] = {S.eu[k], S.ev[k], S.ew[k]};
+    double a2[3], a3[3], xn[3], un[3];
+    const double ih2 = ih * ih, ih3 = ih2 * ih;
+    const double h3 = hs * hs * hs, h4 = h3 * hs;
+    for (int c = 0; c < 3; ++c) {
+        a2[c] = (-6.0 * (a0[c] - a1[c]) - hs * (4.0 * j0[c] + 2.0 * a1[3 + c])) * ih2;
+        a3[c] = (12.0 * (a0[c] - a1[c]) + 6.0 * hs * (j0[c] + a1[3 + c])) * ih3;
+        xn[c] = e[c] + h4 * (a2[c] * (1.0 / 24.0) + hs * a3[c] * (1.0 / 120.0));
+        un[c] = f[c] + h3 * (a2[c] * (1.0 / 6.0) + hs * a3[c] * (1.0 / 24.0));
+        a2[c] += hs * a3[c];
+    }
+    S.x[k] = xn[0]; S.y[k] = xn[1]; S.z[k] = xn[2];
+    S.u[k] = un[0]; S.v[k] = un[1]; S.w[k] = un[2];
+    S.ax[k] = a1[0]; S.ay[k] = a1[1]; S.az[k] = a1[2];
+    S.jx[k] = a1[3]; S.jy[k] = a1[4]; S.jz[k] = a1[5];
+    S.ti[k] = tn;
+    // Aarseth: dt_c^2 = eta (|a| |a2| + |j|^2) / (|j| |a3| + |a2|^2); the level
+    // is the smallest k with (T 2^-k)^2 <= dt_c^2, found without the square
+    // root and the division on the dependent path
+    const double A2 = a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2];
+    const double J2 = a1[3] * a1[3] + a1[4] * a1[4] + a1[5] * a1[5];
+    const double B2 = a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2];
+    const double C2 = a3[0] * a3[0] + a3[1] * a3[1] + a3[2] * a3[2];
+    const double num = eta * (sqrt(A2 * B2) + J2);
+    const double den = sqrt(J2 * C2) + B2;
+    int kn = level_sq(num, den, T);
+    if (kn < lv) {
+        const int up1 = lv - 1;
+        kn = (tn % (1ll << (KMAX - up1)) == 0) ? up1 : lv;
+    }
+    S.lev[k] = kn;
 }
 
 struct HermArgs {
@@ -246,204 +344,258 @@ struct HermArgs {
     int64_t max_steps;
 };
 
-__global__ void __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[32];
-    HermSmem S = carve(smem);
+// Copy the member range [lo, hi) of arrays a..: from CTA `r` of the cluster
+// into this CTA's shared memory.
+__device__ __forceinline__ void pull_range(cg::cluster_group &cl, const HermSmem &S, int r,
+                                           int lo, int hi, double *const *arrs, int narr) {
+    for (int q = 0; q < narr; ++q) {
+        const double *src = cl.map_shared_rank(arrs[q], r);
+        for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) arrs[q][k] = src[k];
+    }
+}
+
+// One set through items 5-7 of the step (Sec. 2.3): K correction at q0,
+// Hermite over tau with individual block steps, K correction at q1. With
+// COOP the cs CTAs of a cluster share the set: every CTA keeps a full copy of
+// the members' state; CTA `rank` evaluates the start-up forces and the K
+// corrections of its member range, exchanged once; in each block step it sums
+// the forces on the active members from its partner range, all partial sums
+// are read from the peers' shared memory in rank order, and every CTA applies
+// the same corrector, so the copies stay identical with one cluster barrier
+// per exchange round (partials double-buffered).
+template <bool COOP>
+__device__ __noinline__ void hermite_set(const Dev &d, const HermArgs &h, const HermSmem &S, int set, int rank,
+                            int cs, long long *redl, int *wcnt) {
+    cg::cluster_group cl = cg::this_cluster();
     const int64_t R = d.rows;
     const int tid = threadIdx.x;
-    int nsets = (int)min((unsigned long long)d.max_sets, d.ctr[C_NSETS]);
-    for (int set = blockIdx.x; set < nsets; set += gridDim.x) {
-        const int st = d.set_start[set];
-        const int n = d.set_start[set + 1] - st;
-        if (n < 1) continue;
-        if (n > HCAP || st + n > d.max_members) {
-            if (tid == 0) atomicOr(d.status, QYM_ST_SET_OVERFLOW);
+    const int st = d.set_start[set];
+    const int n = d.set_start[set + 1] - st;
+    if (n < 1) return;
+    if (n > HCAP || st + n > d.max_members) {
+        if (tid == 0 && rank == 0) atomicOr(d.status, QYM_ST_SET_OVERFLOW);
+        if (rank == 0)
             for (int k = tid; k < n && st + k < d.max_members; k += blockDim.x)
                 d.uf[d.set_mem[st + k]] = -1;
-            continue;
+        return;
+    }
+    // this CTA's member range (COOP) or all members
+    const int mlo = n * rank / cs, mhi = n * (rank + 1) / cs;
+    const int P = lanes_per_member(mhi - mlo, n);
+    const int NG = HTHREADS / P;
+    const int grp = tid / P, lane = tid % P;
+    // members in ascending row order (rank sort)
+    __syncthreads();
+    for (int k = tid; k < n; k += blockDim.x) S.ids[k] = d.set_mem[st + k];
+    __syncthreads();
+    int myid[HCAP / HTHREADS], myrank[HCAP / HTHREADS];
+    for (int c = 0; c < HCAP / HTHREADS; ++c) {
+        int k = tid + c * blockDim.x;
+        myid[c] = k < n ? S.ids[k] : 0;
+        int rk = 0;
+        if (k < n)
+            for (int l = 0; l < n; ++l) rk += S.ids[l] < myid[c];
+        myrank[c] = rk;
+    }
+    __syncthreads();
+    for (int c = 0; c < HCAP / HTHREADS; ++c) {
+        int k = tid + c * blockDim.x;
+        if (k < n) S.ids[myrank[c]] = myid[c];
+    }
+    __syncthreads();
+    const int64_t star = d.offsets[d.sys_of[S.ids[0]]];
+    const double m0 = d.m[star];
+    const TransC tc(d.rcrit[set]);
+    const double G = h.G, tau = h.tau;
+    // state entering the Kepler drift (after the first kick)
+    for (int k = tid; k < n; k += blockDim.x) {
+        int64_t r = S.ids[k];
+        S.ex[k] = S.x[k] = d.q[r];
+        S.ey[k] = S.y[k] = d.q[R + r];
+        S.ez[k] = S.z[k] = d.q[2 * R + r];
+        S.u[k] = d.v[r];
+        S.v[k] = d.v[R + r];
+        S.w[k] = d.v[2 * R + r];
+        S.m[k] = d.m[r];
+    }
+    __syncthreads();
+    // item 5: remove the (1-K) part of the first kick (own members)
+    for (int k0 = mlo; k0 < mhi; k0 += NG) {
+        int k = k0 + grp;
+        double c[3] = {0.0, 0.0, 0.0};
+        if (k < mhi) kcorr_part(S, 0, n, k, lane, P, G, tc, c);
+        group_sum(c, 3, P);
+        if (k < mhi && lane == 0) {
+            S.u[k] -= 0.5 * tau * c[0];
+            S.v[k] -= 0.5 * tau * c[1];
+            S.w[k] -= 0.5 * tau * c[2];
         }
-        const int P = lanes_per_member(n);
-        const int NG = HTHREADS / P;             // member groups in the CTA
-        const int grp = tid / P, lane = tid % P;
-        // members in ascending row order (rank sort)
+    }
+    if (COOP) {
+        cl.sync();
+        double *const arr[3] = {S.u, S.v, S.w};
+        for (int r = 0; r < cs; ++r)
+            if (r != rank) pull_range(cl, S, r, n * r / cs, n * (r + 1) / cs, arr, 3);
+        cl.sync();
+    } else {
         __syncthreads();
-        for (int k = tid; k < n; k += blockDim.x) S.ids[k] = d.set_mem[st + k];
-        __syncthreads();
-        int myid[HCAP / HTHREADS], myrank[HCAP / HTHREADS];
-        for (int c = 0; c < HCAP / HTHREADS; ++c) {
-            int k = tid + c * blockDim.x;
-            myid[c] = k < n ? S.ids[k] : 0;
-            int rk = 0;
-            if (k < n)
-                for (int l = 0; l < n; ++l) rk += S.ids[l] < myid[c];
-            myrank[c] = rk;
+    }
+    for (int k = tid; k < n; k += blockDim.x) {
+        S.eu[k] = S.u[k]; S.ev[k] = S.v[k]; S.ew[k] = S.w[k];
+    }
+    __syncthreads();
+    // start-up: a, adot at t = 0 and the levels from eta_s |a| / |adot|
+    const double sgn = tau >= 0.0 ? 1.0 : -1.0;
+    const double T = fabs(tau);
+    const long long TT = 1ll << KMAX;
+    const double tick = T / (double)TT;
+    const double inv_T = 1.0 / T;
+    for (int k0 = mlo; k0 < mhi; k0 += NG) {
+        int k = k0 + grp;
+        double aj[6] = {0, 0, 0, 0, 0, 0};
+        if (k < mhi) herm_part(S, 0, n, k, lane, P, true, G, m0, tc, h.eps2, aj);
+        group_sum(aj, 6, P);
+        if (k < mhi && lane == 0) {
+            S.ax[k] = aj[0]; S.ay[k] = aj[1]; S.az[k] = aj[2];
+            S.jx[k] = aj[3]; S.jy[k] = aj[4]; S.jz[k] = aj[5];
+            double jn = sqrt(aj[3] * aj[3] + aj[4] * aj[4] + aj[5] * aj[5]);
+            double dt_c = jn > 0.0 ? h.eta_s * sqrt(aj[0] * aj[0] + aj[1] * aj[1] + aj[2] * aj[2]) / jn : T;
+            S.lev[k] = level_of(dt_c, T);
+            S.ti[k] = 0;
         }
-        __syncthreads();
-        for (int c = 0; c < HCAP / HTHREADS; ++c) {
-            int k = tid + c * blockDim.x;
-            if (k < n) S.ids[myrank[c]] = myid[c];
-        }
-        __syncthreads();
-        const int64_t star = d.offsets[d.sys_of[S.ids[0]]];
-        const double m0 = d.m[star];
-        const TransC tc(d.rcrit[set]);
-        const double G = h.G, tau = h.tau;
-        // state entering the Kepler drift (after the first kick)
-        for (int k = tid; k < n; k += blockDim.x) {
-            int64_t r = S.ids[k];
-            S.ex[k] = S.x[k] = d.q[r];
-            S.ey[k] = S.y[k] = d.q[R + r];
-            S.ez[k] = S.z[k] = d.q[2 * R + r];
-            S.u[k] = d.v[r];
-            S.v[k] = d.v[R + r];
-            S.w[k] = d.v[2 * R + r];
-            S.m[k] = d.m[r];
-        }
-        __syncthreads();
-        // item 5: remove the (1-K) part of the first kick
-        for (int k0 = 0; k0 < n; k0 += NG) {
-            int k = k0 + grp;
-            double c[3] = {0.0, 0.0, 0.0};
-            if (k < n) kcorr_part(S, n, k, lane, P, G, tc, c);
-            group_sum(c, 3, P);
-            if (k < n && lane == 0) {
-                S.u[k] -= 0.5 * tau * c[0];
-                S.v[k] -= 0.5 * tau * c[1];
-                S.w[k] -= 0.5 * tau * c[2];
-            }
-        }
-        __syncthreads();
-        for (int k = tid; k < n; k += blockDim.x) {
-            S.eu[k] = S.u[k]; S.ev[k] = S.v[k]; S.ew[k] = S.w[k];
-        }
-        __syncthreads();
-        // start-up: a, adot at t = 0 and the levels from eta_s |a| / |adot|
-        const double sgn = tau >= 0.0 ? 1.0 : -1.0;
-        const double T = fabs(tau);
-        const long long TT = 1ll << KMAX;
-        const double tick = T / (double)TT;
-        for (int k0 = 0; k0 < n; k0 += NG) {
-            int k = k0 + grp;
-            double aj[6] = {0, 0, 0, 0, 0, 0};
-            if (k < n) herm_part(S, n, k, lane, P, G, m0, tc, h.eps2, aj);
-            group_sum(aj, 6, P);
-            if (k < n && lane == 0) {
-                S.ax[k] = aj[0]; S.ay[k] = aj[1]; S.az[k] = aj[2];
-                S.jx[k] = aj[3]; S.jy[k] = aj[4]; S.jz[k] = aj[5];
-                double jn = sqrt(aj[3] * aj[3] + aj[4] * aj[4] + aj[5] * aj[5]);
-                double dt_c = jn > 0.0 ? h.eta_s * sqrt(aj[0] * aj[0] + aj[1] * aj[1] + aj[2] * aj[2]) / jn : T;
-                S.lev[k] = level_of(dt_c, T);
+    }
+    if (COOP) {
+        cl.sync();
+        double *const arr[6] = {S.ax, S.ay, S.az, S.jx, S.jy, S.jz};
+        for (int r = 0; r < cs; ++r) {
+            if (r == rank) continue;
+            const int lo = n * r / cs, hi = n * (r + 1) / cs;
+            pull_range(cl, S, r, lo, hi, arr, 6);
+            const int32_t *pl = cl.map_shared_rank(S.lev, r);
+            for (int k = lo + tid; k < hi; k += blockDim.x) {
+                S.lev[k] = pl[k];
                 S.ti[k] = 0;
             }
         }
-        __shared__ long long redl[32];
-        __shared__ int n_act;
-        int64_t steps = 0;
-        bool capped = false;
-        for (;;) {
-            __syncthreads();
-            // next block time: the earliest end of a member's step
-            long long tn_l = LLONG_MAX;
-            for (int k = tid; k < n; k += blockDim.x)
-                tn_l = min(tn_l, S.ti[k] + (1ll << (KMAX - S.lev[k])));
-            const long long tn = block_min_ll(tn_l, redl);
-            if (tn > TT) break;  // every member has reached tau
-            if (steps >= h.max_steps) { capped = true; break; }
-            if (tid == 0) n_act = 0;
-            // predict every member to tn from its own time; list the active
-            for (int k = tid; k < n; k += blockDim.x) {
-                const double hs = sgn * (double)(tn - S.ti[k]) * tick;
-                const double h6 = hs * (1.0 / 6.0);
-                S.ex[k] = S.x[k] + hs * (S.u[k] + hs * (0.5 * S.ax[k] + h6 * S.jx[k]));
-                S.ey[k] = S.y[k] + hs * (S.v[k] + hs * (0.5 * S.ay[k] + h6 * S.jy[k]));
-                S.ez[k] = S.z[k] + hs * (S.w[k] + hs * (0.5 * S.az[k] + h6 * S.jz[k]));
-                S.eu[k] = S.u[k] + hs * (S.ax[k] + 0.5 * hs * S.jx[k]);
-                S.ev[k] = S.v[k] + hs * (S.ay[k] + 0.5 * hs * S.jy[k]);
-                S.ew[k] = S.w[k] + hs * (S.az[k] + 0.5 * hs * S.jz[k]);
-            }
-            __syncthreads();
-            for (int k = tid; k < n; k += blockDim.x)
-                if (S.ti[k] + (1ll << (KMAX - S.lev[k])) == tn) S.act[atomicAdd(&n_act, 1)] = k;
-            __syncthreads();
-            const int na = n_act;
-            const int PA = lanes_per_member(na);
+        cl.sync();
+    }
+    int64_t steps = 0;
+    bool capped = false;
+    int buf = 0;
+    for (;;) {
+        __syncthreads();
+        // next block time: the earliest end of a member's step
+        long long tn_l = LLONG_MAX;
+        for (int k = tid; k < n; k += blockDim.x)
+            tn_l = min(tn_l, S.ti[k] + (1ll << (KMAX - S.lev[k])));
+        const long long tn = block_min_ll(tn_l, redl);
+        if (tn > TT) break;  // every member has reached tau
+        if (steps >= h.max_steps) { capped = true; break; }
+        const int na = active_list(S, n, tn, wcnt);
+        // predict the partners of this CTA and the active members to tn
+        for (int k = mlo + tid; k < mhi; k += blockDim.x) predict(S, k, tn, sgn, tick);
+        for (int a = tid; a < na; a += blockDim.x) {
+            const int k = S.act[a];
+            if (k < mlo || k >= mhi) predict(S, k, tn, sgn, tick);
+        }
+        __syncthreads();
+        for (int a0 = 0; a0 < na; a0 += ACH) {
+            const int nc = min(ACH, na - a0);
+            const int PA = lanes_per_member(nc, mhi - mlo);
             const int NGA = HTHREADS / PA;
             const int ga = tid / PA, la = tid % PA;
-            // evaluate (split over lanes) and correct (lane 0) the active members
-            for (int k0 = 0; k0 < na; k0 += NGA) {
-                const int slot = k0 + ga;
-                const int k = slot < na ? S.act[slot] : 0;
+            double *pbw = S.pb + buf * 6 * ACH;
+            // partial a, adot of the active members from this CTA's partners
+            for (int s0 = 0; s0 < nc; s0 += NGA) {
+                const int slot = s0 + ga;
+                const int k = slot < nc ? S.act[a0 + slot] : 0;
                 double a1[6] = {0, 0, 0, 0, 0, 0};
-                if (slot < na) herm_part(S, n, k, la, PA, G, m0, tc, h.eps2, a1);
+                if (slot < nc) herm_part(S, mlo, mhi, k, la, PA, rank == 0, G, m0, tc, h.eps2, a1);
                 group_sum(a1, 6, PA);
-                if (slot < na && la == 0) {
-                    const long long dti = 1ll << (KMAX - S.lev[k]);
-                    const double hs = sgn * (double)dti * tick;
-                    double a0[3] = {S.ax[k], S.ay[k], S.az[k]};
-                    double j0[3] = {S.jx[k], S.jy[k], S.jz[k]};
-                    double e[3] = {S.ex[k], S.ey[k], S.ez[k]};
-                    double f[3] = {S.eu[k], S.ev[k], S.ew[k]};
-                    double a2[3], a3[3], xn[3], un[3];
-                    const double ih = 1.0 / hs, ih2 = ih * ih, ih3 = ih2 * ih;
-                    const double h3 = hs * hs * hs, h4 = h3 * hs;
-                    for (int c = 0; c < 3; ++c) {
-                        a2[c] = (-6.0 * (a0[c] - a1[c]) - hs * (4.0 * j0[c] + 2.0 * a1[3 + c])) * ih2;
-                        a3[c] = (12.0 * (a0[c] - a1[c]) + 6.0 * hs * (j0[c] + a1[3 + c])) * ih3;
-                        xn[c] = e[c] + h4 * (a2[c] * (1.0 / 24.0) + hs * a3[c] * (1.0 / 120.0));
-                        un[c] = f[c] + h3 * (a2[c] * (1.0 / 6.0) + hs * a3[c] * (1.0 / 24.0));
-                        a2[c] += hs * a3[c];
-                    }
-                    S.x[k] = xn[0]; S.y[k] = xn[1]; S.z[k] = xn[2];
-                    S.u[k] = un[0]; S.v[k] = un[1]; S.w[k] = un[2];
-                    S.ax[k] = a1[0]; S.ay[k] = a1[1]; S.az[k] = a1[2];
-                    S.jx[k] = a1[3]; S.jy[k] = a1[4]; S.jz[k] = a1[5];
-                    S.ti[k] = tn;
-                    // Aarseth criterion at the end of the step, then the level
-                    double na1 = sqrt(a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
-                    double nj = sqrt(a1[3] * a1[3] + a1[4] * a1[4] + a1[5] * a1[5]);
-                    double n2 = sqrt(a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2]);
-                    double n3 = sqrt(a3[0] * a3[0] + a3[1] * a3[1] + a3[2] * a3[2]);
-                    double den = nj * n3 + n2 * n2;
-                    double dt_c = den > 0.0 ? sqrt(h.eta * (na1 * n2 + nj * nj) / den) : T;
-                    int kn = level_of(dt_c, T);
-                    const int lv = S.lev[k];
-                    if (kn < lv) {  // a larger step: one level, on a commensurate time
-                        const int up1 = lv - 1;
-                        kn = (tn % (1ll << (KMAX - up1)) == 0) ? up1 : lv;
-                    }
-                    S.lev[k] = kn;
+                if (slot < nc && la == 0)
+                    for (int c = 0; c < 6; ++c) pbw[c * ACH + slot] = a1[c];
+            }
+            if (COOP) cl.sync(); else __syncthreads();
+            // sum over the CTAs in rank order, correct (the same in every CTA)
+            for (int slot = tid; slot < nc; slot += blockDim.x) {
+                double a1[6] = {0, 0, 0, 0, 0, 0};
+                for (int r = 0; r < cs; ++r) {
+                    const double *pr = COOP ? cl.map_shared_rank(pbw, r) : pbw;
+                    for (int c = 0; c < 6; ++c) a1[c] += pr[c * ACH + slot];
                 }
+                correct(S, S.act[a0 + slot], a1, tn, sgn, tick, h.eta, T, inv_T);
             }
-            ++steps;
+            buf ^= 1;
         }
+        ++steps;
+    }
+    // peers may still read this CTA's partial sums of the last round
+    if (COOP) cl.sync(); else __syncthreads();
+    if (capped && tid == 0 && rank == 0) atomicOr(d.status, QYM_ST_HERMITE_CAP);
+    // item 7: pre-remove the (1-K) part of the coming kick at q1 (own members)
+    for (int k = tid; k < n; k += blockDim.x) {
+        S.ex[k] = S.x[k]; S.ey[k] = S.y[k]; S.ez[k] = S.z[k];
+    }
+    __syncthreads();
+    for (int k0 = mlo; k0 < mhi; k0 += NG) {
+        int k = k0 + grp;
+        double c[3] = {0.0, 0.0, 0.0};
+        if (k < mhi) kcorr_part(S, 0, n, k, lane, P, G, tc, c);
+        group_sum(c, 3, P);
+        if (k < mhi && lane == 0) {
+            int64_t r = S.ids[k];
+            d.q1[r] = S.x[k];
+            d.q1[R + r] = S.y[k];
+            d.q1[2 * R + r] = S.z[k];
+            d.v1[r] = S.u[k] - 0.5 * tau * c[0];
+            d.v1[R + r] = S.v[k] - 0.5 * tau * c[1];
+            d.v1[2 * R + r] = S.w[k] - 0.5 * tau * c[2];
+            d.uf[r] = -1;
+        }
+    }
+    if (tid == 0 && rank == 0) {
+        atomicAdd(d.ctr + C_SUM_HSTEPS, (unsigned long long)steps);
+        atomicMax(d.ctr + C_MAX_HSET, (unsigned long long)steps);
+    }
+    // the next set reuses shared memory that peers read above
+    if (COOP) cl.sync(); else __syncthreads();
+}
+
+// Sets of at least NBIG members go to whole clusters (the i-th such set to
+// cluster i mod #clusters); the others are taken one CTA at a time in the
+// order of a counter, so CTAs freed early take more.
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long redl[32];
+    __shared__ int wcnt[HTHREADS / 32];
+    __shared__ int next_small;
+    HermSmem S = carve(smem);
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
+    const int nsets = (int)min((unsigned long long)d.max_sets, d.ctr[C_NSETS]);
+    // clusters pay off when large sets are few (one system, a few planets);
+    // with more large sets than clusters, set-level parallelism wins and
+    // every set runs on one CTA
+    int nbig = 0;
+    for (int set = 0; set < nsets && nbig <= ncl; ++set)
+        nbig += d.set_start[set + 1] - d.set_start[set] >= NBIG;
+    const int big = nbig <= ncl ? NBIG : INT_MAX;
+    int ib = 0;
+    for (int set = 0; set < nsets && big == NBIG; ++set) {
+        const int n = d.set_start[set + 1] - d.set_start[set];
+        if (n < big) continue;
+        if (ib++ % ncl != cid) continue;
+        hermite_set<true>(d, h, S, set, rank, CL, redl, wcnt);
+    }
+    for (;;) {
         __syncthreads();
-        if (capped && tid == 0) atomicOr(d.status, QYM_ST_HERMITE_CAP);
-        // item 7: pre-remove the (1-K) part of the coming kick at q1
-        for (int k = tid; k < n; k += blockDim.x) {
-            S.ex[k] = S.x[k]; S.ey[k] = S.y[k]; S.ez[k] = S.z[k];
-        }
+        if (threadIdx.x == 0) next_small = (int)atomicAdd(d.ctr + C_HSMALL, 1ull);
         __syncthreads();
-        for (int k0 = 0; k0 < n; k0 += NG) {
-            int k = k0 + grp;
-            double c[3] = {0.0, 0.0, 0.0};
-            if (k < n) kcorr_part(S, n, k, lane, P, G, tc, c);
-            group_sum(c, 3, P);
-            if (k < n && lane == 0) {
-                int64_t r = S.ids[k];
-                d.q1[r] = S.x[k];
-                d.q1[R + r] = S.y[k];
-                d.q1[2 * R + r] = S.z[k];
-                d.v1[r] = S.u[k] - 0.5 * tau * c[0];
-                d.v1[R + r] = S.v[k] - 0.5 * tau * c[1];
-                d.v1[2 * R + r] = S.w[k] - 0.5 * tau * c[2];
-                d.uf[r] = -1;
-            }
-        }
-        if (tid == 0) {
-            atomicAdd(d.ctr + C_SUM_HSTEPS, (unsigned long long)steps);
-            atomicMax(d.ctr + C_MAX_HSET, (unsigned long long)steps);
-        }
+        const int set = next_small;
+        if (set >= nsets) break;
+        if (d.set_start[set + 1] - d.set_start[set] >= big) continue;
+        hermite_set<false>(d, h, S, set, 0, 1, redl, wcnt);
     }
 }
 

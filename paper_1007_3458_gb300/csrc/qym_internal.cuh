@@ -81,6 +81,7 @@ enum Ctr : int {
     C_SUM_RESCAN,
     C_STEP,          // step index within the current qym_step call
     C_MAX_HSET,      // most Hermite steps taken by one set in one step
+    C_HSMALL,        // next set for the Hermite kernel's per-CTA queue (reset per step)
     C_COUNT
 };
 
