@@ -33,25 +33,23 @@ constexpr int HTHREADS = 256;
 __device__ __forceinline__ void sincos_half_pi(double y, double &sn, double &cs) {
     const bool fold = y > 0.5;
     const double w = 1.5707963267948966 * (fold ? 1.0 - y : y);
-    const double w2 = w * w;
-    double ps = -1.0 / 1307674368000.0;        // -1/15!
-    ps = fma(ps, w2, 1.0 / 6227020800.0);      // +1/13!
-    ps = fma(ps, w2, -1.0 / 39916800.0);       // -1/11!
-    ps = fma(ps, w2, 1.0 / 362880.0);          // +1/9!
-    ps = fma(ps, w2, -1.0 / 5040.0);           // -1/7!
-    ps = fma(ps, w2, 1.0 / 120.0);             // +1/5!
-    ps = fma(ps, w2, -1.0 / 6.0);              // -1/3!
-    ps = fma(ps, w2, 1.0);
+    // both polynomials in x = w^2 by Estrin's scheme (dependent depth 4-5
+    // instead of 8-9: FP64 operations have long latency on this GPU)
+    const double x = w * w, x2 = x * x, x4 = x2 * x2;
+    // sin w / w = 1 - x/3! + x^2/5! - ... - x^7/15!
+    const double s01 = fma(-1.0 / 6.0, x, 1.0);
+    const double s23 = fma(-1.0 / 5040.0, x, 1.0 / 120.0);
+    const double s45 = fma(-1.0 / 39916800.0, x, 1.0 / 362880.0);
+    const double s67 = fma(-1.0 / 1307674368000.0, x, 1.0 / 6227020800.0);
+    const double ps = fma(fma(s67, x2, s45), x4, fma(s23, x2, s01));
     const double sw = w * ps;
-    double pc = 1.0 / 20922789888000.0;        // +1/16!
-    pc = fma(pc, w2, -1.0 / 87178291200.0);    // -1/14!
-    pc = fma(pc, w2, 1.0 / 479001600.0);       // +1/12!
-    pc = fma(pc, w2, -1.0 / 3628800.0);        // -1/10!
-    pc = fma(pc, w2, 1.0 / 40320.0);           // +1/8!
-    pc = fma(pc, w2, -1.0 / 720.0);            // -1/6!
-    pc = fma(pc, w2, 1.0 / 24.0);              // +1/4!
-    pc = fma(pc, w2, -0.5);                    // -1/2!
-    pc = fma(pc, w2, 1.0);
+    // cos w = 1 - x/2! + x^2/4! - ... + x^8/16!
+    const double c01 = fma(-0.5, x, 1.0);
+    const double c23 = fma(-1.0 / 720.0, x, 1.0 / 24.0);
+    const double c45 = fma(-1.0 / 3628800.0, x, 1.0 / 40320.0);
+    const double c67 = fma(-1.0 / 87178291200.0, x, 1.0 / 479001600.0);
+    const double c8 = (1.0 / 20922789888000.0) * (x4 * x4);
+    const double pc = fma(fma(c67, x2, c45), x4, fma(c23, x2, c01)) + c8;
     sn = fold ? pc : sw;
     cs = fold ? sw : pc;
 }
@@ -102,6 +100,11 @@ cudaError_t launch_transition(int64_t n, const double *s, double rc, double *K, 
     return cudaGetLastError();
 }
 
+// shared memory of k_hermite, at file scope so that every array of a set's
+// state is a constant offset (no base pointers held in registers or passed
+// through the stack of the per-set function)
+extern __shared__ __align__(16) unsigned char g_hsmem[];
+
 constexpr int CL = 8;      // CTAs of a cluster sharing one large set
 constexpr int NBIG = 24;   // sets of at least this many members use a whole cluster
 constexpr int ACH = 128;   // active members per partial-force exchange round
@@ -149,23 +152,6 @@ __device__ __forceinline__ int level_of(double dt_c, double T) {
     const double fT = frexp(T, &eT), fd = frexp(dt_c, &ed);
     const int k = eT - ed + (fT > fd ? 1 : 0);
     return k < 0 ? 0 : (k > KMAX ? KMAX : k);
-}
-
-// The same level from dt_c^2 = num / den: the smallest k with
-// T^2 4^-k den <= num (den > 0), from the exponents of num and T^2 den
-__device__ __forceinline__ int level_sq(double num, double den, double T) {
-    if (!(den > 0.0)) return 0;              // dt_c = infinity
-    if (!(num > 0.0)) return KMAX;
-    const double t2d = T * T * den;
-    if (t2d <= num) return 0;
-    int en, et;
-    const double fn = frexp(num, &en), ft = frexp(t2d, &et);
-    // t2d 4^-k <= num  <=>  ft 2^(et - 2k) <= fn 2^en
-    int k = (et - en + 1) >> 1;              // first candidate
-    if (k < 0) k = 0;
-    while (k < KMAX && ldexp(ft, et - 2 * k) > ldexp(fn, en)) ++k;
-    while (k > 0 && ldexp(ft, et - 2 * (k - 1)) <= ldexp(fn, en)) --k;
-    return k;
 }
 
 // Work split inside a CTA: each member of a group of n is handled by P
@@ -294,6 +280,61 @@ __device__ __forceinline__ void predict(const HermSmem &S, int k, long long tn, 
     S.ew[k] = S.w[k] + hs * (S.az[k] + 0.5 * hs * S.jz[k]);
 }
 
+// Level after a step of level lv by the Aarseth criterion,
+// dt_c^2 = eta (|a| |a2| + |j|^2) / (|j| |a3| + |a2|^2), from a = a1[0..2],
+// j = a1[3..5] and the corrector's a2, a3: the smallest k with
+// T 2^-k <= dt_c. With g = 2^-lv, j g, a2 g^2, a3 g^3 are all accelerations
+// times T^0, T^-1, ... scaled alike, and r = eta (|a||a2 g^2| + |j g|^2) /
+// (|j g||a3 g^3| + |a2 g^2|^2) = (dt_c / (T g))^2 T^2, so T 2^-k <= dt_c is
+// T^2 4^(lv - k) <= r. The powers of g and one common power of two that brings
+// every component below 1 are applied exactly through the exponents, and the
+// rest runs in FP32 (an FP64 operation's latency here is fifteen FP32 ones).
+// It only picks a power of two: a different level than an FP64 evaluation
+// needs dt_c within ~1e-7 of a level boundary.
+__device__ __forceinline__ int aarseth_level(const double *a1, const double *a2, const double *a3,
+                                             int lv, double eta, float T2) {
+    const double *src[4] = {a1, a1 + 3, a2, a3};
+    int ex[12], emax = 0;
+    for (int g = 0; g < 4; ++g)
+        for (int c = 0; c < 3; ++c) {
+            const long long bits = __double_as_longlong(src[g][c]);
+            const int eb = (int)((bits >> 52) & 0x7ff);
+            if (eb == 0x7ff) return lv;            // not finite: keep the level
+            ex[3 * g + c] = eb == 0 ? -100000 : eb - g * lv;   // biased, after g^g
+            emax = max(emax, ex[3 * g + c]);
+        }
+    if (emax <= -100000) return KMAX;              // a = j = a2 = a3 = 0
+    float f[12];
+    for (int g = 0; g < 4; ++g)
+        for (int c = 0; c < 3; ++c) {
+            // v 2^(-g lv) 2^-(emax - 1022): below 1 in magnitude, exact
+            const int sh = -g * lv - (emax - 1022);   // <= 1021 (emax >= 1)
+            const double scale =
+                sh < -1022 ? 0.0 : __longlong_as_double((long long)(sh + 1023) << 52);
+            f[3 * g + c] = (float)(src[g][c] * scale);
+        }
+    const float A2 = fmaf(f[0], f[0], fmaf(f[1], f[1], f[2] * f[2]));
+    const float J2 = fmaf(f[3], f[3], fmaf(f[4], f[4], f[5] * f[5]));
+    const float B2 = fmaf(f[6], f[6], fmaf(f[7], f[7], f[8] * f[8]));
+    const float C2 = fmaf(f[9], f[9], fmaf(f[10], f[10], f[11] * f[11]));
+    const float num = (float)eta * (sqrtf(A2 * B2) + J2);
+    const float den = sqrtf(J2 * C2) + B2;
+    if (!(den > 0.0f)) return 0;          // dt_c = infinity: the largest step
+    if (!(num > 0.0f)) return KMAX;
+    const float r = num / den;
+    if (!(r < INFINITY)) return 0;
+    // smallest k in [0, KMAX] with T^2 4^m <= r, m = lv - k: with
+    // r = fr 2^er and T^2 = ft 2^et (fr, ft in [1/2, 1)) and d = er - et, the
+    // largest such m is (d - 1) / 2 for odd d, d / 2 when ft <= fr for even d,
+    // else d / 2 - 1
+    int er, et;
+    const float fr = frexpf(r, &er), ft = frexpf(T2, &et);
+    const int dd = er - et;
+    const int m = (dd & 1) ? (dd - 1) >> 1 : ((ft <= fr) ? dd >> 1 : (dd >> 1) - 1);
+    int k = lv - m;
+    return k < 0 ? 0 : (k > KMAX ? KMAX : k);
+}
+
 // Hermite corrector of member k at the end of its step (new a, adot in a1),
 // then its new level by the Aarseth criterion: a larger step only by one
 // level and on a time commensurate with it
@@ -322,16 +363,7 @@ __device__ __forceinline__ void correct(const HermSmem &S, int k, const double *
     S.ax[k] = a1[0]; S.ay[k] = a1[1]; S.az[k] = a1[2];
     S.jx[k] = a1[3]; S.jy[k] = a1[4]; S.jz[k] = a1[5];
     S.ti[k] = tn;
-    // Aarseth: dt_c^2 = eta (|a| |a2| + |j|^2) / (|j| |a3| + |a2|^2); the level
-    // is the smallest k with (T 2^-k)^2 <= dt_c^2, found without the square
-    // root and the division on the dependent path
-    const double A2 = a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2];
-    const double J2 = a1[3] * a1[3] + a1[4] * a1[4] + a1[5] * a1[5];
-    const double B2 = a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2];
-    const double C2 = a3[0] * a3[0] + a3[1] * a3[1] + a3[2] * a3[2];
-    const double num = eta * (sqrt(A2 * B2) + J2);
-    const double den = sqrt(J2 * C2) + B2;
-    int kn = level_sq(num, den, T);
+    int kn = aarseth_level(a1, a2, a3, lv, eta, (float)(T * T));
     if (kn < lv) {
         const int up1 = lv - 1;
         kn = (tn % (1ll << (KMAX - up1)) == 0) ? up1 : lv;
@@ -343,6 +375,10 @@ struct HermArgs {
     double G, eps2, eta, eta_s, tau;
     int64_t max_steps;
 };
+
+__shared__ long long g_redl[32];
+__shared__ int g_wcnt[HTHREADS / 32];
+__shared__ int g_next_small;
 
 // Copy the member range [lo, hi) of arrays a..: from CTA `r` of the cluster
 // into this CTA's shared memory.
@@ -364,8 +400,11 @@ __device__ __forceinline__ void pull_range(cg::cluster_group &cl, const HermSmem
 // the same corrector, so the copies stay identical with one cluster barrier
 // per exchange round (partials double-buffered).
 template <bool COOP>
-__device__ __noinline__ void hermite_set(const Dev &d, const HermArgs &h, const HermSmem &S, int set, int rank,
-                            int cs, long long *redl, int *wcnt) {
+__device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set, int rank,
+                                         int cs) {
+    const HermSmem S = carve(g_hsmem);
+    long long *redl = g_redl;
+    int *wcnt = g_wcnt;
     cg::cluster_group cl = cg::this_cluster();
     const int64_t R = d.rows;
     const int tid = threadIdx.x;
@@ -505,27 +544,35 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs &h, const 
             const int NGA = HTHREADS / PA;
             const int ga = tid / PA, la = tid % PA;
             double *pbw = S.pb + buf * 6 * ACH;
-            // partial a, adot of the active members from this CTA's partners
+            // a, adot of the active members from this CTA's partners: complete
+            // on one CTA (corrected at once by the group's lane 0), partial
+            // on a cluster (exchanged below)
             for (int s0 = 0; s0 < nc; s0 += NGA) {
                 const int slot = s0 + ga;
                 const int k = slot < nc ? S.act[a0 + slot] : 0;
                 double a1[6] = {0, 0, 0, 0, 0, 0};
                 if (slot < nc) herm_part(S, mlo, mhi, k, la, PA, rank == 0, G, m0, tc, h.eps2, a1);
                 group_sum(a1, 6, PA);
-                if (slot < nc && la == 0)
-                    for (int c = 0; c < 6; ++c) pbw[c * ACH + slot] = a1[c];
-            }
-            if (COOP) cl.sync(); else __syncthreads();
-            // sum over the CTAs in rank order, correct (the same in every CTA)
-            for (int slot = tid; slot < nc; slot += blockDim.x) {
-                double a1[6] = {0, 0, 0, 0, 0, 0};
-                for (int r = 0; r < cs; ++r) {
-                    const double *pr = COOP ? cl.map_shared_rank(pbw, r) : pbw;
-                    for (int c = 0; c < 6; ++c) a1[c] += pr[c * ACH + slot];
+                if (slot < nc && la == 0) {
+                    if (COOP)
+                        for (int c = 0; c < 6; ++c) pbw[c * ACH + slot] = a1[c];
+                    else
+                        correct(S, k, a1, tn, sgn, tick, h.eta, T, inv_T);
                 }
-                correct(S, S.act[a0 + slot], a1, tn, sgn, tick, h.eta, T, inv_T);
             }
-            buf ^= 1;
+            if (COOP) {
+                cl.sync();
+                // sum over the CTAs in rank order, correct (the same in every CTA)
+                for (int slot = tid; slot < nc; slot += blockDim.x) {
+                    double a1[6] = {0, 0, 0, 0, 0, 0};
+                    for (int r = 0; r < cs; ++r) {
+                        const double *pr = cl.map_shared_rank(pbw, r);
+                        for (int c = 0; c < 6; ++c) a1[c] += pr[c * ACH + slot];
+                    }
+                    correct(S, S.act[a0 + slot], a1, tn, sgn, tick, h.eta, T, inv_T);
+                }
+                buf ^= 1;
+            }
         }
         ++steps;
     }
@@ -564,12 +611,7 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs &h, const 
 // Sets of at least NBIG members go to whole clusters (the i-th such set to
 // cluster i mod #clusters); the others are taken one CTA at a time in the
 // order of a counter, so CTAs freed early take more.
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(HTHREADS) k_hermite(Dev d, HermArgs h) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ long long redl[32];
-    __shared__ int wcnt[HTHREADS / 32];
-    __shared__ int next_small;
-    HermSmem S = carve(smem);
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(HTHREADS, 2) k_hermite(Dev d, HermArgs h) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
@@ -586,16 +628,16 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(HTHREADS) k_hermite
         const int n = d.set_start[set + 1] - d.set_start[set];
         if (n < big) continue;
         if (ib++ % ncl != cid) continue;
-        hermite_set<true>(d, h, S, set, rank, CL, redl, wcnt);
+        hermite_set<true>(d, h, set, rank, CL);
     }
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) next_small = (int)atomicAdd(d.ctr + C_HSMALL, 1ull);
+        if (threadIdx.x == 0) g_next_small = (int)atomicAdd(d.ctr + C_HSMALL, 1ull);
         __syncthreads();
-        const int set = next_small;
+        const int set = g_next_small;
         if (set >= nsets) break;
         if (d.set_start[set + 1] - d.set_start[set] >= big) continue;
-        hermite_set<false>(d, h, S, set, 0, 1, redl, wcnt);
+        hermite_set<false>(d, h, set, 0, 1);
     }
 }
 

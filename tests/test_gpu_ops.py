@@ -221,9 +221,10 @@ def test_transition_matches_oracle(torch, oracle):
     ref = np.array([oracle.transition(x, rc) for x in s])
     c = 0.5 * math.pi * 1.1 / rc
     K, Kp, Kpp = K.cpu().numpy(), Kp.cpu().numpy(), Kpp.cpu().numpy()
+    # a few ulp: the polynomial's rounding plus one or two products by c
     assert np.all(np.abs(K - ref[:, 0]) <= 4e-16)
-    assert np.all(np.abs(Kp - ref[:, 1]) <= 4e-16 * c)
-    assert np.all(np.abs(Kpp - ref[:, 2]) <= 4e-16 * c * c)
+    assert np.all(np.abs(Kp - ref[:, 1]) <= 6e-16 * c)
+    assert np.all(np.abs(Kpp - ref[:, 2]) <= 8e-16 * c * c)
     flat = (1.1 * s / rc - 0.1 <= 0) | (1.1 * s / rc - 0.1 >= 1)
     assert np.array_equal(K[flat], ref[flat, 0]) and np.all(Kp[flat] == 0) and np.all(Kpp[flat] == 0)
 
