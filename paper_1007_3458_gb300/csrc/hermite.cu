@@ -23,7 +23,7 @@
 namespace qym {
 namespace cg = cooperative_groups;
 
-constexpr int HCAP = 512;       // members per set held in shared memory
+constexpr int HCAP = 448;       // members per set held in shared memory
 constexpr int HTHREADS = 256;
 
 // sin and cos of (pi/2) y for y in [0, 1]: y > 1/2 is folded onto 1 - y
@@ -105,15 +105,21 @@ cudaError_t launch_transition(int64_t n, const double *s, double rc, double *K, 
 // through the stack of the per-set function)
 extern __shared__ __align__(16) unsigned char g_hsmem[];
 
-constexpr int CL = 8;      // CTAs of a cluster sharing one large set
-constexpr int NBIG = 24;   // sets of at least this many members use a whole cluster
-constexpr int ACH = 128;   // active members per partial-force exchange round
+constexpr int CL = 8;      // CTAs of a cluster sharing one large set (the tree sum below has 8 leaves)
+#ifndef QYM_HERM_NBIG
+#define QYM_HERM_NBIG 24
+#endif
+constexpr int NBIG = QYM_HERM_NBIG;  // sets of at least this many members use a whole cluster
+constexpr int ACH = 64;    // active members per force round (exchange, correction)
 
 struct HermSmem {
     double *ex, *ey, *ez, *eu, *ev, *ew, *m;  // evaluation point of every member
     double *x, *y, *z, *u, *v, *w;            // state at the member's own time
     double *ax, *ay, *az, *jx, *jy, *jz;      // a, adot at the member's own time
-    double *pb;                               // partial a, adot [2][6][ACH]
+    double *pb;                               // partial a, adot [2][6][ACH] (cluster exchange)
+    double *pr;                               // per-lane partial a, adot [6][HTHREADS]
+    double *a1s;                              // a, adot of the round's active members [6][ACH]
+    float *cf;                                // step criterion inputs [12][ACH]
     long long *ti;                            // member time in ticks
     int32_t *lev;                             // member level: step = tau 2^-lev
     int32_t *act;                             // members whose step ends now
@@ -131,15 +137,19 @@ __device__ __forceinline__ HermSmem carve(void *base) {
     s.ax = p; p += HCAP; s.ay = p; p += HCAP; s.az = p; p += HCAP;
     s.jx = p; p += HCAP; s.jy = p; p += HCAP; s.jz = p; p += HCAP;
     s.pb = p; p += 2 * 6 * ACH;
+    s.pr = p; p += 6 * HTHREADS;
+    s.a1s = p; p += 6 * ACH;
     s.ti = (long long *)p; p += HCAP;
-    int32_t *ip = (int32_t *)p;
+    float *fp = (float *)p;
+    s.cf = fp; fp += 12 * ACH;
+    int32_t *ip = (int32_t *)fp;
     s.lev = ip; ip += HCAP;
     s.act = ip; ip += HCAP;
     s.ids = ip;
     return s;
 }
-constexpr size_t kHermSmem =
-    sizeof(double) * (HCAP * 20 + 2 * 6 * ACH) + sizeof(int32_t) * HCAP * 3;
+constexpr size_t kHermSmem = sizeof(double) * (HCAP * 20 + 2 * 6 * ACH + 6 * HTHREADS + 6 * ACH) +
+                             sizeof(float) * 12 * ACH + sizeof(int32_t) * HCAP * 3;
 constexpr int KMAX = 48;
 
 // smallest k with T 2^-k <= dt_c, in [0, KMAX]: with T = fT 2^eT and
@@ -371,6 +381,104 @@ __device__ __forceinline__ void correct(const HermSmem &S, int k, const double *
     S.lev[k] = kn;
 }
 
+// 2^e as a double, -1022 <= e <= 1023 (from the bits: no FP64 instruction)
+__device__ __forceinline__ double pow2d(int e) {
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// v 2^s as a float, the mantissa truncated, by integer operations on the bits
+// (no FP64 instruction): signed zero below the float normal range, +-FLT_MAX
+// above it. Used only for the step-size criterion.
+__device__ __forceinline__ float to_float_scaled(double v, int s) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int eb = (int)((b >> 52) & 0x7ff);
+    if (eb == 0) return __uint_as_float(sign);
+    const int e = eb - 1023 + s;
+    if (e < -126) return __uint_as_float(sign);
+    if (e > 127) return __uint_as_float(sign | 0x7f7fffffu);
+    return __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+}
+
+// The level from the criterion's inputs as floats f[c * ACH] (stride ACH):
+// a (3), j g (3), a2 g^2 (3), a3 g^3 (3), g = 2^-lv; see aarseth_level
+__device__ __forceinline__ int level_from(const float *f, int lv, float eta, float T2) {
+    float q[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const float x = f[(3 * g) * ACH], y = f[(3 * g + 1) * ACH], z = f[(3 * g + 2) * ACH];
+        q[g] = sqrtf(fmaf(x, x, fmaf(y, y, z * z)));
+    }
+    const float num = eta * fmaf(q[0], q[2], q[1] * q[1]);
+    const float den = fmaf(q[1], q[3], q[2] * q[2]);
+    if (!(den > 0.0f)) return 0;
+    if (!(num > 0.0f)) return KMAX;
+    const float r = num / den;
+    if (!(r < INFINITY)) return 0;
+    int er, et;
+    const float fr = frexpf(r, &er), ft = frexpf(T2, &et);
+    const int dd = er - et;
+    const int m = (dd & 1) ? (dd - 1) >> 1 : ((ft <= fr) ? dd >> 1 : (dd >> 1) - 1);
+    const int k = lv - m;
+    return k < 0 ? 0 : (k > KMAX ? KMAX : k);
+}
+
+// component c of member k predicted from its own time to tn
+__device__ __forceinline__ void predict_c(const HermSmem &S, int k, int c, long long tn,
+                                          double stick) {
+    const double hs = (double)(tn - S.ti[k]) * stick;
+    const double h6 = hs * (1.0 / 6.0);
+    double *x = c == 0 ? S.x : (c == 1 ? S.y : S.z);
+    double *u = c == 0 ? S.u : (c == 1 ? S.v : S.w);
+    double *a = c == 0 ? S.ax : (c == 1 ? S.ay : S.az);
+    double *j = c == 0 ? S.jx : (c == 1 ? S.jy : S.jz);
+    double *ex = c == 0 ? S.ex : (c == 1 ? S.ey : S.ez);
+    double *eu = c == 0 ? S.eu : (c == 1 ? S.ev : S.ew);
+    const double ak = a[k], jk = j[k], uk = u[k];
+    ex[k] = x[k] + hs * (uk + hs * (0.5 * ak + h6 * jk));
+    eu[k] = uk + hs * (ak + 0.5 * hs * jk);
+}
+
+// Hermite a, adot of member k from one item: partner mlo + item of this
+// CTA's range, or the star for item == npart (with `star`)
+__device__ __forceinline__ void herm_item(const HermSmem &S, int k, int item, int mlo, int npart,
+                                          bool star, double G, double m0, const TransC &tc,
+                                          double eps2, double *aj) {
+    const double xk = S.ex[k], yk = S.ey[k], zk = S.ez[k];
+    const double uk = S.eu[k], vk = S.ev[k], wk = S.ew[k];
+    if (item == npart) {
+        if (!star) return;
+        double s2 = xk * xk + yk * yk + zk * zk + eps2;
+        double si = rsqrt(s2);
+        double si2 = si * si;
+        double rv = xk * uk + yk * vk + zk * wk;
+        double c = -G * m0 * (si2 * si);
+        double t = 3.0 * rv * si2;
+        aj[0] += c * xk; aj[1] += c * yk; aj[2] += c * zk;
+        aj[3] += c * (uk - t * xk); aj[4] += c * (vk - t * yk); aj[5] += c * (wk - t * zk);
+        return;
+    }
+    const int l = mlo + item;
+    if (l == k) return;
+    double qx = xk - S.ex[l], qy = yk - S.ey[l], qz = zk - S.ez[l];
+    double q2 = qx * qx + qy * qy + qz * qz + eps2;
+    if (q2 >= tc.rc2) return;  // K = 1, K' = K'' = 0: no force, no jerk
+    double px = uk - S.eu[l], py = vk - S.ev[l], pz = wk - S.ew[l];
+    const double qi = rsqrt(q2);
+    const double qi2 = qi * qi;
+    const double sq = q2 * qi;
+    double K, Kp, Kpp;
+    transition(sq, tc, K, Kp, Kpp);
+    double br = 1.0 - K + sq * Kp;
+    double rvl = qx * px + qy * py + qz * pz;
+    double cl = -G * S.m[l] * (qi2 * qi);
+    double tl = 3.0 * rvl * qi2;
+    aj[0] += cl * br * qx; aj[1] += cl * br * qy; aj[2] += cl * br * qz;
+    aj[3] += cl * (rvl * qx * Kpp + (px - tl * qx) * br);
+    aj[4] += cl * (rvl * qy * Kpp + (py - tl * qy) * br);
+    aj[5] += cl * (rvl * qz * Kpp + (pz - tl * qz) * br);
+}
+
 struct HermArgs {
     double G, eps2, eta, eta_s, tau;
     int64_t max_steps;
@@ -442,8 +550,8 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
         if (k < n) S.ids[myrank[c]] = myid[c];
     }
     __syncthreads();
-    const int64_t star = d.offsets[d.sys_of[S.ids[0]]];
-    const double m0 = d.m[star];
+    const int64_t star_row = d.offsets[d.sys_of[S.ids[0]]];
+    const double m0 = d.m[star_row];
     const TransC tc(d.rcrit[set]);
     const double G = h.G, tau = h.tau;
     // state entering the Kepler drift (after the first kick)
@@ -518,6 +626,19 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
         }
         cl.sync();
     }
+    // Block steps. FP64 instructions are issued at about one warp-instruction
+    // per 64 cycles per SM sub-partition here, whatever the number of active
+    // lanes, so the work is split by instruction stream across warps (which
+    // the sub-partitions serve in parallel): one warp per coordinate for the
+    // predictor and the corrector, several warps per member for the forces,
+    // one warp per (member, component) for the sums.
+    const int warp = tid >> 5, wl = tid & 31;
+    const double stick = sgn * tick;
+    const double T2d = T * T, T3 = T2d * T, T4 = T3 * T;
+    const double iT2 = inv_T * inv_T, iT3 = iT2 * inv_T;
+    const float T2f = (float)T2d, etaf = (float)h.eta;
+    const int npart = mhi - mlo;
+    const bool with_star = rank == 0;
     int64_t steps = 0;
     bool capped = false;
     int buf = 0;
@@ -531,47 +652,114 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
         if (tn > TT) break;  // every member has reached tau
         if (steps >= h.max_steps) { capped = true; break; }
         const int na = active_list(S, n, tn, wcnt);
-        // predict the partners of this CTA and the active members to tn
-        for (int k = mlo + tid; k < mhi; k += blockDim.x) predict(S, k, tn, sgn, tick);
-        for (int a = tid; a < na; a += blockDim.x) {
-            const int k = S.act[a];
-            if (k < mlo || k >= mhi) predict(S, k, tn, sgn, tick);
+        // predict this CTA's partners and the active members to tn
+        if (warp < 3) {
+            for (int i = wl; i < npart + na; i += 32) {
+                int k = mlo + i;
+                if (i >= npart) {
+                    k = S.act[i - npart];
+                    if (k >= mlo && k < mhi) continue;
+                }
+                predict_c(S, k, warp, tn, stick);
+            }
         }
         __syncthreads();
         for (int a0 = 0; a0 < na; a0 += ACH) {
             const int nc = min(ACH, na - a0);
-            const int PA = lanes_per_member(nc, mhi - mlo);
-            const int NGA = HTHREADS / PA;
-            const int ga = tid / PA, la = tid % PA;
-            double *pbw = S.pb + buf * 6 * ACH;
-            // a, adot of the active members from this CTA's partners: complete
-            // on one CTA (corrected at once by the group's lane 0), partial
-            // on a cluster (exchanged below)
-            for (int s0 = 0; s0 < nc; s0 += NGA) {
-                const int slot = s0 + ga;
-                const int k = slot < nc ? S.act[a0 + slot] : 0;
-                double a1[6] = {0, 0, 0, 0, 0, 0};
-                if (slot < nc) herm_part(S, mlo, mhi, k, la, PA, rank == 0, G, m0, tc, h.eps2, a1);
-                group_sum(a1, 6, PA);
-                if (slot < nc && la == 0) {
-                    if (COOP)
-                        for (int c = 0; c < 6; ++c) pbw[c * ACH + slot] = a1[c];
-                    else
-                        correct(S, k, a1, tn, sgn, tick, h.eta, T, inv_T);
+            // items per member: the partners and (rank 0) the star
+            const int nitem = npart + (with_star ? 1 : 0);
+            int LA = 1;
+            while (LA < nitem && LA < 128) LA <<= 1;
+            const int NG = HTHREADS / LA;
+            double *dst = COOP ? S.pb + buf * 6 * ACH : S.a1s;
+            for (int s0 = 0; s0 < nc; s0 += NG) {
+                const int slot = s0 + tid / LA, la = tid % LA;
+                double aj[6] = {0, 0, 0, 0, 0, 0};
+                if (slot < nc) {
+                    const int k = S.act[a0 + slot];
+                    for (int it = la; it < nitem; it += LA)
+                        herm_item(S, k, it, mlo, npart, with_star, G, m0, tc, h.eps2, aj);
                 }
+#pragma unroll
+                for (int c = 0; c < 6; ++c) S.pr[c * HTHREADS + tid] = aj[c];
+                __syncthreads();
+                // sums over the LA lanes of each (member, component), one warp
+                // each, in a fixed order
+                const int cnt = min(NG, nc - s0);
+                for (int pi = warp; pi < 6 * cnt; pi += HTHREADS / 32) {
+                    const int sl = pi / 6, c = pi - 6 * sl;
+                    const double *col = S.pr + c * HTHREADS + sl * LA;
+                    double v = 0.0;
+                    for (int m = wl; m < LA; m += 32) v += col[m];
+                    for (int off = (LA < 32 ? LA : 32) >> 1; off > 0; off >>= 1)
+                        v += __shfl_xor_sync(0xffffffffu, v, off);
+                    if (wl == 0) dst[c * ACH + s0 + sl] = v;
+                }
+                __syncthreads();
             }
             if (COOP) {
                 cl.sync();
-                // sum over the CTAs in rank order, correct (the same in every CTA)
-                for (int slot = tid; slot < nc; slot += blockDim.x) {
-                    double a1[6] = {0, 0, 0, 0, 0, 0};
-                    for (int r = 0; r < cs; ++r) {
-                        const double *pr = cl.map_shared_rank(pbw, r);
-                        for (int c = 0; c < 6; ++c) a1[c] += pr[c * ACH + slot];
+                // the CTAs' partial sums in rank order, one warp per coordinate
+                if (warp < 3) {
+                    for (int sl = wl; sl < nc; sl += 32) {
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const int c = warp + 3 * q;
+                            double pv[CL];
+#pragma unroll
+                            for (int r = 0; r < CL; ++r) pv[r] = cl.map_shared_rank(dst, r)[c * ACH + sl];
+                            S.a1s[c * ACH + sl] = ((pv[0] + pv[1]) + (pv[2] + pv[3])) +
+                                                  ((pv[4] + pv[5]) + (pv[6] + pv[7]));
+                        }
                     }
-                    correct(S, S.act[a0 + slot], a1, tn, sgn, tick, h.eta, T, inv_T);
                 }
                 buf ^= 1;
+            }
+            // corrector, one warp per coordinate (the same in every CTA)
+            if (warp < 3) {
+                const int c = warp;
+                double *xa = c == 0 ? S.x : (c == 1 ? S.y : S.z);
+                double *ua = c == 0 ? S.u : (c == 1 ? S.v : S.w);
+                double *aa = c == 0 ? S.ax : (c == 1 ? S.ay : S.az);
+                double *ja = c == 0 ? S.jx : (c == 1 ? S.jy : S.jz);
+                const double *ea = c == 0 ? S.ex : (c == 1 ? S.ey : S.ez);
+                const double *fa = c == 0 ? S.eu : (c == 1 ? S.ev : S.ew);
+                for (int sl = wl; sl < nc; sl += 32) {
+                    const int k = S.act[a0 + sl];
+                    const int lv = S.lev[k];
+                    const double hs = sgn * T * pow2d(-lv);
+                    const double ih2 = iT2 * pow2d(2 * lv), ih3 = sgn * iT3 * pow2d(3 * lv);
+                    const double h3 = sgn * T3 * pow2d(-3 * lv), h4 = T4 * pow2d(-4 * lv);
+                    const double a1c = S.a1s[c * ACH + sl], j1c = S.a1s[(3 + c) * ACH + sl];
+                    const double d = aa[k] - a1c, j0c = ja[k];
+                    double a2 = (-6.0 * d - hs * (4.0 * j0c + 2.0 * j1c)) * ih2;
+                    const double a3 = (12.0 * d + 6.0 * hs * (j0c + j1c)) * ih3;
+                    xa[k] = ea[k] + h4 * (a2 * (1.0 / 24.0) + hs * a3 * (1.0 / 120.0));
+                    ua[k] = fa[k] + h3 * (a2 * (1.0 / 6.0) + hs * a3 * (1.0 / 24.0));
+                    aa[k] = a1c;
+                    ja[k] = j1c;
+                    a2 += hs * a3;
+                    S.cf[c * ACH + sl] = to_float_scaled(a1c, 0);
+                    S.cf[(3 + c) * ACH + sl] = to_float_scaled(j1c, -lv);
+                    S.cf[(6 + c) * ACH + sl] = to_float_scaled(a2, -2 * lv);
+                    S.cf[(9 + c) * ACH + sl] = to_float_scaled(a3, -3 * lv);
+                }
+            }
+            __syncthreads();
+            // new time and level by the Aarseth criterion (FP32 on scaled
+            // inputs); a larger step only by one level and on a commensurate time
+            if (warp == 3) {
+                for (int sl = wl; sl < nc; sl += 32) {
+                    const int k = S.act[a0 + sl];
+                    const int lv = S.lev[k];
+                    int kn = level_from(S.cf + sl, lv, etaf, T2f);
+                    if (kn < lv) {
+                        const int up1 = lv - 1;
+                        kn = (tn & ((1ll << (KMAX - up1)) - 1)) == 0 ? up1 : lv;
+                    }
+                    S.lev[k] = kn;
+                    S.ti[k] = tn;
+                }
             }
         }
         ++steps;
