@@ -242,145 +242,6 @@ __device__ void herm_part(const HermSmem &S, int lo, int hi, int k, int l0, int 
     }
 }
 
-__device__ __forceinline__ long long block_min_ll(long long x, long long *red) {
-    for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
-    int w = threadIdx.x >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = x;
-    __syncthreads();
-    long long r = red[0];
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) r = min(r, red[k]);
-    return r;
-}
-
-// Members whose step ends at tn, listed in ascending member order (the same
-// list in every CTA of a cluster); returns their number.
-__device__ int active_list(const HermSmem &S, int n, long long tn, int *wcnt) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = HTHREADS / 32;
-    int base = 0;
-    for (int c0 = 0; c0 < n; c0 += HTHREADS) {
-        const int k = c0 + threadIdx.x;
-        const bool f = k < n && S.ti[k] + (1ll << (KMAX - S.lev[k])) == tn;
-        const unsigned b = __ballot_sync(0xffffffffu, f);
-        __syncthreads();
-        if (lane == 0) wcnt[w] = __popc(b);
-        __syncthreads();
-        int before = 0, tot = 0;
-        for (int q = 0; q < nw; ++q) {
-            before += q < w ? wcnt[q] : 0;
-            tot += wcnt[q];
-        }
-        if (f) S.act[base + before + __popc(b & ((1u << lane) - 1u))] = k;
-        base += tot;
-    }
-    __syncthreads();
-    return base;
-}
-
-// state of member k predicted from its own time to tn (Hermite predictor)
-__device__ __forceinline__ void predict(const HermSmem &S, int k, long long tn, double sgn,
-                                        double tick) {
-    const double hs = sgn * (double)(tn - S.ti[k]) * tick;
-    const double h6 = hs * (1.0 / 6.0);
-    S.ex[k] = S.x[k] + hs * (S.u[k] + hs * (0.5 * S.ax[k] + h6 * S.jx[k]));
-    S.ey[k] = S.y[k] + hs * (S.v[k] + hs * (0.5 * S.ay[k] + h6 * S.jy[k]));
-    S.ez[k] = S.z[k] + hs * (S.w[k] + hs * (0.5 * S.az[k] + h6 * S.jz[k]));
-    S.eu[k] = S.u[k] + hs * (S.ax[k] + 0.5 * hs * S.jx[k]);
-    S.ev[k] = S.v[k] + hs * (S.ay[k] + 0.5 * hs * S.jy[k]);
-    S.ew[k] = S.w[k] + hs * (S.az[k] + 0.5 * hs * S.jz[k]);
-}
-
-// Level after a step of level lv by the Aarseth criterion,
-// dt_c^2 = eta (|a| |a2| + |j|^2) / (|j| |a3| + |a2|^2), from a = a1[0..2],
-// j = a1[3..5] and the corrector's a2, a3: the smallest k with
-// T 2^-k <= dt_c. With g = 2^-lv, j g, a2 g^2, a3 g^3 are all accelerations
-// times T^0, T^-1, ... scaled alike, and r = eta (|a||a2 g^2| + |j g|^2) /
-// (|j g||a3 g^3| + |a2 g^2|^2) = (dt_c / (T g))^2 T^2, so T 2^-k <= dt_c is
-// T^2 4^(lv - k) <= r. The powers of g and one common power of two that brings
-// every component below 1 are applied exactly through the exponents, and the
-// rest runs in FP32 (an FP64 operation's latency here is fifteen FP32 ones).
-// It only picks a power of two: a different level than an FP64 evaluation
-// needs dt_c within ~1e-7 of a level boundary.
-__device__ __forceinline__ int aarseth_level(const double *a1, const double *a2, const double *a3,
-                                             int lv, double eta, float T2) {
-    const double *src[4] = {a1, a1 + 3, a2, a3};
-    int ex[12], emax = 0;
-    for (int g = 0; g < 4; ++g)
-        for (int c = 0; c < 3; ++c) {
-            const long long bits = __double_as_longlong(src[g][c]);
-            const int eb = (int)((bits >> 52) & 0x7ff);
-            if (eb == 0x7ff) return lv;            // not finite: keep the level
-            ex[3 * g + c] = eb == 0 ? -100000 : eb - g * lv;   // biased, after g^g
-            emax = max(emax, ex[3 * g + c]);
-        }
-    if (emax <= -100000) return KMAX;              // a = j = a2 = a3 = 0
-    float f[12];
-    for (int g = 0; g < 4; ++g)
-        for (int c = 0; c < 3; ++c) {
-            // v 2^(-g lv) 2^-(emax - 1022): below 1 in magnitude, exact
-            const int sh = -g * lv - (emax - 1022);   // <= 1021 (emax >= 1)
-            const double scale =
-                sh < -1022 ? 0.0 : __longlong_as_double((long long)(sh + 1023) << 52);
-            f[3 * g + c] = (float)(src[g][c] * scale);
-        }
-    const float A2 = fmaf(f[0], f[0], fmaf(f[1], f[1], f[2] * f[2]));
-    const float J2 = fmaf(f[3], f[3], fmaf(f[4], f[4], f[5] * f[5]));
-    const float B2 = fmaf(f[6], f[6], fmaf(f[7], f[7], f[8] * f[8]));
-    const float C2 = fmaf(f[9], f[9], fmaf(f[10], f[10], f[11] * f[11]));
-    const float num = (float)eta * (sqrtf(A2 * B2) + J2);
-    const float den = sqrtf(J2 * C2) + B2;
-    if (!(den > 0.0f)) return 0;          // dt_c = infinity: the largest step
-    if (!(num > 0.0f)) return KMAX;
-    const float r = num / den;
-    if (!(r < INFINITY)) return 0;
-    // smallest k in [0, KMAX] with T^2 4^m <= r, m = lv - k: with
-    // r = fr 2^er and T^2 = ft 2^et (fr, ft in [1/2, 1)) and d = er - et, the
-    // largest such m is (d - 1) / 2 for odd d, d / 2 when ft <= fr for even d,
-    // else d / 2 - 1
-    int er, et;
-    const float fr = frexpf(r, &er), ft = frexpf(T2, &et);
-    const int dd = er - et;
-    const int m = (dd & 1) ? (dd - 1) >> 1 : ((ft <= fr) ? dd >> 1 : (dd >> 1) - 1);
-    int k = lv - m;
-    return k < 0 ? 0 : (k > KMAX ? KMAX : k);
-}
-
-// Hermite corrector of member k at the end of its step (new a, adot in a1),
-// then its new level by the Aarseth criterion: a larger step only by one
-// level and on a time commensurate with it
-__device__ __forceinline__ void correct(const HermSmem &S, int k, const double *a1, long long tn,
-                                        double sgn, double tick, double eta, double T,
-                                        double inv_T) {
-    const int lv = S.lev[k];
-    const double hs = sgn * ldexp(T, -lv);           // exact: T 2^-lev
-    const double ih = sgn * ldexp(inv_T, lv);        // 1 / hs up to the rounding of 1/T
-    double a0[3] = {S.ax[k], S.ay[k], S.az[k]};
-    double j0[3] = {S.jx[k], S.jy[k], S.jz[k]};
-    double e[3] = {S.ex[k], S.ey[k], S.ez[k]};
-    double f[3] = {S.eu[k], S.ev[k], S.ew[k]};
-    double a2[3], a3[3], xn[3], un[3];
-    const double ih2 = ih * ih, ih3 = ih2 * ih;
-    const double h3 = hs * hs * hs, h4 = h3 * hs;
-    for (int c = 0; c < 3; ++c) {
-        a2[c] = (-6.0 * (a0[c] - a1[c]) - hs * (4.0 * j0[c] + 2.0 * a1[3 + c])) * ih2;
-        a3[c] = (12.0 * (a0[c] - a1[c]) + 6.0 * hs * (j0[c] + a1[3 + c])) * ih3;
-        xn[c] = e[c] + h4 * (a2[c] * (1.0 / 24.0) + hs * a3[c] * (1.0 / 120.0));
-        un[c] = f[c] + h3 * (a2[c] * (1.0 / 6.0) + hs * a3[c] * (1.0 / 24.0));
-        a2[c] += hs * a3[c];
-    }
-    S.x[k] = xn[0]; S.y[k] = xn[1]; S.z[k] = xn[2];
-    S.u[k] = un[0]; S.v[k] = un[1]; S.w[k] = un[2];
-    S.ax[k] = a1[0]; S.ay[k] = a1[1]; S.az[k] = a1[2];
-    S.jx[k] = a1[3]; S.jy[k] = a1[4]; S.jz[k] = a1[5];
-    S.ti[k] = tn;
-    int kn = aarseth_level(a1, a2, a3, lv, eta, (float)(T * T));
-    if (kn < lv) {
-        const int up1 = lv - 1;
-        kn = (tn % (1ll << (KMAX - up1)) == 0) ? up1 : lv;
-    }
-    S.lev[k] = kn;
-}
-
 // 2^e as a double, -1022 <= e <= 1023 (from the bits: no FP64 instruction)
 __device__ __forceinline__ double pow2d(int e) {
     return __longlong_as_double((long long)(e + 1023) << 52);
@@ -400,8 +261,19 @@ __device__ __forceinline__ float to_float_scaled(double v, int s) {
     return __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
 }
 
-// The level from the criterion's inputs as floats f[c * ACH] (stride ACH):
-// a (3), j g (3), a2 g^2 (3), a3 g^3 (3), g = 2^-lv; see aarseth_level
+// Step levels by the Aarseth criterion,
+// dt_c^2 = eta (|a| |a2| + |j|^2) / (|j| |a3| + |a2|^2), with a, j the new
+// acceleration and jerk and a2, a3 the corrector's derivatives: the new level
+// is the smallest k with T 2^-k <= dt_c. With g = 2^-lv (lv the level of the
+// step just taken), j g, a2 g^2 and a3 g^3 are accelerations scaled alike and
+// r = eta (|a||a2 g^2| + |j g|^2) / (|j g||a3 g^3| + |a2 g^2|^2) =
+// (dt_c / (T g))^2 T^2, so T 2^-k <= dt_c is T^2 4^(lv - k) <= r. The powers
+// of g are applied exactly through the exponents when the inputs are cut to
+// FP32, and the criterion runs in FP32 (an FP64 operation costs about fifteen
+// FP32 ones here). It only picks a power of two: a level different from an
+// FP64 evaluation needs dt_c within ~1e-7 of a level boundary.
+// level_from: that level from the criterion's inputs as floats f[c * ACH]
+// (stride ACH): a (3), j g (3), a2 g^2 (3), a3 g^3 (3)
 __device__ __forceinline__ int level_from(const float *f, int lv, float eta, float T2) {
     float q[4];
 #pragma unroll
@@ -484,9 +356,33 @@ struct HermArgs {
     int64_t max_steps;
 };
 
-__shared__ long long g_redl[32];
-__shared__ int g_wcnt[HTHREADS / 32];
 __shared__ int g_next_small;
+__shared__ long long g_tn;
+__shared__ int g_na;
+
+// Next block time (the earliest end of a member's step) and the members whose
+// step ends then, in member order, by warp 0 alone; every thread reads
+// (tn, na) after the barrier that follows.
+__device__ __forceinline__ void next_block(const int32_t *lev, const long long *ti, int32_t *act,
+                                           int n) {
+    const int wl = threadIdx.x & 31;
+    long long t = LLONG_MAX;
+    for (int k = wl; k < n; k += 32) t = min(t, ti[k] + (1ll << (48 - lev[k])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = min(t, __shfl_xor_sync(0xffffffffu, t, o));
+    int na = 0;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const int k = k0 + wl;
+        const bool f = k < n && ti[k] + (1ll << (48 - lev[k])) == t;
+        const unsigned b = __ballot_sync(0xffffffffu, f);
+        if (f) act[na + __popc(b & ((1u << wl) - 1u))] = k;
+        na += __popc(b);
+    }
+    if (wl == 0) {
+        g_tn = t;
+        g_na = na;
+    }
+}
 
 // Copy the member range [lo, hi) of arrays a..: from CTA `r` of the cluster
 // into this CTA's shared memory.
@@ -511,8 +407,6 @@ template <bool COOP>
 __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set, int rank,
                                          int cs) {
     const HermSmem S = carve(g_hsmem);
-    long long *redl = g_redl;
-    int *wcnt = g_wcnt;
     cg::cluster_group cl = cg::this_cluster();
     const int64_t R = d.rows;
     const int tid = threadIdx.x;
@@ -644,14 +538,12 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
     int buf = 0;
     for (;;) {
         __syncthreads();
-        // next block time: the earliest end of a member's step
-        long long tn_l = LLONG_MAX;
-        for (int k = tid; k < n; k += blockDim.x)
-            tn_l = min(tn_l, S.ti[k] + (1ll << (KMAX - S.lev[k])));
-        const long long tn = block_min_ll(tn_l, redl);
+        if (warp == 0) next_block(S.lev, S.ti, S.act, n);
+        __syncthreads();
+        const long long tn = g_tn;
         if (tn > TT) break;  // every member has reached tau
         if (steps >= h.max_steps) { capped = true; break; }
-        const int na = active_list(S, n, tn, wcnt);
+        const int na = g_na;
         // predict this CTA's partners and the active members to tn
         if (warp < 3) {
             for (int i = wl; i < npart + na; i += 32) {
@@ -666,19 +558,24 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
         __syncthreads();
         for (int a0 = 0; a0 < na; a0 += ACH) {
             const int nc = min(ACH, na - a0);
-            // items per member: the partners and (rank 0) the star
-            const int nitem = npart + (with_star ? 1 : 0);
+            // pair items on warps 0-6 (LA lanes per member), the star's pull
+            // (rank 0) on warp 7, so neither path diverges inside a warp
             int LA = 1;
-            while (LA < nitem && LA < 128) LA <<= 1;
-            const int NG = HTHREADS / LA;
+            while (LA < npart && LA < 64) LA <<= 1;
+            const int NG = min(32, (HTHREADS - 32) / LA);  // warp 7 holds one star per slot
             double *dst = COOP ? S.pb + buf * 6 * ACH : S.a1s;
             for (int s0 = 0; s0 < nc; s0 += NG) {
-                const int slot = s0 + tid / LA, la = tid % LA;
                 double aj[6] = {0, 0, 0, 0, 0, 0};
-                if (slot < nc) {
-                    const int k = S.act[a0 + slot];
-                    for (int it = la; it < nitem; it += LA)
-                        herm_item(S, k, it, mlo, npart, with_star, G, m0, tc, h.eps2, aj);
+                if (warp < 7) {
+                    const int slot = s0 + tid / LA, la = tid % LA;
+                    if (slot < nc) {
+                        const int k = S.act[a0 + slot];
+                        for (int it = la; it < npart; it += LA)
+                            herm_item(S, k, it, mlo, npart, false, G, m0, tc, h.eps2, aj);
+                    }
+                } else if (with_star && wl < min(NG, nc - s0)) {
+                    herm_item(S, S.act[a0 + s0 + wl], npart, mlo, npart, true, G, m0, tc, h.eps2,
+                              aj);
                 }
 #pragma unroll
                 for (int c = 0; c < 6; ++c) S.pr[c * HTHREADS + tid] = aj[c];
@@ -693,27 +590,25 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                     for (int m = wl; m < LA; m += 32) v += col[m];
                     for (int off = (LA < 32 ? LA : 32) >> 1; off > 0; off >>= 1)
                         v += __shfl_xor_sync(0xffffffffu, v, off);
-                    if (wl == 0) dst[c * ACH + s0 + sl] = v;
+                    if (wl == 0) dst[c * ACH + s0 + sl] = v + S.pr[c * HTHREADS + 224 + sl];
                 }
                 __syncthreads();
             }
             if (COOP) {
                 cl.sync();
-                // the CTAs' partial sums in rank order, one warp per coordinate
-                if (warp < 3) {
+                // the CTAs' partial sums in rank order, one warp per component
+                if (warp < 6) {
+                    const int c = warp;
                     for (int sl = wl; sl < nc; sl += 32) {
+                        double pv[CL];
 #pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            const int c = warp + 3 * q;
-                            double pv[CL];
-#pragma unroll
-                            for (int r = 0; r < CL; ++r) pv[r] = cl.map_shared_rank(dst, r)[c * ACH + sl];
-                            S.a1s[c * ACH + sl] = ((pv[0] + pv[1]) + (pv[2] + pv[3])) +
-                                                  ((pv[4] + pv[5]) + (pv[6] + pv[7]));
-                        }
+                        for (int r = 0; r < CL; ++r) pv[r] = cl.map_shared_rank(dst, r)[c * ACH + sl];
+                        S.a1s[c * ACH + sl] = ((pv[0] + pv[1]) + (pv[2] + pv[3])) +
+                                              ((pv[4] + pv[5]) + (pv[6] + pv[7]));
                     }
                 }
                 buf ^= 1;
+                __syncthreads();
             }
             // corrector, one warp per coordinate (the same in every CTA)
             if (warp < 3) {
