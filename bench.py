@@ -58,6 +58,44 @@ def _workload(name):
     return getattr(W, fn)(), desc
 
 
+def rank_workload(name, rank, world, **kw):
+    """The workload one rank integrates. The ensemble's systems are independent
+    problems: with several ranks each rank draws its own batch of the same
+    shape (seed 3 + 1000 rank; rank 0 keeps the reference batch), so the work
+    per GPU is fixed (weak scaling) and no data crosses ranks. A single system
+    has no multi-GPU split here: every rank integrates a replica."""
+    from paper_1007_3458_gb300 import workloads as W
+    fn, desc = WORKLOADS[name]
+    if fn == "ensemble" and world > 1:
+        kw = dict(kw, seed=kw.get("seed", 3) + 1000 * rank)
+        return getattr(W, fn)(**kw), desc + f" (rank {rank}: seed {kw['seed']})"
+    return getattr(W, fn)(**kw), desc
+
+
+def sum_over_ranks(x, device="cpu"):
+    """Sum of x over the ranks of the default process group (x with one
+    rank): the units all ranks processed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def max_over_ranks(x, device="cpu"):
+    """Largest x over the ranks of the default process group (x itself with
+    one rank): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -225,7 +263,7 @@ def run_ours(args):
     dev = torch.cuda.current_device()
     import paper_1007_3458_gb300 as q
     q.build()
-    w, desc = _workload(args.workload)
+    w, desc = rank_workload(args.workload, rank, ws)
     prec = q.QYM_KICK_MIXED if args.prec == "mixed" else q.QYM_KICK_FP64
     # every step starts by writing 256 MB (twice the 129 MB L2), inside the
     # timed region, so no step reuses the previous step's lines
@@ -260,17 +298,13 @@ def run_ours(args):
         sim.step(w.tau, args.steps)
         e1.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), "cuda")
     st = sim.stats()
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     nb = w.n_bodies
-    value = nb * args.steps * ws / (ms / 1e3)
+    nb_all = sum_over_ranks(nb, "cuda")
+    value = nb_all * args.steps / (ms / 1e3)
     pairs = w.pairs_per_kick()
-    gpair = 2 * pairs * args.steps * ws / (ms / 1e3) / 1e9
+    gpair = 2 * sum_over_ranks(pairs, "cuda") * args.steps / (ms / 1e3) / 1e9
 
     # dominant kernel: the all-pairs kick, timed alone on the same stream
     reps = 20
@@ -300,8 +334,8 @@ def run_ours(args):
         sim.step(w.tau, 1)
         qh, vh = q.qym_get_state(sim.ctx, qh, vh)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": nb * e2e_steps * ws / e2e_s, "unit": METRIC,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
+    e2e = {"value": nb_all * e2e_steps / e2e_s, "unit": METRIC,
            "h2d_bytes_per_step": int(qh.nbytes + vh.nbytes),
            "d2h_bytes_per_step": int(qh.nbytes + vh.nbytes),
            "steps": e2e_steps, "what": "qym_set_state + qym_step(tau, 1) + qym_get_state per step"}
@@ -314,6 +348,9 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "fp32-pair/f64-state" if prec else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "kick": args.prec,
+                       "parallelism": ("independent batches per rank" if ws > 1 and
+                                       WORKLOADS[args.workload][0] == "ensemble" else
+                                       "replicas" if ws > 1 else "single GPU"),
                        "tau": w.tau, "bodies": nb, "eps_H": w.eps_H,
                        "l2": "flushed: 256 MB written at the start of every step, inside the timed region"},
             "gpair_per_s": gpair, "stats": st, "gpu_launches": int(st["launches"]),

@@ -232,4 +232,4 @@ def test_ensemble_full_size_sampled(gpu, oracle):
         spread = _chaos_spread(oracle, ws, 3)
         keep = np.array([i not in skip for i in range(b - a)])
         _check_positions(qg[a:b][keep], r.q[keep], spread[keep], rel=1e-11)
-    assert max_set < 512 and st["max_set"] < 512
+    assert max_set < 448 and st["max_set"] < 448
