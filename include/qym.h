@@ -101,6 +101,13 @@ typedef struct qym_params {
     double heavy_mass;          /* mixed kick only: bodies with m >= heavy_mass * m0 (at most
                                    QYM_HEAVY_CAP per system) pull on every body in FP64; the
                                    N^2 part among the others stays FP32. <= 0: off */
+    int32_t merge_kicks;        /* 1: inside one qym_step call, the closing kick of a step
+                                   and the opening kick of the next are one kick of tau
+                                   (exact: E_Dft is a uniform shift and E_Int conserves the
+                                   total momentum, so Int(tau/2) Dft(tau) Int(tau/2) =
+                                   Dft(tau) Int(tau)); one all-pairs pass per step instead
+                                   of two. 0: the paper's two kicks per step */
+    int32_t reserved0;          /* must be 0 */
 } qym_params;
 
 #define QYM_HEAVY_CAP 256

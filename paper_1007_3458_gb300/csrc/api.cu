@@ -109,6 +109,8 @@ static bool valid_params(const qym_params *p, std::string &why) {
     if (p->max_hermite_steps < 1) { why = "max_hermite_steps must be >= 1"; return false; }
     if (p->max_candidates < 0 || p->max_encounters < 0 || p->max_log < 0) { why = "capacities"; return false; }
     if (p->l2_flush_bytes < 0 || p->l2_flush_bytes > ((int64_t)1 << 34)) { why = "l2_flush_bytes"; return false; }
+    if (p->merge_kicks != 0 && p->merge_kicks != 1) { why = "merge_kicks must be 0 or 1"; return false; }
+    if (p->reserved0 != 0) { why = "reserved0 must be 0"; return false; }
     return true;
 }
 
@@ -426,20 +428,11 @@ __global__ void k_step_end(unsigned long long *ctr, int64_t max_cand, int64_t ma
 
 // one step whose opening drift has been applied: ends with the closing drift
 // of this step plus, unless last, the opening drift of the next one
-static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last) {
+// E_Kep of every row over tau, (q, v) -> (q1, v1), with the context's solver,
+// guess and solve log
+static KeplerArgs step_kepler_args(qym_ctx *c, double tau) {
     Dev &d = c->d;
     const qym_params &p = c->p;
-    cudaStream_t st = c->stream;
-    const int enc = p.encounters;
-    cudaError_t e;
-    if (c->flush) {
-        if ((e = cudaMemsetAsync(c->flush, c->launches & 0xff, (size_t)p.l2_flush_bytes, st))) return e;
-    }
-    k_step_begin<<<1, 1, 0, st>>>(d.ctr);
-    // item 2: kick tau/2, with the crude encounter search when encounters are on
-    if ((e = launch_kick_tiles(d, p.kick_prec, enc, p.G, c->tune.threads, c->tune.ipt, st))) return e;
-    if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, enc, p.hill_fixed, st))) return e;
-    // item 3: Kepler drift over tau, (q, v) -> (q1, v1)
     KeplerArgs ka;
     std::memset(&ka, 0, sizeof(ka));
     ka.n = d.rows;
@@ -462,7 +455,24 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last) {
     ka.offsets = d.offsets;
     ka.m = d.m;
     ka.G = p.G;
-    if ((e = launch_kepler(ka, st))) return e;
+    return ka;
+}
+
+static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last) {
+    Dev &d = c->d;
+    const qym_params &p = c->p;
+    cudaStream_t st = c->stream;
+    const int enc = p.encounters;
+    cudaError_t e;
+    if (c->flush) {
+        if ((e = cudaMemsetAsync(c->flush, c->launches & 0xff, (size_t)p.l2_flush_bytes, st))) return e;
+    }
+    k_step_begin<<<1, 1, 0, st>>>(d.ctr);
+    // item 2: kick tau/2, with the crude encounter search when encounters are on
+    if ((e = launch_kick_tiles(d, p.kick_prec, enc, p.G, c->tune.threads, c->tune.ipt, st))) return e;
+    if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, enc, p.hill_fixed, st))) return e;
+    // item 3: Kepler drift over tau, (q, v) -> (q1, v1)
+    if ((e = launch_kepler(step_kepler_args(c, tau), st))) return e;
     if (enc) {
         // items 4-8: rigorous test, sets and r_crit, K corrections + Hermite
         if ((e = launch_refine(d, tau, p.a_E, st))) return e;
@@ -470,7 +480,8 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last) {
         if ((e = launch_hermite(d, p, tau, st))) return e;
     }
     // (q1, v1) -> (q, v) and the float packs for the second kick
-    if ((e = launch_drift_pack_from(d, d.q1, d.v1, 0.0, 0.0, tau, p.a_E, p.G, 0, p.hill_fixed, st)))
+    if ((e = launch_drift_pack_from(d, d.q1, d.v1, 0.0, 0.0, tau, p.a_E, p.G, 0, p.hill_fixed, st,
+                                    0.5 * tau)))
         return e;
     // item 9: kick tau/2
     if ((e = launch_kick_tiles(d, p.kick_prec, 0, p.G, c->tune.threads, c->tune.ipt, st))) return e;
@@ -478,12 +489,78 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last) {
     // item 10 (and item 1 of the next step): drift tau/2 with S = sum m v
     if ((e = launch_momentum(d, st))) return e;
     if ((e = launch_drift_pack_from(d, d.q, d.v, 0.5 * tau, last ? 0.0 : 0.5 * tau, tau, p.a_E,
-                                    p.G, (!last) && enc, p.hill_fixed, st)))
+                                    p.G, (!last) && enc, p.hill_fixed, st, 0.5 * tau)))
         return e;
     k_step_end<<<1, 1, 0, st>>>(d.ctr, d.max_cand, d.max_enc);
     // begin, kick, finish, Kepler, [refine 2, sets 7, Hermite], pack, kick,
     // finish, momentum 2, drift, end
     c->launches += 12 + (enc ? 10 : 0);
+    return cudaGetLastError();
+}
+
+// ---- merged kicks (params.merge_kicks): the closing kick of a step and the
+// opening kick of the next, at the same separations, become one kick of tau.
+// The opening half kick of the first step (with the encounter search):
+static cudaError_t enqueue_opening_kick(qym_ctx *c, double tau) {
+    Dev &d = c->d;
+    const qym_params &p = c->p;
+    cudaStream_t st = c->stream;
+    cudaError_t e;
+    k_step_begin<<<1, 1, 0, st>>>(d.ctr);
+    if ((e = launch_kick_tiles(d, p.kick_prec, p.encounters, p.G, c->tune.threads, c->tune.ipt, st)))
+        return e;
+    if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, p.encounters, p.hill_fixed, st)))
+        return e;
+    c->launches += 3;
+    return cudaGetLastError();
+}
+
+// One step from its Kepler drift on: items 3-8, then either the merged kick of
+// tau that closes this step and opens the next (momentum, drift tau, the next
+// step's packs with its encounter search, kick, finish), or for the last step
+// the closing half kick and half drift.
+static cudaError_t enqueue_unit(qym_ctx *c, double tau, bool last) {
+    Dev &d = c->d;
+    const qym_params &p = c->p;
+    cudaStream_t st = c->stream;
+    const int enc = p.encounters;
+    cudaError_t e;
+    if (c->flush) {
+        if ((e = cudaMemsetAsync(c->flush, c->launches & 0xff, (size_t)p.l2_flush_bytes, st))) return e;
+    }
+    if ((e = launch_kepler(step_kepler_args(c, tau), st))) return e;
+    if (enc) {
+        if ((e = launch_refine(d, tau, p.a_E, st))) return e;
+        if ((e = launch_sets_impl(d, p.a_H, c->ss, st))) return e;
+        if ((e = launch_hermite(d, p, tau, st))) return e;
+    }
+    k_step_end<<<1, 1, 0, st>>>(d.ctr, d.max_cand, d.max_enc);
+    // (q1, v1) -> (q, v)
+    if ((e = launch_drift_pack_from(d, d.q1, d.v1, 0.0, 0.0, tau, p.a_E, p.G, 0, p.hill_fixed, st,
+                                    0.5 * tau)))
+        return e;
+    if (!last) {
+        k_step_begin<<<1, 1, 0, st>>>(d.ctr);
+        if ((e = launch_momentum(d, st))) return e;
+        // the last kick was a step earlier: its |a| bounds this one's only
+        // loosely, so the crude reach allows twice it (and the finisher checks)
+        if ((e = launch_drift_pack_from(d, d.q, d.v, 0.5 * tau, 0.5 * tau, tau, p.a_E, p.G, enc,
+                                        p.hill_fixed, st, tau, 2.0)))
+            return e;
+        if ((e = launch_kick_tiles(d, p.kick_prec, enc, p.G, c->tune.threads, c->tune.ipt, st))) return e;
+        if ((e = launch_kick_finish_v(d, d.v, d.q, tau, p.G, enc, p.hill_fixed, st, 2.0))) return e;
+        // Kepler, [refine 2, sets 7, Hermite], end, copy, begin, momentum 2, drift, kick, finish
+        c->launches += 9 + (enc ? 10 : 0);
+    } else {
+        if ((e = launch_kick_tiles(d, p.kick_prec, 0, p.G, c->tune.threads, c->tune.ipt, st))) return e;
+        if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, 0, p.hill_fixed, st))) return e;
+        if ((e = launch_momentum(d, st))) return e;
+        if ((e = launch_drift_pack_from(d, d.q, d.v, 0.5 * tau, 0.0, tau, p.a_E, p.G, 0,
+                                        p.hill_fixed, st, 0.5 * tau)))
+            return e;
+        // Kepler, [refine 2, sets 7, Hermite], end, copy, kick, finish, momentum 2, drift
+        c->launches += 8 + (enc ? 10 : 0);
+    }
     return cudaGetLastError();
 }
 
@@ -540,7 +617,8 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
     c->launches = 0;
     if (!c->amag_valid) {
         // |a| of the current positions for the first crude search's kick bound
-        CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.0, tau, p.a_E, p.G, 0, p.hill_fixed, st));
+        CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.0, tau, p.a_E, p.G, 0, p.hill_fixed, st,
+                                     0.5 * tau));
         CK(c, launch_kick_tiles(d, p.kick_prec, 0, p.G, c->tune.threads, c->tune.ipt, st));
         CK(c, launch_kick_finish_v(d, d.v, d.q, 0.0, p.G, 0, p.hill_fixed, st));
         c->amag_valid = true;
@@ -549,8 +627,9 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
     // item 1 of the first step: drift tau/2
     CK(c, launch_momentum(d, st));
     CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.5 * tau, tau, p.a_E, p.G, p.encounters,
-                                 p.hill_fixed, st));
+                                 p.hill_fixed, st, 0.5 * tau));
     c->launches += 3;
+    if (p.merge_kicks) CK(c, enqueue_opening_kick(c, tau));
     const int64_t interior = nsteps - 1;
     if (interior > 0) {
         if (c->gexec && c->g_tau != tau) {
@@ -561,7 +640,7 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
             cudaGraph_t g;
             CK(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             int64_t before = c->launches;
-            cudaError_t e = enqueue_step(c, tau, false);
+            cudaError_t e = p.merge_kicks ? enqueue_unit(c, tau, false) : enqueue_step(c, tau, false);
             c->graph_launches = c->launches - before;
             c->launches = before;
             cudaError_t e2 = cudaStreamEndCapture(st, &g);
@@ -577,10 +656,10 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
                 CK(c, cudaGraphLaunch(c->gexec, st));
                 c->launches += c->graph_launches;
             } else
-                CK(c, enqueue_step(c, tau, false));
+                CK(c, p.merge_kicks ? enqueue_unit(c, tau, false) : enqueue_step(c, tau, false));
         }
     }
-    CK(c, enqueue_step(c, tau, true));
+    CK(c, p.merge_kicks ? enqueue_unit(c, tau, true) : enqueue_step(c, tau, true));
     if (c->klog) c->klog_steps += (unsigned long long)nsteps;
     return collect(c, nsteps);
 }
@@ -880,7 +959,8 @@ static qym_status time_kick_shape(qym_ctx *c, int flag, int reps, const KickTune
     Dev &d = c->d;
     const qym_params &p = c->p;
     cudaStream_t st = c->stream;
-    CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.0, 0.1, p.a_E, p.G, flag, p.hill_fixed, st));
+    CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.0, 0.1, p.a_E, p.G, flag, p.hill_fixed, st,
+                                 0.05));
     cudaEvent_t e0, e1;
     CK(c, cudaEventCreate(&e0));
     CK(c, cudaEventCreate(&e1));

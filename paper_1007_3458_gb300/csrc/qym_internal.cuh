@@ -184,11 +184,17 @@ cudaError_t launch_mlp_train(float *w, float *m, float *v, int64_t t0, const flo
 
 // step kernels (step.cu)
 cudaError_t launch_momentum(const Dev &d, cudaStream_t st);
+// kick_span: the time of the kick(s) between this pack and the Kepler drift
+// (tau/2, or tau when two half kicks are merged); it sizes the crude reach
 cudaError_t launch_drift_pack_from(const Dev &d, const double *qs, const double *vs,
                                    double h_close, double h_open, double tau, double a_E,
-                                   double G, int flag_next, int hill_fixed, cudaStream_t st);
+                                   double G, int flag_next, int hill_fixed, cudaStream_t st,
+                                   double kick_span, double a_allow = 1.01);
+// a_allow: the bound on |a| / |a of the last kick| that the crude reach of the
+// preceding pack assumed (checked when check != 0)
 cudaError_t launch_kick_finish_v(const Dev &d, double *v, const double *q, double dt, double G,
-                                 int check, int hill_fixed, cudaStream_t st);
+                                 int check, int hill_fixed, cudaStream_t st,
+                                 double a_allow = 1.01);
 cudaError_t launch_hill_init(const Dev &d, double G, cudaStream_t st);
 cudaError_t launch_to_dh_impl(const Dev &d, int inverse, double *vout, double *mt_scratch,
                               cudaStream_t st);

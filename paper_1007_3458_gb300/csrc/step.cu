@@ -71,6 +71,8 @@ __device__ __forceinline__ float round_up_f(double x) {
 struct DriftArgs {
     const double *qs, *vs;
     double h_close, h_open, tau, a_E, G;
+    double kick_span;  // time of the kick(s) between this pack and the Kepler drift
+    double a_allow;    // bound on |a| of that kick as a multiple of the last |a|
     int flag_next, hill_fixed;
 };
 
@@ -110,7 +112,10 @@ __global__ void __launch_bounds__(256) k_drift_pack(Dev d, DriftArgs a) {
         // crude reach rho_i = F_i (R_i + |tau| (u_i + w_i)):
         //   R_i  a_E times a bound on this step's Hill radius
         //   u_i  speed relative to the local circular velocity Omega (z x Q)
-        //   w_i  bound on the coming half-kick's velocity change, (tau/2)|a|
+        //   w_i  bound on the velocity change of the kick(s) before the Kepler
+        //        drift: (tau/2) 1.01 |a| (the last kick was at the same
+        //        separations), or with merged kicks tau 2 |a| (the last kick
+        //        was a step earlier); the finisher checks the bound
         //   F_i  stretch for the Keplerian shear over one step
         const double m0 = d.m[star];
         const double mu = a.G * m0;
@@ -126,7 +131,7 @@ __global__ void __launch_bounds__(256) k_drift_pack(Dev d, DriftArgs a) {
         double Om = sqrt(mu / (rr * rr * rr));
         double ux = vx + Om * qy, uy = vy - Om * qx, uz = vz;
         double u = sqrt(ux * ux + uy * uy + uz * uz);
-        double w = 0.5 * fabs(a.tau) * 1.01 * (double)d.amag[r];
+        double w = fabs(a.kick_span) * a.a_allow * (double)d.amag[r];
         double sh = fmin(0.8, 2.5 * Om * fabs(a.tau));
         double F = 2.0 / (1.0 - sh);
         double rho = F * (a.a_E * (double)rHb + fabs(a.tau) * (u + w)) + 1e-12 * rr;
@@ -143,13 +148,16 @@ __global__ void __launch_bounds__(256) k_drift_pack(Dev d, DriftArgs a) {
 
 cudaError_t launch_drift_pack_from(const Dev &d, const double *qs, const double *vs,
                                    double h_close, double h_open, double tau, double a_E,
-                                   double G, int flag_next, int hill_fixed, cudaStream_t st) {
+                                   double G, int flag_next, int hill_fixed, cudaStream_t st,
+                                   double kick_span, double a_allow) {
     DriftArgs a;
     a.qs = qs;
     a.vs = vs;
     a.h_close = h_close;
     a.h_open = h_open;
     a.tau = tau;
+    a.kick_span = kick_span;
+    a.a_allow = a_allow;
     a.a_E = a_E;
     a.G = G;
     a.flag_next = flag_next;
@@ -169,6 +177,7 @@ struct FinishArgs {
     double *v;          // velocities to update ([3][rows])
     const double *q;    // positions (for the Hill radius)
     double dt, G;
+    float a_allow;      // the crude reach's bound on |a| / |a of the last kick|
     int check, hill_fixed;
 };
 
@@ -197,7 +206,7 @@ __global__ void __launch_bounds__(256) k_finish(Dev d, FinishArgs a) {
     a.v[r] = vx; a.v[R + r] = vy; a.v[2 * R + r] = vz;
     float an = round_up_f(sqrt(ax * ax + ay * ay + az * az));
     if (a.check) {
-        bool bad = an > 1.01f * d.amag[r] + 1e-30f;
+        bool bad = an > a.a_allow * d.amag[r] + 1e-30f;
         const double m0 = d.m[star];
         double rH = a.hill_fixed ? d.rH_fixed[r] : hill(a.q[r], a.q[R + r], a.q[2 * R + r], d.m[r], m0);
         d.rH[r] = rH;
@@ -211,12 +220,13 @@ __global__ void __launch_bounds__(256) k_finish(Dev d, FinishArgs a) {
 }
 
 cudaError_t launch_kick_finish_v(const Dev &d, double *v, const double *q, double dt, double G,
-                                 int check, int hill_fixed, cudaStream_t st) {
+                                 int check, int hill_fixed, cudaStream_t st, double a_allow) {
     FinishArgs a;
     a.v = v;
     a.q = q;
     a.dt = dt;
     a.G = G;
+    a.a_allow = (float)a_allow;
     a.check = check;
     a.hill_fixed = hill_fixed;
     int tb = 256;

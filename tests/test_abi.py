@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_header_struct_layout_matches_binding():
     # qym_params: 7 doubles, 8 int32, 5 int64 = 56 + 32 + 40 bytes
-    assert ctypes.sizeof(q.qym_params) == 128
+    assert ctypes.sizeof(q.qym_params) == 136
     assert ctypes.sizeof(q.qym_stats) == 10 * 8 + 4 * 3 + 4
 
 

@@ -233,3 +233,38 @@ def test_ensemble_full_size_sampled(gpu, oracle):
         keep = np.array([i not in skip for i in range(b - a)])
         _check_positions(qg[a:b][keep], r.q[keep], spread[keep], rel=1e-11)
     assert max_set < 448 and st["max_set"] < 448
+
+
+def test_merged_kicks_equal_two_kicks(gpu, oracle):
+    """merge_kicks = 1 (one kick of tau between steps inside a call, exact
+    since E_Dft is a uniform shift and E_Int conserves the momentum): the
+    plain DH step gives the two-kick result to rounding over 50 steps, in two
+    calls (the state is synchronised at the end of each)."""
+    w = W.subsample(W.disk_260(), 120, seed=4)
+    a = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=q.QYM_KICK_FP64, encounters=0)
+    b = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=q.QYM_KICK_FP64, encounters=0,
+                     merge_kicks=1)
+    for sim in (a, b):
+        sim.step(w.tau, 30)
+        sim.step(w.tau, 20)
+    qa, va = a.state()
+    qb, vb = b.state()
+    la, lb = a.stats()["launches"], b.stats()["launches"]
+    a.close()
+    b.close()
+    assert _relq(qb, qa).max() <= 1e-12 and _relq(vb, va).max() <= 1e-11
+    r, vh = _run_oracle(oracle, w, 50, encounters=0)
+    assert _relq(qb, r.q).max() <= 1e-12
+    assert lb < la   # fewer kernels: one kick and finish less per interior step
+
+
+def test_merged_kicks_hybrid_step(gpu, oracle):
+    """The hybrid step with merged kicks on the 260-body disk, FP64: the same
+    encounter records as the oracle's two-kick step (up to pairs at the
+    threshold), positions within the chaos-aware tolerance."""
+    w = W.disk_260()
+    qg, vg, enc, st, E = _run_gpu(w, 100, kick_prec=q.QYM_KICK_FP64, merge_kicks=1)
+    r, vh = _run_oracle(oracle, w, 100)
+    skip = _compare_records(enc, r)
+    keep = np.array([i not in skip for i in range(len(w.m))])
+    _check_positions(qg[keep], r.q[keep], _chaos_spread(oracle, w, 100)[keep])
