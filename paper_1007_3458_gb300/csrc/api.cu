@@ -156,6 +156,7 @@ static void carve_all(qym_ctx *c, Carver &k) {
     d.heavy_start = k.take<int32_t>(d.nsys + 1);
     d.heavy_thr = k.take<double>(d.nsys);
     d.cand = k.take<int2>(d.max_cand);
+    d.fchunk = k.take<int4>(d.max_fchunk);
     d.enc = k.take<int2>(d.max_enc);
     d.rescan = k.take<int32_t>(R);
     d.set_start = k.take<int32_t>((size_t)d.max_sets + 1);
@@ -295,6 +296,7 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     sc0[nsys] = (int32_t)mch.size();
     d.nmchunks = (int32_t)mch.size();
     d.max_cand = params->max_candidates ? params->max_candidates : std::max<int64_t>(1 << 20, 16 * R);
+    d.max_fchunk = d.max_cand + R;  // every row flags the chunk holding itself
     d.max_enc = params->max_encounters ? params->max_encounters : std::max<int64_t>(1 << 16, R);
     d.max_log = params->max_log ? params->max_log : (int64_t)1 << 22;
     d.max_sets = (int32_t)R;
@@ -417,6 +419,8 @@ __global__ void k_step_begin(unsigned long long *ctr) {
     ctr[C_NRESCAN] = 0;
     ctr[C_NSETS] = 0;
     ctr[C_HSMALL] = 0;
+    ctr[C_NFCHUNK] = 0;
+    ctr[C_FCDONE] = 0;
 }
 
 __global__ void k_step_end(unsigned long long *ctr, int64_t max_cand, int64_t max_enc) {
@@ -458,6 +462,12 @@ static KeplerArgs step_kepler_args(qym_ctx *c, double tau) {
     return ka;
 }
 
+// kernels a search kick adds after the kick itself (the mixed kick's exact
+// re-test of its flagged chunks)
+static int search_retest(const qym_params &p, int flag) {
+    return (flag && p.kick_prec == QYM_KICK_MIXED) ? 1 : 0;
+}
+
 static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last) {
     Dev &d = c->d;
     const qym_params &p = c->p;
@@ -492,9 +502,9 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last) {
                                     p.G, (!last) && enc, p.hill_fixed, st, 0.5 * tau)))
         return e;
     k_step_end<<<1, 1, 0, st>>>(d.ctr, d.max_cand, d.max_enc);
-    // begin, kick, finish, Kepler, [refine 2, sets 7, Hermite], pack, kick,
-    // finish, momentum 2, drift, end
-    c->launches += 12 + (enc ? 10 : 0);
+    // begin, kick [+ chunk re-test], finish, Kepler, [refine 2, sets 7, Hermite],
+    // pack, kick, finish, momentum 2, drift, end
+    c->launches += 12 + (enc ? 10 : 0) + search_retest(p, enc);
     return cudaGetLastError();
 }
 
@@ -511,7 +521,7 @@ static cudaError_t enqueue_opening_kick(qym_ctx *c, double tau) {
         return e;
     if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, p.encounters, p.hill_fixed, st)))
         return e;
-    c->launches += 3;
+    c->launches += 3 + search_retest(p, p.encounters);
     return cudaGetLastError();
 }
 
@@ -549,8 +559,9 @@ static cudaError_t enqueue_unit(qym_ctx *c, double tau, bool last) {
             return e;
         if ((e = launch_kick_tiles(d, p.kick_prec, enc, p.G, c->tune.threads, c->tune.ipt, st))) return e;
         if ((e = launch_kick_finish_v(d, d.v, d.q, tau, p.G, enc, p.hill_fixed, st, 2.0))) return e;
-        // Kepler, [refine 2, sets 7, Hermite], end, copy, begin, momentum 2, drift, kick, finish
-        c->launches += 9 + (enc ? 10 : 0);
+        // Kepler, [refine 2, sets 7, Hermite], end, copy, begin, momentum 2, drift, kick
+        // [+ chunk re-test], finish
+        c->launches += 9 + (enc ? 10 : 0) + search_retest(p, enc);
     } else {
         if ((e = launch_kick_tiles(d, p.kick_prec, 0, p.G, c->tune.threads, c->tune.ipt, st))) return e;
         if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, 0, p.hill_fixed, st))) return e;

@@ -40,6 +40,9 @@ struct KickArgs {
     int2 *cand;
     int64_t max_cand;
     unsigned long long *ncand;
+    int4 *fchunk;
+    int64_t max_fchunk;
+    unsigned long long *nfchunk;
     int32_t *status;
 };
 
@@ -73,7 +76,8 @@ struct JPairs {
 // Pair forces of the j pairs [p0, p1) for the IPT rows of a thread. With
 // FLAG, each i keeps the minimum over the chunk of r^2 - c_j, c_j = 2 rho_j^2
 // (no branch); since (rho_i + rho_j)^2 <= c_i + c_j, a chunk without a
-// candidate of i has that minimum >= c_i and needs no further look.
+// candidate of i has that minimum >= c_i and needs no further look; a chunk
+// with a smaller minimum is recorded and re-tested exactly by k_flag_chunks.
 template <int IPT, bool FLAG, bool DIAG>
 __device__ __forceinline__ void mixed_chunk(const JPairs &s, int p0, int p1,
                                             const float2 (&nxh)[IPT], const float2 (&nyh)[IPT],
@@ -111,28 +115,20 @@ __device__ __forceinline__ void mixed_chunk(const JPairs &s, int p0, int p1,
     }
 }
 
-// exact pre-check of one i against the j pairs [p0, p1) (rare path):
-// candidates (i, j), i < j < n, with r^2 < c_i + c_j
-__device__ __noinline__ void flag_chunk(const KickArgs &a, const JPairs &s, int p0, int p1, int n,
-                                        int jbase, int gi, float xh, float yh, float zh, float xl,
-                                        float yl, float zl, float ci) {
-    for (int p = p0; p < p1; ++p) {
-        const float4 A = s.a[p], B = s.b[p], C = s.c[p], D = s.d[p];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int j = 2 * p + e;
-            const int gj = jbase + j;
-            if (j >= n || gi >= gj) continue;
-            const float pxh = e ? A.y : A.x, pyh = e ? A.w : A.z, pzh = e ? B.y : B.x;
-            const float pxl = e ? C.y : C.x, pyl = e ? C.w : C.z, pzl = e ? D.y : D.x;
-            const float cj = -(e ? D.w : D.z);
-            float dx = (xh - pxh) + (xl - pxl);
-            float dy = (yh - pyh) + (yl - pyl);
-            float dz = (zh - pzh) + (zl - pzl);
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (r2 < ci + cj) push_candidate(a, gi, gj);
-        }
-    }
+// record that row i's crude minimum over the j rows [j0, j1) fell below c_i
+// (divergent branch, warp-aggregated); k_flag_chunks re-tests them
+__device__ __forceinline__ void push_flag(const KickArgs &a, int i, int j0, int j1) {
+    unsigned mask = __activemask();
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(a.nfchunk, (unsigned long long)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    unsigned long long idx = base + __popc(mask & ((1u << lane) - 1u));
+    if (idx < (unsigned long long)a.max_fchunk)
+        a.fchunk[idx] = make_int4(i, j0, j1, 0);
+    else if (lane == leader)
+        atomicOr(a.status, QYM_ST_CAND_OVERFLOW);
 }
 
 template <int IPT, bool FLAG>
@@ -201,9 +197,7 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
                 two_sum(ahx[k], fx[k].x + fx[k].y, s, e); ahx[k] = s; alx[k] += e;
                 two_sum(ahy[k], fy[k].x + fy[k].y, s, e); ahy[k] = s; aly[k] += e;
                 two_sum(ahz[k], fz[k].x + fz[k].y, s, e); ahz[k] = s; alz[k] += e;
-                if (FLAG && mind[k] < rho[k])
-                    flag_chunk(a, sp, c, ce, n, jt, gi[k], -nxh[k].x, -nyh[k].x, -nzh[k].x,
-                               -nxl[k].x, -nyl[k].x, -nzl[k].x, rho[k]);
+                if (FLAG && mind[k] < rho[k]) push_flag(a, gi[k], jt + 2 * c, jt + min(2 * ce, n));
             }
         }
     }
@@ -215,6 +209,40 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
             out[gi[k]] = (double)ahx[k] + (double)alx[k];
             out[rows + gi[k]] = (double)ahy[k] + (double)aly[k];
             out[2 * rows + gi[k]] = (double)ahz[k] + (double)alz[k];
+        }
+    }
+}
+
+// Exact test of the flagged chunks, one warp per entry, lane l on the j rows
+// j0 + l and j0 + 32 + l: candidates (i, j), i < j, with r^2 < c_i + c_j, the
+// separation formed from the same split positions in the same order as the
+// kick forms it, so the candidate set is the kick's own. The last CTA to
+// finish resets the entry counter for the next search kick.
+__global__ void __launch_bounds__(256) k_flag_chunks(KickArgs a, unsigned long long *done) {
+    unsigned long long n = *(volatile unsigned long long *)a.nfchunk;
+    if (n > (unsigned long long)a.max_fchunk) n = a.max_fchunk;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long e = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+         e < n; e += warps) {
+        const int4 f = a.fchunk[e];
+        const float4 pi = a.pos[f.x], li = a.lo[f.x];
+        for (int j = f.y + lane; j < f.z; j += 32) {
+            if (j <= f.x) continue;
+            const float4 pj = a.pos[j], lj = a.lo[j];
+            const float dx = (pi.x - pj.x) + (li.x - lj.x);
+            const float dy = (pi.y - pj.y) + (li.y - lj.y);
+            const float dz = (pi.z - pj.z) + (li.z - lj.z);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 < li.w + lj.w) push_candidate(a, f.x, j);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1ull) == gridDim.x - 1) {
+            *a.nfchunk = 0;
+            *done = 0;
         }
     }
 }
@@ -366,10 +394,21 @@ cudaError_t launch_kick_tiles(const Dev &d, int prec, int flag, double G, int th
     a.cand = d.cand;
     a.max_cand = d.max_cand;
     a.ncand = d.ctr + C_NCAND;
+    a.fchunk = d.fchunk;
+    a.max_fchunk = d.max_fchunk;
+    a.nfchunk = d.ctr + C_NFCHUNK;
     a.status = d.status;
-    if (prec == QYM_KICK_MIXED)
-        return flag ? launch_mixed<true>(a, d.nitems, threads, ipt, st)
-                    : launch_mixed<false>(a, d.nitems, threads, ipt, st);
+    if (prec == QYM_KICK_MIXED) {
+        if (!flag) return launch_mixed<false>(a, d.nitems, threads, ipt, st);
+        cudaError_t e = launch_mixed<true>(a, d.nitems, threads, ipt, st);
+        if (e) return e;
+        // about one entry per row (its own chunk) plus the close pairs
+        int64_t blocks = (d.rows + 63) / 64;
+        if (blocks > 4 * 152) blocks = 4 * 152;
+        if (blocks < 1) blocks = 1;
+        k_flag_chunks<<<(int)blocks, 256, 0, st>>>(a, d.ctr + C_FCDONE);
+        return cudaGetLastError();
+    }
     return flag ? launch_f64<true>(a, d.nitems, threads, ipt, st)
                 : launch_f64<false>(a, d.nitems, threads, ipt, st);
 }
@@ -536,6 +575,7 @@ cudaError_t launch_accel_single(int64_t rows, const double *m, const double *q, 
         ka.items = d.items; ka.slots = d.item_slot; ka.pos = d.pk_pos; ka.lo = d.pk_lo;
         ka.q = q; ka.m = m; ka.G = G; ka.apart = d.apart; ka.rows = rows;
         ka.cand = nullptr; ka.max_cand = 0; ka.ncand = nullptr; ka.status = nullptr;
+        ka.fchunk = nullptr; ka.max_fchunk = 0; ka.nfchunk = nullptr;
         e = launch_f64<false>(ka, L.nitems, L.tune.threads, L.tune.ipt, st);
     }
     if (e != cudaSuccess) return e;

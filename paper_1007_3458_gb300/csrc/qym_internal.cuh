@@ -44,6 +44,9 @@ struct Dev {
     // encounters
     int2 *cand = nullptr;         // crude candidate pairs (i < j)
     int64_t max_cand = 0;
+    int4 *fchunk = nullptr;       // (i, j0, j1, -): j chunks [j0, j1) of row i whose crude
+                                  // minimum fell below c_i, re-tested pair by pair
+    int64_t max_fchunk = 0;
     int2 *enc = nullptr;          // rigorous encounter pairs
     int64_t max_enc = 0;
     int32_t *rescan = nullptr;    // rows whose crude bounds were exceeded
@@ -82,6 +85,8 @@ enum Ctr : int {
     C_STEP,          // step index within the current qym_step call
     C_MAX_HSET,      // most Hermite steps taken by one set in one step
     C_HSMALL,        // next set for the Hermite kernel's per-CTA queue (reset per step)
+    C_NFCHUNK,       // flagged (row, j chunk) entries of the last search kick
+    C_FCDONE,        // CTAs of the chunk re-test done (its last CTA resets both)
     C_COUNT
 };
 
