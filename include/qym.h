@@ -56,7 +56,7 @@ typedef enum qym_status {
 #define QYM_ST_CAND_OVERFLOW   0x04  /* more crude candidates than max_candidates */
 #define QYM_ST_ENC_OVERFLOW    0x08  /* more encounter pairs than max_encounters */
 #define QYM_ST_SET_OVERFLOW    0x10  /* a set larger than the set capacity (or than
-                                        the 448 members the Hermite holds on chip) */
+                                        the 320 members the Hermite holds on chip) */
 #define QYM_ST_NAN             0x20  /* non-finite state after the Kepler drift */
 #define QYM_ST_UF_CAP          0x40  /* set-building iteration cap reached */
 #define QYM_ST_LOG_OVERFLOW    0x80  /* encounter log of this qym_step call is full */

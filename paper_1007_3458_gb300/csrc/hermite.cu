@@ -11,9 +11,12 @@
 // integer ticks of |tau| / 2^48, member i steps with |tau| 2^-k_i from the
 // Aarseth criterion (eta; eta_s at start-up) rounded down to a power of two,
 // and a step doubles only on a commensurate block time. At each block time
-// every member is predicted and the members whose step ends there are
-// evaluated and corrected. Every loop has a cap and reports through the
-// status word.
+// the members whose step ends there are evaluated and corrected, against
+// their partners predicted to that time; a partner farther than r_crit
+// exerts no force (K = 1), so an FP32 prediction with a bound on its error
+// first rules out the pairs that are surely that far, and only the others
+// are predicted and evaluated in FP64 (the result is the same as evaluating
+// every pair). Every loop has a cap and reports through the status word.
 #include <climits>
 
 #include <cooperative_groups.h>
@@ -23,7 +26,7 @@
 namespace qym {
 namespace cg = cooperative_groups;
 
-constexpr int HCAP = 448;       // members per set held in shared memory
+constexpr int HCAP = 320;       // members per set held in shared memory
 constexpr int HTHREADS = 256;
 
 // sin and cos of (pi/2) y for y in [0, 1]: y > 1/2 is folded onto 1 - y
@@ -112,6 +115,8 @@ constexpr int CL = 8;      // CTAs of a cluster sharing one large set (the tree 
 constexpr int NBIG = QYM_HERM_NBIG;  // sets of at least this many members use a whole cluster
 constexpr int ACH = 64;    // active members per force round (exchange, correction)
 
+constexpr int KMAX = 48;
+
 struct HermSmem {
     double *ex, *ey, *ez, *eu, *ev, *ew, *m;  // evaluation point of every member
     double *x, *y, *z, *u, *v, *w;            // state at the member's own time
@@ -119,11 +124,16 @@ struct HermSmem {
     double *pb;                               // partial a, adot [2][6][ACH] (cluster exchange)
     double *pr;                               // per-lane partial a, adot [6][HTHREADS]
     double *a1s;                              // a, adot of the round's active members [6][ACH]
-    float *cf;                                // step criterion inputs [12][ACH]
+    double *lvt;                              // corrector constants per level [5][KMAX + 1]
     long long *ti;                            // member time in ticks
+    float *f;                                 // x..z, u..w, ax..az, jx..jz cut to FP32 [12][HCAP]
+    float *px, *py, *pz, *pd;                 // FP32 prediction and its error bound
+    float *cf;                                // step criterion inputs [12][ACH]
     int32_t *lev;                             // member level: step = tau 2^-lev
     int32_t *act;                             // members whose step ends now
     int32_t *ids;
+    int32_t *need;                            // member needed in FP64 at this block time
+    int32_t *nl;                              // per coordinate warp: those members [3][HCAP]
 };
 
 __device__ __forceinline__ HermSmem carve(void *base) {
@@ -139,18 +149,25 @@ __device__ __forceinline__ HermSmem carve(void *base) {
     s.pb = p; p += 2 * 6 * ACH;
     s.pr = p; p += 6 * HTHREADS;
     s.a1s = p; p += 6 * ACH;
+    s.lvt = p; p += 5 * (KMAX + 1);
     s.ti = (long long *)p; p += HCAP;
     float *fp = (float *)p;
+    s.f = fp; fp += 12 * HCAP;
+    s.px = fp; fp += HCAP; s.py = fp; fp += HCAP; s.pz = fp; fp += HCAP; s.pd = fp; fp += HCAP;
     s.cf = fp; fp += 12 * ACH;
     int32_t *ip = (int32_t *)fp;
     s.lev = ip; ip += HCAP;
     s.act = ip; ip += HCAP;
-    s.ids = ip;
+    s.ids = ip; ip += HCAP;
+    s.need = ip; ip += HCAP;
+    s.nl = ip;
     return s;
 }
-constexpr size_t kHermSmem = sizeof(double) * (HCAP * 20 + 2 * 6 * ACH + 6 * HTHREADS + 6 * ACH) +
-                             sizeof(float) * 12 * ACH + sizeof(int32_t) * HCAP * 3;
-constexpr int KMAX = 48;
+constexpr size_t kHermSmem =
+    sizeof(double) * (HCAP * 20 + 2 * 6 * ACH + 6 * HTHREADS + 6 * ACH + 5 * (KMAX + 1)) +
+    sizeof(float) * (16 * HCAP + 12 * ACH) + sizeof(int32_t) * HCAP * 7;
+// two CTAs per SM (228 KB of shared memory, 1 KB of it per CTA reserved)
+static_assert(2 * (kHermSmem + 1024) <= 228 * 1024, "Hermite shared memory above two CTAs per SM");
 
 // smallest k with T 2^-k <= dt_c, in [0, KMAX]: with T = fT 2^eT and
 // dt_c = fd 2^ed (fT, fd in [1/2, 1)), T 2^-k <= dt_c exactly when
@@ -311,11 +328,59 @@ __device__ __forceinline__ void predict_c(const HermSmem &S, int k, int c, long 
     eu[k] = uk + hs * (ak + 0.5 * hs * jk);
 }
 
+// FP32 copies of member k's state (truncated: within 2^-23 of the FP64
+// values, relative), kept beside the FP64 state for the FP32 prediction
+__device__ __forceinline__ void store_f32(const HermSmem &S, int k) {
+    const double *src[12] = {S.x, S.y, S.z, S.u, S.v, S.w, S.ax, S.ay, S.az, S.jx, S.jy, S.jz};
+#pragma unroll
+    for (int q = 0; q < 12; ++q) S.f[q * HCAP + k] = to_float_scaled(src[q][k], 0);
+}
+
+// Member k's position predicted to tn in FP32 from the copies, by the same
+// Horner form as the FP64 predictor, and a bound pd on its distance from the
+// FP64 prediction. Each input is within 2^-23 of its FP64 value (hs within
+// 3 2^-24), and each of the three fmaf roundings adds 2^-24 relative to the
+// magnitude of what it rounds, so every term of the polynomial is within
+// 15 2^-24 < 2^-20 of its FP64 value, relative to the sum M of the terms'
+// magnitudes; pd = 2^-18 (M_x + M_y + M_z) (plus 1e-30 for inputs flushed
+// to zero) keeps a factor 4 to spare.
+__device__ __forceinline__ void predict_f32(const HermSmem &S, int k, long long tn, float stickf) {
+    const float hs = (float)(tn - S.ti[k]) * stickf;
+    const float ah = fabsf(hs);
+    const float h6 = hs * (1.0f / 6.0f), ah6 = ah * (1.0f / 6.0f);
+    float *out[3] = {S.px, S.py, S.pz};
+    float m = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float xk = S.f[c * HCAP + k], uk = S.f[(3 + c) * HCAP + k];
+        const float ak = S.f[(6 + c) * HCAP + k], jk = S.f[(9 + c) * HCAP + k];
+        out[c][k] = fmaf(hs, fmaf(hs, fmaf(h6, jk, 0.5f * ak), uk), xk);
+        m += fmaf(ah, fmaf(ah, fmaf(ah6, fabsf(jk), 0.5f * fabsf(ak)), fabsf(uk)), fabsf(xk));
+    }
+    S.pd[k] = fmaf(m, 0x1p-18f, 1e-30f);
+}
+
+// false only when members k and l, both predicted in FP32 to the same time,
+// are surely farther apart than r_crit in their FP64 predictions: then the
+// FP64 pair test (q^2 + eps^2 >= r_crit^2) rejects the pair as well. The
+// separation is within 2^-21 (relative) of that of the FP32 positions, which
+// differ from the FP64 ones by at most pd_k + pd_l; rcf >= r_crit (1 + 2^-20).
+// Written with explicit roundings so that every call gives the same answer.
+__device__ __forceinline__ bool maybe_near(const HermSmem &S, int k, int l, float rcf) {
+    const float dx = __fsub_rn(S.px[k], S.px[l]);
+    const float dy = __fsub_rn(S.py[k], S.py[l]);
+    const float dz = __fsub_rn(S.pz[k], S.pz[l]);
+    const float q = __fsqrt_rn(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))));
+    return __fmul_rn(q, 1.0f - 0x1p-20f) <= __fadd_rn(rcf, __fadd_rn(S.pd[k], S.pd[l]));
+}
+
 // Hermite a, adot of member k from one item: partner mlo + item of this
-// CTA's range, or the star for item == npart (with `star`)
+// CTA's range (skipped at once when maybe_near rules it out), or the star
+// for item == npart (with `star`)
 __device__ __forceinline__ void herm_item(const HermSmem &S, int k, int item, int mlo, int npart,
                                           bool star, double G, double m0, const TransC &tc,
-                                          double eps2, double *aj) {
+                                          double eps2, float rcf, double *aj) {
+    if (item < npart && (mlo + item == k || !maybe_near(S, k, mlo + item, rcf))) return;
     const double xk = S.ex[k], yk = S.ey[k], zk = S.ez[k];
     const double uk = S.eu[k], vk = S.ev[k], wk = S.ew[k];
     if (item == npart) {
@@ -331,7 +396,6 @@ __device__ __forceinline__ void herm_item(const HermSmem &S, int k, int item, in
         return;
     }
     const int l = mlo + item;
-    if (l == k) return;
     double qx = xk - S.ex[l], qy = yk - S.ey[l], qz = zk - S.ez[l];
     double q2 = qx * qx + qy * qy + qz * qz + eps2;
     if (q2 >= tc.rc2) return;  // K = 1, K' = K'' = 0: no force, no jerk
@@ -531,7 +595,20 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
     const double T2d = T * T, T3 = T2d * T, T4 = T3 * T;
     const double iT2 = inv_T * inv_T, iT3 = iT2 * inv_T;
     const float T2f = (float)T2d, etaf = (float)h.eta;
+    const float stickf = (float)stick;
+    const float rcf = __double2float_ru(d.rcrit[set] * (1.0 + 0x1p-20));
     const int npart = mhi - mlo;
+    // FP32 copies of the start-up state; the corrector's constants per level
+    // (products with powers of two, so the table holds the same values)
+    __syncthreads();
+    for (int k = tid; k < n; k += blockDim.x) store_f32(S, k);
+    for (int lv = tid; lv <= KMAX; lv += blockDim.x) {
+        S.lvt[lv] = sgn * T * pow2d(-lv);
+        S.lvt[(KMAX + 1) + lv] = iT2 * pow2d(2 * lv);
+        S.lvt[2 * (KMAX + 1) + lv] = sgn * iT3 * pow2d(3 * lv);
+        S.lvt[3 * (KMAX + 1) + lv] = sgn * T3 * pow2d(-3 * lv);
+        S.lvt[4 * (KMAX + 1) + lv] = T4 * pow2d(-4 * lv);
+    }
     const bool with_star = rank == 0;
     int64_t steps = 0;
     bool capped = false;
@@ -544,16 +621,40 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
         if (tn > TT) break;  // every member has reached tau
         if (steps >= h.max_steps) { capped = true; break; }
         const int na = g_na;
-        // predict this CTA's partners and the active members to tn
-        if (warp < 3) {
-            for (int i = wl; i < npart + na; i += 32) {
-                int k = mlo + i;
-                if (i >= npart) {
-                    k = S.act[i - npart];
-                    if (k >= mlo && k < mhi) continue;
-                }
-                predict_c(S, k, warp, tn, stick);
+        // FP32 prediction of this CTA's partners and the active members to tn
+        for (int k = tid; k < n; k += HTHREADS) S.need[k] = 0;
+        for (int i = tid; i < npart + na; i += HTHREADS) {
+            int k = mlo + i;
+            if (i >= npart) {
+                k = S.act[i - npart];
+                if (k >= mlo && k < mhi) continue;
             }
+            predict_f32(S, k, tn, stickf);
+        }
+        __syncthreads();
+        // members needed in FP64: the active ones and the partners that
+        // maybe_near does not rule out for some active member
+        for (int i = tid; i < na; i += HTHREADS) S.need[S.act[i]] = 1;
+        for (int p = tid; p < na * npart; p += HTHREADS) {
+            const int ia = p / npart, l = mlo + (p - ia * npart);
+            const int k = S.act[ia];
+            if (l != k && maybe_near(S, k, l, rcf)) S.need[l] = 1;
+        }
+        __syncthreads();
+        // their FP64 prediction, one warp per coordinate, each warp listing
+        // them in member order for itself
+        if (warp < 3) {
+            int32_t *nl = S.nl + warp * HCAP;
+            int nn = 0;
+            for (int k0 = 0; k0 < n; k0 += 32) {
+                const int k = k0 + wl;
+                const bool f = k < n && S.need[k] != 0;
+                const unsigned b = __ballot_sync(0xffffffffu, f);
+                if (f) nl[nn + __popc(b & ((1u << wl) - 1u))] = k;
+                nn += __popc(b);
+            }
+            __syncwarp();
+            for (int i = wl; i < nn; i += 32) predict_c(S, nl[i], warp, tn, stick);
         }
         __syncthreads();
         for (int a0 = 0; a0 < na; a0 += ACH) {
@@ -571,11 +672,11 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                     if (slot < nc) {
                         const int k = S.act[a0 + slot];
                         for (int it = la; it < npart; it += LA)
-                            herm_item(S, k, it, mlo, npart, false, G, m0, tc, h.eps2, aj);
+                            herm_item(S, k, it, mlo, npart, false, G, m0, tc, h.eps2, rcf, aj);
                     }
                 } else if (with_star && wl < min(NG, nc - s0)) {
                     herm_item(S, S.act[a0 + s0 + wl], npart, mlo, npart, true, G, m0, tc, h.eps2,
-                              aj);
+                              rcf, aj);
                 }
 #pragma unroll
                 for (int c = 0; c < 6; ++c) S.pr[c * HTHREADS + tid] = aj[c];
@@ -622,17 +723,23 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                 for (int sl = wl; sl < nc; sl += 32) {
                     const int k = S.act[a0 + sl];
                     const int lv = S.lev[k];
-                    const double hs = sgn * T * pow2d(-lv);
-                    const double ih2 = iT2 * pow2d(2 * lv), ih3 = sgn * iT3 * pow2d(3 * lv);
-                    const double h3 = sgn * T3 * pow2d(-3 * lv), h4 = T4 * pow2d(-4 * lv);
+                    const double hs = S.lvt[lv], ih2 = S.lvt[(KMAX + 1) + lv];
+                    const double ih3 = S.lvt[2 * (KMAX + 1) + lv], h3 = S.lvt[3 * (KMAX + 1) + lv];
+                    const double h4 = S.lvt[4 * (KMAX + 1) + lv];
                     const double a1c = S.a1s[c * ACH + sl], j1c = S.a1s[(3 + c) * ACH + sl];
                     const double d = aa[k] - a1c, j0c = ja[k];
                     double a2 = (-6.0 * d - hs * (4.0 * j0c + 2.0 * j1c)) * ih2;
                     const double a3 = (12.0 * d + 6.0 * hs * (j0c + j1c)) * ih3;
-                    xa[k] = ea[k] + h4 * (a2 * (1.0 / 24.0) + hs * a3 * (1.0 / 120.0));
-                    ua[k] = fa[k] + h3 * (a2 * (1.0 / 6.0) + hs * a3 * (1.0 / 24.0));
+                    const double xn = ea[k] + h4 * (a2 * (1.0 / 24.0) + hs * a3 * (1.0 / 120.0));
+                    const double un = fa[k] + h3 * (a2 * (1.0 / 6.0) + hs * a3 * (1.0 / 24.0));
+                    xa[k] = xn;
+                    ua[k] = un;
                     aa[k] = a1c;
                     ja[k] = j1c;
+                    S.f[c * HCAP + k] = to_float_scaled(xn, 0);
+                    S.f[(3 + c) * HCAP + k] = to_float_scaled(un, 0);
+                    S.f[(6 + c) * HCAP + k] = to_float_scaled(a1c, 0);
+                    S.f[(9 + c) * HCAP + k] = to_float_scaled(j1c, 0);
                     a2 += hs * a3;
                     S.cf[c * ACH + sl] = to_float_scaled(a1c, 0);
                     S.cf[(3 + c) * ACH + sl] = to_float_scaled(j1c, -lv);

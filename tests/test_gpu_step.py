@@ -232,7 +232,7 @@ def test_ensemble_full_size_sampled(gpu, oracle):
         spread = _chaos_spread(oracle, ws, 3)
         keep = np.array([i not in skip for i in range(b - a)])
         _check_positions(qg[a:b][keep], r.q[keep], spread[keep], rel=1e-11)
-    assert max_set < 448 and st["max_set"] < 448
+    assert max_set < 320 and st["max_set"] < 320
 
 
 def test_merged_kicks_equal_two_kicks(gpu, oracle):
