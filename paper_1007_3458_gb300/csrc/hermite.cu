@@ -375,12 +375,12 @@ __device__ __forceinline__ bool maybe_near(const HermSmem &S, int k, int l, floa
 }
 
 // Hermite a, adot of member k from one item: partner mlo + item of this
-// CTA's range (skipped at once when maybe_near rules it out), or the star
-// for item == npart (with `star`)
+// CTA's range (with f32, skipped at once when maybe_near rules it out), or
+// the star for item == npart (with `star`)
 __device__ __forceinline__ void herm_item(const HermSmem &S, int k, int item, int mlo, int npart,
                                           bool star, double G, double m0, const TransC &tc,
-                                          double eps2, float rcf, double *aj) {
-    if (item < npart && (mlo + item == k || !maybe_near(S, k, mlo + item, rcf))) return;
+                                          double eps2, bool f32, float rcf, double *aj) {
+    if (item < npart && (mlo + item == k || (f32 && !maybe_near(S, k, mlo + item, rcf)))) return;
     const double xk = S.ex[k], yk = S.ey[k], zk = S.ez[k];
     const double uk = S.eu[k], vk = S.ev[k], wk = S.ew[k];
     if (item == npart) {
@@ -426,20 +426,32 @@ __shared__ int g_na;
 
 // Next block time (the earliest end of a member's step) and the members whose
 // step ends then, in member order, by warp 0 alone; every thread reads
-// (tn, na) after the barrier that follows.
+// (tn, na) after the barrier that follows. The end times stay in registers
+// between the two passes; the minimum (below 2^49) is taken as the minimum of
+// the high words, then of the low words among the lanes that hold it.
 __device__ __forceinline__ void next_block(const int32_t *lev, const long long *ti, int32_t *act,
                                            int n) {
+    constexpr int NI = HCAP / 32;
     const int wl = threadIdx.x & 31;
+    long long te[NI];
     long long t = LLONG_MAX;
-    for (int k = wl; k < n; k += 32) t = min(t, ti[k] + (1ll << (48 - lev[k])));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t = min(t, __shfl_xor_sync(0xffffffffu, t, o));
+    for (int q = 0; q < NI; ++q) {
+        const int k = q * 32 + wl;
+        te[q] = (k < n) ? ti[k] + (1ll << (KMAX - lev[k])) : LLONG_MAX;
+        t = min(t, te[q]);
+    }
+    const unsigned hi = __reduce_min_sync(0xffffffffu, (unsigned)(t >> 32));
+    const unsigned lo =
+        __reduce_min_sync(0xffffffffu, (unsigned)(t >> 32) == hi ? (unsigned)t : 0xffffffffu);
+    t = (long long)(((unsigned long long)hi << 32) | lo);
     int na = 0;
-    for (int k0 = 0; k0 < n; k0 += 32) {
-        const int k = k0 + wl;
-        const bool f = k < n && ti[k] + (1ll << (48 - lev[k])) == t;
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+        if (q * 32 >= n) break;
+        const bool f = te[q] == t;
         const unsigned b = __ballot_sync(0xffffffffu, f);
-        if (f) act[na + __popc(b & ((1u << wl) - 1u))] = k;
+        if (f) act[na + __popc(b & ((1u << wl) - 1u))] = q * 32 + wl;
         na += __popc(b);
     }
     if (wl == 0) {
@@ -621,40 +633,55 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
         if (tn > TT) break;  // every member has reached tau
         if (steps >= h.max_steps) { capped = true; break; }
         const int na = g_na;
-        // FP32 prediction of this CTA's partners and the active members to tn
-        for (int k = tid; k < n; k += HTHREADS) S.need[k] = 0;
-        for (int i = tid; i < npart + na; i += HTHREADS) {
-            int k = mlo + i;
-            if (i >= npart) {
-                k = S.act[i - npart];
-                if (k >= mlo && k < mhi) continue;
+        // Predict this CTA's partners and the active members to tn. When they
+        // fit one warp, one FP64 pass per coordinate predicts them all; above
+        // that the FP32 prediction first rules out the partners that are
+        // surely beyond r_crit of every active member.
+        const bool f32 = npart + na > 32;
+        if (!f32) {
+            if (warp < 3) {
+                const int i = wl;
+                if (i < npart + na) {
+                    int k = mlo + i;
+                    if (i >= npart) k = S.act[i - npart];
+                    if (i < npart || k < mlo || k >= mhi) predict_c(S, k, warp, tn, stick);
+                }
             }
-            predict_f32(S, k, tn, stickf);
-        }
-        __syncthreads();
-        // members needed in FP64: the active ones and the partners that
-        // maybe_near does not rule out for some active member
-        for (int i = tid; i < na; i += HTHREADS) S.need[S.act[i]] = 1;
-        for (int p = tid; p < na * npart; p += HTHREADS) {
-            const int ia = p / npart, l = mlo + (p - ia * npart);
-            const int k = S.act[ia];
-            if (l != k && maybe_near(S, k, l, rcf)) S.need[l] = 1;
-        }
-        __syncthreads();
-        // their FP64 prediction, one warp per coordinate, each warp listing
-        // them in member order for itself
-        if (warp < 3) {
-            int32_t *nl = S.nl + warp * HCAP;
-            int nn = 0;
-            for (int k0 = 0; k0 < n; k0 += 32) {
-                const int k = k0 + wl;
-                const bool f = k < n && S.need[k] != 0;
-                const unsigned b = __ballot_sync(0xffffffffu, f);
-                if (f) nl[nn + __popc(b & ((1u << wl) - 1u))] = k;
-                nn += __popc(b);
+        } else {
+            for (int k = tid; k < n; k += HTHREADS) S.need[k] = 0;
+            for (int i = tid; i < npart + na; i += HTHREADS) {
+                int k = mlo + i;
+                if (i >= npart) {
+                    k = S.act[i - npart];
+                    if (k >= mlo && k < mhi) continue;
+                }
+                predict_f32(S, k, tn, stickf);
             }
-            __syncwarp();
-            for (int i = wl; i < nn; i += 32) predict_c(S, nl[i], warp, tn, stick);
+            __syncthreads();
+            // members needed in FP64: the active ones and the partners that
+            // maybe_near does not rule out for some active member
+            for (int i = tid; i < na; i += HTHREADS) S.need[S.act[i]] = 1;
+            for (int p = tid; p < na * npart; p += HTHREADS) {
+                const int ia = p / npart, l = mlo + (p - ia * npart);
+                const int k = S.act[ia];
+                if (l != k && maybe_near(S, k, l, rcf)) S.need[l] = 1;
+            }
+            __syncthreads();
+            // their FP64 prediction, one warp per coordinate, each warp listing
+            // them in member order for itself
+            if (warp < 3) {
+                int32_t *nl = S.nl + warp * HCAP;
+                int nn = 0;
+                for (int k0 = 0; k0 < n; k0 += 32) {
+                    const int k = k0 + wl;
+                    const bool f = k < n && S.need[k] != 0;
+                    const unsigned b = __ballot_sync(0xffffffffu, f);
+                    if (f) nl[nn + __popc(b & ((1u << wl) - 1u))] = k;
+                    nn += __popc(b);
+                }
+                __syncwarp();
+                for (int i = wl; i < nn; i += 32) predict_c(S, nl[i], warp, tn, stick);
+            }
         }
         __syncthreads();
         for (int a0 = 0; a0 < na; a0 += ACH) {
@@ -672,11 +699,12 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                     if (slot < nc) {
                         const int k = S.act[a0 + slot];
                         for (int it = la; it < npart; it += LA)
-                            herm_item(S, k, it, mlo, npart, false, G, m0, tc, h.eps2, rcf, aj);
+                            herm_item(S, k, it, mlo, npart, false, G, m0, tc, h.eps2, f32, rcf,
+                                      aj);
                     }
                 } else if (with_star && wl < min(NG, nc - s0)) {
                     herm_item(S, S.act[a0 + s0 + wl], npart, mlo, npart, true, G, m0, tc, h.eps2,
-                              rcf, aj);
+                              f32, rcf, aj);
                 }
 #pragma unroll
                 for (int c = 0; c < 6; ++c) S.pr[c * HTHREADS + tid] = aj[c];
