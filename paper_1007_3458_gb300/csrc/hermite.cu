@@ -63,8 +63,9 @@ struct TransC {
     double rc2;  // r_crit^2: K = 1 (and K' = K'' = 0) beyond
     double a;    // 1.1 / r_crit
     double c;    // (pi / 2) a: K' = c cos, K'' = -c^2 sin
+    double nc2;  // -c^2
     __device__ __forceinline__ explicit TransC(double rc)
-        : rc2(rc * rc), a(1.1 / rc), c(0.5 * kPi * (1.1 / rc)) {}
+        : rc2(rc * rc), a(1.1 / rc), c(0.5 * kPi * (1.1 / rc)), nc2(-c * c) {}
 };
 
 // K and its first and second derivatives with respect to s
@@ -80,7 +81,7 @@ __device__ __forceinline__ void transition(double s, const TransC &tc, double &K
         sincos_half_pi(y, sn, cs);
         K = sn;
         Kp = tc.c * cs;
-        Kpp = -tc.c * tc.c * sn;
+        Kpp = tc.nc2 * sn;
     }
 }
 
@@ -117,14 +118,22 @@ constexpr int ACH = 64;    // active members per force round (exchange, correcti
 
 constexpr int KMAX = 48;
 
+// corrector constants of a level's step h (signed), rows of HermSmem::lvt:
+// a2 = (-6 d - h (4 j0 + 2 j1)) / h^2 = A2D d + A2J0 j0 + A2J1 j1,
+// a3 = (12 d + 6 h (j0 + j1)) / h^3 = A3D d + A3J (j0 + j1),
+// x1 = x_p + h^4/24 a2 + h^5/120 a3, v1 = v_p + h^3/6 a2 + h^4/24 a3,
+// and a2 at the end of the step, a2 + h a3 (d = a0 - a1)
+enum LvConst : int { LV_H = 0, LV_A2D, LV_A2J0, LV_A2J1, LV_A3D, LV_A3J, LV_H4, LV_H5, LV_H3, LV_N };
+
 struct HermSmem {
-    double *ex, *ey, *ez, *eu, *ev, *ew, *m;  // evaluation point of every member
+    double *ex, *ey, *ez, *eu, *ev, *ew;      // evaluation point of every member
+    double *gm;                               // -G m of every member
     double *x, *y, *z, *u, *v, *w;            // state at the member's own time
     double *ax, *ay, *az, *jx, *jy, *jz;      // a, adot at the member's own time
     double *pb;                               // partial a, adot [2][6][ACH] (cluster exchange)
     double *pr;                               // per-lane partial a, adot [6][HTHREADS]
     double *a1s;                              // a, adot of the round's active members [6][ACH]
-    double *lvt;                              // corrector constants per level [5][KMAX + 1]
+    double *lvt;                              // corrector constants per level [LV_N][KMAX + 1]
     long long *ti;                            // member time in ticks
     float *f;                                 // x..z, u..w, ax..az, jx..jz cut to FP32 [12][HCAP]
     float *px, *py, *pz, *pd;                 // FP32 prediction and its error bound
@@ -141,7 +150,7 @@ __device__ __forceinline__ HermSmem carve(void *base) {
     HermSmem s;
     s.ex = p; p += HCAP; s.ey = p; p += HCAP; s.ez = p; p += HCAP;
     s.eu = p; p += HCAP; s.ev = p; p += HCAP; s.ew = p; p += HCAP;
-    s.m = p; p += HCAP;
+    s.gm = p; p += HCAP;
     s.x = p; p += HCAP; s.y = p; p += HCAP; s.z = p; p += HCAP;
     s.u = p; p += HCAP; s.v = p; p += HCAP; s.w = p; p += HCAP;
     s.ax = p; p += HCAP; s.ay = p; p += HCAP; s.az = p; p += HCAP;
@@ -149,7 +158,7 @@ __device__ __forceinline__ HermSmem carve(void *base) {
     s.pb = p; p += 2 * 6 * ACH;
     s.pr = p; p += 6 * HTHREADS;
     s.a1s = p; p += 6 * ACH;
-    s.lvt = p; p += 5 * (KMAX + 1);
+    s.lvt = p; p += LV_N * (KMAX + 1);
     s.ti = (long long *)p; p += HCAP;
     float *fp = (float *)p;
     s.f = fp; fp += 12 * HCAP;
@@ -164,7 +173,7 @@ __device__ __forceinline__ HermSmem carve(void *base) {
     return s;
 }
 constexpr size_t kHermSmem =
-    sizeof(double) * (HCAP * 20 + 2 * 6 * ACH + 6 * HTHREADS + 6 * ACH + 5 * (KMAX + 1)) +
+    sizeof(double) * (HCAP * 20 + 2 * 6 * ACH + 6 * HTHREADS + 6 * ACH + LV_N * (KMAX + 1)) +
     sizeof(float) * (16 * HCAP + 12 * ACH) + sizeof(int32_t) * HCAP * 7;
 // two CTAs per SM (228 KB of shared memory, 1 KB of it per CTA reserved)
 static_assert(2 * (kHermSmem + 1024) <= 228 * 1024, "Hermite shared memory above two CTAs per SM");
@@ -199,7 +208,7 @@ __device__ __forceinline__ void group_sum(double *v, int cnt, int P) {
 // partial (1-K)-weighted pair acceleration of member k at the evaluation
 // point, unsmoothed (the kick used the bare separation):
 // sum_l -G m_l q_kl / q^3 [1 - K + q K'] over the partners of this lane
-__device__ void kcorr_part(const HermSmem &S, int lo, int hi, int k, int l0, int P, double G,
+__device__ void kcorr_part(const HermSmem &S, int lo, int hi, int k, int l0, int P,
                            const TransC &tc, double *c) {
     c[0] = c[1] = c[2] = 0.0;
     for (int l = lo + l0; l < hi; l += P) {
@@ -211,7 +220,7 @@ __device__ void kcorr_part(const HermSmem &S, int lo, int hi, int k, int l0, int
         const double q = q2 * qi;
         double K, Kp, Kpp;
         transition(q, tc, K, Kp, Kpp);
-        double wgt = -G * S.m[l] * (qi * qi * qi) * (1.0 - K + q * Kp);
+        double wgt = S.gm[l] * (qi * qi * qi) * (1.0 - K + q * Kp);
         c[0] += wgt * qx;
         c[1] += wgt * qy;
         c[2] += wgt * qz;
@@ -223,7 +232,7 @@ __device__ void kcorr_part(const HermSmem &S, int lo, int hi, int k, int l0, int
 // terms with the transition bracket over this lane's partners (one
 // reciprocal square root per pair: q = q2 / sqrt(q2), 1/q^3, 1/q^2)
 __device__ void herm_part(const HermSmem &S, int lo, int hi, int k, int l0, int P, bool star,
-                          double G, double m0, const TransC &tc, double eps2, double *aj) {
+                          double gm0, const TransC &tc, double eps2, double *aj) {
     const double xk = S.ex[k], yk = S.ey[k], zk = S.ez[k];
     const double uk = S.eu[k], vk = S.ev[k], wk = S.ew[k];
     for (int c = 0; c < 6; ++c) aj[c] = 0.0;
@@ -232,7 +241,7 @@ __device__ void herm_part(const HermSmem &S, int lo, int hi, int k, int l0, int 
         double si = rsqrt(s2);
         double si2 = si * si;
         double rv = xk * uk + yk * vk + zk * wk;
-        double c = -G * m0 * (si2 * si);
+        double c = gm0 * (si2 * si);
         double t = 3.0 * rv * si2;
         aj[0] = c * xk; aj[1] = c * yk; aj[2] = c * zk;
         aj[3] = c * (uk - t * xk); aj[4] = c * (vk - t * yk); aj[5] = c * (wk - t * zk);
@@ -250,7 +259,7 @@ __device__ void herm_part(const HermSmem &S, int lo, int hi, int k, int l0, int 
         transition(sq, tc, K, Kp, Kpp);
         double br = 1.0 - K + sq * Kp;
         double rvl = qx * px + qy * py + qz * pz;
-        double cl = -G * S.m[l] * (qi2 * qi);
+        double cl = S.gm[l] * (qi2 * qi);
         double tl = 3.0 * rvl * qi2;
         aj[0] += cl * br * qx; aj[1] += cl * br * qy; aj[2] += cl * br * qz;
         aj[3] += cl * (rvl * qx * Kpp + (px - tl * qx) * br);
@@ -378,8 +387,8 @@ __device__ __forceinline__ bool maybe_near(const HermSmem &S, int k, int l, floa
 // CTA's range (with f32, skipped at once when maybe_near rules it out), or
 // the star for item == npart (with `star`)
 __device__ __forceinline__ void herm_item(const HermSmem &S, int k, int item, int mlo, int npart,
-                                          bool star, double G, double m0, const TransC &tc,
-                                          double eps2, bool f32, float rcf, double *aj) {
+                                          bool star, double gm0, const TransC &tc, double eps2,
+                                          bool f32, float rcf, double *aj) {
     if (item < npart && (mlo + item == k || (f32 && !maybe_near(S, k, mlo + item, rcf)))) return;
     const double xk = S.ex[k], yk = S.ey[k], zk = S.ez[k];
     const double uk = S.eu[k], vk = S.ev[k], wk = S.ew[k];
@@ -389,7 +398,7 @@ __device__ __forceinline__ void herm_item(const HermSmem &S, int k, int item, in
         double si = rsqrt(s2);
         double si2 = si * si;
         double rv = xk * uk + yk * vk + zk * wk;
-        double c = -G * m0 * (si2 * si);
+        double c = gm0 * (si2 * si);
         double t = 3.0 * rv * si2;
         aj[0] += c * xk; aj[1] += c * yk; aj[2] += c * zk;
         aj[3] += c * (uk - t * xk); aj[4] += c * (vk - t * yk); aj[5] += c * (wk - t * zk);
@@ -405,14 +414,17 @@ __device__ __forceinline__ void herm_item(const HermSmem &S, int k, int item, in
     const double sq = q2 * qi;
     double K, Kp, Kpp;
     transition(sq, tc, K, Kp, Kpp);
-    double br = 1.0 - K + sq * Kp;
-    double rvl = qx * px + qy * py + qz * pz;
-    double cl = -G * S.m[l] * (qi2 * qi);
-    double tl = 3.0 * rvl * qi2;
-    aj[0] += cl * br * qx; aj[1] += cl * br * qy; aj[2] += cl * br * qz;
-    aj[3] += cl * (rvl * qx * Kpp + (px - tl * qx) * br);
-    aj[4] += cl * (rvl * qy * Kpp + (py - tl * qy) * br);
-    aj[5] += cl * (rvl * qz * Kpp + (pz - tl * qz) * br);
+    const double br = 1.0 - K + sq * Kp;
+    const double rvl = qx * px + qy * py + qz * pz;
+    // cl = -G m_l / q^3; the jerk cl [rvl Kpp q + (p - 3 rvl q / q^2) br]
+    // regrouped as cb p + cq q, cb = cl br, cq = cl rvl (Kpp - 3 br / q^2)
+    const double cl = S.gm[l] * (qi2 * qi);
+    const double cb = cl * br;
+    const double cq = (cl * rvl) * fma(-3.0 * qi2, br, Kpp);
+    aj[0] = fma(cb, qx, aj[0]); aj[1] = fma(cb, qy, aj[1]); aj[2] = fma(cb, qz, aj[2]);
+    aj[3] = fma(cb, px, fma(cq, qx, aj[3]));
+    aj[4] = fma(cb, py, fma(cq, qy, aj[4]));
+    aj[5] = fma(cb, pz, fma(cq, qz, aj[5]));
 }
 
 struct HermArgs {
@@ -521,9 +533,9 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
     }
     __syncthreads();
     const int64_t star_row = d.offsets[d.sys_of[S.ids[0]]];
-    const double m0 = d.m[star_row];
+    const double gm0 = -h.G * d.m[star_row];
     const TransC tc(d.rcrit[set]);
-    const double G = h.G, tau = h.tau;
+    const double tau = h.tau;
     // state entering the Kepler drift (after the first kick)
     for (int k = tid; k < n; k += blockDim.x) {
         int64_t r = S.ids[k];
@@ -533,14 +545,14 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
         S.u[k] = d.v[r];
         S.v[k] = d.v[R + r];
         S.w[k] = d.v[2 * R + r];
-        S.m[k] = d.m[r];
+        S.gm[k] = -h.G * d.m[r];
     }
     __syncthreads();
     // item 5: remove the (1-K) part of the first kick (own members)
     for (int k0 = mlo; k0 < mhi; k0 += NG) {
         int k = k0 + grp;
         double c[3] = {0.0, 0.0, 0.0};
-        if (k < mhi) kcorr_part(S, 0, n, k, lane, P, G, tc, c);
+        if (k < mhi) kcorr_part(S, 0, n, k, lane, P, tc, c);
         group_sum(c, 3, P);
         if (k < mhi && lane == 0) {
             S.u[k] -= 0.5 * tau * c[0];
@@ -570,7 +582,7 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
     for (int k0 = mlo; k0 < mhi; k0 += NG) {
         int k = k0 + grp;
         double aj[6] = {0, 0, 0, 0, 0, 0};
-        if (k < mhi) herm_part(S, 0, n, k, lane, P, true, G, m0, tc, h.eps2, aj);
+        if (k < mhi) herm_part(S, 0, n, k, lane, P, true, gm0, tc, h.eps2, aj);
         group_sum(aj, 6, P);
         if (k < mhi && lane == 0) {
             S.ax[k] = aj[0]; S.ay[k] = aj[1]; S.az[k] = aj[2];
@@ -615,11 +627,17 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
     __syncthreads();
     for (int k = tid; k < n; k += blockDim.x) store_f32(S, k);
     for (int lv = tid; lv <= KMAX; lv += blockDim.x) {
-        S.lvt[lv] = sgn * T * pow2d(-lv);
-        S.lvt[(KMAX + 1) + lv] = iT2 * pow2d(2 * lv);
-        S.lvt[2 * (KMAX + 1) + lv] = sgn * iT3 * pow2d(3 * lv);
-        S.lvt[3 * (KMAX + 1) + lv] = sgn * T3 * pow2d(-3 * lv);
-        S.lvt[4 * (KMAX + 1) + lv] = T4 * pow2d(-4 * lv);
+        double *L = S.lvt + lv;
+        const double ih = sgn * inv_T * pow2d(lv), ih2 = iT2 * pow2d(2 * lv);
+        L[LV_H * (KMAX + 1)] = sgn * T * pow2d(-lv);
+        L[LV_A2D * (KMAX + 1)] = -6.0 * ih2;
+        L[LV_A2J0 * (KMAX + 1)] = -4.0 * ih;
+        L[LV_A2J1 * (KMAX + 1)] = -2.0 * ih;
+        L[LV_A3D * (KMAX + 1)] = 12.0 * (sgn * iT3 * pow2d(3 * lv));
+        L[LV_A3J * (KMAX + 1)] = 6.0 * ih2;
+        L[LV_H4 * (KMAX + 1)] = (T4 * pow2d(-4 * lv)) * (1.0 / 24.0);
+        L[LV_H5 * (KMAX + 1)] = (sgn * T4 * T * pow2d(-5 * lv)) * (1.0 / 120.0);
+        L[LV_H3 * (KMAX + 1)] = (sgn * T3 * pow2d(-3 * lv)) * (1.0 / 6.0);
     }
     const bool with_star = rank == 0;
     int64_t steps = 0;
@@ -699,12 +717,11 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                     if (slot < nc) {
                         const int k = S.act[a0 + slot];
                         for (int it = la; it < npart; it += LA)
-                            herm_item(S, k, it, mlo, npart, false, G, m0, tc, h.eps2, f32, rcf,
-                                      aj);
+                            herm_item(S, k, it, mlo, npart, false, gm0, tc, h.eps2, f32, rcf, aj);
                     }
                 } else if (with_star && wl < min(NG, nc - s0)) {
-                    herm_item(S, S.act[a0 + s0 + wl], npart, mlo, npart, true, G, m0, tc, h.eps2,
-                              f32, rcf, aj);
+                    herm_item(S, S.act[a0 + s0 + wl], npart, mlo, npart, true, gm0, tc, h.eps2, f32,
+                              rcf, aj);
                 }
 #pragma unroll
                 for (int c = 0; c < 6; ++c) S.pr[c * HTHREADS + tid] = aj[c];
@@ -751,15 +768,15 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                 for (int sl = wl; sl < nc; sl += 32) {
                     const int k = S.act[a0 + sl];
                     const int lv = S.lev[k];
-                    const double hs = S.lvt[lv], ih2 = S.lvt[(KMAX + 1) + lv];
-                    const double ih3 = S.lvt[2 * (KMAX + 1) + lv], h3 = S.lvt[3 * (KMAX + 1) + lv];
-                    const double h4 = S.lvt[4 * (KMAX + 1) + lv];
+                    const double *L = S.lvt + lv;
+                    constexpr int LS = KMAX + 1;
                     const double a1c = S.a1s[c * ACH + sl], j1c = S.a1s[(3 + c) * ACH + sl];
                     const double d = aa[k] - a1c, j0c = ja[k];
-                    double a2 = (-6.0 * d - hs * (4.0 * j0c + 2.0 * j1c)) * ih2;
-                    const double a3 = (12.0 * d + 6.0 * hs * (j0c + j1c)) * ih3;
-                    const double xn = ea[k] + h4 * (a2 * (1.0 / 24.0) + hs * a3 * (1.0 / 120.0));
-                    const double un = fa[k] + h3 * (a2 * (1.0 / 6.0) + hs * a3 * (1.0 / 24.0));
+                    const double a2 =
+                        fma(L[LV_A2D * LS], d, fma(L[LV_A2J0 * LS], j0c, L[LV_A2J1 * LS] * j1c));
+                    const double a3 = fma(L[LV_A3D * LS], d, L[LV_A3J * LS] * (j0c + j1c));
+                    const double xn = fma(L[LV_H4 * LS], a2, fma(L[LV_H5 * LS], a3, ea[k]));
+                    const double un = fma(L[LV_H3 * LS], a2, fma(L[LV_H4 * LS], a3, fa[k]));
                     xa[k] = xn;
                     ua[k] = un;
                     aa[k] = a1c;
@@ -768,10 +785,10 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                     S.f[(3 + c) * HCAP + k] = to_float_scaled(un, 0);
                     S.f[(6 + c) * HCAP + k] = to_float_scaled(a1c, 0);
                     S.f[(9 + c) * HCAP + k] = to_float_scaled(j1c, 0);
-                    a2 += hs * a3;
+                    const double a2e = fma(L[LV_H * LS], a3, a2);  // a2 at the end of the step
                     S.cf[c * ACH + sl] = to_float_scaled(a1c, 0);
                     S.cf[(3 + c) * ACH + sl] = to_float_scaled(j1c, -lv);
-                    S.cf[(6 + c) * ACH + sl] = to_float_scaled(a2, -2 * lv);
+                    S.cf[(6 + c) * ACH + sl] = to_float_scaled(a2e, -2 * lv);
                     S.cf[(9 + c) * ACH + sl] = to_float_scaled(a3, -3 * lv);
                 }
             }
@@ -805,7 +822,7 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
     for (int k0 = mlo; k0 < mhi; k0 += NG) {
         int k = k0 + grp;
         double c[3] = {0.0, 0.0, 0.0};
-        if (k < mhi) kcorr_part(S, 0, n, k, lane, P, G, tc, c);
+        if (k < mhi) kcorr_part(S, 0, n, k, lane, P, tc, c);
         group_sum(c, 3, P);
         if (k < mhi && lane == 0) {
             int64_t r = S.ids[k];
