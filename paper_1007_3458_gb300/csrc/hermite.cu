@@ -115,6 +115,7 @@ constexpr int CL = 8;      // CTAs of a cluster sharing one large set (the tree 
 #endif
 constexpr int NBIG = QYM_HERM_NBIG;  // sets of at least this many members use a whole cluster
 constexpr int ACH = 64;    // active members per force round (exchange, correction)
+constexpr int RSL = 16;    // members per force round on a cluster (receive buffer slots)
 
 constexpr int KMAX = 48;
 
@@ -130,8 +131,8 @@ struct HermSmem {
     double *gm;                               // -G m of every member
     double *x, *y, *z, *u, *v, *w;            // state at the member's own time
     double *ax, *ay, *az, *jx, *jy, *jz;      // a, adot at the member's own time
-    double *pb;                               // partial a, adot [2][6][ACH] (cluster exchange)
     double *pr;                               // per-lane partial a, adot [6][HTHREADS]
+    double *rb;                               // partials received from each CTA [2][CL][6][RSL]
     double *a1s;                              // a, adot of the round's active members [6][ACH]
     double *lvt;                              // corrector constants per level [LV_N][KMAX + 1]
     long long *ti;                            // member time in ticks
@@ -155,8 +156,8 @@ __device__ __forceinline__ HermSmem carve(void *base) {
     s.u = p; p += HCAP; s.v = p; p += HCAP; s.w = p; p += HCAP;
     s.ax = p; p += HCAP; s.ay = p; p += HCAP; s.az = p; p += HCAP;
     s.jx = p; p += HCAP; s.jy = p; p += HCAP; s.jz = p; p += HCAP;
-    s.pb = p; p += 2 * 6 * ACH;
     s.pr = p; p += 6 * HTHREADS;
+    s.rb = p; p += 2 * CL * 6 * RSL;
     s.a1s = p; p += 6 * ACH;
     s.lvt = p; p += LV_N * (KMAX + 1);
     s.ti = (long long *)p; p += HCAP;
@@ -173,7 +174,7 @@ __device__ __forceinline__ HermSmem carve(void *base) {
     return s;
 }
 constexpr size_t kHermSmem =
-    sizeof(double) * (HCAP * 20 + 2 * 6 * ACH + 6 * HTHREADS + 6 * ACH + LV_N * (KMAX + 1)) +
+    sizeof(double) * (HCAP * 20 + 6 * HTHREADS + 2 * CL * 6 * RSL + 6 * ACH + LV_N * (KMAX + 1)) +
     sizeof(float) * (16 * HCAP + 12 * ACH) + sizeof(int32_t) * HCAP * 7;
 // two CTAs per SM (228 KB of shared memory, 1 KB of it per CTA reserved)
 static_assert(2 * (kHermSmem + 1024) <= 228 * 1024, "Hermite shared memory above two CTAs per SM");
@@ -622,6 +623,10 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
     const float stickf = (float)stick;
     const float rcf = __double2float_ru(d.rcrit[set] * (1.0 + 0x1p-20));
     const int npart = mhi - mlo;
+    // the largest range of the cluster: every CTA derives its lane layout and
+    // its round count from it, so all CTAs pass the same cluster barriers and
+    // lay out their partial sums alike
+    const int npmax = (n + cs - 1) / cs;
     // FP32 copies of the start-up state; the corrector's constants per level
     // (products with powers of two, so the table holds the same values)
     __syncthreads();
@@ -651,15 +656,14 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
         if (tn > TT) break;  // every member has reached tau
         if (steps >= h.max_steps) { capped = true; break; }
         const int na = g_na;
-        // Predict this CTA's partners and the active members to tn. When they
-        // fit one warp, one FP64 pass per coordinate predicts them all; above
-        // that the FP32 prediction first rules out the partners that are
+        // Predict this CTA's partners and the active members to tn. Up to two
+        // warps' worth, FP64 passes over them all (one warp per coordinate);
+        // above that the FP32 prediction first rules out the partners that are
         // surely beyond r_crit of every active member.
-        const bool f32 = npart + na > 32;
+        const bool f32 = npmax + na > 64;
         if (!f32) {
             if (warp < 3) {
-                const int i = wl;
-                if (i < npart + na) {
+                for (int i = wl; i < npart + na; i += 32) {
                     int k = mlo + i;
                     if (i >= npart) k = S.act[i - npart];
                     if (i < npart || k < mlo || k >= mhi) predict_c(S, k, warp, tn, stick);
@@ -707,9 +711,10 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
             // pair items on warps 0-6 (LA lanes per member), the star's pull
             // (rank 0) on warp 7, so neither path diverges inside a warp
             int LA = 1;
-            while (LA < npart && LA < 64) LA <<= 1;
-            const int NG = min(32, (HTHREADS - 32) / LA);  // warp 7 holds one star per slot
-            double *dst = COOP ? S.pb + buf * 6 * ACH : S.a1s;
+            while (LA < npmax && LA < 64) LA <<= 1;
+            // slots per round (warp 7 holds one star per slot; on a cluster at
+            // most RSL, the receive buffer's width)
+            const int NG = min(COOP ? RSL : 32, (HTHREADS - 32) / LA);
             for (int s0 = 0; s0 < nc; s0 += NG) {
                 double aj[6] = {0, 0, 0, 0, 0, 0};
                 if (warp < 7) {
@@ -723,37 +728,59 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                     herm_item(S, S.act[a0 + s0 + wl], npart, mlo, npart, true, gm0, tc, h.eps2, f32,
                               rcf, aj);
                 }
+                double *prb = S.pr;
 #pragma unroll
-                for (int c = 0; c < 6; ++c) S.pr[c * HTHREADS + tid] = aj[c];
-                __syncthreads();
-                // sums over the LA lanes of each (member, component), one warp
-                // each, in a fixed order
+                for (int c = 0; c < 6; ++c) prb[c * HTHREADS + tid] = aj[c];
                 const int cnt = min(NG, nc - s0);
-                for (int pi = warp; pi < 6 * cnt; pi += HTHREADS / 32) {
-                    const int sl = pi / 6, c = pi - 6 * sl;
-                    const double *col = S.pr + c * HTHREADS + sl * LA;
-                    double v = 0.0;
-                    for (int m = wl; m < LA; m += 32) v += col[m];
-                    for (int off = (LA < 32 ? LA : 32) >> 1; off > 0; off >>= 1)
-                        v += __shfl_xor_sync(0xffffffffu, v, off);
-                    if (wl == 0) dst[c * ACH + s0 + sl] = v + S.pr[c * HTHREADS + 224 + sl];
-                }
-                __syncthreads();
-            }
-            if (COOP) {
-                cl.sync();
-                // the CTAs' partial sums in rank order, one warp per component
-                if (warp < 6) {
-                    const int c = warp;
-                    for (int sl = wl; sl < nc; sl += 32) {
+                if (COOP) {
+                    // This CTA's part of every (member, component): its LA lanes
+                    // summed by a group of eight lanes in a fixed order (plus the
+                    // star's pull on rank 0), stored by lane g into CTA g's
+                    // receive buffer under this rank; after the cluster barrier
+                    // every CTA adds the CTAs' parts in rank order. Receive
+                    // buffers are double-buffered: a CTA stores into this one
+                    // again only after the next round's cluster barrier, which
+                    // every CTA passes after reading it.
+                    __syncthreads();
+                    double *rbb = S.rb + buf * (CL * 6 * RSL);
+                    const int g = wl & 7;
+                    for (int pi0 = warp * 4; pi0 < 6 * cnt; pi0 += HTHREADS / 8) {
+                        const int pi = pi0 + (wl >> 3);
+                        const bool live = pi < 6 * cnt;
+                        const int sl = pi / 6, c = pi - 6 * sl;
+                        double v = 0.0;
+                        if (live)
+                            for (int m = g; m < LA; m += 8) v += prb[c * HTHREADS + sl * LA + m];
+                        v += __shfl_xor_sync(0xffffffffu, v, 1);
+                        v += __shfl_xor_sync(0xffffffffu, v, 2);
+                        v += __shfl_xor_sync(0xffffffffu, v, 4);
+                        if (live && with_star) v += prb[c * HTHREADS + 224 + sl];
+                        if (live) cl.map_shared_rank(rbb, g)[(rank * 6 + c) * RSL + sl] = v;
+                    }
+                    cl.sync();
+                    for (int pi = tid; pi < 6 * cnt; pi += HTHREADS) {
+                        const int sl = pi / 6, c = pi - 6 * sl;
                         double pv[CL];
 #pragma unroll
-                        for (int r = 0; r < CL; ++r) pv[r] = cl.map_shared_rank(dst, r)[c * ACH + sl];
-                        S.a1s[c * ACH + sl] = ((pv[0] + pv[1]) + (pv[2] + pv[3])) +
-                                              ((pv[4] + pv[5]) + (pv[6] + pv[7]));
+                        for (int r = 0; r < CL; ++r) pv[r] = rbb[(r * 6 + c) * RSL + sl];
+                        S.a1s[c * ACH + s0 + sl] = ((pv[0] + pv[1]) + (pv[2] + pv[3])) +
+                                                   ((pv[4] + pv[5]) + (pv[6] + pv[7]));
+                    }
+                    buf ^= 1;
+                } else {
+                    __syncthreads();
+                    // sums over the LA lanes of each (member, component), one
+                    // warp each, in a fixed order
+                    for (int pi = warp; pi < 6 * cnt; pi += HTHREADS / 32) {
+                        const int sl = pi / 6, c = pi - 6 * sl;
+                        const double *col = prb + c * HTHREADS + sl * LA;
+                        double v = 0.0;
+                        for (int m = wl; m < LA; m += 32) v += col[m];
+                        for (int off = (LA < 32 ? LA : 32) >> 1; off > 0; off >>= 1)
+                            v += __shfl_xor_sync(0xffffffffu, v, off);
+                        if (wl == 0) S.a1s[c * ACH + s0 + sl] = v + prb[c * HTHREADS + 224 + sl];
                     }
                 }
-                buf ^= 1;
                 __syncthreads();
             }
             // corrector, one warp per coordinate (the same in every CTA)

@@ -156,6 +156,40 @@ def test_batched_systems(gpu, oracle):
         assert np.all(np.abs(E - Eo) <= 1e-12 * np.abs(Eo) + 100 * espread)
 
 
+def _planet_swarm(k, seed):
+    """Star, a Jupiter-mass planet at a = 1 and k light bodies inside its Hill
+    sphere on near-circular orbits about it: one encounter set of k + 1
+    members that the Hermite runs on a cluster of CTAs."""
+    rng = np.random.default_rng(seed)
+    mp = 1e-3
+    rH = (mp / 3) ** (1 / 3)
+    m = np.concatenate([[1.0, mp], np.full(k, 1e-12)])
+    qp, vp = np.array([1.0, 0.0, 0.0]), np.array([0.0, 1.0, 0.0])
+    r = rng.uniform(0.3, 1.0, k) * rH
+    th = rng.uniform(0, 2 * np.pi, k)
+    off = np.stack([r * np.cos(th), r * np.sin(th), rng.normal(0, 0.05, k) * rH], 1)
+    vc = np.sqrt(mp / r) * rng.uniform(0.7, 1.0, k)
+    voff = np.stack([-vc * np.sin(th), vc * np.cos(th), np.zeros(k)], 1)
+    q = np.concatenate([[[0.0, 0.0, 0.0]], [qp], qp + off])
+    v = np.concatenate([[[0.0, 0.0, 0.0]], [vp], vp + voff])
+    return W.Workload("swarm", m, q, v, np.array([0, k + 2]), 2 * np.pi / 40, 3)
+
+
+@pytest.mark.parametrize("k", [35, 68])
+def test_cluster_set_parity(gpu, oracle, k):
+    """One large set on a cluster of 8 CTAs, with k + 1 members such that the
+    CTAs' member ranges straddle a power of two (36 -> 4 or 5 per CTA, 69 ->
+    8 or 9): the records match the oracle and every body stays within the
+    chaos-aware tolerance."""
+    w = _planet_swarm(k, seed=k)
+    qg, vg, enc, st, E = _run_gpu(w, 3, kick_prec=q.QYM_KICK_FP64)
+    r, vh = _run_oracle(oracle, w, 3)
+    assert st["status_bits"] == 0 and st["max_set"] == k + 1
+    skip = _compare_records(enc, r)
+    keep = np.array([i not in skip for i in range(len(w.m))])
+    _check_positions(qg[keep], r.q[keep], _chaos_spread(oracle, w, 3)[keep], rel=1e-11)
+
+
 def test_16384_disk_steps(gpu, oracle):
     """The 16384-body disk, 3 steps, FP64 kick: positions within 1e-12."""
     w = W.disk_16384()
