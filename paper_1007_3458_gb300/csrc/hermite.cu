@@ -33,28 +33,44 @@ constexpr int HTHREADS = 256;
 // (sin and cos swap), so the argument w = (pi/2) y' stays in [0, pi/4], where
 // the Taylor series of sin to w^15 and of cos to w^16 leave truncation errors
 // below 7e-17 and 3e-18 (the next terms, w^17/17! and w^18/18!, at pi/4).
+struct HalfPi {
+    double w, x, x2, x4;  // w = (pi/2) y', y' = y or 1 - y; x = w^2, x^2, x^4
+    bool fold;            // y' = 1 - y: sin and cos swap
+};
+__device__ __forceinline__ HalfPi half_pi_arg(double y) {
+    HalfPi a;
+    a.fold = y > 0.5;
+    a.w = 1.5707963267948966 * (a.fold ? 1.0 - y : y);
+    a.x = a.w * a.w;
+    a.x2 = a.x * a.x;
+    a.x4 = a.x2 * a.x2;
+    return a;
+}
+// both polynomials in x = w^2 by Estrin's scheme (dependent depth 4-5
+// instead of 8-9: FP64 operations have long latency on this GPU)
+// sin w = w (1 - x/3! + x^2/5! - ... - x^7/15!)
+__device__ __forceinline__ double sin_w(const HalfPi &a) {
+    const double s01 = fma(-1.0 / 6.0, a.x, 1.0);
+    const double s23 = fma(-1.0 / 5040.0, a.x, 1.0 / 120.0);
+    const double s45 = fma(-1.0 / 39916800.0, a.x, 1.0 / 362880.0);
+    const double s67 = fma(-1.0 / 1307674368000.0, a.x, 1.0 / 6227020800.0);
+    const double ps = fma(fma(s67, a.x2, s45), a.x4, fma(s23, a.x2, s01));
+    return a.w * ps;
+}
+// cos w = 1 - x/2! + x^2/4! - ... + x^8/16!
+__device__ __forceinline__ double cos_w(const HalfPi &a) {
+    const double c01 = fma(-0.5, a.x, 1.0);
+    const double c23 = fma(-1.0 / 720.0, a.x, 1.0 / 24.0);
+    const double c45 = fma(-1.0 / 3628800.0, a.x, 1.0 / 40320.0);
+    const double c67 = fma(-1.0 / 87178291200.0, a.x, 1.0 / 479001600.0);
+    const double c8 = (1.0 / 20922789888000.0) * (a.x4 * a.x4);
+    return fma(fma(c67, a.x2, c45), a.x4, fma(c23, a.x2, c01)) + c8;
+}
 __device__ __forceinline__ void sincos_half_pi(double y, double &sn, double &cs) {
-    const bool fold = y > 0.5;
-    const double w = 1.5707963267948966 * (fold ? 1.0 - y : y);
-    // both polynomials in x = w^2 by Estrin's scheme (dependent depth 4-5
-    // instead of 8-9: FP64 operations have long latency on this GPU)
-    const double x = w * w, x2 = x * x, x4 = x2 * x2;
-    // sin w / w = 1 - x/3! + x^2/5! - ... - x^7/15!
-    const double s01 = fma(-1.0 / 6.0, x, 1.0);
-    const double s23 = fma(-1.0 / 5040.0, x, 1.0 / 120.0);
-    const double s45 = fma(-1.0 / 39916800.0, x, 1.0 / 362880.0);
-    const double s67 = fma(-1.0 / 1307674368000.0, x, 1.0 / 6227020800.0);
-    const double ps = fma(fma(s67, x2, s45), x4, fma(s23, x2, s01));
-    const double sw = w * ps;
-    // cos w = 1 - x/2! + x^2/4! - ... + x^8/16!
-    const double c01 = fma(-0.5, x, 1.0);
-    const double c23 = fma(-1.0 / 720.0, x, 1.0 / 24.0);
-    const double c45 = fma(-1.0 / 3628800.0, x, 1.0 / 40320.0);
-    const double c67 = fma(-1.0 / 87178291200.0, x, 1.0 / 479001600.0);
-    const double c8 = (1.0 / 20922789888000.0) * (x4 * x4);
-    const double pc = fma(fma(c67, x2, c45), x4, fma(c23, x2, c01)) + c8;
-    sn = fold ? pc : sw;
-    cs = fold ? sw : pc;
+    const HalfPi a = half_pi_arg(y);
+    const double sw = sin_w(a), pc = cos_w(a);
+    sn = a.fold ? pc : sw;
+    cs = a.fold ? sw : pc;
 }
 
 // Constants of the transition function of one set: K(y) = sin(pi y / 2) with
@@ -68,10 +84,13 @@ struct TransC {
         : rc2(rc * rc), a(1.1 / rc), c(0.5 * kPi * (1.1 / rc)), nc2(-c * c) {}
 };
 
+// the transition's argument y = 1.1 s / r_crit - 0.1
+__device__ __forceinline__ double trans_y(double s, const TransC &tc) { return fma(tc.a, s, -0.1); }
+
 // K and its first and second derivatives with respect to s
 __device__ __forceinline__ void transition(double s, const TransC &tc, double &K, double &Kp,
                                            double &Kpp) {
-    const double y = tc.a * s - 0.1;
+    const double y = trans_y(s, tc);
     if (y <= 0.0) {
         K = 0.0; Kp = 0.0; Kpp = 0.0;
     } else if (y >= 1.0) {
@@ -144,6 +163,8 @@ struct HermSmem {
     int32_t *ids;
     int32_t *need;                            // member needed in FP64 at this block time
     int32_t *nl;                              // per coordinate warp: those members [3][HCAP]
+                                              // (need and nl also hold the two-warp force's
+                                              // exchange slots, [2][3][96] doubles)
 };
 
 __device__ __forceinline__ HermSmem carve(void *base) {
@@ -176,6 +197,8 @@ __device__ __forceinline__ HermSmem carve(void *base) {
 constexpr size_t kHermSmem =
     sizeof(double) * (HCAP * 20 + 6 * HTHREADS + 2 * CL * 6 * RSL + 6 * ACH + LV_N * (KMAX + 1)) +
     sizeof(float) * (16 * HCAP + 12 * ACH) + sizeof(int32_t) * HCAP * 7;
+static_assert(2 * 3 * 96 * sizeof(double) <= 4 * HCAP * sizeof(int32_t),
+              "the two-warp force's exchange slots overlay need and nl");
 // two CTAs per SM (228 KB of shared memory, 1 KB of it per CTA reserved)
 static_assert(2 * (kHermSmem + 1024) <= 228 * 1024, "Hermite shared memory above two CTAs per SM");
 
@@ -384,6 +407,29 @@ __device__ __forceinline__ bool maybe_near(const HermSmem &S, int k, int l, floa
     return __fmul_rn(q, 1.0f - 0x1p-20f) <= __fadd_rn(rcf, __fadd_rn(S.pd[k], S.pd[l]));
 }
 
+// Pieces of the pair force shared by the one-lane form (herm_item) and the
+// two-warp form of the block step, written with explicit fused operations
+// so that both give the same bits: q^2 + eps^2; q . p; and from K, K', K''
+// the weights of the acceleration, cb = -G m_l / q^3 [1 - K + q K'], and of
+// the jerk, a' = cb p + cq q with cq = (-G m_l / q^3) (q . p) (K'' - 3 [..] / q^2)
+__device__ __forceinline__ double pair_q2(double qx, double qy, double qz, double eps2) {
+    return fma(qx, qx, fma(qy, qy, fma(qz, qz, eps2)));
+}
+__device__ __forceinline__ double pair_rv(double qx, double qy, double qz, double px, double py,
+                                          double pz) {
+    return fma(qx, px, fma(qy, py, qz * pz));
+}
+__device__ __forceinline__ double pair_cb(double gml, double qi, double qi2, double sq, double K,
+                                          double Kp, double &br, double &cl) {
+    br = fma(sq, Kp, 1.0 - K);
+    cl = gml * (qi2 * qi);
+    return cl * br;
+}
+__device__ __forceinline__ double pair_cq(double cl, double rvl, double qi2, double br,
+                                          double Kpp) {
+    return (cl * rvl) * fma(-3.0 * qi2, br, Kpp);
+}
+
 // Hermite a, adot of member k from one item: partner mlo + item of this
 // CTA's range (with f32, skipped at once when maybe_near rules it out), or
 // the star for item == npart (with `star`)
@@ -406,26 +452,28 @@ __device__ __forceinline__ void herm_item(const HermSmem &S, int k, int item, in
         return;
     }
     const int l = mlo + item;
-    double qx = xk - S.ex[l], qy = yk - S.ey[l], qz = zk - S.ez[l];
-    double q2 = qx * qx + qy * qy + qz * qz + eps2;
+    const double qx = xk - S.ex[l], qy = yk - S.ey[l], qz = zk - S.ez[l];
+    const double q2 = pair_q2(qx, qy, qz, eps2);
     if (q2 >= tc.rc2) return;  // K = 1, K' = K'' = 0: no force, no jerk
-    double px = uk - S.eu[l], py = vk - S.ev[l], pz = wk - S.ew[l];
+    const double px = uk - S.eu[l], py = vk - S.ev[l], pz = wk - S.ew[l];
     const double qi = rsqrt(q2);
     const double qi2 = qi * qi;
     const double sq = q2 * qi;
     double K, Kp, Kpp;
     transition(sq, tc, K, Kp, Kpp);
-    const double br = 1.0 - K + sq * Kp;
-    const double rvl = qx * px + qy * py + qz * pz;
-    // cl = -G m_l / q^3; the jerk cl [rvl Kpp q + (p - 3 rvl q / q^2) br]
-    // regrouped as cb p + cq q, cb = cl br, cq = cl rvl (Kpp - 3 br / q^2)
-    const double cl = S.gm[l] * (qi2 * qi);
-    const double cb = cl * br;
-    const double cq = (cl * rvl) * fma(-3.0 * qi2, br, Kpp);
+    const double rvl = pair_rv(qx, qy, qz, px, py, pz);
+    double br, cl;
+    const double cb = pair_cb(S.gm[l], qi, qi2, sq, K, Kp, br, cl);
+    const double cq = pair_cq(cl, rvl, qi2, br, Kpp);
     aj[0] = fma(cb, qx, aj[0]); aj[1] = fma(cb, qy, aj[1]); aj[2] = fma(cb, qz, aj[2]);
     aj[3] = fma(cb, px, fma(cq, qx, aj[3]));
     aj[4] = fma(cb, py, fma(cq, qy, aj[4]));
     aj[5] = fma(cb, pz, fma(cq, qz, aj[5]));
+}
+
+// the pair barrier of warps 2p and 2p + 1 (named barrier 1 + p, 64 threads)
+__device__ __forceinline__ void pair_bar(int p) {
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + p) : "memory");
 }
 
 struct HermArgs {
@@ -713,25 +761,112 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
             int LA = 1;
             while (LA < npmax && LA < 64) LA <<= 1;
             // slots per round (warp 7 holds one star per slot; on a cluster at
-            // most RSL, the receive buffer's width)
+            // most RSL, the receive buffer's width). When the round's members
+            // fit three warps' worth of lanes, each pair item runs on two warps
+            // of different sub-partitions (pair_bar): the even warp takes sin,
+            // q . p and the acceleration, the odd warp cos and the jerk, which
+            // shortens each warp's FP64 instruction stream by about a third.
+            // Either way every partial is the same sum in the same order.
             const int NG = min(COOP ? RSL : 32, (HTHREADS - 32) / LA);
-            for (int s0 = 0; s0 < nc; s0 += NG) {
-                double aj[6] = {0, 0, 0, 0, 0, 0};
-                if (warp < 7) {
-                    const int slot = s0 + tid / LA, la = tid % LA;
-                    if (slot < nc) {
-                        const int k = S.act[a0 + slot];
-                        for (int it = la; it < npart; it += LA)
-                            herm_item(S, k, it, mlo, npart, false, gm0, tc, h.eps2, f32, rcf, aj);
-                    }
-                } else if (with_star && wl < min(NG, nc - s0)) {
-                    herm_item(S, S.act[a0 + s0 + wl], npart, mlo, npart, true, gm0, tc, h.eps2, f32,
-                              rcf, aj);
-                }
+            const bool paired = nc <= min(COOP ? RSL : 32, 96 / LA);
+            const int NR = paired ? nc : NG;
+            for (int s0 = 0; s0 < nc; s0 += NR) {
+                const int cnt = min(NR, nc - s0);
                 double *prb = S.pr;
+                if (!paired) {
+                    double aj[6] = {0, 0, 0, 0, 0, 0};
+                    if (warp < 7) {
+                        const int slot = s0 + tid / LA, la = tid % LA;
+                        if (slot < s0 + cnt) {
+                            const int k = S.act[a0 + slot];
+                            for (int it = la; it < npart; it += LA)
+                                herm_item(S, k, it, mlo, npart, false, gm0, tc, h.eps2, f32, rcf, aj);
+                        }
+                    } else if (with_star && wl < cnt) {
+                        herm_item(S, S.act[a0 + s0 + wl], npart, mlo, npart, true, gm0, tc, h.eps2,
+                                  f32, rcf, aj);
+                    }
 #pragma unroll
-                for (int c = 0; c < 6; ++c) prb[c * HTHREADS + tid] = aj[c];
-                const int cnt = min(NG, nc - s0);
+                    for (int c = 0; c < 6; ++c) prb[c * HTHREADS + tid] = aj[c];
+                } else if (warp < 6) {
+                    const int role = warp & 1, vl = (warp >> 1) * 32 + wl;
+                    const int slot = vl / LA, la = vl - slot * LA;
+                    const bool sv = slot < cnt;
+                    const int k = sv ? S.act[a0 + slot] : 0;
+                    // exchange slots [2][3][96] (sin, q . p, cos): the FP32
+                    // pass's lists, which are idle until the next block time
+                    double *xch = reinterpret_cast<double *>(S.need);
+                    double acc[3] = {0.0, 0.0, 0.0};
+                    int par = 0;
+                    for (int it0 = 0; it0 < npart; it0 += LA) {
+                        const int l = mlo + it0 + la;
+                        double *xs = xch + par * (3 * 96);
+                        bool valid = sv && it0 + la < npart && l != k &&
+                                     (!f32 || maybe_near(S, k, l, rcf));
+                        double qx = 0.0, qy = 0.0, qz = 0.0, qi = 0.0, qi2 = 0.0, sq = 0.0;
+                        double y = 0.0, mine = 0.0;
+                        bool fold = false;
+                        if (valid) {
+                            qx = S.ex[k] - S.ex[l];
+                            qy = S.ey[k] - S.ey[l];
+                            qz = S.ez[k] - S.ez[l];
+                            const double q2 = pair_q2(qx, qy, qz, h.eps2);
+                            valid = q2 < tc.rc2;  // beyond r_crit: no force, no jerk
+                            if (valid) {
+                                qi = rsqrt(q2);
+                                qi2 = qi * qi;
+                                sq = q2 * qi;
+                                y = trans_y(sq, tc);
+                                if (y > 0.0 && y < 1.0) {
+                                    const HalfPi arg = half_pi_arg(y);
+                                    fold = arg.fold;
+                                    mine = role == 0 ? sin_w(arg) : cos_w(arg);
+                                    xs[2 * 96 * role + vl] = mine;
+                                }
+                                if (role == 0)
+                                    xs[96 + vl] = pair_rv(qx, qy, qz, S.eu[k] - S.eu[l],
+                                                          S.ev[k] - S.ev[l], S.ew[k] - S.ew[l]);
+                            }
+                        }
+                        __syncwarp();
+                        pair_bar(warp >> 1);
+                        if (valid) {
+                            double K = 0.0, Kp = 0.0, Kpp = 0.0;
+                            if (y >= 1.0) {
+                                K = 1.0;
+                            } else if (y > 0.0) {
+                                const double sw = role == 0 ? mine : xs[vl];
+                                const double pc = role == 1 ? mine : xs[2 * 96 + vl];
+                                const double sn = fold ? pc : sw, cs = fold ? sw : pc;
+                                K = sn;
+                                Kp = tc.c * cs;
+                                Kpp = tc.nc2 * sn;
+                            }
+                            double br, cl;
+                            const double cb = pair_cb(S.gm[l], qi, qi2, sq, K, Kp, br, cl);
+                            if (role == 0) {
+                                acc[0] = fma(cb, qx, acc[0]);
+                                acc[1] = fma(cb, qy, acc[1]);
+                                acc[2] = fma(cb, qz, acc[2]);
+                            } else {
+                                const double cq = pair_cq(cl, xs[96 + vl], qi2, br, Kpp);
+                                acc[0] = fma(cb, S.eu[k] - S.eu[l], fma(cq, qx, acc[0]));
+                                acc[1] = fma(cb, S.ev[k] - S.ev[l], fma(cq, qy, acc[1]));
+                                acc[2] = fma(cb, S.ew[k] - S.ew[l], fma(cq, qz, acc[2]));
+                            }
+                        }
+                        par ^= 1;
+                    }
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) prb[(3 * role + c) * HTHREADS + vl] = acc[c];
+                } else if (warp == 7) {
+                    double aj[6] = {0, 0, 0, 0, 0, 0};
+                    if (with_star && wl < cnt)
+                        herm_item(S, S.act[a0 + s0 + wl], npart, mlo, npart, true, gm0, tc, h.eps2,
+                                  f32, rcf, aj);
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) prb[c * HTHREADS + tid] = aj[c];
+                }
                 if (COOP) {
                     // This CTA's part of every (member, component): its LA lanes
                     // summed by a group of eight lanes in a fixed order (plus the
