@@ -128,7 +128,11 @@ cudaError_t launch_transition(int64_t n, const double *s, double rc, double *K, 
 // through the stack of the per-set function)
 extern __shared__ __align__(16) unsigned char g_hsmem[];
 
-constexpr int CL = 8;      // CTAs of a cluster sharing one large set (the tree sum below has 8 leaves)
+#ifndef QYM_HERM_CL
+#define QYM_HERM_CL 8
+#endif
+constexpr int CL = QYM_HERM_CL;  // CTAs of a cluster sharing one large set
+static_assert(CL == 2 || CL == 4 || CL == 8, "a cluster is 2, 4 or 8 CTAs (one lane group of 8 pushes)");
 #ifndef QYM_HERM_NBIG
 #define QYM_HERM_NBIG 24
 #endif
@@ -890,7 +894,7 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                         v += __shfl_xor_sync(0xffffffffu, v, 2);
                         v += __shfl_xor_sync(0xffffffffu, v, 4);
                         if (live && with_star) v += prb[c * HTHREADS + 224 + sl];
-                        if (live) cl.map_shared_rank(rbb, g)[(rank * 6 + c) * RSL + sl] = v;
+                        if (live && g < CL) cl.map_shared_rank(rbb, g)[(rank * 6 + c) * RSL + sl] = v;
                     }
                     cl.sync();
                     for (int pi = tid; pi < 6 * cnt; pi += HTHREADS) {
@@ -898,8 +902,13 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                         double pv[CL];
 #pragma unroll
                         for (int r = 0; r < CL; ++r) pv[r] = rbb[(r * 6 + c) * RSL + sl];
-                        S.a1s[c * ACH + s0 + sl] = ((pv[0] + pv[1]) + (pv[2] + pv[3])) +
-                                                   ((pv[4] + pv[5]) + (pv[6] + pv[7]));
+                        // pairwise tree: rank r with rank r + w, halving w
+#pragma unroll
+                        for (int w = CL / 2; w >= 1; w >>= 1) {
+#pragma unroll
+                            for (int r = 0; r < w; ++r) pv[r] += pv[r + w];
+                        }
+                        S.a1s[c * ACH + s0 + sl] = pv[0];
                     }
                     buf ^= 1;
                 } else {
