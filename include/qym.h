@@ -53,7 +53,9 @@ typedef enum qym_status {
 /* Bits of the device status word (per step, OR-ed). */
 #define QYM_ST_KEPLER_NOCONV   0x01  /* a Kepler solve hit max_kepler_iter */
 #define QYM_ST_HERMITE_CAP     0x02  /* an encounter set hit max_hermite_steps */
-#define QYM_ST_CAND_OVERFLOW   0x04  /* more crude candidates than max_candidates */
+#define QYM_ST_CAND_OVERFLOW   0x04  /* more crude candidates than max_candidates, or
+                                        more flagged (row, chunk) records of the mixed
+                                        search kick than max_candidates + rows */
 #define QYM_ST_ENC_OVERFLOW    0x08  /* more encounter pairs than max_encounters */
 #define QYM_ST_SET_OVERFLOW    0x10  /* a set larger than the set capacity (or than
                                         the 320 members the Hermite holds on chip) */

@@ -190,6 +190,30 @@ def test_cluster_set_parity(gpu, oracle, k):
     _check_positions(qg[keep], r.q[keep], _chaos_spread(oracle, w, 3)[keep], rel=1e-11)
 
 
+def test_large_sets_one_cta_each_parity(gpu, oracle):
+    """More large sets than clusters (40 systems, each a planet with a 68-body
+    swarm): every set runs on one CTA, and with 69 members a CTA first rules
+    out far partners in FP32 before the FP64 work. Sampled systems match the
+    oracle stepping each alone."""
+    sw = [_planet_swarm(68, seed=100 + s) for s in range(40)]
+    m = np.concatenate([w.m for w in sw])
+    qq = np.concatenate([w.q for w in sw])
+    vv = np.concatenate([w.v for w in sw])
+    offs = np.concatenate([[0], np.cumsum([len(w.m) for w in sw])])
+    w = W.Workload("swarms", m, qq, vv, offs, sw[0].tau, 3)
+    qg, vg, enc, st, E = _run_gpu(w, 3, kick_prec=q.QYM_KICK_FP64)
+    assert st["status_bits"] == 0 and st["max_set"] == 69
+    for s in (0, 17, 39):
+        a, b = int(offs[s]), int(offs[s + 1])
+        r, _ = _run_oracle(oracle, sw[s], 3)
+        mine = enc[(enc[:, 1] >= a) & (enc[:, 1] < b)].copy()
+        mine[:, 1:] -= a
+        skip = _compare_records(mine, r)
+        keep = np.array([i not in skip for i in range(b - a)])
+        _check_positions(qg[a:b][keep], r.q[keep], _chaos_spread(oracle, sw[s], 3)[keep],
+                         rel=1e-11)
+
+
 def test_16384_disk_steps(gpu, oracle):
     """The 16384-body disk, 3 steps, FP64 kick: positions within 1e-12."""
     w = W.disk_16384()
