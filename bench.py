@@ -253,6 +253,59 @@ def run_reference(args):
     return 0
 
 
+def precision_compare(q, torch, w, args, dev):
+    """The paper's FP64 kick beside the FP32-compensated one on the same
+    workload: each runs 2 untimed steps, then S timed steps from there; reported
+    are its particle-steps/s and the relative energy change over those steps
+    (the largest and the median over the systems), and for one system the mixed kick's
+    per-particle |a - a_FP64| / |a_FP64| at the mixed run's final positions."""
+    S = 2 if w.n_bodies > 100000 else max(1, min(args.steps, 20))
+    out = {"steps": S}
+    qfin = None
+    for name, prec in (("mixed", q.QYM_KICK_MIXED), ("fp64", q.QYM_KICK_FP64)):
+        sim = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=prec, device=dev,
+                           l2_flush_bytes=256 << 20, eps_H=w.eps_H)
+        if args.autotune:
+            q.qym_autotune(sim.ctx)
+        stream = torch.cuda.ExternalStream(q.qym_get_stream(sim.ctx))
+        sim.step(w.tau, 2)
+        E0 = np.asarray(sim.energy(), dtype=np.float64)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(w.tau, S)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        E1 = np.asarray(sim.energy(), dtype=np.float64)
+        rel_e = np.abs(E1 - E0) / np.abs(E0)
+        out[name] = {"value": w.n_bodies * S / (ms / 1e3), "ms_per_step": ms / S,
+                     "energy_rel_err": float(np.max(rel_e)),
+                     "energy_rel_err_median": float(np.median(rel_e))}
+        if name == "mixed":
+            qfin = sim.state()[0]
+        sim.close()
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    if w.nsys == 1:
+        rows = len(w.m)
+        md = torch.tensor(w.m, dtype=torch.float64, device="cuda")
+        qd = torch.tensor(np.ascontiguousarray(qfin.T), dtype=torch.float64, device="cuda")
+        acc = {}
+        for name, prec in (("mixed", q.QYM_KICK_MIXED), ("fp64", q.QYM_KICK_FP64)):
+            ad = torch.empty_like(qd)
+            work = torch.empty(q.qym_accel_workspace_bytes(rows, prec), dtype=torch.uint8,
+                               device="cuda")
+            q.qym_accel_dev(rows, md, qd, ad, 1.0, prec, work)
+            torch.cuda.synchronize()
+            acc[name] = ad.cpu().numpy().T[1:]
+        n = np.linalg.norm(acc["fp64"], axis=1)
+        rel = np.linalg.norm(acc["mixed"] - acc["fp64"], axis=1) / n
+        out["accel_rel_err_max"] = float(rel.max())
+        out["accel_rel_err_p99"] = float(np.percentile(rel, 99))
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank = _dist()
@@ -364,6 +417,9 @@ def run_ours(args):
                   "candidates": int(sst["candidates"]), "encounters": int(sst["encounters"]),
                   "rescans": int(sst["rescans"]), "hermite_steps_max": int(sst["hermite_steps_max"])}
         sm.close()
+    precision = None
+    if args.precision_too and ws == 1 and prec == q.QYM_KICK_MIXED:
+        precision = precision_compare(q, torch, w, args, dev)
     if rank != 0:
         return 0
     cb = cpu_baseline(w, args.prec, max_seconds=args.cpu_seconds) if ws == 1 else None
@@ -379,6 +435,7 @@ def run_ours(args):
                        "l2": "flushed: 256 MB written at the start of every step, inside the timed region"},
             "gpair_per_s": gpair, "stats": st, "gpu_launches": int(st["launches"]),
             "kicks_per_step": 1 if args.merge_kicks else 2, "merged_kicks": merged,
+            "precision": precision,
             "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cb}
     print(json.dumps(line))
     return 0
@@ -540,6 +597,9 @@ def main():
                     help="1: one kick of tau between steps (exact rewrite of the paper's two)")
     ap.add_argument("--merged-too", type=int, default=1,
                     help="also time the merged-kick step and report it under merged_kicks")
+    ap.add_argument("--precision-too", type=int, default=1,
+                    help="also run the FP64 kick and report both kicks' energy error (and the "
+                         "mixed kick's acceleration error) under precision")
     ap.add_argument("--train", type=int, default=1,
                     help="kepler_1m: train the guess network first (0: standard guess only)")
     ap.add_argument("--autotune", type=int, default=1)
