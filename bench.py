@@ -441,6 +441,48 @@ def run_ours(args):
     return 0
 
 
+def run_sweep(args):
+    """Sensitivity of the step to the Hill factors (Sec. 3.3: a_E sets the
+    encounter detection radius, a_H the transition radius r_crit): for each
+    pair, the same K steps from the workload's initial state, with the relative
+    energy change over them, the particle-steps/s and the encounter work."""
+    import torch
+    import paper_1007_3458_gb300 as q
+    q.build()
+    w, desc = rank_workload(args.workload, 0, 1)
+    a_Es = [float(x) for x in args.sweep_a_e.split(",")]
+    a_Hs = [float(x) for x in args.sweep_a_h.split(",")]
+    points = []
+    for aE in a_Es:
+        for aH in a_Hs:
+            sim = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, a_E=aE, a_H=aH)
+            stream = torch.cuda.ExternalStream(q.qym_get_stream(sim.ctx))
+            E0 = np.asarray(sim.energy(), dtype=np.float64)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sim.step(w.tau, args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            E1 = np.asarray(sim.energy(), dtype=np.float64)
+            st = sim.stats()
+            sim.close()
+            points.append({"a_E": aE, "a_H": aH,
+                           "energy_rel_err": float(np.max(np.abs(E1 - E0) / np.abs(E0))),
+                           "value": w.n_bodies * args.steps / (ms / 1e3),
+                           "encounters": int(st["encounters"]), "sets": int(st["sets"]),
+                           "max_set": int(st["max_set"]), "hermite_steps": int(st["hermite_steps"]),
+                           "status_bits": int(st["status_bits"])})
+    print(json.dumps({"metric": "energy error and particle-steps/s against a_E, a_H",
+                      "unit": METRIC, "steps": args.steps, "data": "synthetic",
+                      "config": {"workload": args.workload, "description": desc, "kick": "mixed",
+                                 "tau": w.tau, "eps_H": w.eps_H},
+                      "points": points}))
+    return 0
+
+
 def hbm_peak_gbs():
     """Measured copy bandwidth of the GB300s, else the fallback."""
     try:
@@ -597,6 +639,10 @@ def main():
                     help="1: one kick of tau between steps (exact rewrite of the paper's two)")
     ap.add_argument("--merged-too", type=int, default=1,
                     help="also time the merged-kick step and report it under merged_kicks")
+    ap.add_argument("--sweep", action="store_true",
+                    help="run the a_E x a_H sensitivity sweep instead (one JSON line)")
+    ap.add_argument("--sweep-a-e", default="1,1.5,2,2.5,3,4,6")
+    ap.add_argument("--sweep-a-h", default="0.5,1,2")
     ap.add_argument("--precision-too", type=int, default=1,
                     help="also run the FP64 kick and report both kicks' energy error (and the "
                          "mixed kick's acceleration error) under precision")
@@ -613,6 +659,8 @@ def main():
         return run_reference(args)
     if args.workload in KEPLER_WORKLOADS:
         return run_kepler(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_ours(args)
 
 
