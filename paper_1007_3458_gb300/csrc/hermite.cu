@@ -490,8 +490,8 @@ __shared__ long long g_tn;
 __shared__ int g_na;
 
 // Next block time (the earliest end of a member's step) and the members whose
-// step ends then, in member order, by warp 0 alone; every thread reads
-// (tn, na) after the barrier that follows. The end times stay in registers
+// step ends then, in member order, by one warp; every thread reads (tn, na)
+// after the barrier that follows. The end times stay in registers
 // between the two passes; the minimum (below 2^49) is taken as the minimum of
 // the high words, then of the low words among the lanes that hold it.
 __device__ __forceinline__ void next_block(const int32_t *lev, const long long *ti, int32_t *act,
@@ -700,9 +700,11 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
     int64_t steps = 0;
     bool capped = false;
     int buf = 0;
+    // the first block time; later ones are found by warp 3 right after it sets
+    // the new levels (it wrote every value the scan reads), so one barrier per
+    // block step publishes them
+    if (warp == 3) next_block(S.lev, S.ti, S.act, n);
     for (;;) {
-        __syncthreads();
-        if (warp == 0) next_block(S.lev, S.ti, S.act, n);
         __syncthreads();
         const long long tn = g_tn;
         if (tn > TT) break;  // every member has reached tau
@@ -980,6 +982,9 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                 }
             }
         }
+        // every thread read (tn, na) before the barriers above; the active
+        // list is no longer read in this block step
+        if (warp == 3) next_block(S.lev, S.ti, S.act, n);
         ++steps;
     }
     // peers may still read this CTA's partial sums of the last round
