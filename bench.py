@@ -149,54 +149,58 @@ def fp32_peak_tflops(sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def cpu_baseline(w, prec_label, max_seconds=20.0):
-    """The oracle as it stands, single thread, on a bounded sample: whole
-    steps of the same workload until about max_seconds have passed."""
+def oracle_sample(w):
+    """The oracle as it stands (single thread) on a bounded sample of the
+    workload: returns (one_step, bodies, scale, description). one_step()
+    advances the sample by one whole step; a step of the full workload costs
+    `scale` times that. A batch is sampled by whole systems (its first 8, stepped
+    one after another); beyond 8192 bodies a single disk is sampled by a random
+    subset of the same disk (one oracle step costs ~N^2 pair evaluations: two
+    kicks and the all-pairs encounter test), its time scaled by (N/n)^2."""
     import oracle as O
     O.build()
-    vd = np.concatenate([O.helio_to_dh(w.m[a:b], w.v[a:b])
-                         for a, b in zip(w.offsets[:-1], w.offsets[1:])])
-    q, v = w.q.copy(), vd
-    nb = w.n_bodies
-    # systems of a batch are stepped one after another: sample whole systems
+    from paper_1007_3458_gb300 import workloads as W
+    prm = O.params(eps_H=w.eps_H)
     if w.nsys > 1:
-        sel = list(range(min(w.nsys, 8)))
-        rows = [(int(w.offsets[s]), int(w.offsets[s + 1])) for s in sel]
-        nb = sum(b - a - 1 for a, b in rows)
-        t0 = time.perf_counter()
-        steps = 0
-        while time.perf_counter() - t0 < max_seconds and steps < 50:
+        rows = [(int(w.offsets[s]), int(w.offsets[s + 1])) for s in range(min(w.nsys, 8))]
+        st = {}
+        for a, b in rows:
+            st[a] = (w.q[a:b].copy(), O.helio_to_dh(w.m[a:b], w.v[a:b]))
+
+        def one_step():
             for a, b in rows:
-                r = O.step(w.m[a:b], q[a:b], v[a:b], [0, b - a], w.tau, 1, O.params(eps_H=w.eps_H))
-                q[a:b], v[a:b] = r.q, r.v
-            steps += 1
-        dt = time.perf_counter() - t0
-        sample = f"first {len(rows)} systems ({nb} bodies), {steps} steps"
-    else:
-        # one oracle step costs ~N^2 pair evaluations (two kicks and the
-        # all-pairs encounter test); beyond ~8192 bodies a random subsample of
-        # the same disk is timed and its rate scaled by (n'/N)^2 per body
-        from paper_1007_3458_gb300 import workloads as W
-        n_full = w.n_bodies
-        n_s = min(n_full, 8192)
-        ws = w if n_s == n_full else W.subsample(w, n_s, seed=0)
-        vs = O.helio_to_dh(ws.m, ws.v) if n_s != n_full else v
-        qs = ws.q.copy() if n_s != n_full else q
-        t0 = time.perf_counter()
-        steps = 0
-        while steps < 1 or (time.perf_counter() - t0 < max_seconds and steps < 50):
-            r = O.step(ws.m, qs, vs, ws.offsets, w.tau, 1, O.params(eps_H=w.eps_H))
-            qs, vs = r.q, r.v
-            steps += 1
-        dt = time.perf_counter() - t0
-        if n_s == n_full:
-            sample = f"{steps} full steps of the workload"
-        else:
-            dt *= (n_full / n_s) ** 2
-            sample = (f"{steps} steps of a {n_s}-body random subsample of the disk, time scaled "
-                      f"by (N/n)^2 to the {n_full}-body disk")
+                qq, vv = st[a]
+                r = O.step(w.m[a:b], qq, vv, [0, b - a], w.tau, 1, prm)
+                st[a] = (r.q, r.v)
+        nb = sum(b - a - 1 for a, b in rows)
+        return one_step, nb, 1.0, f"the first {len(rows)} systems ({nb} bodies)"
+    n_full = w.n_bodies
+    n_s = min(n_full, 8192)
+    ws = w if n_s == n_full else W.subsample(w, n_s, seed=0)
+    st = [ws.q.copy(), O.helio_to_dh(ws.m, ws.v)]
+
+    def one_step():
+        r = O.step(ws.m, st[0], st[1], ws.offsets, w.tau, 1, prm)
+        st[0], st[1] = r.q, r.v
+    if n_s == n_full:
+        return one_step, n_full, 1.0, "the whole workload"
+    return (one_step, n_full, (n_full / n_s) ** 2,
+            f"a {n_s}-body random subsample of the disk, time scaled by (N/n)^2 to the "
+            f"{n_full}-body disk")
+
+
+def cpu_baseline(w, prec_label, max_seconds=20.0):
+    """The oracle's particle-steps/s on a bounded sample (oracle_sample), whole
+    steps until about max_seconds have passed (at most 50)."""
+    one_step, nb, scale, what = oracle_sample(w)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < 1 or (time.perf_counter() - t0 < max_seconds and steps < 50):
+        one_step()
+        steps += 1
+    dt = (time.perf_counter() - t0) * scale
     return {"value": nb * steps / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": sample + " (plain FP64 oracle, single thread)"}
+            "sample": f"{steps} steps of {what} (plain FP64 oracle, single thread)"}
 
 
 def run_reference_kepler(args):
@@ -228,6 +232,9 @@ def run_reference_kepler(args):
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands on the host cores, on this
+    arm's workload and metric. W untimed steps, then K timed steps, each a step
+    of a bounded sample of the workload (oracle_sample)."""
     ws, rank = _dist()
     if rank != 0:
         return 0
@@ -235,18 +242,26 @@ def run_reference(args):
         return run_reference_kepler(args)
     w, desc = _workload(args.workload)
     t_all = time.perf_counter()
+    one_step, nb, scale, what = oracle_sample(w)
     for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state
-    cb = cpu_baseline(w, args.prec, max_seconds=max(5.0, 3.0 * args.steps))
-    line = {"metric": METRIC, "value": cb["value"], "unit": METRIC, "n_gpus": ws,
+        one_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_step()
+    dt = (time.perf_counter() - t0) * scale
+    value = nb * args.steps / dt
+    cb = {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+          "sample": f"{args.steps} timed steps (after {args.warmup} untimed) of {what} "
+                    "(plain FP64 oracle, single thread)"}
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * w.n_bodies / cb["value"] if cb["value"] else None,
+            "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "description": desc, "kick": "fp64",
                        "l2": "n/a (CPU)"},
             "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": METRIC, "h2d_bytes_per_step": 0,
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t_all}
     print(json.dumps(line))
