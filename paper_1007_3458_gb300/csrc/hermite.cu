@@ -1,5 +1,6 @@
 // hermite.cu -- the close-encounter branch of the hybrid step (Sec. 2.2 and
-// Sec. 2.3 items 5-8), one CTA per encounter set:
+// Sec. 2.3 items 5-8), one CTA per encounter set, or a thread-block cluster
+// per set when a few large sets would otherwise run alone:
 //   1. remove the (1-K) part of the first kick at q0 (item 5),
 //   2. integrate the set for tau with a 4th-order Hermite predictor /
 //      evaluate / corrector (Makino & Aarseth, no Ahmad-Cohen) under H'_Kep:
@@ -16,7 +17,13 @@
 // exerts no force (K = 1), so an FP32 prediction with a bound on its error
 // first rules out the pairs that are surely that far, and only the others
 // are predicted and evaluated in FP64 (the result is the same as evaluating
-// every pair). Every loop has a cap and reports through the status word.
+// every pair). FP64 instructions issue at one per 64 cycles per warp here, so
+// each block step is split by instruction stream across warps: a warp per
+// coordinate for predictor and corrector, each pair item on two warps, the
+// star's pull on its own warp, fixed-order sums (a cluster's CTAs push their
+// parts to each other and add them in rank order, so every copy of the set
+// stays bit-identical). Every loop has a cap and reports through the status
+// word.
 #include <climits>
 
 #include <cooperative_groups.h>
