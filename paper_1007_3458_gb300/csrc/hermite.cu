@@ -420,9 +420,9 @@ __device__ __forceinline__ bool maybe_near(const HermSmem &S, int k, int l, floa
 
 // Pieces of the pair force shared by the one-lane form (herm_item) and the
 // two-warp form of the block step, written with explicit fused operations
-// so that both give the same bits: q^2 + eps^2; q . p; and from K, K', K''
-// the weights of the acceleration, cb = -G m_l / q^3 [1 - K + q K'], and of
-// the jerk, a' = cb p + cq q with cq = (-G m_l / q^3) (q . p) (K'' - 3 [..] / q^2)
+// so that both give the same bits: q^2 + eps^2; q . p; cl = -G m_l / q^3;
+// br = 1 - K + q K'; the acceleration cl br q and the jerk cl br p + cq q
+// with cq = cl (q . p) (K'' - 3 br / q^2)
 __device__ __forceinline__ double pair_q2(double qx, double qy, double qz, double eps2) {
     return fma(qx, qx, fma(qy, qy, fma(qz, qz, eps2)));
 }
@@ -430,15 +430,16 @@ __device__ __forceinline__ double pair_rv(double qx, double qy, double qz, doubl
                                           double pz) {
     return fma(qx, px, fma(qy, py, qz * pz));
 }
-__device__ __forceinline__ double pair_cb(double gml, double qi, double qi2, double sq, double K,
-                                          double Kp, double &br, double &cl) {
-    br = fma(sq, Kp, 1.0 - K);
-    cl = gml * (qi2 * qi);
-    return cl * br;
+__device__ __forceinline__ double pair_cl(double gml, double qi, double qi2) {
+    return gml * (qi2 * qi);
 }
-__device__ __forceinline__ double pair_cq(double cl, double rvl, double qi2, double br,
+__device__ __forceinline__ double pair_br(double sq, double K, double Kp) {
+    return fma(sq, Kp, 1.0 - K);
+}
+// m3qi2 = -3 / q^2
+__device__ __forceinline__ double pair_cq(double cl, double rvl, double m3qi2, double br,
                                           double Kpp) {
-    return (cl * rvl) * fma(-3.0 * qi2, br, Kpp);
+    return (cl * rvl) * fma(m3qi2, br, Kpp);
 }
 
 // Hermite a, adot of member k from one item: partner mlo + item of this
@@ -473,9 +474,9 @@ __device__ __forceinline__ void herm_item(const HermSmem &S, int k, int item, in
     double K, Kp, Kpp;
     transition(sq, tc, K, Kp, Kpp);
     const double rvl = pair_rv(qx, qy, qz, px, py, pz);
-    double br, cl;
-    const double cb = pair_cb(S.gm[l], qi, qi2, sq, K, Kp, br, cl);
-    const double cq = pair_cq(cl, rvl, qi2, br, Kpp);
+    const double cl = pair_cl(S.gm[l], qi, qi2), br = pair_br(sq, K, Kp);
+    const double cb = cl * br;
+    const double cq = pair_cq(cl, rvl, -3.0 * qi2, br, Kpp);
     aj[0] = fma(cb, qx, aj[0]); aj[1] = fma(cb, qy, aj[1]); aj[2] = fma(cb, qz, aj[2]);
     aj[3] = fma(cb, px, fma(cq, qx, aj[3]));
     aj[4] = fma(cb, py, fma(cq, qy, aj[4]));
@@ -816,8 +817,8 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                         double *xs = xch + par * (3 * 96);
                         bool valid = sv && it0 + la < npart && l != k &&
                                      (!f32 || maybe_near(S, k, l, rcf));
-                        double qx = 0.0, qy = 0.0, qz = 0.0, qi = 0.0, qi2 = 0.0, sq = 0.0;
-                        double y = 0.0, mine = 0.0;
+                        double qx = 0.0, qy = 0.0, qz = 0.0, qi2 = 0.0, sq = 0.0;
+                        double y = 0.0, mine = 0.0, cl = 0.0, m3 = 0.0, px = 0.0, py = 0.0, pz = 0.0;
                         bool fold = false;
                         if (valid) {
                             qx = S.ex[k] - S.ex[l];
@@ -826,7 +827,7 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                             const double q2 = pair_q2(qx, qy, qz, h.eps2);
                             valid = q2 < tc.rc2;  // beyond r_crit: no force, no jerk
                             if (valid) {
-                                qi = rsqrt(q2);
+                                const double qi = rsqrt(q2);
                                 qi2 = qi * qi;
                                 sq = q2 * qi;
                                 y = trans_y(sq, tc);
@@ -836,9 +837,16 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                                     mine = role == 0 ? sin_w(arg) : cos_w(arg);
                                     xs[2 * 96 * role + vl] = mine;
                                 }
+                                // what does not wait for the partner warp's
+                                // polynomial is done before the barrier
+                                cl = pair_cl(S.gm[l], qi, qi2);
+                                px = S.eu[k] - S.eu[l];
+                                py = S.ev[k] - S.ev[l];
+                                pz = S.ew[k] - S.ew[l];
                                 if (role == 0)
-                                    xs[96 + vl] = pair_rv(qx, qy, qz, S.eu[k] - S.eu[l],
-                                                          S.ev[k] - S.ev[l], S.ew[k] - S.ew[l]);
+                                    xs[96 + vl] = pair_rv(qx, qy, qz, px, py, pz);
+                                else
+                                    m3 = -3.0 * qi2;
                             }
                         }
                         __syncwarp();
@@ -855,17 +863,17 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                                 Kp = tc.c * cs;
                                 Kpp = tc.nc2 * sn;
                             }
-                            double br, cl;
-                            const double cb = pair_cb(S.gm[l], qi, qi2, sq, K, Kp, br, cl);
+                            const double br = pair_br(sq, K, Kp);
+                            const double cb = cl * br;
                             if (role == 0) {
                                 acc[0] = fma(cb, qx, acc[0]);
                                 acc[1] = fma(cb, qy, acc[1]);
                                 acc[2] = fma(cb, qz, acc[2]);
                             } else {
-                                const double cq = pair_cq(cl, xs[96 + vl], qi2, br, Kpp);
-                                acc[0] = fma(cb, S.eu[k] - S.eu[l], fma(cq, qx, acc[0]));
-                                acc[1] = fma(cb, S.ev[k] - S.ev[l], fma(cq, qy, acc[1]));
-                                acc[2] = fma(cb, S.ew[k] - S.ew[l], fma(cq, qz, acc[2]));
+                                const double cq = pair_cq(cl, xs[96 + vl], m3, br, Kpp);
+                                acc[0] = fma(cb, px, fma(cq, qx, acc[0]));
+                                acc[1] = fma(cb, py, fma(cq, qy, acc[1]));
+                                acc[2] = fma(cb, pz, fma(cq, qz, acc[2]));
                             }
                         }
                         par ^= 1;
