@@ -206,9 +206,14 @@ def qym_autotune(ctx):
 
 
 def qym_get_state(ctx, q=None, v=None):
+    """Positions and velocities [rows, 3]; q and v, when given, are filled in
+    place (C-contiguous float64 [rows, 3], e.g. views of pinned memory)."""
     rows, _ = qym_shape(ctx)
     q = np.empty((rows, 3)) if q is None else q
     v = np.empty((rows, 3)) if v is None else v
+    for a in (q, v):
+        if a.dtype != np.float64 or a.shape != (rows, 3) or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("qym_get_state: buffers must be C-contiguous float64 [rows, 3]")
     _check(lib().qym_get_state(ctx, _d(q), _d(v)), ctx)
     return q, v
 

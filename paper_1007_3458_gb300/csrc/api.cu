@@ -54,6 +54,7 @@ struct qym_ctx {
     int64_t klog_cap = 0;
     unsigned long long klog_steps = 0;   // steps logged so far
     unsigned long long *klog_base = nullptr;  // device copy of klog_steps (arena)
+    int32_t *hflag = nullptr;    // state upload: bit 1 non-finite position, bit 2 velocity
 };
 
 #define FAIL(ctx, code, msg)                         \
@@ -179,17 +180,28 @@ static void carve_all(qym_ctx *c, Carver &k) {
     c->mt = k.take<double>(d.nsys);
     c->mlp_w = k.take<float>(QYM_MLP_NW);
     c->klog_base = k.take<unsigned long long>(1);
+    c->hflag = k.take<int32_t>(1);
 }
 
-static void soa_from_aos(const double *aos, int64_t R, std::vector<double> &out) {
-    out.resize(3 * R);
-    for (int64_t i = 0; i < R; ++i)
-        for (int c = 0; c < 3; ++c) out[c * R + i] = aos[3 * i + c];
+// The caller's rows [R][3] <-> the device's [3][R]. The transposes run on the
+// device, so a pinned host buffer goes to and from the GPU in one DMA each;
+// between steps the kick's partial sums are idle and stage the rows.
+__global__ void k_soa_from_aos(int64_t R, const double *aos, double *soa, const int64_t *offsets,
+                               const int32_t *sys_of, int32_t *bad, int32_t bit) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const bool star = offsets[sys_of[r]] == r;  // star rows are held at zero
+    for (int c = 0; c < 3; ++c) {
+        const double x = star ? 0.0 : aos[3 * r + c];
+        if (!isfinite(x)) atomicOr(bad, bit);
+        soa[c * R + r] = x;
+    }
 }
 
-static void aos_from_soa(const std::vector<double> &soa, int64_t R, double *aos) {
-    for (int64_t i = 0; i < R; ++i)
-        for (int c = 0; c < 3; ++c) aos[3 * i + c] = soa[c * R + i];
+__global__ void k_aos_from_soa(int64_t R, const double *soa, double *aos) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    for (int c = 0; c < 3; ++c) aos[3 * r + c] = soa[c * R + r];
 }
 
 // Launch shape of the kick for this batch: enough CTAs to fill the GPU
@@ -215,22 +227,27 @@ static KickTune default_tune(const std::vector<int64_t> &off, int prec) {
 static qym_status upload_state(qym_ctx *c, const double *q, const double *v) {
     Dev &d = c->d;
     const int64_t R = d.rows;
-    std::vector<double> qs, vs;
-    soa_from_aos(q, R, qs);
-    soa_from_aos(v, R, vs);
-    for (int32_t s = 0; s < d.nsys; ++s) {  // star rows held at zero
-        int64_t r = c->h_offsets[s];
-        for (int k = 0; k < 3; ++k) qs[k * R + r] = vs[k * R + r] = 0.0;
-    }
-    for (double x : qs)
-        if (!std::isfinite(x)) FAIL(c, QYM_EINVAL, "non-finite position");
-    for (double x : vs)
-        if (!std::isfinite(x)) FAIL(c, QYM_EINVAL, "non-finite velocity");
-    CK(c, cudaMemcpyAsync(d.q, qs.data(), sizeof(double) * 3 * R, cudaMemcpyHostToDevice, c->stream));
-    CK(c, cudaMemcpyAsync(d.v, vs.data(), sizeof(double) * 3 * R, cudaMemcpyHostToDevice, c->stream));
-    if (c->p.coords == 0) CK(c, launch_to_dh_impl(d, 0, nullptr, c->mt, c->stream));
-    if (c->p.hill_fixed) CK(c, launch_hill_init(d, c->p.G, c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
+    cudaStream_t st = c->stream;
+    // rows land in the partial-sum buffer (at least 4 slots of [3][R]), are
+    // transposed and checked into (q1, v1), and only a valid state replaces (q, v)
+    double *sq = d.apart, *sv = d.apart + 3 * R;
+    const unsigned g = (unsigned)((R + 255) / 256);
+    CK(c, cudaMemcpyAsync(sq, q, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, st));
+    CK(c, cudaMemcpyAsync(sv, v, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, st));
+    CK(c, cudaMemsetAsync(c->hflag, 0, sizeof(int32_t), st));
+    k_soa_from_aos<<<g, 256, 0, st>>>(R, sq, d.q1, d.offsets, d.sys_of, c->hflag, 1);
+    k_soa_from_aos<<<g, 256, 0, st>>>(R, sv, d.v1, d.offsets, d.sys_of, c->hflag, 2);
+    CK(c, cudaGetLastError());
+    int32_t bad = 0;
+    CK(c, cudaMemcpyAsync(&bad, c->hflag, sizeof(bad), cudaMemcpyDeviceToHost, st));
+    CK(c, cudaStreamSynchronize(st));
+    if (bad & 1) FAIL(c, QYM_EINVAL, "non-finite position");
+    if (bad & 2) FAIL(c, QYM_EINVAL, "non-finite velocity");
+    CK(c, cudaMemcpyAsync(d.q, d.q1, sizeof(double) * 3 * R, cudaMemcpyDeviceToDevice, st));
+    CK(c, cudaMemcpyAsync(d.v, d.v1, sizeof(double) * 3 * R, cudaMemcpyDeviceToDevice, st));
+    if (c->p.coords == 0) CK(c, launch_to_dh_impl(d, 0, nullptr, c->mt, st));
+    if (c->p.hill_fixed) CK(c, launch_hill_init(d, c->p.G, st));
+    CK(c, cudaStreamSynchronize(st));
     c->amag_valid = false;
     return QYM_OK;
 }
@@ -680,22 +697,26 @@ extern "C" qym_status qym_get_state(qym_ctx *c, double *q, double *v) {
     if (!c) FAIL(nullptr, QYM_EINVAL, "qym_get_state: NULL context");
     Dev &d = c->d;
     const int64_t R = d.rows;
-    std::vector<double> buf(3 * R);
+    cudaStream_t st = c->stream;
+    const unsigned g = (unsigned)((R + 255) / 256);
+    // transposed into the (idle) partial-sum buffer, then one copy each
+    double *aq = d.apart, *av = d.apart + 3 * R;
     if (q) {
-        CK(c, cudaMemcpyAsync(buf.data(), d.q, sizeof(double) * 3 * R, cudaMemcpyDeviceToHost, c->stream));
-        CK(c, cudaStreamSynchronize(c->stream));
-        aos_from_soa(buf, R, q);
+        k_aos_from_soa<<<g, 256, 0, st>>>(R, d.q, aq);
+        CK(c, cudaGetLastError());
+        CK(c, cudaMemcpyAsync(q, aq, sizeof(double) * 3 * R, cudaMemcpyDeviceToHost, st));
     }
     if (v) {
         const double *src = d.v;
         if (c->p.coords == 0) {
-            CK(c, launch_to_dh_impl(d, 1, d.v1, c->mt, c->stream));
+            CK(c, launch_to_dh_impl(d, 1, d.v1, c->mt, st));
             src = d.v1;
         }
-        CK(c, cudaMemcpyAsync(buf.data(), src, sizeof(double) * 3 * R, cudaMemcpyDeviceToHost, c->stream));
-        CK(c, cudaStreamSynchronize(c->stream));
-        aos_from_soa(buf, R, v);
+        k_aos_from_soa<<<g, 256, 0, st>>>(R, src, av);
+        CK(c, cudaGetLastError());
+        CK(c, cudaMemcpyAsync(v, av, sizeof(double) * 3 * R, cudaMemcpyDeviceToHost, st));
     }
+    CK(c, cudaStreamSynchronize(st));
     return QYM_OK;
 }
 
