@@ -485,7 +485,30 @@ static int search_retest(const qym_params &p, int flag) {
     return (flag && p.kick_prec == QYM_KICK_MIXED) ? 1 : 0;
 }
 
-static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last) {
+// The opening kick of a step with the crude encounter search when no |a| of
+// an earlier kick bounds this one (after qym_init or qym_set_state): the kick
+// runs first, then the reaches are built from the kicked state (no |a|
+// allowance needed) and a pass over the tiles runs the search alone.
+static cudaError_t enqueue_fresh_search_kick(qym_ctx *c, double dt) {
+    Dev &d = c->d;
+    const qym_params &p = c->p;
+    cudaStream_t st = c->stream;
+    cudaError_t e;
+    if ((e = launch_kick_tiles(d, p.kick_prec, KICK_FORCE, p.G, c->tune.threads, c->tune.ipt, st)))
+        return e;
+    if ((e = launch_kick_finish_v(d, d.v, d.q, dt, p.G, 0, p.hill_fixed, st))) return e;
+    if ((e = launch_drift_pack_from(d, d.q, d.v, 0.0, 0.0, dt, p.a_E, p.G, 2, p.hill_fixed, st,
+                                    0.0)))
+        return e;
+    if ((e = launch_kick_tiles(d, p.kick_prec, KICK_SEARCH_ONLY, p.G, c->tune.threads,
+                               c->tune.ipt, st)))
+        return e;
+    // kick, finish, pack, search [+ chunk re-test]
+    c->launches += 4 + search_retest(p, 1);
+    return cudaSuccess;
+}
+
+static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last, bool fresh = false) {
     Dev &d = c->d;
     const qym_params &p = c->p;
     cudaStream_t st = c->stream;
@@ -496,8 +519,14 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last) {
     }
     k_step_begin<<<1, 1, 0, st>>>(d.ctr);
     // item 2: kick tau/2, with the crude encounter search when encounters are on
-    if ((e = launch_kick_tiles(d, p.kick_prec, enc, p.G, c->tune.threads, c->tune.ipt, st))) return e;
-    if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, enc, p.hill_fixed, st))) return e;
+    if (enc && fresh) {
+        if ((e = enqueue_fresh_search_kick(c, 0.5 * tau))) return e;
+        c->launches -= 2 + search_retest(p, enc);  // counted below as kick and finish
+    } else {
+        if ((e = launch_kick_tiles(d, p.kick_prec, enc, p.G, c->tune.threads, c->tune.ipt, st)))
+            return e;
+        if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, enc, p.hill_fixed, st))) return e;
+    }
     // item 3: Kepler drift over tau, (q, v) -> (q1, v1)
     if ((e = launch_kepler(step_kepler_args(c, tau), st))) return e;
     if (enc) {
@@ -528,17 +557,19 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last) {
 // ---- merged kicks (params.merge_kicks): the closing kick of a step and the
 // opening kick of the next, at the same separations, become one kick of tau.
 // The opening half kick of the first step (with the encounter search):
-static cudaError_t enqueue_opening_kick(qym_ctx *c, double tau) {
+static cudaError_t enqueue_opening_kick(qym_ctx *c, double tau, bool fresh) {
     Dev &d = c->d;
     const qym_params &p = c->p;
     cudaStream_t st = c->stream;
     cudaError_t e;
     k_step_begin<<<1, 1, 0, st>>>(d.ctr);
+    c->launches += 1;
+    if (p.encounters && fresh) return enqueue_fresh_search_kick(c, 0.5 * tau);
     if ((e = launch_kick_tiles(d, p.kick_prec, p.encounters, p.G, c->tune.threads, c->tune.ipt, st)))
         return e;
     if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, p.encounters, p.hill_fixed, st)))
         return e;
-    c->launches += 3 + search_retest(p, p.encounters);
+    c->launches += 2 + search_retest(p, p.encounters);
     return cudaGetLastError();
 }
 
@@ -643,22 +674,25 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
         CK(c, cudaMemcpyAsync(c->klog_base, &c->klog_steps, sizeof(c->klog_steps),
                               cudaMemcpyHostToDevice, st));
     c->launches = 0;
-    if (!c->amag_valid) {
-        // |a| of the current positions for the first crude search's kick bound
-        CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.0, tau, p.a_E, p.G, 0, p.hill_fixed, st,
-                                     0.5 * tau));
-        CK(c, launch_kick_tiles(d, p.kick_prec, 0, p.G, c->tune.threads, c->tune.ipt, st));
-        CK(c, launch_kick_finish_v(d, d.v, d.q, 0.0, p.G, 0, p.hill_fixed, st));
-        c->amag_valid = true;
-        c->launches += 3;
-    }
+    // without the |a| of an earlier kick the first search runs after its kick
+    const bool fresh = !c->amag_valid;
+    c->amag_valid = true;  // every kick's finisher records |a|
     // item 1 of the first step: drift tau/2
     CK(c, launch_momentum(d, st));
-    CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.5 * tau, tau, p.a_E, p.G, p.encounters,
-                                 p.hill_fixed, st, 0.5 * tau));
+    CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.5 * tau, tau, p.a_E, p.G,
+                                 p.encounters && !fresh, p.hill_fixed, st, 0.5 * tau));
     c->launches += 3;
-    if (p.merge_kicks) CK(c, enqueue_opening_kick(c, tau));
-    const int64_t interior = nsteps - 1;
+    int64_t rest = nsteps;  // steps (or merged units) still to enqueue
+    if (p.merge_kicks) {
+        CK(c, enqueue_opening_kick(c, tau, fresh));
+    } else if (fresh) {
+        CK(c, enqueue_step(c, tau, nsteps == 1, true));
+        if (--rest == 0) {
+            if (c->klog) c->klog_steps += (unsigned long long)nsteps;
+            return collect(c, nsteps);
+        }
+    }
+    const int64_t interior = rest - 1;
     if (interior > 0) {
         if (c->gexec && c->g_tau != tau) {
             cudaGraphExecDestroy(c->gexec);

@@ -78,7 +78,8 @@ struct JPairs {
 // (no branch); since (rho_i + rho_j)^2 <= c_i + c_j, a chunk without a
 // candidate of i has that minimum >= c_i and needs no further look; a chunk
 // with a smaller minimum is recorded and re-tested exactly by k_flag_chunks.
-template <int IPT, bool FLAG, bool DIAG>
+// Without FORCE only the search runs (the same separations and r^2).
+template <int IPT, bool FLAG, bool DIAG, bool FORCE>
 __device__ __forceinline__ void mixed_chunk(const JPairs &s, int p0, int p1,
                                             const float2 (&nxh)[IPT], const float2 (&nyh)[IPT],
                                             const float2 (&nzh)[IPT], const float2 (&nxl)[IPT],
@@ -98,15 +99,17 @@ __device__ __forceinline__ void mixed_chunk(const JPairs &s, int p0, int p1,
             const float2 dy = __fadd2_rn(__fadd2_rn(yh, nyh[k]), __fadd2_rn(yl, nyl[k]));
             const float2 dz = __fadd2_rn(__fadd2_rn(zh, nzh[k]), __fadd2_rn(zl, nzl[k]));
             const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-            const float2 ri = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
-            float2 sm = __fmul2_rn(__fmul2_rn(gm, ri), __fmul2_rn(ri, ri));
-            if (DIAG) {
-                sm.x = (r2.x > 0.0f) ? sm.x : 0.0f;
-                sm.y = (r2.y > 0.0f) ? sm.y : 0.0f;
+            if (FORCE) {
+                const float2 ri = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+                float2 sm = __fmul2_rn(__fmul2_rn(gm, ri), __fmul2_rn(ri, ri));
+                if (DIAG) {
+                    sm.x = (r2.x > 0.0f) ? sm.x : 0.0f;
+                    sm.y = (r2.y > 0.0f) ? sm.y : 0.0f;
+                }
+                fx[k] = __ffma2_rn(sm, dx, fx[k]);
+                fy[k] = __ffma2_rn(sm, dy, fy[k]);
+                fz[k] = __ffma2_rn(sm, dz, fz[k]);
             }
-            fx[k] = __ffma2_rn(sm, dx, fx[k]);
-            fy[k] = __ffma2_rn(sm, dy, fy[k]);
-            fz[k] = __ffma2_rn(sm, dz, fz[k]);
             if (FLAG) {
                 const float2 t = __fadd2_rn(r2, nc);
                 mind[k] = fminf(mind[k], fminf(t.x, t.y));
@@ -131,7 +134,8 @@ __device__ __forceinline__ void push_flag(const KickArgs &a, int i, int j0, int 
         atomicOr(a.status, QYM_ST_CAND_OVERFLOW);
 }
 
-template <int IPT, bool FLAG>
+// FORCE = false: the crude search alone (no partial sums written)
+template <int IPT, bool FLAG, bool FORCE>
 __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
     __shared__ float4 s_a[TILE / 2], s_b[TILE / 2], s_c[TILE / 2], s_d[TILE / 2];
     const JPairs sp{s_a, s_b, s_c, s_d};
@@ -188,19 +192,24 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
                 mind[k] = 3.0e38f;
             }
             if (diag)
-                mixed_chunk<IPT, FLAG, true>(sp, c, ce, nxh, nyh, nzh, nxl, nyl, nzl, fx, fy, fz, mind);
+                mixed_chunk<IPT, FLAG, true, FORCE>(sp, c, ce, nxh, nyh, nzh, nxl, nyl, nzl, fx, fy,
+                                                    fz, mind);
             else
-                mixed_chunk<IPT, FLAG, false>(sp, c, ce, nxh, nyh, nzh, nxl, nyl, nzl, fx, fy, fz, mind);
+                mixed_chunk<IPT, FLAG, false, FORCE>(sp, c, ce, nxh, nyh, nzh, nxl, nyl, nzl, fx, fy,
+                                                     fz, mind);
 #pragma unroll
             for (int k = 0; k < IPT; ++k) {
-                float s, e;
-                two_sum(ahx[k], fx[k].x + fx[k].y, s, e); ahx[k] = s; alx[k] += e;
-                two_sum(ahy[k], fy[k].x + fy[k].y, s, e); ahy[k] = s; aly[k] += e;
-                two_sum(ahz[k], fz[k].x + fz[k].y, s, e); ahz[k] = s; alz[k] += e;
+                if (FORCE) {
+                    float s, e;
+                    two_sum(ahx[k], fx[k].x + fx[k].y, s, e); ahx[k] = s; alx[k] += e;
+                    two_sum(ahy[k], fy[k].x + fy[k].y, s, e); ahy[k] = s; aly[k] += e;
+                    two_sum(ahz[k], fz[k].x + fz[k].y, s, e); ahz[k] = s; alz[k] += e;
+                }
                 if (FLAG && mind[k] < rho[k]) push_flag(a, gi[k], jt + 2 * c, jt + min(2 * ce, n));
             }
         }
     }
+    if (!FORCE) return;
     const int64_t rows = a.rows;
     double *out = a.apart + (int64_t)slot * 3 * rows;
 #pragma unroll
@@ -248,7 +257,7 @@ __global__ void __launch_bounds__(256) k_flag_chunks(KickArgs a, unsigned long l
 }
 
 // ---------------------------------------------------------------- FP64 form
-template <int IPT, bool FLAG>
+template <int IPT, bool FLAG, bool FORCE>
 __global__ void __launch_bounds__(256) k_kick_fp64(KickArgs a) {
     __shared__ D4 s_q[TILE];
     __shared__ float s_rho[TILE];
@@ -288,12 +297,14 @@ __global__ void __launch_bounds__(256) k_kick_fp64(KickArgs a) {
             for (int k = 0; k < IPT; ++k) {
                 double dx = xi[k] - p.x, dy = yi[k] - p.y, dz = zi[k] - p.z;
                 double r2 = dx * dx + dy * dy + dz * dz;
-                double ri = rsqrt(r2);
-                double s = p.w * (ri * ri) * ri;
-                s = (r2 > 0.0) ? s : 0.0;
-                ax[k] -= s * dx;
-                ay[k] -= s * dy;
-                az[k] -= s * dz;
+                if (FORCE) {
+                    double ri = rsqrt(r2);
+                    double s = p.w * (ri * ri) * ri;
+                    s = (r2 > 0.0) ? s : 0.0;
+                    ax[k] -= s * dx;
+                    ay[k] -= s * dy;
+                    az[k] -= s * dz;
+                }
                 if (FLAG) {
                     if ((float)r2 < rho[k] + s_rho[j]) {
                         int gj = jt + j;
@@ -303,6 +314,7 @@ __global__ void __launch_bounds__(256) k_kick_fp64(KickArgs a) {
             }
         }
     }
+    if (!FORCE) return;
     double *out = a.apart + (int64_t)slot * 3 * rows;
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
@@ -355,25 +367,25 @@ void kick_items_host(const int64_t *offsets, int32_t nsys, const KickTune &t, in
     *splits_used = t.splits;
 }
 
-template <bool FLAG>
+template <bool FLAG, bool FORCE>
 static cudaError_t launch_mixed(const KickArgs &a, int nitems, int threads, int ipt,
                                 cudaStream_t st) {
     switch (ipt) {
-    case 1: k_kick_mixed<1, FLAG><<<nitems, threads, 0, st>>>(a); break;
-    case 2: k_kick_mixed<2, FLAG><<<nitems, threads, 0, st>>>(a); break;
-    case 4: k_kick_mixed<4, FLAG><<<nitems, threads, 0, st>>>(a); break;
+    case 1: k_kick_mixed<1, FLAG, FORCE><<<nitems, threads, 0, st>>>(a); break;
+    case 2: k_kick_mixed<2, FLAG, FORCE><<<nitems, threads, 0, st>>>(a); break;
+    case 4: k_kick_mixed<4, FLAG, FORCE><<<nitems, threads, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-template <bool FLAG>
+template <bool FLAG, bool FORCE>
 static cudaError_t launch_f64(const KickArgs &a, int nitems, int threads, int ipt,
                               cudaStream_t st) {
     switch (ipt) {
-    case 1: k_kick_fp64<1, FLAG><<<nitems, threads, 0, st>>>(a); break;
-    case 2: k_kick_fp64<2, FLAG><<<nitems, threads, 0, st>>>(a); break;
-    default: k_kick_fp64<2, FLAG><<<nitems, threads, 0, st>>>(a); break;
+    case 1: k_kick_fp64<1, FLAG, FORCE><<<nitems, threads, 0, st>>>(a); break;
+    case 2: k_kick_fp64<2, FLAG, FORCE><<<nitems, threads, 0, st>>>(a); break;
+    default: k_kick_fp64<2, FLAG, FORCE><<<nitems, threads, 0, st>>>(a); break;
     }
     return cudaGetLastError();
 }
@@ -398,9 +410,13 @@ cudaError_t launch_kick_tiles(const Dev &d, int prec, int flag, double G, int th
     a.max_fchunk = d.max_fchunk;
     a.nfchunk = d.ctr + C_NFCHUNK;
     a.status = d.status;
+    if (flag != KICK_FORCE && flag != KICK_SEARCH && flag != KICK_SEARCH_ONLY)
+        return cudaErrorInvalidValue;
     if (prec == QYM_KICK_MIXED) {
-        if (!flag) return launch_mixed<false>(a, d.nitems, threads, ipt, st);
-        cudaError_t e = launch_mixed<true>(a, d.nitems, threads, ipt, st);
+        if (flag == KICK_FORCE) return launch_mixed<false, true>(a, d.nitems, threads, ipt, st);
+        cudaError_t e = flag == KICK_SEARCH
+                            ? launch_mixed<true, true>(a, d.nitems, threads, ipt, st)
+                            : launch_mixed<true, false>(a, d.nitems, threads, ipt, st);
         if (e) return e;
         // about one entry per row (its own chunk) plus the close pairs
         int64_t blocks = (d.rows + 63) / 64;
@@ -409,8 +425,9 @@ cudaError_t launch_kick_tiles(const Dev &d, int prec, int flag, double G, int th
         k_flag_chunks<<<(int)blocks, 256, 0, st>>>(a, d.ctr + C_FCDONE);
         return cudaGetLastError();
     }
-    return flag ? launch_f64<true>(a, d.nitems, threads, ipt, st)
-                : launch_f64<false>(a, d.nitems, threads, ipt, st);
+    if (flag == KICK_FORCE) return launch_f64<false, true>(a, d.nitems, threads, ipt, st);
+    return flag == KICK_SEARCH ? launch_f64<true, true>(a, d.nitems, threads, ipt, st)
+                               : launch_f64<true, false>(a, d.nitems, threads, ipt, st);
 }
 
 // ---------------------------------------------------------------- single system
@@ -576,7 +593,7 @@ cudaError_t launch_accel_single(int64_t rows, const double *m, const double *q, 
         ka.q = q; ka.m = m; ka.G = G; ka.apart = d.apart; ka.rows = rows;
         ka.cand = nullptr; ka.max_cand = 0; ka.ncand = nullptr; ka.status = nullptr;
         ka.fchunk = nullptr; ka.max_fchunk = 0; ka.nfchunk = nullptr;
-        e = launch_f64<false>(ka, L.nitems, L.tune.threads, L.tune.ipt, st);
+        e = launch_f64<false, true>(ka, L.nitems, L.tune.threads, L.tune.ipt, st);
     }
     if (e != cudaSuccess) return e;
     k_sum_partials<<<(unsigned)((rows + tb - 1) / tb), tb, 0, st>>>(rows, L.splits, d.apart, hl, m,

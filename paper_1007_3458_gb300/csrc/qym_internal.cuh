@@ -210,6 +210,12 @@ struct KickTune {
     int32_t ipt = 2;        // i rows per thread
     int32_t splits = 1;     // j splits per system
 };
+// flag: what a pass over the tiles does
+enum KickMode {
+    KICK_FORCE = 0,        // the interaction sums only
+    KICK_SEARCH = 1,       // the sums and the crude encounter search
+    KICK_SEARCH_ONLY = 2,  // the crude encounter search alone (no sums written)
+};
 cudaError_t launch_kick_tiles(const Dev &d, int prec, int flag, double G, int threads, int ipt,
                               cudaStream_t st);
 cudaError_t launch_accel_single(int64_t rows, const double *m, const double *q, double *a,

@@ -67,7 +67,9 @@ __device__ __forceinline__ float round_up_f(double x) {
 // E_Dft: Q += h S / m0 for h_close then h_open (each a separate half-drift,
 // Sec. 2.3 items 10 and 1), read from (qs, vs) and written to (d.q, d.v);
 // then the float packs of the coming kick, with the crude encounter reach when
-// the coming kick searches for encounters (Sec. 2.4).
+// the coming kick searches for encounters (Sec. 2.4). flag_next = 2: the packs
+// of a search that runs after the step's first kick, on the state that enters
+// the Kepler drift; the Hill radius of the step is recorded here then.
 struct DriftArgs {
     const double *qs, *vs;
     double h_close, h_open, tau, a_E, G;
@@ -125,6 +127,7 @@ __global__ void __launch_bounds__(256) k_drift_pack(Dev d, DriftArgs a) {
         } else {
             rH = hill(qx, qy, qz, mm, m0);  // positions do not change in the kick
         }
+        if (a.flag_next == 2) d.rH[r] = rH;
         float rHb = round_up_f(rH * (1.0 + 1e-6));
         d.rH_bound[r] = rHb;
         double rr = sqrt(qx * qx + qy * qy + qz * qz);
