@@ -313,7 +313,9 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     sc0[nsys] = (int32_t)mch.size();
     d.nmchunks = (int32_t)mch.size();
     d.max_cand = params->max_candidates ? params->max_candidates : std::max<int64_t>(1 << 20, 16 * R);
-    d.max_fchunk = d.max_cand + R;  // every row flags the chunk holding itself
+    // a flagged chunk holds a partner within the crude bound: at most two
+    // records per candidate pair, plus a margin of one per row
+    d.max_fchunk = d.max_cand + R;
     d.max_enc = params->max_encounters ? params->max_encounters : std::max<int64_t>(1 << 16, R);
     d.max_log = params->max_log ? params->max_log : (int64_t)1 << 22;
     d.max_sets = (int32_t)R;
@@ -1109,6 +1111,8 @@ extern "C" qym_status qym_autotune(qym_ctx *c) {
     }
     qym_status s = apply_tune(c, best);
     if (s != QYM_OK) return s;
+    c->stats.kick_tile_i = best.threads * best.ipt;
+    c->stats.kick_tile_splits = best.splits;
     c->amag_valid = false;
     return QYM_OK;
 }

@@ -46,6 +46,13 @@ struct KickArgs {
     int32_t *status;
 };
 
+// min(a, b, c) in one instruction (the three-input form of sm_100 and later)
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // append candidate (i, j) from a divergent branch, warp-aggregated
 __device__ __forceinline__ void push_candidate(const KickArgs &a, int i, int j) {
     unsigned mask = __activemask();
@@ -78,9 +85,12 @@ struct JPairs {
 // (no branch); since (rho_i + rho_j)^2 <= c_i + c_j, a chunk without a
 // candidate of i has that minimum >= c_i and needs no further look; a chunk
 // with a smaller minimum is recorded and re-tested exactly by k_flag_chunks.
-// Without FORCE only the search runs (the same separations and r^2).
+// In a chunk of the diagonal tile the row's own j (r^2 = 0) is left out of
+// the minimum. Without FORCE only the search runs (the same separations and
+// r^2).
 template <int IPT, bool FLAG, bool DIAG, bool FORCE>
-__device__ __forceinline__ void mixed_chunk(const JPairs &s, int p0, int p1,
+__device__ __forceinline__ void mixed_chunk(const JPairs &s, int p0, int p1, int jt,
+                                            const int (&gi)[IPT],
                                             const float2 (&nxh)[IPT], const float2 (&nyh)[IPT],
                                             const float2 (&nzh)[IPT], const float2 (&nxl)[IPT],
                                             const float2 (&nyl)[IPT], const float2 (&nzl)[IPT],
@@ -111,8 +121,12 @@ __device__ __forceinline__ void mixed_chunk(const JPairs &s, int p0, int p1,
                 fz[k] = __ffma2_rn(sm, dz, fz[k]);
             }
             if (FLAG) {
-                const float2 t = __fadd2_rn(r2, nc);
-                mind[k] = fminf(mind[k], fminf(t.x, t.y));
+                float2 t = __fadd2_rn(r2, nc);
+                if (DIAG) {  // a row is not its own partner
+                    t.x = (jt + 2 * p == gi[k]) ? 3.0e38f : t.x;
+                    t.y = (jt + 2 * p + 1 == gi[k]) ? 3.0e38f : t.y;
+                }
+                mind[k] = fmin3(mind[k], t.x, t.y);
             }
         }
     }
@@ -192,11 +206,11 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
                 mind[k] = 3.0e38f;
             }
             if (diag)
-                mixed_chunk<IPT, FLAG, true, FORCE>(sp, c, ce, nxh, nyh, nzh, nxl, nyl, nzl, fx, fy,
-                                                    fz, mind);
+                mixed_chunk<IPT, FLAG, true, FORCE>(sp, c, ce, jt, gi, nxh, nyh, nzh, nxl, nyl, nzl,
+                                                    fx, fy, fz, mind);
             else
-                mixed_chunk<IPT, FLAG, false, FORCE>(sp, c, ce, nxh, nyh, nzh, nxl, nyl, nzl, fx, fy,
-                                                     fz, mind);
+                mixed_chunk<IPT, FLAG, false, FORCE>(sp, c, ce, jt, gi, nxh, nyh, nzh, nxl, nyl, nzl,
+                                                     fx, fy, fz, mind);
 #pragma unroll
             for (int k = 0; k < IPT; ++k) {
                 if (FORCE) {
@@ -205,7 +219,10 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
                     two_sum(ahy[k], fy[k].x + fy[k].y, s, e); ahy[k] = s; aly[k] += e;
                     two_sum(ahz[k], fz[k].x + fz[k].y, s, e); ahz[k] = s; alz[k] += e;
                 }
-                if (FLAG && mind[k] < rho[k]) push_flag(a, gi[k], jt + 2 * c, jt + min(2 * ce, n));
+                // only partners j > i become candidates, so a chunk wholly at or
+                // below the row needs no record
+                const int j1 = jt + min(2 * ce, n);
+                if (FLAG && mind[k] < rho[k] && j1 - 1 > gi[k]) push_flag(a, gi[k], jt + 2 * c, j1);
             }
         }
     }
