@@ -144,6 +144,20 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
+# DRAM bytes (read + written) per launch of the mixed kick, from one ncu
+# capture of each workload's kick after autotuning (dram__bytes_read.sum +
+# dram__bytes_write.sum, the mean of the searching and the plain kick, three
+# launches each); keyed by (workload, rows per CTA, j-splits), since the
+# partial-sum slots written grow with the splits. The captures are summarised
+# in profiles/k_kick_mixed_<workload>.md; a shape not captured reports null,
+# and so does any kick kernel changed since.
+KICK_DRAM_BYTES = {
+    ("disk_16384", 256, 64): 6.244e5,
+    ("disk_262144", 256, 64): 3.623e8,
+    ("ensemble_512", 256, 4): 7.707e7,
+}
+
+
 def fp32_peak_tflops(sm_mhz):
     """FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -388,7 +402,9 @@ def run_ours(args):
     peak = fp32_peak_tflops(2070.0)
     roof = {"bound": "alu", "kernel": "k_kick_mixed" if prec else "k_kick_fp64",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None,
+            "traffic": (KICK_DRAM_BYTES.get((args.workload, st["kick_tile_i"], st["kick_tile_splits"]))
+                        if prec else None),
+            "traffic_unit": "bytes per launch (ncu)",
             "convention": "20 flop per ordered pair, FP32 FMA-pipe peak 152 SM x 128 x 2 x 2070 MHz",
             "kick_ms_with_search": k1_ms, "kick_ms_plain": k2_ms,
             "gpair_per_s_kernel": pairs / (kick_ms / 1e3) / 1e9}
