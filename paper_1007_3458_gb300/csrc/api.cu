@@ -163,6 +163,9 @@ static void carve_all(qym_ctx *c, Carver &k) {
     d.set_start = k.take<int32_t>((size_t)d.max_sets + 1);
     d.set_mem = k.take<int32_t>(d.max_members);
     d.rcrit = k.take<double>(d.max_sets);
+    d.hcost = k.take<int32_t>(R);
+    d.hq = k.take<int32_t>(d.max_sets);
+    d.hcl = k.take<int32_t>(kHermMaxClusters);
     d.uf = k.take<int32_t>(R);
     d.log = k.take<int64_t>(3 * (size_t)d.max_log);
     d.ctr = k.take<unsigned long long>(C_COUNT);
@@ -550,9 +553,9 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last, bool fresh = 
                                     p.G, (!last) && enc, p.hill_fixed, st, 0.5 * tau)))
         return e;
     k_step_end<<<1, 1, 0, st>>>(d.ctr, d.max_cand, d.max_enc);
-    // begin, kick [+ chunk re-test], finish, Kepler, [refine 2, sets 7, Hermite],
+    // begin, kick [+ chunk re-test], finish, Kepler, [refine 2, sets 7, Hermite plan, Hermite],
     // pack, kick, finish, momentum 2, drift, end
-    c->launches += 12 + (enc ? 10 : 0) + search_retest(p, enc);
+    c->launches += 12 + (enc ? 11 : 0) + search_retest(p, enc);
     return cudaGetLastError();
 }
 
@@ -609,9 +612,9 @@ static cudaError_t enqueue_unit(qym_ctx *c, double tau, bool last) {
             return e;
         if ((e = launch_kick_tiles(d, p.kick_prec, enc, p.G, c->tune.threads, c->tune.ipt, st))) return e;
         if ((e = launch_kick_finish_v(d, d.v, d.q, tau, p.G, enc, p.hill_fixed, st, 2.0))) return e;
-        // Kepler, [refine 2, sets 7, Hermite], end, copy, begin, momentum 2, drift, kick
+        // Kepler, [refine 2, sets 7, Hermite plan, Hermite], end, copy, begin, momentum 2, drift, kick
         // [+ chunk re-test], finish
-        c->launches += 9 + (enc ? 10 : 0) + search_retest(p, enc);
+        c->launches += 9 + (enc ? 11 : 0) + search_retest(p, enc);
     } else {
         if ((e = launch_kick_tiles(d, p.kick_prec, 0, p.G, c->tune.threads, c->tune.ipt, st))) return e;
         if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, 0, p.hill_fixed, st))) return e;
@@ -619,8 +622,8 @@ static cudaError_t enqueue_unit(qym_ctx *c, double tau, bool last) {
         if ((e = launch_drift_pack_from(d, d.q, d.v, 0.5 * tau, 0.0, tau, p.a_E, p.G, 0,
                                         p.hill_fixed, st, 0.5 * tau)))
             return e;
-        // Kepler, [refine 2, sets 7, Hermite], end, copy, kick, finish, momentum 2, drift
-        c->launches += 8 + (enc ? 10 : 0);
+        // Kepler, [refine 2, sets 7, Hermite plan, Hermite], end, copy, kick, finish, momentum 2, drift
+        c->launches += 8 + (enc ? 11 : 0);
     }
     return cudaGetLastError();
 }

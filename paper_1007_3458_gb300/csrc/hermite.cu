@@ -1024,6 +1024,7 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
             d.v1[R + r] = S.v[k] - 0.5 * tau * c[1];
             d.v1[2 * R + r] = S.w[k] - 0.5 * tau * c[2];
             d.uf[r] = -1;
+            d.hcost[r] = (int32_t)min(steps, (int64_t)INT_MAX);
         }
     }
     if (tid == 0 && rank == 0) {
@@ -1034,36 +1035,119 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
     if (COOP) cl.sync(); else __syncthreads();
 }
 
-// Sets of at least NBIG members go to whole clusters (the i-th such set to
-// cluster i mod #clusters); the others are taken one CTA at a time in the
+// The Hermite kernel's schedule for this step. A set's chain of block steps
+// runs on one CTA (or one cluster) from start to end, so the step lasts as
+// long as its longest set; which set that is can be foreseen, since a close
+// pair stays close over consecutive steps. A set's predicted cost is the
+// largest count of block steps among its members' sets of the previous step
+// (hcost; 0 for rows that were in no set). Sets of at least NBIG members with
+// the highest predicted cost (then the most members, then the lowest index)
+// take the ncl clusters, one each; the other sets form the per-CTA queue in
+// descending predicted cost, so the longest chains start first. With more
+// than kPlanCap sets the queue keeps the set order and no cluster is used.
+// One CTA of 1024 threads; the sets are ordered by a bitonic sort of 64-bit
+// keys in shared memory.
+constexpr int kPlanCap = 4096;
+__global__ void __launch_bounds__(1024) k_hermite_plan(Dev d, int ncl) {
+    __shared__ unsigned long long key[kPlanCap];
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x;
+    const int nsets = (int)min((unsigned long long)d.max_sets, d.ctr[C_NSETS]);
+    if (ncl > kHermMaxClusters) ncl = kHermMaxClusters;
+    for (int c = tid; c < kHermMaxClusters; c += blockDim.x) d.hcl[c] = -1;
+    if (nsets > kPlanCap) {
+        for (int k = tid; k < nsets; k += blockDim.x) d.hq[k] = k;
+        if (tid == 0) d.ctr[C_HNQ] = (unsigned long long)nsets;
+        return;
+    }
+    int P = 1;
+    while (P < nsets) P <<= 1;
+    // key: predicted cost (31 bits) | members (16 bits) | 0xffff - set index
+    for (int k = tid; k < P; k += blockDim.x) {
+        unsigned long long kk = 0;
+        if (k < nsets) {
+            const int st = d.set_start[k];
+            const int n = d.set_start[k + 1] - st;
+            int cost = 0;
+            for (int m = 0; m < n && st + m < d.max_members; ++m)
+                cost = max(cost, d.hcost[d.set_mem[st + m]]);
+            kk = ((unsigned long long)min(max(cost, 0), 0x7fffffff) << 32) |
+                 ((unsigned long long)min(max(n, 0), 0xffff) << 16) | (unsigned long long)(0xffff - k);
+        }
+        key[k] = kk;
+    }
+    __syncthreads();
+    // descending bitonic sort (padding keys are 0 and sink to the end)
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int k = tid; k < P; k += blockDim.x) {
+                const int o = k ^ stride;
+                if (o > k) {
+                    const bool desc = (k & size) == 0;
+                    const unsigned long long a = key[k], b = key[o];
+                    if (desc ? a < b : a > b) {
+                        key[k] = b;
+                        key[o] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // in sorted order: eligible = at least NBIG members; the first ncl
+    // eligible sets go to the clusters, the rest keep their order in the queue
+    constexpr int PER = kPlanCap / 1024;
+    const int k0 = tid * PER;
+    int e[PER], cnt = 0;
+    for (int i = 0; i < PER; ++i) {
+        const int k = k0 + i;
+        e[i] = (k < nsets && (int)((key[k] >> 16) & 0xffff) >= NBIG) ? 1 : 0;
+        cnt += e[i];
+    }
+    // exclusive prefix of cnt over the threads
+    const int lane = tid & 31, w = tid >> 5;
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    int before = incl - cnt;
+    for (int k = 0; k < w; ++k) before += wsum[k];
+    int total = 0;
+    for (int k = 0; k < 32; ++k) total += wsum[k];
+    for (int i = 0; i < PER; ++i) {
+        const int k = k0 + i;
+        if (k >= nsets) break;
+        const int set = 0xffff - (int)(key[k] & 0xffff);
+        if (e[i] && before < ncl) {
+            d.hcl[before] = set;
+        } else {
+            d.hq[k - min(before, ncl)] = set;
+        }
+        before += e[i];
+    }
+    if (tid == 0) d.ctr[C_HNQ] = (unsigned long long)(nsets - min(total, ncl));
+}
+
+// Each cluster first integrates the set the plan gave it (all its CTAs on
+// one set), then every CTA takes sets one at a time from the queue, in the
 // order of a counter, so CTAs freed early take more.
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(HTHREADS, 2) k_hermite(Dev d, HermArgs h) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
-    const int nsets = (int)min((unsigned long long)d.max_sets, d.ctr[C_NSETS]);
-    // clusters pay off when large sets are few (one system, a few planets);
-    // with more large sets than clusters, set-level parallelism wins and
-    // every set runs on one CTA
-    int nbig = 0;
-    for (int set = 0; set < nsets && nbig <= ncl; ++set)
-        nbig += d.set_start[set + 1] - d.set_start[set] >= NBIG;
-    const int big = nbig <= ncl ? NBIG : INT_MAX;
-    int ib = 0;
-    for (int set = 0; set < nsets && big == NBIG; ++set) {
-        const int n = d.set_start[set + 1] - d.set_start[set];
-        if (n < big) continue;
-        if (ib++ % ncl != cid) continue;
-        hermite_set<true>(d, h, set, rank, CL);
-    }
+    const int cid = blockIdx.x / CL;
+    const int cset = cid < kHermMaxClusters ? d.hcl[cid] : -1;
+    if (cset >= 0) hermite_set<true>(d, h, cset, rank, CL);
+    const int nq = (int)d.ctr[C_HNQ];
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) g_next_small = (int)atomicAdd(d.ctr + C_HSMALL, 1ull);
         __syncthreads();
-        const int set = g_next_small;
-        if (set >= nsets) break;
-        if (d.set_start[set + 1] - d.set_start[set] >= big) continue;
-        hermite_set<false>(d, h, set, 0, 1);
+        const int k = g_next_small;
+        if (k >= nq) break;
+        hermite_set<false>(d, h, d.hq[k], 0, 1);
     }
 }
 
@@ -1080,7 +1164,15 @@ cudaError_t launch_hermite(const Dev &d, const qym_params &p, double tau, cudaSt
     h.eta_s = p.eta_s;
     h.tau = tau;
     h.max_steps = p.max_hermite_steps;
-    k_hermite<<<2 * 152, HTHREADS, kHermSmem, st>>>(d, h);
+    constexpr int kGrid = 2 * 152;
+    static_assert(kGrid / CL <= kHermMaxClusters, "more clusters than plan entries");
+    k_hermite_plan<<<1, 1024, 0, st>>>(d, kGrid / CL);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the plan has read the previous step's costs; this step's sets write theirs
+    e = cudaMemsetAsync(d.hcost, 0, sizeof(int32_t) * (size_t)d.rows, st);
+    if (e != cudaSuccess) return e;
+    k_hermite<<<kGrid, HTHREADS, kHermSmem, st>>>(d, h);
     return cudaGetLastError();
 }
 

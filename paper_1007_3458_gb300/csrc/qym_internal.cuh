@@ -9,6 +9,7 @@
 namespace qym {
 
 constexpr double kPi = 3.14159265358979323846;
+constexpr int kHermMaxClusters = 160;  // entries of Dev::hcl (2 x 152 CTAs in clusters of 2 or more)
 
 // ---------------------------------------------------------------- layout
 // Device state of a context. Rows of all systems are concatenated; each
@@ -54,6 +55,12 @@ struct Dev {
     int32_t *set_mem = nullptr;   // [max_members]
     double *rcrit = nullptr;      // [max_sets]
     int32_t max_sets = 0, max_members = 0;
+    // Hermite schedule: block steps of the set each row was in during the
+    // last step (0 for rows in no set), the per-CTA queue of sets in order of
+    // predicted cost, and the set each thread-block cluster takes (-1: none)
+    int32_t *hcost = nullptr;     // [rows]
+    int32_t *hq = nullptr;        // [max_sets]
+    int32_t *hcl = nullptr;       // [kHermMaxClusters]
     int32_t *uf = nullptr;        // [rows] union-find parents, kept at -1 when idle
     int64_t *log = nullptr;       // [max_log][3] encounter records of one qym_step call
     int64_t max_log = 0;
@@ -87,6 +94,7 @@ enum Ctr : int {
     C_HSMALL,        // next set for the Hermite kernel's per-CTA queue (reset per step)
     C_NFCHUNK,       // flagged (row, j chunk) entries of the last search kick
     C_FCDONE,        // CTAs of the chunk re-test done (its last CTA resets both)
+    C_HNQ,           // sets in the Hermite kernel's per-CTA queue this step
     C_COUNT
 };
 
