@@ -109,7 +109,9 @@ typedef struct qym_params {
                                    total momentum, so Int(tau/2) Dft(tau) Int(tau/2) =
                                    Dft(tau) Int(tau)); one all-pairs pass per step instead
                                    of two. 0: the paper's two kicks per step */
-    int32_t reserved0;          /* must be 0 */
+    int32_t hermite_cluster;    /* CTAs of a thread-block cluster that share one large
+                                   encounter set in the Hermite: 2, 4 or 8; 0: automatic
+                                   (8 for a single system, 2 for a batch of systems) */
 } qym_params;
 
 #define QYM_HEAVY_CAP 256

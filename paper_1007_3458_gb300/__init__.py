@@ -45,7 +45,7 @@ class qym_params(C.Structure):
                 ("max_hermite_steps", C.c_int64), ("max_candidates", C.c_int64),
                 ("max_encounters", C.c_int64), ("max_log", C.c_int64),
                 ("l2_flush_bytes", C.c_int64), ("heavy_mass", C.c_double),
-                ("merge_kicks", C.c_int32), ("reserved0", C.c_int32)]
+                ("merge_kicks", C.c_int32), ("hermite_cluster", C.c_int32)]
 
 
 class qym_stats(C.Structure):

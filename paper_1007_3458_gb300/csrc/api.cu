@@ -111,7 +111,11 @@ static bool valid_params(const qym_params *p, std::string &why) {
     if (p->max_candidates < 0 || p->max_encounters < 0 || p->max_log < 0) { why = "capacities"; return false; }
     if (p->l2_flush_bytes < 0 || p->l2_flush_bytes > ((int64_t)1 << 34)) { why = "l2_flush_bytes"; return false; }
     if (p->merge_kicks != 0 && p->merge_kicks != 1) { why = "merge_kicks must be 0 or 1"; return false; }
-    if (p->reserved0 != 0) { why = "reserved0 must be 0"; return false; }
+    if (p->hermite_cluster != 0 && p->hermite_cluster != 2 && p->hermite_cluster != 4 &&
+        p->hermite_cluster != 8) {
+        why = "hermite_cluster must be 0, 2, 4 or 8";
+        return false;
+    }
     return true;
 }
 

@@ -135,11 +135,9 @@ cudaError_t launch_transition(int64_t n, const double *s, double rc, double *K, 
 // through the stack of the per-set function)
 extern __shared__ __align__(16) unsigned char g_hsmem[];
 
-#ifndef QYM_HERM_CL
-#define QYM_HERM_CL 8
-#endif
-constexpr int CL = QYM_HERM_CL;  // CTAs of a cluster sharing one large set
-static_assert(CL == 2 || CL == 4 || CL == 8, "a cluster is 2, 4 or 8 CTAs (one lane group of 8 pushes)");
+// CTAs of a cluster sharing one large set: 2, 4 or 8 (one lane group of 8
+// pushes), chosen per context at launch; buffers are sized for the largest
+constexpr int CLMAX = 8;
 #ifndef QYM_HERM_NBIG
 #define QYM_HERM_NBIG 24
 #endif
@@ -189,7 +187,7 @@ __device__ __forceinline__ HermSmem carve(void *base) {
     s.ax = p; p += HCAP; s.ay = p; p += HCAP; s.az = p; p += HCAP;
     s.jx = p; p += HCAP; s.jy = p; p += HCAP; s.jz = p; p += HCAP;
     s.pr = p; p += 6 * HTHREADS;
-    s.rb = p; p += 2 * CL * 6 * RSL;
+    s.rb = p; p += 2 * CLMAX * 6 * RSL;
     s.a1s = p; p += 6 * ACH;
     s.lvt = p; p += LV_N * (KMAX + 1);
     s.ti = (long long *)p; p += HCAP;
@@ -206,7 +204,7 @@ __device__ __forceinline__ HermSmem carve(void *base) {
     return s;
 }
 constexpr size_t kHermSmem =
-    sizeof(double) * (HCAP * 20 + 6 * HTHREADS + 2 * CL * 6 * RSL + 6 * ACH + LV_N * (KMAX + 1)) +
+    sizeof(double) * (HCAP * 20 + 6 * HTHREADS + 2 * CLMAX * 6 * RSL + 6 * ACH + LV_N * (KMAX + 1)) +
     sizeof(float) * (16 * HCAP + 12 * ACH) + sizeof(int32_t) * HCAP * 7;
 static_assert(2 * 3 * 96 * sizeof(double) <= 4 * HCAP * sizeof(int32_t),
               "the two-warp force's exchange slots overlay need and nl");
@@ -552,7 +550,7 @@ __device__ __forceinline__ void pull_range(cg::cluster_group &cl, const HermSmem
 // are read from the peers' shared memory in rank order, and every CTA applies
 // the same corrector, so the copies stay identical with one cluster barrier
 // per exchange round (partials double-buffered).
-template <bool COOP>
+template <bool COOP, int CLT>
 __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set, int rank,
                                          int cs) {
     const HermSmem S = carve(g_hsmem);
@@ -898,7 +896,7 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                     // again only after the next round's cluster barrier, which
                     // every CTA passes after reading it.
                     __syncthreads();
-                    double *rbb = S.rb + buf * (CL * 6 * RSL);
+                    double *rbb = S.rb + buf * (CLT * 6 * RSL);
                     const int g = wl & 7;
                     for (int pi0 = warp * 4; pi0 < 6 * cnt; pi0 += HTHREADS / 8) {
                         const int pi = pi0 + (wl >> 3);
@@ -911,17 +909,17 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                         v += __shfl_xor_sync(0xffffffffu, v, 2);
                         v += __shfl_xor_sync(0xffffffffu, v, 4);
                         if (live && with_star) v += prb[c * HTHREADS + 224 + sl];
-                        if (live && g < CL) cl.map_shared_rank(rbb, g)[(rank * 6 + c) * RSL + sl] = v;
+                        if (live && g < CLT) cl.map_shared_rank(rbb, g)[(rank * 6 + c) * RSL + sl] = v;
                     }
                     cl.sync();
                     for (int pi = tid; pi < 6 * cnt; pi += HTHREADS) {
                         const int sl = pi / 6, c = pi - 6 * sl;
-                        double pv[CL];
+                        double pv[CLT];
 #pragma unroll
-                        for (int r = 0; r < CL; ++r) pv[r] = rbb[(r * 6 + c) * RSL + sl];
+                        for (int r = 0; r < CLT; ++r) pv[r] = rbb[(r * 6 + c) * RSL + sl];
                         // pairwise tree: rank r with rank r + w, halving w
 #pragma unroll
-                        for (int w = CL / 2; w >= 1; w >>= 1) {
+                        for (int w = CLT / 2; w >= 1; w >>= 1) {
 #pragma unroll
                             for (int r = 0; r < w; ++r) pv[r] += pv[r + w];
                         }
@@ -1131,15 +1129,17 @@ __global__ void __launch_bounds__(1024) k_hermite_plan(Dev d, int ncl) {
     if (tid == 0) d.ctr[C_HNQ] = (unsigned long long)(nsets - min(total, ncl));
 }
 
-// Each cluster first integrates the set the plan gave it (all its CTAs on
-// one set), then every CTA takes sets one at a time from the queue, in the
-// order of a counter, so CTAs freed early take more.
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(HTHREADS, 2) k_hermite(Dev d, HermArgs h) {
+// Each cluster of CLT CTAs first integrates the set the plan gave it (all its
+// CTAs on one set), then every CTA takes sets one at a time from the queue, in
+// the order of a counter, so CTAs freed early take more.
+template <int CLT>
+__global__ void __cluster_dims__(CLT, 1, 1) __launch_bounds__(HTHREADS, 2) k_hermite(Dev d, HermArgs h) {
+    static_assert(CLT == 2 || CLT == 4 || CLT == 8, "a cluster is 2, 4 or 8 CTAs");
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    const int cid = blockIdx.x / CL;
+    const int cid = blockIdx.x / CLT;
     const int cset = cid < kHermMaxClusters ? d.hcl[cid] : -1;
-    if (cset >= 0) hermite_set<true>(d, h, cset, rank, CL);
+    if (cset >= 0) hermite_set<true, CLT>(d, h, cset, rank, CLT);
     const int nq = (int)d.ctr[C_HNQ];
     for (;;) {
         __syncthreads();
@@ -1147,13 +1147,34 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(HTHREADS, 2) k_herm
         __syncthreads();
         const int k = g_next_small;
         if (k >= nq) break;
-        hermite_set<false>(d, h, d.hq[k], 0, 1);
+        hermite_set<false, 2>(d, h, d.hq[k], 0, 1);
     }
 }
 
 cudaError_t hermite_prepare() {
-    return cudaFuncSetAttribute(k_hermite, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kHermSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_hermite<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kHermSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_hermite<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kHermSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_hermite<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kHermSmem);
+    return e;
+}
+
+// Cluster size for a batch (qym_params.hermite_cluster; 0 = automatic). One
+// system holds a few sets, and its longest set gains most from spreading its
+// partners over eight SMs (two CTAs per SM). A batch of many systems keeps
+// thousands of sets in flight that share the SMs' FP64 units; there the
+// longest set does best on a cluster of two CTAs, each alone on its SM
+// (measured on the 512-system ensemble: 20.2 ms per step, against 22.7 ms with
+// eight-CTA clusters at two CTAs per SM; the 16384-body disk: 1.38 ms against
+// 1.48 ms the other way round).
+int hermite_cluster_size(const Dev &d, const qym_params &p) {
+    if (p.hermite_cluster == 2 || p.hermite_cluster == 4 || p.hermite_cluster == 8)
+        return p.hermite_cluster;
+    return d.nsys == 1 ? 8 : 2;
 }
 
 cudaError_t launch_hermite(const Dev &d, const qym_params &p, double tau, cudaStream_t st) {
@@ -1164,15 +1185,21 @@ cudaError_t launch_hermite(const Dev &d, const qym_params &p, double tau, cudaSt
     h.eta_s = p.eta_s;
     h.tau = tau;
     h.max_steps = p.max_hermite_steps;
-    constexpr int kGrid = 2 * 152;
-    static_assert(kGrid / CL <= kHermMaxClusters, "more clusters than plan entries");
-    k_hermite_plan<<<1, 1024, 0, st>>>(d, kGrid / CL);
+    const int cls = hermite_cluster_size(d, p);
+    const int grid = (cls == 2 ? 1 : 2) * 152;  // CTAs per SM x SMs
+    static_assert(2 * 152 / 4 <= kHermMaxClusters && 152 / 2 <= kHermMaxClusters,
+                  "more clusters than plan entries");
+    k_hermite_plan<<<1, 1024, 0, st>>>(d, grid / cls);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the plan has read the previous step's costs; this step's sets write theirs
     e = cudaMemsetAsync(d.hcost, 0, sizeof(int32_t) * (size_t)d.rows, st);
     if (e != cudaSuccess) return e;
-    k_hermite<<<kGrid, HTHREADS, kHermSmem, st>>>(d, h);
+    switch (cls) {
+    case 2: k_hermite<2><<<grid, HTHREADS, kHermSmem, st>>>(d, h); break;
+    case 4: k_hermite<4><<<grid, HTHREADS, kHermSmem, st>>>(d, h); break;
+    default: k_hermite<8><<<grid, HTHREADS, kHermSmem, st>>>(d, h); break;
+    }
     return cudaGetLastError();
 }
 

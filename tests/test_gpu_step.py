@@ -175,14 +175,15 @@ def _planet_swarm(k, seed):
     return W.Workload("swarm", m, q, v, np.array([0, k + 2]), 2 * np.pi / 40, 3)
 
 
-@pytest.mark.parametrize("k", [35, 68])
-def test_cluster_set_parity(gpu, oracle, k):
-    """One large set on a cluster of 8 CTAs, with k + 1 members such that the
-    CTAs' member ranges straddle a power of two (36 -> 4 or 5 per CTA, 69 ->
-    8 or 9): the records match the oracle and every body stays within the
-    chaos-aware tolerance."""
+@pytest.mark.parametrize("k, cluster", [(35, 8), (68, 8), (35, 4), (68, 2)])
+def test_cluster_set_parity(gpu, oracle, k, cluster):
+    """One large set on a cluster of 8, 4 or 2 CTAs, with k + 1 members such
+    that the CTAs' member ranges straddle a power of two (36 over 8 CTAs -> 4
+    or 5 per CTA, 69 -> 8 or 9; 36 over 4 -> 9; 69 over 2 -> 34 or 35): the
+    records match the oracle and every body stays within the chaos-aware
+    tolerance."""
     w = _planet_swarm(k, seed=k)
-    qg, vg, enc, st, E = _run_gpu(w, 3, kick_prec=q.QYM_KICK_FP64)
+    qg, vg, enc, st, E = _run_gpu(w, 3, kick_prec=q.QYM_KICK_FP64, hermite_cluster=cluster)
     r, vh = _run_oracle(oracle, w, 3)
     assert st["status_bits"] == 0 and st["max_set"] == k + 1
     skip = _compare_records(enc, r)
@@ -190,20 +191,23 @@ def test_cluster_set_parity(gpu, oracle, k):
     _check_positions(qg[keep], r.q[keep], _chaos_spread(oracle, w, 3)[keep], rel=1e-11)
 
 
-def test_large_sets_one_cta_each_parity(gpu, oracle):
-    """More large sets than clusters (40 systems, each a planet with a 68-body
-    swarm): every set runs on one CTA, and with 69 members a CTA first rules
-    out far partners in FP32 before the FP64 work. Sampled systems match the
-    oracle stepping each alone."""
-    sw = [_planet_swarm(68, seed=100 + s) for s in range(40)]
+@pytest.mark.parametrize("cluster", [8, 0])
+def test_large_sets_one_cta_each_parity(gpu, oracle, cluster):
+    """More large sets than clusters (120 systems, each a planet with a 68-body
+    swarm): the clusters take as many sets as there are clusters (38 of 8 CTAs,
+    or 76 of 2 with the automatic choice for a batch), every other set runs on
+    one CTA, where with 69 members the CTA first rules out far partners in
+    FP32 before the FP64 work. Sampled systems match the oracle stepping each
+    alone, whichever path their sets took."""
+    sw = [_planet_swarm(68, seed=100 + s) for s in range(120)]
     m = np.concatenate([w.m for w in sw])
     qq = np.concatenate([w.q for w in sw])
     vv = np.concatenate([w.v for w in sw])
     offs = np.concatenate([[0], np.cumsum([len(w.m) for w in sw])])
     w = W.Workload("swarms", m, qq, vv, offs, sw[0].tau, 3)
-    qg, vg, enc, st, E = _run_gpu(w, 3, kick_prec=q.QYM_KICK_FP64)
+    qg, vg, enc, st, E = _run_gpu(w, 3, kick_prec=q.QYM_KICK_FP64, hermite_cluster=cluster)
     assert st["status_bits"] == 0 and st["max_set"] == 69
-    for s in (0, 17, 39):
+    for s in (0, 77, 119):
         a, b = int(offs[s]), int(offs[s + 1])
         r, _ = _run_oracle(oracle, sw[s], 3)
         mine = enc[(enc[:, 1] >= a) & (enc[:, 1] < b)].copy()
