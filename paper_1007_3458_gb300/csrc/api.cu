@@ -169,6 +169,7 @@ static void carve_all(qym_ctx *c, Carver &k) {
     d.rcrit = k.take<double>(d.max_sets);
     d.hcost = k.take<int32_t>(R);
     d.hq = k.take<int32_t>(d.max_sets);
+    d.hsetcost = k.take<int32_t>(d.max_sets);
     d.hcl = k.take<int32_t>(kHermMaxClusters);
     d.uf = k.take<int32_t>(R);
     d.log = k.take<int64_t>(3 * (size_t)d.max_log);

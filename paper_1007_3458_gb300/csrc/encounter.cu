@@ -255,7 +255,9 @@ __global__ void __launch_bounds__(1024) k_uf_number(Dev d, const int32_t *blk, i
 }
 
 // each member finds its root (compressing the path), adds itself to its set
-// size and raises the set's r_crit (a_H times the largest Hill radius)
+// size, raises the set's r_crit (a_H times the largest Hill radius) and the
+// set's predicted Hermite cost (the block steps of the member's set in the
+// previous step)
 __global__ void __launch_bounds__(256) k_uf_members(Dev d, const int32_t *sid, int32_t *size,
                                                     unsigned long long *rc_bits, double a_H) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -269,6 +271,8 @@ __global__ void __launch_bounds__(256) k_uf_members(Dev d, const int32_t *sid, i
     atomicAdd(size + s, 1);
     double rc = a_H * d.rH[r];
     atomicMax(rc_bits + s, (unsigned long long)__double_as_longlong(rc));
+    const int32_t hc = d.hcost[r];
+    if (hc > 0) atomicMax(d.hsetcost + s, hc);
 }
 
 // set_start = exclusive scan of set sizes (one CTA); the fill counters reset

@@ -1038,11 +1038,13 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
 // long as its longest set; which set that is can be foreseen, since a close
 // pair stays close over consecutive steps. A set's predicted cost is the
 // largest count of block steps among its members' sets of the previous step
-// (hcost; 0 for rows that were in no set). Sets of at least NBIG members with
-// the highest predicted cost (then the most members, then the lowest index)
-// take the ncl clusters, one each; the other sets form the per-CTA queue in
-// descending predicted cost, so the longest chains start first. With more
-// than kPlanCap sets the queue keeps the set order and no cluster is used.
+// (hcost; 0 for rows that were in no set), raised per member by the set
+// builder into hsetcost, which the plan reads and clears. Sets of at least
+// NBIG members with the highest predicted cost (then the most members, then
+// the lowest index) take the ncl clusters, one each; the other sets form the
+// per-CTA queue in descending predicted cost, so the longest chains start
+// first. With more than kPlanCap sets the queue keeps the set order and no
+// cluster is used.
 // One CTA of 1024 threads; the sets are ordered by a bitonic sort of 64-bit
 // keys in shared memory.
 constexpr int kPlanCap = 4096;
@@ -1054,7 +1056,10 @@ __global__ void __launch_bounds__(1024) k_hermite_plan(Dev d, int ncl) {
     if (ncl > kHermMaxClusters) ncl = kHermMaxClusters;
     for (int c = tid; c < kHermMaxClusters; c += blockDim.x) d.hcl[c] = -1;
     if (nsets > kPlanCap) {
-        for (int k = tid; k < nsets; k += blockDim.x) d.hq[k] = k;
+        for (int k = tid; k < nsets; k += blockDim.x) {
+            d.hq[k] = k;
+            d.hsetcost[k] = 0;
+        }
         if (tid == 0) d.ctr[C_HNQ] = (unsigned long long)nsets;
         return;
     }
@@ -1064,11 +1069,9 @@ __global__ void __launch_bounds__(1024) k_hermite_plan(Dev d, int ncl) {
     for (int k = tid; k < P; k += blockDim.x) {
         unsigned long long kk = 0;
         if (k < nsets) {
-            const int st = d.set_start[k];
-            const int n = d.set_start[k + 1] - st;
-            int cost = 0;
-            for (int m = 0; m < n && st + m < d.max_members; ++m)
-                cost = max(cost, d.hcost[d.set_mem[st + m]]);
+            const int n = d.set_start[k + 1] - d.set_start[k];
+            const int cost = d.hsetcost[k];
+            d.hsetcost[k] = 0;
             kk = ((unsigned long long)min(max(cost, 0), 0x7fffffff) << 32) |
                  ((unsigned long long)min(max(n, 0), 0xffff) << 16) | (unsigned long long)(0xffff - k);
         }

@@ -59,6 +59,8 @@ struct Dev {
     // last step (0 for rows in no set), the per-CTA queue of sets in order of
     // predicted cost, and the set each thread-block cluster takes (-1: none)
     int32_t *hcost = nullptr;     // [rows]
+    int32_t *hsetcost = nullptr;  // [max_sets] largest hcost over each set's members
+                                  // (raised by the set builder, cleared by the plan)
     int32_t *hq = nullptr;        // [max_sets]
     int32_t *hcl = nullptr;       // [kHermMaxClusters]
     int32_t *uf = nullptr;        // [rows] union-find parents, kept at -1 when idle
