@@ -1,6 +1,6 @@
 // hermite.cu -- the close-encounter branch of the hybrid step (Sec. 2.2 and
 // Sec. 2.3 items 5-8), one CTA per encounter set, or a thread-block cluster
-// per set when a few large sets would otherwise run alone:
+// (2, 4 or 8 CTAs) for each of the large sets predicted to take longest:
 //   1. remove the (1-K) part of the first kick at q0 (item 5),
 //   2. integrate the set for tau with a 4th-order Hermite predictor /
 //      evaluate / corrector (Makino & Aarseth, no Ahmad-Cohen) under H'_Kep:
