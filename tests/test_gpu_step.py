@@ -363,3 +363,32 @@ def test_merged_kicks_hybrid_step(gpu, oracle):
     skip = _compare_records(enc, r)
     keep = np.array([i not in skip for i in range(len(w.m))])
     _check_positions(qg[keep], r.q[keep], _chaos_spread(oracle, w, 100)[keep])
+
+
+@pytest.mark.parametrize("case", ["batch", "swarm"])
+def test_repeat_runs_bit_identical(gpu, case):
+    """The same calls on two fresh contexts give the same bits: every sum has
+    a fixed order, and the Hermite's schedule (which large sets take
+    clusters, the queue order) follows only the context's own past. A batch
+    of 80 planet swarms (more large sets than the 76 two-CTA clusters, so the
+    plan and the queue both matter) and one swarm on an eight-CTA cluster."""
+    if case == "batch":
+        sw = [_planet_swarm(30, seed=300 + s) for s in range(80)]
+        w = W.Workload("swarms", np.concatenate([x.m for x in sw]),
+                       np.concatenate([x.q for x in sw]), np.concatenate([x.v for x in sw]),
+                       np.concatenate([[0], np.cumsum([len(x.m) for x in sw])]), sw[0].tau, 4)
+    else:
+        w = _planet_swarm(68, seed=7)
+    runs = []
+    for _ in range(2):
+        sim = q.Simulation(w.m, w.q, w.v, w.offsets)
+        sim.step(w.tau, 2)
+        sim.step(w.tau, 2)
+        qq, vv = sim.state()
+        runs.append((qq, vv, sim.encounters(), sim.stats()))
+        sim.close()
+    (q0, v0, e0, s0), (q1, v1, e1, s1) = runs
+    assert s0["status_bits"] == 0 and s0["max_set"] >= 24
+    assert np.array_equal(q0, q1) and np.array_equal(v0, v1)
+    assert np.array_equal(e0, e1)
+    assert s0["hermite_steps"] == s1["hermite_steps"] and s0["sets"] == s1["sets"]
