@@ -37,6 +37,16 @@ def test_header_struct_layout_matches_binding():
     # qym_params: 7 doubles, 8 int32, 5 int64 = 56 + 32 + 40 bytes
     assert ctypes.sizeof(q.qym_params) == 136
     assert ctypes.sizeof(q.qym_stats) == 10 * 8 + 4 * 3 + 4
+    # the same fields in the same order and of the same types as the header
+    txt = open(os.path.join(ROOT, "include", "qym.h")).read()
+    ctype = {"double": ctypes.c_double, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64}
+    for struct, binding in (("qym_params", q.qym_params), ("qym_stats", q.qym_stats)):
+        body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (struct, struct), txt, re.S).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        fields = []
+        for t, names in re.findall(r"\b(double|int32_t|int64_t)\s+([^;]+);", body):
+            fields += [(n.strip(), ctype[t]) for n in names.split(",")]
+        assert fields == list(binding._fields_), struct
 
 
 def test_defaults(lib):
@@ -51,6 +61,10 @@ def test_argument_checks_without_gpu(lib):
         q.qym_init(p, [0, 1], [1.0], np.zeros((1, 3)), np.zeros((1, 3)))
     assert e.value.status == q.QYM_EINVAL  # a system without bodies
     p.eta = -1
+    with pytest.raises(q.QymError) as e:
+        q.qym_init(p, [0, 2], [1.0, 1e-3], np.zeros((2, 3)), np.zeros((2, 3)))
+    assert e.value.status == q.QYM_EINVAL
+    p = q.qym_default_params(hermite_cluster=3)  # clusters are 2, 4 or 8 CTAs (0: automatic)
     with pytest.raises(q.QymError) as e:
         q.qym_init(p, [0, 2], [1.0, 1e-3], np.zeros((2, 3)), np.zeros((2, 3)))
     assert e.value.status == q.QYM_EINVAL
