@@ -148,9 +148,10 @@ class ClockSampler:
 # capture of each workload's kick after autotuning (dram__bytes_read.sum +
 # dram__bytes_write.sum, the mean of the searching and the plain kick, three
 # launches each); keyed by (workload, rows per CTA, j-splits), since the
-# partial-sum slots written grow with the splits. The captures are summarised
-# in profiles/k_kick_mixed_<workload>.md; a shape not captured reports null,
-# and so does any kick kernel changed since.
+# partial-sum slots written grow with the splits; a shape not captured
+# reports null. The figures hold for the kick kernels as captured (the
+# capture commands sit with the ncu summaries under profiles/) and are to be
+# taken again whenever those kernels change.
 KICK_DRAM_BYTES = {
     ("disk_16384", 256, 64): 6.244e5,
     ("disk_262144", 256, 64): 3.623e8,
