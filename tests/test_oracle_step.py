@@ -177,3 +177,90 @@ def test_hybrid_step_all_hermite_limit(oracle):
                     oracle.params(eta=0.005, eta_s=0.0025, a_E=100.0, a_H=400.0))
     assert r.status == 0 and len(r.encounters) == 400
     assert abs(oracle.energy(m, r.q, r.v) - E0) / abs(E0) < 1e-6
+
+
+def _nbody_reference(G, m, q_h, v_h, T):
+    """The Newtonian N-body problem integrated in the barycentric frame by an
+    independent high-order solver (DOP853), returned as heliocentric
+    positions at time T."""
+    from scipy.integrate import solve_ivp
+    M = m.sum()
+    X0 = -(m[1:, None] * q_h[1:]).sum(0) / M
+    V0 = -(m[1:, None] * v_h[1:]).sum(0) / M
+    X = q_h + X0
+    X[0] = X0
+    V = v_h + V0
+    V[0] = V0
+    n = len(m)
+
+    def rhs(t, y):
+        x = y[:3 * n].reshape(n, 3)
+        d = x[:, None, :] - x[None, :, :]
+        r3 = np.linalg.norm(d, axis=2) ** 3
+        np.fill_diagonal(r3, np.inf)
+        a = -G * np.sum(m[None, :, None] * d / r3[:, :, None], axis=1)
+        return np.concatenate([y[3 * n:], a.ravel()])
+
+    sol = solve_ivp(rhs, (0.0, T), np.concatenate([X.ravel(), V.ravel()]), method="DOP853",
+                    rtol=1e-13, atol=1e-15)
+    x = sol.y[:3 * n, -1].reshape(n, 3)
+    return x - x[0]
+
+
+def test_step_converges_to_newtonian_nbody_in_general_units(oracle):
+    """With G = 0.7 and a star of mass 2.5 (units in which neither is 1, so
+    that every G and every division by m0 of Sec. 2 counts: the drift moves Q
+    by tau S / m0, the Kepler term uses G m0, the kick G m_j), a star and two
+    eccentric, inclined planets stepped for two inner orbits converge to the
+    Newtonian N-body solution at second order: halving tau divides the
+    position error by four."""
+    G, m0 = 0.7, 2.5
+    m = np.array([m0, 4e-3, 2e-3])
+    mu = G * (m0 + m[1:])
+    qh, vh = W.elements_to_cartesian(mu, np.array([1.0, 1.9]), np.array([0.1, 0.06]),
+                                     np.array([0.05, 0.12]), np.array([0.3, 2.0]),
+                                     np.array([1.0, 4.0]), np.array([0.5, 2.5]))
+    qh = np.concatenate([[[0.0, 0.0, 0.0]], qh])
+    vh = np.concatenate([[[0.0, 0.0, 0.0]], vh])
+    P = 2 * math.pi * math.sqrt(1.0 / (G * m0))
+    T = 2 * P
+    qref = _nbody_reference(G, m, qh, vh, T)
+    v = oracle.helio_to_dh(m, vh)
+    prm = oracle.params(G=G, encounters=0)
+    errs = []
+    for n in (100, 200):
+        r = oracle.step(m, qh, v, [0, 3], T / n, n, prm)
+        errs.append(np.linalg.norm(r.q[1:] - qref[1:], axis=1).max())
+    ratio = errs[0] / errs[1]
+    assert 3.5 < ratio < 4.5, (errs, ratio)
+    assert errs[1] < 1e-4, errs
+
+
+def test_encounter_threshold_uses_hill_radii_entering_kepler(oracle):
+    """Reading R6: the threshold a_E (r_H,i + r_H,j) of a step's rigorous test
+    takes the Hill radii at the bodies' distances in the state that enters
+    that step's Kepler drift (after the opening half drift; the kick moves no
+    position). The thresholds the step reports for the passage of two
+    eccentric planets equal those recomputed from that state, and differ
+    from the ones the state after the drift would give."""
+    m, q, vh = _crossing_planets()
+    v = oracle.helio_to_dh(m, vh)
+    tau = 0.00255 * 2 * math.pi
+    prm = oracle.params(a_E=2.5, a_H=1.0)
+    r = oracle.step(m, q, v, [0, 3], tau, 2000, prm)
+    assert len(r.encounters) > 0
+    apart = 0.0
+    for k in (0, len(r.encounters) // 2, len(r.encounters) - 1):
+        s = int(r.encounters[k, 0])
+        rs = oracle.step(m, q, v, [0, 3], tau, s, prm)
+        q_in = oracle.drift(m, rs.q, rs.v, 0.5 * tau)
+        rH = oracle.hill_radii(m, q_in, rs.v)
+        thr2 = (2.5 * (rH[1] + rH[2])) ** 2
+        assert abs(r.enc_d2[k, 1] / thr2 - 1) < 1e-13, (k, r.enc_d2[k, 1], thr2)
+        # the same from the state the Kepler drift produces
+        vk = oracle.kick(m, q_in, rs.v, 0.5 * tau)
+        q1, v1, _, _, bad = oracle.kepler_drift(q_in[1:], vk[1:], m[0], tau)
+        assert bad == 0
+        rH1 = oracle.hill_radii(m, np.concatenate([[[0.0, 0.0, 0.0]], q1]), rs.v)
+        apart = max(apart, abs((2.5 * (rH1[1] + rH1[2])) ** 2 / thr2 - 1))
+    assert apart > 1e-6  # the two readings are told apart here
