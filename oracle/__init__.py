@@ -387,3 +387,16 @@ def step(m, q, v, offsets, tau, nsteps, prm: Params | None = None, step0=0,
                       np.concatenate(d2s) if d2s else np.zeros((0, 2)),
                       np.concatenate(nears) if nears else np.zeros((0, 3), np.int64),
                       np.concatenate(nd2s) if nd2s else np.zeros((0, 2)), stats, status)
+
+
+# an edited copy of mlp.py standing in for this package's (the tests that
+# plant mistakes in the oracle load one in a child process); unset: mlp.py
+_MLP_OVERRIDE = os.environ.get("QYM_ORACLE_MLP")
+if _MLP_OVERRIDE:
+    import importlib.util as _ilu
+    import sys as _sys
+
+    _spec = _ilu.spec_from_file_location(__name__ + ".mlp", _MLP_OVERRIDE)
+    mlp = _ilu.module_from_spec(_spec)
+    _sys.modules[__name__ + ".mlp"] = mlp
+    _spec.loader.exec_module(mlp)
