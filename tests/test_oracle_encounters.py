@@ -149,12 +149,13 @@ def test_transition_function_values_and_derivatives(oracle):
         assert abs(Kpn - Kpp) <= 1e-5 * (abs(Kpp) + 1)
 
 
-def _U_K(m, q, rc, weight):
-    """Pair potential of the set with weight(K) (Eqs. 6-7), via oracle.transition."""
+def _U_K(m, q, rc, weight, eps=0.0):
+    """Pair potential of the set with weight(K) (Eqs. 6-7), via oracle.transition;
+    with eps > 0 every pair distance is the softened sqrt(d^2 + eps^2)."""
     U = 0.0
     for i in range(len(m)):
         for j in range(i + 1, len(m)):
-            d = np.linalg.norm(q[i] - q[j])
+            d = math.sqrt(float(np.sum((q[i] - q[j]) ** 2)) + eps * eps)
             U -= m[i] * m[j] * weight(d) / d
     return U
 
@@ -184,10 +185,12 @@ def test_kcorr_turns_full_kick_into_K_weighted_kick(oracle):
 
 
 # ------------------------------------------------------------ Hermite
-def _phi_set(mm, x, rc, m0=1.0):
-    """H'_Kep potential of a set: star term + (1-K)-weighted pairs (Eq. 6)."""
-    U = -np.sum(m0 * mm / np.linalg.norm(x, axis=1))
-    return U + _U_K(mm, x, rc, lambda d: 1.0 - oracle_transition(d, rc))
+def _phi_set(mm, x, rc, m0=1.0, eps=0.0):
+    """H'_Kep potential of a set: star term + (1-K)-weighted pairs (Eq. 6),
+    every distance softened to sqrt(d^2 + eps^2) when eps > 0 (the Hermite
+    smoothing of Sec. 2.4, reading R16)."""
+    U = -np.sum(m0 * mm / np.sqrt(np.sum(x * x, 1) + eps * eps))
+    return U + _U_K(mm, x, rc, lambda d: 1.0 - oracle_transition(d, rc), eps)
 
 
 def oracle_transition(d, rc):
@@ -195,28 +198,31 @@ def oracle_transition(d, rc):
     return O.transition(d, rc)[0]
 
 
-def test_hermite_force_and_jerk(oracle):
+@pytest.mark.parametrize("eps", [0.0, 0.01])
+def test_hermite_force_and_jerk(oracle, eps):
     """Hermite acceleration = -grad(Phi')/m (Sec. 2.2 with Eq. 6) by central
-    differences; jerk = d a / dt along the velocities, by central differences
-    of the acceleration at x +- h u."""
+    differences, with the smoothing eps either 0 or comparable to the pair
+    separations (the potential then softened the same way); jerk = d a / dt
+    along the velocities, by central differences of the acceleration at
+    x +- h u."""
     rng = np.random.default_rng(5)
     k = 5
     mm = np.array([3e-4, 1e-4, 2e-5, 1e-5, 0.0])
     x = np.array([1.0, 0.2, 0.0]) + rng.normal(0, 0.02, (k, 3))
     u = np.array([-0.2, 1.0, 0.0]) + rng.normal(0, 0.05, (k, 3))
     rc = 0.04
-    a, j = oracle.hermite_force(mm, x, u, rc)
+    a, j = oracle.hermite_force(mm, x, u, rc, eps=eps)
     h = 1e-7
     for i in range(k - 1):
         for c in range(3):
             xp, xm = x.copy(), x.copy()
             xp[i, c] += h
             xm[i, c] -= h
-            g = (_phi_set(mm, xp, rc) - _phi_set(mm, xm, rc)) / (2 * h)
+            g = (_phi_set(mm, xp, rc, eps=eps) - _phi_set(mm, xm, rc, eps=eps)) / (2 * h)
             assert abs(-g / mm[i] - a[i, c]) <= 1e-6 * np.abs(a[i]).max()
     hh = 1e-6
-    ap, _ = oracle.hermite_force(mm, x + hh * u, u, rc)
-    am, _ = oracle.hermite_force(mm, x - hh * u, u, rc)
+    ap, _ = oracle.hermite_force(mm, x + hh * u, u, rc, eps=eps)
+    am, _ = oracle.hermite_force(mm, x - hh * u, u, rc, eps=eps)
     jn = (ap - am) / (2 * hh)
     assert np.all(np.abs(jn - j) <= 1e-5 * (np.abs(j).max(1, keepdims=True) + 1e-12))
 

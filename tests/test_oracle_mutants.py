@@ -127,6 +127,66 @@ MUTANTS = [
     ('step_hill_from_end_state', 'step',
      'or_hill_radii(rows, m, q0, v0, G, rH);',
      'or_hill_radii(rows, m, q, v, G, rH);'),
+    ('uf_root_not_smallest', 'encounters',
+     'if (a < b) parent[b] = a; else parent[a] = b;   /* root = smallest index */',
+     'parent[a] = b;'),
+    ('sets_member_order', 'encounters',
+     'members[set_start[s] + fill[s]++] = i;',
+     'members[set_start[s + 1] - 1 - fill[s]++] = i;'),
+    ('rcrit_min_not_max', 'encounters',
+     'if (rH[members[k]] > mx) mx = rH[members[k]];',
+     'if (mx == 0.0 || rH[members[k]] < mx) mx = rH[members[k]];'),
+    ('laguerre_sign_minus', 'kepler',
+     'dx = n * rf / (1.0 + sq);',
+     'dx = n * rf / (1.0 - sq);'),
+    ('residual_tolerance_loose', 'kepler',
+     'if (fabs(F) <= 1e-14 * scale) {',
+     'if (fabs(F) <= 1e-8 * scale) {'),
+    ('bracket_not_widened', 'kepler',
+     'double xb = sqmu * dt / rp * (1.0 + 1e-12);',
+     'double xb = sqmu * dt / rp * (1.0 - 1e-9);'),
+    ('standard_guess_r0_squared', 'kepler',
+     'x = sqmu * dt / r0;\n    else if (guess == 1)',
+     'x = sqmu * dt / (r0 * r0);\n    else if (guess == 1)'),
+    ('kick_double_dt', 'encounters',
+     'for (int k = 0; k < 3; ++k) v[3 * i + k] += dt * a[3 * i + k];',
+     'for (int k = 0; k < 3; ++k) v[3 * i + k] += 2.0 * dt * a[3 * i + k];'),
+    ('first_drift_full_tau', 'step',
+     '/* item 1: drift tau/2 */\n        or_drift(rows, m, q, v, 0.5 * tau);',
+     '/* item 1: drift tau/2 */\n        or_drift(rows, m, q, v, tau);'),
+    ('kcorr_q1_uses_q0', 'step',
+     '/* item 7: pre-remove the (1-K) part of the coming kick at q1 */\n                    or_kcorr(k, members + k0, m, q, v, G, rcrit[st], 0.5 * tau);',
+     '/* item 7: pre-remove the (1-K) part of the coming kick at q1 */\n                    or_kcorr(k, members + k0, m, q0, v, G, rcrit[st], 0.5 * tau);'),
+    ('kcorr_sign', 'encounters',
+     'for (int k = 0; k < 3; ++k) v[3 * mem[a] + k] -= dt * dv[3 * a + k];',
+     'for (int k = 0; k < 3; ++k) v[3 * mem[a] + k] += dt * dv[3 * a + k];'),
+    ('hermite_smoothing_dropped', 'encounters',
+     'double s2 = dot3(d, d) + eps * eps;',
+     'double s2 = dot3(d, d);'),
+    ('hermite_star_mass_body', 'encounters',
+     'double w = -G * m0 / (s2 * s);',
+     'double w = -G * (m0 + mm[i]) / (s2 * s);'),
+    ('hermite_startup_eta', 'encounters',
+     'double dt_c = jn > 0.0 ? eta_s * norm3(a0 + 3 * i) / jn : T;',
+     'double dt_c = jn > 0.0 ? norm3(a0 + 3 * i) / jn : T;'),
+    ('hermite_level_up_any_time', 'encounters',
+     'kn = (tn % ((int64_t)1 << (OR_KMAX - up1)) == 0) ? up1 : lev[i];',
+     'kn = up1;'),
+    ('hermite_a2_j_weights', 'encounters',
+     'a2[c] = (-6.0 * (a0[id] - a1[id]) - h * (4.0 * j0[id] + 2.0 * j1[id])) / (h * h);',
+     'a2[c] = (-6.0 * (a0[id] - a1[id]) - h * (2.0 * j0[id] + 4.0 * j1[id])) / (h * h);'),
+    ('energy_kinetic_no_half', 'forces',
+     'E += 0.5 * m[i] * dot3(v + 3 * i, v + 3 * i);',
+     'E += m[i] * dot3(v + 3 * i, v + 3 * i);'),
+    ('energy_star_term_sign', 'forces',
+     'E -= G * m[0] * m[i] / sqrt(dot3(q + 3 * i, q + 3 * i));',
+     'E += G * m[0] * m[i] / sqrt(dot3(q + 3 * i, q + 3 * i));'),
+    ('dmin_skips_interior_roots', 'encounters',
+     'if (u[k] > 0.0 && u[k] < 1.0) {',
+     'if (u[k] > 0.0 && u[k] < 0.5) {'),
+    ('encounters_strict_upper_only_ij', 'step',
+     'for (int64_t j = i + 1; j < rows; ++j) {\n            double dq0[3], dv0[3], dq1[3], dv1[3];\n            pair_diffs(q0, v0, q1, v1, i, j, dq0, dv0, dq1, dv1);\n            double R = a_E * (rH[i] + rH[j]);',
+     'for (int64_t j = i + 2; j < rows; ++j) {\n            double dq0[3], dv0[3], dq1[3], dv1[3];\n            pair_diffs(q0, v0, q1, v1, i, j, dq0, dv0, dq1, dv1);\n            double R = a_E * (rH[i] + rH[j]);'),
 ]
 
 
