@@ -265,3 +265,32 @@ def test_unbound_orbits_converge_and_match_ode(oracle):
         for k in rng.choice(n, 8, replace=False):
             qr, vr = _two_body_ode(q0[k], v0[k], 1.0, dt)
             assert np.linalg.norm(q1[k] - qr) <= 1e-8 * max(np.linalg.norm(qr), 1.0), (dt, k)
+
+
+def test_kepler_residual_closed_forms(oracle):
+    """The residual |F(x)| / (sum of the magnitudes of F's terms) that judges
+    every root (Appendix, reading R13): 1 exactly at x = 0 for any orbit (F(0)
+    = -sqrt(mu) dt is its only term); on a circular orbit F(x) = -sqrt(mu) dt
+    + r0 x, so it is 0 at the root sqrt(mu) dt / r0 and 1/3 at twice the root;
+    on eccentric orbits the converged roots meet 1e-14 and a root moved by
+    1e-9 of itself does not."""
+    mu, dt = 1.3, 0.7
+    r0 = 2.0
+    vc = math.sqrt(mu / r0)
+    qc = np.array([[r0, 0.0, 0.0], [0.0, 0.0, r0]])
+    vcv = np.array([[0.0, vc, 0.0], [vc, 0.0, 0.0]])
+    xs = math.sqrt(mu) * dt / r0
+    res = oracle.kepler_residuals(qc, vcv, mu, dt, np.array([xs, xs]))
+    assert np.all(res <= 4e-16)
+    assert np.all(oracle.kepler_residuals(qc, vcv, mu, dt, np.zeros(2)) == 1.0)
+    assert np.allclose(oracle.kepler_residuals(qc, vcv, mu, dt, np.array([2 * xs, 2 * xs])),
+                       1.0 / 3.0, rtol=1e-14, atol=0)
+    rng = np.random.default_rng(4)
+    q, v = W.elements_to_cartesian(mu, rng.uniform(0.5, 5, 40), rng.uniform(0, 0.9, 40),
+                                   rng.uniform(0, 3, 40), rng.uniform(0, 6, 40),
+                                   rng.uniform(0, 6, 40), rng.uniform(0, 6, 40))
+    _, _, x, _, bad = oracle.kepler_drift(q, v, mu, dt)
+    assert bad == 0
+    assert oracle.kepler_residuals(q, v, mu, dt, x).max() <= 1e-14
+    assert oracle.kepler_residuals(q, v, mu, dt, x * (1 + 1e-9)).min() > 1e-12
+    assert np.all(oracle.kepler_residuals(q, v, mu, dt, np.zeros(len(x))) == 1.0)
