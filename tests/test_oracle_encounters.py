@@ -93,7 +93,10 @@ def test_encounter_list_brute_force_small_n(oracle, seed):
     assert all(i < j for i, j in pairs)
     assert [tuple(p) for p in pairs] == sorted(flagged)
     # the selected-rows variant finds the same pairs for those rows
-    sel = np.unique(pairs[:, 0])[:3] if len(pairs) else np.array([1])
+    # rows taken as the lower and as the upper index of a pair, so that
+    # partners on both sides of a selected row count
+    sel = np.unique(np.concatenate([pairs[:2, 0], pairs[-2:, 1]])) if len(pairs) else np.array([1])
+    assert len(pairs) == 0 or any(p[1] in sel and p[0] not in sel for p in pairs)
     pr, _, _ = oracle.encounters_rows(q0, v0, q1, v1, rH, tau, a_E, sel)
     want = {tuple(p) for p in pairs if p[0] in sel or p[1] in sel}
     assert {tuple(p) for p in pr} == want

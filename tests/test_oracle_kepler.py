@@ -294,3 +294,33 @@ def test_kepler_residual_closed_forms(oracle):
     assert oracle.kepler_residuals(q, v, mu, dt, x).max() <= 1e-14
     assert oracle.kepler_residuals(q, v, mu, dt, x * (1 + 1e-9)).min() > 1e-12
     assert np.all(oracle.kepler_residuals(q, v, mu, dt, np.zeros(len(x))) == 1.0)
+
+
+def test_learned_guess_falls_back_to_laguerre_from_standard_guess(oracle):
+    """Guess mode 2 (a guess given per body, as the learned network's): when
+    the solve from the given guess does not converge within the iteration
+    cap, Laguerre from the standard guess sqrt(mu) dt / r0 runs with the same
+    cap. Guesses 40x the root with Newton and a cap one above what Laguerre
+    from the standard guess needs: the result is that Laguerre solve's, bit
+    for bit, and the iterations of both attempts are reported."""
+    rng = np.random.default_rng(11)
+    n = 200
+    q, v = W.elements_to_cartesian(1.0, rng.uniform(0.5, 5, n), rng.uniform(0.3, 0.95, n),
+                                   rng.uniform(0, 3, n), rng.uniform(0, 6, n),
+                                   rng.uniform(0, 6, n), rng.uniform(0, 6, n))
+    dt = 2.0
+    q1s, v1s, xs, itL, bad = oracle.kepler_drift(q, v, 1.0, dt, solver=0, guess=0)
+    assert bad == 0
+    xg = 40.0 * xs
+    _, _, _, itN, bad = oracle.kepler_drift(q, v, 1.0, dt, solver=1, guess=2, x_guess=xg)
+    assert bad == 0
+    sel = np.nonzero(itN > itL + 1)[0]
+    assert len(sel) > 50
+    for cap in np.unique(itL[sel] + 1):
+        idx = sel[itL[sel] + 1 == cap]
+        q1, v1, x, it, bad = oracle.kepler_drift(q[idx], v[idx], 1.0, dt, solver=1, guess=2,
+                                                 x_guess=xg[idx], max_iter=int(cap))
+        assert bad == 0
+        assert np.array_equal(x, xs[idx])
+        assert np.array_equal(q1, q1s[idx]) and np.array_equal(v1, v1s[idx])
+        assert np.all(it == cap + itL[idx])

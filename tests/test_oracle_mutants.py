@@ -193,6 +193,51 @@ MUTANTS = [
     ('residual_scale_offset', 'kepler',
      'double scale = fabs(sqmu * dt) + fabs(sig * xx * xx * C) +',
      'double scale = 1.0 + fabs(sqmu * dt) + fabs(sig * xx * xx * C) +'),
+    ('accel_rows_wrong_row', 'forces',
+     'for (int64_t k = 0; k < nsel; ++k) or_accel_row(rows, m, q, G, sel[k], a + 3 * k);',
+     'for (int64_t k = 0; k < nsel; ++k) or_accel_row(rows, m, q, G, sel[0], a + 3 * k);'),
+    ('accel_row_includes_star', 'forces',
+     'for (int64_t j = 1; j < rows; ++j) {\n        if (j == i) continue;',
+     'for (int64_t j = 0; j < rows; ++j) {\n        if (j == i) continue;'),
+    ('encounters_rows_unordered', 'encounters',
+     'int64_t a = i < j ? i : j, b = i < j ? j : i;',
+     'int64_t a = i, b = j;'),
+    ('encounters_rows_skips_lower', 'encounters',
+     'for (int64_t j = 1; j < rows; ++j) {\n            if (j == i) continue;\n            double dq0[3]',
+     'for (int64_t j = i + 1; j < rows; ++j) {\n            if (j == i) continue;\n            double dq0[3]'),
+    ('guess_mode_ignores_given_x', 'kepler',
+     '    else\n        x = x_guess;',
+     '    else\n        x = sqmu * dt / r0;'),
+    ('fallback_newton_not_laguerre', 'kepler',
+     'st = or_kepler_solve_br(sqmu, dt, r0, sig, alpha, 0, max_iter, lo, hi, &x, &it2);',
+     'st = or_kepler_solve_br(sqmu, dt, r0, sig, alpha, solver, 2, lo, hi, &x, &it2);'),
+    ('iters_not_reported', 'kepler',
+     'if (iters_out) iters_out[i] = it;',
+     'if (iters_out) iters_out[i] = 0;'),
+    ('hermite_ticks_off_by_one', 'encounters',
+     'const int64_t TT = (int64_t)1 << OR_KMAX;      /* tau in ticks */',
+     'const int64_t TT = ((int64_t)1 << OR_KMAX) - 1;      /* tau in ticks */'),
+    ('hermite_backward_sign_ignored', 'encounters',
+     'const double T = fabs(tau), sg = tau >= 0.0 ? 1.0 : -1.0;',
+     'const double T = fabs(tau), sg = 1.0;'),
+    ('hermite_steps_not_counted', 'encounters',
+     '        ++steps;\n    }\n    for (int64_t i = 0; i < k; ++i)',
+     '    }\n    for (int64_t i = 0; i < k; ++i)'),
+    ('hermite_corrects_everyone', 'encounters',
+     'if (ti[i] + dti != tn) continue;',
+     'if (ti[i] + dti < tn) continue;'),
+    ('step_stats_encounters_not_counted', 'step',
+     'stats[0] += npairs;',
+     'stats[0] += 0;'),
+    ('step_records_step_index', 'step',
+     'enc[3 * ne_total] = step0 + s;',
+     'enc[3 * ne_total] = s;'),
+    ('kepler_energy_mu_with_body', 'kepler',
+     'double alpha = 2.0 / r0 - v2 / mu;',
+     'double alpha = 2.0 / r0 - v2 / (mu * 1.000001);'),
+    ('sets_rcrit_from_first_member', 'encounters',
+     'for (int64_t k = set_start[s]; k < set_start[s + 1]; ++k)\n            if (rH[members[k]] > mx) mx = rH[members[k]];',
+     'mx = rH[members[set_start[s]]];'),
 ]
 
 

@@ -147,6 +147,7 @@ def test_hybrid_step_handles_close_encounters(oracle):
     assert r.status == 0
     assert len(r.encounters) > 0 and r.stats[4] > 0
     assert set(map(tuple, r.encounters[:, 1:])) == {(1, 2)}
+    assert r.stats[0] == len(r.encounters)
     assert np.all(np.diff(r.encounters[:, 0]) >= 0) and r.encounters[:, 0].max() < steps
     dE = abs(oracle.energy(m, r.q, r.v) - E0) / abs(E0)
     assert dE < 3e-5
@@ -264,3 +265,21 @@ def test_encounter_threshold_uses_hill_radii_entering_kepler(oracle):
         rH1 = oracle.hill_radii(m, np.concatenate([[[0.0, 0.0, 0.0]], q1]), rs.v)
         apart = max(apart, abs((2.5 * (rH1[1] + rH1[2])) ** 2 / thr2 - 1))
     assert apart > 1e-6  # the two readings are told apart here
+
+
+def test_split_run_continues_exactly(oracle):
+    """A run of 1500 steps through the planets' passage (records in steps
+    1139-1421) and the same run in two calls split at step 1300, the second
+    numbering its steps from 1300 (step0): the oracle completes every step
+    inside a call, so the states agree to the bit and the encounter records
+    (step, i, j) are the same list."""
+    m, q, vh = _crossing_planets()
+    v = oracle.helio_to_dh(m, vh)
+    tau = 0.00255 * 2 * math.pi
+    prm = oracle.params(a_E=2.5, a_H=1.0)
+    whole = oracle.step(m, q, v, [0, 3], tau, 1500, prm)
+    a = oracle.step(m, q, v, [0, 3], tau, 1300, prm)
+    b = oracle.step(m, a.q, a.v, [0, 3], tau, 200, prm, step0=1300)
+    assert len(whole.encounters) > 0 and len(a.encounters) > 0 and len(b.encounters) > 0
+    assert np.array_equal(whole.q, b.q) and np.array_equal(whole.v, b.v)
+    assert np.array_equal(whole.encounters, np.concatenate([a.encounters, b.encounters]))
