@@ -147,31 +147,60 @@ class ClockSampler:
 # DRAM bytes (read + written) per launch of the mixed kick, from one ncu
 # capture of each workload's kick after autotuning (dram__bytes_read.sum +
 # dram__bytes_write.sum, the mean of the searching and the plain kick, three
-# launches each); keyed by (workload, rows per CTA, j-splits), since the
-# partial-sum slots written grow with the splits; a shape not captured
-# reports null. The figures hold for the kick kernels as captured (the
-# capture commands sit with the ncu summaries under profiles/) and are to be
-# taken again whenever those kernels change.
+# launches each); keyed by (workload, rows per CTA, j-splits, digest of the
+# kick's source at the capture), since the partial-sum slots written grow
+# with the splits. A shape or a kick source not captured reports null (the
+# capture commands sit with the ncu summaries under profiles/).
 KICK_DRAM_BYTES = {
-    ("disk_16384", 256, 64): 6.244e5,
-    ("disk_262144", 256, 64): 3.623e8,
-    ("ensemble_512", 256, 4): 7.707e7,
 }
 
 
-def fp32_peak_tflops(sm_mhz):
-    """FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def probe_peaks(q, dev, reps=5):
+    """Measured FMA throughput of this GPU (qym_probe_fma: long chains of
+    independent FFMA, packed FFMA2 and DFMA on every SM, CUDA events): the
+    best of `reps` launches of each after one untimed launch, with the SM
+    clock sampled meanwhile. The FP32 pipe peak is the larger of the scalar
+    and the packed figure."""
+    out = {}
+    with ClockSampler(dev) as clk:
+        for name, kind, iters in (("ffma", 0, 1 << 17), ("ffma2", 1, 1 << 16),
+                                  ("dfma", 2, 1 << 12)):
+            q.qym_probe_fma(kind, iters)
+            best = max(q.qym_probe_fma(kind, iters)[0] for _ in range(reps))
+            out[name] = best
+    out["fp32"] = max(out["ffma"], out["ffma2"])
+    out["clocks"] = clk.summary()
+    out["how"] = ("qym_probe_fma: 4 x SMs CTAs of 256 threads, 8 independent FMA chains per "
+                  "thread, best of %d launches (CUDA events)" % reps)
+    return out
 
 
-def oracle_sample(w):
-    """The oracle as it stands (single thread) on a bounded sample of the
-    workload: returns (one_step, bodies, scale, description). one_step()
-    advances the sample by one whole step; a step of the full workload costs
-    `scale` times that. A batch is sampled by whole systems (its first 8, stepped
-    one after another); beyond 8192 bodies a single disk is sampled by a random
-    subset of the same disk (one oracle step costs ~N^2 pair evaluations: two
-    kicks and the all-pairs encounter test), its time scaled by (N/n)^2."""
+def source_digest(*names):
+    """sha256 (first 16 hex digits) of kernel sources, so that a DRAM traffic
+    figure captured for one version of a kernel is not reported for another."""
+    import hashlib
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1007_3458_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(w, n_max=8192):
+    """The oracle on a bounded sample of the workload: returns (one_step,
+    bodies, scale, description, sample_bodies). one_step() advances the sample
+    by one whole step; a step of the full workload costs `scale` times that. A
+    batch is sampled by whole systems (its first 8, stepped one after
+    another); beyond n_max bodies a single disk is sampled by a random subset
+    of the same disk (one oracle step costs ~N^2 pair evaluations: two kicks
+    and the all-pairs encounter test), its time scaled by (N/n)^2."""
     import oracle as O
     O.build()
     from paper_1007_3458_gb300 import workloads as W
@@ -188,9 +217,9 @@ def oracle_sample(w):
                 r = O.step(w.m[a:b], qq, vv, [0, b - a], w.tau, 1, prm)
                 st[a] = (r.q, r.v)
         nb = sum(b - a - 1 for a, b in rows)
-        return one_step, nb, 1.0, f"the first {len(rows)} systems ({nb} bodies)"
+        return one_step, nb, 1.0, f"the first {len(rows)} systems ({nb} bodies)", nb
     n_full = w.n_bodies
-    n_s = min(n_full, 8192)
+    n_s = min(n_full, n_max)
     ws = w if n_s == n_full else W.subsample(w, n_s, seed=0)
     st = [ws.q.copy(), O.helio_to_dh(ws.m, ws.v)]
 
@@ -198,24 +227,33 @@ def oracle_sample(w):
         r = O.step(ws.m, st[0], st[1], ws.offsets, w.tau, 1, prm)
         st[0], st[1] = r.q, r.v
     if n_s == n_full:
-        return one_step, n_full, 1.0, "the whole workload"
+        return one_step, n_full, 1.0, "the whole workload", n_full
     return (one_step, n_full, (n_full / n_s) ** 2,
             f"a {n_s}-body random subsample of the disk, time scaled by (N/n)^2 to the "
-            f"{n_full}-body disk")
+            f"{n_full}-body disk", n_s)
 
 
-def cpu_baseline(w, prec_label, max_seconds=20.0):
+def cpu_baseline(w, threads=1, max_seconds=20.0, n_max=8192):
     """The oracle's particle-steps/s on a bounded sample (oracle_sample), whole
-    steps until about max_seconds have passed (at most 50)."""
-    one_step, nb, scale, what = oracle_sample(w)
-    t0 = time.perf_counter()
-    steps = 0
-    while steps < 1 or (time.perf_counter() - t0 < max_seconds and steps < 50):
-        one_step()
-        steps += 1
-    dt = (time.perf_counter() - t0) * scale
-    return {"value": nb * steps / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} steps of {what} (plain FP64 oracle, single thread)"}
+    steps until about max_seconds have passed (at most 50), on `threads`
+    threads (its loops over bodies; results identical for any count)."""
+    import oracle as O
+    one_step, nb, scale, what, ns = oracle_sample(w, n_max)
+    O.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        steps = 0
+        while steps < 1 or (time.perf_counter() - t0 < max_seconds and steps < 50):
+            one_step()
+            steps += 1
+        raw = time.perf_counter() - t0
+    finally:
+        O.set_threads(1)
+    dt = raw * scale
+    return {"value": nb * steps / dt, "unit": METRIC, "cores": threads, "kind": "oracle",
+            "sample": f"{steps} steps of {what} (plain FP64 oracle, "
+                      + ("single thread)" if threads == 1 else f"its body loops on {threads} threads)"),
+            "sample_value": ns * steps / raw, "scaled": scale != 1.0}
 
 
 def run_reference_kepler(args):
@@ -226,18 +264,21 @@ def run_reference_kepler(args):
     from paper_1007_3458_gb300 import workloads as W
     O.build()
     qq, vv, dt = W.test_particles(1 << 20, seed=4)
-    m = 20000
+    cores = host_cores()
+    m = 100000 * cores
     solver = 1 if args.solver == "newton" else 0
+    O.set_threads(cores)
     for _ in range(args.warmup):
         O.kepler_drift(qq[:m], vv[:m], 1.0, dt, solver=solver)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         O.kepler_drift(qq[:m], vv[:m], 1.0, dt, solver=solver)
     cdt = time.perf_counter() - t0
+    O.set_threads(1)
     value = m * args.steps / cdt
-    cb = {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+    cb = {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
           "sample": f"first {m} particles, {args.steps} timed drifts after {args.warmup} untimed, "
-                    "standard guess (plain FP64 oracle, single thread)"}
+                    f"standard guess (plain FP64 oracle, its body loop on {cores} threads)"}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * len(qq) / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -251,9 +292,12 @@ def run_reference_kepler(args):
 
 
 def run_reference(args):
-    """The reference arm: the oracle as it stands on the host cores, on this
-    arm's workload and metric. W untimed steps, then K timed steps, each a step
-    of a bounded sample of the workload (oracle_sample)."""
+    """The reference arm: the oracle on the host cores (its loops over bodies
+    on every core; results identical to one thread), on this arm's workload
+    and metric. W untimed steps, then K timed steps, each a step of the whole
+    workload up to 32768 bodies, else of a random subsample scaled by (N/n)^2
+    (oracle_sample)."""
+    import oracle as O
     ws, rank = _dist()
     if rank != 0:
         return 0
@@ -261,24 +305,34 @@ def run_reference(args):
         return run_reference_kepler(args)
     w, desc = _workload(args.workload)
     t_all = time.perf_counter()
-    one_step, nb, scale, what = oracle_sample(w)
+    cores = host_cores()
+    one_step, nb, scale, what, ns = oracle_sample(w, 32768)
+    O.set_threads(cores)
     for _ in range(args.warmup):
         one_step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         one_step()
-    dt = (time.perf_counter() - t0) * scale
+    raw = time.perf_counter() - t0
+    O.set_threads(1)
+    dt = raw * scale
     value = nb * args.steps / dt
-    cb = {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+    cb = {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
           "sample": f"{args.steps} timed steps (after {args.warmup} untimed) of {what} "
-                    "(plain FP64 oracle, single thread)"}
+                    f"(plain FP64 oracle, its body loops on {cores} threads)",
+          "sample_value": ns * args.steps / raw}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "description": desc, "kick": "fp64",
-                       "l2": "n/a (CPU)"},
+                       "l2": "n/a (CPU)",
+                       "sampling": ("none: every step is a step of the whole workload"
+                                    if scale == 1.0 else
+                                    f"each step is a step of a {ns}-body subsample; time scaled "
+                                    f"by (N/n)^2 = {scale:.4g}"),
+                       "sample_bodies": ns},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
@@ -400,14 +454,21 @@ def run_ours(args):
     kick_ms = 0.5 * (k1_ms + k2_ms)
     achieved = 20.0 * pairs / (kick_ms / 1e3) / 1e12
     clocks = clk.summary()
-    peak = fp32_peak_tflops(2070.0)
+    probe = probe_peaks(q, dev)
+    peak = probe["fp32"] if prec else probe["dfma"]
+    digest = source_digest("kick.cu")
     roof = {"bound": "alu", "kernel": "k_kick_mixed" if prec else "k_kick_fp64",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": (KICK_DRAM_BYTES.get((args.workload, st["kick_tile_i"], st["kick_tile_splits"]))
-                        if prec else None),
-            "traffic_unit": "bytes per launch (ncu)",
-            "convention": "20 flop per ordered pair, FP32 FMA-pipe peak 152 SM x 128 x 2 x 2070 MHz",
+            "peak_source": "measured (qym_probe_fma, %s)" % ("FP32 FMA pipe" if prec else "FP64"),
+            "peak_probe": probe,
+            "traffic": (KICK_DRAM_BYTES.get((args.workload, st["kick_tile_i"], st["kick_tile_splits"],
+                                             digest)) if prec else None),
+            "traffic_unit": "bytes per launch (ncu)", "kick_source_digest": digest,
+            "convention": "20 flop per ordered pair over the mean launch time of the searching "
+                          "and the plain kick",
             "kick_ms_with_search": k1_ms, "kick_ms_plain": k2_ms,
+            "frac_with_search": 20.0 * pairs / (k1_ms / 1e3) / 1e12 / peak,
+            "frac_plain": 20.0 * pairs / (k2_ms / 1e3) / 1e12 / peak,
             "gpair_per_s_kernel": pairs / (kick_ms / 1e3) / 1e9}
 
     # end to end through the C ABI with host buffers: per step, the state goes
@@ -462,7 +523,11 @@ def run_ours(args):
         precision = precision_compare(q, torch, w, args, dev)
     if rank != 0:
         return 0
-    cb = cpu_baseline(w, args.prec, max_seconds=args.cpu_seconds) if ws == 1 else None
+    cb = None
+    if ws == 1:
+        cb = cpu_baseline(w, 1, max_seconds=args.cpu_seconds)
+        cb["all_cores"] = cpu_baseline(w, host_cores(), max_seconds=args.cpu_seconds,
+                                       n_max=32768)
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -645,6 +710,16 @@ def run_kepler(args):
         cdt = time.perf_counter() - t0
         cb = {"value": m / cdt, "unit": METRIC, "cores": 1, "kind": "oracle",
               "sample": f"first {m} particles, one drift, standard guess (plain FP64 oracle, single thread)"}
+        cores = host_cores()
+        O.set_threads(cores)
+        m2 = 200000
+        t0 = time.perf_counter()
+        O.kepler_drift(qq[:m2], vv[:m2], 1.0, dt, solver=1 if args.solver == "newton" else 0)
+        cdt = time.perf_counter() - t0
+        O.set_threads(1)
+        cb["all_cores"] = {"value": m2 / cdt, "unit": METRIC, "cores": cores, "kind": "oracle",
+                           "sample": f"first {m2} particles, one drift, standard guess (plain "
+                                     f"FP64 oracle, its body loop on {cores} threads)"}
     line = {"metric": METRIC, "value": head["value"], "unit": METRIC, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -217,6 +217,22 @@ qym_status qym_set_mlp(qym_ctx *ctx, const float *weights, int64_t n);
  * cap = 0 (rows NULL) stops logging. */
 qym_status qym_set_kepler_log(qym_ctx *ctx, float *rows, int64_t cap);
 
+/* Record the inputs of the rigorous encounter test (Sec. 2.3 item 4, Sec.
+ * 2.4) of the last step of every following qym_step call: the state entering
+ * the Kepler drift (positions q0 after the opening drift, velocities v0 after
+ * the first kick), the Kepler drift's result (q1, v1, before the Hermite
+ * replaces the encounter sets' rows) and the Hill radii rH the test used.
+ * q0, v0, q1, v1: device float64[3][rows] (all x, then y, then z); rH:
+ * device float64[rows]; caller owned, written by device-to-device copies on
+ * the context's stream inside qym_step, kept until replaced. Positions are
+ * heliocentric, velocities barycentric (the DH coordinates the test works
+ * in), star rows zero. With these arrays the encounter records of that step
+ * (qym_get_encounters) can be recomputed exactly by anyone: they are the
+ * pairs i < j of one system with d_min^2 < (a_E (rH_i + rH_j))^2. All five
+ * NULL stops recording; a mix of NULL and non-NULL is QYM_EINVAL. */
+qym_status qym_set_encounter_snapshot(qym_ctx *ctx, double *q0, double *v0, double *q1,
+                                      double *v1, double *rH);
+
 /* Message for the last error on ctx (ctx may be NULL: last context-free error
  * of the calling thread). The string lives until the next call on ctx. */
 const char *qym_last_error(const qym_ctx *ctx);
@@ -336,11 +352,16 @@ qym_status qym_accel_dev(int64_t rows, const double *m, const double *q, double 
  * which every GPU that loads the library holds until the process exits.
  * The paper has no counterpart; this is a deployment convenience.
  *  rows     2 .. QYM_STATIC_MAX_ROWS; larger systems return QYM_EINVAL with a
- *           message from qym_static_last_error() (use qym_accel_dev then)
+ *           clear message (use qym_accel_dev then)
  *  m, q, a, G, prec, heavy_mass, stream: as qym_accel_dev (caller-owned)
+ * Error messages go where every context-free call's go (qym_last_error(NULL));
+ * qym_static_last_error() returns the same text.
  * The call allocates nothing (no cudaMalloc or allocating library routine).
- * Its first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture. All calls
+ * The array's device address is looked up, with the current device, on every
+ * call that is not being captured into a CUDA graph (so a device reset between
+ * calls is harmless); a call made during a capture uses the address its last
+ * call on that device found, so make one call on a device before capturing
+ * it (a capture without one fails with QYM_ECUDA). All calls
  * share the one array and every call rewrites all of the scratch it reads,
  * so nothing carries over between calls; calls that overlap on the GPU (on
  * different streams, or from several threads) race on it and must be
@@ -368,6 +389,22 @@ qym_status qym_encounter_test_dev(int64_t rows, const double *q0, const double *
 size_t qym_energy_workspace_bytes(int64_t rows);
 qym_status qym_energy_dev(int64_t rows, const double *m, const double *q, const double *v,
                           double G, double *E, void *work, size_t work_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Arithmetic peak of the current device, measured: blocks_per_sm x SMs CTAs
+ * of 256 threads each run 8 independent chains of `iters` fused
+ * multiply-adds (kind 0: FP32 FFMA, 1: packed FP32x2 FFMA2, counted as two
+ * lanes each, 2: FP64 DFMA), timed by CUDA events on `stream`. *tflops gets
+ * 2 flops per lane-FMA over the elapsed time, *ms (if not NULL) that time.
+ * Waits for the launch. These are the denominators of the roofline fractions
+ * of the FP32 kick (Sec. 2, Eq. 4: 20 flops per pair by convention) and the
+ * FP64 Kepler drift (Appendix); the paper has no such call. QYM_EINVAL for
+ * kind outside 0..2, iters < 1 or blocks_per_sm outside 1..8. */
+qym_status qym_probe_fma(int32_t kind, int64_t iters, int32_t blocks_per_sm, double *tflops,
+                         double *ms, void *stream);
 
 #ifdef __cplusplus
 }

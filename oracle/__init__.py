@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                               "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"])
+                               "-fopenmp", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -98,7 +98,21 @@ def lib():
         L.or_step.argtypes = [C.c_int64, D, D, D, C.POINTER(Params), C.c_double, C.c_int64,
                               C.c_int64, D, I64, D, C.c_int64, I64, I64, I64, D, C.c_int64, I64]
         L.or_step.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int]
+        L.or_set_threads.restype = None
+        L.or_get_threads.argtypes = []
+        L.or_get_threads.restype = C.c_int
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads for the loops over bodies (kick, Kepler drift, all-pairs
+    encounter test); results are bit-identical for any count. 1 by default."""
+    lib().or_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().or_get_threads())
 
 
 def _d(a):

@@ -49,7 +49,12 @@
  *      the K correction.
  *   R12 Stumpff series used for |y| < 0.1, summed to the y^8 term.
  *   R13 Kepler iteration stops when |F| <= 1e-14 times the sum of the
- *      magnitudes of F's terms, or |dx| <= 2^-50 |x|.
+ *      magnitudes of F's terms at an evaluated x. A step below 2^-50 |x| (or
+ *      a bracket that narrow) is followed by one more evaluation at the new
+ *      x; if that still misses 1e-14, the iteration stops there anyway, at
+ *      whichever of the last two points has the smaller residual: the root
+ *      is then known to rounding, and on orbits with r1 >> r0 no double
+ *      need meet 1e-14 (F moves by F' = r1 per unit of x).
  *   R14 standard starting guess x0 = sqrt(mu) dt / r0; the paper's x0 = r0 is
  *      kept as a separate guess mode.
  *   R15 the iteration is kept inside the bracket [0, sqrt(mu) dt / r_p]
@@ -63,6 +68,16 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* Threads for the loops over bodies (the all-pairs kick, the Kepler drift of
+ * each body, the all-pairs encounter test), 1 by default. Every body's result
+ * is computed by one thread in the same order whatever the count, and the
+ * encounter list is assembled in row order, so results are bit-identical for
+ * any count. Only the all-core CPU baseline sets it; built without OpenMP the
+ * pragmas are ignored and the loops run on one thread. */
+static int g_threads = 1;
+void or_set_threads(int n) { g_threads = n > 0 ? n : 1; }
+int or_get_threads(void) { return g_threads; }
 
 #define OR_PI 3.14159265358979323846
 
@@ -145,6 +160,10 @@ int or_kepler_solve_br(double sqmu, double dt, double r0, double sig, double alp
     double x = *x_io;
     if (!(x >= lo && x <= hi)) x = (isfinite(lo) && isfinite(hi)) ? 0.5 * (lo + hi) : x;
     double dx_old = INFINITY;
+    /* after a step at the rounding level: the point it started from and its
+     * relative residual */
+    int settle = 0;
+    double x_prev = x, res_prev = INFINITY;
     int it;
     for (it = 0; it < max_iter; ++it) {
         double F, Fp, Fpp;
@@ -163,6 +182,13 @@ int or_kepler_solve_br(double sqmu, double dt, double r0, double sig, double alp
                        fabs((1.0 - r0 * alpha) * x * x * x * S) + r0 * fabs(x);
         if (fabs(F) <= 1e-14 * scale) {
             *x_io = x;
+            *iters = it;
+            return 0;
+        }
+        if (settle) {
+            /* evaluated after a rounding-level step and still above 1e-14:
+             * keep the better of the last two points (R13) */
+            *x_io = fabs(F) / scale <= res_prev ? x : x_prev;
             *iters = it;
             return 0;
         }
@@ -186,12 +212,12 @@ int or_kepler_solve_br(double sqmu, double dt, double r0, double sig, double alp
             dx = x - xn;
         }
         dx_old = dx;
-        x = xn;
-        if (fabs(dx) <= 0x1p-50 * fabs(x) || (isfinite(lo) && isfinite(hi) && hi - lo <= 0x1p-50 * fabs(x))) {
-            *x_io = x;
-            *iters = it + 1;
-            return 0;
+        if (fabs(dx) <= 0x1p-50 * fabs(xn) || (isfinite(lo) && isfinite(hi) && hi - lo <= 0x1p-50 * fabs(xn))) {
+            settle = 1;
+            x_prev = x;
+            res_prev = fabs(F) / scale;
         }
+        x = xn;
     }
     *x_io = x;
     *iters = it;
@@ -267,6 +293,7 @@ int64_t or_kepler_drift(int64_t n, const double *q0, const double *v0, double *q
                         const double *x_guess, int32_t max_iter, double *x_out, int32_t *iters_out)
 {
     int64_t bad = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : bad) num_threads(g_threads) if (g_threads > 1)
     for (int64_t i = 0; i < n; ++i) {
         double x;
         int32_t it;
@@ -339,6 +366,7 @@ void or_accel_row(int64_t rows, const double *m, const double *q, double G, int6
 void or_accel_int(int64_t rows, const double *m, const double *q, double G, double *a)
 {
     a[0] = a[1] = a[2] = 0.0;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads) if (g_threads > 1)
     for (int64_t i = 1; i < rows; ++i) or_accel_row(rows, m, q, G, i, a + 3 * i);
 }
 
@@ -492,37 +520,159 @@ int64_t or_encounters(int64_t rows, const double *q0, const double *v0, const do
 /* as or_encounters; in addition, unflagged pairs with threshold^2 <= d^2 <
  * threshold^2 (1 + band) ("near misses", for tests) go to near[] with their
  * (d^2, threshold^2) */
+/* flagged pairs and near misses of a range of rows, in (i, j) order */
+typedef struct {
+    int64_t *pairs, *near;
+    double *d2, *thr2, *near_d2;
+    int64_t cap, cnt, near_cap, near_cnt;
+    int want_near;
+} enc_out;
+
+static void enc_push(int64_t **p, double **x, int64_t *cap, int64_t n)
+{
+    if (n < *cap) return;
+    *cap = 2 * *cap + 64;
+    *p = (int64_t *)realloc(*p, sizeof(int64_t) * 2 * *cap);
+    *x = (double *)realloc(*x, sizeof(double) * 2 * *cap);
+}
+
+/* row i against every j > i: flagged pairs into o (all of them counted,
+ * the first o->cap written), near misses likewise */
+static void enc_row(int64_t rows, const double *q0, const double *v0, const double *q1,
+                    const double *v1, const double *rH, double tau, double a_E, double band,
+                    int64_t i, enc_out *o)
+{
+    for (int64_t j = i + 1; j < rows; ++j) {
+        double dq0[3], dv0[3], dq1[3], dv1[3];
+        pair_diffs(q0, v0, q1, v1, i, j, dq0, dv0, dq1, dv1);
+        double R = a_E * (rH[i] + rH[j]);
+        double dm = or_pair_dmin2(dq0, dv0, dq1, dv1, tau);
+        if (dm < R * R) {
+            if (o->cnt < o->cap) {
+                o->pairs[2 * o->cnt] = i;
+                o->pairs[2 * o->cnt + 1] = j;
+                if (o->d2) o->d2[o->cnt] = dm;
+                if (o->thr2) o->thr2[o->cnt] = R * R;
+            }
+            ++o->cnt;
+        } else if (o->want_near && dm < R * R * (1.0 + band)) {
+            if (o->near_cnt < o->near_cap) {
+                o->near[2 * o->near_cnt] = i;
+                o->near[2 * o->near_cnt + 1] = j;
+                o->near_d2[2 * o->near_cnt] = dm;
+                o->near_d2[2 * o->near_cnt + 1] = R * R;
+            }
+            ++o->near_cnt;
+        }
+    }
+}
+
 int64_t or_encounters_near(int64_t rows, const double *q0, const double *v0, const double *q1,
                            const double *v1, const double *rH, double tau, double a_E,
                            int64_t *pairs, double *d2, double *thr2, int64_t cap, double band,
                            int64_t *near, double *near_d2, int64_t near_cap, int64_t *near_count)
 {
-    int64_t cnt = 0;
-    for (int64_t i = 1; i < rows; ++i)
-        for (int64_t j = i + 1; j < rows; ++j) {
-            double dq0[3], dv0[3], dq1[3], dv1[3];
-            pair_diffs(q0, v0, q1, v1, i, j, dq0, dv0, dq1, dv1);
-            double R = a_E * (rH[i] + rH[j]);
-            double dm = or_pair_dmin2(dq0, dv0, dq1, dv1, tau);
-            if (dm < R * R) {
-                if (cnt < cap) {
-                    pairs[2 * cnt] = i;
-                    pairs[2 * cnt + 1] = j;
-                    if (d2) d2[cnt] = dm;
-                    if (thr2) thr2[cnt] = R * R;
-                }
-                ++cnt;
-            } else if (near_count && dm < R * R * (1.0 + band)) {
-                if (*near_count < near_cap) {
-                    near[2 * *near_count] = i;
-                    near[2 * *near_count + 1] = j;
-                    near_d2[2 * *near_count] = dm;
-                    near_d2[2 * *near_count + 1] = R * R;
-                }
-                ++*near_count;
+    enc_out o = {pairs, near, d2, thr2, near_d2, cap, 0, near_cap,
+                 near_count ? *near_count : 0, near_count != NULL};
+    if (g_threads <= 1) {
+        for (int64_t i = 1; i < rows; ++i) enc_row(rows, q0, v0, q1, v1, rH, tau, a_E, band, i, &o);
+        if (near_count) *near_count = o.near_cnt;
+        return o.cnt;
+    }
+    /* several threads: chunks of rows with equal pair counts, each into
+     * buffers of its own, then appended in row order */
+    enum { NCH = 256 };
+    int64_t bound[NCH + 1];
+    double tot = 0.5 * (double)(rows - 1) * (double)(rows - 2);
+    bound[0] = 1;
+    for (int c = 1; c < NCH; ++c) {
+        /* rows [1, b) hold about c / NCH of the pairs */
+        double f = (double)c / NCH, n1 = (double)(rows - 1);
+        double b = 1.0 + n1 - sqrt(n1 * n1 - 2.0 * f * tot);
+        int64_t bi = (int64_t)b;
+        if (bi < bound[c - 1]) bi = bound[c - 1];
+        if (bi > rows) bi = rows;
+        bound[c] = bi;
+    }
+    bound[NCH] = rows;
+    enc_out part[NCH];
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
+    for (int c = 0; c < NCH; ++c) {
+        int64_t pc = 64, nc = 64;
+        enc_out *w = &part[c];
+        w->pairs = (int64_t *)malloc(sizeof(int64_t) * 2 * pc);
+        w->d2 = (double *)malloc(sizeof(double) * 2 * pc);
+        w->thr2 = NULL;
+        w->near = (int64_t *)malloc(sizeof(int64_t) * 2 * nc);
+        w->near_d2 = (double *)malloc(sizeof(double) * 2 * nc);
+        w->cnt = w->near_cnt = 0;
+        w->want_near = near_count != NULL;
+        for (int64_t i = bound[c]; i < bound[c + 1]; ++i) {
+            /* room for the row's every pair is not known in advance: grow
+             * the chunk's buffers between rows (d2 holds d^2 and thr^2) */
+            enc_out r = {NULL, NULL, NULL, NULL, NULL, 0, 0, 0, 0, w->want_near};
+            int64_t rp = 16, rn = 16;
+            r.pairs = (int64_t *)malloc(sizeof(int64_t) * 2 * rp);
+            r.d2 = (double *)malloc(sizeof(double) * rp);
+            r.thr2 = (double *)malloc(sizeof(double) * rp);
+            r.near = (int64_t *)malloc(sizeof(int64_t) * 2 * rn);
+            r.near_d2 = (double *)malloc(sizeof(double) * 2 * rn);
+            r.cap = rp;
+            r.near_cap = rn;
+            enc_row(rows, q0, v0, q1, v1, rH, tau, a_E, band, i, &r);
+            if (r.cnt > rp || r.near_cnt > rn) {
+                /* more than fit: the row once more with room for all */
+                rp = r.cnt > rp ? r.cnt : rp;
+                rn = r.near_cnt > rn ? r.near_cnt : rn;
+                r.pairs = (int64_t *)realloc(r.pairs, sizeof(int64_t) * 2 * rp);
+                r.d2 = (double *)realloc(r.d2, sizeof(double) * rp);
+                r.thr2 = (double *)realloc(r.thr2, sizeof(double) * rp);
+                r.near = (int64_t *)realloc(r.near, sizeof(int64_t) * 2 * rn);
+                r.near_d2 = (double *)realloc(r.near_d2, sizeof(double) * 2 * rn);
+                r.cap = rp;
+                r.near_cap = rn;
+                r.cnt = r.near_cnt = 0;
+                enc_row(rows, q0, v0, q1, v1, rH, tau, a_E, band, i, &r);
             }
+            for (int64_t k = 0; k < r.cnt; ++k) {
+                enc_push(&w->pairs, &w->d2, &pc, w->cnt);
+                w->pairs[2 * w->cnt] = r.pairs[2 * k];
+                w->pairs[2 * w->cnt + 1] = r.pairs[2 * k + 1];
+                w->d2[2 * w->cnt] = r.d2[k];
+                w->d2[2 * w->cnt + 1] = r.thr2[k];
+                ++w->cnt;
+            }
+            for (int64_t k = 0; k < r.near_cnt; ++k) {
+                enc_push(&w->near, &w->near_d2, &nc, w->near_cnt);
+                w->near[2 * w->near_cnt] = r.near[2 * k];
+                w->near[2 * w->near_cnt + 1] = r.near[2 * k + 1];
+                w->near_d2[2 * w->near_cnt] = r.near_d2[2 * k];
+                w->near_d2[2 * w->near_cnt + 1] = r.near_d2[2 * k + 1];
+                ++w->near_cnt;
+            }
+            free(r.pairs); free(r.d2); free(r.thr2); free(r.near); free(r.near_d2);
         }
-    return cnt;
+    }
+    for (int c = 0; c < NCH; ++c) {
+        enc_out *w = &part[c];
+        for (int64_t k = 0; k < w->cnt; ++k, ++o.cnt)
+            if (o.cnt < o.cap) {
+                o.pairs[2 * o.cnt] = w->pairs[2 * k];
+                o.pairs[2 * o.cnt + 1] = w->pairs[2 * k + 1];
+                if (o.d2) o.d2[o.cnt] = w->d2[2 * k];
+                if (o.thr2) o.thr2[o.cnt] = w->d2[2 * k + 1];
+            }
+        for (int64_t k = 0; k < w->near_cnt; ++k, ++o.near_cnt)
+            if (o.want_near && o.near_cnt < o.near_cap) {
+                o.near[2 * o.near_cnt] = w->near[2 * k];
+                o.near[2 * o.near_cnt + 1] = w->near[2 * k + 1];
+                o.near_d2[2 * o.near_cnt] = w->near_d2[2 * k];
+                o.near_d2[2 * o.near_cnt + 1] = w->near_d2[2 * k + 1];
+            }
+        free(w->pairs); free(w->d2); free(w->near); free(w->near_d2);
+    }
+    if (near_count) *near_count = o.near_cnt;
+    return o.cnt;
 }
 
 /* rigorous test of selected rows i against all j != i (sampled parity) */

@@ -100,6 +100,8 @@ def lib():
     L.qym_kepler_drift_dev.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_int32,
                                        C.c_int32, P, C.c_int32, P, P, P, P, P, P]
     L.qym_set_kepler_log.argtypes = [P, P, C.c_int64]
+    L.qym_set_encounter_snapshot.argtypes = [P, P, P, P, P, P]
+    L.qym_probe_fma.argtypes = [C.c_int32, C.c_int64, C.c_int32, D, D, P]
     L.qym_transition_dev.argtypes = [C.c_int64, P, C.c_double, P, P, P, P]
     L.qym_mlp_workspace_bytes.argtypes = []
     L.qym_mlp_workspace_bytes.restype = C.c_size_t
@@ -130,7 +132,7 @@ def lib():
                  "qym_kepler_drift_dev", "qym_accel_dev", "qym_encounter_test_dev",
                  "qym_energy_dev", "qym_set_kepler_log", "qym_mlp_forward_dev",
                  "qym_mlp_grad_dev", "qym_mlp_adam_dev", "qym_mlp_train_dev",
-                 "qym_transition_dev"):
+                 "qym_transition_dev", "qym_set_encounter_snapshot", "qym_probe_fma"):
         getattr(L, name).restype = S
     _lib = L
     return L
@@ -258,6 +260,24 @@ def qym_set_kepler_log(ctx, rows, cap=None):
     else:
         cap = rows.shape[0] if cap is None else cap
         _check(lib().qym_set_kepler_log(ctx, _ptr(rows), cap), ctx)
+
+
+def qym_set_encounter_snapshot(ctx, q0=None, v0=None, q1=None, v1=None, rH=None):
+    """CUDA float64 tensors [3, rows] (q0, v0, q1, v1) and [rows] (rH) that
+    receive the rigorous encounter test's inputs of the last step of each
+    following qym_step call; all None stops recording."""
+    _check(lib().qym_set_encounter_snapshot(ctx, _ptr(q0), _ptr(v0), _ptr(q1), _ptr(v1),
+                                            _ptr(rH)), ctx)
+
+
+def qym_probe_fma(kind, iters=1 << 16, blocks_per_sm=4, stream=None):
+    """Measured FMA throughput of the device (kind 0: FP32 FFMA, 1: FP32x2
+    FFMA2, 2: FP64 DFMA): (TFLOP/s, ms)."""
+    tf = C.c_double()
+    ms = C.c_double()
+    _check(lib().qym_probe_fma(kind, iters, blocks_per_sm, C.byref(tf), C.byref(ms),
+                               _stream(stream)))
+    return tf.value, ms.value
 
 
 def qym_last_error(ctx=None) -> str:
@@ -397,6 +417,9 @@ class Simulation:
 
     def set_kepler_log(self, rows, cap=None):
         qym_set_kepler_log(self.ctx, rows, cap)
+
+    def set_encounter_snapshot(self, q0=None, v0=None, q1=None, v1=None, rH=None):
+        qym_set_encounter_snapshot(self.ctx, q0, v0, q1, v1, rH)
 
     def close(self):
         if self.ctx:

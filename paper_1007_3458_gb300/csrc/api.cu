@@ -21,6 +21,12 @@ using namespace qym;
 
 static thread_local std::string g_err;
 
+namespace qym {
+// the message qym_last_error(NULL) returns, for context-free calls of other
+// translation units
+void set_thread_error(const std::string &msg) { g_err = msg; }
+}  // namespace qym
+
 struct qym_ctx {
     qym_params p;
     cudaStream_t stream = nullptr;
@@ -55,6 +61,9 @@ struct qym_ctx {
     unsigned long long klog_steps = 0;   // steps logged so far
     unsigned long long *klog_base = nullptr;  // device copy of klog_steps (arena)
     int32_t *hflag = nullptr;    // state upload: bit 1 non-finite position, bit 2 velocity
+    // caller's device arrays receiving the encounter test's inputs of the
+    // last step of each qym_step call (q0, v0, q1, v1 [3][rows], rH [rows])
+    double *snap[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 #define FAIL(ctx, code, msg)                         \
@@ -495,6 +504,21 @@ static int search_retest(const qym_params &p, int flag) {
     return (flag && p.kick_prec == QYM_KICK_MIXED) ? 1 : 0;
 }
 
+// copies of the rigorous encounter test's inputs (qym_set_encounter_snapshot):
+// (q, v) enter the Kepler drift, (q1, v1) its result, before the Hermite
+static cudaError_t enqueue_snapshot(qym_ctx *c) {
+    if (!c->snap[0]) return cudaSuccess;
+    const Dev &d = c->d;
+    const size_t b3 = sizeof(double) * 3 * (size_t)d.rows;
+    const double *src[5] = {d.q, d.v, d.q1, d.v1, d.rH};
+    for (int k = 0; k < 5; ++k) {
+        cudaError_t e = cudaMemcpyAsync(c->snap[k], src[k], k < 4 ? b3 : b3 / 3,
+                                        cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // The opening kick of a step with the crude encounter search when no |a| of
 // an earlier kick bounds this one (after qym_init or qym_set_state): the kick
 // runs first, then the reaches are built from the kicked state (no |a|
@@ -539,6 +563,7 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last, bool fresh = 
     }
     // item 3: Kepler drift over tau, (q, v) -> (q1, v1)
     if ((e = launch_kepler(step_kepler_args(c, tau), st))) return e;
+    if (last && (e = enqueue_snapshot(c))) return e;
     if (enc) {
         // items 4-8: rigorous test, sets and r_crit, K corrections + Hermite
         if ((e = launch_refine(d, tau, p.a_E, st))) return e;
@@ -597,6 +622,7 @@ static cudaError_t enqueue_unit(qym_ctx *c, double tau, bool last) {
         if ((e = cudaMemsetAsync(c->flush, c->launches & 0xff, (size_t)p.l2_flush_bytes, st))) return e;
     }
     if ((e = launch_kepler(step_kepler_args(c, tau), st))) return e;
+    if (last && (e = enqueue_snapshot(c))) return e;
     if (enc) {
         if ((e = launch_refine(d, tau, p.a_E, st))) return e;
         if ((e = launch_sets_impl(d, p.a_H, c->ss, st))) return e;
@@ -846,6 +872,17 @@ extern "C" qym_status qym_set_kepler_log(qym_ctx *c, float *rows, int64_t cap) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
     }
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_set_encounter_snapshot(qym_ctx *c, double *q0, double *v0, double *q1,
+                                                 double *v1, double *rH) {
+    if (!c) FAIL(nullptr, QYM_EINVAL, "qym_set_encounter_snapshot: NULL context");
+    double *in[5] = {q0, v0, q1, v1, rH};
+    int n = 0;
+    for (int k = 0; k < 5; ++k) n += in[k] != nullptr;
+    if (n != 0 && n != 5) FAIL(c, QYM_EINVAL, "qym_set_encounter_snapshot: all five arrays or none");
+    for (int k = 0; k < 5; ++k) c->snap[k] = in[k];
     return QYM_OK;
 }
 

@@ -153,6 +153,10 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
             const bool have_br = isfinite(lo) && isfinite(hi);
             if (!(x >= lo && x <= hi) && have_br) x = 0.5 * (lo + hi);
             double dx_old = INFINITY;
+            // after a step at the rounding level: the point it started from
+            // and its relative residual
+            bool settle = false;
+            double x_prev = x, res_prev = INFINITY;
             for (int it = 0; it < a.max_iter; ++it) {
                 double F, Fp, Fpp;
                 eq.eval(x, F, Fp, Fpp, C, S);
@@ -168,6 +172,14 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
                 double scale = fabs(eq.sqmu_dt) + fabs(eq.sig * x2 * C) +
                                fabs(eq.b * x2 * x * S) + r0 * fabs(x);
                 if (fabs(F) <= 1e-14 * scale) { --iters; conv = true; cs_at_x = true; break; }
+                if (settle) {
+                    // evaluated after a rounding-level step and still above
+                    // 1e-14: the better of the last two points is the root
+                    --iters;
+                    conv = true;
+                    if (fabs(F) / scale <= res_prev) cs_at_x = true; else x = x_prev;
+                    break;
+                }
                 double dx;
                 if (solver == QYM_SOLVER_LAGUERRE) {
                     // Laguerre, n = 5: dx = n F / (F' + sgn(F') sqrt|(n-1)^2 F'^2 - n(n-1) F F''|),
@@ -186,17 +198,18 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
                     dx = x - xn;
                 }
                 dx_old = dx;
-                x = xn;
-                if (fabs(dx) <= 0x1p-50 * fabs(x) ||
-                    (isfinite(lo) && isfinite(hi) && hi - lo <= 0x1p-50 * fabs(x))) {
-                    conv = true;
-                    break;
+                if (fabs(dx) <= 0x1p-50 * fabs(xn) ||
+                    (isfinite(lo) && isfinite(hi) && hi - lo <= 0x1p-50 * fabs(xn))) {
+                    settle = true;
+                    x_prev = x;
+                    res_prev = fabs(F) / scale;
                 }
+                x = xn;
             }
         }
         // f and g functions at the root (Appendix); r before fdot, gdot. The
-        // residual test already evaluated C, S at this x; a step-size exit
-        // moved x after the last evaluation
+        // last evaluation left C, S at this x unless the iteration kept the
+        // point before it, or ran out of iterations after a step
         double x2 = x * x;
         double y = eq.alpha * x2;
         if (!cs_at_x) stumpff(y, C, S);

@@ -18,19 +18,27 @@ static std::mutex g_static_mu;
 static void *g_static_ptr[128];  // device address of the array, per device ordinal
 
 // The array's name in host code is a host-side stand-in, not a device
-// address; its device address is looked up once per device, with that device
-// current, and cached.
-static cudaError_t static_scratch(void **out) {
+// address. Its device address is looked up with the device current on every
+// call that is not being captured into a CUDA graph (a lookup allocates
+// nothing and is cheap), so a context torn down and created again (after
+// cudaDeviceReset, say) gets the array's new address; during a capture the
+// address from the last call on that device is used.
+static cudaError_t static_scratch(cudaStream_t stream, void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
         g_static_ptr[dev] = p;
+    } else if (!g_static_ptr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_static_ptr[dev];
     return cudaSuccess;
@@ -40,6 +48,14 @@ static cudaError_t static_scratch(void **out) {
 
 static thread_local std::string g_static_err;
 
+// errors go to the library's context-free message (qym_last_error(NULL)) and
+// to this call's own getter, which returns the same text
+static qym_status static_fail(qym_status st, const std::string &msg) {
+    g_static_err = msg;
+    qym::set_thread_error(msg);
+    return st;
+}
+
 extern "C" const char *qym_static_last_error(void) { return g_static_err.c_str(); }
 
 extern "C" size_t qym_static_scratch_bytes(void) { return qym::kStaticScratchBytes; }
@@ -48,34 +64,26 @@ extern "C" qym_status qym_accel_dev_static(int64_t rows, const double *m, const 
                                            double *a, double G, int32_t prec, double heavy_mass,
                                            void *stream) {
     using namespace qym;
-    if (rows < 2 || !m || !q || !a) {
-        g_static_err = "qym_accel_dev_static: rows < 2 or a NULL array";
-        return QYM_EINVAL;
-    }
-    if (prec != QYM_KICK_FP64 && prec != QYM_KICK_MIXED) {
-        g_static_err = "qym_accel_dev_static: prec must be QYM_KICK_FP64 or QYM_KICK_MIXED";
-        return QYM_EINVAL;
-    }
-    if (rows > QYM_STATIC_MAX_ROWS) {
-        g_static_err = "qym_accel_dev_static: " + std::to_string(rows) + " rows exceed the fixed "
-                       "scratch limit of " + std::to_string((long long)QYM_STATIC_MAX_ROWS) +
-                       " rows; use qym_accel_dev with a caller workspace";
-        return QYM_EINVAL;
-    }
+    if (rows < 2 || !m || !q || !a)
+        return static_fail(QYM_EINVAL, "qym_accel_dev_static: rows < 2 or a NULL array");
+    if (prec != QYM_KICK_FP64 && prec != QYM_KICK_MIXED)
+        return static_fail(QYM_EINVAL,
+                           "qym_accel_dev_static: prec must be QYM_KICK_FP64 or QYM_KICK_MIXED");
+    if (rows > QYM_STATIC_MAX_ROWS)
+        return static_fail(QYM_EINVAL, "qym_accel_dev_static: " + std::to_string(rows) +
+                                           " rows exceed the fixed scratch limit of " +
+                                           std::to_string((long long)QYM_STATIC_MAX_ROWS) +
+                                           " rows; use qym_accel_dev with a caller workspace");
     size_t need = accel_single_workspace(rows, prec);
-    if (need > kStaticScratchBytes) {  // guarded by the row limit; checked anyway
-        g_static_err = "qym_accel_dev_static: scratch of " + std::to_string(need) +
-                       " bytes exceeds the fixed array";
-        return QYM_EINVAL;
-    }
+    if (need > kStaticScratchBytes)  // guarded by the row limit; checked anyway
+        return static_fail(QYM_EINVAL, "qym_accel_dev_static: scratch of " +
+                                           std::to_string(need) + " bytes exceeds the fixed array");
     void *scratch = nullptr;
-    cudaError_t e = static_scratch(&scratch);
+    cudaError_t e = static_scratch((cudaStream_t)stream, &scratch);
     if (e == cudaSuccess)
         e = launch_accel_single(rows, m, q, a, G, prec, heavy_mass, scratch, kStaticScratchBytes,
                                 (cudaStream_t)stream);
-    if (e != cudaSuccess) {
-        g_static_err = std::string("qym_accel_dev_static: ") + cudaGetErrorString(e);
-        return QYM_ECUDA;
-    }
+    if (e != cudaSuccess)
+        return static_fail(QYM_ECUDA, std::string("qym_accel_dev_static: ") + cudaGetErrorString(e));
     return QYM_OK;
 }

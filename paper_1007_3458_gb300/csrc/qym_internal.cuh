@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/qym.h"
 
 namespace qym {
@@ -154,6 +156,9 @@ __device__ __forceinline__ void heavy_pull(const int32_t *hs, int nh, int64_t i,
         az -= s * dz;
     }
 }
+
+// the calling thread's context-free error message (qym_last_error(NULL))
+void set_thread_error(const std::string &msg);
 
 // ---------------------------------------------------------------- launches
 // Each returns cudaSuccess or the launch error. All work goes on `st`.

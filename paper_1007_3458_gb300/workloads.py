@@ -230,6 +230,63 @@ def ensemble(nsys=512, n_lo=64, n_hi=4096, seed=3, nsteps=1000, name=None):
                     eps_H=4.7e-4)
 
 
+def crossers(seed=6, n_disk=500, n_ecc=150, n_retro=100, n_hill=40, n_hyper=30, nsteps=40,
+             name=None):
+    """A disk stirred up to test the close-encounter search where it is
+    hardest: star + a Jupiter-mass planet at a = 1 (circular) + a 3e-4 planet
+    at a = 1.6 (e = 0.05, i = 0.02) + a cold disk of planetesimals (1e-9, a
+    uniform in [0.5, 3], Rayleigh(0.01) e and i), joined by
+      * eccentric crossers: a uniform in [0.7, 2.5], e uniform in [0.5, 0.9],
+        i uniform in [0, 90 deg];
+      * retrograde bodies: a uniform in [0.6, 2.5], e uniform in [0, 0.6],
+        i uniform in [90, 180 deg];
+      * bodies within 1.5 Hill radii of the Jupiter-mass planet moving at
+        0.05-1.5 times its orbital speed relative to it in random directions
+        (many on hyperbolic orbits about the star);
+      * hyperbolic flybys: r uniform in [1.5, 3], speed 1.1-2 times the local
+        escape speed, aimed at a random point of the planet's orbit.
+    All light bodies have m = 1e-9; tau = P(a=1)/40."""
+    G, m0 = 1.0, 1.0
+    rng = np.random.default_rng(seed)
+    mp = np.array([1e-3, 3e-4])
+    qp, vp = elements_to_cartesian(G * (m0 + mp), np.array([1.0, 1.6]), np.array([0.0, 0.05]),
+                                   np.array([0.0, 0.02]), rng.uniform(0, TWO_PI, 2),
+                                   rng.uniform(0, TWO_PI, 2), rng.uniform(0, TWO_PI, 2))
+    disk = _population(rng, n_disk, 1e-9, 0.5, 3.0, 0.01, 0.01, G, m0)
+
+    def _elems(n, a_lo, a_hi, e_lo, e_hi, i_lo, i_hi):
+        a = rng.uniform(a_lo, a_hi, n)
+        e = rng.uniform(e_lo, e_hi, n)
+        inc = rng.uniform(i_lo, i_hi, n)
+        q, v = elements_to_cartesian(G * (m0 + 1e-9), a, e, inc, rng.uniform(0, TWO_PI, n),
+                                     rng.uniform(0, TWO_PI, n), rng.uniform(0, TWO_PI, n))
+        return np.full(n, 1e-9), q, v
+
+    ecc = _elems(n_ecc, 0.7, 2.5, 0.5, 0.9, 0.0, 0.5 * math.pi)
+    retro = _elems(n_retro, 0.6, 2.5, 0.0, 0.6, 0.5 * math.pi, math.pi)
+    # inside the Jupiter-mass planet's Hill sphere, fast and slow
+    rH = (mp[0] / 3.0) ** (1.0 / 3.0)
+    d = rng.normal(size=(n_hill, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    u = rng.normal(size=(n_hill, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    vc = np.linalg.norm(vp[0])
+    hq = qp[0] + d * (rng.uniform(0.3, 1.5, n_hill) * rH)[:, None]
+    hv = vp[0] + u * (rng.uniform(0.05, 1.5, n_hill) * vc)[:, None]
+    # flybys from outside, aimed at the planet's orbit
+    r = rng.uniform(1.5, 3.0, n_hyper)
+    ph = rng.uniform(0, TWO_PI, n_hyper)
+    fq = np.stack([r * np.cos(ph), r * np.sin(ph), rng.normal(0, 0.05, n_hyper)], 1)
+    tgt_ph = rng.uniform(0, TWO_PI, n_hyper)
+    tgt = np.stack([np.cos(tgt_ph), np.sin(tgt_ph), np.zeros(n_hyper)], 1)
+    aim = (tgt - fq) / np.linalg.norm(tgt - fq, axis=1, keepdims=True)
+    fv = aim * (np.sqrt(2.0 * G * m0 / r) * rng.uniform(1.1, 2.0, n_hyper))[:, None]
+    m, q, v = _assemble([(mp, qp, vp), disk, ecc, retro, (np.full(n_hill, 1e-9), hq, hv),
+                         (np.full(n_hyper, 1e-9), fq, fv)], m0)
+    return Workload(name or "crossers", m, q, v, np.array([0, len(m)], dtype=np.int64), TAU_A1,
+                    nsteps, eps_H=4.7e-4)
+
+
 def test_particles(n=1048576, seed=4):
     """Massless test particles about a unit-mass star: a log-uniform in
     [0.5, 50], e uniform in [0, 0.9], inclination and angles uniform.

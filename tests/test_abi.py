@@ -83,6 +83,8 @@ def test_argument_checks_without_gpu(lib):
                                  None) == q.QYM_EINVAL
     assert lib.qym_set_mlp(None, None, q.QYM_MLP_NW) == q.QYM_EINVAL
     assert lib.qym_set_kepler_log(None, None, 0) == q.QYM_EINVAL
+    assert lib.qym_set_encounter_snapshot(None, None, None, None, None, None) == q.QYM_EINVAL
+    assert lib.qym_probe_fma(3, 10, 4, None, None, None) == q.QYM_EINVAL
     assert lib.qym_transition_dev(4, None, 0.0, None, None, None, None) == q.QYM_EINVAL
     assert lib.qym_transition_dev(0, None, 1.0, None, None, None, None) == q.QYM_OK
     assert lib.qym_accel_workspace_bytes(1, 1) == 0

@@ -123,6 +123,41 @@ def test_mixed_hybrid_step(gpu, oracle):
     assert abs(E[0] - Eo) <= 1e-9 * abs(E0)
 
 
+def test_mixed_energy_1000_steps(gpu, oracle):
+    """The mixed-precision kick over the configured 1000 steps of the 260-body
+    disk: the relative energy change matches the FP64 oracle's to within
+    1e-9 (the mixed path's accuracy target per 1000 steps), and the records
+    agree up to pairs at the threshold."""
+    w = W.disk_260()
+    qg, vg, enc, st, E = _run_gpu(w, 1000, eps_H=w.eps_H)
+    r, vh = _run_oracle(oracle, w, 1000, eps_H=w.eps_H)
+    assert st["status_bits"] == 0
+    vd = oracle.helio_to_dh(w.m, w.v)
+    E0 = oracle.energy(w.m, w.q, vd)
+    Eo = oracle.energy(w.m, r.q, r.v)
+    print(f"\n  dE/E oracle {(Eo - E0) / abs(E0):.6e}, GPU mixed {(E[0] - E0) / abs(E0):.6e}")
+    assert abs(E[0] - Eo) <= 1e-9 * abs(E0)
+    _compare_records(enc, r)
+
+
+@pytest.mark.parametrize("a_E, a_H", [(1.0, 0.5), (6.0, 2.0)])
+def test_hill_factor_parity(gpu, oracle, a_E, a_H):
+    """The hybrid step at the ends of the Hill-factor sweep (a_E the encounter
+    radius of Sec. 2.4, a_H the transition radius r_crit of Sec. 2.2), FP64
+    kick, 300 steps of the 260-body disk (at a_E = 1 the first encounters come
+    after step 100): records equal up to pairs at the threshold, positions
+    within the chaos-aware tolerance."""
+    w = W.disk_260()
+    prm = dict(a_E=a_E, a_H=a_H, eps_H=w.eps_H)
+    n = 300
+    qg, vg, enc, st, E = _run_gpu(w, n, kick_prec=q.QYM_KICK_FP64, **prm)
+    r, vh = _run_oracle(oracle, w, n, **prm)
+    assert st["status_bits"] == 0 and len(r.encounters) > 0
+    skip = _compare_records(enc, r)
+    keep = np.array([i not in skip for i in range(len(w.m))])
+    _check_positions(qg[keep], r.q[keep], _chaos_spread(oracle, w, n, **prm)[keep])
+
+
 def _compare_records(enc, r, band=1e-9):
     """Encounter records equal, except pairs whose interpolated d_min lies
     within `band` (relative) of the 3-Hill-radius threshold on the oracle's

@@ -283,3 +283,27 @@ def test_split_run_continues_exactly(oracle):
     assert len(whole.encounters) > 0 and len(a.encounters) > 0 and len(b.encounters) > 0
     assert np.array_equal(whole.q, b.q) and np.array_equal(whole.v, b.v)
     assert np.array_equal(whole.encounters, np.concatenate([a.encounters, b.encounters]))
+
+
+def test_threads_give_identical_results(oracle):
+    """The oracle's loops over bodies on several threads (used only by the
+    all-core CPU baseline) give the single-thread results bit for bit: every
+    body's sum is formed by one thread in the same order, and the encounter
+    records and near misses are assembled in row order. A stirred disk with
+    encounters in most steps."""
+    from paper_1007_3458_gb300 import workloads as W
+    w = W.crossers()
+    v = oracle.helio_to_dh(w.m, w.v)
+    prm = oracle.params(eps_H=w.eps_H)
+    runs = []
+    try:
+        for th in (1, 4):
+            oracle.set_threads(th)
+            assert oracle.get_threads() == th
+            runs.append(oracle.step(w.m, w.q, v, w.offsets, w.tau, 6, prm))
+    finally:
+        oracle.set_threads(1)
+    a, b = runs
+    assert len(a.encounters) > 0
+    for f in ("q", "v", "encounters", "enc_d2", "near", "near_d2", "stats"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
