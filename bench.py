@@ -11,9 +11,11 @@ kick; --prec fp64 runs the plain FP64 kick instead.
                   [--impl ours|reference] [--workload NAME]
 
 --impl reference times the plain FP64 CPU oracle (the only reference this
-method has here) on a bounded sample of the same workload. With several GPUs
-(torchrun), every rank integrates its own replica (the single-system step has
-no multi-GPU path here); rank 0 prints.
+method has here) on the host cores, on the same workload (a bounded sample
+above 32768 bodies). With several GPUs (torchrun) a single disk's step is
+split over them (contiguous row blocks, NCCL all-gathers between the phases;
+strong scaling), while the ensemble's ranks integrate batches of their own
+(weak scaling); rank 0 prints.
 """
 from __future__ import annotations
 
@@ -63,7 +65,7 @@ def rank_workload(name, rank, world, **kw):
     problems: with several ranks each rank draws its own batch of the same
     shape (seed 3 + 1000 rank; rank 0 keeps the reference batch), so the work
     per GPU is fixed (weak scaling) and no data crosses ranks. A single system
-    has no multi-GPU split here: every rank integrates a replica."""
+    is the same on every rank: its step is split over the ranks (run_split)."""
     from paper_1007_3458_gb300 import workloads as W
     fn, desc = WORKLOADS[name]
     if fn == "ensemble" and world > 1:
@@ -394,9 +396,118 @@ def precision_compare(q, torch, w, args, dev):
     return out
 
 
+def run_split(args):
+    """One system's step split over the job's GPUs (paper_1007_3458_gb300.split):
+    every rank holds the whole disk and computes its block of rows; the
+    exchanges between the phases go through NCCL all-gathers. The total work
+    is fixed whatever the number of GPUs (strong scaling). --split 1 runs this
+    path on one GPU too."""
+    import torch
+    import torch.distributed as dist
+    ws, rank = _dist()
+    if not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29517")
+        dist.init_process_group("nccl", rank=rank, world_size=ws)
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.cuda.current_device()
+    import paper_1007_3458_gb300 as q
+    from paper_1007_3458_gb300 import split as SP
+    q.build()
+    w, desc = _workload(args.workload)
+    if w.nsys != 1:
+        raise SystemExit("the split step is for a single system")
+    prec = q.QYM_KICK_MIXED if args.prec == "mixed" else q.QYM_KICK_FP64
+    sim = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=prec, device=dev, eps_H=w.eps_H)
+    if args.autotune:
+        q.qym_autotune(sim.ctx)
+    eng = SP.GpuEngine(sim, rank, ws)
+    run = SP.SplitRun(eng, SP.TorchComm())
+    run.step(w.tau, max(args.warmup, 3))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        dist.barrier()
+        torch.cuda.synchronize()
+
+    # timed region: K steps, each after writing 256 MB (L2 is 129 MB), host
+    # time around them with the device synchronised on both sides, max over ranks
+    with ClockSampler(dev) as clk:
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1)
+            run.step(w.tau, 1)
+        barrier()
+        ms = 1e3 * (time.perf_counter() - t0)
+    ms = max_over_ranks(ms, "cuda")
+    st = sim.stats()
+    nb = w.n_bodies
+    value = nb * args.steps / (ms / 1e3)
+    lo, hi = eng.own
+    k1_ms, pairs_all = q.qym_time_kick(sim.ctx, 1, 10)
+    k2_ms, _ = q.qym_time_kick(sim.ctx, 0, 10)
+    own_pairs = (hi - lo) * (nb - 1)
+    kick_ms = 0.5 * (k1_ms + k2_ms)
+    probe = probe_peaks(q, dev)
+    achieved = 20.0 * own_pairs / (kick_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": "k_kick_mixed" if prec else "k_kick_fp64",
+            "achieved": achieved, "peak": probe["fp32"] if prec else probe["dfma"],
+            "unit": "TFLOP/s", "traffic": None, "peak_probe": probe,
+            "convention": "20 flop per ordered pair of this rank's rows, mean of the searching "
+                          "and the plain kick"}
+    roof["frac"] = achieved / roof["peak"]
+    # end to end: the state from pinned host memory, one split step, back
+    q0h, v0h = sim.state()
+    qh = torch.empty(q0h.shape, dtype=torch.float64, pin_memory=True).numpy()
+    vh = torch.empty(v0h.shape, dtype=torch.float64, pin_memory=True).numpy()
+    qh[:] = q0h
+    vh[:] = v0h
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.set_state(qh, vh)
+        run.step(w.tau, 1)
+        qh, vh = q.qym_get_state(sim.ctx, qh, vh)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
+    e2e = {"value": nb * e2e_steps / e2e_s, "unit": METRIC,
+           "h2d_bytes_per_step": int(qh.nbytes + vh.nbytes),
+           "d2h_bytes_per_step": int(qh.nbytes + vh.nbytes), "steps": e2e_steps,
+           "what": "qym_set_state + one split step + qym_get_state per step on every rank"}
+    sim.close()
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+    cb = None
+    if ws == 1:
+        cb = cpu_baseline(w, 1, max_seconds=args.cpu_seconds)
+        cb["all_cores"] = cpu_baseline(w, host_cores(), max_seconds=args.cpu_seconds,
+                                       n_max=32768)
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None,
+            "dtype": "fp32-pair/f64-state" if prec else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "kick": args.prec,
+                       "parallelism": f"one system split over {ws} GPU(s): contiguous row "
+                                      "blocks, NCCL all-gathers between the phases",
+                       "tau": w.tau, "bodies": nb, "eps_H": w.eps_H, "own_rows": [lo, hi],
+                       "l2": "flushed: 256 MB written before every step, inside the timed region",
+                       "timing": "host clock around K one-step runs, device synchronised on "
+                                 "both sides, max over ranks"},
+            "stats": st, "gpu_launches": int(st["launches"]) * args.steps,
+            "roofline": roof, "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cb}
+    print(json.dumps(line))
+    dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import torch
     ws, rank = _dist()
+    if args.split or (ws > 1 and WORKLOADS[args.workload][0] != "ensemble"):
+        return run_split(args)
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -765,6 +876,9 @@ def main():
                     help="kepler_1m: train the guess network first (0: standard guess only)")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--split", type=int, default=0,
+                    help="1: a single system's step split over the job's GPUs even on one GPU "
+                         "(with several GPUs a single system always is)")
     ap.add_argument("--kick-only", action="store_true",
                     help="launch only the kick kernels a few times (profiling)")
     args = ap.parse_args()

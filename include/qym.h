@@ -391,6 +391,101 @@ qym_status qym_energy_dev(int64_t rows, const double *m, const double *q, const 
                           double G, double *E, void *work, size_t work_bytes, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* One system's step split over several GPUs (one process and one context  */
+/* per GPU). Every context holds the whole state. Context `rank` of `world`  */
+/* owns the contiguous block of bodies qym_split_rows gives (equal blocks,   */
+/* the last one shorter): it computes the kick of those rows against every  */
+/* row (Sec. 2, Eq. 4) with the crude encounter search of those rows (Sec.  */
+/* 2.4), their Kepler drift (Appendix), the rigorous test of their           */
+/* candidates, and the Hermite sub-integration (Sec. 2.2-2.3) of the         */
+/* encounter sets whose lowest row it owns. The momentum sum, the drifts     */
+/* (Sec. 2, Eq. 2), the kick operand packs and the encounter sets are        */
+/* computed on every context from identical data in a fixed order, so they   */
+/* agree to the bit without an exchange. The caller runs the phases of each  */
+/* step in order and moves data between the contexts after some of them:     */
+/*                                                                           */
+/*   OPEN      first step of a run only: momentum, opening drift, packs      */
+/*   KICK1     step begin, first kick of the own rows (with the search       */
+/*             unless this is the run's first step after init / set_state),   */
+/*             finish of the own rows;                                       */
+/*             then allgather v, amag and rH of the own rows                 */
+/*   SEARCH    (first step of a run only) reaches of every row from the      */
+/*             kicked state, search of the own rows                          */
+/*   KEPLER    Kepler drift of the own rows; then allgather q1, v1           */
+/*   REFINE    rigorous test of the own candidates; then gather every        */
+/*             context's pairs (enc[0 .. qym_split_encounter_count)) and     */
+/*             give the concatenation to qym_split_import_encounters on      */
+/*             every context (the order of the pairs does not matter)        */
+/*   HERMITE   encounter sets of all pairs, Hermite of the own sets; then    */
+/*             every context sends the rows set_mem[first .. first + count)  */
+/*             (qym_split_owned_members) with their q1, v1 and hcost to all  */
+/*             the others, which write them over their own copies            */
+/*   KICK2     pack from (q1, v1), second kick and finish of the own rows;   */
+/*             then allgather v and amag of the own rows                     */
+/*   CLOSE     momentum, closing drift (and, unless last, the next step's    */
+/*             opening drift and packs), step end; with last = 1 it waits    */
+/*             for the device and returns the run's status as qym_step does   */
+/* A run is OPEN, then for each step KICK1, SEARCH, KEPLER, REFINE, HERMITE,  */
+/* KICK2, CLOSE (last = 1 on its last step). With encounters off the         */
+/* SEARCH, REFINE and HERMITE phases do nothing. Arrays of the state are     */
+/* structure-of-arrays [3][rows] (v: barycentric), per-row arrays [rows];    */
+/* qym_split_arrays gives their device addresses (valid until               */
+/* qym_destroy) and the context's stream, on which every phase enqueues its  */
+/* work: exchanges must be ordered after it. The Kepler solve log            */
+/* (qym_set_kepler_log) is not available on a split context. Results equal   */
+/* those of qym_step on one GPU to rounding: the kick of a row sums the same  */
+/* partial slots in the same order, and only which sets take thread-block     */
+/* clusters in the Hermite (hence a set's summation order) can differ.       */
+/* ------------------------------------------------------------------------ */
+#define QYM_PHASE_OPEN    0
+#define QYM_PHASE_KICK1   1
+#define QYM_PHASE_SEARCH  2
+#define QYM_PHASE_KEPLER  3
+#define QYM_PHASE_REFINE  4
+#define QYM_PHASE_HERMITE 5
+#define QYM_PHASE_KICK2   6
+#define QYM_PHASE_CLOSE   7
+
+typedef struct qym_split_view {
+    int64_t rows, own_lo, own_hi;  /* all rows; the own rows [own_lo, own_hi) */
+    double *q, *v;                 /* [3][rows] state (v after the first kick in REFINE) */
+    double *q1, *v1;               /* [3][rows] Kepler result / Hermite result */
+    double *rH;                    /* [rows] Hill radii of the step */
+    float *amag;                   /* [rows] |a| of the last kick (sizes the next search) */
+    int32_t *hcost;                /* [rows] Hermite block steps of each row's set */
+    int32_t *enc;                  /* [max_enc][2] encounter pairs (i < j) */
+    int64_t max_enc;
+    int32_t *set_mem;              /* members of the encounter sets, set by set */
+    void *stream;                  /* the context's cudaStream_t */
+} qym_split_view;
+
+/* The block of bodies of context `rank` of `world` over a system of `rows`
+ * rows (star at row 0): rows [*lo, *hi), possibly empty. */
+void qym_split_rows(int64_t rows, int32_t rank, int32_t world, int64_t *lo, int64_t *hi);
+
+/* Make ctx (one system; no Kepler solve log) context `rank` of `world`. The
+ * kick items are rebuilt for the own rows; the next phase OPEN starts a run. */
+qym_status qym_split_init(qym_ctx *ctx, int32_t rank, int32_t world);
+
+/* Enqueue one phase (QYM_PHASE_*) of a step of size tau; last marks the run's
+ * last step (CLOSE). QYM_EINVAL for an unknown phase or a context that is
+ * not split; CLOSE with last = 1 returns the run's status. */
+qym_status qym_split_phase(qym_ctx *ctx, int32_t phase, double tau, int32_t last);
+
+qym_status qym_split_arrays(qym_ctx *ctx, qym_split_view *view);
+
+/* Pairs the own rigorous test found this step (waits for the device). */
+qym_status qym_split_encounter_count(qym_ctx *ctx, int64_t *n);
+
+/* This step's encounter pairs from every context (device int32[n][2], i < j):
+ * they replace the list and become the step's records (qym_get_encounters). */
+qym_status qym_split_import_encounters(qym_ctx *ctx, const int32_t *pairs, int64_t n);
+
+/* After HERMITE: the members of the own sets are set_mem[*first .. *first +
+ * *count) (waits for the device). */
+qym_status qym_split_owned_members(qym_ctx *ctx, int64_t *first, int64_t *count);
+
+/* ------------------------------------------------------------------------ */
 /* Measurement                                                              */
 /* ------------------------------------------------------------------------ */
 

@@ -676,9 +676,10 @@ int64_t or_encounters_near(int64_t rows, const double *q0, const double *v0, con
 }
 
 /* rigorous test of selected rows i against all j != i (sampled parity) */
-int64_t or_encounters_rows(int64_t rows, const double *q0, const double *v0, const double *q1,
-                           const double *v1, const double *rH, double tau, double a_E, int64_t nsel,
-                           const int64_t *sel, int64_t *pairs, double *d2, double *thr2, int64_t cap)
+static int64_t enc_rows_serial(int64_t rows, const double *q0, const double *v0, const double *q1,
+                               const double *v1, const double *rH, double tau, double a_E,
+                               int64_t nsel, const int64_t *sel, int64_t *pairs, double *d2,
+                               double *thr2, int64_t cap)
 {
     int64_t cnt = 0;
     for (int64_t s = 0; s < nsel; ++s) {
@@ -702,6 +703,32 @@ int64_t or_encounters_rows(int64_t rows, const double *q0, const double *v0, con
         }
     }
     return cnt;
+}
+
+int64_t or_encounters_rows(int64_t rows, const double *q0, const double *v0, const double *q1,
+                           const double *v1, const double *rH, double tau, double a_E, int64_t nsel,
+                           const int64_t *sel, int64_t *pairs, double *d2, double *thr2, int64_t cap)
+{
+    if (g_threads <= 1 || nsel < 2)
+        return enc_rows_serial(rows, q0, v0, q1, v1, rH, tau, a_E, nsel, sel, pairs, d2, thr2, cap);
+    /* several threads: each selected row counted, then written at its offset
+     * (the same pairs in the same order as one thread) */
+    int64_t *off = (int64_t *)calloc(nsel + 1, sizeof(int64_t));
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
+    for (int64_t s = 0; s < nsel; ++s)
+        off[s + 1] = enc_rows_serial(rows, q0, v0, q1, v1, rH, tau, a_E, 1, sel + s, NULL, NULL,
+                                     NULL, 0);
+    for (int64_t s = 0; s < nsel; ++s) off[s + 1] += off[s];
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
+    for (int64_t s = 0; s < nsel; ++s) {
+        int64_t room = cap - off[s];
+        if (room <= 0) continue;
+        enc_rows_serial(rows, q0, v0, q1, v1, rH, tau, a_E, 1, sel + s, pairs + 2 * off[s],
+                        d2 ? d2 + off[s] : NULL, thr2 ? thr2 + off[s] : NULL, room);
+    }
+    int64_t total = off[nsel];
+    free(off);
+    return total;
 }
 
 /* ------------------------------------------------------------------ */

@@ -28,6 +28,8 @@ QYM_SOLVER_LAGUERRE, QYM_SOLVER_NEWTON = 0, 1
 QYM_GUESS_STANDARD, QYM_GUESS_R0, QYM_GUESS_MLP = 0, 1, 2
 QYM_STATIC_MAX_ROWS = 32768
 QYM_MLP_NW = 4555
+(QYM_PHASE_OPEN, QYM_PHASE_KICK1, QYM_PHASE_SEARCH, QYM_PHASE_KEPLER, QYM_PHASE_REFINE,
+ QYM_PHASE_HERMITE, QYM_PHASE_KICK2, QYM_PHASE_CLOSE) = range(8)
 
 
 class QymError(RuntimeError):
@@ -58,6 +60,14 @@ class qym_stats(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class qym_split_view(C.Structure):
+    _fields_ = [("rows", C.c_int64), ("own_lo", C.c_int64), ("own_hi", C.c_int64),
+                ("q", C.c_void_p), ("v", C.c_void_p), ("q1", C.c_void_p), ("v1", C.c_void_p),
+                ("rH", C.c_void_p), ("amag", C.c_void_p), ("hcost", C.c_void_p),
+                ("enc", C.c_void_p), ("max_enc", C.c_int64), ("set_mem", C.c_void_p),
+                ("stream", C.c_void_p)]
 
 
 _lib = None
@@ -102,6 +112,14 @@ def lib():
     L.qym_set_kepler_log.argtypes = [P, P, C.c_int64]
     L.qym_set_encounter_snapshot.argtypes = [P, P, P, P, P, P]
     L.qym_probe_fma.argtypes = [C.c_int32, C.c_int64, C.c_int32, D, D, P]
+    L.qym_split_rows.argtypes = [C.c_int64, C.c_int32, C.c_int32, I64, I64]
+    L.qym_split_rows.restype = None
+    L.qym_split_init.argtypes = [P, C.c_int32, C.c_int32]
+    L.qym_split_phase.argtypes = [P, C.c_int32, C.c_double, C.c_int32]
+    L.qym_split_arrays.argtypes = [P, C.POINTER(qym_split_view)]
+    L.qym_split_encounter_count.argtypes = [P, I64]
+    L.qym_split_import_encounters.argtypes = [P, P, C.c_int64]
+    L.qym_split_owned_members.argtypes = [P, I64, I64]
     L.qym_transition_dev.argtypes = [C.c_int64, P, C.c_double, P, P, P, P]
     L.qym_mlp_workspace_bytes.argtypes = []
     L.qym_mlp_workspace_bytes.restype = C.c_size_t
@@ -132,7 +150,10 @@ def lib():
                  "qym_kepler_drift_dev", "qym_accel_dev", "qym_encounter_test_dev",
                  "qym_energy_dev", "qym_set_kepler_log", "qym_mlp_forward_dev",
                  "qym_mlp_grad_dev", "qym_mlp_adam_dev", "qym_mlp_train_dev",
-                 "qym_transition_dev", "qym_set_encounter_snapshot", "qym_probe_fma"):
+                 "qym_transition_dev", "qym_set_encounter_snapshot", "qym_probe_fma",
+                 "qym_split_init", "qym_split_phase", "qym_split_arrays",
+                 "qym_split_encounter_count", "qym_split_import_encounters",
+                 "qym_split_owned_members"):
         getattr(L, name).restype = S
     _lib = L
     return L

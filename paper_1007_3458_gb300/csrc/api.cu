@@ -64,6 +64,10 @@ struct qym_ctx {
     // caller's device arrays receiving the encounter test's inputs of the
     // last step of each qym_step call (q0, v0, q1, v1 [3][rows], rH [rows])
     double *snap[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // the step of one system split over several GPUs (qym_split_*)
+    int32_t split_rank = 0, split_world = 0;  // world 0: not split
+    bool split_fresh = false;   // this run's first kick has no |a| of an earlier one
+    int64_t *owned_info = nullptr;  // device [2]: first member and count of the own sets
 };
 
 #define FAIL(ctx, code, msg)                         \
@@ -176,6 +180,7 @@ static void carve_all(qym_ctx *c, Carver &k) {
     d.set_start = k.take<int32_t>((size_t)d.max_sets + 1);
     d.set_mem = k.take<int32_t>(d.max_members);
     d.rcrit = k.take<double>(d.max_sets);
+    d.set_root = k.take<int32_t>(d.max_sets);
     d.hcost = k.take<int32_t>(R);
     d.hq = k.take<int32_t>(d.max_sets);
     d.hsetcost = k.take<int32_t>(d.max_sets);
@@ -198,6 +203,7 @@ static void carve_all(qym_ctx *c, Carver &k) {
     c->mlp_w = k.take<float>(QYM_MLP_NW);
     c->klog_base = k.take<unsigned long long>(1);
     c->hflag = k.take<int32_t>(1);
+    c->owned_info = k.take<int64_t>(2);
 }
 
 // The caller's rows [R][3] <-> the device's [3][R]. The transposes run on the
@@ -667,7 +673,7 @@ static qym_status collect(qym_ctx *c, int64_t nsteps) {
     CK(c, cudaMemcpyAsync(&status, d.status, sizeof(status), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     qym_stats &s = c->stats;
-    s.steps = nsteps;
+    s.steps = nsteps ? nsteps : (int64_t)ctr[C_STEP];  // 0: a split run counts its own
     s.candidates = (int64_t)ctr[C_SUM_CAND];
     s.encounters = (int64_t)ctr[C_SUM_ENC];
     s.sets = (int64_t)ctr[C_SUM_SETS];
@@ -872,6 +878,243 @@ extern "C" qym_status qym_set_kepler_log(qym_ctx *c, float *rows, int64_t cap) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
     }
+    return QYM_OK;
+}
+
+static qym_status apply_tune(qym_ctx *c, const KickTune &t);
+
+// ------------------------------------------------------------------ split step
+// One system's step over several GPUs: every GPU holds the whole state, and
+// computes the kick of its own contiguous block of rows against all rows
+// (with the crude search of those rows), their kick finish and Kepler drift,
+// the rigorous test of their candidates and the Hermite of the encounter sets
+// whose lowest row is its own; the caller exchanges the results between the
+// phases (qym_split_phase). Everything else (momentum, drifts, packs, the
+// encounter sets) is computed on every GPU from identical data in a fixed
+// order, so it agrees to the bit without a collective.
+
+__global__ void k_owned_members(Dev d, int64_t *info) {
+    // first member (in set_mem) and member count of the sets rooted in
+    // [own_lo, own_hi); sets are numbered by their lowest row
+    const int nall = (int)min((unsigned long long)d.max_sets, d.ctr[C_NSETS]);
+    int a = 0, b = nall;
+    while (a < b) { const int m = (a + b) >> 1; if (d.set_root[m] < d.own_lo) a = m + 1; else b = m; }
+    const int lo = a;
+    b = nall;
+    while (a < b) { const int m = (a + b) >> 1; if (d.set_root[m] < d.own_hi) a = m + 1; else b = m; }
+    const int hi = a;
+    info[0] = lo < nall ? d.set_start[lo] : 0;
+    info[1] = (lo < hi) ? (int64_t)d.set_start[hi] - d.set_start[lo] : 0;
+}
+
+// the gathered encounter pairs of every GPU become this step's list, and its
+// records (step, i, j)
+__global__ void k_import_encounters(Dev d, const int2 *pairs, int64_t n) {
+    const int64_t cap = min(n, d.max_enc);
+    const unsigned long long step = d.ctr[C_STEP];
+    const unsigned long long l0 = d.ctr[C_LOG];
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int2 p = pairs[k];
+        if (k < cap) d.enc[k] = p;
+        const unsigned long long l = l0 + (unsigned long long)k;
+        if (l < (unsigned long long)d.max_log) {
+            d.log[3 * l] = (int64_t)step;
+            d.log[3 * l + 1] = p.x;
+            d.log[3 * l + 2] = p.y;
+        }
+    }
+}
+
+__global__ void k_import_count(Dev d, int64_t n) {
+    d.ctr[C_NENC] = (unsigned long long)n;
+    if (n > d.max_enc) atomicOr(d.status, QYM_ST_ENC_OVERFLOW);
+    const unsigned long long l = d.ctr[C_LOG] + (unsigned long long)n;
+    if (l > (unsigned long long)d.max_log) atomicOr(d.status, QYM_ST_LOG_OVERFLOW);
+    d.ctr[C_LOG] = l;
+}
+
+extern "C" qym_status qym_split_init(qym_ctx *c, int32_t rank, int32_t world) {
+    if (!c) FAIL(nullptr, QYM_EINVAL, "qym_split_init: NULL context");
+    if (c->d.nsys != 1) FAIL(c, QYM_EINVAL, "qym_split_init: one system per context");
+    if (world < 1 || rank < 0 || rank >= world) FAIL(c, QYM_EINVAL, "qym_split_init: bad rank or world");
+    if (c->klog) FAIL(c, QYM_EINVAL, "qym_split_init: the Kepler solve log is not split");
+    int64_t lo = 0, hi = 0;
+    qym_split_rows(c->d.rows, rank, world, &lo, &hi);
+    Dev &d = c->d;
+    d.own_lo = lo;
+    d.own_hi = hi;
+    if (hi <= lo) d.own_hi = d.own_lo = d.rows;  // nothing of its own: past the last row
+    d.log_refine = 0;
+    c->split_rank = rank;
+    c->split_world = world;
+    c->amag_valid = false;
+    qym_status st = apply_tune(c, c->tune);
+    if (st != QYM_OK) return st;
+    return QYM_OK;
+}
+
+extern "C" void qym_split_rows(int64_t rows, int32_t rank, int32_t world, int64_t *lo, int64_t *hi) {
+    // the bodies (rows 1 .. rows-1) in contiguous blocks of equal size, the
+    // last one shorter
+    const int64_t nb = rows - 1;
+    const int64_t blk = world > 0 ? (nb + world - 1) / world : nb;
+    int64_t a = 1 + (int64_t)rank * blk, b = a + blk;
+    if (a > rows) a = rows;
+    if (b > rows) b = rows;
+    if (lo) *lo = a;
+    if (hi) *hi = b;
+}
+
+extern "C" qym_status qym_split_phase(qym_ctx *c, int32_t phase, double tau, int32_t last) {
+    if (!c) FAIL(nullptr, QYM_EINVAL, "qym_split_phase: NULL context");
+    if (!c->split_world) FAIL(c, QYM_EINVAL, "qym_split_phase: qym_split_init first");
+    if (!(tau != 0.0) || !std::isfinite(tau)) FAIL(c, QYM_EINVAL, "qym_split_phase: bad tau");
+    Dev &d = c->d;
+    const qym_params &p = c->p;
+    cudaStream_t st = c->stream;
+    const int enc = p.encounters;
+    CK(c, cudaSetDevice(p.device));
+    switch (phase) {
+    case QYM_PHASE_OPEN: {
+        if (p.guess == QYM_GUESS_MLP && !c->mlp_set)
+            FAIL(c, QYM_EINVAL, "qym_split_phase: QYM_GUESS_MLP needs a network (qym_set_mlp)");
+        CK(c, cudaMemsetAsync(d.ctr, 0, sizeof(unsigned long long) * C_COUNT, st));
+        CK(c, cudaMemsetAsync(d.status, 0, sizeof(int32_t), st));
+        c->split_fresh = !c->amag_valid;
+        c->amag_valid = true;
+        c->launches = 0;
+        CK(c, launch_momentum(d, st));
+        CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.5 * tau, tau, p.a_E, p.G,
+                                     enc && !c->split_fresh, p.hill_fixed, st, 0.5 * tau));
+        c->launches += 3;
+        break;
+    }
+    case QYM_PHASE_KICK1: {
+        k_step_begin<<<1, 1, 0, st>>>(d.ctr);
+        const int flag = (enc && !c->split_fresh) ? KICK_SEARCH : KICK_FORCE;
+        CK(c, launch_kick_tiles(d, p.kick_prec, flag, p.G, c->tune.threads, c->tune.ipt, st));
+        CK(c, launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, flag == KICK_SEARCH, p.hill_fixed, st));
+        c->launches += 3 + search_retest(p, flag == KICK_SEARCH);
+        break;
+    }
+    case QYM_PHASE_SEARCH: {
+        // after a first kick without the search: the reaches from the kicked
+        // state of every row, then the search of the own rows alone
+        if (enc && c->split_fresh) {
+            CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.0, 0.5 * tau, p.a_E, p.G, 2,
+                                         p.hill_fixed, st, 0.0));
+            CK(c, launch_kick_tiles(d, p.kick_prec, KICK_SEARCH_ONLY, p.G, c->tune.threads,
+                                    c->tune.ipt, st));
+            c->launches += 2 + search_retest(p, 1);
+        }
+        c->split_fresh = false;
+        break;
+    }
+    case QYM_PHASE_KEPLER: {
+        KeplerArgs ka = step_kepler_args(c, tau);
+        ka.n = d.own_hi - d.own_lo;
+        ka.row0 = d.own_lo;
+        ka.log = nullptr;
+        CK(c, launch_kepler(ka, st));
+        c->launches += 1;
+        break;
+    }
+    case QYM_PHASE_REFINE: {
+        if (enc) {
+            CK(c, launch_refine(d, tau, p.a_E, st));
+            c->launches += 2;
+        }
+        break;
+    }
+    case QYM_PHASE_HERMITE: {
+        if (enc) {
+            CK(c, launch_sets_impl(d, p.a_H, c->ss, st));
+            CK(c, launch_hermite(d, p, tau, st));
+            k_owned_members<<<1, 1, 0, st>>>(d, c->owned_info);
+            CK(c, cudaGetLastError());
+            c->launches += 12;
+        }
+        break;
+    }
+    case QYM_PHASE_KICK2: {
+        CK(c, launch_drift_pack_from(d, d.q1, d.v1, 0.0, 0.0, tau, p.a_E, p.G, 0, p.hill_fixed, st,
+                                     0.5 * tau));
+        CK(c, launch_kick_tiles(d, p.kick_prec, KICK_FORCE, p.G, c->tune.threads, c->tune.ipt, st));
+        CK(c, launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, 0, p.hill_fixed, st));
+        c->launches += 3;
+        break;
+    }
+    case QYM_PHASE_CLOSE: {
+        CK(c, launch_momentum(d, st));
+        CK(c, launch_drift_pack_from(d, d.q, d.v, 0.5 * tau, last ? 0.0 : 0.5 * tau, tau, p.a_E,
+                                     p.G, (!last) && enc, p.hill_fixed, st, 0.5 * tau));
+        k_step_end<<<1, 1, 0, st>>>(d.ctr, d.max_cand, d.max_enc);
+        CK(c, cudaGetLastError());
+        c->launches += 4;
+        if (last) return collect(c, (int64_t)0);
+        break;
+    }
+    default:
+        FAIL(c, QYM_EINVAL, "qym_split_phase: unknown phase");
+    }
+    CK(c, cudaGetLastError());
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_split_arrays(qym_ctx *c, qym_split_view *view) {
+    if (!c || !view) FAIL(c, QYM_EINVAL, "qym_split_arrays: NULL argument");
+    const Dev &d = c->d;
+    view->rows = d.rows;
+    view->own_lo = d.own_hi > 0 ? d.own_lo : 0;
+    view->own_hi = d.own_hi > 0 ? d.own_hi : d.rows;
+    view->q = d.q;
+    view->v = d.v;
+    view->q1 = d.q1;
+    view->v1 = d.v1;
+    view->rH = d.rH;
+    view->amag = d.amag;
+    view->hcost = d.hcost;
+    view->enc = (int32_t *)d.enc;
+    view->max_enc = d.max_enc;
+    view->set_mem = d.set_mem;
+    view->stream = (void *)c->stream;
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_split_encounter_count(qym_ctx *c, int64_t *n) {
+    if (!c || !n) FAIL(c, QYM_EINVAL, "qym_split_encounter_count: NULL argument");
+    unsigned long long k = 0;
+    CK(c, cudaMemcpyAsync(&k, c->d.ctr + C_NENC, sizeof(k), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (k > (unsigned long long)c->d.max_enc) FAIL(c, QYM_EOVERFLOW, "encounter capacity exceeded");
+    *n = (int64_t)k;
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_split_import_encounters(qym_ctx *c, const int32_t *pairs, int64_t n) {
+    if (!c || n < 0 || (n > 0 && !pairs)) FAIL(c, QYM_EINVAL, "qym_split_import_encounters: bad argument");
+    if (!c->split_world) FAIL(c, QYM_EINVAL, "qym_split_import_encounters: qym_split_init first");
+    cudaStream_t st = c->stream;
+    if (n > 0) {
+        k_import_encounters<<<64, 256, 0, st>>>(c->d, (const int2 *)pairs, n);
+        CK(c, cudaGetLastError());
+    }
+    k_import_count<<<1, 1, 0, st>>>(c->d, n);
+    CK(c, cudaGetLastError());
+    c->launches += 1 + (n > 0);
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_split_owned_members(qym_ctx *c, int64_t *first, int64_t *count) {
+    if (!c || !first || !count) FAIL(c, QYM_EINVAL, "qym_split_owned_members: NULL argument");
+    int64_t info[2] = {0, 0};
+    if (c->p.encounters) {
+        CK(c, cudaMemcpyAsync(info, c->owned_info, sizeof(info), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    *first = info[0];
+    *count = info[1];
     return QYM_OK;
 }
 
@@ -1109,14 +1352,18 @@ extern "C" qym_status qym_time_kick(qym_ctx *c, int32_t with_search, int32_t rep
 // largest item count and split count seen so far are reused when they fit)
 static qym_status apply_tune(qym_ctx *c, const KickTune &t) {
     Dev &d = c->d;
-    int32_t n = kick_items_count(c->h_offsets.data(), d.nsys, t);
+    const int64_t ilo = d.own_hi > 0 ? d.own_lo : 0, ihi = d.own_hi > 0 ? d.own_hi : INT64_MAX;
+    int32_t n = kick_items_count(c->h_offsets.data(), d.nsys, t, ilo, ihi);
     if (n > c->items_cap || t.splits > c->splits_cap) FAIL(c, QYM_EINVAL, "launch shape exceeds the item buffers");
-    std::vector<int4> items(n);
-    std::vector<int32_t> slots(n);
+    std::vector<int4> items(n ? n : 1);
+    std::vector<int32_t> slots(n ? n : 1);
     int32_t ni = 0, spu = 0;
-    kick_items_host(c->h_offsets.data(), d.nsys, t, items.data(), slots.data(), &ni, &spu, n);
-    CK(c, cudaMemcpyAsync(d.items, items.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, c->stream));
-    CK(c, cudaMemcpyAsync(d.item_slot, slots.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
+    kick_items_host(c->h_offsets.data(), d.nsys, t, items.data(), slots.data(), &ni, &spu, n, ilo,
+                    ihi);
+    if (n) {
+        CK(c, cudaMemcpyAsync(d.items, items.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(d.item_slot, slots.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
+    }
     CK(c, cudaStreamSynchronize(c->stream));
     d.nitems = n;
     d.splits = t.splits;

@@ -98,6 +98,7 @@ __device__ __forceinline__ void push_encounter(const Dev &d, int i, int j) {
         d.enc[k] = make_int2(i, j);
     else
         atomicOr(d.status, QYM_ST_ENC_OVERFLOW);
+    if (!d.log_refine) return;
     unsigned long long l = atomicAdd(d.ctr + C_LOG, 1ull);
     if (l < (unsigned long long)d.max_log) {
         d.log[3 * l] = (int64_t)d.ctr[C_STEP];
@@ -251,6 +252,7 @@ __global__ void __launch_bounds__(1024) k_uf_number(Dev d, const int32_t *blk, i
         int s = blk[blockIdx.x] + before;
         sid[r] = s;
         size[s] = 0;
+        if (s < d.max_sets) d.set_root[s] = (int32_t)r;
     }
 }
 

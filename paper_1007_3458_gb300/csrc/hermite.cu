@@ -1048,17 +1048,40 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
 // One CTA of 1024 threads; the sets are ordered by a bitonic sort of 64-bit
 // keys in shared memory.
 constexpr int kPlanCap = 4096;
+// When a system's step is split over several GPUs (own_hi > 0) this context
+// integrates only the sets whose lowest row is its own: sets are numbered in
+// the order of their lowest rows, so those are the index range [s_lo, s_hi).
 __global__ void __launch_bounds__(1024) k_hermite_plan(Dev d, int ncl) {
     __shared__ unsigned long long key[kPlanCap];
     __shared__ int wsum[32];
+    __shared__ int s_range[2];
     const int tid = threadIdx.x;
-    const int nsets = (int)min((unsigned long long)d.max_sets, d.ctr[C_NSETS]);
+    const int nall = (int)min((unsigned long long)d.max_sets, d.ctr[C_NSETS]);
+    if (tid == 0) {
+        int lo = 0, hi = nall;
+        if (d.own_hi > 0) {
+            // first set whose root is >= own_lo, and >= own_hi (roots ascend)
+            int a = 0, b = nall;
+            while (a < b) { const int m = (a + b) >> 1; if (d.set_root[m] < d.own_lo) a = m + 1; else b = m; }
+            lo = a;
+            b = nall;
+            while (a < b) { const int m = (a + b) >> 1; if (d.set_root[m] < d.own_hi) a = m + 1; else b = m; }
+            hi = a;
+        }
+        s_range[0] = lo;
+        s_range[1] = hi;
+    }
+    __syncthreads();
+    const int s_lo = s_range[0];
+    const int nsets = s_range[1] - s_lo;
     if (ncl > kHermMaxClusters) ncl = kHermMaxClusters;
     for (int c = tid; c < kHermMaxClusters; c += blockDim.x) d.hcl[c] = -1;
+    for (int k = tid; k < nall; k += blockDim.x)
+        if (k < s_lo || k >= s_lo + nsets) d.hsetcost[k] = 0;
     if (nsets > kPlanCap) {
         for (int k = tid; k < nsets; k += blockDim.x) {
-            d.hq[k] = k;
-            d.hsetcost[k] = 0;
+            d.hq[k] = s_lo + k;
+            d.hsetcost[s_lo + k] = 0;
         }
         if (tid == 0) d.ctr[C_HNQ] = (unsigned long long)nsets;
         return;
@@ -1066,12 +1089,14 @@ __global__ void __launch_bounds__(1024) k_hermite_plan(Dev d, int ncl) {
     int P = 1;
     while (P < nsets) P <<= 1;
     // key: predicted cost (31 bits) | members (16 bits) | 0xffff - set index
+    // (set indices relative to s_lo)
     for (int k = tid; k < P; k += blockDim.x) {
         unsigned long long kk = 0;
         if (k < nsets) {
-            const int n = d.set_start[k + 1] - d.set_start[k];
-            const int cost = d.hsetcost[k];
-            d.hsetcost[k] = 0;
+            const int sk = s_lo + k;
+            const int n = d.set_start[sk + 1] - d.set_start[sk];
+            const int cost = d.hsetcost[sk];
+            d.hsetcost[sk] = 0;
             kk = ((unsigned long long)min(max(cost, 0), 0x7fffffff) << 32) |
                  ((unsigned long long)min(max(n, 0), 0xffff) << 16) | (unsigned long long)(0xffff - k);
         }
@@ -1121,7 +1146,7 @@ __global__ void __launch_bounds__(1024) k_hermite_plan(Dev d, int ncl) {
     for (int i = 0; i < PER; ++i) {
         const int k = k0 + i;
         if (k >= nsets) break;
-        const int set = 0xffff - (int)(key[k] & 0xffff);
+        const int set = s_lo + 0xffff - (int)(key[k] & 0xffff);
         if (e[i] && before < ncl) {
             d.hcl[before] = set;
         } else {
@@ -1152,6 +1177,16 @@ __global__ void __cluster_dims__(CLT, 1, 1) __launch_bounds__(HTHREADS, 2) k_her
         if (k >= nq) break;
         hermite_set<false, 2>(d, h, d.hq[k], 0, 1);
     }
+}
+
+// every member of every set leaves the union-find (-1) and, when this context
+// integrated only its own sets, the other sets' members get their states and
+// costs from the GPUs that did
+__global__ void k_uf_clear_members(Dev d) {
+    const unsigned long long n = min(d.ctr[C_NMEM], (unsigned long long)d.max_members);
+    for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (unsigned long long)gridDim.x * blockDim.x)
+        d.uf[d.set_mem[k]] = -1;
 }
 
 cudaError_t hermite_prepare() {
@@ -1203,6 +1238,9 @@ cudaError_t launch_hermite(const Dev &d, const qym_params &p, double tau, cudaSt
     case 4: k_hermite<4><<<grid, HTHREADS, kHermSmem, st>>>(d, h); break;
     default: k_hermite<8><<<grid, HTHREADS, kHermSmem, st>>>(d, h); break;
     }
+    e = cudaGetLastError();
+    if (e != cudaSuccess || d.own_hi == 0) return e;
+    k_uf_clear_members<<<152, 256, 0, st>>>(d);
     return cudaGetLastError();
 }
 

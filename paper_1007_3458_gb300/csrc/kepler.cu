@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int iters = 0;
     const bool act = k < a.n;
-    const int64_t r = act ? (a.rows ? a.rows[k] : k) : 0;
+    const int64_t r = act ? (a.rows ? a.rows[k] : a.row0 + k) : 0;
     const int64_t ld = a.ld;
     double qx = 0.0, qy = 0.0, qz = 0.0, vx = 0.0, vy = 0.0, vz = 0.0, mu = 1.0;
     if (act) {

@@ -347,27 +347,36 @@ __global__ void __launch_bounds__(256) k_kick_fp64(KickArgs a) {
 // Items for a batch: for each system (bodies are rows lo+1 .. hi-1), i-blocks
 // of threads*ipt rows times `splits` contiguous j-ranges. Every (i-block,
 // split) pair gets an item, even when its j-range is empty, so every slot of
-// every row is written.
-int32_t kick_items_count(const int64_t *offsets, int32_t nsys, const KickTune &t) {
+// every row is written. Only rows in [i_lo, i_hi) get i-blocks (a rank's own
+// rows when a system's step is split over several GPUs); the j-ranges always
+// cover the whole system, so a row's partial sums do not depend on the range.
+static int64_t items_i_begin(int64_t b0, int64_t i_lo) { return b0 > i_lo ? b0 : i_lo; }
+static int64_t items_i_end(int64_t b1, int64_t i_hi) { return b1 < i_hi ? b1 : i_hi; }
+
+int32_t kick_items_count(const int64_t *offsets, int32_t nsys, const KickTune &t, int64_t i_lo,
+                         int64_t i_hi) {
     int64_t tot = 0;
     const int64_t ti = (int64_t)t.threads * t.ipt;
     for (int32_t s = 0; s < nsys; ++s) {
-        int64_t nb = offsets[s + 1] - offsets[s] - 1;
-        tot += ((nb + ti - 1) / ti) * t.splits;
+        const int64_t a = items_i_begin(offsets[s] + 1, i_lo), b = items_i_end(offsets[s + 1], i_hi);
+        const int64_t nb = b - a;
+        if (nb > 0) tot += ((nb + ti - 1) / ti) * t.splits;
     }
     return (int32_t)tot;
 }
 
 void kick_items_host(const int64_t *offsets, int32_t nsys, const KickTune &t, int4 *items,
-                     int32_t *slots, int32_t *nitems, int32_t *splits_used, int32_t max_items) {
+                     int32_t *slots, int32_t *nitems, int32_t *splits_used, int32_t max_items,
+                     int64_t i_lo, int64_t i_hi) {
     const int64_t ti = (int64_t)t.threads * t.ipt;
     int32_t n = 0;
     for (int32_t s = 0; s < nsys; ++s) {
         int64_t b0 = offsets[s] + 1, b1 = offsets[s + 1];
         int64_t nb = b1 - b0;
         int64_t chunk = (nb + t.splits - 1) / t.splits;
-        for (int64_t i0 = b0; i0 < b1; i0 += ti) {
-            int64_t i1 = i0 + ti < b1 ? i0 + ti : b1;
+        const int64_t ia = items_i_begin(b0, i_lo), ib = items_i_end(b1, i_hi);
+        for (int64_t i0 = ia; i0 < ib; i0 += ti) {
+            int64_t i1 = i0 + ti < ib ? i0 + ti : ib;
             for (int32_t sp = 0; sp < t.splits; ++sp) {
                 int64_t j0 = b0 + sp * chunk, j1 = j0 + chunk;
                 if (j0 > b1) j0 = b1;

@@ -76,6 +76,13 @@ struct Dev {
     // counters (device): see Counters below
     unsigned long long *ctr = nullptr;
     int32_t *status = nullptr;    // QYM_ST_* bits
+    // a system's step split over several GPUs: this context computes the
+    // rows [own_lo, own_hi) (kick rows, finisher, Kepler drift, the
+    // candidates of those rows, the Hermite of the sets whose lowest row is
+    // among them); own_hi = 0: every row
+    int64_t own_lo = 0, own_hi = 0;
+    int32_t *set_root = nullptr;  // [max_sets] lowest row of each set (sets are numbered by it)
+    int32_t log_refine = 1;       // the rigorous test logs its pairs (0: the split's import does)
 };
 
 // device counters, indices into Dev::ctr
@@ -169,7 +176,8 @@ struct KeplerArgs {
     const double *q0, *v0; // [3][ld] inputs
     double *q1, *v1;       // [3][ld] outputs
     int64_t ld;            // leading dimension (stride between x, y, z blocks)
-    const int64_t *rows;   // optional row map: body k is row rows[k]; NULL = identity
+    const int64_t *rows;   // optional row map: body k is row rows[k]; NULL: row row0 + k
+    int64_t row0;
     double mu, dt;
     int32_t solver, guess, max_iter;
     const float *mlp_w;    // guess network weights (QYM_GUESS_MLP) or NULL
@@ -237,10 +245,12 @@ cudaError_t launch_accel_single(int64_t rows, const double *m, const double *q, 
                                 double G, int prec, double heavy_mass, void *work,
                                 size_t work_bytes, cudaStream_t st);
 size_t accel_single_workspace(int64_t rows, int prec);
+// items of the i rows in [i_lo, i_hi) (default: all rows) against all j
 void kick_items_host(const int64_t *offsets, int32_t nsys, const KickTune &t,
                      int4 *items, int32_t *slots, int32_t *nitems, int32_t *splits_used,
-                     int32_t max_items);
-int32_t kick_items_count(const int64_t *offsets, int32_t nsys, const KickTune &t);
+                     int32_t max_items, int64_t i_lo = 0, int64_t i_hi = INT64_MAX);
+int32_t kick_items_count(const int64_t *offsets, int32_t nsys, const KickTune &t,
+                         int64_t i_lo = 0, int64_t i_hi = INT64_MAX);
 
 // encounter.cu
 struct SetScratch {

@@ -187,6 +187,7 @@ struct FinishArgs {
 __global__ void __launch_bounds__(256) k_finish(Dev d, FinishArgs a) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= d.rows) return;
+    if (d.own_hi > 0 && (r < d.own_lo || r >= d.own_hi)) return;  // another GPU's row
     const int sys = d.sys_of[r];
     const int64_t star = d.offsets[sys];
     if (r == star) return;

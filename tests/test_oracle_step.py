@@ -307,3 +307,19 @@ def test_threads_give_identical_results(oracle):
     assert len(a.encounters) > 0
     for f in ("q", "v", "encounters", "enc_d2", "near", "near_d2", "stats"):
         assert np.array_equal(getattr(a, f), getattr(b, f)), f
+    # the selected-rows test: the same pairs in the same order
+    q1, v1, *_ = oracle.kepler_drift(w.q[1:], v[1:], 1.0, w.tau)
+    q1 = np.concatenate([[[0.0, 0.0, 0.0]], q1])
+    v1 = np.concatenate([[[0.0, 0.0, 0.0]], v1])
+    rH = oracle.hill_radii(w.m, w.q, v)
+    sel = np.arange(1, len(w.m), 3)
+    outs = []
+    try:
+        for th in (1, 4):
+            oracle.set_threads(th)
+            outs.append(oracle.encounters_rows(w.q, v, q1, v1, rH, w.tau, 3.0, sel))
+    finally:
+        oracle.set_threads(1)
+    assert len(outs[0][0]) > 0
+    for x, y in zip(*outs):
+        assert np.array_equal(x, y)
