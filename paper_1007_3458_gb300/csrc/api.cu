@@ -68,6 +68,9 @@ struct qym_ctx {
     int32_t split_rank = 0, split_world = 0;  // world 0: not split
     bool split_fresh = false;   // this run's first kick has no |a| of an earlier one
     int64_t *owned_info = nullptr;  // device [2]: first member and count of the own sets
+    // the kick's Morton order of the bodies (one system, mixed kick)
+    bool sort_rows = false;
+    SortScratch sortw{};
 };
 
 #define FAIL(ctx, code, msg)                         \
@@ -133,6 +136,12 @@ static bool valid_params(const qym_params *p, std::string &why) {
 }
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// bodies from which a single system's kick holds them in Morton order
+constexpr int64_t kSortMinBodies = 2048;
+// steps between re-sorts inside one qym_step call (bodies drift apart slowly;
+// the order only affects speed)
+constexpr int64_t kSortEvery = 32;
 
 // ------------------------------------------------------------------ arena
 struct Carver {
@@ -204,6 +213,18 @@ static void carve_all(qym_ctx *c, Carver &k) {
     c->klog_base = k.take<unsigned long long>(1);
     c->hflag = k.take<int32_t>(1);
     c->owned_info = k.take<int64_t>(2);
+    if (c->sort_rows) {
+        d.perm = k.take<int32_t>(R);
+        d.inv = k.take<int32_t>(R);
+        c->sortw.box = k.take<int>(8);
+        c->sortw.k0 = k.take<uint32_t>(R);
+        c->sortw.k1 = k.take<uint32_t>(R);
+        c->sortw.v0 = k.take<int32_t>(R);
+        c->sortw.v1 = k.take<int32_t>(R);
+        c->sortw.hist = k.take<uint32_t>(256 * (size_t)sort_blocks(R));
+        d.far = k.take<float4>(R);
+        d.tile = k.take<float4>(3 * (size_t)((R - 1 + kKickTile - 1) / kKickTile));
+    }
 }
 
 // The caller's rows [R][3] <-> the device's [3][R]. The transposes run on the
@@ -270,6 +291,7 @@ static qym_status upload_state(qym_ctx *c, const double *q, const double *v) {
     CK(c, cudaMemcpyAsync(d.v, d.v1, sizeof(double) * 3 * R, cudaMemcpyDeviceToDevice, st));
     if (c->p.coords == 0) CK(c, launch_to_dh_impl(d, 0, nullptr, c->mt, st));
     if (c->p.hill_fixed) CK(c, launch_hill_init(d, c->p.G, st));
+    if (d.perm) CK(c, launch_sort_rows(d.rows, d.q, c->sortw, d.perm, d.inv, st));
     CK(c, cudaStreamSynchronize(st));
     c->amag_valid = false;
     return QYM_OK;
@@ -368,6 +390,9 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     c->n_heavy = (int64_t)hrows.size();
     d.heavy_split = split ? 1 : 0;
 
+    // one system of at least two tiles' worth of bodies, mixed kick: the kick
+    // holds the bodies in Morton order (sort.cu)
+    c->sort_rows = nsys == 1 && params->kick_prec == QYM_KICK_MIXED && R - 1 >= kSortMinBodies;
     Carver dry{nullptr, 0, true};
     carve_all(c, dry);
     size_t bytes = dry.off;
@@ -404,7 +429,8 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     std::vector<int4> items(d.nitems);
     std::vector<int32_t> slots(d.nitems);
     int32_t ni = 0, spu = 0;
-    kick_items_host(offsets, nsys, c->tune, items.data(), slots.data(), &ni, &spu, d.nitems);
+    kick_items_host(offsets, nsys, c->tune, items.data(), slots.data(), &ni, &spu, d.nitems, 0,
+                    INT64_MAX, c->sort_rows ? kKickTile : 1);
     std::vector<int4> eit(c->neitems);
     std::vector<int32_t> eis(c->neitems), ei0(nsys + 1);
     energy_items_host(offsets, nsys, eit.data(), eis.data(), ei0.data());
@@ -716,6 +742,11 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
         CK(c, cudaMemcpyAsync(c->klog_base, &c->klog_steps, sizeof(c->klog_steps),
                               cudaMemcpyHostToDevice, st));
     c->launches = 0;
+    if (d.perm) {
+        // the kick's order from the positions at the start of the call
+        CK(c, launch_sort_rows(d.rows, d.q, c->sortw, d.perm, d.inv, st));
+        c->launches += 16;
+    }
     // without the |a| of an earlier kick the first search runs after its kick
     const bool fresh = !c->amag_valid;
     c->amag_valid = true;  // every kick's finisher records |a|
@@ -756,6 +787,15 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
             c->g_tau = tau;
         }
         for (int64_t k = 0; k < interior; ++k) {
+            if (d.perm && k > 0 && k % kSortEvery == 0) {
+                // re-sort between steps and lay the packs of the coming kick out
+                // again in the new order (the same values: no drift)
+                CK(c, launch_sort_rows(d.rows, d.q, c->sortw, d.perm, d.inv, st));
+                CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.0, tau, p.a_E, p.G, p.encounters,
+                                             p.hill_fixed, st, p.merge_kicks ? tau : 0.5 * tau,
+                                             p.merge_kicks ? 2.0 : 1.01));
+                c->launches += 17;
+            }
             if (c->gexec) {
                 CK(c, cudaGraphLaunch(c->gexec, st));
                 c->launches += c->graph_launches;
@@ -946,6 +986,8 @@ extern "C" qym_status qym_split_init(qym_ctx *c, int32_t rank, int32_t world) {
     d.own_hi = hi;
     if (hi <= lo) d.own_hi = d.own_lo = d.rows;  // nothing of its own: past the last row
     d.log_refine = 0;
+    d.perm = d.inv = nullptr;  // the split's kick items are in row order
+    d.far = d.tile = nullptr;
     c->split_rank = rank;
     c->split_world = world;
     c->amag_valid = false;
@@ -1359,7 +1401,7 @@ static qym_status apply_tune(qym_ctx *c, const KickTune &t) {
     std::vector<int32_t> slots(n ? n : 1);
     int32_t ni = 0, spu = 0;
     kick_items_host(c->h_offsets.data(), d.nsys, t, items.data(), slots.data(), &ni, &spu, n, ilo,
-                    ihi);
+                    ihi, d.perm ? kKickTile : 1);
     if (n) {
         CK(c, cudaMemcpyAsync(d.items, items.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, c->stream));
         CK(c, cudaMemcpyAsync(d.item_slot, slots.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));

@@ -20,7 +20,7 @@
 
 namespace qym {
 
-constexpr int TILE = 256;
+constexpr int TILE = kKickTile;
 constexpr int FOLD = 64;
 #ifndef QYM_KICK_UNROLL
 #define QYM_KICK_UNROLL 4
@@ -44,7 +44,20 @@ struct KickArgs {
     int64_t max_fchunk;
     unsigned long long *nfchunk;
     int32_t *status;
+    int32_t far_tiles;      // 1: tiles far from a warp's rows take the one-add separation
+    const int32_t *perm;    // row of each position of the packs (NULL: row order)
+    const float4 *far;      // (o_x, o_y, o_z, G m): offset from the tile's reference point
+    const float4 *tile;     // per tile: (c_x, c_y, c_z, R), box min (x, y, z, -), box max
 };
+
+// a + b + c for |c| far below |a + b|, rounded once: the rounding error of
+// a + b (Knuth's two-sum) joins c before the last rounding
+__device__ __forceinline__ float ds_add(float a, float b, float c) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return __fadd_rn(s, __fadd_rn(e, c));
+}
 
 // min(a, b, c) in one instruction (the three-input form of sm_100 and later)
 __device__ __forceinline__ float fmin3(float a, float b, float c) {
@@ -132,6 +145,54 @@ __device__ __forceinline__ void mixed_chunk(const JPairs &s, int p0, int p1, int
     }
 }
 
+// The same for a tile far from every row of the warp (far_tile): the j rows
+// are held as FP32 offsets o_j = Q_j - c from the tile's reference point c
+// (two j per float4 pair: (ox0, ox1, oy0, oy1), (oz0, oz1, Gm0, Gm1)) and
+// each row as d_i = c - Q_i, formed once per tile in double-single and
+// rounded; the separation is one packed add o_j + d_i per coordinate instead
+// of three. With every pair at least the tile's radius R apart, both offsets
+// are at most about the separation, so its relative error stays a few
+// 2^-24; the rest (r^2, rsqrt, m r^-3, force, search) is the near form's.
+struct JFar {
+    float4 *a, *b, *d;  // d: the near layout's fourth float4, for -c0, -c1
+};
+
+template <int IPT, bool FLAG, bool FORCE>
+__device__ __forceinline__ void far_chunk(const JFar &s, int p0, int p1, const float2 (&dxi)[IPT],
+                                          const float2 (&dyi)[IPT], const float2 (&dzi)[IPT],
+                                          float2 (&fx)[IPT], float2 (&fy)[IPT], float2 (&fz)[IPT],
+                                          float (&mind)[IPT]) {
+#pragma unroll kPairUnroll
+    for (int p = p0; p < p1; ++p) {
+        const float4 A = s.a[p], B = s.b[p];
+        const float2 ox = make_float2(A.x, A.y), oy = make_float2(A.z, A.w);
+        const float2 oz = make_float2(B.x, B.y), gm = make_float2(B.z, B.w);
+        float2 nc = make_float2(0.0f, 0.0f);
+        if (FLAG) {
+            const float4 D = s.d[p];
+            nc = make_float2(D.z, D.w);
+        }
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            const float2 dx = __fadd2_rn(ox, dxi[k]);
+            const float2 dy = __fadd2_rn(oy, dyi[k]);
+            const float2 dz = __fadd2_rn(oz, dzi[k]);
+            const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            if (FORCE) {
+                const float2 ri = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+                const float2 sm = __fmul2_rn(__fmul2_rn(gm, ri), __fmul2_rn(ri, ri));
+                fx[k] = __ffma2_rn(sm, dx, fx[k]);
+                fy[k] = __ffma2_rn(sm, dy, fy[k]);
+                fz[k] = __ffma2_rn(sm, dz, fz[k]);
+            }
+            if (FLAG) {
+                const float2 t = __fadd2_rn(r2, nc);
+                mind[k] = fmin3(mind[k], t.x, t.y);
+            }
+        }
+    }
+}
+
 // record that row i's crude minimum over the j rows [j0, j1) fell below c_i
 // (divergent branch, warp-aggregated); k_flag_chunks re-tests them
 __device__ __forceinline__ void push_flag(const KickArgs &a, int i, int j0, int j1) {
@@ -152,7 +213,9 @@ __device__ __forceinline__ void push_flag(const KickArgs &a, int i, int j0, int 
 template <int IPT, bool FLAG, bool FORCE>
 __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
     __shared__ float4 s_a[TILE / 2], s_b[TILE / 2], s_c[TILE / 2], s_d[TILE / 2];
+    __shared__ float4 s_fa[TILE / 2], s_fb[TILE / 2];
     const JPairs sp{s_a, s_b, s_c, s_d};
+    const JFar sf{s_fa, s_fb, s_d};
     const int4 it = a.items[blockIdx.x];
     const int slot = a.slots[blockIdx.x];
     float rho[IPT];
@@ -179,23 +242,79 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
     for (int jt = it.z; jt < it.w; jt += TILE) {
         const int n = min(TILE, it.w - jt);
         const int np = (n + 1) >> 1;
-        __syncthreads();
+        const bool diag = (jt < i_hi) && (jt + n > i_lo);
+        // Far tiles (a.far_tiles: the bodies in Morton order, tiles aligned
+        // at position 1 + TILE t, their data from k_tile_prep): a warp whose
+        // every row lies at least the tile's radius R outside its box takes
+        // the one-add separation; every pair is then at least R apart,
+        // |o_j| <= R <= r and |d_i| <= 2 r, so that with o_j and d_i each
+        // rounded once the separation is within 4 2^-24 r (the row test's
+        // own rounding is within its 2% margin).
+        bool far = false;
+        float2 dxi[IPT], dyi[IPT], dzi[IPT];
+        float4 m0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (a.far_tiles && !diag) {
+            const float4 *tm = a.tile + 3 * ((jt - 1) / TILE);
+            m0 = tm[0];
+            const float4 m1 = tm[1], m2 = tm[2];
+            const float R = m0.w;
+            bool mine = true;
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                const float x = -nxh[k].x, y = -nyh[k].x, z = -nzh[k].x;
+                const float ex = fmaxf(fmaxf(m1.x - x, x - m2.x), 0.0f);
+                const float ey = fmaxf(fmaxf(m1.y - y, y - m2.y), 0.0f);
+                const float ez = fmaxf(fmaxf(m1.z - z, z - m2.z), 0.0f);
+                mine = mine && (ex * ex + ey * ey + ez * ez >= 1.02f * R * R);
+            }
+            far = __all_sync(0xffffffffu, mine);
+        }
+        // which layouts this CTA's warps need
+        const bool any_far = __syncthreads_or(far);
+        const bool any_near = __syncthreads_or(!far);
         for (int t = threadIdx.x; t < np; t += blockDim.x) {
             const int j0 = jt + 2 * t;
-            const float4 p0 = a.pos[j0], l0 = a.lo[j0];
-            // an odd tail is padded with a massless row far from everything
-            float4 p1 = make_float4(2e18f, 2e18f, 2e18f, 0.0f), l1 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (2 * t + 1 < n) {
-                p1 = a.pos[j0 + 1];
-                l1 = a.lo[j0 + 1];
+            const bool two = 2 * t + 1 < n;
+            if (any_near) {
+                const float4 p0 = a.pos[j0], l0 = a.lo[j0];
+                // an odd tail is padded with a massless row far from everything
+                float4 p1 = make_float4(2e18f, 2e18f, 2e18f, 0.0f), l1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (two) {
+                    p1 = a.pos[j0 + 1];
+                    l1 = a.lo[j0 + 1];
+                }
+                s_a[t] = make_float4(p0.x, p1.x, p0.y, p1.y);
+                s_b[t] = make_float4(p0.z, p1.z, p0.w, p1.w);
+                s_c[t] = make_float4(l0.x, l1.x, l0.y, l1.y);
+                s_d[t] = make_float4(l0.z, l1.z, -l0.w, -l1.w);
             }
-            s_a[t] = make_float4(p0.x, p1.x, p0.y, p1.y);
-            s_b[t] = make_float4(p0.z, p1.z, p0.w, p1.w);
-            s_c[t] = make_float4(l0.x, l1.x, l0.y, l1.y);
-            s_d[t] = make_float4(l0.z, l1.z, -l0.w, -l1.w);
+            if (any_far) {
+                const float4 f0 = a.far[j0];
+                float4 f1 = make_float4(2e18f, 2e18f, 2e18f, 0.0f);
+                float c1 = 0.0f;
+                if (two) {
+                    f1 = a.far[j0 + 1];
+                    c1 = a.lo[j0 + 1].w;
+                }
+                s_fa[t] = make_float4(f0.x, f1.x, f0.y, f1.y);
+                s_fb[t] = make_float4(f0.z, f1.z, f0.w, f1.w);
+                if (FLAG && !any_near) s_d[t] = make_float4(0.f, 0.f, -a.lo[j0].w, -c1);
+            }
         }
         __syncthreads();
-        const bool diag = (jt < i_hi) && (jt + n > i_lo);
+        if (far) {
+            // d_i = c - Q_i = (c - x_hi) - x_lo rounded once, duplicated for
+            // the packed form
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                const float dx = ds_add(m0.x, nxh[k].x, nxl[k].x);
+                const float dy = ds_add(m0.y, nyh[k].x, nyl[k].x);
+                const float dz = ds_add(m0.z, nzh[k].x, nzl[k].x);
+                dxi[k] = make_float2(dx, dx);
+                dyi[k] = make_float2(dy, dy);
+                dzi[k] = make_float2(dz, dz);
+            }
+        }
         for (int c = 0; c < np; c += FOLD / 2) {
             const int ce = min(c + FOLD / 2, np);
             float2 fx[IPT], fy[IPT], fz[IPT];
@@ -205,7 +324,9 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
                 fx[k] = fy[k] = fz[k] = make_float2(0.0f, 0.0f);
                 mind[k] = 3.0e38f;
             }
-            if (diag)
+            if (far)
+                far_chunk<IPT, FLAG, FORCE>(sf, c, ce, dxi, dyi, dzi, fx, fy, fz, mind);
+            else if (diag)
                 mixed_chunk<IPT, FLAG, true, FORCE>(sp, c, ce, jt, gi, nxh, nyh, nzh, nxl, nyl, nzl,
                                                     fx, fy, fz, mind);
             else
@@ -242,8 +363,10 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
 // Exact test of the flagged chunks, one warp per entry, lane l on the j rows
 // j0 + l and j0 + 32 + l: candidates (i, j), i < j, with r^2 < c_i + c_j, the
 // separation formed from the same split positions in the same order as the
-// kick forms it, so the candidate set is the kick's own. The last CTA to
-// finish resets the entry counter for the next search kick.
+// kick forms it, so the candidate set is the kick's own. Entries hold
+// positions of the packs' order (each pair once: from the smaller position);
+// candidates are rows. The last CTA to finish resets the entry counter for
+// the next search kick.
 __global__ void __launch_bounds__(256) k_flag_chunks(KickArgs a, unsigned long long *done) {
     unsigned long long n = *(volatile unsigned long long *)a.nfchunk;
     if (n > (unsigned long long)a.max_fchunk) n = a.max_fchunk;
@@ -260,7 +383,15 @@ __global__ void __launch_bounds__(256) k_flag_chunks(KickArgs a, unsigned long l
             const float dy = (pi.y - pj.y) + (li.y - lj.y);
             const float dz = (pi.z - pj.z) + (li.z - lj.z);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (r2 < li.w + lj.w) push_candidate(a, f.x, j);
+            if (r2 < li.w + lj.w) {
+                // positions of the kick's order -> rows, smaller row first
+                int ri = f.x, rj = j;
+                if (a.perm) {
+                    ri = a.perm[ri];
+                    rj = a.perm[rj];
+                }
+                push_candidate(a, min(ri, rj), max(ri, rj));
+            }
         }
     }
     __syncthreads();
@@ -367,13 +498,14 @@ int32_t kick_items_count(const int64_t *offsets, int32_t nsys, const KickTune &t
 
 void kick_items_host(const int64_t *offsets, int32_t nsys, const KickTune &t, int4 *items,
                      int32_t *slots, int32_t *nitems, int32_t *splits_used, int32_t max_items,
-                     int64_t i_lo, int64_t i_hi) {
+                     int64_t i_lo, int64_t i_hi, int32_t align) {
     const int64_t ti = (int64_t)t.threads * t.ipt;
     int32_t n = 0;
     for (int32_t s = 0; s < nsys; ++s) {
         int64_t b0 = offsets[s] + 1, b1 = offsets[s + 1];
         int64_t nb = b1 - b0;
         int64_t chunk = (nb + t.splits - 1) / t.splits;
+        chunk = (chunk + align - 1) / align * align;  // j-ranges start on tiles
         const int64_t ia = items_i_begin(b0, i_lo), ib = items_i_end(b1, i_hi);
         for (int64_t i0 = ia; i0 < ib; i0 += ti) {
             int64_t i1 = i0 + ti < ib ? i0 + ti : ib;
@@ -416,6 +548,56 @@ static cudaError_t launch_f64(const KickArgs &a, int nitems, int threads, int ip
     return cudaGetLastError();
 }
 
+// Per tile of TILE consecutive positions (from position 1; the bodies in
+// Morton order): the bounding box of the hi parts, a reference point c at its
+// middle, a radius R >= max |Q_j - c| (rounded up, with room for the lo parts
+// and the rounding of c), and each body's offset o_j = Q_j - c, rounded once
+// (two-sum of x_hi - c, then x_lo added), beside its G m.
+__global__ void __launch_bounds__(TILE) k_tile_prep(int64_t npos, const float4 *pos,
+                                                    const float4 *lo, float4 *far, float4 *tile) {
+    __shared__ float s_m[TILE / 32][6];
+    __shared__ float s_c[3];
+    const int64_t p = 1 + (int64_t)blockIdx.x * TILE + threadIdx.x;
+    const bool act = p < npos;
+    float4 P = make_float4(0.f, 0.f, 0.f, 0.f), L = P;
+    if (act) {
+        P = pos[p];
+        L = lo[p];
+    }
+    float m[6] = {act ? P.x : 3e38f, act ? P.y : 3e38f, act ? P.z : 3e38f,
+                  act ? -P.x : 3e38f, act ? -P.y : 3e38f, act ? -P.z : 3e38f};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) m[q] = warp_min(m[q]);
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < 6; ++q) s_m[threadIdx.x >> 5][q] = m[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b[6];
+        for (int q = 0; q < 6; ++q) {
+            b[q] = s_m[0][q];
+            for (int w = 1; w < TILE / 32; ++w) b[q] = fminf(b[q], s_m[w][q]);
+        }
+        float hr2 = 0.0f, big = 0.0f, c[3];
+        for (int q = 0; q < 3; ++q) {
+            const float l = b[q], h = -b[q + 3];
+            c[q] = 0.5f * (l + h);
+            const float e = fmaxf(__fsub_ru(h, c[q]), __fsub_ru(c[q], l));
+            hr2 = __fmaf_ru(e, e, hr2);
+            big = fmaxf(big, fmaxf(fabsf(l), fabsf(h)));
+            s_c[q] = c[q];
+        }
+        const float R = __fadd_ru(__fsqrt_ru(hr2), 4.0f * 1.1920929e-7f * big);
+        float4 *t = tile + 3 * blockIdx.x;
+        t[0] = make_float4(c[0], c[1], c[2], R);
+        t[1] = make_float4(b[0], b[1], b[2], 0.0f);
+        t[2] = make_float4(-b[3], -b[4], -b[5], 0.0f);
+    }
+    __syncthreads();
+    if (act)
+        far[p] = make_float4(ds_add(P.x, -s_c[0], L.x), ds_add(P.y, -s_c[1], L.y),
+                             ds_add(P.z, -s_c[2], L.z), P.w);
+}
+
 cudaError_t launch_kick_tiles(const Dev &d, int prec, int flag, double G, int threads, int ipt,
                               cudaStream_t st) {
     if (d.nitems <= 0) return cudaSuccess;
@@ -436,6 +618,16 @@ cudaError_t launch_kick_tiles(const Dev &d, int prec, int flag, double G, int th
     a.max_fchunk = d.max_fchunk;
     a.nfchunk = d.ctr + C_NFCHUNK;
     a.status = d.status;
+    a.far_tiles = (d.perm && d.far && prec == QYM_KICK_MIXED) ? 1 : 0;
+    a.perm = d.perm;
+    a.far = d.far;
+    a.tile = d.tile;
+    if (a.far_tiles) {
+        const int64_t ntiles = (d.rows - 1 + TILE - 1) / TILE;
+        k_tile_prep<<<(unsigned)ntiles, TILE, 0, st>>>(d.rows, d.pk_pos, d.pk_lo, d.far, d.tile);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     if (flag != KICK_FORCE && flag != KICK_SEARCH && flag != KICK_SEARCH_ONLY)
         return cudaErrorInvalidValue;
     if (prec == QYM_KICK_MIXED) {
@@ -462,7 +654,12 @@ struct SingleLayout {
     size_t off_pos, off_lo, off_items, off_slots, off_apart, off_heavy, total;
     int32_t nitems, splits;
     KickTune tune;
+    bool sorted;   // bodies held in Morton order (mixed kick, >= kSortMinBodies bodies)
+    size_t off_perm, off_inv, off_box, off_k0, off_k1, off_v0, off_v1, off_hist, off_far, off_tile;
 };
+
+// bodies from which a system's mixed kick holds them in Morton order (sort.cu)
+constexpr int64_t kSingleSortMin = 2048;
 
 static SingleLayout single_layout(int64_t rows, int prec) {
     SingleLayout L;
@@ -489,6 +686,21 @@ static SingleLayout single_layout(int64_t rows, int prec) {
     L.off_slots = o; o = al(o + sizeof(int32_t) * L.nitems);
     L.off_apart = o; o = al(o + sizeof(double) * 3 * rows * L.splits);
     L.off_heavy = o; o = al(o + sizeof(int32_t) * (QYM_HEAVY_CAP + 1));
+    L.sorted = prec == QYM_KICK_MIXED && nb >= kSingleSortMin;
+    L.off_perm = L.off_inv = L.off_box = L.off_k0 = L.off_k1 = L.off_v0 = L.off_v1 = L.off_hist = 0;
+    L.off_far = L.off_tile = 0;
+    if (L.sorted) {
+        L.off_perm = o; o = al(o + sizeof(int32_t) * rows);
+        L.off_inv = o; o = al(o + sizeof(int32_t) * rows);
+        L.off_box = o; o = al(o + sizeof(int) * 8);
+        L.off_k0 = o; o = al(o + sizeof(uint32_t) * rows);
+        L.off_k1 = o; o = al(o + sizeof(uint32_t) * rows);
+        L.off_v0 = o; o = al(o + sizeof(int32_t) * rows);
+        L.off_v1 = o; o = al(o + sizeof(int32_t) * rows);
+        L.off_hist = o; o = al(o + sizeof(uint32_t) * 256 * (size_t)sort_blocks(rows));
+        L.off_far = o; o = al(o + sizeof(float4) * rows);
+        L.off_tile = o; o = al(o + sizeof(float4) * 3 * (size_t)((rows - 1 + TILE - 1) / TILE));
+    }
     L.total = o;
     return L;
 }
@@ -532,9 +744,10 @@ __global__ void __launch_bounds__(1024) k_heavy_thr_single(int64_t rows, const d
 }
 
 __global__ void k_pack_single(int64_t rows, const double *m, const double *q, double G,
-                              const int32_t *hl, float4 *pos, float4 *lo) {
+                              const int32_t *hl, float4 *pos, float4 *lo, const int32_t *inv) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= rows) return;
+    const int64_t pi = inv ? inv[i] : i;  // the kick's order
     float xh, xl, yh, yl, zh, zl;
     split_ds(q[i], xh, xl);
     split_ds(q[rows + i], yh, yl);
@@ -545,16 +758,17 @@ __global__ void k_pack_single(int64_t rows, const double *m, const double *q, do
         for (int k = 0; k < nh; ++k)
             if (hl[k] == (int32_t)i) gm = 0.0f;
     }
-    pos[i] = make_float4(xh, yh, zh, gm);
-    lo[i] = make_float4(xl, yl, zl, 0.0f);
+    pos[pi] = make_float4(xh, yh, zh, gm);
+    lo[pi] = make_float4(xl, yl, zl, 0.0f);
 }
 
 __global__ void k_items_single(int64_t rows, int32_t ti, int32_t splits, int4 *items,
-                               int32_t *slots, int32_t nitems) {
+                               int32_t *slots, int32_t nitems, int32_t align) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nitems) return;
     int64_t b0 = 1, b1 = rows, nb = rows - 1;
     int64_t chunk = (nb + splits - 1) / splits;
+    chunk = (chunk + align - 1) / align * align;  // j-ranges start on tiles
     int ib = idx / splits, sp = idx % splits;
     int64_t i0 = b0 + (int64_t)ib * ti, i1 = i0 + ti < b1 ? i0 + ti : b1;
     int64_t j0 = b0 + sp * chunk, j1 = j0 + chunk;
@@ -566,13 +780,14 @@ __global__ void k_items_single(int64_t rows, int32_t ti, int32_t splits, int4 *i
 
 __global__ void k_sum_partials(int64_t rows, int32_t splits, const double *apart,
                                const int32_t *hl, const double *m, const double *q, double G,
-                               double *a) {
+                               double *a, const int32_t *inv) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= rows) return;
     double s[3] = {0.0, 0.0, 0.0};
     if (i > 0) {
+        const int64_t pi = inv ? inv[i] : i;  // the kick's order
         for (int c = 0; c < 3; ++c)
-            for (int sp = 0; sp < splits; ++sp) s[c] += apart[((int64_t)sp * 3 + c) * rows + i];
+            for (int sp = 0; sp < splits; ++sp) s[c] += apart[((int64_t)sp * 3 + c) * rows + pi];
         if (hl)
             heavy_pull(hl, hl[QYM_HEAVY_CAP], i, q[i], q[rows + i], q[2 * rows + i], q, m, rows, G,
                        s[0], s[1], s[2]);
@@ -605,11 +820,27 @@ cudaError_t launch_accel_single(int64_t rows, const double *m, const double *q, 
         hl = (int32_t *)(w + L.off_heavy);
         k_heavy_thr_single<<<1, 1024, 0, st>>>(rows, m, heavy_mass, hl);
     }
+    if (L.sorted) {
+        // the bodies in Morton order, as the step's kick holds them
+        d.perm = (int32_t *)(w + L.off_perm);
+        d.inv = (int32_t *)(w + L.off_inv);
+        d.far = (float4 *)(w + L.off_far);
+        d.tile = (float4 *)(w + L.off_tile);
+        SortScratch ss;
+        ss.box = (int *)(w + L.off_box);
+        ss.k0 = (uint32_t *)(w + L.off_k0);
+        ss.k1 = (uint32_t *)(w + L.off_k1);
+        ss.v0 = (int32_t *)(w + L.off_v0);
+        ss.v1 = (int32_t *)(w + L.off_v1);
+        ss.hist = (uint32_t *)(w + L.off_hist);
+        cudaError_t e = launch_sort_rows(rows, q, ss, d.perm, d.inv, st);
+        if (e != cudaSuccess) return e;
+    }
     k_pack_single<<<(unsigned)((rows + tb - 1) / tb), tb, 0, st>>>(rows, m, q, G, hl, d.pk_pos,
-                                                                    d.pk_lo);
+                                                                    d.pk_lo, d.inv);
     k_items_single<<<(L.nitems + tb - 1) / tb, tb, 0, st>>>(rows, L.tune.threads * L.tune.ipt,
                                                              L.splits, d.items, d.item_slot,
-                                                             L.nitems);
+                                                             L.nitems, L.sorted ? TILE : 1);
     cudaError_t e;
     if (prec == QYM_KICK_MIXED) {
         e = launch_kick_tiles(d, prec, 0, G, L.tune.threads, L.tune.ipt, st);
@@ -618,12 +849,13 @@ cudaError_t launch_accel_single(int64_t rows, const double *m, const double *q, 
         ka.items = d.items; ka.slots = d.item_slot; ka.pos = d.pk_pos; ka.lo = d.pk_lo;
         ka.q = q; ka.m = m; ka.G = G; ka.apart = d.apart; ka.rows = rows;
         ka.cand = nullptr; ka.max_cand = 0; ka.ncand = nullptr; ka.status = nullptr;
-        ka.fchunk = nullptr; ka.max_fchunk = 0; ka.nfchunk = nullptr;
+        ka.fchunk = nullptr; ka.max_fchunk = 0; ka.nfchunk = nullptr; ka.far_tiles = 0;
+        ka.perm = nullptr; ka.far = nullptr; ka.tile = nullptr;
         e = launch_f64<false, true>(ka, L.nitems, L.tune.threads, L.tune.ipt, st);
     }
     if (e != cudaSuccess) return e;
     k_sum_partials<<<(unsigned)((rows + tb - 1) / tb), tb, 0, st>>>(rows, L.splits, d.apart, hl, m,
-                                                                     q, G, a);
+                                                                     q, G, a, d.inv);
     return cudaGetLastError();
 }
 

@@ -83,6 +83,11 @@ struct Dev {
     int64_t own_lo = 0, own_hi = 0;
     int32_t *set_root = nullptr;  // [max_sets] lowest row of each set (sets are numbered by it)
     int32_t log_refine = 1;       // the rigorous test logs its pairs (0: the split's import does)
+    // order of the bodies in the kick's packs and partial sums (sort.cu):
+    // position p holds row perm[p], row r sits at position inv[r]; NULL: row order
+    int32_t *perm = nullptr, *inv = nullptr;
+    float4 *far = nullptr;   // [rows] (offset from the tile's reference point, G m) in that order
+    float4 *tile = nullptr;  // [3 x tiles] reference point and radius, box min, box max
 };
 
 // device counters, indices into Dev::ctr
@@ -248,9 +253,22 @@ size_t accel_single_workspace(int64_t rows, int prec);
 // items of the i rows in [i_lo, i_hi) (default: all rows) against all j
 void kick_items_host(const int64_t *offsets, int32_t nsys, const KickTune &t,
                      int4 *items, int32_t *slots, int32_t *nitems, int32_t *splits_used,
-                     int32_t max_items, int64_t i_lo = 0, int64_t i_hi = INT64_MAX);
+                     int32_t max_items, int64_t i_lo = 0, int64_t i_hi = INT64_MAX,
+                     int32_t align = 1);
+constexpr int kKickTile = 256;  // j rows per shared-memory tile of the kick
 int32_t kick_items_count(const int64_t *offsets, int32_t nsys, const KickTune &t,
                          int64_t i_lo = 0, int64_t i_hi = INT64_MAX);
+
+// sort.cu: Morton order of a system's bodies for the kick
+struct SortScratch {
+    int *box;              // [6]
+    uint32_t *k0, *k1;     // [rows] keys
+    int32_t *v0, *v1;      // [rows] rows
+    uint32_t *hist;        // [256 * sort_blocks(rows)]
+};
+int64_t sort_blocks(int64_t n);
+cudaError_t launch_sort_rows(int64_t rows, const double *q, const SortScratch &s, int32_t *perm,
+                             int32_t *inv, cudaStream_t st);
 
 // encounter.cu
 struct SetScratch {

@@ -139,14 +139,17 @@ __global__ void __launch_bounds__(256) k_drift_pack(Dev d, DriftArgs a) {
         double F = 2.0 / (1.0 - sh);
         double rho = F * (a.a_E * (double)rHb + fabs(a.tau) * (u + w)) + 1e-12 * rr;
         // kernels test r^2 < c_i + c_j with c = 2 rho^2 >= ... a superset of
-        // r < rho_i + rho_j, as (rho_i + rho_j)^2 <= 2 rho_i^2 + 2 rho_j^2
-        reach = round_up_f(2.0 * rho * rho * (1.0 + 1e-6));
+        // r < rho_i + rho_j, as (rho_i + rho_j)^2 <= 2 rho_i^2 + 2 rho_j^2;
+        // the factor covers the FP32 rounding of r^2 (a few 1e-7 relative,
+        // also in the kick's far-tile form)
+        reach = round_up_f(2.0 * rho * rho * (1.0 + 4e-6));
     }
     // heavy bodies enter the FP32 tiles with zero mass (their pull is added
     // in FP64 by the finisher); they still take part in the encounter search
     float gm = (d.heavy_split && r != star && mm >= d.heavy_thr[sys]) ? 0.0f : (float)(a.G * mm);
-    d.pk_pos[r] = make_float4(xh, yh, zh, gm);
-    d.pk_lo[r] = make_float4(xl, yl, zl, reach);
+    const int64_t pr = d.inv ? d.inv[r] : r;  // the kick's order
+    d.pk_pos[pr] = make_float4(xh, yh, zh, gm);
+    d.pk_lo[pr] = make_float4(xl, yl, zl, reach);
 }
 
 cudaError_t launch_drift_pack_from(const Dev &d, const double *qs, const double *vs,
@@ -193,11 +196,12 @@ __global__ void __launch_bounds__(256) k_finish(Dev d, FinishArgs a) {
     if (r == star) return;
     const int64_t R = d.rows;
     double ax = 0.0, ay = 0.0, az = 0.0;
+    const int64_t pr = d.inv ? d.inv[r] : r;  // the kick's order
     for (int s = 0; s < d.splits; ++s) {
         const double *p = d.apart + (int64_t)s * 3 * R;
-        ax += p[r];
-        ay += p[R + r];
-        az += p[2 * R + r];
+        ax += p[pr];
+        ay += p[R + pr];
+        az += p[2 * R + pr];
     }
     if (d.heavy_split) {
         int h0 = d.heavy_start[sys], h1 = d.heavy_start[sys + 1];

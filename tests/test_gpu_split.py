@@ -91,8 +91,10 @@ def _relq(a, b):
 def test_split_matches_unsplit_step(torch, prec):
     """The 16384-body disk, 4 hybrid steps: one rank and two ranks through the
     phases give the unsplit qym_step's encounter records exactly, and its
-    positions and velocities to rounding (1e-13 relative; bit-identical unless
-    a large set took a thread-block cluster in one run and not the other)."""
+    positions and velocities to rounding (FP64 kick: 1e-13 relative,
+    bit-identical unless a large set took a thread-block cluster in one run
+    and not the other; mixed kick: 1e-8, the FP32 sums grouped in another
+    order)."""
     w = W.disk_16384()
     n = 4
     ref = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, kick_prec=prec)
@@ -106,7 +108,11 @@ def test_split_matches_unsplit_step(torch, prec):
             assert np.array_equal(enc, er), (world, rank, len(enc), len(er))
             dq, dv = _relq(qq, qr).max(), _relq(vv, vr).max()
             print(f"\n  world {world} rank {rank}: max rel dq {dq:.3g} dv {dv:.3g}")
-            assert dq <= 1e-13 and dv <= 1e-13, (world, rank, dq, dv)
+            # FP64: the same bits; mixed: the unsplit step holds the bodies in
+            # Morton order (sort.cu) and the split in row order, which groups
+            # the FP32 tile sums differently
+            tol = 1e-13 if prec == q.QYM_KICK_FP64 else 1e-8
+            assert dq <= tol and dv <= tol, (world, rank, dq, dv)
 
 
 def test_split_three_ranks_uneven_blocks(torch):
