@@ -519,8 +519,10 @@ def run_ours(args):
     prec = q.QYM_KICK_MIXED if args.prec == "mixed" else q.QYM_KICK_FP64
     # every step starts by writing 256 MB (twice the 129 MB L2), inside the
     # timed region, so no step reuses the previous step's lines
+    search = q.QYM_SEARCH_BINNED if args.search == "binned" else q.QYM_SEARCH_FUSED
     sim = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=prec, device=dev,
-                       l2_flush_bytes=256 << 20, eps_H=w.eps_H, merge_kicks=args.merge_kicks)
+                       l2_flush_bytes=256 << 20, eps_H=w.eps_H, merge_kicks=args.merge_kicks,
+                       search=search)
     if args.autotune:
         q.qym_autotune(sim.ctx)
     if args.kick_only:
@@ -562,7 +564,10 @@ def run_ours(args):
     reps = 20
     k1_ms, _ = q.qym_time_kick(sim.ctx, 1, reps)
     k2_ms, _ = q.qym_time_kick(sim.ctx, 0, reps)
-    kick_ms = 0.5 * (k1_ms + k2_ms)
+    # the step's two kicks: with the binned search both are plain; with the
+    # fused one the first carries the search
+    binned = sim.params.search == q.QYM_SEARCH_BINNED
+    kick_ms = k2_ms if binned else 0.5 * (k1_ms + k2_ms)
     achieved = 20.0 * pairs / (kick_ms / 1e3) / 1e12
     clocks = clk.summary()
     probe = probe_peaks(q, dev)
@@ -575,8 +580,10 @@ def run_ours(args):
             "traffic": (KICK_DRAM_BYTES.get((args.workload, st["kick_tile_i"], st["kick_tile_splits"],
                                              digest)) if prec else None),
             "traffic_unit": "bytes per launch (ncu)", "kick_source_digest": digest,
-            "convention": "20 flop per ordered pair over the mean launch time of the searching "
-                          "and the plain kick",
+            "convention": ("20 flop per ordered pair over the plain kick's launch time (the "
+                           "binned search leaves both kicks of a step plain)" if binned else
+                           "20 flop per ordered pair over the mean launch time of the searching "
+                           "and the plain kick"),
             "kick_ms_with_search": k1_ms, "kick_ms_plain": k2_ms,
             "frac_with_search": 20.0 * pairs / (k1_ms / 1e3) / 1e12 / peak,
             "frac_plain": 20.0 * pairs / (k2_ms / 1e3) / 1e12 / peak,
@@ -610,7 +617,7 @@ def run_ours(args):
     merged = None
     if not args.merge_kicks and args.merged_too:
         sm = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=prec, device=dev,
-                          l2_flush_bytes=256 << 20, eps_H=w.eps_H, merge_kicks=1)
+                          l2_flush_bytes=256 << 20, eps_H=w.eps_H, merge_kicks=1, search=search)
         if args.autotune:
             q.qym_autotune(sm.ctx)
         sms = torch.cuda.ExternalStream(q.qym_get_stream(sm.ctx))
@@ -629,6 +636,32 @@ def run_ours(args):
                   "candidates": int(sst["candidates"]), "encounters": int(sst["encounters"]),
                   "rescans": int(sst["rescans"]), "hermite_steps_max": int(sst["hermite_steps_max"])}
         sm.close()
+    # the same steps with the other encounter search (binned after the drift /
+    # fused into the first kick), for comparison
+    other = None
+    if args.search_too:
+        alt = q.QYM_SEARCH_FUSED if search == q.QYM_SEARCH_BINNED else q.QYM_SEARCH_BINNED
+        so = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=prec, device=dev,
+                          l2_flush_bytes=256 << 20, eps_H=w.eps_H, merge_kicks=args.merge_kicks,
+                          search=alt)
+        if args.autotune:
+            q.qym_autotune(so.ctx)
+        sos = torch.cuda.ExternalStream(q.qym_get_stream(so.ctx))
+        so.step(w.tau, max(args.warmup, 3))
+        barrier()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(sos)
+        so.step(w.tau, args.steps)
+        g1.record(sos)
+        barrier()
+        oms = max_over_ranks(g0.elapsed_time(g1), "cuda")
+        ost = so.stats()
+        other = {"search": "fused" if alt == q.QYM_SEARCH_FUSED else "binned",
+                 "value": nb_all * args.steps / (oms / 1e3), "ms_per_step": oms / args.steps,
+                 "candidates": int(ost["candidates"]), "encounters": int(ost["encounters"]),
+                 "rescans": int(ost["rescans"]), "launches": int(ost["launches"])}
+        so.close()
     precision = None
     if args.precision_too and ws == 1 and prec == q.QYM_KICK_MIXED:
         precision = precision_compare(q, torch, w, args, dev)
@@ -644,6 +677,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "fp32-pair/f64-state" if prec else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "kick": args.prec,
+                       "search": "binned" if binned else "fused",
                        "parallelism": ("independent batches per rank" if ws > 1 and
                                        WORKLOADS[args.workload][0] == "ensemble" else
                                        "replicas" if ws > 1 else "single GPU"),
@@ -651,6 +685,7 @@ def run_ours(args):
                        "l2": "flushed: 256 MB written at the start of every step, inside the timed region"},
             "gpair_per_s": gpair, "stats": st, "gpu_launches": int(st["launches"]),
             "kicks_per_step": 1 if args.merge_kicks else 2, "merged_kicks": merged,
+            "other_search": other,
             "precision": precision,
             "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cb}
     print(json.dumps(line))
@@ -876,6 +911,10 @@ def main():
                     help="kepler_1m: train the guess network first (0: standard guess only)")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--search", default="binned", choices=["binned", "fused"],
+                    help="close-encounter search: binned after the drift, or fused into the kick")
+    ap.add_argument("--search-too", type=int, default=1,
+                    help="also time the other encounter search and report it under other_search")
     ap.add_argument("--split", type=int, default=0,
                     help="1: a single system's step split over the job's GPUs even on one GPU "
                          "(with several GPUs a single system always is)")

@@ -112,7 +112,25 @@ typedef struct qym_params {
     int32_t hermite_cluster;    /* CTAs of a thread-block cluster that share one large
                                    encounter set in the Hermite: 2, 4 or 8; 0: automatic
                                    (8 for a single system, 2 for a batch of systems) */
+    int32_t search;             /* how the close-encounter candidates are found (Sec. 2.4):
+                                   QYM_SEARCH_FUSED or QYM_SEARCH_BINNED */
 } qym_params;
+
+/* Close-encounter search: which pairs the rigorous test (Sec. 2.4) examines.
+ * FUSED: a crude reach per body from the state before the first kick, tested
+ *   inside that kick over all pairs (the paper's crude sweep riding on the
+ *   kick); rows whose kick or Hill radius exceeds what the reach assumed are
+ *   re-searched exactly.
+ * BINNED: after the Kepler drift, per body a box that holds its cubic
+ *   Hermite path over the step widened by a_E r_H and a bound on how far the
+ *   test's cubic can fall below the paths' distance; tiles of bodies (the
+ *   kick's Morton order for one system) and pairs of overlapping tiles; within
+ *   them pairs of overlapping boxes, filtered by the test's cubic in FP32 with
+ *   an error allowance. Every pair the test can flag is examined, by
+ *   construction; the kicks carry no search. A split context (qym_split_init)
+ *   always uses FUSED. */
+#define QYM_SEARCH_FUSED  0
+#define QYM_SEARCH_BINNED 1
 
 #define QYM_HEAVY_CAP 256
 

@@ -71,6 +71,11 @@ struct qym_ctx {
     // the kick's Morton order of the bodies (one system, mixed kick)
     bool sort_rows = false;
     SortScratch sortw{};
+    // binned encounter search (params.search == QYM_SEARCH_BINNED)
+    bool binned = false;
+    SearchArgs sarg{};
+    int32_t nstiles = 0;
+    int64_t nstpairs = 0;
 };
 
 #define FAIL(ctx, code, msg)                         \
@@ -111,6 +116,7 @@ extern "C" qym_status qym_default_params(qym_params *p) {
     p->max_log = 0;
     p->l2_flush_bytes = 0;
     p->heavy_mass = 1e-7;
+    p->search = QYM_SEARCH_BINNED;
     return QYM_OK;
 }
 
@@ -127,6 +133,10 @@ static bool valid_params(const qym_params *p, std::string &why) {
     if (p->max_candidates < 0 || p->max_encounters < 0 || p->max_log < 0) { why = "capacities"; return false; }
     if (p->l2_flush_bytes < 0 || p->l2_flush_bytes > ((int64_t)1 << 34)) { why = "l2_flush_bytes"; return false; }
     if (p->merge_kicks != 0 && p->merge_kicks != 1) { why = "merge_kicks must be 0 or 1"; return false; }
+    if (p->search != QYM_SEARCH_FUSED && p->search != QYM_SEARCH_BINNED) {
+        why = "search must be QYM_SEARCH_FUSED or QYM_SEARCH_BINNED";
+        return false;
+    }
     if (p->hermite_cluster != 0 && p->hermite_cluster != 2 && p->hermite_cluster != 4 &&
         p->hermite_cluster != 8) {
         why = "hermite_cluster must be 0, 2, 4 or 8";
@@ -224,6 +234,25 @@ static void carve_all(qym_ctx *c, Carver &k) {
         c->sortw.hist = k.take<uint32_t>(256 * (size_t)sort_blocks(R));
         d.far = k.take<float4>(R);
         d.tile = k.take<float4>(3 * (size_t)((R - 1 + kKickTile - 1) / kKickTile));
+    }
+    if (c->binned) {
+        SearchArgs &a = c->sarg;
+        a.vmax = k.take<int32_t>(d.nsys);
+        a.box_lo = k.take<float4>(R);
+        a.box_hi = k.take<float4>(R);
+        a.x0h = k.take<float4>(R);
+        a.x0l = k.take<float4>(R);
+        a.x1h = k.take<float4>(R);
+        a.x1l = k.take<float4>(R);
+        a.v0f = k.take<float4>(R);
+        a.v1f = k.take<float4>(R);
+        a.tbox = k.take<float4>(2 * (size_t)c->nstiles);
+        a.tiles = k.take<int4>(c->nstiles);
+        a.tpairs = k.take<int2>(c->nstpairs);
+        a.active = k.take<int2>(c->nstpairs);
+        a.nactive = k.take<unsigned long long>(1);
+        a.ntiles = c->nstiles;
+        a.ntpairs = c->nstpairs;
     }
 }
 
@@ -393,6 +422,14 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     // one system of at least two tiles' worth of bodies, mixed kick: the kick
     // holds the bodies in Morton order (sort.cu)
     c->sort_rows = nsys == 1 && params->kick_prec == QYM_KICK_MIXED && R - 1 >= kSortMinBodies;
+    c->binned = params->encounters && params->search == QYM_SEARCH_BINNED;
+    std::vector<int4> stiles;
+    std::vector<int2> stpairs;
+    if (c->binned) {
+        search_tiles_host(offsets, nsys, stiles, stpairs);
+        c->nstiles = (int32_t)stiles.size();
+        c->nstpairs = (int64_t)stpairs.size();
+    }
     Carver dry{nullptr, 0, true};
     carve_all(c, dry);
     size_t bytes = dry.off;
@@ -448,6 +485,12 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
         CKI(cudaMemcpyAsync(d.heavy_rows, hrows.data(), sizeof(int32_t) * hrows.size(), cudaMemcpyHostToDevice, c->stream));
     CKI(cudaMemcpyAsync(d.heavy_start, hstart.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, c->stream));
     CKI(cudaMemcpyAsync(d.heavy_thr, hthr.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, c->stream));
+    if (c->binned && c->nstiles) {
+        CKI(cudaMemcpyAsync((void *)c->sarg.tiles, stiles.data(), sizeof(int4) * stiles.size(),
+                            cudaMemcpyHostToDevice, c->stream));
+        CKI(cudaMemcpyAsync((void *)c->sarg.tpairs, stpairs.data(), sizeof(int2) * stpairs.size(),
+                            cudaMemcpyHostToDevice, c->stream));
+    }
     CKI(cudaStreamSynchronize(c->stream));  // host vectors go out of scope below
     CKI(hermite_prepare());
     if (params->l2_flush_bytes > 0) CKI(cudaMalloc(&c->flush, (size_t)params->l2_flush_bytes));
@@ -536,6 +579,17 @@ static int search_retest(const qym_params &p, int flag) {
     return (flag && p.kick_prec == QYM_KICK_MIXED) ? 1 : 0;
 }
 
+// 1 when the first kick of a step carries the crude encounter search
+// (QYM_SEARCH_FUSED); with QYM_SEARCH_BINNED the search follows the drift
+static int fused_search(const qym_ctx *c) { return (c->p.encounters && !c->binned) ? 1 : 0; }
+
+// the binned search's candidates, after the Kepler drift
+static cudaError_t enqueue_binned_search(qym_ctx *c, double tau) {
+    if (!c->binned) return cudaSuccess;
+    c->launches += 5;
+    return launch_binned_search(c->d, c->sarg, tau, c->p.a_E, c->stream);
+}
+
 // copies of the rigorous encounter test's inputs (qym_set_encounter_snapshot):
 // (q, v) enter the Kepler drift, (q1, v1) its result, before the Hermite
 static cudaError_t enqueue_snapshot(qym_ctx *c) {
@@ -584,20 +638,25 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last, bool fresh = 
         if ((e = cudaMemsetAsync(c->flush, c->launches & 0xff, (size_t)p.l2_flush_bytes, st))) return e;
     }
     k_step_begin<<<1, 1, 0, st>>>(d.ctr);
-    // item 2: kick tau/2, with the crude encounter search when encounters are on
-    if (enc && fresh) {
+    const int fz = fused_search(c);
+    // item 2: kick tau/2, with the crude encounter search when it is fused
+    if (fz && fresh) {
         if ((e = enqueue_fresh_search_kick(c, 0.5 * tau))) return e;
-        c->launches -= 2 + search_retest(p, enc);  // counted below as kick and finish
+        c->launches -= 2 + search_retest(p, fz);  // counted below as kick and finish
     } else {
-        if ((e = launch_kick_tiles(d, p.kick_prec, enc, p.G, c->tune.threads, c->tune.ipt, st)))
+        if ((e = launch_kick_tiles(d, p.kick_prec, fz, p.G, c->tune.threads, c->tune.ipt, st)))
             return e;
-        if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, enc, p.hill_fixed, st))) return e;
+        // the finisher records the step's Hill radii (and audits a fused search)
+        if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, enc ? (fz ? 1 : 2) : 0,
+                                      p.hill_fixed, st)))
+            return e;
     }
     // item 3: Kepler drift over tau, (q, v) -> (q1, v1)
     if ((e = launch_kepler(step_kepler_args(c, tau), st))) return e;
     if (last && (e = enqueue_snapshot(c))) return e;
     if (enc) {
-        // items 4-8: rigorous test, sets and r_crit, K corrections + Hermite
+        // items 4-8: [binned search,] rigorous test, sets and r_crit, K corrections + Hermite
+        if ((e = enqueue_binned_search(c, tau))) return e;
         if ((e = launch_refine(d, tau, p.a_E, st))) return e;
         if ((e = launch_sets_impl(d, p.a_H, c->ss, st))) return e;
         if ((e = launch_hermite(d, p, tau, st))) return e;
@@ -612,12 +671,12 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last, bool fresh = 
     // item 10 (and item 1 of the next step): drift tau/2 with S = sum m v
     if ((e = launch_momentum(d, st))) return e;
     if ((e = launch_drift_pack_from(d, d.q, d.v, 0.5 * tau, last ? 0.0 : 0.5 * tau, tau, p.a_E,
-                                    p.G, (!last) && enc, p.hill_fixed, st, 0.5 * tau)))
+                                    p.G, (!last) && fz, p.hill_fixed, st, 0.5 * tau)))
         return e;
     k_step_end<<<1, 1, 0, st>>>(d.ctr, d.max_cand, d.max_enc);
     // begin, kick [+ chunk re-test], finish, Kepler, [refine 2, sets 7, Hermite plan, Hermite],
     // pack, kick, finish, momentum 2, drift, end
-    c->launches += 12 + (enc ? 11 : 0) + search_retest(p, enc);
+    c->launches += 12 + (enc ? 11 : 0) + search_retest(p, fz);
     return cudaGetLastError();
 }
 
@@ -631,12 +690,14 @@ static cudaError_t enqueue_opening_kick(qym_ctx *c, double tau, bool fresh) {
     cudaError_t e;
     k_step_begin<<<1, 1, 0, st>>>(d.ctr);
     c->launches += 1;
-    if (p.encounters && fresh) return enqueue_fresh_search_kick(c, 0.5 * tau);
-    if ((e = launch_kick_tiles(d, p.kick_prec, p.encounters, p.G, c->tune.threads, c->tune.ipt, st)))
+    const int fz = fused_search(c);
+    if (fz && fresh) return enqueue_fresh_search_kick(c, 0.5 * tau);
+    if ((e = launch_kick_tiles(d, p.kick_prec, fz, p.G, c->tune.threads, c->tune.ipt, st)))
         return e;
-    if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, p.encounters, p.hill_fixed, st)))
+    if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G,
+                                  p.encounters ? (fz ? 1 : 2) : 0, p.hill_fixed, st)))
         return e;
-    c->launches += 2 + search_retest(p, p.encounters);
+    c->launches += 2 + search_retest(p, fz);
     return cudaGetLastError();
 }
 
@@ -655,7 +716,9 @@ static cudaError_t enqueue_unit(qym_ctx *c, double tau, bool last) {
     }
     if ((e = launch_kepler(step_kepler_args(c, tau), st))) return e;
     if (last && (e = enqueue_snapshot(c))) return e;
+    const int fz = fused_search(c);
     if (enc) {
+        if ((e = enqueue_binned_search(c, tau))) return e;
         if ((e = launch_refine(d, tau, p.a_E, st))) return e;
         if ((e = launch_sets_impl(d, p.a_H, c->ss, st))) return e;
         if ((e = launch_hermite(d, p, tau, st))) return e;
@@ -670,14 +733,16 @@ static cudaError_t enqueue_unit(qym_ctx *c, double tau, bool last) {
         if ((e = launch_momentum(d, st))) return e;
         // the last kick was a step earlier: its |a| bounds this one's only
         // loosely, so the crude reach allows twice it (and the finisher checks)
-        if ((e = launch_drift_pack_from(d, d.q, d.v, 0.5 * tau, 0.5 * tau, tau, p.a_E, p.G, enc,
+        if ((e = launch_drift_pack_from(d, d.q, d.v, 0.5 * tau, 0.5 * tau, tau, p.a_E, p.G, fz,
                                         p.hill_fixed, st, tau, 2.0)))
             return e;
-        if ((e = launch_kick_tiles(d, p.kick_prec, enc, p.G, c->tune.threads, c->tune.ipt, st))) return e;
-        if ((e = launch_kick_finish_v(d, d.v, d.q, tau, p.G, enc, p.hill_fixed, st, 2.0))) return e;
+        if ((e = launch_kick_tiles(d, p.kick_prec, fz, p.G, c->tune.threads, c->tune.ipt, st))) return e;
+        if ((e = launch_kick_finish_v(d, d.v, d.q, tau, p.G, enc ? (fz ? 1 : 2) : 0, p.hill_fixed,
+                                      st, 2.0)))
+            return e;
         // Kepler, [refine 2, sets 7, Hermite plan, Hermite], end, copy, begin, momentum 2, drift, kick
         // [+ chunk re-test], finish
-        c->launches += 9 + (enc ? 11 : 0) + search_retest(p, enc);
+        c->launches += 9 + (enc ? 11 : 0) + search_retest(p, fz);
     } else {
         if ((e = launch_kick_tiles(d, p.kick_prec, 0, p.G, c->tune.threads, c->tune.ipt, st))) return e;
         if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, 0, p.hill_fixed, st))) return e;
@@ -753,7 +818,7 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
     // item 1 of the first step: drift tau/2
     CK(c, launch_momentum(d, st));
     CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.5 * tau, tau, p.a_E, p.G,
-                                 p.encounters && !fresh, p.hill_fixed, st, 0.5 * tau));
+                                 fused_search(c) && !fresh, p.hill_fixed, st, 0.5 * tau));
     c->launches += 3;
     int64_t rest = nsteps;  // steps (or merged units) still to enqueue
     if (p.merge_kicks) {
@@ -791,8 +856,9 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
                 // re-sort between steps and lay the packs of the coming kick out
                 // again in the new order (the same values: no drift)
                 CK(c, launch_sort_rows(d.rows, d.q, c->sortw, d.perm, d.inv, st));
-                CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.0, tau, p.a_E, p.G, p.encounters,
-                                             p.hill_fixed, st, p.merge_kicks ? tau : 0.5 * tau,
+                CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.0, tau, p.a_E, p.G,
+                                             fused_search(c), p.hill_fixed, st,
+                                             p.merge_kicks ? tau : 0.5 * tau,
                                              p.merge_kicks ? 2.0 : 1.01));
                 c->launches += 17;
             }
@@ -988,6 +1054,8 @@ extern "C" qym_status qym_split_init(qym_ctx *c, int32_t rank, int32_t world) {
     d.log_refine = 0;
     d.perm = d.inv = nullptr;  // the split's kick items are in row order
     d.far = d.tile = nullptr;
+    c->p.search = QYM_SEARCH_FUSED;  // the split's candidates come with each rank's kick
+    c->binned = false;
     c->split_rank = rank;
     c->split_world = world;
     c->amag_valid = false;
@@ -1439,7 +1507,7 @@ extern "C" qym_status qym_autotune(qym_ctx *c) {
         qym_status s = apply_tune(c, t);
         if (s != QYM_OK) return s;
         double ms = 0.0;
-        s = time_kick_shape(c, c->p.encounters, 3, t, &ms);
+        s = time_kick_shape(c, fused_search(c), 3, t, &ms);
         if (s != QYM_OK) return s;
         if (ms < best_ms) { best_ms = ms; best = t; }
     }

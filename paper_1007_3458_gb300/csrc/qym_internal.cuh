@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/qym.h"
 
@@ -269,6 +270,25 @@ struct SortScratch {
 int64_t sort_blocks(int64_t n);
 cudaError_t launch_sort_rows(int64_t rows, const double *q, const SortScratch &s, int32_t *perm,
                              int32_t *inv, cudaStream_t st);
+
+// search.cu: candidates by spatial binning after the Kepler drift
+struct SearchArgs {
+    double tau, a_E;
+    const int32_t *vmax;     // [nsys] float bits
+    float4 *box_lo, *box_hi; // [rows] widened boxes by position
+    float4 *x0h, *x0l, *x1h, *x1l, *v0f, *v1f;  // [rows] by position (x0h.w: a_E r_H)
+    float4 *tbox;            // [2 x tiles] tile boxes (lo, hi)
+    const int4 *tiles;       // (system, p0, p1, -)
+    int32_t ntiles;
+    const int2 *tpairs;      // (tile I, tile J), I <= J, same system
+    int64_t ntpairs;
+    int2 *active;            // tile pairs whose boxes overlap
+    unsigned long long *nactive;
+};
+cudaError_t launch_binned_search(const Dev &d, const SearchArgs &s, double tau, double a_E,
+                                 cudaStream_t st);
+void search_tiles_host(const int64_t *offsets, int32_t nsys, std::vector<int4> &tiles,
+                       std::vector<int2> &tpairs);
 
 // encounter.cu
 struct SetScratch {

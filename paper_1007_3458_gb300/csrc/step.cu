@@ -177,8 +177,9 @@ cudaError_t launch_drift_pack_from(const Dev &d, const double *qs, const double 
 // v += dt * sum over slots of the partial accelerations (fixed slot order);
 // |a| is kept for the next crude search. After the first kick of a step
 // (check != 0) the Hill radius of this step is computed from the state that
-// enters the Kepler drift, and rows whose crude-search bounds (|a| allowance,
-// Hill radius bound) were exceeded are queued for an exact re-search.
+// enters the Kepler drift, and (check == 1, the search fused into this kick)
+// rows whose crude-search bounds (|a| allowance, Hill radius bound) were
+// exceeded are queued for an exact re-search.
 struct FinishArgs {
     double *v;          // velocities to update ([3][rows])
     const double *q;    // positions (for the Hill radius)
@@ -214,11 +215,12 @@ __global__ void __launch_bounds__(256) k_finish(Dev d, FinishArgs a) {
     a.v[r] = vx; a.v[R + r] = vy; a.v[2 * R + r] = vz;
     float an = round_up_f(sqrt(ax * ax + ay * ay + az * az));
     if (a.check) {
-        bool bad = an > a.a_allow * d.amag[r] + 1e-30f;
         const double m0 = d.m[star];
         double rH = a.hill_fixed ? d.rH_fixed[r] : hill(a.q[r], a.q[R + r], a.q[2 * R + r], d.m[r], m0);
         d.rH[r] = rH;
-        if (rH > (double)d.rH_bound[r]) bad = true;
+        // check 1 (the search fused into this kick): audit its reach
+        bool bad = a.check == 1 && (an > a.a_allow * d.amag[r] + 1e-30f ||
+                                    rH > (double)d.rH_bound[r]);
         if (bad) {
             unsigned long long k = atomicAdd(d.ctr + C_NRESCAN, 1ull);
             if (k < (unsigned long long)R) d.rescan[k] = (int32_t)r;

@@ -56,18 +56,20 @@ def _check_hill(oracle, w, q0, v0, rH):
     assert rel.max() <= 2e-15, rel.max()
 
 
-def test_dense_disk_records_sampled(torch, oracle):
+@pytest.mark.parametrize("search", [q.QYM_SEARCH_BINNED, q.QYM_SEARCH_FUSED])
+def test_dense_disk_records_sampled(torch, oracle, search):
     """The 262144-body embryo disk (64 embryos of 1e-6 among 262080
-    planetesimals of 1e-11, the dense-encounter configuration), mixed kick:
-    for every embryo and 64 random planetesimals, the step's encounter records
-    involving them equal the oracle's test of those rows against all 262143
-    partners, on the first step of a call (search after a fresh kick) and on
-    the last step of a three-step call (search fused into the kick, |a| of the
-    previous kick as allowance). The Kepler output of the step matches the
-    oracle's drift of the same state on a sample of bodies."""
+    planetesimals of 1e-11, the dense-encounter configuration), mixed kick,
+    binned and fused searches: for every embryo and 64 random planetesimals,
+    the step's encounter records involving them equal the oracle's test of
+    those rows against all 262143 partners, on the first step of a call and on
+    the last step of a three-step call (with the fused search: a search after
+    a fresh kick, then one inside the kick with the |a| of the previous kick
+    as allowance). The Kepler output of the step matches the oracle's drift of
+    the same state on a sample of bodies."""
     w = W.disk_262144()
     R = len(w.m)
-    sim = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H)
+    sim = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, search=search)
     snap = Snapshot(torch, sim, R)
     rng = np.random.default_rng(12)
     sel = np.concatenate([np.arange(1, 65), rng.choice(np.arange(65, R), 64, replace=False)])
@@ -94,19 +96,22 @@ def test_dense_disk_records_sampled(torch, oracle):
     sim.close()
 
 
+@pytest.mark.parametrize("search", [q.QYM_SEARCH_BINNED, q.QYM_SEARCH_FUSED])
 @pytest.mark.parametrize("prec, merge", [(q.QYM_KICK_MIXED, 0), (q.QYM_KICK_FP64, 0),
                                          (q.QYM_KICK_MIXED, 1)])
-def test_search_superset_adversarial(torch, oracle, prec, merge):
+def test_search_superset_adversarial(torch, oracle, prec, merge, search):
     """A stirred disk (workloads.crossers: eccentric crossers up to e = 0.9,
     inclinations up to 90 deg, retrograde bodies, bodies inside a Jupiter-mass
     planet's Hill sphere at up to 1.5 times its orbital speed, hyperbolic
     flybys): on one-step calls and on the last step of four-step calls (the
     step graph, and with merged kicks the allowance of a kick a whole step
     earlier), the GPU's records equal the oracle's all-pairs rigorous test on
-    the step's own inputs."""
+    the step's own inputs; for the binned search (its candidate set a superset
+    by construction) and the fused one (a reach per body, audited)."""
     w = W.crossers()
     R = len(w.m)
-    sim = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, kick_prec=prec, merge_kicks=merge)
+    sim = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, kick_prec=prec, merge_kicks=merge,
+                       search=search)
     snap = Snapshot(torch, sim, R)
     calls = [1] * 12 + [4, 4, 4]
     checked = 0

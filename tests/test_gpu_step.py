@@ -316,11 +316,14 @@ def test_state_round_trip_and_resume(gpu, oracle):
 def test_error_statuses(gpu):
     """Capacities and caps report statuses; the context stays usable."""
     w = W.disk_260()
-    sim = q.Simulation(w.m, w.q, w.v, w.offsets, max_candidates=1)
-    with pytest.raises(q.QymError) as e:
-        sim.step(w.tau, 30)
-    assert e.value.status == q.QYM_EOVERFLOW
-    sim.close()
+    wc = W.crossers()
+    for search in (q.QYM_SEARCH_FUSED, q.QYM_SEARCH_BINNED):
+        sim = q.Simulation(wc.m, wc.q, wc.v, wc.offsets, max_candidates=1, search=search,
+                           eps_H=wc.eps_H)
+        with pytest.raises(q.QymError) as e:
+            sim.step(wc.tau, 5)
+        assert e.value.status == q.QYM_EOVERFLOW
+        sim.close()
     sim = q.Simulation(w.m, w.q, w.v, w.offsets, max_kepler_iter=1, encounters=0)
     with pytest.raises(q.QymError) as e:
         sim.step(w.tau, 2)
