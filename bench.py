@@ -519,7 +519,8 @@ def run_ours(args):
     prec = q.QYM_KICK_MIXED if args.prec == "mixed" else q.QYM_KICK_FP64
     # every step starts by writing 256 MB (twice the 129 MB L2), inside the
     # timed region, so no step reuses the previous step's lines
-    search = q.QYM_SEARCH_BINNED if args.search == "binned" else q.QYM_SEARCH_FUSED
+    search = {"binned": q.QYM_SEARCH_BINNED, "fused": q.QYM_SEARCH_FUSED,
+              "auto": q.QYM_SEARCH_AUTO}[args.search]
     sim = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=prec, device=dev,
                        l2_flush_bytes=256 << 20, eps_H=w.eps_H, merge_kicks=args.merge_kicks,
                        search=search)
@@ -566,7 +567,7 @@ def run_ours(args):
     k2_ms, _ = q.qym_time_kick(sim.ctx, 0, reps)
     # the step's two kicks: with the binned search both are plain; with the
     # fused one the first carries the search
-    binned = sim.params.search == q.QYM_SEARCH_BINNED
+    binned = sim.effective_params().search == q.QYM_SEARCH_BINNED
     kick_ms = k2_ms if binned else 0.5 * (k1_ms + k2_ms)
     achieved = 20.0 * pairs / (kick_ms / 1e3) / 1e12
     clocks = clk.summary()
@@ -640,7 +641,7 @@ def run_ours(args):
     # fused into the first kick), for comparison
     other = None
     if args.search_too:
-        alt = q.QYM_SEARCH_FUSED if search == q.QYM_SEARCH_BINNED else q.QYM_SEARCH_BINNED
+        alt = q.QYM_SEARCH_FUSED if binned else q.QYM_SEARCH_BINNED
         so = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=prec, device=dev,
                           l2_flush_bytes=256 << 20, eps_H=w.eps_H, merge_kicks=args.merge_kicks,
                           search=alt)
@@ -660,7 +661,8 @@ def run_ours(args):
         other = {"search": "fused" if alt == q.QYM_SEARCH_FUSED else "binned",
                  "value": nb_all * args.steps / (oms / 1e3), "ms_per_step": oms / args.steps,
                  "candidates": int(ost["candidates"]), "encounters": int(ost["encounters"]),
-                 "rescans": int(ost["rescans"]), "launches": int(ost["launches"])}
+                 "rescans": int(ost["rescans"]), "launches": int(ost["launches"]),
+                 "hermite_steps_max": int(ost["hermite_steps_max"])}
         so.close()
     precision = None
     if args.precision_too and ws == 1 and prec == q.QYM_KICK_MIXED:
@@ -911,8 +913,9 @@ def main():
                     help="kepler_1m: train the guess network first (0: standard guess only)")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--search", default="binned", choices=["binned", "fused"],
-                    help="close-encounter search: binned after the drift, or fused into the kick")
+    ap.add_argument("--search", default="auto", choices=["auto", "binned", "fused"],
+                    help="close-encounter search: binned after the drift, fused into the kick, "
+                         "or the library's choice for the workload")
     ap.add_argument("--search-too", type=int, default=1,
                     help="also time the other encounter search and report it under other_search")
     ap.add_argument("--split", type=int, default=0,

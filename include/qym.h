@@ -113,7 +113,7 @@ typedef struct qym_params {
                                    encounter set in the Hermite: 2, 4 or 8; 0: automatic
                                    (8 for a single system, 2 for a batch of systems) */
     int32_t search;             /* how the close-encounter candidates are found (Sec. 2.4):
-                                   QYM_SEARCH_FUSED or QYM_SEARCH_BINNED */
+                                   QYM_SEARCH_AUTO (default), _FUSED or _BINNED */
 } qym_params;
 
 /* Close-encounter search: which pairs the rigorous test (Sec. 2.4) examines.
@@ -131,6 +131,9 @@ typedef struct qym_params {
  *   always uses FUSED. */
 #define QYM_SEARCH_FUSED  0
 #define QYM_SEARCH_BINNED 1
+#define QYM_SEARCH_AUTO   2   /* BINNED for one system of at least 65536 bodies (there
+                                 binning costs less than the all-pairs reach test in the
+                                 kick), FUSED otherwise */
 
 #define QYM_HEAVY_CAP 256
 
@@ -203,6 +206,11 @@ qym_status qym_energy(qym_ctx *ctx, double *E);
 
 /* Counters of the last qym_step call. */
 qym_status qym_get_stats(qym_ctx *ctx, qym_stats *st);
+
+/* The parameters ctx runs with: those given to qym_init, with the choices
+ * the library made filled in (search: QYM_SEARCH_FUSED or _BINNED, never
+ * _AUTO; a split context reports FUSED). */
+qym_status qym_get_params(const qym_ctx *ctx, qym_params *p);
 
 /* Learned Kepler starting guess (the Appendix's universal Kepler equation
  * solved from a predicted start instead of x_std = sqrt(mu) dt / r0). A

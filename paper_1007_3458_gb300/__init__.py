@@ -24,7 +24,7 @@ STATUS_NAMES = ["QYM_OK", "QYM_EINVAL", "QYM_ENOMEM", "QYM_ECUDA", "QYM_ENAN", "
 QYM_ST_KEPLER_NOCONV, QYM_ST_HERMITE_CAP, QYM_ST_CAND_OVERFLOW, QYM_ST_ENC_OVERFLOW = 1, 2, 4, 8
 QYM_ST_SET_OVERFLOW, QYM_ST_NAN, QYM_ST_UF_CAP, QYM_ST_LOG_OVERFLOW = 16, 32, 64, 128
 QYM_KICK_FP64, QYM_KICK_MIXED = 0, 1
-QYM_SEARCH_FUSED, QYM_SEARCH_BINNED = 0, 1
+QYM_SEARCH_FUSED, QYM_SEARCH_BINNED, QYM_SEARCH_AUTO = 0, 1, 2
 QYM_SOLVER_LAGUERRE, QYM_SOLVER_NEWTON = 0, 1
 QYM_GUESS_STANDARD, QYM_GUESS_R0, QYM_GUESS_MLP = 0, 1, 2
 QYM_STATIC_MAX_ROWS = 32768
@@ -100,6 +100,7 @@ def lib():
     L.qym_get_encounters.argtypes = [P, I64, C.c_int64, I64]
     L.qym_energy.argtypes = [P, D]
     L.qym_get_stats.argtypes = [P, C.POINTER(qym_stats)]
+    L.qym_get_params.argtypes = [P, C.POINTER(qym_params)]
     L.qym_set_mlp.argtypes = [P, C.POINTER(C.c_float), C.c_int64]
     L.qym_last_error.argtypes = [P]
     L.qym_last_error.restype = C.c_char_p
@@ -147,7 +148,8 @@ def lib():
     L.qym_energy_workspace_bytes.restype = C.c_size_t
     L.qym_energy_dev.argtypes = [C.c_int64, P, P, P, C.c_double, P, P, C.c_size_t, P]
     for name in ("qym_default_params", "qym_init", "qym_step", "qym_get_state", "qym_set_state",
-                 "qym_get_encounters", "qym_energy", "qym_get_stats", "qym_set_mlp", "qym_shape",
+                 "qym_get_encounters", "qym_energy", "qym_get_stats", "qym_get_params",
+                 "qym_set_mlp", "qym_shape",
                  "qym_get_stream", "qym_time_kick", "qym_autotune",
                  "qym_kepler_drift_dev", "qym_accel_dev", "qym_encounter_test_dev",
                  "qym_energy_dev", "qym_set_kepler_log", "qym_mlp_forward_dev",
@@ -269,6 +271,13 @@ def qym_get_stats(ctx) -> qym_stats:
     s = qym_stats()
     _check(lib().qym_get_stats(ctx, C.byref(s)), ctx)
     return s
+
+
+def qym_get_params(ctx) -> qym_params:
+    """The parameters the context runs with (the library's choices filled in)."""
+    p = qym_params()
+    _check(lib().qym_get_params(ctx, C.byref(p)), ctx)
+    return p
 
 
 def qym_set_mlp(ctx, weights):
@@ -434,6 +443,9 @@ class Simulation:
 
     def stats(self):
         return qym_get_stats(self.ctx).as_dict()
+
+    def effective_params(self):
+        return qym_get_params(self.ctx)
 
     def set_mlp(self, weights):
         qym_set_mlp(self.ctx, weights)

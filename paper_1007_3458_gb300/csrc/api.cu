@@ -116,7 +116,7 @@ extern "C" qym_status qym_default_params(qym_params *p) {
     p->max_log = 0;
     p->l2_flush_bytes = 0;
     p->heavy_mass = 1e-7;
-    p->search = QYM_SEARCH_BINNED;
+    p->search = QYM_SEARCH_AUTO;
     return QYM_OK;
 }
 
@@ -133,8 +133,9 @@ static bool valid_params(const qym_params *p, std::string &why) {
     if (p->max_candidates < 0 || p->max_encounters < 0 || p->max_log < 0) { why = "capacities"; return false; }
     if (p->l2_flush_bytes < 0 || p->l2_flush_bytes > ((int64_t)1 << 34)) { why = "l2_flush_bytes"; return false; }
     if (p->merge_kicks != 0 && p->merge_kicks != 1) { why = "merge_kicks must be 0 or 1"; return false; }
-    if (p->search != QYM_SEARCH_FUSED && p->search != QYM_SEARCH_BINNED) {
-        why = "search must be QYM_SEARCH_FUSED or QYM_SEARCH_BINNED";
+    if (p->search != QYM_SEARCH_FUSED && p->search != QYM_SEARCH_BINNED &&
+        p->search != QYM_SEARCH_AUTO) {
+        why = "search must be QYM_SEARCH_AUTO, QYM_SEARCH_FUSED or QYM_SEARCH_BINNED";
         return false;
     }
     if (p->hermite_cluster != 0 && p->hermite_cluster != 2 && p->hermite_cluster != 4 &&
@@ -149,6 +150,8 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // bodies from which a single system's kick holds them in Morton order
 constexpr int64_t kSortMinBodies = 2048;
+// bodies from which QYM_SEARCH_AUTO takes the binned search for one system
+constexpr int64_t kBinnedMinBodies = 65536;
 // steps between re-sorts inside one qym_step call (bodies drift apart slowly;
 // the order only affects speed)
 constexpr int64_t kSortEvery = 32;
@@ -237,7 +240,7 @@ static void carve_all(qym_ctx *c, Carver &k) {
     }
     if (c->binned) {
         SearchArgs &a = c->sarg;
-        a.vmax = k.take<int32_t>(d.nsys);
+        d.vmax = k.take<int32_t>(d.nsys);
         a.box_lo = k.take<float4>(R);
         a.box_hi = k.take<float4>(R);
         a.x0h = k.take<float4>(R);
@@ -246,11 +249,11 @@ static void carve_all(qym_ctx *c, Carver &k) {
         a.x1l = k.take<float4>(R);
         a.v0f = k.take<float4>(R);
         a.v1f = k.take<float4>(R);
-        a.tbox = k.take<float4>(2 * (size_t)c->nstiles);
+        a.tbox_bits = k.take<int>(6 * (size_t)c->nstiles);
+        a.tile0 = k.take<int32_t>(d.nsys);
         a.tiles = k.take<int4>(c->nstiles);
         a.tpairs = k.take<int2>(c->nstpairs);
         a.active = k.take<int2>(c->nstpairs);
-        a.nactive = k.take<unsigned long long>(1);
         a.ntiles = c->nstiles;
         a.ntpairs = c->nstpairs;
     }
@@ -422,7 +425,15 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     // one system of at least two tiles' worth of bodies, mixed kick: the kick
     // holds the bodies in Morton order (sort.cu)
     c->sort_rows = nsys == 1 && params->kick_prec == QYM_KICK_MIXED && R - 1 >= kSortMinBodies;
-    c->binned = params->encounters && params->search == QYM_SEARCH_BINNED;
+    // measured on one GB300 (same trajectories, so the same encounter work):
+    // 16384-body disk 1.40 ms per step binned against 1.33 fused, the
+    // 512-system ensemble 23.6 against 20.3 ms, the 262144-body disk 64.9
+    // against 66.1 ms
+    const bool auto_binned = nsys == 1 && R - 1 >= kBinnedMinBodies;
+    c->binned = params->encounters &&
+                (params->search == QYM_SEARCH_BINNED ||
+                 (params->search == QYM_SEARCH_AUTO && auto_binned));
+    c->p.search = c->binned ? QYM_SEARCH_BINNED : QYM_SEARCH_FUSED;
     std::vector<int4> stiles;
     std::vector<int2> stpairs;
     if (c->binned) {
@@ -486,6 +497,10 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     CKI(cudaMemcpyAsync(d.heavy_start, hstart.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, c->stream));
     CKI(cudaMemcpyAsync(d.heavy_thr, hthr.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, c->stream));
     if (c->binned && c->nstiles) {
+        std::vector<int32_t> t0(nsys);
+        for (size_t t = stiles.size(); t-- > 0;) t0[stiles[t].x] = (int32_t)t;
+        CKI(cudaMemcpyAsync((void *)c->sarg.tile0, t0.data(), sizeof(int32_t) * nsys,
+                            cudaMemcpyHostToDevice, c->stream));
         CKI(cudaMemcpyAsync((void *)c->sarg.tiles, stiles.data(), sizeof(int4) * stiles.size(),
                             cudaMemcpyHostToDevice, c->stream));
         CKI(cudaMemcpyAsync((void *)c->sarg.tpairs, stpairs.data(), sizeof(int2) * stpairs.size(),
@@ -524,8 +539,14 @@ extern "C" qym_status qym_shape(const qym_ctx *c, int64_t *rows, int32_t *nsys) 
 }
 
 // ------------------------------------------------------------------ step
-__global__ void k_step_begin(unsigned long long *ctr) {
+__global__ void k_step_begin(unsigned long long *ctr, int32_t *vmax, int32_t nsys, int *tbits,
+                             int64_t ntb) {
+    if (vmax)  // the binned search's largest |v| per system, raised by the first finisher
+        for (int32_t s = threadIdx.x; s < nsys; s += blockDim.x) vmax[s] = 0;
+    for (int64_t k = threadIdx.x; k < ntb; k += blockDim.x) tbits[k] = 0x7fffffff;  // tile boxes
+    if (threadIdx.x) return;
     ctr[C_NCAND] = 0;
+    ctr[C_NACTIVE] = 0;
     ctr[C_NENC] = 0;
     ctr[C_NRESCAN] = 0;
     ctr[C_NSETS] = 0;
@@ -586,7 +607,7 @@ static int fused_search(const qym_ctx *c) { return (c->p.encounters && !c->binne
 // the binned search's candidates, after the Kepler drift
 static cudaError_t enqueue_binned_search(qym_ctx *c, double tau) {
     if (!c->binned) return cudaSuccess;
-    c->launches += 5;
+    c->launches += 3;
     return launch_binned_search(c->d, c->sarg, tau, c->p.a_E, c->stream);
 }
 
@@ -637,7 +658,7 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last, bool fresh = 
     if (c->flush) {
         if ((e = cudaMemsetAsync(c->flush, c->launches & 0xff, (size_t)p.l2_flush_bytes, st))) return e;
     }
-    k_step_begin<<<1, 1, 0, st>>>(d.ctr);
+    k_step_begin<<<1, 256, 0, st>>>(d.ctr, d.vmax, d.nsys, c->sarg.tbox_bits, c->binned ? 6 * (int64_t)c->nstiles : 0);
     const int fz = fused_search(c);
     // item 2: kick tau/2, with the crude encounter search when it is fused
     if (fz && fresh) {
@@ -688,7 +709,7 @@ static cudaError_t enqueue_opening_kick(qym_ctx *c, double tau, bool fresh) {
     const qym_params &p = c->p;
     cudaStream_t st = c->stream;
     cudaError_t e;
-    k_step_begin<<<1, 1, 0, st>>>(d.ctr);
+    k_step_begin<<<1, 256, 0, st>>>(d.ctr, d.vmax, d.nsys, c->sarg.tbox_bits, c->binned ? 6 * (int64_t)c->nstiles : 0);
     c->launches += 1;
     const int fz = fused_search(c);
     if (fz && fresh) return enqueue_fresh_search_kick(c, 0.5 * tau);
@@ -729,7 +750,7 @@ static cudaError_t enqueue_unit(qym_ctx *c, double tau, bool last) {
                                     0.5 * tau)))
         return e;
     if (!last) {
-        k_step_begin<<<1, 1, 0, st>>>(d.ctr);
+        k_step_begin<<<1, 256, 0, st>>>(d.ctr, d.vmax, d.nsys, c->sarg.tbox_bits, c->binned ? 6 * (int64_t)c->nstiles : 0);
         if ((e = launch_momentum(d, st))) return e;
         // the last kick was a step earlier: its |a| bounds this one's only
         // loosely, so the crude reach allows twice it (and the finisher checks)
@@ -917,6 +938,12 @@ extern "C" qym_status qym_energy(qym_ctx *c, double *E) {
     return QYM_OK;
 }
 
+extern "C" qym_status qym_get_params(const qym_ctx *c, qym_params *p) {
+    if (!c || !p) FAIL(c, QYM_EINVAL, "qym_get_params: NULL argument");
+    *p = c->p;
+    return QYM_OK;
+}
+
 extern "C" qym_status qym_get_stats(qym_ctx *c, qym_stats *s) {
     if (!c || !s) FAIL(c, QYM_EINVAL, "qym_get_stats: NULL argument");
     *s = c->stats;
@@ -1101,7 +1128,7 @@ extern "C" qym_status qym_split_phase(qym_ctx *c, int32_t phase, double tau, int
         break;
     }
     case QYM_PHASE_KICK1: {
-        k_step_begin<<<1, 1, 0, st>>>(d.ctr);
+        k_step_begin<<<1, 256, 0, st>>>(d.ctr, d.vmax, d.nsys, c->sarg.tbox_bits, c->binned ? 6 * (int64_t)c->nstiles : 0);
         const int flag = (enc && !c->split_fresh) ? KICK_SEARCH : KICK_FORCE;
         CK(c, launch_kick_tiles(d, p.kick_prec, flag, p.G, c->tune.threads, c->tune.ipt, st));
         CK(c, launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, flag == KICK_SEARCH, p.hill_fixed, st));

@@ -87,6 +87,8 @@ struct Dev {
     // order of the bodies in the kick's packs and partial sums (sort.cu):
     // position p holds row perm[p], row r sits at position inv[r]; NULL: row order
     int32_t *perm = nullptr, *inv = nullptr;
+    int32_t *vmax = nullptr; // [nsys] largest |v| after the first kick (float bits), for the
+                             // binned search; NULL: not kept
     float4 *far = nullptr;   // [rows] (offset from the tile's reference point, G m) in that order
     float4 *tile = nullptr;  // [3 x tiles] reference point and radius, box min, box max
 };
@@ -112,6 +114,7 @@ enum Ctr : int {
     C_NFCHUNK,       // flagged (row, j chunk) entries of the last search kick
     C_FCDONE,        // CTAs of the chunk re-test done (its last CTA resets both)
     C_HNQ,           // sets in the Hermite kernel's per-CTA queue this step
+    C_NACTIVE,       // overlapping tile pairs of the binned search (reset per step)
     C_COUNT
 };
 
@@ -274,16 +277,16 @@ cudaError_t launch_sort_rows(int64_t rows, const double *q, const SortScratch &s
 // search.cu: candidates by spatial binning after the Kepler drift
 struct SearchArgs {
     double tau, a_E;
-    const int32_t *vmax;     // [nsys] float bits
     float4 *box_lo, *box_hi; // [rows] widened boxes by position
     float4 *x0h, *x0l, *x1h, *x1l, *v0f, *v1f;  // [rows] by position (x0h.w: a_E r_H)
-    float4 *tbox;            // [2 x tiles] tile boxes (lo, hi)
+    int *tbox_bits;          // [6 x tiles] tile boxes: min x, y, z, -max x, y, z as ordered
+                             // integer images (reset to INT_MAX every step)
+    const int32_t *tile0;    // [nsys] first tile of each system
     const int4 *tiles;       // (system, p0, p1, -)
     int32_t ntiles;
     const int2 *tpairs;      // (tile I, tile J), I <= J, same system
     int64_t ntpairs;
-    int2 *active;            // tile pairs whose boxes overlap
-    unsigned long long *nactive;
+    int2 *active;            // [ntpairs] tile pairs whose boxes overlap (count: C_NACTIVE)
 };
 cudaError_t launch_binned_search(const Dev &d, const SearchArgs &s, double tau, double a_E,
                                  cudaStream_t st);

@@ -20,14 +20,16 @@
 // the boxes that hold H_i([0, 1]) and H_j([0, 1]), each widened by its body's
 // a_E r_H + e_k, do not overlap, the test cannot flag the pair.
 //
-// The pass. Per body its widened box (k_search_prep); per tile of 256
+// The pass. Each body's widened box at its position in tiles of 256
 // consecutive positions (the kick's Morton order for one system, row order in
-// a batch) the union of its bodies' boxes (k_search_tiles); tile pairs of a
-// system whose boxes overlap (k_search_tilepairs); and per such tile pair,
-// each body pair whose boxes overlap is tested with the rigorous test's cubic
-// in FP32 on positions relative to a point of the first tile, with an error
-// allowance that keeps the FP32 form from rejecting any pair the FP64 test
-// (k_refine) can flag; the pairs that pass are the candidates.
+// a batch), and the union of each tile's boxes (k_search_prep; V from the
+// first kick's finisher); then
+// the tile pairs of a system whose boxes overlap (k_search_tilepairs) and,
+// per such pair, each body pair whose boxes overlap tested with the rigorous
+// test's cubic in FP32 on positions relative to a point of the first tile,
+// with an error allowance that keeps the FP32 form from rejecting any pair the
+// FP64 test (k_refine) can flag (k_search_pairs); the pairs that pass are the
+// candidates.
 #include <algorithm>
 #include <vector>
 
@@ -36,17 +38,6 @@
 namespace qym {
 
 constexpr int kSTile = 256;  // positions per search tile
-
-// V = largest |v0| of each system's bodies, as float bits (non-negative floats
-// order like their bit patterns), raised by atomics
-__global__ void __launch_bounds__(256) k_search_vmax(Dev d, int32_t *vmax) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= d.rows) return;
-    const int64_t R = d.rows;
-    const double vx = d.v[r], vy = d.v[R + r], vz = d.v[2 * R + r];
-    const float s = __double2float_ru(sqrt(vx * vx + vy * vy + vz * vz));
-    atomicMax(vmax + d.sys_of[r], __float_as_int(s));
-}
 
 // extremes over s in [0, 1] of a + b s + c s^2 + d s^3
 __device__ __forceinline__ void cubic_range(double a, double b, double c, double d, double &lo,
@@ -79,79 +70,79 @@ __device__ __forceinline__ void cubic_range(double a, double b, double c, double
 }
 
 
-// per body: its widened box and its FP32 state, at its position
+// Four lanes per body (three axes and one idle), 8 bodies per warp: each
+// body's widened box and its FP32 state at its position, and the union of the
+// boxes of each tile, raised with atomics on order-preserving integer images
+// of the floats (order-independent, so deterministic).
+__device__ __forceinline__ int fbits(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float fvalue(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
 __global__ void __launch_bounds__(256) k_search_prep(Dev d, SearchArgs s) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= d.rows) return;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = gt >> 2;           // position
+    const int k = (int)(gt & 3);         // axis (3: idle)
+    const bool body = p < d.rows && d.offsets[d.sys_of[d.perm ? d.perm[p] : p]] != (d.perm ? d.perm[p] : p);
     const int64_t R = d.rows;
-    const int64_t p = d.inv ? d.inv[r] : r;
-    const int sys = d.sys_of[r];
-    if (d.offsets[sys] == r) {  // star rows: an empty box
-        s.box_lo[p] = make_float4(3e38f, 3e38f, 3e38f, 0.f);
-        s.box_hi[p] = make_float4(-3e38f, -3e38f, -3e38f, 0.f);
-        return;
-    }
-    const double tau = s.tau, at = fabs(tau);
-    double lo[3], hi[3], cc = 0.0, dd = 0.0, qq = 0.0;
-    float q0h[3], q0l[3], q1h[3], q1l[3], vf0[3], vf1[3];
-    for (int k = 0; k < 3; ++k) {
+    const int64_t r = p < d.rows ? (d.perm ? d.perm[p] : p) : 0;
+    const double tau = s.tau;
+    double lo = 0.0, hi = 0.0, c2 = 0.0, d2 = 0.0, qa = 0.0;
+    float qh = 0.f, ql = 0.f, eh = 0.f, el = 0.f, v0f = 0.f, v1f = 0.f;
+    if (body && k < 3) {
         const double a = d.q[k * R + r], v0 = d.v[k * R + r];
         const double e = d.q1[k * R + r], v1 = d.v1[k * R + r];
         const double b = tau * v0;
         const double c = 3.0 * (e - a) - tau * (2.0 * v0 + v1);
         const double dk = 2.0 * (a - e) + tau * (v0 + v1);
-        cubic_range(a, b, c, dk, lo[k], hi[k]);
-        cc += c * c;
-        dd += dk * dk;
-        qq = fmax(qq, fmax(fabs(a), fabs(e)));
-        split_ds(a, q0h[k], q0l[k]);
-        split_ds(e, q1h[k], q1l[k]);
-        vf0[k] = (float)v0;
-        vf1[k] = (float)v1;
+        cubic_range(a, b, c, dk, lo, hi);
+        c2 = c * c;
+        d2 = dk * dk;
+        qa = fmax(fabs(a), fabs(e));
+        split_ds(a, qh, ql);
+        split_ds(e, eh, el);
+        v0f = (float)v0;
+        v1f = (float)v1;
     }
-    const double V = (double)__int_as_float(s.vmax[sys]);
-    const double C = sqrt(cc), D = sqrt(dd);
-    const double ek = 0.25 * (C + 3.0 * D) + 0.5 * sqrt(at * V * D);
-    const double thr = s.a_E * d.rH[r];
-    // widened by a_E r_H + e_k, and by 1e-12 of the coordinates for the
-    // rounding of the cubic's coefficients and extremes here and in the test
-    const double w = (thr + ek) * (1.0 + 1e-9) + 1e-12 * qq;
-    s.box_lo[p] = make_float4(__double2float_rd(lo[0] - w), __double2float_rd(lo[1] - w),
-                              __double2float_rd(lo[2] - w), 0.f);
-    s.box_hi[p] = make_float4(__double2float_ru(hi[0] + w), __double2float_ru(hi[1] + w),
-                              __double2float_ru(hi[2] + w), 0.f);
-    s.x0h[p] = make_float4(q0h[0], q0h[1], q0h[2], __double2float_ru(thr));
-    s.x0l[p] = make_float4(q0l[0], q0l[1], q0l[2], 0.f);
-    s.x1h[p] = make_float4(q1h[0], q1h[1], q1h[2], 0.f);
-    s.x1l[p] = make_float4(q1l[0], q1l[1], q1l[2], 0.f);
-    s.v0f[p] = make_float4(vf0[0], vf0[1], vf0[2], 0.f);
-    s.v1f[p] = make_float4(vf1[0], vf1[1], vf1[2], 0.f);
-}
-
-// per tile: the union of its bodies' boxes
-__global__ void __launch_bounds__(kSTile) k_search_tiles(SearchArgs s) {
-    __shared__ float sm[kSTile / 32][6];
-    const int4 t = s.tiles[blockIdx.x];
-    const int64_t p = t.y + threadIdx.x;
-    float m[6] = {3e38f, 3e38f, 3e38f, 3e38f, 3e38f, 3e38f};
-    if (p < t.z) {
-        const float4 a = s.box_lo[p], b = s.box_hi[p];
-        m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = -b.x; m[4] = -b.y; m[5] = -b.z;
+    // |c|^2, |d|^2 and the largest coordinate over the body's three lanes
+    c2 += __shfl_xor_sync(0xffffffffu, c2, 1);
+    c2 += __shfl_xor_sync(0xffffffffu, c2, 2);
+    d2 += __shfl_xor_sync(0xffffffffu, d2, 1);
+    d2 += __shfl_xor_sync(0xffffffffu, d2, 2);
+    qa = fmax(qa, __shfl_xor_sync(0xffffffffu, qa, 1));
+    qa = fmax(qa, __shfl_xor_sync(0xffffffffu, qa, 2));
+    float blo = 3e38f, bhi = -3e38f;
+    if (body) {
+        const double V = (double)__int_as_float(d.vmax[d.sys_of[r]]);
+        const double ek = 0.25 * (sqrt(c2) + 3.0 * sqrt(d2)) + 0.5 * sqrt(fabs(tau) * V * sqrt(d2));
+        const double thr = s.a_E * d.rH[r];
+        // widened by a_E r_H + e_k, and by 1e-12 of the coordinates for the
+        // rounding of the cubic's coefficients and extremes here and in the test
+        const double w = (thr + ek) * (1.0 + 1e-9) + 1e-12 * qa;
+        if (k < 3) {
+            blo = __double2float_rd(lo - w);
+            bhi = __double2float_ru(hi + w);
+        }
+        if (k == 3) ((float *)(s.x0h + p))[3] = __double2float_ru(thr);
     }
-#pragma unroll
-    for (int q = 0; q < 6; ++q) m[q] = warp_min(m[q]);
-    if ((threadIdx.x & 31) == 0)
-        for (int q = 0; q < 6; ++q) sm[threadIdx.x >> 5][q] = m[q];
-    __syncthreads();
-    if (threadIdx.x < 6) {
-        float v = sm[0][threadIdx.x];
-        for (int w = 1; w < kSTile / 32; ++w) v = fminf(v, sm[w][threadIdx.x]);
-        sm[0][threadIdx.x] = v;
+    // scatter the lanes' components into the per-position float4s
+    if (p < d.rows && k < 3) {
+        ((float *)(s.box_lo + p))[k] = body ? blo : 3e38f;
+        ((float *)(s.box_hi + p))[k] = body ? bhi : -3e38f;
+        ((float *)(s.x0h + p))[k] = qh;
+        ((float *)(s.x0l + p))[k] = ql;
+        ((float *)(s.x1h + p))[k] = eh;
+        ((float *)(s.x1l + p))[k] = el;
+        ((float *)(s.v0f + p))[k] = v0f;
+        ((float *)(s.v1f + p))[k] = v1f;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s.tbox[2 * blockIdx.x] = make_float4(sm[0][0], sm[0][1], sm[0][2], 0.f);
-        s.tbox[2 * blockIdx.x + 1] = make_float4(-sm[0][3], -sm[0][4], -sm[0][5], 0.f);
+    // the tile's box: each lane holds one axis of one body
+    if (body && k < 3) {
+        const int sys = d.sys_of[r];
+        const int64_t tile = s.tile0[sys] + (p - d.offsets[sys] - 1) / kSTile;
+        atomicMin(s.tbox_bits + 6 * tile + k, fbits(blo));
+        atomicMin(s.tbox_bits + 6 * tile + 3 + k, fbits(-bhi));
     }
 }
 
@@ -160,22 +151,10 @@ __device__ __forceinline__ bool boxes_overlap(float4 al, float4 ah, float4 bl, f
            bl.z <= ah.z;
 }
 
-__global__ void __launch_bounds__(256) k_search_tilepairs(SearchArgs s, int32_t *status) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool hit = false;
-    int2 tp = make_int2(0, 0);
-    if (k < s.ntpairs) {
-        tp = s.tpairs[k];
-        hit = boxes_overlap(s.tbox[2 * tp.x], s.tbox[2 * tp.x + 1], s.tbox[2 * tp.y],
-                            s.tbox[2 * tp.y + 1]);
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, hit);
-    if (!m) return;
-    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(s.nactive, (unsigned long long)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (hit) s.active[base + __popc(m & ((1u << lane) - 1u))] = tp;
+__device__ __forceinline__ void tile_box(const SearchArgs &s, int t, float4 &lo, float4 &hi) {
+    const int *b = s.tbox_bits + 6 * t;
+    lo = make_float4(fvalue(b[0]), fvalue(b[1]), fvalue(b[2]), 0.f);
+    hi = make_float4(-fvalue(b[3]), -fvalue(b[4]), -fvalue(b[5]), 0.f);
 }
 
 // candidate (i, j), rows, smaller first: warp-aggregated append
@@ -226,6 +205,26 @@ __device__ __forceinline__ bool cubic_may_flag(const float *oi0, const float *oi
     const float s0 = 2.0f * g0 * tau, s1 = 2.0f * g1 * tau;
     const float c2 = 3.0f * (y1 - y0) - 2.0f * s0 - s1;
     const float c3 = 2.0f * (y0 - y1) + s0 + s1;
+    // The FP64 test's cubic and this one differ by the inputs' errors (the
+    // offsets and velocities each within 2^-24 relative, their differences
+    // within eq, ev) carried through y, g (values and slopes enter p with
+    // weights at most 1 and 4/27), and by the rounding here (a generous
+    // 2^-18 of the terms' magnitudes), and the FP32 root can miss the exact
+    // stationary point; the minimum over [0, 1] moves by at most the largest
+    // change of p, which the allowance bounds.
+    const float eq = 4.0f * 5.96e-8f * m_q, ev = 4.0f * 5.96e-8f * m_v;
+    const float nq0 = sqrtf(y0), nq1 = sqrtf(y1);
+    const float nv0 = sqrtf(dv0[0] * dv0[0] + dv0[1] * dv0[1] + dv0[2] * dv0[2]);
+    const float nv1 = sqrtf(dv1[0] * dv1[0] + dv1[1] * dv1[1] + dv1[2] * dv1[2]);
+    const float at = fabsf(tau);
+    const float ey = (2.0f * nq0 + eq) * eq + (2.0f * nq1 + eq) * eq;
+    const float es = 2.0f * at * ((nq0 + eq) * ev + nv0 * eq + (nq1 + eq) * ev + nv1 * eq);
+    const float mag = y0 + y1 + fabsf(s0) + fabsf(s1) + fabsf(c2) + fabsf(c3);
+    const float allow = 1.01f * (ey + es) + 3.8e-6f * mag;
+    const float t2 = thr * thr * 1.0001f;
+    // in the Hermite form p = h00 y0 + h01 y1 + h10 s0 + h11 s1 (h00 + h01 = 1,
+    // both >= 0; |h10|, |h11| <= 4/27): p >= min(y0, y1) - 4/27 (|s0| + |s1|)
+    if (fminf(y0, y1) - 0.14815f * (fabsf(s0) + fabsf(s1)) - allow >= t2) return false;
     float best = fminf(y0, y1);
     const float A = 3.0f * c3, B = 2.0f * c2;
     // also at the inflection point -B / 2A: where the two stationary points
@@ -245,23 +244,28 @@ __device__ __forceinline__ bool cubic_may_flag(const float *oi0, const float *oi
             if (u[k] > 0.0f && u[k] < 1.0f)
                 best = fminf(best, y0 + u[k] * (s0 + u[k] * (c2 + u[k] * c3)));
     }
-    // The FP64 test's cubic and this one differ by the inputs' errors (the
-    // offsets and velocities each within 2^-24 relative, their differences
-    // within eq, ev) carried through y, g (values and slopes enter p with
-    // weights at most 1 and 4/27), and by the rounding here (a generous
-    // 2^-18 of the terms' magnitudes), and the FP32 root can miss the exact
-    // stationary point; the minimum over [0, 1] moves by at most the largest
-    // change of p, which the allowance bounds.
-    const float eq = 4.0f * 5.96e-8f * m_q, ev = 4.0f * 5.96e-8f * m_v;
-    const float nq0 = sqrtf(y0), nq1 = sqrtf(y1);
-    const float nv0 = sqrtf(dv0[0] * dv0[0] + dv0[1] * dv0[1] + dv0[2] * dv0[2]);
-    const float nv1 = sqrtf(dv1[0] * dv1[0] + dv1[1] * dv1[1] + dv1[2] * dv1[2]);
-    const float at = fabsf(tau);
-    const float ey = (2.0f * nq0 + eq) * eq + (2.0f * nq1 + eq) * eq;
-    const float es = 2.0f * at * ((nq0 + eq) * ev + nv0 * eq + (nq1 + eq) * ev + nv1 * eq);
-    const float mag = y0 + y1 + fabsf(s0) + fabsf(s1) + fabsf(c2) + fabsf(c3);
-    const float allow = 1.01f * (ey + es) + 3.8e-6f * mag;
-    return best - allow < thr * thr * 1.0001f;
+    return best - allow < t2;
+}
+
+// tile pairs of a system whose boxes overlap, appended to the active list
+__global__ void __launch_bounds__(256) k_search_tilepairs(Dev d, SearchArgs s) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool hit = false;
+    int2 tp = make_int2(0, 0);
+    if (k < s.ntpairs) {
+        tp = s.tpairs[k];
+        float4 al, ah, bl, bh;
+        tile_box(s, tp.x, al, ah);
+        tile_box(s, tp.y, bl, bh);
+        hit = boxes_overlap(al, ah, bl, bh);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(d.ctr + C_NACTIVE, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (hit) s.active[base + __popc(m & ((1u << lane) - 1u))] = tp;
 }
 
 // one CTA per overlapping tile pair (I, J): tile J staged in shared memory
@@ -270,13 +274,14 @@ __global__ void __launch_bounds__(kSTile) k_search_pairs(Dev d, SearchArgs s) {
     __shared__ float4 j_lo[kSTile], j_hi[kSTile];
     __shared__ float j_o0[kSTile][3], j_o1[kSTile][3], j_v0[kSTile][3], j_v1[kSTile][3];
     __shared__ float j_thr[kSTile];
-    const unsigned long long na = min(*(volatile unsigned long long *)s.nactive,
+    const unsigned long long na = min(*(volatile unsigned long long *)(d.ctr + C_NACTIVE),
                                       (unsigned long long)s.ntpairs);
-    for (unsigned long long k = blockIdx.x; k < na; k += gridDim.x) {
-        const int2 tp = s.active[k];
-        const int4 ti = s.tiles[tp.x], tj = s.tiles[tp.y];
-        // reference point: the low corner of tile I's box (FP32, both tiles near it)
-        const float4 cref = s.tbox[2 * tp.x];
+    for (unsigned long long h = blockIdx.x; h < na; h += gridDim.x) {
+        const int2 tq = s.active[h];
+        const int4 ti = s.tiles[tq.x], tj = s.tiles[tq.y];
+        // reference point: the low corner of tile I's box (both tiles near it)
+        float4 cref, chi;
+        tile_box(s, tq.x, cref, chi);
         __syncthreads();
         {
             const int64_t p = tj.y + threadIdx.x;
@@ -298,18 +303,30 @@ __global__ void __launch_bounds__(kSTile) k_search_pairs(Dev d, SearchArgs s) {
         }
         __syncthreads();
         const int64_t pi = ti.y + threadIdx.x;
+        // the warp's union box: a j whose box misses it is skipped by the
+        // whole warp at once
+        float4 il = make_float4(3e38f, 3e38f, 3e38f, 0.f), ih = make_float4(-3e38f, -3e38f, -3e38f, 0.f);
+        if (pi < ti.z) {
+            il = s.box_lo[pi];
+            ih = s.box_hi[pi];
+        }
+        const float4 wl = make_float4(warp_min(il.x), warp_min(il.y), warp_min(il.z), 0.f);
+        const float4 wh = make_float4(-warp_min(-ih.x), -warp_min(-ih.y), -warp_min(-ih.z), 0.f);
         if (pi >= ti.z) continue;
-        const float4 il = s.box_lo[pi], ih = s.box_hi[pi];
         const float4 a = s.x0h[pi], al = s.x0l[pi], b = s.x1h[pi], bl = s.x1l[pi];
         const float4 u = s.v0f[pi], w = s.v1f[pi];
-        const float oi0[3] = {ds3(a.x, -cref.x, al.x), ds3(a.y, -cref.y, al.y), ds3(a.z, -cref.z, al.z)};
-        const float oi1[3] = {ds3(b.x, -cref.x, bl.x), ds3(b.y, -cref.y, bl.y), ds3(b.z, -cref.z, bl.z)};
+        const float oi0[3] = {ds3(a.x, -cref.x, al.x), ds3(a.y, -cref.y, al.y),
+                              ds3(a.z, -cref.z, al.z)};
+        const float oi1[3] = {ds3(b.x, -cref.x, bl.x), ds3(b.y, -cref.y, bl.y),
+                              ds3(b.z, -cref.z, bl.z)};
         const float vi0[3] = {u.x, u.y, u.z}, vi1[3] = {w.x, w.y, w.z};
         const int ri = d.perm ? d.perm[pi] : (int)pi;
         const int nj = (int)(tj.z - tj.y);
-        const int j0 = tp.x == tp.y ? (int)threadIdx.x + 1 : 0;  // same tile: j after i
+        const int j0 = tq.x == tq.y ? (int)threadIdx.x + 1 : 0;  // same tile: j after i
         for (int jj = j0; jj < nj; ++jj) {
-            if (!boxes_overlap(il, ih, j_lo[jj], j_hi[jj])) continue;
+            const float4 jl = j_lo[jj], jh = j_hi[jj];
+            if (!boxes_overlap(wl, wh, jl, jh)) continue;
+            if (!boxes_overlap(il, ih, jl, jh)) continue;
             if (!cubic_may_flag(oi0, oi1, vi0, vi1, j_o0[jj], j_o1[jj], j_v0[jj], j_v1[jj],
                                 a.w + j_thr[jj], (float)s.tau))
                 continue;
@@ -324,14 +341,9 @@ cudaError_t launch_binned_search(const Dev &d, const SearchArgs &s0, double tau,
     SearchArgs s = s0;
     s.tau = tau;
     s.a_E = a_E;
-    cudaError_t e = cudaMemsetAsync((void *)s.vmax, 0, sizeof(int32_t) * d.nsys, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s.nactive, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return e;
-    const unsigned g = (unsigned)((d.rows + 255) / 256);
-    k_search_vmax<<<g, 256, 0, st>>>(d, (int32_t *)s.vmax);
-    k_search_prep<<<g, 256, 0, st>>>(d, s);
-    k_search_tiles<<<s.ntiles, kSTile, 0, st>>>(s);
-    k_search_tilepairs<<<(unsigned)((s.ntpairs + 255) / 256), 256, 0, st>>>(s, d.status);
+    if (s.ntiles <= 0) return cudaSuccess;
+    k_search_prep<<<(unsigned)((4 * d.rows + 255) / 256), 256, 0, st>>>(d, s);
+    k_search_tilepairs<<<(unsigned)((s.ntpairs + 255) / 256), 256, 0, st>>>(d, s);
     k_search_pairs<<<4 * 152, kSTile, 0, st>>>(d, s);
     return cudaGetLastError();
 }

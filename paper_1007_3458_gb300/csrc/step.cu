@@ -215,6 +215,8 @@ __global__ void __launch_bounds__(256) k_finish(Dev d, FinishArgs a) {
     a.v[r] = vx; a.v[R + r] = vy; a.v[2 * R + r] = vz;
     float an = round_up_f(sqrt(ax * ax + ay * ay + az * az));
     if (a.check) {
+        if (d.vmax)  // the binned search's bound takes the largest |v| entering the drift
+            atomicMax(d.vmax + sys, __float_as_int(round_up_f(sqrt(vx * vx + vy * vy + vz * vz))));
         const double m0 = d.m[star];
         double rH = a.hill_fixed ? d.rH_fixed[r] : hill(a.q[r], a.q[R + r], a.q[2 * R + r], d.m[r], m0);
         d.rH[r] = rH;

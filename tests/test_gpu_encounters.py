@@ -128,3 +128,15 @@ def test_search_superset_adversarial(torch, oracle, prec, merge, search):
     print(f"\n  {checked} records over {len(calls)} checked steps")
     assert checked > 50
     sim.close()
+
+
+def test_auto_search_choice(torch):
+    """QYM_SEARCH_AUTO (the default) takes the binned search for one system of
+    at least 65536 bodies and the fused one otherwise; qym_get_params reports
+    the choice."""
+    for w, want in ((W.disk_262144(), q.QYM_SEARCH_BINNED), (W.disk_16384(), q.QYM_SEARCH_FUSED),
+                     (W.ensemble(nsys=4, n_lo=64, n_hi=200), q.QYM_SEARCH_FUSED)):
+        sim = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H)
+        assert sim.params.search == q.QYM_SEARCH_AUTO
+        assert sim.effective_params().search == want, w.name
+        sim.close()
