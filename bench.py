@@ -154,6 +154,9 @@ class ClockSampler:
 # with the splits. A shape or a kick source not captured reports null (the
 # capture commands sit with the ncu summaries under profiles/).
 KICK_DRAM_BYTES = {
+    # shape 128 threads x 2 rows x 64 splits (256 rows per CTA)
+    ("disk_16384", 256, 64, "05e8966306e64e5a"): 8.94e5,
+    ("disk_262144", 256, 64, "05e8966306e64e5a"): 3.64e8,
 }
 
 
@@ -524,7 +527,9 @@ def run_ours(args):
     sim = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=prec, device=dev,
                        l2_flush_bytes=256 << 20, eps_H=w.eps_H, merge_kicks=args.merge_kicks,
                        search=search)
-    if args.autotune:
+    if args.shape:
+        q.qym_set_kick_shape(sim.ctx, *[int(x) for x in args.shape.split(",")])
+    elif args.autotune:
         q.qym_autotune(sim.ctx)
     if args.kick_only:
         # a few launches of the kick kernels alone (for a profiler capture)
@@ -916,6 +921,8 @@ def main():
     ap.add_argument("--search", default="auto", choices=["auto", "binned", "fused"],
                     help="close-encounter search: binned after the drift, fused into the kick, "
                          "or the library's choice for the workload")
+    ap.add_argument("--shape", default="",
+                    help="threads,ipt,splits: the kick's launch shape instead of autotuning")
     ap.add_argument("--search-too", type=int, default=1,
                     help="also time the other encounter search and report it under other_search")
     ap.add_argument("--split", type=int, default=0,

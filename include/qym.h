@@ -282,6 +282,12 @@ qym_status qym_get_stream(const qym_ctx *ctx, void **stream);
 qym_status qym_time_kick(qym_ctx *ctx, int32_t with_search, int32_t reps, double *ms_per_launch,
                          int64_t *pairs);
 
+/* Set the kick launch shape: threads per CTA (128 or 256), i rows per thread
+ * (1, 2, or 4 for the mixed kick) and j splits per system (1 .. the largest
+ * the context's buffers hold, at least 4); QYM_EINVAL otherwise. For
+ * reproducing a shape the tuner chose (qym_stats kick_tile_i, _splits). */
+qym_status qym_set_kick_shape(qym_ctx *ctx, int32_t threads, int32_t ipt, int32_t splits);
+
 /* Pick the kick launch shape (threads per CTA, rows per thread, j splits)
  * by timing candidate shapes with qym_time_kick on the current state, and
  * keep the fastest. The state is unchanged; results can differ from the

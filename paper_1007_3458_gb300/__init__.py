@@ -110,6 +110,7 @@ def lib():
     L.qym_get_stream.argtypes = [P, C.POINTER(P)]
     L.qym_time_kick.argtypes = [P, C.c_int32, C.c_int32, D, I64]
     L.qym_autotune.argtypes = [P]
+    L.qym_set_kick_shape.argtypes = [P, C.c_int32, C.c_int32, C.c_int32]
     L.qym_kepler_drift_dev.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_int32,
                                        C.c_int32, P, C.c_int32, P, P, P, P, P, P]
     L.qym_set_kepler_log.argtypes = [P, P, C.c_int64]
@@ -150,7 +151,7 @@ def lib():
     for name in ("qym_default_params", "qym_init", "qym_step", "qym_get_state", "qym_set_state",
                  "qym_get_encounters", "qym_energy", "qym_get_stats", "qym_get_params",
                  "qym_set_mlp", "qym_shape",
-                 "qym_get_stream", "qym_time_kick", "qym_autotune",
+                 "qym_get_stream", "qym_time_kick", "qym_autotune", "qym_set_kick_shape",
                  "qym_kepler_drift_dev", "qym_accel_dev", "qym_encounter_test_dev",
                  "qym_energy_dev", "qym_set_kepler_log", "qym_mlp_forward_dev",
                  "qym_mlp_grad_dev", "qym_mlp_adam_dev", "qym_mlp_train_dev",
@@ -230,6 +231,10 @@ def qym_time_kick(ctx, with_search=0, reps=10):
 
 def qym_autotune(ctx):
     _check(lib().qym_autotune(ctx), ctx)
+
+
+def qym_set_kick_shape(ctx, threads, ipt, splits):
+    _check(lib().qym_set_kick_shape(ctx, threads, ipt, splits), ctx)
 
 
 def qym_get_state(ctx, q=None, v=None):

@@ -70,6 +70,7 @@ struct qym_ctx {
     int64_t *owned_info = nullptr;  // device [2]: first member and count of the own sets
     // the kick's Morton order of the bodies (one system, mixed kick)
     bool sort_rows = false;
+    bool sort_current = false;  // the order was taken from the present state (set_state)
     SortScratch sortw{};
     // binned encounter search (params.search == QYM_SEARCH_BINNED)
     bool binned = false;
@@ -324,6 +325,7 @@ static qym_status upload_state(qym_ctx *c, const double *q, const double *v) {
     if (c->p.coords == 0) CK(c, launch_to_dh_impl(d, 0, nullptr, c->mt, st));
     if (c->p.hill_fixed) CK(c, launch_hill_init(d, c->p.G, st));
     if (d.perm) CK(c, launch_sort_rows(d.rows, d.q, c->sortw, d.perm, d.inv, st));
+    c->sort_current = d.perm != nullptr;
     CK(c, cudaStreamSynchronize(st));
     c->amag_valid = false;
     return QYM_OK;
@@ -828,11 +830,13 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
         CK(c, cudaMemcpyAsync(c->klog_base, &c->klog_steps, sizeof(c->klog_steps),
                               cudaMemcpyHostToDevice, st));
     c->launches = 0;
-    if (d.perm) {
-        // the kick's order from the positions at the start of the call
+    if (d.perm && !c->sort_current) {
+        // the kick's order from the positions at the start of the call (unless
+        // set_state has just taken it)
         CK(c, launch_sort_rows(d.rows, d.q, c->sortw, d.perm, d.inv, st));
         c->launches += 16;
     }
+    c->sort_current = false;
     // without the |a| of an earlier kick the first search runs after its kick
     const bool fresh = !c->amag_valid;
     c->amag_valid = true;  // every kick's finisher records |a|
@@ -1509,6 +1513,25 @@ static qym_status apply_tune(qym_ctx *c, const KickTune &t) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
     }
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_set_kick_shape(qym_ctx *c, int32_t threads, int32_t ipt, int32_t splits) {
+    if (!c) FAIL(nullptr, QYM_EINVAL, "qym_set_kick_shape: NULL context");
+    const bool mixed = c->p.kick_prec == QYM_KICK_MIXED;
+    if ((threads != 128 && threads != 256) || !(ipt == 1 || ipt == 2 || (mixed && ipt == 4)) ||
+        splits < 1 || splits > c->splits_cap)
+        FAIL(c, QYM_EINVAL, "qym_set_kick_shape: threads 128 or 256, ipt 1, 2 (or 4 for the mixed "
+                            "kick), splits 1 .. the context's cap");
+    CK(c, cudaSetDevice(c->p.device));
+    KickTune t;
+    t.threads = threads;
+    t.ipt = ipt;
+    t.splits = splits;
+    qym_status s = apply_tune(c, t);
+    if (s != QYM_OK) return s;
+    c->stats.kick_tile_i = threads * ipt;
+    c->stats.kick_tile_splits = splits;
     return QYM_OK;
 }
 

@@ -188,22 +188,37 @@ struct FinishArgs {
     int check, hill_fixed;
 };
 
+constexpr int kFinLanes = 4;  // lanes that share one row's partial sums
+
 __global__ void __launch_bounds__(256) k_finish(Dev d, FinishArgs a) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= d.rows) return;
+    // kFinLanes lanes per position of the kick's order: lane q sums the slots
+    // q, q + 4, ... (loads coalesced across positions, dependent FP64 adds in
+    // chains a quarter as long), the four parts added in a fixed tree; lane 0
+    // then does the row's own work
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t pr = gt / kFinLanes;
+    const int q = (int)(gt % kFinLanes);
+    const int64_t R = d.rows;
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    if (pr < R)
+        for (int s = q; s < d.splits; s += kFinLanes) {
+            const double *p = d.apart + (int64_t)s * 3 * R;
+            ax += p[pr];
+            ay += p[R + pr];
+            az += p[2 * R + pr];
+        }
+#pragma unroll
+    for (int o = 1; o < kFinLanes; o <<= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+    }
+    if (pr >= R || q != 0) return;
+    const int64_t r = d.perm ? d.perm[pr] : pr;
     if (d.own_hi > 0 && (r < d.own_lo || r >= d.own_hi)) return;  // another GPU's row
     const int sys = d.sys_of[r];
     const int64_t star = d.offsets[sys];
     if (r == star) return;
-    const int64_t R = d.rows;
-    double ax = 0.0, ay = 0.0, az = 0.0;
-    const int64_t pr = d.inv ? d.inv[r] : r;  // the kick's order
-    for (int s = 0; s < d.splits; ++s) {
-        const double *p = d.apart + (int64_t)s * 3 * R;
-        ax += p[pr];
-        ay += p[R + pr];
-        az += p[2 * R + pr];
-    }
     if (d.heavy_split) {
         int h0 = d.heavy_start[sys], h1 = d.heavy_start[sys + 1];
         heavy_pull(d.heavy_rows + h0, h1 - h0, r, a.q[r], a.q[R + r], a.q[2 * R + r], a.q, d.m, R,
@@ -242,7 +257,7 @@ cudaError_t launch_kick_finish_v(const Dev &d, double *v, const double *q, doubl
     a.check = check;
     a.hill_fixed = hill_fixed;
     int tb = 256;
-    k_finish<<<(unsigned)((d.rows + tb - 1) / tb), tb, 0, st>>>(d, a);
+    k_finish<<<(unsigned)((kFinLanes * d.rows + tb - 1) / tb), tb, 0, st>>>(d, a);
     return cudaGetLastError();
 }
 
