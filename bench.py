@@ -153,6 +153,14 @@ class ClockSampler:
 # kick's source at the capture), since the partial-sum slots written grow
 # with the splits. A shape or a kick source not captured reports null (the
 # capture commands sit with the ncu summaries under profiles/).
+# FP64-pipe warp instructions of one k_kepler launch on the 1,048,576 test
+# particles (ncu sm__inst_executed_pipe_fp64.sum), per (solver, guess, source
+# digest of kepler.cu + mlp.cuh)
+KEPLER_FP64_WARP_INST = {
+    ("newton32", "standard", "0b39927b0f9b323f"): 12912141,
+    ("newton", "standard", "0b39927b0f9b323f"): 23561161,
+}
+
 KICK_DRAM_BYTES = {
     # shape 128 threads x 2 rows x 64 splits (256 rows per CTA)
     ("disk_16384", 256, 64, "05e8966306e64e5a"): 8.94e5,
@@ -764,7 +772,8 @@ def run_kepler(args):
     from paper_1007_3458_gb300 import guess as G
     from paper_1007_3458_gb300 import workloads as W
     q.build()
-    solver = q.QYM_SOLVER_NEWTON if args.solver == "newton" else q.QYM_SOLVER_LAGUERRE
+    solver = {"newton": q.QYM_SOLVER_NEWTON, "newton32": q.QYM_SOLVER_NEWTON32,
+              "laguerre": q.QYM_SOLVER_LAGUERRE}[args.solver]
     t_train = time.perf_counter()
     if args.train:
         wts, losses, nrows = G.train_default()
@@ -782,8 +791,8 @@ def run_kepler(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def drift(guess, x=None, it=None, st=None):
-        q.qym_kepler_drift_dev(n, q0, v0, q1, v1, 1.0, dt, solver, guess,
+    def drift(guess, x=None, it=None, st=None, slv=None):
+        q.qym_kepler_drift_dev(n, q0, v0, q1, v1, 1.0, dt, solver if slv is None else slv, guess,
                                wd if guess == q.QYM_GUESS_MLP else None, 50, x_out=x,
                                iters=it, status=st)
 
@@ -794,13 +803,23 @@ def run_kepler(args):
         torch.cuda.synchronize()
 
     res = {}
-    arms = (("standard", q.QYM_GUESS_STANDARD), ("learned", q.QYM_GUESS_MLP))
-    for name, guess in arms[:2 if args.train else 1]:
+    # the headline (solver, guess) first, then the other solvers and guesses
+    # for comparison, each timed the same way
+    solvers = {"newton": q.QYM_SOLVER_NEWTON, "newton32": q.QYM_SOLVER_NEWTON32,
+               "laguerre": q.QYM_SOLVER_LAGUERRE}
+    guesses = (("standard", q.QYM_GUESS_STANDARD), ("learned", q.QYM_GUESS_MLP))
+    arms = [(args.solver, args.guess)]
+    if args.compare:
+        arms += [(sn, gn) for sn in ("newton32", "newton", "laguerre") for gn, _ in guesses
+                 if (sn, gn) != arms[0] and (args.train or gn == "standard")]
+    for sname, name in arms:
+        guess = dict(guesses)[name]
+        slv = solvers[sname]
         it = torch.empty(n, dtype=torch.int32, device="cuda")
         st = torch.zeros(1, dtype=torch.int32, device="cuda")
-        drift(guess, it=it, st=st)
+        drift(guess, it=it, st=st, slv=slv)
         for _ in range(args.warmup):
-            drift(guess)
+            drift(guess, slv=slv)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
         with ClockSampler(dev) as clk:
@@ -808,7 +827,7 @@ def run_kepler(args):
             for a, b in ev:
                 flush.fill_(1)          # L2 flushed between timed drifts (outside the events)
                 a.record(stream)
-                drift(guess)
+                drift(guess, slv=slv)
                 b.record(stream)
             barrier()
         ms = sum(a.elapsed_time(b) for a, b in ev)
@@ -818,10 +837,12 @@ def run_kepler(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
         itn = it.cpu().numpy()
-        res[name] = {"value": n * args.steps * ws / (ms / 1e3), "ms_per_step": ms / args.steps,
-                     "iterations_mean": float(itn.mean()), "iterations_max": int(itn.max()),
-                     "status": int(st.item()), "clocks": clk.summary()}
-    head = res[args.guess]
+        res[f"{sname}/{name}"] = {"value": n * args.steps * ws / (ms / 1e3),
+                                  "ms_per_step": ms / args.steps,
+                                  "iterations_mean": float(itn.mean()),
+                                  "iterations_max": int(itn.max()),
+                                  "status": int(st.item()), "clocks": clk.summary()}
+    head = res[f"{args.solver}/{args.guess}"]
     # end to end through the C ABI with host buffers: the state goes host ->
     # device, one drift, device -> host
     hq = torch.from_numpy(np.ascontiguousarray(qq.T)).pin_memory()
@@ -843,14 +864,30 @@ def run_kepler(args):
     e2e = {"value": n * e2e_steps * ws / e2e_s, "unit": METRIC, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
            "what": "pinned H2D of (q, v) + qym_kepler_drift_dev + D2H of (q1, v1) per step"}
-    # roofline of k_kepler: 96 algorithmic bytes per particle (read q0, v0,
-    # write q1, v1, float64 x 3 each)
-    peak, which = hbm_peak_gbs()
-    achieved = 96.0 * n / (head["ms_per_step"] / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_kepler<%s>" % ("true" if args.guess == "learned" else "false"),
-            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_source": which,
-            "bytes_per_particle": 96}
+    # roofline of k_kepler: bound by FP64 issue, not by its 96 bytes per
+    # particle (read q0, v0, write q1, v1, float64 x 3 each). Achieved = the
+    # FP64-pipe instructions ncu counted for one launch of this source (x 32
+    # lanes: issue slots, divergent lanes included) over the live launch
+    # time; peak = the DFMA instruction rate measured by qym_probe_fma.
+    peak_gbs, which = hbm_peak_gbs()
+    hbm = 96.0 * n / (head["ms_per_step"] / 1e3) / 1e9
+    kdig = source_digest("kepler.cu", "mlp.cuh")
+    fp64_inst = KEPLER_FP64_WARP_INST.get((args.solver, args.guess, kdig))
+    pk = probe_peaks(q, dev)
+    dfma_rate = pk["dfma"] / 2.0 * 1e3          # 1e9 FP64 thread-instructions/s
+    achieved = fp64_inst * 32 / (head["ms_per_step"] / 1e3) / 1e9 if fp64_inst else None
+    roof = {"bound": "alu", "kernel": "k_kepler<%s>" % ("true" if args.guess == "learned" else "false"),
+            "achieved": achieved, "peak": dfma_rate, "unit": "G FP64 instr/s",
+            "frac": achieved / dfma_rate if achieved else None,
+            "peak_source": "measured (qym_probe_fma DFMA: %.3f TFLOP/s)" % pk["dfma"],
+            "fp64_warp_instructions_per_launch": fp64_inst, "kepler_source_digest": kdig,
+            "convention": ("FP64-pipe warp instructions of one launch (ncu "
+                           "sm__inst_executed_pipe_fp64.sum, this source) x 32 over the live launch "
+                           "time, against the measured DFMA thread-instruction rate; null when the "
+                           "source has changed since the count was taken"),
+            "traffic": None,
+            "hbm": {"achieved": hbm, "peak": peak_gbs, "unit": "GB/s", "frac": hbm / peak_gbs,
+                    "peak_source": which, "bytes_per_particle": 96}}
     if rank != 0:
         return 0
     cb = None
@@ -859,7 +896,7 @@ def run_kepler(args):
         O.build()
         m = 20000
         t0 = time.perf_counter()
-        O.kepler_drift(qq[:m], vv[:m], 1.0, dt, solver=1 if args.solver == "newton" else 0)
+        O.kepler_drift(qq[:m], vv[:m], 1.0, dt, solver=0 if args.solver == "laguerre" else 1)
         cdt = time.perf_counter() - t0
         cb = {"value": m / cdt, "unit": METRIC, "cores": 1, "kind": "oracle",
               "sample": f"first {m} particles, one drift, standard guess (plain FP64 oracle, single thread)"}
@@ -867,7 +904,7 @@ def run_kepler(args):
         O.set_threads(cores)
         m2 = 200000
         t0 = time.perf_counter()
-        O.kepler_drift(qq[:m2], vv[:m2], 1.0, dt, solver=1 if args.solver == "newton" else 0)
+        O.kepler_drift(qq[:m2], vv[:m2], 1.0, dt, solver=0 if args.solver == "laguerre" else 1)
         cdt = time.perf_counter() - t0
         O.set_threads(1)
         cb["all_cores"] = {"value": m2 / cdt, "unit": METRIC, "cores": cores, "kind": "oracle",
@@ -899,10 +936,12 @@ def main():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default="disk_16384",
                     choices=sorted(WORKLOADS) + sorted(KEPLER_WORKLOADS))
-    ap.add_argument("--guess", default="learned", choices=["standard", "learned"],
+    ap.add_argument("--guess", default="standard", choices=["standard", "learned"],
                     help="kepler_1m: the starting guess of the headline number")
-    ap.add_argument("--solver", default="newton", choices=["newton", "laguerre"],
-                    help="kepler_1m: Kepler solver")
+    ap.add_argument("--compare", type=int, default=1,
+                    help="kepler_1m: also time the other solvers and guesses")
+    ap.add_argument("--solver", default="newton32", choices=["newton", "newton32", "laguerre"],
+                    help="kepler_1m: Kepler solver (newton32: FP32 Newton steps, then FP64 Laguerre)")
     ap.add_argument("--merge-kicks", type=int, default=0,
                     help="1: one kick of tau between steps (exact rewrite of the paper's two)")
     ap.add_argument("--merged-too", type=int, default=1,

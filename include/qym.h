@@ -71,6 +71,10 @@ typedef enum qym_status {
 /* Kepler solver and starting guess (Appendix). */
 #define QYM_SOLVER_LAGUERRE 0   /* Laguerre, n = 5 */
 #define QYM_SOLVER_NEWTON   1
+#define QYM_SOLVER_NEWTON32 2   /* Newton steps in FP32 from the starting guess until a step
+                                   falls below 1e-5 |x|, then Laguerre in FP64 under the same
+                                   residual test and bracket: the same root, fewer FP64
+                                   evaluations; the iteration count adds both kinds */
 #define QYM_GUESS_STANDARD  0   /* x0 = sqrt(mu) dt / r0 */
 #define QYM_GUESS_R0        1   /* x0 = r0, as the Appendix does */
 #define QYM_GUESS_MLP       2   /* learned guess (qym_set_mlp); falls back to

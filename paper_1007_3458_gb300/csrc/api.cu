@@ -127,7 +127,8 @@ static bool valid_params(const qym_params *p, std::string &why) {
     if (!(p->eps_H >= 0.0)) { why = "eps_H must be >= 0"; return false; }
     if (!(p->eta > 0.0) || !(p->eta_s > 0.0)) { why = "eta, eta_s must be > 0"; return false; }
     if (p->kick_prec != QYM_KICK_FP64 && p->kick_prec != QYM_KICK_MIXED) { why = "kick_prec"; return false; }
-    if (p->solver != QYM_SOLVER_LAGUERRE && p->solver != QYM_SOLVER_NEWTON) { why = "solver"; return false; }
+    if (p->solver != QYM_SOLVER_LAGUERRE && p->solver != QYM_SOLVER_NEWTON &&
+        p->solver != QYM_SOLVER_NEWTON32) { why = "solver"; return false; }
     if (p->guess < 0 || p->guess > 2) { why = "guess"; return false; }
     if (p->max_kepler_iter < 1) { why = "max_kepler_iter must be >= 1"; return false; }
     if (p->max_hermite_steps < 1) { why = "max_hermite_steps must be >= 1"; return false; }
@@ -1282,7 +1283,7 @@ extern "C" qym_status qym_kepler_drift_dev(int64_t n, const double *q0, const do
                                            float *log_rows, int32_t *status, void *stream) {
     if (n < 0 || !(mu > 0.0) || max_iter < 1 || !std::isfinite(dt))
         FAIL(nullptr, QYM_EINVAL, "qym_kepler_drift_dev: bad n, mu, dt or max_iter");
-    if (solver != QYM_SOLVER_LAGUERRE && solver != QYM_SOLVER_NEWTON)
+    if (solver != QYM_SOLVER_LAGUERRE && solver != QYM_SOLVER_NEWTON && solver != QYM_SOLVER_NEWTON32)
         FAIL(nullptr, QYM_EINVAL, "qym_kepler_drift_dev: solver");
     if (guess < QYM_GUESS_STANDARD || guess > QYM_GUESS_MLP)
         FAIL(nullptr, QYM_EINVAL, "qym_kepler_drift_dev: guess");

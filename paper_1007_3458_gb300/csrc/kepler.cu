@@ -16,29 +16,40 @@
 
 namespace qym {
 
-// Stumpff functions (Appendix, Eqs. 2.40). Near y = 0 the alternating series
-// C = sum_k (-y)^k / (2k+2)!, S = sum_k (-y)^k / (2k+3)! in Horner form to
-// the y^8 term; elsewhere the closed forms, C through 2 sin^2(s/2) / y to
-// avoid the cancellation of 1 - cos s.
+// Stumpff functions C = c2(y), S = c3(y) (Appendix, Eqs. 2.40) by quartering
+// the argument: y is scaled by 4^-k into |y| < 1 (exactly, a power of two),
+// where the series C = sum_n (-y)^n / (2n+2)!, S = sum_n (-y)^n / (2n+3)! to
+// the y^8 term is exact to rounding (the first omitted term is below 1e-18),
+// and k doublings of s = sqrt(y) then follow from the double-angle formulas
+// of sin and cos:  c2(4y) = c1(y)^2 / 2,  c3(4y) = (c3(y) + c1(y) c2(y)) / 4,
+// with c1(y) = 1 - y c3(y) = sin(s) / s formed afresh at each level. Only
+// multiply-adds, no division, square root or transcendental call, and the
+// same instructions for bound and unbound orbits. Past 4^64 (s > 2^64) C and
+// S are NaN, which the iteration treats as a point beyond the root.
 __device__ __forceinline__ void stumpff(double y, double &C, double &S) {
-    if (fabs(y) < 0.1) {
-        // 1/(2k+2)! and 1/(2k+3)! for k = 0..8, alternating signs
-        C = 1.0 / 2.0 + y * (-1.0 / 24.0 + y * (1.0 / 720.0 + y * (-1.0 / 40320.0 +
-            y * (1.0 / 3628800.0 + y * (-1.0 / 479001600.0 + y * (1.0 / 87178291200.0 +
-            y * (-1.0 / 20922789888000.0 + y * (1.0 / 6402373705728000.0))))))));
-        S = 1.0 / 6.0 + y * (-1.0 / 120.0 + y * (1.0 / 5040.0 + y * (-1.0 / 362880.0 +
-            y * (1.0 / 39916800.0 + y * (-1.0 / 6227020800.0 + y * (1.0 / 1307674368000.0 +
-            y * (-1.0 / 355687428096000.0 + y * (1.0 / 121645100408832000.0))))))));
-    } else if (y > 0.0) {
-        double s = sqrt(y);
-        double sh, ch;
-        sincos(0.5 * s, &sh, &ch);
-        C = 2.0 * sh * sh / y;
-        S = (s - 2.0 * sh * ch) / (y * s);
-    } else {
-        double s = sqrt(-y);
-        C = (cosh(s) - 1.0) / (-y);
-        S = (sinh(s) - s) / ((-y) * s);
+    int k = 0;
+    if (!(fabs(y) < 1.0)) {
+        // |y| in [2^e, 2^(e+1)): k = floor(e/2) + 1 puts y / 4^k in [1/4, 1)
+        const int e = ((__double2hiint(y) >> 20) & 0x7ff) - 1023;
+        k = e / 2 + 1;
+        if (k > 64) {
+            C = S = __longlong_as_double(0x7ff8000000000000ll);
+            return;
+        }
+        y *= __hiloint2double((1023 - 2 * k) << 20, 0);
+    }
+    // 1/(2n+2)! and 1/(2n+3)! for n = 0..8, alternating signs
+    C = 1.0 / 2.0 + y * (-1.0 / 24.0 + y * (1.0 / 720.0 + y * (-1.0 / 40320.0 +
+        y * (1.0 / 3628800.0 + y * (-1.0 / 479001600.0 + y * (1.0 / 87178291200.0 +
+        y * (-1.0 / 20922789888000.0 + y * (1.0 / 6402373705728000.0))))))));
+    S = 1.0 / 6.0 + y * (-1.0 / 120.0 + y * (1.0 / 5040.0 + y * (-1.0 / 362880.0 +
+        y * (1.0 / 39916800.0 + y * (-1.0 / 6227020800.0 + y * (1.0 / 1307674368000.0 +
+        y * (-1.0 / 355687428096000.0 + y * (1.0 / 121645100408832000.0))))))));
+    for (int i = 0; i < k; ++i) {
+        const double c1 = fma(-y, S, 1.0);
+        S = 0.25 * fma(c1, C, S);
+        C = 0.5 * c1 * c1;
+        y *= 4.0;
     }
 }
 
@@ -56,6 +67,60 @@ struct KepEq {
         Fpp = sig * (1.0 - y * C) + b * x * oyS;
     }
 };
+
+// Stumpff functions in FP32 for the first iterations of QYM_SOLVER_NEWTON32:
+// the series to the y^6 term for |y| < 1 (its truncation below 1e-11, so
+// only FP32 rounding remains), the closed forms beyond (s - sin s and
+// sinh s - s lose at most about three bits there)
+__device__ __forceinline__ void stumpff_f32(float y, float &C, float &S) {
+    if (fabsf(y) < 1.0f) {
+        C = 0.5f + y * (-1.0f / 24.0f + y * (1.0f / 720.0f + y * (-1.0f / 40320.0f +
+            y * (1.0f / 3628800.0f + y * (-1.0f / 479001600.0f + y * (1.0f / 87178291200.0f))))));
+        S = 1.0f / 6.0f + y * (-1.0f / 120.0f + y * (1.0f / 5040.0f + y * (-1.0f / 362880.0f +
+            y * (1.0f / 39916800.0f + y * (-1.0f / 6227020800.0f + y * (1.0f / 1307674368000.0f))))));
+    } else if (y > 0.0f) {
+        const float s = sqrtf(y);
+        float sh, ch;
+        sincosf(0.5f * s, &sh, &ch);
+        C = 2.0f * sh * sh / y;
+        S = (s - 2.0f * sh * ch) / (y * s);
+    } else {
+        const float s = sqrtf(-y);
+        C = (coshf(s) - 1.0f) / (-y);
+        S = (sinhf(s) - s) / ((-y) * s);
+    }
+}
+
+// QYM_SOLVER_NEWTON32: Newton's method on F in FP32 from x while it stays in
+// the bracket [lo, hi] (at most 12 steps), until a step falls below 1e-5 |x|;
+// x then holds the FP32 root (relative error about 1e-7, more where F's terms
+// cancel) and the FP64 iteration finishes from there under the unchanged
+// residual test. Returns
+// the FP32 steps taken, and leaves x unchanged (0 steps counted) when the FP32
+// form fails (a step leaves the bracket, F or F' is not finite).
+__device__ __forceinline__ int newton_f32(const KepEq &eq, double lo, double hi, double &x) {
+    const float sq = (float)eq.sqmu_dt, r0 = (float)eq.r0, sig = (float)eq.sig;
+    const float al = (float)eq.alpha, b = (float)eq.b;
+    const float lof = (float)lo, hif = (float)hi;
+    float xf = (float)x;
+    for (int it = 0; it < 12; ++it) {
+        const float x2 = xf * xf, y = al * x2;
+        float C, S;
+        stumpff_f32(y, C, S);
+        const float F = sig * x2 * C + b * x2 * xf * S + r0 * xf - sq;
+        const float Fp = sig * xf * (1.0f - y * S) + b * x2 * C + r0;
+        if (!isfinite(F) || !(Fp > 0.0f) || !isfinite(Fp)) return 0;
+        const float dx = F / Fp;
+        const float xn = xf - dx;
+        if (!(xn >= lof && xn <= hif)) return 0;
+        xf = xn;
+        if (fabsf(dx) <= 1e-5f * fabsf(xf)) {
+            x = (double)xf;
+            return it + 1;
+        }
+    }
+    return 0;
+}
 
 template <bool MLP>
 __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
@@ -101,11 +166,15 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
         }
         {
         double vv = vx * vx + vy * vy + vz * vz;
+        // the FP64 pipe bounds this kernel: divisions by mu, sqrt(mu) and r0
+        // become products with reciprocals formed once (within an ulp of the
+        // quotients)
+        const double imu = 1.0 / mu, ir0 = 1.0 / r0, isqmu = sqmu * imu;
         KepEq eq;
         eq.sqmu_dt = sqmu * dt;
         eq.r0 = r0;
-        eq.alpha = 2.0 / r0 - vv / mu;
-        eq.sig = (qx * vx + qy * vy + qz * vz) / sqmu;
+        eq.alpha = 2.0 * ir0 - vv * imu;
+        eq.sig = (qx * vx + qy * vy + qz * vz) * isqmu;
         eq.b = 1.0 - r0 * eq.alpha;
         double x;
         if (a.guess == QYM_GUESS_R0)
@@ -113,7 +182,7 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
         else if (MLP && have_mlp)
             x = x_mlp;
         else
-            x = eq.sqmu_dt / r0;
+            x = eq.sqmu_dt * ir0;
         if (a.x0_out) a.x0_out[k] = x;
         int solver = a.solver;
         bool conv = false;
@@ -122,30 +191,38 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
         // Root bracket: F(0) = -sqrt(mu) dt and F' = r >= r_p (periapsis
         // distance), so the root lies between 0 and sqrt(mu) dt / r_p; for an
         // unbound orbit also |x| <= 700 / sqrt(-alpha), past which C and S
-        // overflow. Widened by 1e-12 for the rounding of r_p.
+        // overflow. Widened by 1e-12 for the rounding of r_p = p / (1 + e).
         double lo = -INFINITY, hi = INFINITY;
         {
             double hx = qy * vz - qz * vy, hy = qz * vx - qx * vz, hz = qx * vy - qy * vx;
-            double p = (hx * hx + hy * hy + hz * hz) / mu;
+            double p = (hx * hx + hy * hy + hz * hz) * imu;
             double ecc = sqrt(fmax(0.0, 1.0 - p * eq.alpha));
-            double rp = p / (1.0 + ecc);
-            if (rp > 0.0) {
-                double xb = eq.sqmu_dt / rp * (1.0 + 1e-12);
+            if (p > 0.0) {
+                double xb = eq.sqmu_dt * (1.0 + ecc) / p * (1.0 + 1e-12);
                 if (dt >= 0.0) { lo = 0.0; hi = xb; } else { lo = xb; hi = 0.0; }
             }
             if (eq.alpha < 0.0) {
-                double xm = 700.0 / sqrt(-eq.alpha);
+                // rsqrt within 2 ulp: the bound is widened by 1e-12
+                double xm = 700.0 * (1.0 + 1e-12) * rsqrt(-eq.alpha);
                 if (dt >= 0.0) { lo = fmax(lo, 0.0); hi = fmin(hi, xm); }
                 else { lo = fmax(lo, -xm); hi = fmin(hi, 0.0); }
             }
         }
         const double lo0 = lo, hi0 = hi;
+        if (solver == QYM_SOLVER_NEWTON32) {
+            // FP32 Newton steps first, then the FP64 iteration in Laguerre's
+            // form: from the FP32 root (about 1e-7) one cubic step reaches
+            // the rounding level, so the evaluation after it meets the
+            // residual test
+            iters += newton_f32(eq, lo, hi, x);
+            solver = QYM_SOLVER_LAGUERRE;
+        }
         // two passes at most: the requested start, then (learned guess only)
         // Laguerre from the standard guess if the first did not converge
         for (int pass = 0; pass < 2 && !conv; ++pass) {
             if (pass == 1) {
                 if (!MLP) break;
-                x = eq.sqmu_dt / r0;
+                x = eq.sqmu_dt * ir0;
                 solver = QYM_SOLVER_LAGUERRE;
                 lo = lo0;
                 hi = hi0;
@@ -184,7 +261,7 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
                 if (solver == QYM_SOLVER_LAGUERRE) {
                     // Laguerre, n = 5: dx = n F / (F' + sgn(F') sqrt|(n-1)^2 F'^2 - n(n-1) F F''|),
                     // with F' taken out of the root so that F'^2 never overflows
-                    const double rf = F / Fp, rpp = Fpp / Fp;
+                    const double iFp = 1.0 / Fp, rf = F * iFp, rpp = Fpp * iFp;
                     dx = 5.0 * rf / (1.0 + sqrt(fabs(16.0 - 20.0 * rf * rpp)));
                 } else {
                     dx = F / Fp;
@@ -213,12 +290,12 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
         double x2 = x * x;
         double y = eq.alpha * x2;
         if (!cs_at_x) stumpff(y, C, S);
-        double f = 1.0 - x2 / r0 * C;
-        double g = dt - x2 * x / sqmu * S;
+        double f = 1.0 - x2 * C * ir0;
+        double g = dt - x2 * x * S * isqmu;
         double nx = f * qx + g * vx, ny = f * qy + g * vy, nz = f * qz + g * vz;
-        double rr = sqrt(nx * nx + ny * ny + nz * nz);
-        double fd = sqmu * x * (y * S - 1.0) / (rr * r0);
-        double gd = 1.0 - x2 / rr * C;
+        double irr = 1.0 / sqrt(nx * nx + ny * ny + nz * nz);
+        double fd = sqmu * x * (y * S - 1.0) * irr * ir0;
+        double gd = 1.0 - x2 * C * irr;
         double ux = fd * qx + gd * vx, uy = fd * qy + gd * vy, uz = fd * qz + gd * vz;
         a.q1[r] = nx; a.q1[ld + r] = ny; a.q1[2 * ld + r] = nz;
         a.v1[r] = ux; a.v1[ld + r] = uy; a.v1[2 * ld + r] = uz;

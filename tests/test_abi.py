@@ -75,6 +75,8 @@ def test_argument_checks_without_gpu(lib):
                                     50, None, None, None, None, None, None) == q.QYM_EINVAL
     assert lib.qym_kepler_drift_dev(4, None, None, None, None, 1.0, 1.0, 0, 7, None, 50, None,
                                     None, None, None, None, None) == q.QYM_EINVAL
+    assert lib.qym_kepler_drift_dev(4, None, None, None, None, 1.0, 1.0, 3, 0, None, 50, None,
+                                    None, None, None, None, None) == q.QYM_EINVAL
     assert lib.qym_mlp_workspace_bytes() >= 256 * q.QYM_MLP_NW * 4
     assert lib.qym_mlp_forward_dev(-1, None, None, None, None) == q.QYM_EINVAL
     assert lib.qym_mlp_grad_dev(0, None, None, None, None, None, 0, None) == q.QYM_EINVAL

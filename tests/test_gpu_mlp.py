@@ -270,12 +270,17 @@ def test_learned_guess_gain_on_test_particles(torch, oracle):
     q0, v0 = _soa(torch, qq), _soa(torch, vv)
     wd = torch.from_numpy(wts).cuda()
     res = {}
-    for name, guess in (("standard", q.QYM_GUESS_STANDARD), ("mlp", q.QYM_GUESS_MLP)):
+    # the last two arms take FP32 Newton steps before the FP64 ones
+    arms = (("standard", q.QYM_GUESS_STANDARD, q.QYM_SOLVER_NEWTON),
+            ("mlp", q.QYM_GUESS_MLP, q.QYM_SOLVER_NEWTON),
+            ("standard32", q.QYM_GUESS_STANDARD, q.QYM_SOLVER_NEWTON32),
+            ("mlp32", q.QYM_GUESS_MLP, q.QYM_SOLVER_NEWTON32))
+    for name, guess, solver in arms:
         q1, v1 = torch.empty_like(q0), torch.empty_like(v0)
         x = torch.empty(n, dtype=torch.float64, device="cuda")
         it = torch.empty(n, dtype=torch.int32, device="cuda")
         st = torch.zeros(1, dtype=torch.int32, device="cuda")
-        q.qym_kepler_drift_dev(n, q0, v0, q1, v1, 1.0, dt, q.QYM_SOLVER_NEWTON, guess,
+        q.qym_kepler_drift_dev(n, q0, v0, q1, v1, 1.0, dt, solver, guess,
                                wd if guess == q.QYM_GUESS_MLP else None, 50, x_out=x, iters=it,
                                status=st)
         torch.cuda.synchronize()
@@ -285,27 +290,27 @@ def test_learned_guess_gain_on_test_particles(torch, oracle):
     print(f"\nrows {nrows}, loss first {losses[:10].mean():.4g} last {losses[-100:].mean():.4g}; "
           f"Newton iterations: standard {it_s:.3f} (max {res['standard'][2].max()}), "
           f"learned {it_m:.3f} (max {res['mlp'][2].max()})")
-    print("  histogram standard", np.bincount(res["standard"][2])[:12])
-    print("  histogram learned ", np.bincount(res["mlp"][2])[:12])
+    for name in res:
+        print(f"  histogram {name:10s}", np.bincount(res[name][2])[:14])
     assert it_m < 0.85 * it_s
-    # the solver stops at |F| <= 1e-14 (sum of |terms|) in its own rounding;
-    # after a step at the rounding level it takes one more evaluation and
-    # stops there even above 1e-14 (where r1 >> r0 a step of one ulp in x
-    # moves F by more than that): such a root must have no neighbouring
-    # double that meets 1e-14. Re-evaluated by the oracle, F also carries a
-    # few more ulp of the sum of |terms|.
+    # every root meets |F| <= 1e-14 (sum of |terms|), re-evaluated by the
+    # oracle (whose F carries a few more ulp of that sum: eps), unless no
+    # double next to it meets 1e-14 either: after a step at the rounding
+    # level the solver evaluates once more and keeps the better of the two
+    # points, which can sit above 1e-14 only where a step of one ulp in x
+    # moves F by more than that (r1 >> r0)
     eps = 8 * 2.0 ** -53
     for name in res:
         x = res[name][1]
         r = oracle.kepler_residuals(qq, vv, 1.0, dt, x)
         over = np.nonzero(r > 1e-14 + eps)[0]
         print(f"  {name}: max residual {r.max():.3g}, {len(over)} roots above 1e-14")
-        assert r.max() <= 2e-14 and len(over) <= 16, (name, float(r.max()), len(over))
         for d in (np.inf, -np.inf):
             rn = oracle.kepler_residuals(qq[over], vv[over], 1.0, dt, np.nextafter(x[over], d))
             assert np.all(rn > 1e-14 - eps), (name, over[rn <= 1e-14 - eps], rn[rn <= 1e-14 - eps])
-    # both roots meet the residual: the states agree within its conditioning
-    qs, qm = res["standard"][0], res["mlp"][0]
+    # every root meets the residual: the states agree within its conditioning
+    qs = res["standard"][0]
     _, dqt = _root_tolerance(qq, vv, dt, res["standard"][1], qs)
     floor = 2e-15 * (np.linalg.norm(qs, axis=1) + np.linalg.norm(qq, axis=1))
-    assert np.all(np.linalg.norm(qs - qm, axis=1) <= dqt + floor)
+    for name in ("mlp", "standard32", "mlp32"):
+        assert np.all(np.linalg.norm(qs - res[name][0], axis=1) <= dqt + floor), name

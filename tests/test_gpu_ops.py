@@ -83,6 +83,33 @@ def test_kepler_matches_oracle(torch, oracle, solver, guess, dt):
     assert np.mean(it[ok] == itr[ok]) > (0.99 if solver == 0 else 0.95)
 
 
+@pytest.mark.parametrize("dt", [0.01, 1.756203, -0.7, 25.0])
+def test_kepler_newton32_matches_oracle(torch, oracle, dt):
+    """QYM_SOLVER_NEWTON32 (FP32 Newton steps, then FP64 Laguerre under the same
+    residual test and bracket) reaches the oracle's root: the states agree
+    wherever both converged, within the tolerance of the FP64 solvers; 40
+    hyperbolic rows among them."""
+    qq, vv, a, e = _orbits(3000 + 37, seed=int(abs(dt) * 100) + 7)
+    r = np.linalg.norm(qq[:40], axis=1)
+    vv = vv.copy()
+    vv[:40] *= (1.5 * np.sqrt(2.0 / r) / np.linalg.norm(vv[:40], axis=1))[:, None]
+    q1, v1, x, it, st = _kepler_gpu(torch, qq, vv, 1.0, dt, q.QYM_SOLVER_NEWTON32, 0)
+    r1, u1, xr, itr, bad = oracle.kepler_drift(qq, vv, 1.0, dt, 0, 0)
+    assert bad == 0
+    ok = it < 50
+    assert ok.mean() > 0.5 and ok[:40].all()
+    if abs(dt) < 2.0:
+        assert ok.all() and st == 0
+    # the bound rows as in the FP64 solvers' test; the hyperbolic rows by the
+    # relative state error
+    scale = (1.0 + abs(dt) / (2 * math.pi * a ** 1.5)) / (1.0 - e)
+    scale[:40] = 1.0
+    dq = np.linalg.norm(q1 - r1, axis=1) / np.linalg.norm(r1, axis=1)
+    dv = np.linalg.norm(v1 - u1, axis=1) / np.linalg.norm(u1, axis=1)
+    assert np.all(dq[ok] <= 1e-12 * scale[ok]), dq[ok].max()
+    assert np.all(dv[ok] <= 1e-12 * scale[ok]), dv[ok].max()
+
+
 def test_kepler_unbound_and_star_rows(torch, oracle):
     """Hyperbolic and near-parabolic orbits stay finite (Appendix: universal
     variables); a row at the origin (a star row) is left at zero."""

@@ -185,8 +185,8 @@ MUTANTS = [
      'if (u[k] > 0.0 && u[k] < 1.0) {',
      'if (u[k] > 0.0 && u[k] < 0.5) {'),
     ('encounters_strict_upper_only_ij', 'step',
-     'for (int64_t j = i + 1; j < rows; ++j) {\n            double dq0[3], dv0[3], dq1[3], dv1[3];\n            pair_diffs(q0, v0, q1, v1, i, j, dq0, dv0, dq1, dv1);\n            double R = a_E * (rH[i] + rH[j]);',
-     'for (int64_t j = i + 2; j < rows; ++j) {\n            double dq0[3], dv0[3], dq1[3], dv1[3];\n            pair_diffs(q0, v0, q1, v1, i, j, dq0, dv0, dq1, dv1);\n            double R = a_E * (rH[i] + rH[j]);'),
+     'for (int64_t j = i + 1; j < rows; ++j) {\n        double dq0[3], dv0[3], dq1[3], dv1[3];\n        pair_diffs(q0, v0, q1, v1, i, j, dq0, dv0, dq1, dv1);\n        double R = a_E * (rH[i] + rH[j]);',
+     'for (int64_t j = i + 2; j < rows; ++j) {\n        double dq0[3], dv0[3], dq1[3], dv1[3];\n        pair_diffs(q0, v0, q1, v1, i, j, dq0, dv0, dq1, dv1);\n        double R = a_E * (rH[i] + rH[j]);'),
     ('residual_scale_inflated', 'kepler',
      'res[i] = fabs(F) / scale;',
      'res[i] = fabs(F) / (1e6 * scale);'),
