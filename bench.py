@@ -146,13 +146,6 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-# DRAM bytes (read + written) per launch of the mixed kick, from one ncu
-# capture of each workload's kick after autotuning (dram__bytes_read.sum +
-# dram__bytes_write.sum, the mean of the searching and the plain kick, three
-# launches each); keyed by (workload, rows per CTA, j-splits, digest of the
-# kick's source at the capture), since the partial-sum slots written grow
-# with the splits. A shape or a kick source not captured reports null (the
-# capture commands sit with the ncu summaries under profiles/).
 # FP64-pipe warp instructions of one k_kepler launch on the 1,048,576 test
 # particles (ncu sm__inst_executed_pipe_fp64.sum), per (solver, guess, source
 # digest of kepler.cu + mlp.cuh)
@@ -161,10 +154,17 @@ KEPLER_FP64_WARP_INST = {
     ("newton", "standard", "0b39927b0f9b323f"): 23561161,
 }
 
+# DRAM bytes (read + written) per launch of the mixed kick, from one ncu
+# capture of each workload's kick after autotuning (dram__bytes_read.sum +
+# dram__bytes_write.sum, the mean over the launches of the first steps, both
+# kinds of kick where the step has both); keyed by (workload, rows per CTA, j-splits, digest of the
+# kick's source at the capture), since the partial-sum slots written grow
+# with the splits. A shape or a kick source not captured reports null (the
+# capture commands sit with the ncu summaries under profiles/).
 KICK_DRAM_BYTES = {
     # shape 128 threads x 2 rows x 64 splits (256 rows per CTA)
-    ("disk_16384", 256, 64, "05e8966306e64e5a"): 8.94e5,
-    ("disk_262144", 256, 64, "05e8966306e64e5a"): 3.64e8,
+    ("disk_16384", 256, 64, "3e97bc3c36908ece"): 9.25e5,
+    ("disk_262144", 256, 64, "3e97bc3c36908ece"): 2.30e7,
 }
 
 
@@ -601,7 +601,8 @@ def run_ours(args):
             "kick_ms_with_search": k1_ms, "kick_ms_plain": k2_ms,
             "frac_with_search": 20.0 * pairs / (k1_ms / 1e3) / 1e12 / peak,
             "frac_plain": 20.0 * pairs / (k2_ms / 1e3) / 1e12 / peak,
-            "gpair_per_s_kernel": pairs / (kick_ms / 1e3) / 1e9}
+            "gpair_per_s_kernel": pairs / (kick_ms / 1e3) / 1e9,
+            "kick_shape": {"rows_per_cta": st["kick_tile_i"], "splits": st["kick_tile_splits"]}}
 
     # end to end through the C ABI with host buffers: per step, the state goes
     # host -> device (qym_set_state), one step, device -> host (qym_get_state),

@@ -50,6 +50,7 @@ struct qym_ctx {
     std::string err;
     int32_t status_bits = 0;
     int32_t items_cap = 0, splits_cap = 0;  // sizes of the item and partial buffers
+    int32_t *kick_cnt = nullptr;            // per i-block arrival counters of the kick
     int64_t n_heavy = 0;    // heavy bodies over all systems
     int64_t launches = 0;   // kernels enqueued by the current qym_step call
     int64_t graph_launches = 0;  // kernels in one replay of the step graph
@@ -171,6 +172,8 @@ struct Carver {
     }
 };
 
+static void choose_slot_sums(qym_ctx *c);
+
 static void carve_all(qym_ctx *c, Carver &k) {
     Dev &d = c->d;
     const int64_t R = d.rows;
@@ -190,6 +193,7 @@ static void carve_all(qym_ctx *c, Carver &k) {
     d.apart = k.take<double>((size_t)3 * R * c->splits_cap);
     d.items = k.take<int4>(c->items_cap);
     d.item_slot = k.take<int32_t>(c->items_cap);
+    c->kick_cnt = k.take<int32_t>(c->items_cap);  // zero with the arena
     d.mchunks = k.take<int4>(d.nmchunks);
     d.mpart = k.take<double>(3 * (size_t)d.nmchunks);
     d.sys_chunk0 = k.take<int32_t>(d.nsys + 1);
@@ -453,6 +457,7 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     }
     Carver real{(char *)c->arena, 0, false};
     carve_all(c, real);
+    choose_slot_sums(c);
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaFree(c->arena);
         delete c;
@@ -1490,6 +1495,19 @@ extern "C" qym_status qym_time_kick(qym_ctx *c, int32_t with_search, int32_t rep
     return QYM_OK;
 }
 
+// Where the kick's partial slots are added: by the finisher (k_finish), or,
+// once the slots outgrow half of the 129 MB L2, by each i-block's last CTA
+// inside the kick, which discards the dead slots from L2 so that they never
+// reach HBM (kick.cu). With the slots in L2 the finisher's sum spreads over
+// every SM and costs nothing in HBM; the in-kick sum puts an i-block's FP64
+// adds on one SM (14 us for 64 slots of 256 rows), which a short kick (the
+// 16384-body disk: 0.14 ms) would feel.
+constexpr int64_t kSlotSumInKickBytes = 64ll << 20;
+static void choose_slot_sums(qym_ctx *c) {
+    Dev &d = c->d;
+    d.kick_cnt = 24 * d.rows * (int64_t)d.splits > kSlotSumInKickBytes ? c->kick_cnt : nullptr;
+}
+
 // rebuild the work items for a launch shape (device buffers sized for the
 // largest item count and split count seen so far are reused when they fit)
 static qym_status apply_tune(qym_ctx *c, const KickTune &t) {
@@ -1509,6 +1527,7 @@ static qym_status apply_tune(qym_ctx *c, const KickTune &t) {
     CK(c, cudaStreamSynchronize(c->stream));
     d.nitems = n;
     d.splits = t.splits;
+    choose_slot_sums(c);
     c->tune = t;
     if (c->gexec) {  // the captured step holds the old shape
         cudaGraphExecDestroy(c->gexec);

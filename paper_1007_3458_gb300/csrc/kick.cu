@@ -48,7 +48,78 @@ struct KickArgs {
     const int32_t *perm;    // row of each position of the packs (NULL: row order)
     const float4 *far;      // (o_x, o_y, o_z, G m): offset from the tile's reference point
     const float4 *tile;     // per tile: (c_x, c_y, c_z, R), box min (x, y, z, -), box max
+    int32_t *blk_cnt = nullptr;  // arrivals per i-block (NULL: each slot stays for the finisher)
+    int32_t splits = 1;          // items (slots) per i-block
 };
+
+// The last CTA of an i-block to finish (arrivals counted per i-block, the
+// counter reset by that CTA for the next launch) adds the block's `splits`
+// slots into slot 0, in the order a reader of the slots used (lane q of
+// four summing slots q, q + 4, ..., the four parts added as (0 + 1) + (2 + 3)),
+// and discards the other slots' lines from L2 (PTX discard.global.L2): they
+// are dead, and discarded lines are not written back, so the partial sums of
+// all splits stay on chip and HBM sees only slot 0. Lines shared with a
+// neighbouring i-block's rows are kept.
+// (not inlined: as a call it leaves the register allocation of the kick's
+// tile loop as it is without this epilogue)
+template <int IPT>
+__device__ __noinline__ void sum_block_slots(const KickArgs &a, const int (&gi)[IPT], int i_lo,
+                                             int i_hi) {
+    __shared__ int s_last;
+    __syncthreads();  // every thread's slot stores issued
+    if (threadIdx.x == 0) {
+        // release: the block's slot stores (ordered before by the barrier)
+        // precede the arrival; acquire: the last arrival sees every slot
+        const int blk = (int)(blockIdx.x / a.splits);
+        int old;
+        asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;"
+                     : "=r"(old)
+                     : "l"(a.blk_cnt + blk)
+                     : "memory");
+        s_last = old == a.splits - 1;
+        if (s_last) a.blk_cnt[blk] = 0;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    const int64_t rows = a.rows;
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+        if (gi[k] < i_hi) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double *p = a.apart + (int64_t)c * rows + gi[k];
+                const int64_t st = 3 * rows;
+                double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+                int s = 0;
+                for (; s + 3 < a.splits; s += 4) {
+                    p0 += __ldcg(p + s * st);
+                    p1 += __ldcg(p + (s + 1) * st);
+                    p2 += __ldcg(p + (s + 2) * st);
+                    p3 += __ldcg(p + (s + 3) * st);
+                }
+                if (s < a.splits) p0 += __ldcg(p + s * st);
+                if (s + 1 < a.splits) p1 += __ldcg(p + (s + 1) * st);
+                if (s + 2 < a.splits) p2 += __ldcg(p + (s + 2) * st);
+                a.apart[(int64_t)c * rows + gi[k]] = (p0 + p1) + (p2 + p3);
+            }
+        }
+    }
+    __syncthreads();  // every read done before a line goes
+    // whole 128-byte lines inside this block's rows of slots 1 .. splits-1:
+    // per slot-component row sc, the lines from the first 128-byte boundary
+    // at or after row i_lo to the last one at or before row i_hi
+    const int L = (int)(((int64_t)(i_hi - i_lo) * 8 + 127) >> 7);  // lines a row range can span
+    const int tot = (a.splits - 1) * 3 * L;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        const int sc = 3 + t / L;
+        const uintptr_t base = (uintptr_t)(a.apart + (int64_t)sc * rows);
+        const uintptr_t l0 = (base + (uintptr_t)i_lo * 8 + 127) & ~(uintptr_t)127;
+        const uintptr_t l1 = (base + (uintptr_t)i_hi * 8) & ~(uintptr_t)127;
+        const uintptr_t line = l0 + ((uintptr_t)(t % L) << 7);
+        if (line < l1)  // [line, line + 128) inside [start, end)
+            asm volatile("discard.global.L2 [%0], 128;" ::"l"(line) : "memory");
+    }
+}
 
 // a + b + c for |c| far below |a + b|, rounded once: the rounding error of
 // a + b (Knuth's two-sum) joins c before the last rounding
@@ -358,6 +429,7 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
             out[2 * rows + gi[k]] = (double)ahz[k] + (double)alz[k];
         }
     }
+    if (a.blk_cnt) sum_block_slots<IPT>(a, gi, it.x, it.y);
 }
 
 // Exact test of the flagged chunks, one warp per entry, lane l on the j rows
@@ -472,6 +544,7 @@ __global__ void __launch_bounds__(256) k_kick_fp64(KickArgs a) {
             out[2 * rows + gi[k]] = az[k];
         }
     }
+    if (a.blk_cnt) sum_block_slots<IPT>(a, gi, it.x, it.y);
 }
 
 // ---------------------------------------------------------------- items
@@ -622,6 +695,8 @@ cudaError_t launch_kick_tiles(const Dev &d, int prec, int flag, double G, int th
     a.perm = d.perm;
     a.far = d.far;
     a.tile = d.tile;
+    a.blk_cnt = d.kick_cnt;
+    a.splits = d.splits;
     if (a.far_tiles) {
         const int64_t ntiles = (d.rows - 1 + TILE - 1) / TILE;
         k_tile_prep<<<(unsigned)ntiles, TILE, 0, st>>>(d.rows, d.pk_pos, d.pk_lo, d.far, d.tile);

@@ -35,6 +35,8 @@ struct Dev {
     float *rH_bound = nullptr;    // [rows] Hill radius bound used by the crude test
     double *apart = nullptr;      // [splits][3][rows] kick partial accelerations
     int32_t splits = 1;
+    int32_t *kick_cnt = nullptr;  // arrivals per i-block: with it the kick's last CTA of
+                                  // each i-block adds the slots into slot 0 (kick.cu)
     // kick work items (one CTA each): (i0, i1, j0, j1) and the partial slot
     int4 *items = nullptr;
     int32_t *item_slot = nullptr;

@@ -200,8 +200,9 @@ __global__ void __launch_bounds__(256) k_finish(Dev d, FinishArgs a) {
     const int q = (int)(gt % kFinLanes);
     const int64_t R = d.rows;
     double ax = 0.0, ay = 0.0, az = 0.0;
+    const int nslots = d.kick_cnt ? 1 : d.splits;  // the kick added its slots into slot 0
     if (pr < R)
-        for (int s = q; s < d.splits; s += kFinLanes) {
+        for (int s = q; s < nslots; s += kFinLanes) {
             const double *p = d.apart + (int64_t)s * 3 * R;
             ax += p[pr];
             ay += p[R + pr];

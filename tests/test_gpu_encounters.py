@@ -66,7 +66,11 @@ def test_dense_disk_records_sampled(torch, oracle, search):
     the last step of a three-step call (with the fused search: a search after
     a fresh kick, then one inside the kick with the |a| of the previous kick
     as allowance). The Kepler output of the step matches the oracle's drift of
-    the same state on a sample of bodies."""
+    the same state on a sample of bodies, and the first kick's accelerations
+    (the velocity change it made, over tau/2) match the oracle's on a sample
+    within the mixed kick's 1e-6: on this disk the kick adds its 64 partial
+    slots per row inside the kick (each i-block's last CTA) instead of in the
+    finisher."""
     w = W.disk_262144()
     R = len(w.m)
     sim = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, search=search)
@@ -86,6 +90,12 @@ def test_dense_disk_records_sampled(torch, oracle, search):
         k = rng.choice(np.arange(1, R), 2000, replace=False)
         r1, u1, *_ = oracle.kepler_drift(q0[k], v0[k], 1.0, w.tau)
         assert np.max(np.linalg.norm(q1[k] - r1, axis=1) / np.linalg.norm(r1, axis=1)) <= 1e-12
+        if nsteps == 1:
+            # first step of a fresh context: v0 = DH velocity + (tau/2) a(q0)
+            a_gpu = (v0[k] - oracle.helio_to_dh(w.m, w.v)[k]) / (0.5 * w.tau)
+            a_ref = oracle.accel_rows(w.m, q0, k)
+            err = np.linalg.norm(a_gpu - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)
+            assert err.max() <= 1e-6, err.max()
         pairs, d2, t2 = oracle.encounters_rows(q0, v0, q1, v1, rH, w.tau, w.a_E, sel)
         ref = {tuple(p) for p in pairs.tolist()}
         got = {tuple(p) for p in mine.tolist() if in_sel[p[0]] or in_sel[p[1]]}
