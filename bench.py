@@ -844,6 +844,39 @@ def run_kepler(args):
                                   "iterations_max": int(itn.max()),
                                   "status": int(st.item()), "clocks": clk.summary()}
     head = res[f"{args.solver}/{args.guess}"]
+    # the guess trained on planetary-system logs alone (no test particles):
+    # Newton iterations (FP64) on the test particles, where it extrapolates,
+    # and on a held-out disk of the same kind as its training disk
+    variants = None
+    if args.train and args.compare:
+        t1 = time.perf_counter()
+        w_disk, l_disk, n_disk = G.train_disk_only()
+        t1 = time.perf_counter() - t1
+        wdd = torch.from_numpy(w_disk).cuda()
+
+        def iters(qq_, vv_, dt_, weights, guess):
+            m_ = len(qq_)
+            a0 = torch.from_numpy(np.ascontiguousarray(qq_.T)).cuda()
+            b0 = torch.from_numpy(np.ascontiguousarray(vv_.T)).cuda()
+            a1, b1 = torch.empty_like(a0), torch.empty_like(b0)
+            it_ = torch.empty(m_, dtype=torch.int32, device="cuda")
+            st_ = torch.zeros(1, dtype=torch.int32, device="cuda")
+            q.qym_kepler_drift_dev(m_, a0, b0, a1, b1, 1.0, dt_, q.QYM_SOLVER_NEWTON, guess,
+                                   weights, 50, iters=it_, status=st_)
+            torch.cuda.synchronize()
+            return float(it_.float().mean().item()), int(st_.item())
+
+        hq, hv, htau = G.heldout_disk()
+        variants = {"disk_only": {"rows": n_disk, "train_seconds": t1,
+                                  "loss_first": float(l_disk[:10].mean()),
+                                  "loss_last": float(l_disk[-100:].mean())},
+                    "newton_iterations": {}}
+        for label, (a_, b_, d_) in (("test_particles", (qq, vv, dt)),
+                                    ("heldout_disk", (hq, hv, htau))):
+            variants["newton_iterations"][label] = {
+                "standard": iters(a_, b_, d_, None, q.QYM_GUESS_STANDARD),
+                "learned_default": iters(a_, b_, d_, wd, q.QYM_GUESS_MLP),
+                "learned_disk_only": iters(a_, b_, d_, wdd, q.QYM_GUESS_MLP)}
     # end to end through the C ABI with host buffers: the state goes host ->
     # device, one drift, device -> host
     hq = torch.from_numpy(np.ascontiguousarray(qq.T)).pin_memory()
@@ -922,7 +955,8 @@ def run_kepler(args):
                        "training": {"rows": nrows, "seconds": t_train,
                                     "loss_first": float(losses[:10].mean()),
                                     "loss_last": float(losses[-100:].mean())}},
-            "compare": res, "gpu_launches": args.steps, "roofline": roof,
+            "compare": res, "guess_training_variants": variants,
+            "gpu_launches": args.steps, "roofline": roof,
             "clocks": head["clocks"], "e2e": e2e, "cpu_baseline": cb}
     print(json.dumps(line))
     return 0

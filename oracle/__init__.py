@@ -46,13 +46,15 @@ class Params(C.Structure):
     _fields_ = [("G", C.c_double), ("a_E", C.c_double), ("a_H", C.c_double),
                 ("eps_H", C.c_double), ("eta", C.c_double), ("eta_s", C.c_double),
                 ("solver", C.c_int32), ("guess", C.c_int32), ("encounters", C.c_int32),
-                ("max_kepler_iter", C.c_int32), ("max_hermite_steps", C.c_int64)]
+                ("max_kepler_iter", C.c_int32), ("max_hermite_steps", C.c_int64),
+                ("whole_hermite", C.c_int32), ("planet_mass", C.c_double)]
 
 
 def params(G=1.0, a_E=3.0, a_H=1.0, eps_H=1e-6, eta=0.02, eta_s=0.01, solver=0, guess=0,
-           encounters=1, max_kepler_iter=50, max_hermite_steps=100000) -> Params:
+           encounters=1, max_kepler_iter=50, max_hermite_steps=100000, whole_hermite=0,
+           planet_mass=1e-7) -> Params:
     return Params(G, a_E, a_H, eps_H, eta, eta_s, solver, guess, encounters, max_kepler_iter,
-                  max_hermite_steps)
+                  max_hermite_steps, whole_hermite, planet_mass)
 
 
 def lib():
@@ -341,7 +343,8 @@ class StepResult:
     enc_d2: np.ndarray       # [k, 2] (d_min^2, threshold^2) of each record
     near: np.ndarray         # [k, 3] unflagged pairs within 2e-6 of the threshold (d^2)
     near_d2: np.ndarray      # [k, 2] their (d_min^2, threshold^2)
-    stats: np.ndarray        # pairs, sets, largest set, Kepler iterations, Hermite steps, Kepler failures
+    stats: np.ndarray        # pairs, sets, largest set, Kepler iterations, Hermite steps, Kepler
+                             # failures, steps integrated whole by the Hermite
     status: int
 
 
@@ -358,7 +361,7 @@ def step(m, q, v, offsets, tau, nsteps, prm: Params | None = None, step0=0,
     encs = []
     d2s = []
     nears, nd2s = [], []
-    stats = np.zeros(6, dtype=np.int64)
+    stats = np.zeros(7, dtype=np.int64)
     status = 0
     for s in range(len(offsets) - 1):
         lo, hi = int(offsets[s]), int(offsets[s + 1])
@@ -376,7 +379,7 @@ def step(m, q, v, offsets, tau, nsteps, prm: Params | None = None, step0=0,
             nd = np.zeros((ncap, 2))
             ncnt = np.zeros(1, dtype=np.int64)
             qt, vt = qs.copy(), vs.copy()
-            st_s = np.zeros(6, dtype=np.int64)
+            st_s = np.zeros(7, dtype=np.int64)
             st = lib().or_step(hi - lo, _d(ms), _d(qt), _d(vt), C.byref(prm), tau, nsteps, step0,
                                None if rhs is None else _d(rhs), _i64(enc), _d(ed2), cap,
                                _i64(cnt), _i64(st_s), _i64(nr), _d(nd), ncap, _i64(ncnt))
@@ -394,7 +397,7 @@ def step(m, q, v, offsets, tau, nsteps, prm: Params | None = None, step0=0,
         nn[:, 1:] += lo
         nears.append(nn)
         nd2s.append(nd[:k].copy())
-        stats[[0, 1, 3, 4, 5]] += st_s[[0, 1, 3, 4, 5]]
+        stats[[0, 1, 3, 4, 5, 6]] += st_s[[0, 1, 3, 4, 5, 6]]
         stats[2] = max(stats[2], st_s[2])
         status = status or st
     return StepResult(q, v, np.concatenate(encs) if encs else np.zeros((0, 3), np.int64),

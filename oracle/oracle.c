@@ -88,6 +88,8 @@ typedef struct {
     int32_t encounters;        /* 0 plain DH step, 1 hybrid step with encounters */
     int32_t max_kepler_iter;
     int64_t max_hermite_steps;
+    int32_t whole_hermite;     /* 1: Sec. 2.3, last paragraph (see or_step) */
+    double planet_mass;        /* planets: m >= planet_mass * m0 */
 } or_params;
 
 /* ------------------------------------------------------------------ */
@@ -1002,13 +1004,35 @@ int or_hermite_set(int64_t k, const int64_t *mem, const double *m, double m0, do
     return status;
 }
 
+/* Sec. 2.3, last paragraph: does some encounter set hold two or more
+ * planets (bodies with m >= mp)?                                      */
+static int or_planets_meet(int64_t nsets, const int64_t *set_start, const int64_t *members,
+                           const double *m, double mp)
+{
+    for (int64_t st = 0; st < nsets; ++st) {
+        int np = 0;
+        for (int64_t a = set_start[st]; a < set_start[st + 1]; ++a)
+            if (m[members[a]] >= mp) ++np;
+        if (np >= 2) return 1;
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Sec. 2, Eq. 5 and Sec. 2.3: one system, nsteps hybrid DH steps.      */
 /* q, v: DH state (heliocentric Q, barycentric v), star row zero.       */
 /* enc: (step, i, j) records up to enc_cap, enc_d2 (optional) their     */
 /* (d_min^2, threshold^2); *enc_count gets the total.                   */
-/* stats[0..5]: encounter pairs, sets, largest set, Kepler iterations,  */
-/* Hermite steps, Kepler non-convergences (summed over steps).          */
+/* stats[0..6]: encounter pairs, sets, largest set, Kepler iterations,  */
+/* Hermite steps, Kepler non-convergences (summed over steps), steps    */
+/* integrated whole by the Hermite.                                     */
+/* With p->whole_hermite (Sec. 2.3, last paragraph, reading R11): when   */
+/* a step's encounter sets put two planets in one set, that step is     */
+/* redone for the whole system by the Hermite: from the positions after */
+/* the opening drift and the velocities entering the first kick, every  */
+/* body is integrated over tau under H_Kep + H_Int (star fixed at the   */
+/* origin, K = 0 for every pair: r_crit infinite), no K corrections and */
+/* no second kick; the closing drift follows as usual.                  */
 /* rH_fixed: NULL -> Hill radii from the orbit entering each Kepler step  */
 /* (reading R6); else per-body radii held fixed for the whole run.       */
 /* Returns 0, or a nonzero status (1 Kepler, 2 Hermite cap).            */
@@ -1030,11 +1054,16 @@ int or_step(int64_t rows, const double *m, double *q, double *v, const or_params
     int64_t *set_start = (int64_t *)malloc(sizeof(int64_t) * (rows + 1));
     int64_t *members = (int64_t *)malloc(sizeof(int64_t) * rows);
     double *rcrit = (double *)malloc(sizeof(double) * rows);
+    double *vpre = p->whole_hermite ? (double *)malloc(b3) : NULL;
+    int64_t *allmem = p->whole_hermite ? (int64_t *)malloc(sizeof(int64_t) * (nb > 0 ? nb : 1)) : NULL;
+    for (int64_t i = 0; allmem && i < nb; ++i) allmem[i] = i + 1;
     int status = 0;
     int64_t ne_total = enc_count ? *enc_count : 0;
     for (int64_t s = 0; s < nsteps; ++s) {
+        int whole = 0;
         /* item 1: drift tau/2 */
         or_drift(rows, m, q, v, 0.5 * tau);
+        if (vpre) memcpy(vpre, v, b3);  /* the velocities entering the first kick */
         /* item 2: interaction tau/2, all pairs, no transition function */
         or_kick(rows, m, q, v, G, 0.5 * tau);
         /* item 3: Kepler tau from (q0, v0) to (q, v); star row stays zero */
@@ -1100,7 +1129,26 @@ int or_step(int64_t rows, const double *m, double *q, double *v, const or_params
                     stats[0] += npairs;
                     stats[1] += nsets;
                 }
-                for (int64_t st = 0; st < nsets; ++st) {
+                if (p->whole_hermite)
+                    whole = or_planets_meet(nsets, set_start, members, m, p->planet_mass * m0);
+                if (whole) {
+                    for (int64_t st = 0; st < nsets; ++st) {
+                        int64_t k = set_start[st + 1] - set_start[st];
+                        if (stats && k > stats[2]) stats[2] = k;
+                    }
+                    /* the whole system from (q0, velocities entering the first kick) */
+                    memcpy(q, q0, b3);
+                    memcpy(v, vpre, b3);
+                    int64_t hs = 0;
+                    if (or_hermite_set(nb, allmem, m, m0, q, v, G, INFINITY, p->eps_H, p->eta,
+                                       p->eta_s, tau, p->max_hermite_steps, &hs))
+                        status = 2;
+                    if (stats) {
+                        stats[4] += hs;
+                        stats[6] += 1;
+                    }
+                }
+                for (int64_t st = 0; !whole && st < nsets; ++st) {
                     int64_t k0 = set_start[st], k = set_start[st + 1] - k0;
                     if (stats && k > stats[2]) stats[2] = k;
                     /* item 5: remove the (1-K) part of the first kick at q0 */
@@ -1123,13 +1171,13 @@ int or_step(int64_t rows, const double *m, double *q, double *v, const or_params
                 }
             }
         }
-        /* item 9: interaction tau/2 */
-        or_kick(rows, m, q, v, G, 0.5 * tau);
+        /* item 9: interaction tau/2 (not after a whole-system Hermite) */
+        if (!whole) or_kick(rows, m, q, v, G, 0.5 * tau);
         /* item 10: drift tau/2 */
         or_drift(rows, m, q, v, 0.5 * tau);
     }
     if (enc_count) *enc_count = ne_total;
     free(q0); free(v0); free(rH); free(its); free(pairs); free(pd2); free(pt2);
-    free(set_of); free(set_start); free(members); free(rcrit);
+    free(set_of); free(set_start); free(members); free(rcrit); free(vpre); free(allmem);
     return status;
 }

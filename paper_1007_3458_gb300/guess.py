@@ -91,3 +91,22 @@ def train_default(seed=0, disk_steps=300, particle_steps=5, **fit_kw):
                       log_particle_rows(qq, vv, dt, particle_steps)])
     wts, losses = fit(rows, seed=seed, **fit_kw)
     return wts, losses, int(rows.shape[0])
+
+
+def train_disk_only(seed=0, disk_steps=600, **fit_kw):
+    """The network fitted to planetary-system logs alone (no test particles):
+    the Kepler solves of `disk_steps` steps of the 16384-body disk (seed 1).
+    Its domain is the disk's (dt / P below about 0.03); on the test
+    particles, which reach dt / P = 0.79, it extrapolates. Returns (weights,
+    losses, number of rows)."""
+    rows = log_system_rows(W.disk_16384(), disk_steps)
+    wts, losses = fit(rows, seed=seed, **fit_kw)
+    return wts, losses, int(rows.shape[0])
+
+
+def heldout_disk(seed=8):
+    """A disk drawn like the 16384-body disk from another seed, its
+    planetesimals' heliocentric states and the step tau: solves the
+    disk-only network has not seen."""
+    w = W.outer_disk(n_planetesimals=16380, m_pl=1e-10, seed=seed, name="disk_16384_heldout")
+    return w.q[5:], w.v[5:], w.tau

@@ -287,6 +287,26 @@ def crossers(seed=6, n_disk=500, n_ecc=150, n_retro=100, n_hill=40, n_hyper=30, 
                     nsteps, eps_H=4.7e-4)
 
 
+def planet_encounter(n_planetesimals=60, seed=9, sep=0.6, phase=0.12, nsteps=20, name=None):
+    """Two Jupiter-mass planets in a close encounter (the case of Sec. 2.3's
+    last paragraph): star + planets of 1e-3 on circular coplanar orbits at
+    a = 5 and 5 + sep, the second `phase` radians ahead (0.78 AU apart for
+    the defaults, inside the 3 x 2 mutual Hill radii of the encounter test),
+    + a cold disk of planetesimals (1e-9, a uniform in [8, 14], Rayleigh(0.01)
+    e and i); tau = P(a=5)/40."""
+    G, m0 = 1.0, 1.0
+    rng = np.random.default_rng(seed)
+    mp = np.array([1e-3, 1e-3])
+    M0 = rng.uniform(0.0, TWO_PI)
+    qp, vp = elements_to_cartesian(G * (m0 + mp), np.array([5.0, 5.0 + sep]), np.zeros(2),
+                                   np.zeros(2), np.zeros(2), np.zeros(2),
+                                   np.array([M0, M0 + phase]))
+    disk = _population(rng, n_planetesimals, 1e-9, 8.0, 14.0, 0.01, 0.01, G, m0)
+    m, q, v = _assemble([(mp, qp, vp), disk], m0)
+    return Workload(name or f"planet_encounter_{len(m)}", m, q, v,
+                    np.array([0, len(m)], dtype=np.int64), TAU_A5, nsteps, eps_H=4.7e-4)
+
+
 def test_particles(n=1048576, seed=4):
     """Massless test particles about a unit-mass star: a log-uniform in
     [0.5, 50], e uniform in [0, 0.9], inclination and angles uniform.

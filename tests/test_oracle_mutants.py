@@ -19,6 +19,18 @@ SRC = os.path.join(ROOT, "oracle", "oracle.c")
 # oracle.c: (name, pin file that must fail: tests/test_oracle_<file>.py,
 # original text, planted text)
 MUTANTS = [
+    ('whole_restarts_from_kicked_v', 'whole',
+     'memcpy(v, vpre, b3);',
+     'memcpy(v, v0, b3);'),
+    ('whole_keeps_second_kick', 'whole',
+     'if (!whole) or_kick(rows, m, q, v, G, 0.5 * tau);',
+     'or_kick(rows, m, q, v, G, 0.5 * tau);'),
+    ('whole_one_planet_enough', 'whole',
+     'if (np >= 2) return 1;',
+     'if (np >= 1) return 1;'),
+    ('whole_keeps_transition', 'whole',
+     'G, INFINITY, p->eps_H, p->eta,',
+     'G, rcrit[0], p->eps_H, p->eta,'),
     ('stumpff_series_factorial', 'kepler',
      'term_s *= -y / ((2.0 * k + 4.0) * (2.0 * k + 5.0));',
      'term_s *= -y / ((2.0 * k + 4.0) * (2.0 * k + 6.0));'),
