@@ -42,6 +42,13 @@ WORKLOADS = {
 METRIC = "particle-steps/s"
 # E_Kep alone on massless test particles: a "step" is one Kepler drift of
 # every particle; the learned guess is compared with the standard one
+# the whole-system Hermite (Sec. 2.3, last paragraph): every step of these
+# switches (two Jupiter-mass planets 0.8 AU apart)
+WHOLE_WORKLOADS = {
+    "planet_encounter_16384": (16381, "two Jupiter-mass planets at a = 5 and 5.6 AU, 0.12 rad "
+                                      "apart, + 16381 planetesimals (1e-9, a 8-14 AU), seed 9; "
+                                      "whole_hermite = 1"),
+}
 KEPLER_WORKLOADS = {
     "kepler_1m": "1,048,576 massless test particles about a unit star: a log-uniform 0.5-50, "
                  "e uniform 0-0.9, seed 4; tau = P(a=5)/40; E_Kep only",
@@ -759,6 +766,53 @@ def hbm_peak_gbs():
         return 6800.0, "fallback"
 
 
+def run_whole(args):
+    """Steps that switch to the whole-system Hermite (whole.cu): time per step
+    (the host drives the block steps and reads the sets back each step, so
+    the step is timed on the host clock around synchronised calls), block
+    steps per step, and the energy error beside the hybrid step's."""
+    import torch
+    import paper_1007_3458_gb300 as q
+    from paper_1007_3458_gb300 import workloads as W
+    q.build()
+    npl, desc = WHOLE_WORKLOADS[args.workload]
+    w = W.planet_encounter(n_planetesimals=npl, name=args.workload)
+    prec = q.QYM_KICK_MIXED if args.prec == "mixed" else q.QYM_KICK_FP64
+    out = {}
+    for label, wh in (("whole", 1), ("hybrid", 0)):
+        sim = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=prec, eps_H=w.eps_H,
+                           whole_hermite=wh)
+        E0 = sim.energy()[0]
+        sim.step(w.tau, args.warmup)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.step(w.tau, args.steps)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = sim.stats()
+        E1 = sim.energy()[0]
+        sim.close()
+        out[label] = {"ms_per_step": 1e3 * dt / args.steps,
+                      "value": len(w.m[1:]) * args.steps / dt,
+                      "whole_steps": int(st["whole_steps"]),
+                      "hermite_block_steps": int(st["hermite_steps"]),
+                      "us_per_block_step": (1e6 * dt / st["hermite_steps"]
+                                            if wh and st["hermite_steps"] else None),
+                      "launches": int(st["launches"]),
+                      "energy_error_after": abs(E1 / E0 - 1.0), "status": int(st["status_bits"])}
+    head = out["whole"]
+    line = {"metric": METRIC, "value": head["value"], "unit": METRIC, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (whole-system Hermite)", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "tau": w.tau,
+                       "kick": args.prec, "timing": "host clock around synchronised qym_step "
+                       "calls (the switch reads the sets back every step)"},
+            "compare": out, "gpu_launches": head["launches"]}
+    print(json.dumps(line))
+    return 0
+
+
 def run_kepler(args):
     """E_Kep of 1,048,576 test particles (Appendix): timed drifts with the
     standard and the learned starting guess."""
@@ -970,7 +1024,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default="disk_16384",
-                    choices=sorted(WORKLOADS) + sorted(KEPLER_WORKLOADS))
+                    choices=sorted(WORKLOADS) + sorted(KEPLER_WORKLOADS) + sorted(WHOLE_WORKLOADS))
     ap.add_argument("--guess", default="standard", choices=["standard", "learned"],
                     help="kepler_1m: the starting guess of the headline number")
     ap.add_argument("--compare", type=int, default=1,
@@ -1011,6 +1065,8 @@ def main():
         return run_reference(args)
     if args.workload in KEPLER_WORKLOADS:
         return run_kepler(args)
+    if args.workload in WHOLE_WORKLOADS:
+        return run_whole(args)
     if args.sweep:
         return run_sweep(args)
     return run_ours(args)

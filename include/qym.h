@@ -118,6 +118,18 @@ typedef struct qym_params {
                                    (8 for a single system, 2 for a batch of systems) */
     int32_t search;             /* how the close-encounter candidates are found (Sec. 2.4):
                                    QYM_SEARCH_AUTO (default), _FUSED or _BINNED */
+    int32_t whole_hermite;      /* 1: Sec. 2.3, last paragraph: when a step's encounter sets
+                                   put two planets in one set, that system's step is redone
+                                   by the Hermite for every body: from the positions after the
+                                   opening drift and the velocities entering the first kick,
+                                   all bodies over tau under H_Kep + H_Int (star fixed at the
+                                   origin, every pair with its full force, smoothed with
+                                   eps_H), no K corrections and no second kick, then the
+                                   closing drift. qym_step then reads the sets back once per
+                                   step (no step graph); not with merge_kicks or a split
+                                   step. 0 (default): off */
+    double planet_mass;         /* planets for whole_hermite: m >= planet_mass * m0
+                                   (default 1e-7) */
 } qym_params;
 
 /* Close-encounter search: which pairs the rigorous test (Sec. 2.4) examines.
@@ -154,6 +166,7 @@ typedef struct qym_stats {
     int64_t hermite_steps_max;  /* most Hermite steps one set took within one step */
     int32_t status_bits;        /* OR of QYM_ST_* seen */
     int32_t kick_tile_i, kick_tile_splits;  /* launch shape in use */
+    int32_t whole_steps;        /* steps integrated whole by the Hermite (whole_hermite) */
 } qym_stats;
 
 typedef struct qym_ctx qym_ctx;   /* opaque; owned by the library */

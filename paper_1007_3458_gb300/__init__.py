@@ -49,7 +49,8 @@ class qym_params(C.Structure):
                 ("max_encounters", C.c_int64), ("max_log", C.c_int64),
                 ("l2_flush_bytes", C.c_int64), ("heavy_mass", C.c_double),
                 ("merge_kicks", C.c_int32), ("hermite_cluster", C.c_int32),
-                ("search", C.c_int32)]
+                ("search", C.c_int32), ("whole_hermite", C.c_int32),
+                ("planet_mass", C.c_double)]
 
 
 class qym_stats(C.Structure):
@@ -58,7 +59,7 @@ class qym_stats(C.Structure):
                 ("hermite_steps", C.c_int64), ("rescans", C.c_int64), ("launches", C.c_int64),
                 ("hermite_steps_max", C.c_int64),
                 ("status_bits", C.c_int32), ("kick_tile_i", C.c_int32),
-                ("kick_tile_splits", C.c_int32)]
+                ("kick_tile_splits", C.c_int32), ("whole_steps", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

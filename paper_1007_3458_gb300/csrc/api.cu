@@ -78,6 +78,13 @@ struct qym_ctx {
     SearchArgs sarg{};
     int32_t nstiles = 0;
     int64_t nstpairs = 0;
+    // whole-system Hermite (params.whole_hermite): scratch for the largest
+    // system, the star masses, this qym_step call's counts
+    WholeArgs wh{};
+    int64_t wh_nbmax = 0;
+    std::vector<double> h_m0;
+    std::vector<int32_t> h_wh_flag;
+    int64_t wh_steps = 0, wh_hsteps = 0, wh_hmax = 0;
 };
 
 #define FAIL(ctx, code, msg)                         \
@@ -119,6 +126,8 @@ extern "C" qym_status qym_default_params(qym_params *p) {
     p->l2_flush_bytes = 0;
     p->heavy_mass = 1e-7;
     p->search = QYM_SEARCH_AUTO;
+    p->whole_hermite = 0;
+    p->planet_mass = 1e-7;
     return QYM_OK;
 }
 
@@ -144,6 +153,12 @@ static bool valid_params(const qym_params *p, std::string &why) {
     if (p->hermite_cluster != 0 && p->hermite_cluster != 2 && p->hermite_cluster != 4 &&
         p->hermite_cluster != 8) {
         why = "hermite_cluster must be 0, 2, 4 or 8";
+        return false;
+    }
+    if (p->whole_hermite != 0 && p->whole_hermite != 1) { why = "whole_hermite must be 0 or 1"; return false; }
+    if (!(p->planet_mass >= 0.0) || !std::isfinite(p->planet_mass)) { why = "planet_mass must be >= 0"; return false; }
+    if (p->whole_hermite && p->merge_kicks) {
+        why = "whole_hermite needs the paper's two kicks per step (merge_kicks = 0)";
         return false;
     }
     return true;
@@ -243,6 +258,27 @@ static void carve_all(qym_ctx *c, Carver &k) {
         c->sortw.hist = k.take<uint32_t>(256 * (size_t)sort_blocks(R));
         d.far = k.take<float4>(R);
         d.tile = k.take<float4>(3 * (size_t)((R - 1 + kKickTile - 1) / kKickTile));
+    }
+    if (c->p.whole_hermite) {
+        WholeArgs &w = c->wh;
+        const int64_t L = std::max<int64_t>(1, c->wh_nbmax);
+        d.wh_flag = k.take<int32_t>(d.nsys);
+        d.vpre = k.take<double>(3 * (size_t)R);
+        w.grid = 8 * 152;
+        w.x = k.take<double>(3 * (size_t)L);
+        w.u = k.take<double>(3 * (size_t)L);
+        w.xp = k.take<double>(3 * (size_t)L);
+        w.up = k.take<double>(3 * (size_t)L);
+        w.a0 = k.take<double>(3 * (size_t)L);
+        w.j0 = k.take<double>(3 * (size_t)L);
+        w.part = k.take<double>(6 * (size_t)std::max<int64_t>(L, w.grid));
+        w.ti = k.take<long long>(L);
+        w.lev = k.take<int32_t>(L);
+        w.act = k.take<int32_t>(L);
+        w.ctl = k.take<int32_t>(WC_COUNT);
+        w.tn = k.take<long long>(1);
+        w.steps = k.take<long long>(1);
+        w.ld = L;
     }
     if (c->binned) {
         SearchArgs &a = c->sarg;
@@ -370,6 +406,14 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     Dev &d = c->d;
     d.rows = R;
     d.nsys = nsys;
+    if (params->whole_hermite) {
+        c->h_m0.resize(nsys);
+        c->h_wh_flag.assign(nsys, 0);
+        for (int32_t s = 0; s < nsys; ++s) {
+            c->h_m0[s] = m[offsets[s]];
+            c->wh_nbmax = std::max<int64_t>(c->wh_nbmax, offsets[s + 1] - offsets[s] - 1);
+        }
+    }
     c->tune = default_tune(c->h_offsets, params->kick_prec);
     d.nitems = kick_items_count(offsets, nsys, c->tune);
     d.splits = c->tune.splits;
@@ -657,6 +701,62 @@ static cudaError_t enqueue_fresh_search_kick(qym_ctx *c, double dt) {
     return cudaSuccess;
 }
 
+// Sec. 2.3, last paragraph: the systems whose sets put two planets in one set
+// this step (the sets just built) are integrated whole by the Hermite into
+// (q1, v1); the host reads the flags and drives the block steps in chunks of
+// 32 (four kernels each), reading the done flag after each chunk.
+static cudaError_t enqueue_whole(qym_ctx *c, double tau) {
+    Dev &d = c->d;
+    const qym_params &p = c->p;
+    cudaStream_t st = c->stream;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(d.wh_flag, 0, sizeof(int32_t) * d.nsys, st))) return e;
+    if ((e = launch_wh_trigger(d, p.planet_mass, d.wh_flag, st))) return e;
+    if ((e = cudaMemcpyAsync(c->h_wh_flag.data(), d.wh_flag, sizeof(int32_t) * d.nsys,
+                             cudaMemcpyDeviceToHost, st)))
+        return e;
+    if ((e = cudaStreamSynchronize(st))) return e;
+    c->launches += 2;
+    for (int32_t s = 0; s < d.nsys; ++s) {
+        if (!c->h_wh_flag[s]) continue;
+        WholeArgs w = c->wh;
+        w.R = d.rows;
+        w.r0 = c->h_offsets[s];
+        w.nb = (int32_t)(c->h_offsets[s + 1] - w.r0 - 1);
+        w.m = d.m;
+        w.G = p.G;
+        w.m0 = c->h_m0[s];
+        w.eps2 = p.eps_H * p.eps_H;
+        w.eta = p.eta;
+        w.eta_s = p.eta_s;
+        w.T = std::fabs(tau);
+        w.sg = tau >= 0.0 ? 1.0 : -1.0;
+        w.tick = w.T / (double)(1ll << 48);
+        w.max_steps = p.max_hermite_steps;
+        w.status = d.status;
+        if ((e = launch_wh_start(w, d.q, d.vpre, st))) return e;
+        c->launches += 4;
+        int32_t done = 0;
+        const int64_t chunks = p.max_hermite_steps / 32 + 2;
+        for (int64_t k = 0; k < chunks && !done; ++k) {
+            if ((e = launch_wh_blocks(w, 32, st))) return e;
+            if ((e = cudaMemcpyAsync(&done, w.ctl + WC_DONE, sizeof(done), cudaMemcpyDeviceToHost, st)))
+                return e;
+            if ((e = cudaStreamSynchronize(st))) return e;
+            c->launches += 4 * 32;
+        }
+        long long steps = 0;
+        if ((e = cudaMemcpyAsync(&steps, w.steps, sizeof(steps), cudaMemcpyDeviceToHost, st))) return e;
+        if ((e = launch_wh_store(w, d.q1, d.v1, st))) return e;
+        if ((e = cudaStreamSynchronize(st))) return e;
+        c->launches += 1;
+        c->wh_steps += 1;
+        c->wh_hsteps += steps;
+        c->wh_hmax = std::max<int64_t>(c->wh_hmax, steps);
+    }
+    return cudaSuccess;
+}
+
 static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last, bool fresh = false) {
     Dev &d = c->d;
     const qym_params &p = c->p;
@@ -668,6 +768,10 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last, bool fresh = 
     }
     k_step_begin<<<1, 256, 0, st>>>(d.ctr, d.vmax, d.nsys, c->sarg.tbox_bits, c->binned ? 6 * (int64_t)c->nstiles : 0);
     const int fz = fused_search(c);
+    // the velocities entering the first kick, for a whole-system Hermite
+    if (p.whole_hermite &&
+        (e = cudaMemcpyAsync(d.vpre, d.v, sizeof(double) * 3 * d.rows, cudaMemcpyDeviceToDevice, st)))
+        return e;
     // item 2: kick tau/2, with the crude encounter search when it is fused
     if (fz && fresh) {
         if ((e = enqueue_fresh_search_kick(c, 0.5 * tau))) return e;
@@ -688,15 +792,19 @@ static cudaError_t enqueue_step(qym_ctx *c, double tau, bool last, bool fresh = 
         if ((e = enqueue_binned_search(c, tau))) return e;
         if ((e = launch_refine(d, tau, p.a_E, st))) return e;
         if ((e = launch_sets_impl(d, p.a_H, c->ss, st))) return e;
+        // (the sets of a system integrated whole are left out of the Hermite)
+        if (p.whole_hermite && (e = enqueue_whole(c, tau))) return e;
         if ((e = launch_hermite(d, p, tau, st))) return e;
     }
     // (q1, v1) -> (q, v) and the float packs for the second kick
     if ((e = launch_drift_pack_from(d, d.q1, d.v1, 0.0, 0.0, tau, p.a_E, p.G, 0, p.hill_fixed, st,
                                     0.5 * tau)))
         return e;
-    // item 9: kick tau/2
+    // item 9: kick tau/2 (not for a system integrated whole)
     if ((e = launch_kick_tiles(d, p.kick_prec, 0, p.G, c->tune.threads, c->tune.ipt, st))) return e;
-    if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, 0, p.hill_fixed, st))) return e;
+    if ((e = launch_kick_finish_v(d, d.v, d.q, 0.5 * tau, p.G, 0, p.hill_fixed, st, 1.01,
+                                  p.whole_hermite)))
+        return e;
     // item 10 (and item 1 of the next step): drift tau/2 with S = sum m v
     if ((e = launch_momentum(d, st))) return e;
     if ((e = launch_drift_pack_from(d, d.q, d.v, 0.5 * tau, last ? 0.0 : 0.5 * tau, tau, p.a_E,
@@ -806,6 +914,9 @@ static qym_status collect(qym_ctx *c, int64_t nsteps) {
     s.hermite_steps_max = (int64_t)ctr[C_MAX_HSET];
     s.kick_tile_i = c->tune.threads * c->tune.ipt;
     s.kick_tile_splits = c->tune.splits;
+    s.whole_steps = (int32_t)c->wh_steps;
+    s.hermite_steps += c->wh_hsteps;
+    s.hermite_steps_max = std::max<int64_t>(s.hermite_steps_max, c->wh_hmax);
     c->status_bits = status;
     if (status & QYM_ST_NAN) FAIL(c, QYM_ENAN, "non-finite state after a Kepler drift");
     if (status & (QYM_ST_KEPLER_NOCONV | QYM_ST_HERMITE_CAP))
@@ -836,6 +947,7 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
         CK(c, cudaMemcpyAsync(c->klog_base, &c->klog_steps, sizeof(c->klog_steps),
                               cudaMemcpyHostToDevice, st));
     c->launches = 0;
+    c->wh_steps = c->wh_hsteps = c->wh_hmax = 0;
     if (d.perm && !c->sort_current) {
         // the kick's order from the positions at the start of the call (unless
         // set_state has just taken it)
@@ -867,7 +979,8 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
             cudaGraphExecDestroy(c->gexec);
             c->gexec = nullptr;
         }
-        if (!c->gexec && interior >= 2) {
+        // (a whole-system Hermite reads the sets back mid-step: no graph)
+        if (!c->gexec && interior >= 2 && !p.whole_hermite) {
             cudaGraph_t g;
             CK(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             int64_t before = c->launches;
@@ -1080,6 +1193,7 @@ __global__ void k_import_count(Dev d, int64_t n) {
 extern "C" qym_status qym_split_init(qym_ctx *c, int32_t rank, int32_t world) {
     if (!c) FAIL(nullptr, QYM_EINVAL, "qym_split_init: NULL context");
     if (c->d.nsys != 1) FAIL(c, QYM_EINVAL, "qym_split_init: one system per context");
+    if (c->p.whole_hermite) FAIL(c, QYM_EINVAL, "qym_split_init: not with whole_hermite");
     if (world < 1 || rank < 0 || rank >= world) FAIL(c, QYM_EINVAL, "qym_split_init: bad rank or world");
     if (c->klog) FAIL(c, QYM_EINVAL, "qym_split_init: the Kepler solve log is not split");
     int64_t lo = 0, hi = 0;

@@ -567,6 +567,13 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
                 d.uf[d.set_mem[st + k]] = -1;
         return;
     }
+    // a system integrated whole by the Hermite this step (whole.cu): its
+    // members only leave the union-find
+    if (d.wh_flag && d.wh_flag[d.sys_of[d.set_mem[st]]]) {
+        if (rank == 0)
+            for (int k = tid; k < n; k += blockDim.x) d.uf[d.set_mem[st + k]] = -1;
+        return;
+    }
     // this CTA's member range (COOP) or all members
     const int mlo = n * rank / cs, mhi = n * (rank + 1) / cs;
     const int P = lanes_per_member(mhi - mlo, n);

@@ -37,6 +37,9 @@ struct Dev {
     int32_t splits = 1;
     int32_t *kick_cnt = nullptr;  // arrivals per i-block: with it the kick's last CTA of
                                   // each i-block adds the slots into slot 0 (kick.cu)
+    int32_t *wh_flag = nullptr;   // [nsys] 1: this step of the system is integrated whole
+                                  // by the Hermite (whole.cu); its sets are not
+    double *vpre = nullptr;       // [3][rows] velocities entering the first kick
     // kick work items (one CTA each): (i0, i1, j0, j1) and the partial slot
     int4 *items = nullptr;
     int32_t *item_slot = nullptr;
@@ -231,9 +234,11 @@ cudaError_t launch_drift_pack_from(const Dev &d, const double *qs, const double 
                                    double kick_span, double a_allow = 1.01);
 // a_allow: the bound on |a| / |a of the last kick| that the crude reach of the
 // preceding pack assumed (checked when check != 0)
+// skip_whole: leave v of the systems flagged in d.wh_flag (their step was
+// integrated whole: no second kick)
 cudaError_t launch_kick_finish_v(const Dev &d, double *v, const double *q, double dt, double G,
                                  int check, int hill_fixed, cudaStream_t st,
-                                 double a_allow = 1.01);
+                                 double a_allow = 1.01, int skip_whole = 0);
 cudaError_t launch_hill_init(const Dev &d, double G, cudaStream_t st);
 cudaError_t launch_to_dh_impl(const Dev &d, int inverse, double *vout, double *mt_scratch,
                               cudaStream_t st);
@@ -312,6 +317,31 @@ cudaError_t hermite_prepare();
 cudaError_t launch_transition(int64_t n, const double *s, double rc, double *K, double *Kp,
                               double *Kpp, cudaStream_t st);
 cudaError_t launch_hermite(const Dev &d, const qym_params &p, double tau, cudaStream_t st);
+
+// whole.cu: the whole-system Hermite (Sec. 2.3, last paragraph)
+enum WholeCtl { WC_NA = 0, WC_DONE, WC_NCH, WC_COUNT };
+struct WholeArgs {
+    int64_t R;           // rows of the context's [3][R] arrays
+    int64_t r0;          // the system's star row; its bodies are rows r0+1 .. r0+nb
+    int64_t ld;          // stride of the scratch arrays' coordinates
+    int32_t nb;          // bodies
+    int32_t grid;        // CTAs of the force kernel
+    const double *m;
+    double G, m0, eps2, eta, eta_s, T, sg, tick;
+    int64_t max_steps;   // block steps
+    double *x, *u, *xp, *up, *a0, *j0;  // [3][ld]
+    double *part;        // [max(grid, nb)][6] partner-range sums
+    long long *ti;       // [nb] time of each body (ticks of |tau| 2^-48)
+    int32_t *lev;        // [nb] step level
+    int32_t *act;        // [nb] bodies of the block step
+    int32_t *ctl;        // [WC_COUNT]
+    long long *tn, *steps;
+    int32_t *status;
+};
+cudaError_t launch_wh_trigger(const Dev &d, double planet_mass, int32_t *flag, cudaStream_t st);
+cudaError_t launch_wh_start(const WholeArgs &w, const double *q, const double *vpre, cudaStream_t st);
+cudaError_t launch_wh_blocks(const WholeArgs &w, int nblocks, cudaStream_t st);
+cudaError_t launch_wh_store(const WholeArgs &w, double *q1, double *v1, cudaStream_t st);
 
 // energy.cu
 int32_t energy_items_host(const int64_t *offsets, int32_t nsys, int4 *items, int32_t *isys,

@@ -186,6 +186,7 @@ struct FinishArgs {
     double dt, G;
     float a_allow;      // the crude reach's bound on |a| / |a of the last kick|
     int check, hill_fixed;
+    int skip_whole;     // v of systems flagged in d.wh_flag stays
 };
 
 constexpr int kFinLanes = 4;  // lanes that share one row's partial sums
@@ -225,10 +226,13 @@ __global__ void __launch_bounds__(256) k_finish(Dev d, FinishArgs a) {
         heavy_pull(d.heavy_rows + h0, h1 - h0, r, a.q[r], a.q[R + r], a.q[2 * R + r], a.q, d.m, R,
                    a.G, ax, ay, az);
     }
-    double vx = a.v[r] + a.dt * ax;
-    double vy = a.v[R + r] + a.dt * ay;
-    double vz = a.v[2 * R + r] + a.dt * az;
-    a.v[r] = vx; a.v[R + r] = vy; a.v[2 * R + r] = vz;
+    double vx = a.v[r], vy = a.v[R + r], vz = a.v[2 * R + r];
+    if (!(a.skip_whole && d.wh_flag && d.wh_flag[sys])) {
+        vx += a.dt * ax;
+        vy += a.dt * ay;
+        vz += a.dt * az;
+        a.v[r] = vx; a.v[R + r] = vy; a.v[2 * R + r] = vz;
+    }
     float an = round_up_f(sqrt(ax * ax + ay * ay + az * az));
     if (a.check) {
         if (d.vmax)  // the binned search's bound takes the largest |v| entering the drift
@@ -248,8 +252,10 @@ __global__ void __launch_bounds__(256) k_finish(Dev d, FinishArgs a) {
 }
 
 cudaError_t launch_kick_finish_v(const Dev &d, double *v, const double *q, double dt, double G,
-                                 int check, int hill_fixed, cudaStream_t st, double a_allow) {
+                                 int check, int hill_fixed, cudaStream_t st, double a_allow,
+                                 int skip_whole) {
     FinishArgs a;
+    a.skip_whole = skip_whole;
     a.v = v;
     a.q = q;
     a.dt = dt;
