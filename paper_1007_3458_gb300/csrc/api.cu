@@ -83,6 +83,9 @@ struct qym_ctx {
     WholeArgs wh{};
     int64_t wh_nbmax = 0;
     std::vector<double> h_m0;
+    std::vector<int32_t> h_wh_heavy;      // each system's heavy bodies (indices of its bodies)
+    std::vector<int64_t> h_wh_heavy_off;  // [nsys+1] their ranges
+    int32_t *wh_heavy = nullptr;          // device copy
     std::vector<int32_t> h_wh_flag;
     int64_t wh_steps = 0, wh_hsteps = 0, wh_hmax = 0;
 };
@@ -272,6 +275,11 @@ static void carve_all(qym_ctx *c, Carver &k) {
         w.a0 = k.take<double>(3 * (size_t)L);
         w.j0 = k.take<double>(3 * (size_t)L);
         w.part = k.take<double>(6 * (size_t)std::max<int64_t>(L, w.grid));
+        w.pf_hi = k.take<float4>(L);
+        w.pf_lo = k.take<float4>(L);
+        w.vf_hi = k.take<float4>(L);
+        w.vf_lo = k.take<float4>(L);
+        c->wh_heavy = k.take<int32_t>(std::max<size_t>(1, c->h_wh_heavy.size()));
         w.ti = k.take<long long>(L);
         w.lev = k.take<int32_t>(L);
         w.act = k.take<int32_t>(L);
@@ -409,9 +417,15 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     if (params->whole_hermite) {
         c->h_m0.resize(nsys);
         c->h_wh_flag.assign(nsys, 0);
+        c->h_wh_heavy_off.assign(nsys + 1, 0);
         for (int32_t s = 0; s < nsys; ++s) {
             c->h_m0[s] = m[offsets[s]];
             c->wh_nbmax = std::max<int64_t>(c->wh_nbmax, offsets[s + 1] - offsets[s] - 1);
+            // heavy: m >= heavy_mass m0 (every body when heavy_mass <= 0)
+            const double thr = params->heavy_mass > 0.0 ? params->heavy_mass * m[offsets[s]] : 0.0;
+            for (int64_t r = offsets[s] + 1; r < offsets[s + 1]; ++r)
+                if (m[r] >= thr) c->h_wh_heavy.push_back((int32_t)(r - offsets[s] - 1));
+            c->h_wh_heavy_off[s + 1] = (int64_t)c->h_wh_heavy.size();
         }
     }
     c->tune = default_tune(c->h_offsets, params->kick_prec);
@@ -535,6 +549,9 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     std::vector<int32_t> eis(c->neitems), ei0(nsys + 1);
     energy_items_host(offsets, nsys, eit.data(), eis.data(), ei0.data());
     CKI(cudaMemcpyAsync(d.offsets, offsets, sizeof(int64_t) * (nsys + 1), cudaMemcpyHostToDevice, c->stream));
+    if (!c->h_wh_heavy.empty())
+        CKI(cudaMemcpyAsync(c->wh_heavy, c->h_wh_heavy.data(), sizeof(int32_t) * c->h_wh_heavy.size(),
+                            cudaMemcpyHostToDevice, c->stream));
     CKI(cudaMemcpyAsync(d.sys_of, sys_of.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, c->stream));
     CKI(cudaMemcpyAsync(d.m, m, sizeof(double) * R, cudaMemcpyHostToDevice, c->stream));
     CKI(cudaMemcpyAsync(d.items, items.data(), sizeof(int4) * d.nitems, cudaMemcpyHostToDevice, c->stream));
@@ -734,6 +751,9 @@ static cudaError_t enqueue_whole(qym_ctx *c, double tau) {
         w.tick = w.T / (double)(1ll << 48);
         w.max_steps = p.max_hermite_steps;
         w.status = d.status;
+        w.heavy_thr = p.heavy_mass > 0.0 ? p.heavy_mass * w.m0 : 0.0;
+        w.heavy = c->wh_heavy + c->h_wh_heavy_off[s];
+        w.nheavy = (int32_t)(c->h_wh_heavy_off[s + 1] - c->h_wh_heavy_off[s]);
         if ((e = launch_wh_start(w, d.q, d.vpre, st))) return e;
         c->launches += 4;
         int32_t done = 0;

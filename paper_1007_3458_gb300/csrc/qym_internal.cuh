@@ -330,6 +330,14 @@ struct WholeArgs {
     double G, m0, eps2, eta, eta_s, T, sg, tick;
     int64_t max_steps;   // block steps
     double *x, *u, *xp, *up, *a0, *j0;  // [3][ld]
+    // the prediction split into float hi + lo parts for the light partners'
+    // FP32 pair terms: (x, y, z, G m) and (x, y, z, -) of the position, the
+    // velocity's the same; heavy bodies (m >= heavy_thr) enter at G m = 0 and
+    // are summed in FP64 over `heavy` instead
+    float4 *pf_hi, *pf_lo, *vf_hi, *vf_lo;  // [ld]
+    double heavy_thr;
+    const int32_t *heavy;  // the system's heavy bodies (indices of its bodies, ascending)
+    int32_t nheavy;
     double *part;        // [max(grid, nb)][6] partner-range sums
     long long *ti;       // [nb] time of each body (ticks of |tau| 2^-48)
     int32_t *lev;        // [nb] step level

@@ -10,15 +10,22 @@
 //
 // A system of any size: the state lives in global memory and each block step
 // is four kernels, enqueued by the host in chunks (the paper computes the
-// accelerations and jerks on the GPU and steps on the CPU):
+// accelerations and jerks on the GPU and steps on the CPU). As in the mixed
+// kick, the pull of the light bodies (m < heavy_mass m0) is an FP32 pair term
+// on double-single separations, and the heavy bodies' pull is FP64 (they
+// carry almost all of the interaction; a light body's pull enters the sums
+// at 1e-7 of itself):
 //   k_wh_next     one CTA: the next block time t_n (the earliest end of a
 //                 body's step), the bodies whose step ends there in row order,
 //                 the split of their partner sums over CTAs; `done` at tau
-//   k_wh_predict  every body predicted to t_n from its own time
+//   k_wh_predict  every body predicted to t_n from its own time (FP64, and
+//                 split into float hi + lo parts)
 //   k_wh_force    (active body, partner range) items over a fixed grid: the
-//                 range's pair accelerations and jerks, summed in a fixed tree
-//   k_wh_correct  per active body: its ranges in order plus the star's pull,
-//                 the corrector, the Aarseth criterion and the new level
+//                 range's light pair accelerations and jerks, summed in a
+//                 fixed tree
+//   k_wh_correct  per active body: its ranges in order, the heavy bodies' and
+//                 the star's pull in FP64, the corrector, the Aarseth
+//                 criterion and the new level
 // Time runs in integer ticks of |tau| / 2^48 as in the set Hermite; a level
 // grows by one only on a commensurate block time. Every kernel returns at once
 // when `done` is set, so a chunk may run past tau without effect.
@@ -172,51 +179,69 @@ __global__ void __launch_bounds__(256) k_wh_predict(WholeArgs w) {
     if (i >= w.nb) return;
     const long long tn = *w.tn;
     const double h = w.sg * (double)(tn - w.ti[i]) * w.tick;
+    float ph[3], pl[3], vh[3], vl[3];
     for (int c = 0; c < 3; ++c) {
         const int64_t id = c * w.ld + i;
         const double x = w.x[id], u = w.u[id], a = w.a0[id], j = w.j0[id];
-        w.xp[id] = x + h * (u + h * (0.5 * a + h * j / 6.0));
-        w.up[id] = u + h * (a + 0.5 * h * j);
+        const double xp = x + h * (u + h * (0.5 * a + h * j / 6.0));
+        const double up = u + h * (a + 0.5 * h * j);
+        w.xp[id] = xp;
+        w.up[id] = up;
+        split_ds(xp, ph[c], pl[c]);
+        split_ds(up, vh[c], vl[c]);
     }
+    const double mj = w.m[w.r0 + 1 + i];
+    const float gm = mj >= w.heavy_thr ? 0.0f : (float)(w.G * mj);
+    w.pf_hi[i] = make_float4(ph[0], ph[1], ph[2], gm);
+    w.pf_lo[i] = make_float4(pl[0], pl[1], pl[2], 0.0f);
+    w.vf_hi[i] = make_float4(vh[0], vh[1], vh[2], 0.0f);
+    w.vf_lo[i] = make_float4(vl[0], vl[1], vl[2], 0.0f);
 }
 
-// pair accelerations and jerks of the active bodies over partner ranges:
-// item (k, c) = active body k, range c of nch; each thread a stride of the
-// range, the CTA's six sums by warp trees then in warp order
+// the light partners' accelerations and jerks on the active bodies over
+// partner ranges: item (k, c) = active body k, range c of nch; each thread a
+// stride of the range in FP32 (separations as double-single differences, the
+// smoothed pair term of the set Hermite with K = 0), its sums then in FP64 by
+// warp trees and in warp order
 __global__ void __launch_bounds__(kForceThreads) k_wh_force(WholeArgs w) {
     __shared__ double s_part[kForceThreads / 32][6];
     if (w.ctl[WC_DONE]) return;
     const int na = w.ctl[WC_NA], nch = w.ctl[WC_NCH];
     const int64_t items = (int64_t)na * nch;
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-    const int64_t ld = w.ld;
+    const float eps2 = (float)w.eps2;
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const int k = (int)(it / nch), c = (int)(it - (int64_t)k * nch);
         const int64_t i = w.act[k];
         const int64_t lo = w.nb * c / nch, hi = w.nb * (c + 1) / nch;
-        const double xi = w.xp[i], yi = w.xp[ld + i], zi = w.xp[2 * ld + i];
-        const double ui = w.up[i], vi = w.up[ld + i], wi = w.up[2 * ld + i];
-        double s[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        const float4 pih = w.pf_hi[i], pil = w.pf_lo[i], vih = w.vf_hi[i], vil = w.vf_lo[i];
+        float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int64_t j = lo + tid; j < hi; j += blockDim.x) {
             if (j == i) continue;
-            const double dx = xi - w.xp[j], dy = yi - w.xp[ld + j], dz = zi - w.xp[2 * ld + j];
-            const double ex = ui - w.up[j], ey = vi - w.up[ld + j], ez = wi - w.up[2 * ld + j];
-            const double s2 = dx * dx + dy * dy + dz * dz + w.eps2;
-            const double is = rsqrt(s2), is2 = is * is;
-            const double g = -w.G * w.m[w.r0 + 1 + j] * is * is2;   // -G m_j / s^3
-            const double t3 = 3.0 * (dx * ex + dy * ey + dz * ez) * is2;
-            s[0] = fma(g, dx, s[0]);
-            s[1] = fma(g, dy, s[1]);
-            s[2] = fma(g, dz, s[2]);
-            s[3] = fma(g, ex - t3 * dx, s[3]);
-            s[4] = fma(g, ey - t3 * dy, s[4]);
-            s[5] = fma(g, ez - t3 * dz, s[5]);
+            const float4 pjh = w.pf_hi[j], pjl = w.pf_lo[j], vjh = w.vf_hi[j], vjl = w.vf_lo[j];
+            const float dx = (pih.x - pjh.x) + (pil.x - pjl.x);
+            const float dy = (pih.y - pjh.y) + (pil.y - pjl.y);
+            const float dz = (pih.z - pjh.z) + (pil.z - pjl.z);
+            const float ex = (vih.x - vjh.x) + (vil.x - vjl.x);
+            const float ey = (vih.y - vjh.y) + (vil.y - vjl.y);
+            const float ez = (vih.z - vjh.z) + (vil.z - vjl.z);
+            const float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+            const float is = rsqrt_ftz(s2), is2 = is * is;
+            const float g = -pjh.w * is * is2;   // -G m_j / s^3 (0 for a heavy body)
+            const float t3 = 3.0f * fmaf(dx, ex, fmaf(dy, ey, dz * ez)) * is2;
+            s[0] = fmaf(g, dx, s[0]);
+            s[1] = fmaf(g, dy, s[1]);
+            s[2] = fmaf(g, dz, s[2]);
+            s[3] = fmaf(g, fmaf(-t3, dx, ex), s[3]);
+            s[4] = fmaf(g, fmaf(-t3, dy, ey), s[4]);
+            s[5] = fmaf(g, fmaf(-t3, dz, ez), s[5]);
         }
+        double sd[6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) s[q] = warp_sum(s[q]);
+        for (int q = 0; q < 6; ++q) sd[q] = warp_sum((double)s[q]);
         if (lane == 0)
 #pragma unroll
-            for (int q = 0; q < 6; ++q) s_part[wp][q] = s[q];
+            for (int q = 0; q < 6; ++q) s_part[wp][q] = sd[q];
         __syncthreads();
         if (tid < 6) {
             double v = 0.0;
@@ -253,6 +278,23 @@ __global__ void __launch_bounds__(128) k_wh_correct(WholeArgs w, int startup) {
             a1[q] += p[6 * c + q];
             j1[q] += p[6 * c + 3 + q];
         }
+    // the heavy bodies' pull in FP64 (the oracle's pair term with K = 0)
+    for (int h = 0; h < w.nheavy; ++h) {
+        const int64_t j = w.heavy[h];
+        if (j == i) continue;
+        const double dx = w.xp[i] - w.xp[j], dy = w.xp[ld + i] - w.xp[ld + j];
+        const double dz = w.xp[2 * ld + i] - w.xp[2 * ld + j];
+        const double ex = w.up[i] - w.up[j], ey = w.up[ld + i] - w.up[ld + j];
+        const double ez = w.up[2 * ld + i] - w.up[2 * ld + j];
+        const double s2 = dx * dx + dy * dy + dz * dz + w.eps2;
+        const double s = sqrt(s2);
+        const double rv = dx * ex + dy * ey + dz * ez;
+        const double g = -w.G * w.m[w.r0 + 1 + j] / (s2 * s);
+        a1[0] += g * dx; a1[1] += g * dy; a1[2] += g * dz;
+        j1[0] += g * (ex - 3.0 * rv * dx / s2);
+        j1[1] += g * (ey - 3.0 * rv * dy / s2);
+        j1[2] += g * (ez - 3.0 * rv * dz / s2);
+    }
     const double T = w.T;
     if (startup) {
         for (int q = 0; q < 3; ++q) {
