@@ -131,8 +131,8 @@ MUTANTS = [
      'or_kcorr(k, members + k0, m, q0, v0, G, rcrit[st], 0.5 * tau);',
      'or_kcorr(k, members + k0, m, q0, v0, G, rcrit[st], tau);'),
     ('step_second_kick_missing', 'step',
-     '/* item 9: interaction tau/2 */\n        or_kick(rows, m, q, v, G, 0.5 * tau);',
-     '/* item 9: interaction tau/2 */'),
+     'if (!whole) or_kick(rows, m, q, v, G, 0.5 * tau);',
+     'if (!whole) (void)0;'),
     ('step_hermite_from_kepler_state', 'step',
      'q[3 * i + c] = q0[3 * i + c];\n                            v[3 * i + c] = v0[3 * i + c];',
      '(void)0;'),
