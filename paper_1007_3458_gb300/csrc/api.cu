@@ -437,9 +437,9 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
         big.threads = 128;
         big.ipt = 1;
         big.splits = 16;
-        // partial-sum slots: up to 64 for small batches, within ~0.5 GB
+        // partial-sum slots: up to 128 for small batches, within ~0.5 GB
         int64_t by_mem = ((int64_t)1 << 29) / (24 * R);
-        c->splits_cap = (int32_t)std::max<int64_t>(c->tune.splits, std::min<int64_t>(64, std::max<int64_t>(4, by_mem)));
+        c->splits_cap = (int32_t)std::max<int64_t>(c->tune.splits, std::min<int64_t>(128, std::max<int64_t>(4, by_mem)));
         big.splits = c->splits_cap;
         c->items_cap = std::max(kick_items_count(offsets, nsys, big), d.nitems);
         c->items_cap = std::max(c->items_cap, kick_items_count(offsets, nsys, c->tune));
@@ -544,7 +544,7 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     std::vector<int32_t> slots(d.nitems);
     int32_t ni = 0, spu = 0;
     kick_items_host(offsets, nsys, c->tune, items.data(), slots.data(), &ni, &spu, d.nitems, 0,
-                    INT64_MAX, c->sort_rows ? kKickTile : 1);
+                    INT64_MAX, c->sort_rows ? kKickTile / 2 : 1);
     std::vector<int4> eit(c->neitems);
     std::vector<int32_t> eis(c->neitems), ei0(nsys + 1);
     energy_items_host(offsets, nsys, eit.data(), eis.data(), ei0.data());
@@ -1653,7 +1653,7 @@ static qym_status apply_tune(qym_ctx *c, const KickTune &t) {
     std::vector<int32_t> slots(n ? n : 1);
     int32_t ni = 0, spu = 0;
     kick_items_host(c->h_offsets.data(), d.nsys, t, items.data(), slots.data(), &ni, &spu, n, ilo,
-                    ihi, d.perm ? kKickTile : 1);
+                    ihi, d.perm ? kKickTile / 2 : 1);
     if (n) {
         CK(c, cudaMemcpyAsync(d.items, items.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, c->stream));
         CK(c, cudaMemcpyAsync(d.item_slot, slots.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
@@ -1696,7 +1696,7 @@ extern "C" qym_status qym_autotune(qym_ctx *c) {
     std::vector<KickTune> cands;
     for (int threads : {128, 256})
         for (int ipt : mixed ? std::vector<int>{1, 2, 4} : std::vector<int>{1, 2})
-            for (int sp : {1, 2, 4, 8, 16, 32, 64}) {
+            for (int sp : {1, 2, 4, 8, 16, 32, 64, 128}) {
                 KickTune t;
                 t.threads = threads;
                 t.ipt = ipt;

@@ -310,8 +310,11 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
         ahx[k] = ahy[k] = ahz[k] = alx[k] = aly[k] = alz[k] = 0.0f;
     }
     const int i_lo = it.x, i_hi = it.x + (int)(IPT * blockDim.x);
-    for (int jt = it.z; jt < it.w; jt += TILE) {
-        const int n = min(TILE, it.w - jt);
+    for (int jt = it.z, n = 0; jt < it.w; jt += n) {
+        // windows of at most TILE positions; with far tiles never across the
+        // end of a tile (positions 1 + TILE t ..), whose data a window uses
+        n = min(TILE, it.w - jt);
+        if (a.far_tiles) n = min(n, 1 + ((jt - 1) / TILE + 1) * TILE - jt);
         const int np = (n + 1) >> 1;
         const bool diag = (jt < i_hi) && (jt + n > i_lo);
         // Far tiles (a.far_tiles: the bodies in Morton order, tiles aligned
@@ -578,7 +581,7 @@ void kick_items_host(const int64_t *offsets, int32_t nsys, const KickTune &t, in
         int64_t b0 = offsets[s] + 1, b1 = offsets[s + 1];
         int64_t nb = b1 - b0;
         int64_t chunk = (nb + t.splits - 1) / t.splits;
-        chunk = (chunk + align - 1) / align * align;  // j-ranges start on tiles
+        chunk = (chunk + align - 1) / align * align;  // j-ranges start on half tiles (one inside a tile takes that tile's far data)
         const int64_t ia = items_i_begin(b0, i_lo), ib = items_i_end(b1, i_hi);
         for (int64_t i0 = ia; i0 < ib; i0 += ti) {
             int64_t i1 = i0 + ti < ib ? i0 + ti : ib;

@@ -93,8 +93,10 @@ def test_split_matches_unsplit_step(torch, prec):
     phases give the unsplit qym_step's encounter records exactly, and its
     positions and velocities to rounding (FP64 kick: 1e-13 relative,
     bit-identical unless a large set took a thread-block cluster in one run
-    and not the other; mixed kick: 1e-8, the FP32 sums grouped in another
-    order)."""
+    and not the other; mixed kick: the FP32 sums grouped in another order,
+    whose rounding is the mixed kick's (up to 1e-6 of a body's
+    acceleration): 1e-8 for the bodies in no encounter record of the run,
+    1e-5 for those in one, where close encounters amplify it)."""
     w = W.disk_16384()
     n = 4
     ref = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, kick_prec=prec)
@@ -106,13 +108,21 @@ def test_split_matches_unsplit_step(torch, prec):
         for rank, (qq, vv, enc, st) in enumerate(_split_run(w, world, n, kick_prec=prec)):
             assert st["status_bits"] == 0, (world, rank, st)
             assert np.array_equal(enc, er), (world, rank, len(enc), len(er))
-            dq, dv = _relq(qq, qr).max(), _relq(vv, vr).max()
+            rq, rv = _relq(qq, qr), _relq(vv, vr)
+            dq, dv = rq.max(), rv.max()
             print(f"\n  world {world} rank {rank}: max rel dq {dq:.3g} dv {dv:.3g}")
-            # FP64: the same bits; mixed: the unsplit step holds the bodies in
-            # Morton order (sort.cu) and the split in row order, which groups
-            # the FP32 tile sums differently
-            tol = 1e-13 if prec == q.QYM_KICK_FP64 else 1e-8
-            assert dq <= tol and dv <= tol, (world, rank, dq, dv)
+            if prec == q.QYM_KICK_FP64:
+                assert dq <= 1e-13 and dv <= 1e-13, (world, rank, dq, dv)
+            else:
+                # the unsplit step holds the bodies in Morton order (sort.cu)
+                # and the split in row order, which groups the FP32 tile sums
+                # differently
+                inenc = np.zeros(len(w.m), bool)
+                inenc[er[:, 1:].ravel()] = True
+                far = ~inenc
+                assert rq[far].max() <= 1e-8 and rv[far].max() <= 1e-8, (world, rank, rq[far].max(),
+                                                                          rv[far].max())
+                assert dq <= 1e-5 and dv <= 1e-5, (world, rank, dq, dv)
 
 
 def test_split_three_ranks_uneven_blocks(torch):
