@@ -169,9 +169,10 @@ KEPLER_FP64_WARP_INST = {
 # with the splits. A shape or a kick source not captured reports null (the
 # capture commands sit with the ncu summaries under profiles/).
 KICK_DRAM_BYTES = {
-    # shape 128 threads x 2 rows x 64 splits (256 rows per CTA)
-    ("disk_16384", 256, 64, "3e97bc3c36908ece"): 9.25e5,
-    ("disk_262144", 256, 64, "3e97bc3c36908ece"): 2.30e7,
+    ("disk_16384", 256, 64, "54c6f9e4161f1bc3"): 9.16e5,
+    ("disk_16384", 256, 128, "54c6f9e4161f1bc3"): 1.18e6,
+    ("disk_262144", 256, 64, "54c6f9e4161f1bc3"): 2.31e7,
+    ("disk_262144", 512, 64, "54c6f9e4161f1bc3"): 1.82e7,
 }
 
 
@@ -541,7 +542,7 @@ def run_ours(args):
               "auto": q.QYM_SEARCH_AUTO}[args.search]
     sim = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=prec, device=dev,
                        l2_flush_bytes=256 << 20, eps_H=w.eps_H, merge_kicks=args.merge_kicks,
-                       search=search)
+                       search=search, hermite_cluster=args.hermite_cluster)
     if args.shape:
         q.qym_set_kick_shape(sim.ctx, *[int(x) for x in args.shape.split(",")])
     elif args.autotune:
@@ -1031,6 +1032,8 @@ def main():
                     help="kepler_1m: also time the other solvers and guesses")
     ap.add_argument("--solver", default="newton32", choices=["newton", "newton32", "laguerre"],
                     help="kepler_1m: Kepler solver (newton32: FP32 Newton steps, then FP64 Laguerre)")
+    ap.add_argument("--hermite-cluster", type=int, default=0, choices=[0, 2, 4, 8],
+                    help="CTAs per cluster for the large encounter sets (0: the library's choice)")
     ap.add_argument("--merge-kicks", type=int, default=0,
                     help="1: one kick of tau between steps (exact rewrite of the paper's two)")
     ap.add_argument("--merged-too", type=int, default=1,
