@@ -430,3 +430,20 @@ def test_repeat_runs_bit_identical(gpu, case):
     assert np.array_equal(q0, q1) and np.array_equal(v0, v1)
     assert np.array_equal(e0, e1)
     assert s0["hermite_steps"] == s1["hermite_steps"] and s0["sets"] == s1["sets"]
+
+
+def test_newton32_step_matches_laguerre(gpu, oracle):
+    """The hybrid step with E_Kep by FP32 Newton steps finished in FP64
+    (QYM_SOLVER_NEWTON32) against the paper's Laguerre: both stop at the same
+    1e-14 residual, so 100 steps of the 260-body disk (FP64 kick) end with
+    the same records and positions within the chaos-aware tolerance of the
+    oracle's Laguerre run."""
+    w = W.disk_260()
+    n = 100
+    qg, vg, enc, st, E = _run_gpu(w, n, kick_prec=q.QYM_KICK_FP64, eps_H=w.eps_H,
+                                  solver=q.QYM_SOLVER_NEWTON32)
+    assert st["status_bits"] == 0
+    r, vh = _run_oracle(oracle, w, n, eps_H=w.eps_H)
+    skip = _compare_records(enc, r)
+    keep = np.array([i not in skip for i in range(len(w.m))])
+    _check_positions(qg[keep], r.q[keep], _chaos_spread(oracle, w, n, eps_H=w.eps_H)[keep])
