@@ -217,6 +217,16 @@ qym_status qym_set_state(qym_ctx *ctx, const double *q, const double *v);
  * found (which may exceed cap; only cap records are written). */
 qym_status qym_get_encounters(qym_ctx *ctx, int64_t *recs, int64_t cap, int64_t *count);
 
+/* Copy the order in which the kick holds the bodies' operand packs to host
+ * int32 order[rows]: position p holds row order[p]. A single system of at
+ * least 2048 bodies with the mixed kick is held along a Morton curve of its
+ * positions (ordered by (code, row); taken at qym_set_state, at the start of
+ * every qym_step call and every 32 steps within one; the star row stays at
+ * 0); otherwise the order is the identity. Results depend on it only through
+ * the grouping of the FP32 sums of the single-precision interaction step
+ * (Sec. 2). */
+qym_status qym_get_order(qym_ctx *ctx, int32_t *order);
+
 /* Total energy H_Dft + H_Kep + H_Int of each system (Sec. 2, Eqs. 2-4, star
  * mass restored for the pair sum), FP64, into host double E[nsys]. */
 qym_status qym_energy(qym_ctx *ctx, double *E);

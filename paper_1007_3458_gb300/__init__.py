@@ -100,6 +100,7 @@ def lib():
     L.qym_set_state.argtypes = [P, D, D]
     L.qym_get_encounters.argtypes = [P, I64, C.c_int64, I64]
     L.qym_energy.argtypes = [P, D]
+    L.qym_get_order.argtypes = [P, C.POINTER(C.c_int32)]
     L.qym_get_stats.argtypes = [P, C.POINTER(qym_stats)]
     L.qym_get_params.argtypes = [P, C.POINTER(qym_params)]
     L.qym_set_mlp.argtypes = [P, C.POINTER(C.c_float), C.c_int64]
@@ -150,7 +151,7 @@ def lib():
     L.qym_energy_workspace_bytes.restype = C.c_size_t
     L.qym_energy_dev.argtypes = [C.c_int64, P, P, P, C.c_double, P, P, C.c_size_t, P]
     for name in ("qym_default_params", "qym_init", "qym_step", "qym_get_state", "qym_set_state",
-                 "qym_get_encounters", "qym_energy", "qym_get_stats", "qym_get_params",
+                 "qym_get_encounters", "qym_get_order", "qym_energy", "qym_get_stats", "qym_get_params",
                  "qym_set_mlp", "qym_shape",
                  "qym_get_stream", "qym_time_kick", "qym_autotune", "qym_set_kick_shape",
                  "qym_kepler_drift_dev", "qym_accel_dev", "qym_encounter_test_dev",
@@ -264,6 +265,14 @@ def qym_get_encounters(ctx):
     out = np.zeros((max(cnt.value, 1), 3), dtype=np.int64)
     _check(lib().qym_get_encounters(ctx, out.ctypes.data_as(I64), cnt.value, C.byref(cnt)), ctx)
     return out[:cnt.value]
+
+
+def qym_get_order(ctx):
+    """The kick's body order, int32 [rows]: position p holds row order[p]."""
+    rows, _ = qym_shape(ctx)
+    out = np.zeros(rows, dtype=np.int32)
+    _check(lib().qym_get_order(ctx, out.ctypes.data_as(C.POINTER(C.c_int32))), ctx)
+    return out
 
 
 def qym_energy(ctx):
@@ -446,6 +455,9 @@ class Simulation:
 
     def energy(self):
         return qym_energy(self.ctx)
+
+    def order(self):
+        return qym_get_order(self.ctx)
 
     def stats(self):
         return qym_get_stats(self.ctx).as_dict()

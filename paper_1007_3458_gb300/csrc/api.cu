@@ -43,9 +43,10 @@ struct qym_ctx {
     void *flush = nullptr; // L2 flush buffer (params.l2_flush_bytes)
     SetScratch ss;
     bool amag_valid = false;
-    // graph of one interior step
-    cudaGraphExec_t gexec = nullptr;
-    double g_tau = 0.0;
+    // graphs of one interior step and of a call's closing step
+    cudaGraphExec_t gexec = nullptr, gexec_last = nullptr;
+    double g_tau = 0.0, g_tau_last = 0.0;
+    int64_t graph_launches_last = 0;
     qym_stats stats;
     std::string err;
     int32_t status_bits = 0;
@@ -192,6 +193,14 @@ struct Carver {
 
 static void choose_slot_sums(qym_ctx *c);
 
+// the captured steps, dropped whenever what they hold by value changes (the
+// launch shape, the log and snapshot pointers, tau)
+static void drop_graphs(qym_ctx *c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->gexec_last) cudaGraphExecDestroy(c->gexec_last);
+    c->gexec = c->gexec_last = nullptr;
+}
+
 static void carve_all(qym_ctx *c, Carver &k) {
     Dev &d = c->d;
     const int64_t R = d.rows;
@@ -312,14 +321,20 @@ static void carve_all(qym_ctx *c, Carver &k) {
 // The caller's rows [R][3] <-> the device's [3][R]. The transposes run on the
 // device, so a pinned host buffer goes to and from the GPU in one DMA each;
 // between steps the kick's partial sums are idle and stage the rows.
+// host rows [R][3] -> [3][R] with star rows zero; `bit` set in *bad for a
+// non-finite value, and with `cur` (the state held now, [3][R]) `cbit` set
+// when some value differs from it bit for bit
 __global__ void k_soa_from_aos(int64_t R, const double *aos, double *soa, const int64_t *offsets,
-                               const int32_t *sys_of, int32_t *bad, int32_t bit) {
+                               const int32_t *sys_of, int32_t *bad, int32_t bit,
+                               const double *cur = nullptr, int32_t cbit = 0) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     const bool star = offsets[sys_of[r]] == r;  // star rows are held at zero
     for (int c = 0; c < 3; ++c) {
         const double x = star ? 0.0 : aos[3 * r + c];
         if (!isfinite(x)) atomicOr(bad, bit);
+        if (cur && __double_as_longlong(x) != __double_as_longlong(cur[c * R + r]))
+            atomicOr(bad, cbit);
         soa[c * R + r] = x;
     }
 }
@@ -361,12 +376,12 @@ static qym_status upload_state(qym_ctx *c, const double *q, const double *v) {
     CK(c, cudaMemcpyAsync(sq, q, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, st));
     CK(c, cudaMemcpyAsync(sv, v, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, st));
     CK(c, cudaMemsetAsync(c->hflag, 0, sizeof(int32_t), st));
-    k_soa_from_aos<<<g, 256, 0, st>>>(R, sq, d.q1, d.offsets, d.sys_of, c->hflag, 1);
+    k_soa_from_aos<<<g, 256, 0, st>>>(R, sq, d.q1, d.offsets, d.sys_of, c->hflag, 1, d.q, 4);
     k_soa_from_aos<<<g, 256, 0, st>>>(R, sv, d.v1, d.offsets, d.sys_of, c->hflag, 2);
     CK(c, cudaGetLastError());
     int32_t bad = 0;
     CK(c, cudaMemcpyAsync(&bad, c->hflag, sizeof(bad), cudaMemcpyDeviceToHost, st));
-    CK(c, cudaStreamSynchronize(st));
+    CK(c, cudaStreamSynchronize(st));  // (the host arrays are free from here on)
     if (bad & 1) FAIL(c, QYM_EINVAL, "non-finite position");
     if (bad & 2) FAIL(c, QYM_EINVAL, "non-finite velocity");
     CK(c, cudaMemcpyAsync(d.q, d.q1, sizeof(double) * 3 * R, cudaMemcpyDeviceToDevice, st));
@@ -375,8 +390,12 @@ static qym_status upload_state(qym_ctx *c, const double *q, const double *v) {
     if (c->p.hill_fixed) CK(c, launch_hill_init(d, c->p.G, st));
     if (d.perm) CK(c, launch_sort_rows(d.rows, d.q, c->sortw, d.perm, d.inv, st));
     c->sort_current = d.perm != nullptr;
-    CK(c, cudaStreamSynchronize(st));
-    c->amag_valid = false;
+    // The |a| of the last kick bounds the coming kick's (the crude search's
+    // allowance) only at the same separations: kept when every position is
+    // the one held before, bit for bit (a state read back and set again), so
+    // that the next step fuses its search into the kick; any other state
+    // makes that step search after its kick.
+    if (bad & 4) c->amag_valid = false;
     return QYM_OK;
 }
 
@@ -590,7 +609,7 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
 
 extern "C" void qym_destroy(qym_ctx *c) {
     if (!c) return;
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    drop_graphs(c);
     if (c->stream) {
         cudaStreamSynchronize(c->stream);
         cudaStreamDestroy(c->stream);
@@ -1033,7 +1052,32 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
                 CK(c, p.merge_kicks ? enqueue_unit(c, tau, false) : enqueue_step(c, tau, false));
         }
     }
-    CK(c, p.merge_kicks ? enqueue_unit(c, tau, true) : enqueue_step(c, tau, true));
+    // the closing step (or unit) of the call, replayed from its own graph
+    if (c->gexec_last && c->g_tau_last != tau) {
+        cudaGraphExecDestroy(c->gexec_last);
+        c->gexec_last = nullptr;
+    }
+    if (!c->gexec_last && !p.whole_hermite) {
+        cudaGraph_t g;
+        CK(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int64_t before = c->launches;
+        cudaError_t e = p.merge_kicks ? enqueue_unit(c, tau, true) : enqueue_step(c, tau, true);
+        c->graph_launches_last = c->launches - before;
+        c->launches = before;
+        cudaError_t e2 = cudaStreamEndCapture(st, &g);
+        if (e != cudaSuccess) FAIL(c, QYM_ECUDA, std::string("step capture: ") + cudaGetErrorString(e));
+        if (e2 != cudaSuccess) FAIL(c, QYM_ECUDA, std::string("end capture: ") + cudaGetErrorString(e2));
+        e = cudaGraphInstantiate(&c->gexec_last, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) FAIL(c, QYM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        c->g_tau_last = tau;
+    }
+    if (c->gexec_last) {
+        CK(c, cudaGraphLaunch(c->gexec_last, st));
+        c->launches += c->graph_launches_last;
+    } else {
+        CK(c, p.merge_kicks ? enqueue_unit(c, tau, true) : enqueue_step(c, tau, true));
+    }
     if (c->klog) c->klog_steps += (unsigned long long)nsteps;
     return collect(c, nsteps);
 }
@@ -1069,6 +1113,19 @@ extern "C" qym_status qym_get_state(qym_ctx *c, double *q, double *v) {
 extern "C" qym_status qym_set_state(qym_ctx *c, const double *q, const double *v) {
     if (!c || !q || !v) FAIL(c, QYM_EINVAL, "qym_set_state: NULL argument");
     return upload_state(c, q, v);
+}
+
+extern "C" qym_status qym_get_order(qym_ctx *c, int32_t *order) {
+    if (!c || !order) FAIL(c, QYM_EINVAL, "qym_get_order: NULL argument");
+    Dev &d = c->d;
+    if (d.perm) {
+        CK(c, cudaMemcpyAsync(order, d.perm, sizeof(int32_t) * d.rows, cudaMemcpyDeviceToHost,
+                              c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    } else {
+        for (int64_t r = 0; r < d.rows; ++r) order[r] = (int32_t)r;
+    }
+    return QYM_OK;
 }
 
 extern "C" qym_status qym_energy(qym_ctx *c, double *E) {
@@ -1149,11 +1206,7 @@ extern "C" qym_status qym_set_kepler_log(qym_ctx *c, float *rows, int64_t cap) {
     c->klog = cap > 0 ? rows : nullptr;
     c->klog_cap = cap;
     c->klog_steps = 0;
-    // the step graph holds the log pointers: capture again
-    if (c->gexec) {
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
-    }
+    drop_graphs(c);  // the step graphs hold the log pointers: capture again
     return QYM_OK;
 }
 
@@ -1407,6 +1460,7 @@ extern "C" qym_status qym_set_encounter_snapshot(qym_ctx *c, double *q0, double 
     for (int k = 0; k < 5; ++k) n += in[k] != nullptr;
     if (n != 0 && n != 5) FAIL(c, QYM_EINVAL, "qym_set_encounter_snapshot: all five arrays or none");
     for (int k = 0; k < 5; ++k) c->snap[k] = in[k];
+    drop_graphs(c);  // the closing step's graph holds the snapshot copies
     return QYM_OK;
 }
 
@@ -1663,10 +1717,7 @@ static qym_status apply_tune(qym_ctx *c, const KickTune &t) {
     d.splits = t.splits;
     choose_slot_sums(c);
     c->tune = t;
-    if (c->gexec) {  // the captured step holds the old shape
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
-    }
+    drop_graphs(c);  // the captured steps hold the old shape
     return QYM_OK;
 }
 

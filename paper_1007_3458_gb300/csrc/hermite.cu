@@ -142,6 +142,12 @@ constexpr int CLMAX = 8;
 #define QYM_HERM_NBIG 24
 #endif
 constexpr int NBIG = QYM_HERM_NBIG;  // sets of at least this many members use a whole cluster
+#ifndef QYM_HERM_F32MIN
+#define QYM_HERM_F32MIN 64
+#endif
+// partners of a CTA plus active members above which the FP32 prediction
+// screens the partners before the FP64 one
+constexpr int F32MIN = QYM_HERM_F32MIN;
 constexpr int ACH = 64;    // active members per force round (exchange, correction)
 constexpr int RSL = 16;    // members per force round on a cluster (receive buffer slots)
 
@@ -727,7 +733,7 @@ __device__ __noinline__ void hermite_set(const Dev &d, const HermArgs h, int set
         // warps' worth, FP64 passes over them all (one warp per coordinate);
         // above that the FP32 prediction first rules out the partners that are
         // surely beyond r_crit of every active member.
-        const bool f32 = npmax + na > 64;
+        const bool f32 = npmax + na > F32MIN;
         if (!f32) {
             if (warp < 3) {
                 for (int i = wl; i < npart + na; i += 32) {

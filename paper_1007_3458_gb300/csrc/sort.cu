@@ -6,9 +6,13 @@
 // and results depend on it only through the grouping of the FP32 tile sums.
 //
 // Keys: 10 bits per axis of the position scaled into the cube over the
-// system's bounding box, interleaved into 30 bits. Sort: stable least-significant-digit radix
-// sort of (key, row) over four 8-bit digits; deterministic (per-block digit
-// counts, a scan, and ranks within a block from warp match masks).
+// system's bounding box, interleaved into 30 bits; bodies ordered by (key,
+// row). Sort: stable least-significant-digit radix sort of (key, row) over
+// four 8-bit digits; deterministic (per-block digit counts, a scan, and ranks
+// within a block from warp match masks). (A bitonic sort of the 64-bit words
+// (key, row) in one CTA's shared memory took 0.16 ms for 16384 bodies, against
+// about 0.04 ms for these 16 launches: each of its 105 stages moves every word
+// through shared memory.)
 #include <algorithm>
 #include <utility>
 
@@ -60,11 +64,9 @@ __device__ __forceinline__ uint32_t spread10(uint32_t x) {
     return x;
 }
 
-__global__ void __launch_bounds__(256) k_sort_keys(int64_t rows, const double *q, const int *box,
-                                                    uint32_t *keys, int32_t *vals) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // body k = row k + 1
-    if (k >= rows - 1) return;
-    const int64_t r = k + 1;
+// Morton code of row r from the box (min, -max per axis, as fkey images)
+__device__ __forceinline__ uint32_t morton_code(int64_t rows, const double *q, int64_t r,
+                                                const int *box) {
     // one scale for the three axes (cubic cells): a thin disk then orders by
     // its plane first instead of splitting its few bodies' heights at the top
     float span = 0.0f;
@@ -77,7 +79,14 @@ __global__ void __launch_bounds__(256) k_sort_keys(int64_t rows, const double *q
         const uint32_t b = min((uint32_t)(u * 1024.0f), 1023u);
         code |= spread10(b) << c;
     }
-    keys[k] = code;
+    return code;
+}
+__global__ void __launch_bounds__(256) k_sort_keys(int64_t rows, const double *q, const int *box,
+                                                    uint32_t *keys, int32_t *vals) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // body k = row k + 1
+    if (k >= rows - 1) return;
+    const int64_t r = k + 1;
+    keys[k] = morton_code(rows, q, r, box);
     vals[k] = (int32_t)r;
 }
 

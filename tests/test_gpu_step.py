@@ -313,6 +313,36 @@ def test_state_round_trip_and_resume(gpu, oracle):
     assert _relq(qb, qa).max() <= 1e-13
 
 
+def test_set_state_of_the_held_positions_keeps_the_fused_search(gpu):
+    """A state read back and set again (positions bit for bit) leaves the
+    next step on the fused search (the last kick's |a| still bounds it): the
+    same encounter records and state as a run without the round trip, and
+    two launches fewer than after a state with one position moved, which
+    searches after its kick (the stirred disk of crossers: encounters from
+    the first step on)."""
+    w = W.crossers()
+
+    def run(edit):
+        s = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H)
+        s.step(w.tau, 2)
+        if edit is not None:
+            qs, vs = s.state()
+            edit(qs)
+            s.set_state(qs, vs)
+        s.step(w.tau, 3)
+        out = s.state(), s.encounters(), s.stats()
+        s.close()
+        return out
+
+    (qa, va), ea, _ = run(None)
+    (qb, vb), eb, sb = run(lambda x: None)
+    (qc, vc), ec, sc = run(lambda x: x.__setitem__((7, 0), x[7, 0] * (1 + 1e-15)))
+    assert sb["status_bits"] == 0 and sc["status_bits"] == 0
+    assert np.array_equal(eb, ea) and _relq(qb, qa).max() <= 1e-13
+    assert sc["launches"] == sb["launches"] + 2 and sc["rescans"] == 0
+    assert sb["encounters"] > 0
+
+
 def test_error_statuses(gpu):
     """Capacities and caps report statuses; the context stays usable."""
     w = W.disk_260()
