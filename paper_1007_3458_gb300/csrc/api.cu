@@ -27,6 +27,14 @@ namespace qym {
 void set_thread_error(const std::string &msg) { g_err = msg; }
 }  // namespace qym
 
+// A piece of a step call captured as a CUDA graph for the tau it was taken
+// with, and the kernels one replay launches
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    double tau = 0.0;
+    int64_t launches = 0;
+};
+
 struct qym_ctx {
     qym_params p;
     cudaStream_t stream = nullptr;
@@ -43,10 +51,9 @@ struct qym_ctx {
     void *flush = nullptr; // L2 flush buffer (params.l2_flush_bytes)
     SetScratch ss;
     bool amag_valid = false;
-    // graphs of one interior step and of a call's closing step
-    cudaGraphExec_t gexec = nullptr, gexec_last = nullptr;
-    double g_tau = 0.0, g_tau_last = 0.0;
-    int64_t graph_launches_last = 0;
+    // captured pieces of a call: an interior step, the closing step, the
+    // call's opening (counters, [Morton order,] drift) with and without the sort
+    StepGraph g_step, g_last, g_open[2];
     qym_stats stats;
     std::string err;
     int32_t status_bits = 0;
@@ -54,7 +61,6 @@ struct qym_ctx {
     int32_t *kick_cnt = nullptr;            // per i-block arrival counters of the kick
     int64_t n_heavy = 0;    // heavy bodies over all systems
     int64_t launches = 0;   // kernels enqueued by the current qym_step call
-    int64_t graph_launches = 0;  // kernels in one replay of the step graph
     // learned Kepler guess and the log of Kepler solves
     float *mlp_w = nullptr;      // [QYM_MLP_NW] device weights (arena)
     bool mlp_set = false;
@@ -195,10 +201,48 @@ static void choose_slot_sums(qym_ctx *c);
 
 // the captured steps, dropped whenever what they hold by value changes (the
 // launch shape, the log and snapshot pointers, tau)
+static void drop_graph(StepGraph &g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+}
 static void drop_graphs(qym_ctx *c) {
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    if (c->gexec_last) cudaGraphExecDestroy(c->gexec_last);
-    c->gexec = c->gexec_last = nullptr;
+    drop_graph(c->g_step);
+    drop_graph(c->g_last);
+    drop_graph(c->g_open[0]);
+    drop_graph(c->g_open[1]);
+}
+
+// Replay g, capturing it first from `enqueue` (which counts its launches in
+// c->launches) when it is missing or was taken with another tau.
+template <class F>
+static cudaError_t replay(qym_ctx *c, StepGraph &g, double tau, F &&enqueue) {
+    cudaStream_t st = c->stream;
+    if (g.exec && g.tau != tau) drop_graph(g);
+    cudaError_t e;
+    if (!g.exec) {
+        cudaGraph_t gr;
+        if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal))) return e;
+        const int64_t before = c->launches;
+        e = enqueue();
+        g.launches = c->launches - before;
+        c->launches = before;
+        const cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+        if (e != cudaSuccess) {
+            if (e2 == cudaSuccess) cudaGraphDestroy(gr);
+            return e;
+        }
+        if (e2 != cudaSuccess) return e2;
+        e = cudaGraphInstantiate(&g.exec, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) {
+            g.exec = nullptr;
+            return e;
+        }
+        g.tau = tau;
+    }
+    if ((e = cudaGraphLaunch(g.exec, st))) return e;
+    c->launches += g.launches;
+    return cudaSuccess;
 }
 
 static void carve_all(qym_ctx *c, Carver &k) {
@@ -974,9 +1018,9 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
     const qym_params &p = c->p;
     cudaStream_t st = c->stream;
     CK(c, cudaSetDevice(p.device));
-    CK(c, cudaMemsetAsync(d.ctr, 0, sizeof(unsigned long long) * C_COUNT, st));
-    CK(c, cudaMemsetAsync(d.status, 0, sizeof(int32_t), st));
     if (nsteps == 0) {
+        CK(c, cudaMemsetAsync(d.ctr, 0, sizeof(unsigned long long) * C_COUNT, st));
+        CK(c, cudaMemsetAsync(d.status, 0, sizeof(int32_t), st));
         std::memset(&c->stats, 0, sizeof(c->stats));
         return QYM_OK;
     }
@@ -987,21 +1031,30 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
                               cudaMemcpyHostToDevice, st));
     c->launches = 0;
     c->wh_steps = c->wh_hsteps = c->wh_hmax = 0;
-    if (d.perm && !c->sort_current) {
-        // the kick's order from the positions at the start of the call (unless
-        // set_state has just taken it)
-        CK(c, launch_sort_rows(d.rows, d.q, c->sortw, d.perm, d.inv, st));
-        c->launches += 16;
-    }
+    // the kick's order from the positions at the start of the call (unless
+    // set_state has just taken it)
+    const bool sort = d.perm && !c->sort_current;
     c->sort_current = false;
     // without the |a| of an earlier kick the first search runs after its kick
     const bool fresh = !c->amag_valid;
     c->amag_valid = true;  // every kick's finisher records |a|
-    // item 1 of the first step: drift tau/2
-    CK(c, launch_momentum(d, st));
-    CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.5 * tau, tau, p.a_E, p.G,
-                                 fused_search(c) && !fresh, p.hill_fixed, st, 0.5 * tau));
-    c->launches += 3;
+    // the call's counters, the order, and item 1 of the first step: drift tau/2
+    auto opening = [&]() -> cudaError_t {
+        cudaError_t e;
+        if ((e = cudaMemsetAsync(d.ctr, 0, sizeof(unsigned long long) * C_COUNT, st))) return e;
+        if ((e = cudaMemsetAsync(d.status, 0, sizeof(int32_t), st))) return e;
+        if (sort) {
+            if ((e = launch_sort_rows(d.rows, d.q, c->sortw, d.perm, d.inv, st))) return e;
+            c->launches += 16;
+        }
+        if ((e = launch_momentum(d, st))) return e;
+        if ((e = launch_drift_pack_from(d, d.q, d.v, 0.0, 0.5 * tau, tau, p.a_E, p.G,
+                                        fused_search(c) && !fresh, p.hill_fixed, st, 0.5 * tau)))
+            return e;
+        c->launches += 3;
+        return cudaSuccess;
+    };
+    CK(c, fresh ? opening() : replay(c, c->g_open[sort ? 1 : 0], tau, opening));
     int64_t rest = nsteps;  // steps (or merged units) still to enqueue
     if (p.merge_kicks) {
         CK(c, enqueue_opening_kick(c, tau, fresh));
@@ -1013,71 +1066,31 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
         }
     }
     const int64_t interior = rest - 1;
-    if (interior > 0) {
-        if (c->gexec && c->g_tau != tau) {
-            cudaGraphExecDestroy(c->gexec);
-            c->gexec = nullptr;
+    auto one = [&]() -> cudaError_t {
+        return p.merge_kicks ? enqueue_unit(c, tau, false) : enqueue_step(c, tau, false);
+    };
+    // (a whole-system Hermite reads the sets back mid-step: no graph; a lone
+    // interior step is not worth a capture)
+    const bool graphs = !p.whole_hermite;
+    for (int64_t k = 0; k < interior; ++k) {
+        if (d.perm && k > 0 && k % kSortEvery == 0) {
+            // re-sort between steps and lay the packs of the coming kick out
+            // again in the new order (the same values: no drift)
+            CK(c, launch_sort_rows(d.rows, d.q, c->sortw, d.perm, d.inv, st));
+            CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.0, tau, p.a_E, p.G,
+                                         fused_search(c), p.hill_fixed, st,
+                                         p.merge_kicks ? tau : 0.5 * tau,
+                                         p.merge_kicks ? 2.0 : 1.01));
+            c->launches += 17;
         }
-        // (a whole-system Hermite reads the sets back mid-step: no graph)
-        if (!c->gexec && interior >= 2 && !p.whole_hermite) {
-            cudaGraph_t g;
-            CK(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            int64_t before = c->launches;
-            cudaError_t e = p.merge_kicks ? enqueue_unit(c, tau, false) : enqueue_step(c, tau, false);
-            c->graph_launches = c->launches - before;
-            c->launches = before;
-            cudaError_t e2 = cudaStreamEndCapture(st, &g);
-            if (e != cudaSuccess) FAIL(c, QYM_ECUDA, std::string("step capture: ") + cudaGetErrorString(e));
-            if (e2 != cudaSuccess) FAIL(c, QYM_ECUDA, std::string("end capture: ") + cudaGetErrorString(e2));
-            e = cudaGraphInstantiate(&c->gexec, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) FAIL(c, QYM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-            c->g_tau = tau;
-        }
-        for (int64_t k = 0; k < interior; ++k) {
-            if (d.perm && k > 0 && k % kSortEvery == 0) {
-                // re-sort between steps and lay the packs of the coming kick out
-                // again in the new order (the same values: no drift)
-                CK(c, launch_sort_rows(d.rows, d.q, c->sortw, d.perm, d.inv, st));
-                CK(c, launch_drift_pack_from(d, d.q, d.v, 0.0, 0.0, tau, p.a_E, p.G,
-                                             fused_search(c), p.hill_fixed, st,
-                                             p.merge_kicks ? tau : 0.5 * tau,
-                                             p.merge_kicks ? 2.0 : 1.01));
-                c->launches += 17;
-            }
-            if (c->gexec) {
-                CK(c, cudaGraphLaunch(c->gexec, st));
-                c->launches += c->graph_launches;
-            } else
-                CK(c, p.merge_kicks ? enqueue_unit(c, tau, false) : enqueue_step(c, tau, false));
-        }
+        if (graphs && (interior >= 2 || c->g_step.exec)) CK(c, replay(c, c->g_step, tau, one));
+        else CK(c, one());
     }
-    // the closing step (or unit) of the call, replayed from its own graph
-    if (c->gexec_last && c->g_tau_last != tau) {
-        cudaGraphExecDestroy(c->gexec_last);
-        c->gexec_last = nullptr;
-    }
-    if (!c->gexec_last && !p.whole_hermite) {
-        cudaGraph_t g;
-        CK(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        int64_t before = c->launches;
-        cudaError_t e = p.merge_kicks ? enqueue_unit(c, tau, true) : enqueue_step(c, tau, true);
-        c->graph_launches_last = c->launches - before;
-        c->launches = before;
-        cudaError_t e2 = cudaStreamEndCapture(st, &g);
-        if (e != cudaSuccess) FAIL(c, QYM_ECUDA, std::string("step capture: ") + cudaGetErrorString(e));
-        if (e2 != cudaSuccess) FAIL(c, QYM_ECUDA, std::string("end capture: ") + cudaGetErrorString(e2));
-        e = cudaGraphInstantiate(&c->gexec_last, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) FAIL(c, QYM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-        c->g_tau_last = tau;
-    }
-    if (c->gexec_last) {
-        CK(c, cudaGraphLaunch(c->gexec_last, st));
-        c->launches += c->graph_launches_last;
-    } else {
-        CK(c, p.merge_kicks ? enqueue_unit(c, tau, true) : enqueue_step(c, tau, true));
-    }
+    // the closing step (or unit) of the call
+    auto last = [&]() -> cudaError_t {
+        return p.merge_kicks ? enqueue_unit(c, tau, true) : enqueue_step(c, tau, true);
+    };
+    CK(c, graphs ? replay(c, c->g_last, tau, last) : last());
     if (c->klog) c->klog_steps += (unsigned long long)nsteps;
     return collect(c, nsteps);
 }
