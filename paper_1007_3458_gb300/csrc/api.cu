@@ -54,6 +54,7 @@ struct qym_ctx {
     // captured pieces of a call: an interior step, the closing step, the
     // call's opening (counters, [Morton order,] drift) with and without the sort
     StepGraph g_step, g_last, g_open[2];
+    StepGraph g_upload;  // qym_set_state after its check: the state in, converted, ordered
     qym_stats stats;
     std::string err;
     int32_t status_bits = 0;
@@ -210,6 +211,7 @@ static void drop_graphs(qym_ctx *c) {
     drop_graph(c->g_last);
     drop_graph(c->g_open[0]);
     drop_graph(c->g_open[1]);
+    drop_graph(c->g_upload);
 }
 
 // Replay g, capturing it first from `enqueue` (which counts its launches in
@@ -428,11 +430,20 @@ static qym_status upload_state(qym_ctx *c, const double *q, const double *v) {
     CK(c, cudaStreamSynchronize(st));  // (the host arrays are free from here on)
     if (bad & 1) FAIL(c, QYM_EINVAL, "non-finite position");
     if (bad & 2) FAIL(c, QYM_EINVAL, "non-finite velocity");
-    CK(c, cudaMemcpyAsync(d.q, d.q1, sizeof(double) * 3 * R, cudaMemcpyDeviceToDevice, st));
-    CK(c, cudaMemcpyAsync(d.v, d.v1, sizeof(double) * 3 * R, cudaMemcpyDeviceToDevice, st));
-    if (c->p.coords == 0) CK(c, launch_to_dh_impl(d, 0, nullptr, c->mt, st));
-    if (c->p.hill_fixed) CK(c, launch_hill_init(d, c->p.G, st));
-    if (d.perm) CK(c, launch_sort_rows(d.rows, d.q, c->sortw, d.perm, d.inv, st));
+    auto commit = [&]() -> cudaError_t {
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(d.q, d.q1, sizeof(double) * 3 * R, cudaMemcpyDeviceToDevice, st)))
+            return e;
+        if ((e = cudaMemcpyAsync(d.v, d.v1, sizeof(double) * 3 * R, cudaMemcpyDeviceToDevice, st)))
+            return e;
+        if (c->p.coords == 0 && (e = launch_to_dh_impl(d, 0, nullptr, c->mt, st))) return e;
+        if (c->p.hill_fixed && (e = launch_hill_init(d, c->p.G, st))) return e;
+        if (d.perm && (e = launch_sort_rows(d.rows, d.q, c->sortw, d.perm, d.inv, st))) return e;
+        return cudaSuccess;
+    };
+    const int64_t launches = c->launches;  // (the last step call's count stays)
+    CK(c, replay(c, c->g_upload, 1.0, commit));
+    c->launches = launches;
     c->sort_current = d.perm != nullptr;
     // The |a| of the last kick bounds the coming kick's (the crude search's
     // allowance) only at the same separations: kept when every position is
