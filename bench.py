@@ -157,8 +157,8 @@ class ClockSampler:
 # particles (ncu sm__inst_executed_pipe_fp64.sum), per (solver, guess, source
 # digest of kepler.cu + mlp.cuh)
 KEPLER_FP64_WARP_INST = {
-    ("newton32", "standard", "0b39927b0f9b323f"): 12912141,
-    ("newton", "standard", "0b39927b0f9b323f"): 23561161,
+    ("newton32", "standard", "52815e32767a71e8"): 12070789,
+    ("newton", "standard", "52815e32767a71e8"): 23102409,
 }
 
 # DRAM bytes (read + written) per launch of the mixed kick, from one ncu

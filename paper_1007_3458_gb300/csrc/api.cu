@@ -274,6 +274,7 @@ static void carve_all(qym_ctx *c, Carver &k) {
     d.heavy_rows = k.take<int32_t>(c->n_heavy);
     d.heavy_start = k.take<int32_t>(d.nsys + 1);
     d.heavy_thr = k.take<double>(d.nsys);
+    d.kmu = k.take<double>(3 * (size_t)d.nsys);
     d.cand = k.take<int2>(d.max_cand);
     d.fchunk = k.take<int4>(d.max_fchunk);
     d.enc = k.take<int2>(d.max_enc);
@@ -559,6 +560,14 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     }
     hstart[nsys] = (int32_t)hrows.size();
     c->n_heavy = (int64_t)hrows.size();
+    // E_Kep's mu = G m0 per system with sqrt(mu) and 1/mu (IEEE, as on the device)
+    std::vector<double> kmu(3 * (size_t)nsys);
+    for (int32_t s = 0; s < nsys; ++s) {
+        const double mu = params->G * m[offsets[s]];
+        kmu[3 * s] = mu;
+        kmu[3 * s + 1] = std::sqrt(mu);
+        kmu[3 * s + 2] = 1.0 / mu;
+    }
     d.heavy_split = split ? 1 : 0;
 
     // one system of at least two tiles' worth of bodies, mixed kick: the kick
@@ -639,6 +648,7 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
         CKI(cudaMemcpyAsync(d.heavy_rows, hrows.data(), sizeof(int32_t) * hrows.size(), cudaMemcpyHostToDevice, c->stream));
     CKI(cudaMemcpyAsync(d.heavy_start, hstart.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, c->stream));
     CKI(cudaMemcpyAsync(d.heavy_thr, hthr.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, c->stream));
+    CKI(cudaMemcpyAsync(d.kmu, kmu.data(), sizeof(double) * 3 * nsys, cudaMemcpyHostToDevice, c->stream));
     if (c->binned && c->nstiles) {
         std::vector<int32_t> t0(nsys);
         for (size_t t = stiles.size(); t-- > 0;) t0[stiles[t].x] = (int32_t)t;
@@ -731,9 +741,7 @@ static KeplerArgs step_kepler_args(qym_ctx *c, double tau) {
     ka.status = d.status;
     ka.iter_sum = d.ctr + C_SUM_KITER;
     ka.sys_of = d.sys_of;
-    ka.offsets = d.offsets;
-    ka.m = d.m;
-    ka.G = p.G;
+    ka.kmu = d.kmu;
     return ka;
 }
 
@@ -1515,6 +1523,8 @@ extern "C" qym_status qym_kepler_drift_dev(int64_t n, const double *q0, const do
     a.q0 = q0; a.v0 = v0; a.q1 = q1; a.v1 = v1;
     a.ld = n;
     a.mu = mu;
+    a.sqmu = std::sqrt(mu);
+    a.imu = 1.0 / mu;
     a.dt = dt;
     a.solver = solver;
     a.guess = guess;

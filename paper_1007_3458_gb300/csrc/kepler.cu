@@ -129,14 +129,21 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
     const bool act = k < a.n;
     const int64_t r = act ? (a.rows ? a.rows[k] : a.row0 + k) : 0;
     const int64_t ld = a.ld;
-    double qx = 0.0, qy = 0.0, qz = 0.0, vx = 0.0, vy = 0.0, vz = 0.0, mu = 1.0;
+    double qx = 0.0, qy = 0.0, qz = 0.0, vx = 0.0, vy = 0.0, vz = 0.0;
+    // mu = G m0 with sqrt(mu) and 1/mu, formed once per system on the host
+    // (correctly rounded, as sqrt and the division here would give them)
+    double mu = 1.0, sqmu = 1.0, imu = 1.0;
     if (act) {
         qx = a.q0[r]; qy = a.q0[ld + r]; qz = a.q0[2 * ld + r];
         vx = a.v0[r]; vy = a.v0[ld + r]; vz = a.v0[2 * ld + r];
-        mu = a.sys_of ? a.G * a.m[a.offsets[a.sys_of[r]]] : a.mu;
+        if (a.kmu) {
+            const double *km = a.kmu + 3 * (int64_t)a.sys_of[r];
+            mu = km[0]; sqmu = km[1]; imu = km[2];
+        } else {
+            mu = a.mu; sqmu = a.sqmu; imu = a.imu;
+        }
     }
     const double dt = a.dt;
-    const double sqmu = sqrt(mu);
     const double r0 = sqrt(qx * qx + qy * qy + qz * qz);
     const bool feat = act && r0 > 0.0 && dt != 0.0;
     float u[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -169,7 +176,7 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
         // the FP64 pipe bounds this kernel: divisions by mu, sqrt(mu) and r0
         // become products with reciprocals formed once (within an ulp of the
         // quotients)
-        const double imu = 1.0 / mu, ir0 = 1.0 / r0, isqmu = sqmu * imu;
+        const double ir0 = 1.0 / r0, isqmu = sqmu * imu;
         KepEq eq;
         eq.sqmu_dt = sqmu * dt;
         eq.r0 = r0;
@@ -260,9 +267,16 @@ __global__ void __launch_bounds__(256) k_kepler(KeplerArgs a) {
                 double dx;
                 if (solver == QYM_SOLVER_LAGUERRE) {
                     // Laguerre, n = 5: dx = n F / (F' + sgn(F') sqrt|(n-1)^2 F'^2 - n(n-1) F F''|),
-                    // with F' taken out of the root so that F'^2 never overflows
-                    const double iFp = 1.0 / Fp, rf = F * iFp, rpp = Fpp * iFp;
-                    dx = 5.0 * rf / (1.0 + sqrt(fabs(16.0 - 20.0 * rf * rpp)));
+                    // with F' taken out of the root so that F'^2 never overflows:
+                    // dx = rf 5 / (1 + sqrt|16 - 20 z|), rf = F / F', z = rf F'' / F'.
+                    // Near the root (|z| < 1e-6) the factor is its series
+                    // 1 + z / 2 + 13 z^2 / 32 (next term 0.38 z^3 < 4e-19): the same
+                    // step to rounding without the square root and the division
+                    const double iFp = 1.0 / Fp, rf = F * iFp, z = rf * (Fpp * iFp);
+                    if (fabs(z) < 1e-6)
+                        dx = rf * fma(z, fma(13.0 / 32.0, z, 0.5), 1.0);
+                    else
+                        dx = 5.0 * rf / (1.0 + sqrt(fabs(16.0 - 20.0 * z)));
                 } else {
                     dx = F / Fp;
                 }

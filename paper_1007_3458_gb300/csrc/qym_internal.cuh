@@ -78,6 +78,7 @@ struct Dev {
     int32_t *heavy_rows = nullptr;   // ascending rows, system by system
     int32_t *heavy_start = nullptr;  // [nsys+1]
     double *heavy_thr = nullptr;     // [nsys] mass threshold (+inf: no split)
+    double *kmu = nullptr;           // [nsys][3] mu = G m0, sqrt(mu), 1/mu (E_Kep)
     int32_t heavy_split = 0;         // 1 when the kick in use is the mixed one
     // counters (device): see Counters below
     unsigned long long *ctr = nullptr;
@@ -192,7 +193,7 @@ struct KeplerArgs {
     int64_t ld;            // leading dimension (stride between x, y, z blocks)
     const int64_t *rows;   // optional row map: body k is row rows[k]; NULL: row row0 + k
     int64_t row0;
-    double mu, dt;
+    double mu, sqmu, imu, dt;   // mu with sqrt(mu) and 1/mu (all rows, when kmu is NULL)
     int32_t solver, guess, max_iter;
     const float *mlp_w;    // guess network weights (QYM_GUESS_MLP) or NULL
     double *x_out;         // [n] or NULL
@@ -205,11 +206,9 @@ struct KeplerArgs {
     int32_t *iters;        // [n] or NULL
     int32_t *status;       // or NULL
     unsigned long long *iter_sum;  // or NULL
-    // per-row gravitational parameter mu = G m[star of row] when sys_of != NULL
+    // per-row mu, sqrt(mu), 1/mu: kmu[3 sys_of[row] + 0..2] when kmu != NULL
     const int32_t *sys_of;
-    const int64_t *offsets;
-    const double *m;
-    double G;
+    const double *kmu;
 };
 cudaError_t launch_kepler(const KeplerArgs &a, cudaStream_t st);
 
