@@ -540,7 +540,7 @@ def run_ours(args):
     # every step starts by writing 256 MB (twice the 129 MB L2), inside the
     # timed region, so no step reuses the previous step's lines
     search = {"binned": q.QYM_SEARCH_BINNED, "fused": q.QYM_SEARCH_FUSED,
-              "auto": q.QYM_SEARCH_AUTO}[args.search]
+              "auto": q.QYM_SEARCH_AUTO, "escape": q.QYM_SEARCH_ESCAPE}[args.search]
     sim = q.Simulation(w.m, w.q, w.v, w.offsets, kick_prec=prec, device=dev,
                        l2_flush_bytes=256 << 20, eps_H=w.eps_H, merge_kicks=args.merge_kicks,
                        search=search, hermite_cluster=args.hermite_cluster)
@@ -589,7 +589,8 @@ def run_ours(args):
     k2_ms, _ = q.qym_time_kick(sim.ctx, 0, reps)
     # the step's two kicks: with the binned search both are plain; with the
     # fused one the first carries the search
-    binned = sim.effective_params().search == q.QYM_SEARCH_BINNED
+    sim_search = sim.effective_params().search
+    binned = sim_search == q.QYM_SEARCH_BINNED
     kick_ms = k2_ms if binned else 0.5 * (k1_ms + k2_ms)
     achieved = 20.0 * pairs / (kick_ms / 1e3) / 1e12
     clocks = clk.summary()
@@ -703,7 +704,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "fp32-pair/f64-state" if prec else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "kick": args.prec,
-                       "search": "binned" if binned else "fused",
+                       "search": {q.QYM_SEARCH_BINNED: "binned", q.QYM_SEARCH_ESCAPE: "escape"}.get(
+                           sim_search, "fused"),
                        "parallelism": ("independent batches per rank" if ws > 1 and
                                        WORKLOADS[args.workload][0] == "ensemble" else
                                        "replicas" if ws > 1 else "single GPU"),
@@ -1052,9 +1054,10 @@ def main():
                     help="kepler_1m: train the guess network first (0: standard guess only)")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--search", default="auto", choices=["auto", "binned", "fused"],
+    ap.add_argument("--search", default="auto", choices=["auto", "binned", "fused", "escape"],
                     help="close-encounter search: binned after the drift, fused into the kick, "
-                         "or the library's choice for the workload")
+                         "the paper's escape-velocity sweep (fused into the kick), or the "
+                         "library's choice for the workload")
     ap.add_argument("--shape", default="",
                     help="threads,ipt,splits: the kick's launch shape instead of autotuning")
     ap.add_argument("--search-too", type=int, default=1,

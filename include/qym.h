@@ -117,7 +117,7 @@ typedef struct qym_params {
                                    encounter set in the Hermite: 2, 4 or 8; 0: automatic
                                    (8 for a single system, 2 for a batch of systems) */
     int32_t search;             /* how the close-encounter candidates are found (Sec. 2.4):
-                                   QYM_SEARCH_AUTO (default), _FUSED or _BINNED */
+                                   QYM_SEARCH_AUTO (default), _FUSED, _BINNED or _ESCAPE */
     int32_t whole_hermite;      /* 1: Sec. 2.3, last paragraph: when a step's encounter sets
                                    put two planets in one set, that system's step is redone
                                    by the Hermite for every body: from the positions after the
@@ -150,6 +150,15 @@ typedef struct qym_params {
 #define QYM_SEARCH_AUTO   2   /* BINNED for one system of at least 65536 bodies (there
                                  binning costs less than the all-pairs reach test in the
                                  kick), FUSED otherwise */
+/* ESCAPE: the paper's own crude sweep (Sec. 2.4), fused into the first kick like
+ *   FUSED: a pair is a candidate when its separation at the start of the step is
+ *   below a_E times the Hill radii plus the distance a body covers at its escape
+ *   velocity sqrt(2 G m0 / |Q|) over tau, each body contributing its own term
+ *   (rho_i = a_E r_H,i + |tau| v_esc,i; tested as r^2 < 2 rho_i^2 + 2 rho_j^2). No
+ *   |a| allowance and no re-search: as the paper notes, a body moving faster than
+ *   escape can be missed (the other modes' lists equal the all-pairs test). A
+ *   split context uses FUSED. */
+#define QYM_SEARCH_ESCAPE 3
 
 #define QYM_HEAVY_CAP 256
 

@@ -24,7 +24,7 @@ STATUS_NAMES = ["QYM_OK", "QYM_EINVAL", "QYM_ENOMEM", "QYM_ECUDA", "QYM_ENAN", "
 QYM_ST_KEPLER_NOCONV, QYM_ST_HERMITE_CAP, QYM_ST_CAND_OVERFLOW, QYM_ST_ENC_OVERFLOW = 1, 2, 4, 8
 QYM_ST_SET_OVERFLOW, QYM_ST_NAN, QYM_ST_UF_CAP, QYM_ST_LOG_OVERFLOW = 16, 32, 64, 128
 QYM_KICK_FP64, QYM_KICK_MIXED = 0, 1
-QYM_SEARCH_FUSED, QYM_SEARCH_BINNED, QYM_SEARCH_AUTO = 0, 1, 2
+QYM_SEARCH_FUSED, QYM_SEARCH_BINNED, QYM_SEARCH_AUTO, QYM_SEARCH_ESCAPE = 0, 1, 2, 3
 QYM_SOLVER_LAGUERRE, QYM_SOLVER_NEWTON, QYM_SOLVER_NEWTON32 = 0, 1, 2
 QYM_GUESS_STANDARD, QYM_GUESS_R0, QYM_GUESS_MLP = 0, 1, 2
 QYM_STATIC_MAX_ROWS = 32768

@@ -157,8 +157,8 @@ static bool valid_params(const qym_params *p, std::string &why) {
     if (p->l2_flush_bytes < 0 || p->l2_flush_bytes > ((int64_t)1 << 34)) { why = "l2_flush_bytes"; return false; }
     if (p->merge_kicks != 0 && p->merge_kicks != 1) { why = "merge_kicks must be 0 or 1"; return false; }
     if (p->search != QYM_SEARCH_FUSED && p->search != QYM_SEARCH_BINNED &&
-        p->search != QYM_SEARCH_AUTO) {
-        why = "search must be QYM_SEARCH_AUTO, QYM_SEARCH_FUSED or QYM_SEARCH_BINNED";
+        p->search != QYM_SEARCH_AUTO && p->search != QYM_SEARCH_ESCAPE) {
+        why = "search must be QYM_SEARCH_AUTO, QYM_SEARCH_FUSED, QYM_SEARCH_BINNED or QYM_SEARCH_ESCAPE";
         return false;
     }
     if (p->hermite_cluster != 0 && p->hermite_cluster != 2 && p->hermite_cluster != 4 &&
@@ -581,7 +581,8 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     c->binned = params->encounters &&
                 (params->search == QYM_SEARCH_BINNED ||
                  (params->search == QYM_SEARCH_AUTO && auto_binned));
-    c->p.search = c->binned ? QYM_SEARCH_BINNED : QYM_SEARCH_FUSED;
+    d.escape_reach = params->encounters && params->search == QYM_SEARCH_ESCAPE ? 1 : 0;
+    c->p.search = c->binned ? QYM_SEARCH_BINNED : (d.escape_reach ? QYM_SEARCH_ESCAPE : QYM_SEARCH_FUSED);
     std::vector<int4> stiles;
     std::vector<int2> stpairs;
     if (c->binned) {
@@ -1055,7 +1056,8 @@ extern "C" qym_status qym_step(qym_ctx *c, double tau, int64_t nsteps) {
     const bool sort = d.perm && !c->sort_current;
     c->sort_current = false;
     // without the |a| of an earlier kick the first search runs after its kick
-    const bool fresh = !c->amag_valid;
+    // (the escape-velocity reach needs none)
+    const bool fresh = !c->amag_valid && !d.escape_reach;
     c->amag_valid = true;  // every kick's finisher records |a|
     // the call's counters, the order, and item 1 of the first step: drift tau/2
     auto opening = [&]() -> cudaError_t {
@@ -1311,6 +1313,7 @@ extern "C" qym_status qym_split_init(qym_ctx *c, int32_t rank, int32_t world) {
     d.perm = d.inv = nullptr;  // the split's kick items are in row order
     d.far = d.tile = nullptr;
     c->p.search = QYM_SEARCH_FUSED;  // the split's candidates come with each rank's kick
+    d.escape_reach = 0;
     c->binned = false;
     c->split_rank = rank;
     c->split_world = world;

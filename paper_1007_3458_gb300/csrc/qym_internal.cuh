@@ -80,6 +80,7 @@ struct Dev {
     double *heavy_thr = nullptr;     // [nsys] mass threshold (+inf: no split)
     double *kmu = nullptr;           // [nsys][3] mu = G m0, sqrt(mu), 1/mu (E_Kep)
     int32_t heavy_split = 0;         // 1 when the kick in use is the mixed one
+    int32_t escape_reach = 0;        // 1: the crude reach is the escape-velocity one
     // counters (device): see Counters below
     unsigned long long *ctr = nullptr;
     int32_t *status = nullptr;    // QYM_ST_* bits

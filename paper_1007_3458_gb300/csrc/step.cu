@@ -131,13 +131,21 @@ __global__ void __launch_bounds__(256) k_drift_pack(Dev d, DriftArgs a) {
         float rHb = round_up_f(rH * (1.0 + 1e-6));
         d.rH_bound[r] = rHb;
         double rr = sqrt(qx * qx + qy * qy + qz * qz);
-        double Om = sqrt(mu / (rr * rr * rr));
-        double ux = vx + Om * qy, uy = vy - Om * qx, uz = vz;
-        double u = sqrt(ux * ux + uy * uy + uz * uz);
-        double w = fabs(a.kick_span) * a.a_allow * (double)d.amag[r];
-        double sh = fmin(0.8, 2.5 * Om * fabs(a.tau));
-        double F = 2.0 / (1.0 - sh);
-        double rho = F * (a.a_E * (double)rHb + fabs(a.tau) * (u + w)) + 1e-12 * rr;
+        double rho;
+        if (d.escape_reach) {
+            // QYM_SEARCH_ESCAPE, the paper's crude sweep (Sec. 2.4): a_E times
+            // the Hill radius plus the distance covered at the escape
+            // velocity over the step
+            rho = a.a_E * (double)rHb + fabs(a.tau) * sqrt(2.0 * mu / rr) + 1e-12 * rr;
+        } else {
+            double Om = sqrt(mu / (rr * rr * rr));
+            double ux = vx + Om * qy, uy = vy - Om * qx, uz = vz;
+            double u = sqrt(ux * ux + uy * uy + uz * uz);
+            double w = fabs(a.kick_span) * a.a_allow * (double)d.amag[r];
+            double sh = fmin(0.8, 2.5 * Om * fabs(a.tau));
+            double F = 2.0 / (1.0 - sh);
+            rho = F * (a.a_E * (double)rHb + fabs(a.tau) * (u + w)) + 1e-12 * rr;
+        }
         // kernels test r^2 < c_i + c_j with c = 2 rho^2 >= ... a superset of
         // r < rho_i + rho_j, as (rho_i + rho_j)^2 <= 2 rho_i^2 + 2 rho_j^2;
         // the factor covers the FP32 rounding of r^2 (a few 1e-7 relative,
@@ -241,7 +249,7 @@ __global__ void __launch_bounds__(256) k_finish(Dev d, FinishArgs a) {
         double rH = a.hill_fixed ? d.rH_fixed[r] : hill(a.q[r], a.q[R + r], a.q[2 * R + r], d.m[r], m0);
         d.rH[r] = rH;
         // check 1 (the search fused into this kick): audit its reach
-        bool bad = a.check == 1 && (an > a.a_allow * d.amag[r] + 1e-30f ||
+        bool bad = a.check == 1 && !d.escape_reach && (an > a.a_allow * d.amag[r] + 1e-30f ||
                                     rH > (double)d.rH_bound[r]);
         if (bad) {
             unsigned long long k = atomicAdd(d.ctr + C_NRESCAN, 1ull);

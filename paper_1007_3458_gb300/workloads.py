@@ -307,6 +307,25 @@ def planet_encounter(n_planetesimals=60, seed=9, sep=0.6, phase=0.12, nsteps=20,
                     np.array([0, len(m)], dtype=np.int64), TAU_A5, nsteps, eps_H=4.7e-4)
 
 
+def escape_flyby(speed=2.3, miss=0.005, name="escape_flyby"):
+    """The case Sec. 2.4 says its crude sweep can miss: star + a planetesimal
+    (1e-9) on a circular orbit at 10 AU + a body of 1e-9 moving at `speed`
+    (2.3: five times the escape speed at 10 AU) along -x on a straight line
+    that passes `miss` AU from the planetesimal's position at mid-step (its
+    circular motion written out); tau = P(a=5)/40. The pair starts 2.04 AU
+    apart, farther than the two bodies' escape distances over the step
+    (1.55 AU in the r^2 < 2 rho_i^2 + 2 rho_j^2 form), and meets well inside
+    3 Hill radii."""
+    G, m0, mp = 1.0, 1.0, 1e-9
+    tau = TAU_A5
+    om = math.sqrt(G * (m0 + mp) / 1000.0)  # circular at 10 AU
+    th = 0.5 * tau * om
+    tgt = np.array([10.0 * math.cos(th), 10.0 * math.sin(th) + miss, 0.0])
+    q = np.array([[0.0, 0.0, 0.0], [10.0, 0.0, 0.0], tgt + np.array([0.5 * tau * speed, 0.0, 0.0])])
+    v = np.array([[0.0, 0.0, 0.0], [0.0, 10.0 * om, 0.0], [-speed, 0.0, 0.0]])
+    return Workload(name, np.array([m0, mp, mp]), q, v, np.array([0, 3], dtype=np.int64), tau, 1)
+
+
 def test_particles(n=1048576, seed=4):
     """Massless test particles about a unit-mass star: a log-uniform in
     [0.5, 50], e uniform in [0, 0.9], inclination and angles uniform.

@@ -150,3 +150,53 @@ def test_auto_search_choice(torch):
         assert sim.params.search == q.QYM_SEARCH_AUTO
         assert sim.effective_params().search == want, w.name
         sim.close()
+
+
+def test_escape_velocity_search(torch, oracle):
+    """QYM_SEARCH_ESCAPE, the paper's own crude sweep (Sec. 2.4: a_E Hill
+    radii plus the distance covered at the escape velocity over the step):
+    on the 260-body disk and the stirred disk of crossers its records equal
+    the oracle's all-pairs rigorous test on each step's inputs (one-step
+    calls and the last step of four-step calls), with no audit or re-search
+    (on the cold disk with six times the fused reach's candidates, on the
+    crossers, whose fast bodies widen the fused reach, with a sixth); on a
+    body at five
+    times the escape speed aimed at a planetesimal (workloads.escape_flyby)
+    it misses the encounter the oracle and the fused search find, as the
+    paper says it can."""
+    for w, calls in ((W.disk_260(), [1] * 6 + [4, 4]), (W.crossers(), [1] * 8 + [4, 4])):
+        R = len(w.m)
+        sim = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, search=q.QYM_SEARCH_ESCAPE)
+        assert sim.effective_params().search == q.QYM_SEARCH_ESCAPE
+        snap = Snapshot(torch, sim, R)
+        cand = 0
+        for nsteps in calls:
+            sim.step(w.tau, nsteps)
+            st = sim.stats()
+            assert st["status_bits"] == 0 and st["rescans"] == 0, st
+            cand += st["candidates"]
+            mine = _last_step_records(sim, nsteps)
+            q0, v0, q1, v1, rH = snap.host()
+            pairs, _, _ = oracle.encounters(q0, v0, q1, v1, rH, w.tau, w.a_E)
+            assert np.array_equal(mine, pairs), (w.name, len(mine), len(pairs))
+        sim.close()
+        fused = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, search=q.QYM_SEARCH_FUSED)
+        fc = 0
+        for nsteps in calls:
+            fused.step(w.tau, nsteps)
+            fc += fused.stats()["candidates"]
+        fused.close()
+        print(f"\n  {w.name}: candidates escape {cand}, fused {fc}")
+        if w.name == "disk_260":
+            assert cand > fc
+    w = W.escape_flyby()
+    vd = oracle.helio_to_dh(w.m, w.v)
+    ref = oracle.step(w.m, w.q, vd, w.offsets, w.tau, 1, oracle.params(eps_H=w.eps_H))
+    assert [tuple(x) for x in ref.encounters] == [(0, 1, 2)]
+    got = {}
+    for name, search in (("escape", q.QYM_SEARCH_ESCAPE), ("fused", q.QYM_SEARCH_FUSED)):
+        sim = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, search=search)
+        sim.step(w.tau, 1)
+        got[name] = [tuple(x) for x in sim.encounters()]
+        sim.close()
+    assert got["fused"] == [(0, 1, 2)] and got["escape"] == [], got
