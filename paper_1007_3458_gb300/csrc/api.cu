@@ -1683,7 +1683,12 @@ static int64_t pairs_per_kick(const qym_ctx *c) {
 
 // the kick kernel alone on the current state (packs rebuilt first; the
 // candidate counter is reset after, the velocities are not touched)
-static qym_status time_kick_shape(qym_ctx *c, int flag, int reps, const KickTune &t, double *ms) {
+// Mean time of `reps` launches of the kick (flag: with the fused search),
+// or with `finish` of a step's pair of kicks (the flag's kick and a plain
+// one), each with its finisher (which sums the partial slots; dt = 0 leaves
+// the velocities as they are), per kick.
+static qym_status time_kick_shape(qym_ctx *c, int flag, int reps, const KickTune &t, double *ms,
+                                  bool finish = false) {
     Dev &d = c->d;
     const qym_params &p = c->p;
     cudaStream_t st = c->stream;
@@ -1692,9 +1697,17 @@ static qym_status time_kick_shape(qym_ctx *c, int flag, int reps, const KickTune
     cudaEvent_t e0, e1;
     CK(c, cudaEventCreate(&e0));
     CK(c, cudaEventCreate(&e1));
-    CK(c, launch_kick_tiles(d, p.kick_prec, flag, p.G, t.threads, t.ipt, st));  // warm
+    auto one = [&](int f) -> cudaError_t {
+        cudaError_t e = launch_kick_tiles(d, p.kick_prec, f, p.G, t.threads, t.ipt, st);
+        if (e == cudaSuccess && finish) e = launch_kick_finish_v(d, d.v, d.q, 0.0, p.G, 0, p.hill_fixed, st);
+        return e;
+    };
+    CK(c, one(flag));  // warm
     CK(c, cudaEventRecord(e0, st));
-    for (int r = 0; r < reps; ++r) CK(c, launch_kick_tiles(d, p.kick_prec, flag, p.G, t.threads, t.ipt, st));
+    for (int r = 0; r < reps; ++r) {
+        CK(c, one(flag));
+        if (finish) CK(c, one(0));
+    }
     CK(c, cudaEventRecord(e1, st));
     CK(c, cudaEventSynchronize(e1));
     float f = 0.f;
@@ -1704,7 +1717,7 @@ static qym_status time_kick_shape(qym_ctx *c, int flag, int reps, const KickTune
     CK(c, cudaMemsetAsync(d.ctr + C_NCAND, 0, sizeof(unsigned long long), st));
     CK(c, cudaMemsetAsync(d.status, 0, sizeof(int32_t), st));
     CK(c, cudaStreamSynchronize(st));
-    *ms = (double)f / reps;
+    *ms = (double)f / (finish ? 2 * reps : reps);
     return QYM_OK;
 }
 
@@ -1799,7 +1812,9 @@ extern "C" qym_status qym_autotune(qym_ctx *c) {
         qym_status s = apply_tune(c, t);
         if (s != QYM_OK) return s;
         double ms = 0.0;
-        s = time_kick_shape(c, fused_search(c), 3, t, &ms);
+        // a step's two kicks with their finishers: more j-splits shorten a
+        // kick's tail but give the finisher more partial slots to add
+        s = time_kick_shape(c, fused_search(c), 3, t, &ms, true);
         if (s != QYM_OK) return s;
         if (ms < best_ms) { best_ms = ms; best = t; }
     }
