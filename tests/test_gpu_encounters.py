@@ -152,7 +152,9 @@ def test_auto_search_choice(torch):
         sim.close()
 
 
-def test_escape_velocity_search(torch, oracle):
+@pytest.mark.parametrize("prec, merge", [(q.QYM_KICK_MIXED, 0), (q.QYM_KICK_FP64, 0),
+                                         (q.QYM_KICK_MIXED, 1)])
+def test_escape_velocity_search(torch, oracle, prec, merge):
     """QYM_SEARCH_ESCAPE, the paper's own crude sweep (Sec. 2.4: a_E Hill
     radii plus the distance covered at the escape velocity over the step):
     on the 260-body disk and the stirred disk of crossers its records equal
@@ -163,10 +165,11 @@ def test_escape_velocity_search(torch, oracle):
     body at five
     times the escape speed aimed at a planetesimal (workloads.escape_flyby)
     it misses the encounter the oracle and the fused search find, as the
-    paper says it can."""
+    paper says it can. With the mixed and the FP64 kick, and with merged kicks."""
     for w, calls in ((W.disk_260(), [1] * 6 + [4, 4]), (W.crossers(), [1] * 8 + [4, 4])):
         R = len(w.m)
-        sim = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, search=q.QYM_SEARCH_ESCAPE)
+        sim = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, search=q.QYM_SEARCH_ESCAPE,
+                           kick_prec=prec, merge_kicks=merge)
         assert sim.effective_params().search == q.QYM_SEARCH_ESCAPE
         snap = Snapshot(torch, sim, R)
         cand = 0
@@ -180,7 +183,8 @@ def test_escape_velocity_search(torch, oracle):
             pairs, _, _ = oracle.encounters(q0, v0, q1, v1, rH, w.tau, w.a_E)
             assert np.array_equal(mine, pairs), (w.name, len(mine), len(pairs))
         sim.close()
-        fused = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, search=q.QYM_SEARCH_FUSED)
+        fused = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, search=q.QYM_SEARCH_FUSED,
+                             kick_prec=prec, merge_kicks=merge)
         fc = 0
         for nsteps in calls:
             fused.step(w.tau, nsteps)
@@ -195,7 +199,8 @@ def test_escape_velocity_search(torch, oracle):
     assert [tuple(x) for x in ref.encounters] == [(0, 1, 2)]
     got = {}
     for name, search in (("escape", q.QYM_SEARCH_ESCAPE), ("fused", q.QYM_SEARCH_FUSED)):
-        sim = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, search=search)
+        sim = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, search=search,
+                           kick_prec=prec, merge_kicks=merge)
         sim.step(w.tau, 1)
         got[name] = [tuple(x) for x in sim.encounters()]
         sim.close()
