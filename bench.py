@@ -614,6 +614,10 @@ def run_ours(args):
             "gpair_per_s_kernel": pairs / (kick_ms / 1e3) / 1e9,
             "kick_shape": {"rows_per_cta": st["kick_tile_i"], "splits": st["kick_tile_splits"]}}
 
+    # E_Dft alone (the momentum reduction and the drift with the kick's packs)
+    # against HBM; the state is put back
+    edft = edft_roofline(q, sim, w)
+
     # end to end through the C ABI with host buffers: per step, the state goes
     # host -> device (qym_set_state), one step, device -> host (qym_get_state),
     # the state in pinned host memory
@@ -715,7 +719,7 @@ def run_ours(args):
             "kicks_per_step": 1 if args.merge_kicks else 2, "merged_kicks": merged,
             "other_search": other,
             "precision": precision,
-            "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cb}
+            "roofline": roof, "edft": edft, "clocks": clocks, "e2e": e2e, "cpu_baseline": cb}
     print(json.dumps(line))
     return 0
 
@@ -760,6 +764,27 @@ def run_sweep(args):
                                  "tau": w.tau, "eps_H": w.eps_H},
                       "points": points}))
     return 0
+
+
+# E_Dft's algorithmic bytes per row: the reduction reads m and v (32 B); the
+# drift reads Q and writes it (48 B) and writes the kick's float packs (32 B)
+EDFT_MOMENTUM_BYTES = 32
+EDFT_DRIFT_BYTES = 80
+
+
+def edft_roofline(q, sim, w, reps=20):
+    """E_Dft (Sec. 2, Eq. 2) timed alone through qym_time_drift (CUDA events on
+    the context's stream, the state put back): achieved GB/s of its two
+    launches against the measured HBM copy bandwidth."""
+    mom_ms, drift_ms = q.qym_time_drift(sim.ctx, w.tau, reps)
+    rows = len(w.m)
+    peak, which = hbm_peak_gbs()
+    out = {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_source": which, "rows": rows}
+    for name, ms, bpr in (("momentum", mom_ms, EDFT_MOMENTUM_BYTES),
+                          ("drift", drift_ms, EDFT_DRIFT_BYTES)):
+        gbs = rows * bpr / (ms / 1e3) / 1e9
+        out[name] = {"ms": ms, "bytes_per_row": bpr, "achieved": gbs, "frac": gbs / peak}
+    return out
 
 
 def hbm_peak_gbs():

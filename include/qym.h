@@ -318,6 +318,15 @@ qym_status qym_get_stream(const qym_ctx *ctx, void **stream);
 qym_status qym_time_kick(qym_ctx *ctx, int32_t with_search, int32_t reps, double *ms_per_launch,
                          int64_t *pairs);
 
+/* Time E_Dft (Sec. 2, Eq. 2) of ctx alone: `reps` launches each of the
+ * barycentric-momentum reduction (S = sum m v per system) and of the drift
+ * (Q += (tau/2) S / m0 twice, the closing and the next opening half-drift,
+ * then the kick's float packs) on the ctx stream, bracketed by CUDA events;
+ * the drift reads a copy of the state and the state is put back afterwards.
+ * *ms_momentum and *ms_drift get the mean launch times in milliseconds. */
+qym_status qym_time_drift(qym_ctx *ctx, double tau, int32_t reps, double *ms_momentum,
+                          double *ms_drift);
+
 /* Set the kick launch shape: threads per CTA (128 or 256), i rows per thread
  * (1, 2, or 4 for the mixed kick) and j splits per system (1 .. the largest
  * the context's buffers hold, at least 4); QYM_EINVAL otherwise. For

@@ -111,6 +111,7 @@ def lib():
     L.qym_shape.argtypes = [P, I64, C.POINTER(C.c_int32)]
     L.qym_get_stream.argtypes = [P, C.POINTER(P)]
     L.qym_time_kick.argtypes = [P, C.c_int32, C.c_int32, D, I64]
+    L.qym_time_drift.argtypes = [P, C.c_double, C.c_int32, D, D]
     L.qym_autotune.argtypes = [P]
     L.qym_set_kick_shape.argtypes = [P, C.c_int32, C.c_int32, C.c_int32]
     L.qym_kepler_drift_dev.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_int32,
@@ -153,7 +154,7 @@ def lib():
     for name in ("qym_default_params", "qym_init", "qym_step", "qym_get_state", "qym_set_state",
                  "qym_get_encounters", "qym_get_order", "qym_energy", "qym_get_stats", "qym_get_params",
                  "qym_set_mlp", "qym_shape",
-                 "qym_get_stream", "qym_time_kick", "qym_autotune", "qym_set_kick_shape",
+                 "qym_get_stream", "qym_time_kick", "qym_time_drift", "qym_autotune", "qym_set_kick_shape",
                  "qym_kepler_drift_dev", "qym_accel_dev", "qym_encounter_test_dev",
                  "qym_energy_dev", "qym_set_kepler_log", "qym_mlp_forward_dev",
                  "qym_mlp_grad_dev", "qym_mlp_adam_dev", "qym_mlp_train_dev",
@@ -221,6 +222,13 @@ def qym_get_stream(ctx) -> int:
     h = P()
     _check(lib().qym_get_stream(ctx, C.byref(h)), ctx)
     return h.value or 0
+
+
+def qym_time_drift(ctx, tau, reps=10):
+    """(ms per momentum reduction, ms per drift + pack), state unchanged."""
+    a, b = C.c_double(), C.c_double()
+    _check(lib().qym_time_drift(ctx, tau, reps, C.byref(a), C.byref(b)), ctx)
+    return a.value, b.value
 
 
 def qym_time_kick(ctx, with_search=0, reps=10):

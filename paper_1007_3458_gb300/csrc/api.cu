@@ -519,13 +519,17 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
         c->items_cap = std::max(kick_items_count(offsets, nsys, big), d.nitems);
         c->items_cap = std::max(c->items_cap, kick_items_count(offsets, nsys, c->tune));
     }
-    // momentum chunks of at most 1024 rows, never crossing systems
+    // momentum chunks, never crossing systems: about two per SM, of 512 to
+    // 4096 rows (a CTA's FP64 reduction of its partial sums costs about as
+    // much as 1024 rows of m v, so large inputs take large chunks; a small
+    // one takes short ones, its time being the loads' latency)
+    const int64_t kMomChunk = std::min<int64_t>(4096, std::max<int64_t>(512, (R / 304 + 255) / 256 * 256));
     std::vector<int4> mch;
     std::vector<int32_t> sc0(nsys + 1);
     for (int32_t s = 0; s < nsys; ++s) {
         sc0[s] = (int32_t)mch.size();
-        for (int64_t r0 = offsets[s]; r0 < offsets[s + 1]; r0 += 1024)
-            mch.push_back(make_int4((int)r0, (int)std::min<int64_t>(r0 + 1024, offsets[s + 1]), s, 0));
+        for (int64_t r0 = offsets[s]; r0 < offsets[s + 1]; r0 += kMomChunk)
+            mch.push_back(make_int4((int)r0, (int)std::min<int64_t>(r0 + kMomChunk, offsets[s + 1]), s, 0));
     }
     sc0[nsys] = (int32_t)mch.size();
     d.nmchunks = (int32_t)mch.size();
@@ -1718,6 +1722,46 @@ static qym_status time_kick_shape(qym_ctx *c, int flag, int reps, const KickTune
     CK(c, cudaMemsetAsync(d.status, 0, sizeof(int32_t), st));
     CK(c, cudaStreamSynchronize(st));
     *ms = (double)f / (finish ? 2 * reps : reps);
+    return QYM_OK;
+}
+
+extern "C" qym_status qym_time_drift(qym_ctx *c, double tau, int32_t reps, double *ms_momentum,
+                                     double *ms_drift) {
+    if (!c || reps < 1 || !ms_momentum || !ms_drift || !(tau != 0.0) || !std::isfinite(tau))
+        FAIL(c, QYM_EINVAL, "qym_time_drift: bad argument");
+    CK(c, cudaSetDevice(c->p.device));
+    Dev &d = c->d;
+    const qym_params &p = c->p;
+    cudaStream_t st = c->stream;
+    const size_t b3 = sizeof(double) * 3 * (size_t)d.rows;
+    // the drift reads (q1, v1), copies of the state (idle between steps)
+    CK(c, cudaMemcpyAsync(d.q1, d.q, b3, cudaMemcpyDeviceToDevice, st));
+    CK(c, cudaMemcpyAsync(d.v1, d.v, b3, cudaMemcpyDeviceToDevice, st));
+    cudaEvent_t e0, e1, e2;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    CK(c, cudaEventCreate(&e2));
+    CK(c, launch_momentum(d, st));  // warm
+    CK(c, cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; ++r) CK(c, launch_momentum(d, st));
+    CK(c, cudaEventRecord(e1, st));
+    for (int r = 0; r < reps; ++r)
+        CK(c, launch_drift_pack_from(d, d.q1, d.v1, 0.5 * tau, 0.5 * tau, tau, p.a_E, p.G, 0,
+                                     p.hill_fixed, st, 0.5 * tau));
+    CK(c, cudaEventRecord(e2, st));
+    CK(c, cudaEventSynchronize(e2));
+    float f01 = 0.f, f12 = 0.f;
+    CK(c, cudaEventElapsedTime(&f01, e0, e1));
+    CK(c, cudaEventElapsedTime(&f12, e1, e2));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    // the state back (the next call packs the kick's operands again)
+    CK(c, cudaMemcpyAsync(d.q, d.q1, b3, cudaMemcpyDeviceToDevice, st));
+    CK(c, cudaMemcpyAsync(d.v, d.v1, b3, cudaMemcpyDeviceToDevice, st));
+    CK(c, cudaStreamSynchronize(st));
+    *ms_momentum = (double)f01 / reps;
+    *ms_drift = (double)f12 / reps;
     return QYM_OK;
 }
 

@@ -7,18 +7,17 @@
 
 namespace qym {
 
-__device__ __forceinline__ bool is_star(const Dev &d, int64_t r) {
-    return d.offsets[d.sys_of[r]] == r;
-}
-
 // ---------------------------------------------------------------- E_Dft
 // chunk partial sums of m_i v_i (bodies only), deterministic tree order
+// (a chunk lies in one system, ch.z: its star row is known per chunk)
 __global__ void __launch_bounds__(256) k_mom_chunks(Dev d) {
     const int4 ch = d.mchunks[blockIdx.x];
+    const int64_t star = d.offsets[ch.z];
     double sx = 0.0, sy = 0.0, sz = 0.0;
     const int64_t R = d.rows;
+#pragma unroll 4
     for (int64_t r = ch.x + threadIdx.x; r < ch.y; r += blockDim.x) {
-        if (is_star(d, r)) continue;
+        if (r == star) continue;
         double mm = d.m[r];
         sx += mm * d.v[r];
         sy += mm * d.v[R + r];
@@ -38,18 +37,23 @@ __global__ void __launch_bounds__(256) k_mom_chunks(Dev d) {
     }
 }
 
+// S of each system from its chunks' partial sums, one warp per system: lane l
+// adds the chunks l, l + 32, ... in order, then a fixed shuffle tree (the
+// loads of a long system's chunk list overlap instead of following one another)
 __global__ void k_mom_final(Dev d) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (s >= d.nsys) return;
     double t[3] = {0.0, 0.0, 0.0};
-    for (int c = d.sys_chunk0[s]; c < d.sys_chunk0[s + 1]; ++c)
+    for (int c = d.sys_chunk0[s] + lane; c < d.sys_chunk0[s + 1]; c += 32)
         for (int k = 0; k < 3; ++k) t[k] += d.mpart[3 * c + k];
-    for (int k = 0; k < 3; ++k) d.S[3 * s + k] = t[k];
+    for (int k = 0; k < 3; ++k) t[k] = warp_sum(t[k]);
+    if (lane < 3) d.S[3 * s + lane] = lane == 0 ? t[0] : (lane == 1 ? t[1] : t[2]);
 }
 
 cudaError_t launch_momentum(const Dev &d, cudaStream_t st) {
     k_mom_chunks<<<d.nmchunks, 256, 0, st>>>(d);
-    k_mom_final<<<(d.nsys + 127) / 128, 128, 0, st>>>(d);
+    k_mom_final<<<(unsigned)((32 * (int64_t)d.nsys + 127) / 128), 128, 0, st>>>(d);
     return cudaGetLastError();
 }
 
@@ -78,10 +82,27 @@ struct DriftArgs {
     int flag_next, hill_fixed;
 };
 
+// the systems whose shifts a CTA of k_drift_pack forms once (its rows span at
+// most this many systems; else every row forms its own)
+constexpr int kDriftSys = 8;
+
 __global__ void __launch_bounds__(256) k_drift_pack(Dev d, DriftArgs a) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= d.rows) return;
+    // The shifts (h S_k) / m0 of the CTA's systems, the same quotients every
+    // row would form: FP64 divisions cost ~385 cycles and ~8 FP64-pipe
+    // instructions here, six per row otherwise.
+    __shared__ double sh_shift[kDriftSys][6];
     const int64_t R = d.rows;
+    const int64_t rb = (int64_t)blockIdx.x * blockDim.x;
+    const int s_lo = d.sys_of[rb], s_hi = d.sys_of[min(rb + (int64_t)blockDim.x, R) - 1];
+    const bool cached = s_hi - s_lo < kDriftSys;
+    if (cached && threadIdx.x < 6 * (s_hi - s_lo + 1)) {
+        const int ss = s_lo + threadIdx.x / 6, k = threadIdx.x % 6;
+        const double h = k < 3 ? a.h_close : a.h_open;
+        sh_shift[threadIdx.x / 6][k] = h * d.S[3 * ss + k % 3] / d.m[d.offsets[ss]];
+    }
+    __syncthreads();
+    int64_t r = rb + threadIdx.x;
+    if (r >= R) return;
     const int sys = d.sys_of[r];
     const int64_t star = d.offsets[sys];
     double qx = a.qs[r], qy = a.qs[R + r], qz = a.qs[2 * R + r];
@@ -89,17 +110,24 @@ __global__ void __launch_bounds__(256) k_drift_pack(Dev d, DriftArgs a) {
     if (r == star) {
         qx = qy = qz = vx = vy = vz = 0.0;
     } else {
-        const double m0 = d.m[star];
-        const double Sx = d.S[3 * sys], Sy = d.S[3 * sys + 1], Sz = d.S[3 * sys + 2];
+        double sh[6];
+        if (cached) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sh[k] = sh_shift[sys - s_lo][k];
+        } else {
+            const double m0 = d.m[star];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sh[k] = (k < 3 ? a.h_close : a.h_open) * d.S[3 * sys + k % 3] / m0;
+        }
         if (a.h_close != 0.0) {
-            qx += a.h_close * Sx / m0;
-            qy += a.h_close * Sy / m0;
-            qz += a.h_close * Sz / m0;
+            qx += sh[0];
+            qy += sh[1];
+            qz += sh[2];
         }
         if (a.h_open != 0.0) {
-            qx += a.h_open * Sx / m0;
-            qy += a.h_open * Sy / m0;
-            qz += a.h_open * Sz / m0;
+            qx += sh[3];
+            qy += sh[4];
+            qz += sh[5];
         }
     }
     d.q[r] = qx; d.q[R + r] = qy; d.q[2 * R + r] = qz;

@@ -343,6 +343,28 @@ def test_set_state_of_the_held_positions_keeps_the_fused_search(gpu):
     assert sb["encounters"] > 0
 
 
+def test_time_drift_leaves_the_state(gpu):
+    """qym_time_drift (E_Dft timed alone) puts the state back bit for bit, and
+    the steps after it equal those without it; batches and single systems."""
+    for w in (W.disk_260(), W.ensemble(nsys=4, n_lo=64, n_hi=300)):
+        runs = []
+        for timed in (False, True):
+            s = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H)
+            s.step(w.tau, 2)
+            q0, v0 = s.state()
+            if timed:
+                mom, drift = q.qym_time_drift(s.ctx, w.tau, 3)
+                assert mom > 0 and drift > 0
+                q1, v1 = s.state()
+                assert np.array_equal(q1, q0) and np.array_equal(v1, v0)
+            s.step(w.tau, 2)
+            runs.append((s.state(), s.encounters()))
+            s.close()
+        (qa, va), ea = runs[0]
+        (qb, vb), eb = runs[1]
+        assert np.array_equal(qa, qb) and np.array_equal(va, vb) and np.array_equal(ea, eb)
+
+
 def test_error_statuses(gpu):
     """Capacities and caps report statuses; the context stays usable."""
     w = W.disk_260()
