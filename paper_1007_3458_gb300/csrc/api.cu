@@ -275,6 +275,7 @@ static void carve_all(qym_ctx *c, Carver &k) {
     d.heavy_start = k.take<int32_t>(d.nsys + 1);
     d.heavy_thr = k.take<double>(d.nsys);
     d.kmu = k.take<double>(3 * (size_t)d.nsys);
+    d.hfac = k.take<double>(R);
     d.cand = k.take<int2>(d.max_cand);
     d.fchunk = k.take<int4>(d.max_fchunk);
     d.enc = k.take<int2>(d.max_enc);
@@ -564,6 +565,12 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     }
     hstart[nsys] = (int32_t)hrows.size();
     c->n_heavy = (int64_t)hrows.size();
+    // the Hill radius's mass factor (m / 3 m0)^(1/3) of every row (Eq. 9),
+    // formed once: the FP64 cube root costs tens of FP64 instructions a row
+    std::vector<double> hfac(R, 0.0);
+    for (int32_t s = 0; s < nsys; ++s)
+        for (int64_t r = offsets[s] + 1; r < offsets[s + 1]; ++r)
+            hfac[r] = std::cbrt(m[r] / (3.0 * m[offsets[s]]));
     // E_Kep's mu = G m0 per system with sqrt(mu) and 1/mu (IEEE, as on the device)
     std::vector<double> kmu(3 * (size_t)nsys);
     for (int32_t s = 0; s < nsys; ++s) {
@@ -654,6 +661,7 @@ extern "C" qym_status qym_init(const qym_params *params, int32_t nsys, const int
     CKI(cudaMemcpyAsync(d.heavy_start, hstart.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, c->stream));
     CKI(cudaMemcpyAsync(d.heavy_thr, hthr.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, c->stream));
     CKI(cudaMemcpyAsync(d.kmu, kmu.data(), sizeof(double) * 3 * nsys, cudaMemcpyHostToDevice, c->stream));
+    CKI(cudaMemcpyAsync(d.hfac, hfac.data(), sizeof(double) * R, cudaMemcpyHostToDevice, c->stream));
     if (c->binned && c->nstiles) {
         std::vector<int32_t> t0(nsys);
         for (size_t t = stiles.size(); t-- > 0;) t0[stiles[t].x] = (int32_t)t;

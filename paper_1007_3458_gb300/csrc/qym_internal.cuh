@@ -79,6 +79,7 @@ struct Dev {
     int32_t *heavy_start = nullptr;  // [nsys+1]
     double *heavy_thr = nullptr;     // [nsys] mass threshold (+inf: no split)
     double *kmu = nullptr;           // [nsys][3] mu = G m0, sqrt(mu), 1/mu (E_Kep)
+    double *hfac = nullptr;          // [rows] (m / 3 m0)^(1/3): r_H = |Q| hfac (0 for stars)
     int32_t heavy_split = 0;         // 1 when the kick in use is the mixed one
     int32_t escape_reach = 0;        // 1: the crude reach is the escape-velocity one
     // counters (device): see Counters below

@@ -57,10 +57,11 @@ cudaError_t launch_momentum(const Dev &d, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Hill radius at the body's heliocentric distance: r_H = |Q| (m / 3 m0)^(1/3)
-__device__ __forceinline__ double hill(double qx, double qy, double qz, double m, double m0) {
+// Hill radius at the body's heliocentric distance: r_H = |Q| (m / 3 m0)^(1/3),
+// the factor (m / 3 m0)^(1/3) of each row formed once on the host (hfac)
+__device__ __forceinline__ double hill(double qx, double qy, double qz, double hf) {
     double r = sqrt(qx * qx + qy * qy + qz * qz);
-    return r * cbrt(m / (3.0 * m0));
+    return r * hf;
 }
 
 __device__ __forceinline__ float round_up_f(double x) {
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(256) k_drift_pack(Dev d, DriftArgs a) {
         if (a.hill_fixed) {
             rH = d.rH_fixed[r];
         } else {
-            rH = hill(qx, qy, qz, mm, m0);  // positions do not change in the kick
+            rH = hill(qx, qy, qz, d.hfac[r]);  // positions do not change in the kick
         }
         if (a.flag_next == 2) d.rH[r] = rH;
         float rHb = round_up_f(rH * (1.0 + 1e-6));
@@ -273,8 +274,7 @@ __global__ void __launch_bounds__(256) k_finish(Dev d, FinishArgs a) {
     if (a.check) {
         if (d.vmax)  // the binned search's bound takes the largest |v| entering the drift
             atomicMax(d.vmax + sys, __float_as_int(round_up_f(sqrt(vx * vx + vy * vy + vz * vz))));
-        const double m0 = d.m[star];
-        double rH = a.hill_fixed ? d.rH_fixed[r] : hill(a.q[r], a.q[R + r], a.q[2 * R + r], d.m[r], m0);
+        double rH = a.hill_fixed ? d.rH_fixed[r] : hill(a.q[r], a.q[R + r], a.q[2 * R + r], d.hfac[r]);
         d.rH[r] = rH;
         // check 1 (the search fused into this kick): audit its reach
         bool bad = a.check == 1 && !d.escape_reach && (an > a.a_allow * d.amag[r] + 1e-30f ||
@@ -311,8 +311,7 @@ __global__ void k_hill_init(Dev d, double G) {
     const int64_t R = d.rows;
     const int64_t star = d.offsets[d.sys_of[r]];
     if (r == star) { d.rH_fixed[r] = 0.0; return; }
-    const double m0 = d.m[star];
-    d.rH_fixed[r] = hill(d.q[r], d.q[R + r], d.q[2 * R + r], d.m[r], m0);
+    d.rH_fixed[r] = hill(d.q[r], d.q[R + r], d.q[2 * R + r], d.hfac[r]);
 }
 
 cudaError_t launch_hill_init(const Dev &d, double G, cudaStream_t st) {

@@ -46,9 +46,9 @@ def _last_step_records(sim, nsteps):
 
 def _check_hill(oracle, w, q0, v0, rH):
     """The Hill radii of the step (reading R6: at |Q| of the state entering the
-    Kepler drift) agree with the oracle's to a few ulp (the device's cbrt
-    and the host's round differently); the records are compared with the
-    oracle run on the device's radii, so they stay comparable bit for bit."""
+    Kepler drift) agree with the oracle's to a few ulp (the device forms |Q|
+    with fused multiply-adds); the records are compared with the oracle run
+    on the device's radii, so they stay comparable bit for bit."""
     ref = oracle.hill_radii(w.m, q0, v0)
     body = np.ones(len(w.m), bool)
     body[w.offsets[:-1]] = False
