@@ -169,10 +169,10 @@ KEPLER_FP64_WARP_INST = {
 # with the splits. A shape or a kick source not captured reports null (the
 # capture commands sit with the ncu summaries under profiles/).
 KICK_DRAM_BYTES = {
-    ("disk_16384", 256, 64, "54c6f9e4161f1bc3"): 9.16e5,
-    ("disk_16384", 256, 128, "54c6f9e4161f1bc3"): 1.18e6,
-    ("disk_262144", 256, 64, "54c6f9e4161f1bc3"): 2.31e7,
-    ("disk_262144", 512, 64, "54c6f9e4161f1bc3"): 1.82e7,
+    ("disk_16384", 256, 64, "55ec22d21306f6b3"): 9.13e5,
+    ("disk_16384", 256, 128, "55ec22d21306f6b3"): 1.18e6,
+    ("disk_262144", 256, 64, "55ec22d21306f6b3"): 2.33e7,
+    ("disk_262144", 512, 64, "55ec22d21306f6b3"): 1.85e7,
 }
 
 

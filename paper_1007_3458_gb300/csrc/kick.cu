@@ -325,6 +325,12 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
         // rounded once the separation is within 4 2^-24 r (the row test's
         // own rounding is within its 2% margin).
         bool far = false;
+        // quiet (searching kick, far window): no pair of the window can be a
+        // candidate, as every row lies farther from the tile's box than its
+        // reach and the tile's largest one allow (r^2 >= c_i + c_max, with
+        // a 3% and an absolute margin for the FP32 box distance): the window
+        // takes the plain far form, with no search arithmetic
+        bool quiet = false;
         float2 dxi[IPT], dyi[IPT], dzi[IPT];
         float4 m0 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (a.far_tiles && !diag) {
@@ -332,16 +338,20 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
             m0 = tm[0];
             const float4 m1 = tm[1], m2 = tm[2];
             const float R = m0.w;
-            bool mine = true;
+            bool mine = true, calm = true;
 #pragma unroll
             for (int k = 0; k < IPT; ++k) {
                 const float x = -nxh[k].x, y = -nyh[k].x, z = -nzh[k].x;
                 const float ex = fmaxf(fmaxf(m1.x - x, x - m2.x), 0.0f);
                 const float ey = fmaxf(fmaxf(m1.y - y, y - m2.y), 0.0f);
                 const float ez = fmaxf(fmaxf(m1.z - z, z - m2.z), 0.0f);
-                mine = mine && (ex * ex + ey * ey + ez * ez >= 1.02f * R * R);
+                const float d2 = ex * ex + ey * ey + ez * ez;
+                mine = mine && (d2 >= 1.02f * R * R);
+                if (FLAG)
+                    calm = calm && (d2 >= 1.03f * (rho[k] + m1.w) + 1e-9f * (x * x + y * y + z * z));
             }
             far = __all_sync(0xffffffffu, mine);
+            if (FLAG) quiet = far && __all_sync(0xffffffffu, calm);
         }
         // which layouts this CTA's warps need
         const bool any_far = __syncthreads_or(far);
@@ -398,7 +408,9 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
                 fx[k] = fy[k] = fz[k] = make_float2(0.0f, 0.0f);
                 mind[k] = 3.0e38f;
             }
-            if (far)
+            if (quiet)
+                far_chunk<IPT, false, FORCE>(sf, c, ce, dxi, dyi, dzi, fx, fy, fz, mind);
+            else if (far)
                 far_chunk<IPT, FLAG, FORCE>(sf, c, ce, dxi, dyi, dzi, fx, fy, fz, mind);
             else if (diag)
                 mixed_chunk<IPT, FLAG, true, FORCE>(sp, c, ce, jt, gi, nxh, nyh, nzh, nxl, nyl, nzl,
@@ -627,11 +639,12 @@ static cudaError_t launch_f64(const KickArgs &a, int nitems, int threads, int ip
 // Per tile of TILE consecutive positions (from position 1; the bodies in
 // Morton order): the bounding box of the hi parts, a reference point c at its
 // middle, a radius R >= max |Q_j - c| (rounded up, with room for the lo parts
-// and the rounding of c), and each body's offset o_j = Q_j - c, rounded once
-// (two-sum of x_hi - c, then x_lo added), beside its G m.
+// and the rounding of c), the largest crude-search reach c_j of its bodies
+// (tile[1].w), and each body's offset o_j = Q_j - c, rounded once (two-sum of
+// x_hi - c, then x_lo added), beside its G m.
 __global__ void __launch_bounds__(TILE) k_tile_prep(int64_t npos, const float4 *pos,
                                                     const float4 *lo, float4 *far, float4 *tile) {
-    __shared__ float s_m[TILE / 32][6];
+    __shared__ float s_m[TILE / 32][7];
     __shared__ float s_c[3];
     const int64_t p = 1 + (int64_t)blockIdx.x * TILE + threadIdx.x;
     const bool act = p < npos;
@@ -640,16 +653,18 @@ __global__ void __launch_bounds__(TILE) k_tile_prep(int64_t npos, const float4 *
         P = pos[p];
         L = lo[p];
     }
-    float m[6] = {act ? P.x : 3e38f, act ? P.y : 3e38f, act ? P.z : 3e38f,
-                  act ? -P.x : 3e38f, act ? -P.y : 3e38f, act ? -P.z : 3e38f};
+    // (m[6]: minus the largest search reach c of the tile's bodies)
+    float m[7] = {act ? P.x : 3e38f, act ? P.y : 3e38f, act ? P.z : 3e38f,
+                  act ? -P.x : 3e38f, act ? -P.y : 3e38f, act ? -P.z : 3e38f,
+                  act ? -L.w : 3e38f};
 #pragma unroll
-    for (int q = 0; q < 6; ++q) m[q] = warp_min(m[q]);
+    for (int q = 0; q < 7; ++q) m[q] = warp_min(m[q]);
     if ((threadIdx.x & 31) == 0)
-        for (int q = 0; q < 6; ++q) s_m[threadIdx.x >> 5][q] = m[q];
+        for (int q = 0; q < 7; ++q) s_m[threadIdx.x >> 5][q] = m[q];
     __syncthreads();
     if (threadIdx.x == 0) {
-        float b[6];
-        for (int q = 0; q < 6; ++q) {
+        float b[7];
+        for (int q = 0; q < 7; ++q) {
             b[q] = s_m[0][q];
             for (int w = 1; w < TILE / 32; ++w) b[q] = fminf(b[q], s_m[w][q]);
         }
@@ -665,7 +680,7 @@ __global__ void __launch_bounds__(TILE) k_tile_prep(int64_t npos, const float4 *
         const float R = __fadd_ru(__fsqrt_ru(hr2), 4.0f * 1.1920929e-7f * big);
         float4 *t = tile + 3 * blockIdx.x;
         t[0] = make_float4(c[0], c[1], c[2], R);
-        t[1] = make_float4(b[0], b[1], b[2], 0.0f);
+        t[1] = make_float4(b[0], b[1], b[2], fmaxf(-b[6], 0.0f));
         t[2] = make_float4(-b[3], -b[4], -b[5], 0.0f);
     }
     __syncthreads();
