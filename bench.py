@@ -169,10 +169,10 @@ KEPLER_FP64_WARP_INST = {
 # with the splits. A shape or a kick source not captured reports null (the
 # capture commands sit with the ncu summaries under profiles/).
 KICK_DRAM_BYTES = {
-    ("disk_16384", 256, 64, "55ec22d21306f6b3"): 9.13e5,
-    ("disk_16384", 256, 128, "55ec22d21306f6b3"): 1.18e6,
-    ("disk_262144", 256, 64, "55ec22d21306f6b3"): 2.33e7,
-    ("disk_262144", 512, 64, "55ec22d21306f6b3"): 1.85e7,
+    ("disk_16384", 256, 64, "3d6b39905dba5b88"): 9.17e5,
+    ("disk_16384", 256, 128, "3d6b39905dba5b88"): 1.24e6,
+    ("disk_262144", 256, 64, "3d6b39905dba5b88"): 2.35e7,
+    ("disk_262144", 512, 64, "3d6b39905dba5b88"): 1.85e7,
 }
 
 

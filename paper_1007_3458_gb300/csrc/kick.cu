@@ -325,11 +325,12 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
         // rounded once the separation is within 4 2^-24 r (the row test's
         // own rounding is within its 2% margin).
         bool far = false;
-        // quiet (searching kick, far window): no pair of the window can be a
-        // candidate, as every row lies farther from the tile's box than its
-        // reach and the tile's largest one allow (r^2 >= c_i + c_max, with
-        // a 3% and an absolute margin for the FP32 box distance): the window
-        // takes the plain far form, with no search arithmetic
+        // quiet (searching kick, a window of another block's tile): no pair
+        // of the window can be a candidate, as every row lies farther from
+        // the tile's box than its reach and the tile's largest one allow
+        // (r^2 >= c_i + c_max, with a 3% and an absolute margin for the FP32
+        // box distance): the window takes the plain form, far or near, with
+        // no search arithmetic
         bool quiet = false;
         float2 dxi[IPT], dyi[IPT], dzi[IPT];
         float4 m0 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
                     calm = calm && (d2 >= 1.03f * (rho[k] + m1.w) + 1e-9f * (x * x + y * y + z * z));
             }
             far = __all_sync(0xffffffffu, mine);
-            if (FLAG) quiet = far && __all_sync(0xffffffffu, calm);
+            if (FLAG) quiet = __all_sync(0xffffffffu, calm);
         }
         // which layouts this CTA's warps need
         const bool any_far = __syncthreads_or(far);
@@ -408,10 +409,13 @@ __global__ void __launch_bounds__(256) k_kick_mixed(KickArgs a) {
                 fx[k] = fy[k] = fz[k] = make_float2(0.0f, 0.0f);
                 mind[k] = 3.0e38f;
             }
-            if (quiet)
+            if (far && quiet)
                 far_chunk<IPT, false, FORCE>(sf, c, ce, dxi, dyi, dzi, fx, fy, fz, mind);
             else if (far)
                 far_chunk<IPT, FLAG, FORCE>(sf, c, ce, dxi, dyi, dzi, fx, fy, fz, mind);
+            else if (quiet)
+                mixed_chunk<IPT, false, false, FORCE>(sp, c, ce, jt, gi, nxh, nyh, nzh, nxl, nyl,
+                                                      nzl, fx, fy, fz, mind);
             else if (diag)
                 mixed_chunk<IPT, FLAG, true, FORCE>(sp, c, ce, jt, gi, nxh, nyh, nzh, nxl, nyl, nzl,
                                                     fx, fy, fz, mind);
