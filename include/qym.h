@@ -323,7 +323,8 @@ qym_status qym_time_kick(qym_ctx *ctx, int32_t with_search, int32_t reps, double
  * (Q += (tau/2) S / m0 twice, the closing and the next opening half-drift,
  * then the kick's float packs) on the ctx stream, bracketed by CUDA events;
  * the drift reads a copy of the state and the state is put back afterwards.
- * *ms_momentum and *ms_drift get the mean launch times in milliseconds. */
+ * *ms_momentum and *ms_drift get the mean launch times in milliseconds.
+ * QYM_EINVAL for reps < 1, tau zero or not finite, or a NULL pointer. */
 qym_status qym_time_drift(qym_ctx *ctx, double tau, int32_t reps, double *ms_momentum,
                           double *ms_drift);
 
