@@ -343,6 +343,33 @@ def test_set_state_of_the_held_positions_keeps_the_fused_search(gpu):
     assert sb["encounters"] > 0
 
 
+def test_step_graphs_follow_tau(gpu):
+    """A call's steps are replayed from graphs captured for its tau: after
+    calls with tau, a call with tau / 2 on the same context gives the bits of
+    a fresh context started from the same state (no encounters, so the first
+    call's search makes no difference), and steps with -tau retrace the
+    plain DH step (time reversal to rounding)."""
+    w = W.disk_16384()
+    # democratic-heliocentric coordinates in and out: the state read back
+    # starts the fresh context bit for bit
+    a = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, encounters=0, coords=1)
+    a.step(w.tau, 3)
+    a.step(w.tau, 3)
+    qm, vm = a.state()
+    b = q.Simulation(w.m, qm, vm, w.offsets, eps_H=w.eps_H, encounters=0, coords=1)
+    for sim in (a, b):
+        sim.step(0.5 * w.tau, 4)
+    (qa, va), (qb, vb) = a.state(), b.state()
+    b.close()
+    assert np.array_equal(qa, qb) and np.array_equal(va, vb), (_relq(qa, qb).max(),
+                                                              _relq(va, vb).max())
+    a.step(-0.5 * w.tau, 4)
+    a.step(-w.tau, 6)
+    qr, vr = a.state()
+    a.close()
+    assert _relq(qr, w.q).max() <= 1e-11
+
+
 def test_time_drift_leaves_the_state(gpu):
     """qym_time_drift (E_Dft timed alone) puts the state back bit for bit, and
     the steps after it equal those without it; batches and single systems."""
