@@ -205,3 +205,23 @@ def test_escape_velocity_search(torch, oracle, prec, merge):
         got[name] = [tuple(x) for x in sim.encounters()]
         sim.close()
     assert got["fused"] == [(0, 1, 2)] and got["escape"] == [], got
+
+
+def test_snapshot_set_after_steps(torch, oracle):
+    """Snapshot arrays given to a context that has already replayed its step
+    graphs (captured without the snapshot copies) are filled from the next
+    call on: the graphs are captured again, and the records of that call's
+    last step equal the oracle's all-pairs test on the arrays' contents."""
+    w = W.crossers()
+    sim = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H)
+    sim.step(w.tau, 4)
+    sim.step(w.tau, 1)
+    snap = Snapshot(torch, sim, len(w.m))
+    for b in snap.b:
+        b.fill_(float("nan"))
+    sim.step(w.tau, 4)
+    q0, v0, q1, v1, rH = snap.host()
+    assert np.isfinite(q1).all() and np.isfinite(rH).all()
+    pairs, _, _ = oracle.encounters(q0, v0, q1, v1, rH, w.tau, w.a_E)
+    assert len(pairs) > 0 and np.array_equal(_last_step_records(sim, 4), pairs)
+    sim.close()
