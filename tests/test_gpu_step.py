@@ -370,6 +370,25 @@ def test_step_graphs_follow_tau(gpu):
     assert _relq(qr, w.q).max() <= 1e-11
 
 
+def test_step_graphs_follow_the_kick_shape(gpu):
+    """A launch shape set after steps were replayed from graphs is the one
+    the next call runs: the same bits as a fresh context started from the same
+    state with that shape."""
+    w = W.disk_16384()
+    a = q.Simulation(w.m, w.q, w.v, w.offsets, eps_H=w.eps_H, encounters=0, coords=1)
+    a.step(w.tau, 3)
+    qm, vm = a.state()
+    b = q.Simulation(w.m, qm, vm, w.offsets, eps_H=w.eps_H, encounters=0, coords=1)
+    for sim in (a, b):
+        q.qym_set_kick_shape(sim.ctx, 256, 1, 16)
+        sim.step(w.tau, 3)
+    (qa, va), (qb, vb) = a.state(), b.state()
+    assert a.stats()["kick_tile_splits"] == 16
+    a.close()
+    b.close()
+    assert np.array_equal(qa, qb) and np.array_equal(va, vb)
+
+
 def test_time_drift_leaves_the_state(gpu):
     """qym_time_drift (E_Dft timed alone) puts the state back bit for bit, and
     the steps after it equal those without it; batches and single systems."""
