@@ -313,3 +313,33 @@ def test_hermite_backward_returns_to_start(oracle):
     assert st1 == 0 and st2 == 0 and s1 > 5 and s2 > 5
     assert np.abs(qf - q).max() > 0.1
     assert np.abs(qb - q).max() < 1e-8 and np.abs(vb - v).max() < 1e-8
+
+
+def test_escape_flyby_meets_inside_the_threshold_beyond_the_escape_reach(oracle):
+    """The flyby of `workloads.escape_flyby` (a body at five times the escape
+    speed aimed at a planetesimal) is an encounter by the rigorous all-pairs
+    test of Sec. 2.4, while the pair starts farther apart than the escape
+    rule of that section reaches (a_E Hill radii plus the distance covered at
+    the escape velocity over the step, each body's own term, in the
+    r^2 < 2 rho_i^2 + 2 rho_j^2 form): the case the paper says its crude
+    sweep can miss. The straight-line construction is checked against the
+    Kepler flow: the closest approach over the step is within 1e-3 AU of the
+    aimed 0.005 AU."""
+    w = W.escape_flyby()
+    m, q = w.m, w.q
+    v = oracle.helio_to_dh(m, w.v)
+    r = oracle.step(m, q, v, w.offsets, w.tau, 1, oracle.params(eps_H=w.eps_H))
+    assert [tuple(x) for x in r.encounters] == [(0, 1, 2)]
+    rH = oracle.hill_radii(m, q, v)
+    rr = np.linalg.norm(q[1:], axis=1)
+    rho = w.a_E * rH[1:] + w.tau * np.sqrt(2.0 * m[0] / rr)
+    sep = np.linalg.norm(q[1] - q[2])
+    assert sep > 1.2 * np.sqrt(2 * rho[0] ** 2 + 2 * rho[1] ** 2)
+    # closest approach along the two Kepler orbits, sampled over the step
+    ts = np.linspace(0.0, w.tau, 2001)
+    d = []
+    for t in ts:
+        q1 = oracle.kepler_drift(q[1:2], w.v[1:2], m[0] + m[1], t)[0] if t > 0 else q[1:2]
+        q2 = oracle.kepler_drift(q[2:3], w.v[2:3], m[0] + m[2], t)[0] if t > 0 else q[2:3]
+        d.append(np.linalg.norm(q1[0] - q2[0]))
+    assert abs(min(d) - 0.005) < 1e-3, min(d)
