@@ -91,6 +91,16 @@ def test_argument_checks_without_gpu(lib):
     assert lib.qym_transition_dev(0, None, 1.0, None, None, None, None) == q.QYM_OK
     assert lib.qym_accel_workspace_bytes(1, 1) == 0
     assert lib.qym_accel_workspace_bytes(16385, 1) > 16385 * 3 * 8
+    # context calls refuse a NULL context or NULL outputs before any CUDA work
+    d = ctypes.c_double()
+    assert lib.qym_get_order(None, None) == q.QYM_EINVAL
+    assert lib.qym_time_drift(None, 1.0, 3, ctypes.byref(d), ctypes.byref(d)) == q.QYM_EINVAL
+    assert lib.qym_time_kick(None, 0, 3, ctypes.byref(d), None) == q.QYM_EINVAL
+    # the escape-velocity search is a valid mode; other values are refused
+    p = q.qym_default_params(search=7)
+    with pytest.raises(q.QymError) as e:
+        q.qym_init(p, [0, 2], [1.0, 1e-3], np.zeros((2, 3)), np.zeros((2, 3)))
+    assert e.value.status == q.QYM_EINVAL and "QYM_SEARCH_ESCAPE" in str(e.value)
 
 
 def test_mlp_layout_constants_agree():
